@@ -1,0 +1,294 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle itself.
+
+Each test names the passage of arXiv 2602.16797 (section, algorithm, fact or theorem) or the
+external definition it checks against. All run on the CPU (no GPU marker).
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2602_16797_gb300 import workloads as wl
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+U64 = 2.0 ** -53
+
+
+def _subspace_sin(V1, V2):
+    """Largest principal angle (its sine) between span(V1) and span(V2), both orthonormal."""
+    Q1, _ = np.linalg.qr(V1)
+    Q2, _ = np.linalg.qr(V2)
+    # ||(I - Q2 Q2^H) Q1||_2; sqrt(1 - cos^2) would lose half the digits
+    return float(np.linalg.norm(Q1 - Q2 @ (Q2.conj().T @ Q1), 2))
+
+
+def _distortion(A, S):
+    """Distortion eta of S on range(A) (Definition of a subspace embedding, Sec. 1.2):
+    the extreme squared singular values of S Q_A are 1 -+ eta."""
+    Q, _ = np.linalg.qr(A)
+    s = np.linalg.svd(S @ Q, compute_uv=False)
+    return float(max(s.max() ** 2 - 1.0, 1.0 - s.min() ** 2))
+
+
+# ---------------------------------------------------------------------------------------------
+# SplitMix64 and the SparseStack pattern (Sec. 2.2)
+# ---------------------------------------------------------------------------------------------
+
+def test_splitmix64_published_vectors():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "splitmix64.txt")) if l.strip() and l[0] != "#"]
+    assert len(rows) == 8
+    for seed, idx, out in rows:
+        got = int(oracle.splitmix64(int(seed), int(idx)))
+        assert got == int(out), (seed, idx)
+
+
+@pytest.mark.parametrize("m,d,zeta", [(500, 200, 8), (777, 1500, 8), (300, 37, 4), (64, 8, 8)])
+def test_sparse_stack_structure(m, d, zeta):
+    """Each column of S has exactly one +-zeta^{-1/2} in each of its zeta pieces, the pieces are
+    [floor(jd/zeta), floor((j+1)d/zeta)), and every column has unit norm (Sec. 2.2)."""
+    dest, sign = oracle.sparse_stack(m, d, zeta, seed=11)
+    b = np.array([(j * d) // zeta for j in range(zeta + 1)])
+    for j in range(zeta):
+        assert np.all(dest[:, j] >= b[j]) and np.all(dest[:, j] < b[j + 1])
+    assert set(np.unique(sign)) <= {1.0, -1.0}
+    S = oracle.sketch_dense_matrix(m, d, zeta, seed=11)
+    assert np.all(np.count_nonzero(S, axis=0) == zeta)
+    np.testing.assert_allclose(np.linalg.norm(S, axis=0), 1.0, rtol=0, atol=4 * U64)
+    assert np.all(np.abs(S[S != 0]) == 1.0 / np.sqrt(zeta))
+
+
+def test_sparse_stack_uniform_positions_and_signs():
+    """Positions are uniform inside each piece and signs are fair coins (chi-square / binomial
+    bounds at very small false-alarm probability); E[S^T S] = I off the diagonal."""
+    m, d, zeta = 200_000, 40, 4
+    dest, sign = oracle.sparse_stack(m, d, zeta, seed=3)
+    for j in range(zeta):
+        lo = (j * d) // zeta
+        counts = np.bincount(dest[:, j] - lo, minlength=d // zeta)
+        e = m / (d // zeta)
+        chi2 = float(((counts - e) ** 2 / e).sum())
+        assert chi2 < 60.0, chi2            # 9 dof: P(chi2 > 60) ~ 1e-9
+    frac = (sign > 0).mean()
+    assert abs(frac - 0.5) < 6 * 0.5 / np.sqrt(sign.size)
+    S = oracle.sketch_dense_matrix(4000, 64, 8, seed=5)
+    G = S.T @ S
+    off = G[~np.eye(G.shape[0], dtype=bool)]
+    assert abs(off.mean()) < 1e-3
+
+
+def test_sketch_matches_dense_S_on_integers():
+    """SA = S A exactly for small-integer A (all partial sums exact in float64)."""
+    rng = np.random.default_rng(0)
+    m, n, d, zeta = 700, 9, 40, 4
+    A = rng.integers(-50, 50, size=(m, n)).astype(np.float64)
+    S = oracle.sketch_dense_matrix(m, d, zeta, seed=9)
+    got = oracle.sketch(A, d, zeta, seed=9) * np.sqrt(zeta)
+    want = (S * np.sqrt(zeta)) @ A
+    assert np.array_equal(np.round(want), got)
+    Ac = A + 1j * rng.integers(-50, 50, size=(m, n))
+    gotc = oracle.sketch(Ac, d, zeta, seed=9) * np.sqrt(zeta)
+    assert np.array_equal(np.round((S * np.sqrt(zeta)) @ Ac.real), gotc.real)
+    assert np.array_equal(np.round((S * np.sqrt(zeta)) @ Ac.imag), gotc.imag)
+
+
+@pytest.mark.parametrize("precision,dt", [("f64", np.float64), ("f32", np.float32)])
+def test_sketch_sums_in_ascending_source_order(precision, dt):
+    """The documented summation order (ascending source row per destination, one scaling at the
+    end) holds bit for bit: compared with an explicit sequential loop."""
+    rng = np.random.default_rng(1)
+    m, n, d, zeta = 300, 5, 24, 3
+    A = rng.standard_normal((m, n)) * np.exp(rng.uniform(-20, 20, (m, 1)))
+    dest, sign = oracle.sparse_stack(m, d, zeta, seed=4)
+    acc = np.zeros((d, n), dtype=dt)
+    Aw = A.astype(dt)
+    for i in range(m):
+        for j in range(zeta):
+            acc[dest[i, j]] = acc[dest[i, j]] + dt(sign[i, j]) * Aw[i]
+    want = acc * dt(1.0 / np.sqrt(zeta))
+    got = oracle.sketch(A, d, zeta, seed=4, precision=precision)
+    assert got.dtype == dt
+    assert np.array_equal(got, want)
+
+
+# ---------------------------------------------------------------------------------------------
+# Sketch factorisation, preconditioner and start (Sec. 2.1, Sec. 3.1 Facts)
+# ---------------------------------------------------------------------------------------------
+
+def test_sketch_svd_is_svd_of_sketch():
+    """Sigma~ and V~ reproduce (SA)^H (SA) = V~ Sigma~^2 V~^H and R^H R of a Householder QR."""
+    rng = np.random.default_rng(2)
+    SA = rng.standard_normal((160, 40)) @ np.diag(np.logspace(0, -5, 40))
+    s, V = oracle.sketch_svd(SA)
+    assert np.all(np.diff(s) <= 0)
+    G = SA.T @ SA
+    np.testing.assert_allclose(V @ np.diag(s ** 2) @ V.T, G, atol=50 * U64 * s[0] ** 2)
+    R = oracle.householder_r(SA)
+    assert np.all(np.diag(R) >= 0) and np.allclose(np.tril(R, -1), 0)
+    np.testing.assert_allclose(R.T @ R, G, atol=50 * U64 * s[0] ** 2)
+
+
+@pytest.mark.parametrize("complex_", [False, True])
+def test_randomized_preconditioning_fact(complex_):
+    """Fact (randomized preconditioning, Sec. 3.1): with P = V~ Sigma~^{-1} the squared singular
+    values of A P lie in [1/(1+eta), 1/(1-eta)] for the measured distortion eta of S."""
+    rng = np.random.default_rng(5)
+    m, n, zeta = 3000, 40, 8
+    sigma = np.logspace(0, -9, n)
+    A, _, _ = wl.planted(rng, m, sigma, complex_=complex_)
+    d = 16 * n        # d = 4n gives eta ~ 1 in this squared-norm definition; the Fact needs eta < 1
+    S = oracle.sketch_dense_matrix(m, d, zeta, seed=21)
+    eta = _distortion(A, S)
+    assert 0 < eta < 1
+    s, V = oracle.sketch_svd(oracle.sketch(A, d, zeta, seed=21))
+    P = V / s[None, :]
+    sv = np.linalg.svd(A @ P, compute_uv=False)
+    slack = 1e-6      # the rounding of a kappa = 1e9 problem
+    assert sv.max() ** 2 <= 1.0 / (1.0 - eta) + slack
+    assert sv.min() ** 2 >= 1.0 / (1.0 + eta) - slack
+    # sharper: the singular values of A P are exactly the reciprocals of those of S Q_A
+    Q, _ = np.linalg.qr(A)
+    ssq = np.linalg.svd(S @ Q, compute_uv=False)
+    np.testing.assert_allclose(np.sort(sv), np.sort(1.0 / ssq), rtol=1e-6)
+
+
+def test_sketch_and_solve_fact():
+    """Fact (sketch-and-solve, Sec. 3.1): v0 = P e_n / ||P e_n|| satisfies
+    ||A v0||^2 <= (1+eta)/(1-eta) sigma_min(A)^2."""
+    rng = np.random.default_rng(6)
+    m, n, zeta = 4000, 50, 8
+    sigma = np.concatenate([np.logspace(0, -3, n - 1), [1e-5]])
+    A, s_true, _ = wl.planted(rng, m, sigma)
+    d = 16 * n
+    S = oracle.sketch_dense_matrix(m, d, zeta, seed=8)
+    eta = _distortion(A, S)
+    assert eta < 1
+    s, V = oracle.sketch_svd(oracle.sketch(A, d, zeta, seed=8))
+    v0 = V[:, -1]
+    lhs = np.linalg.norm(A @ v0) ** 2
+    assert lhs <= (1 + eta) / (1 - eta) * s_true[-1] ** 2 * (1 + 1e-8)
+
+
+# ---------------------------------------------------------------------------------------------
+# The full method against closed forms and dense SVD
+# ---------------------------------------------------------------------------------------------
+
+def test_planted_small_workload():
+    """4000 x 50, sigma_50 = 1e-10: converges to the planted sigma and vector within the
+    backward-stable floors u sigma_1/sigma_min (value) and u/gap_abs (vector) (Sec. 4)."""
+    A, s, V = wl.planted_small_gap_free()
+    r = oracle.rlobpcg(A, k=1, zeta=8, seed=7)
+    assert r["stop_reason"] == "converged"
+    rel = abs(r["sigma"][0] - s[-1]) / s[-1]
+    assert rel < 10 * U64 * s[0] / s[-1]
+    gap_abs = (s[-2] - s[-1]) / s[0]
+    assert _subspace_sin(r["V"], V[:, -1:]) < 10 * U64 / gap_abs
+    # invariants: ||A v|| = sigma, unit v, residual below the sketched tolerance at stop
+    np.testing.assert_allclose(np.linalg.norm(A @ r["V"][:, 0]), r["sigma"][0], rtol=1e-5)
+    np.testing.assert_allclose(np.linalg.norm(r["V"][:, 0]), 1.0, atol=1e-14)
+    assert r["resid"][0] <= r["sigma11"] ** 2 * oracle.default_tau(50)
+
+
+@pytest.mark.parametrize("complex_", [False, True])
+def test_block_planted_cluster(complex_):
+    """Block version (Alg. 2), k = b = 3 with a clustered bottom: the 3-dim subspace and all three
+    values match the planted ones; V^H V = I and ||A v_j|| = sigma_j."""
+    rng = np.random.default_rng(12)
+    n, k = 45, 3
+    sigma = np.concatenate([np.logspace(0, -4, n - k), [3e-9, 2e-9, 1e-9]])
+    A, s, V = wl.planted(rng, 3000, sigma, complex_=complex_)
+    # the per-column stagnation checks rarely all hold at once for b = 3 (Sec. 4.2 notes that
+    # larger blocks forestall termination), so cap the run; the accuracy is what is pinned
+    r = oracle.rlobpcg(A, k=k, seed=3, max_iter=40)
+    np.testing.assert_allclose(r["sigma"], s[::-1][:k], rtol=20 * U64 * s[0] / s[-1])
+    gap_abs = (s[-k - 1] - s[-k]) / s[0]
+    assert _subspace_sin(r["V"], V[:, -k:]) < 20 * U64 / gap_abs
+    np.testing.assert_allclose(r["V"].conj().T @ r["V"], np.eye(k), atol=1e-13)
+    np.testing.assert_allclose(np.linalg.norm(A @ r["V"], axis=0), r["sigma"], rtol=1e-5)
+
+
+def test_dense_svd_agreement():
+    """Well-conditioned small case: sigma to 1e-10 relative and the subspace to 1e-8 against
+    LAPACK's dense SVD of A."""
+    rng = np.random.default_rng(13)
+    A = rng.standard_normal((1500, 36)) @ np.diag(np.linspace(1, 3, 36))
+    r = oracle.rlobpcg(A, k=2, seed=1)
+    _, s, Vh = np.linalg.svd(A, full_matrices=False)
+    np.testing.assert_allclose(r["sigma"], s[::-1][:2], rtol=1e-10)
+    assert _subspace_sin(r["V"], Vh.T[:, -2:]) < 1e-8
+
+
+def test_exact_nullspace():
+    """A = B C with B 3000 x 57, C 57 x 60: V spans null(C) and ||A V|| is at rounding level."""
+    A, C = wl.exact_nullspace(seed=5, m=3000, n=60, rank=57)
+    r = oracle.rlobpcg(A, k=3, d=3 * 60, seed=2)
+    _, _, Vh = np.linalg.svd(C)
+    null = Vh.conj().T[:, 57:]
+    assert _subspace_sin(r["V"], null) < 1e-10
+    nA = np.linalg.norm(A, 2)
+    assert np.linalg.norm(A @ r["V"], 2) < 100 * U64 * nA * np.sqrt(60)
+
+
+def test_loewner_backward_error():
+    """Loewner matrix (Sec. 5 family): sigma_min is at noise level, so only the backward error
+    ||L V|| <= c u ||L||_F and orthonormality are pinned (parity unpinned in sigma and V)."""
+    L = wl.loewner(seed=4, m=2500, n=40)
+    r = oracle.rlobpcg(L, k=2, seed=6)
+    assert np.linalg.norm(L @ r["V"], 2) <= 50 * U64 * np.linalg.norm(L) * np.sqrt(40)
+    np.testing.assert_allclose(r["V"].T @ r["V"], np.eye(2), atol=1e-13)
+
+
+def test_theorem1_geometric_rate():
+    """Theorem 1: when eta < gap/(2+gap), (||A v_k||^2 - sigma_n^2)/sigma_n^2 <= C gap q^{2k}
+    with q = eta + (1-eta)/(1+gap) and C = 2 eta / ((1-eta) gap - 2 eta)."""
+    rng = np.random.default_rng(21)
+    m, n, zeta = 4000, 40, 8
+    s_n, gap = 1e-2, 3.0
+    sigma = np.concatenate([np.geomspace(1.0, 0.1, n - 2), [s_n * np.sqrt(1 + gap), s_n]])
+    A, _, _ = wl.planted(rng, m, sigma)
+    d = 12 * n
+    S = oracle.sketch_dense_matrix(m, d, zeta, seed=14)
+    eta = _distortion(A, S)
+    assert eta < gap / (2 + gap)
+    q = eta + (1 - eta) / (1 + gap)
+    Cc = 2 * eta / ((1 - eta) * gap - 2 * eta)
+    r = oracle.rlobpcg(A, k=1, d=d, zeta=zeta, seed=14, fixed_iters=12)
+    thetas = np.concatenate([r["theta0"][-1:], r["theta_hist"][1:, -1]])
+    floor = 100 * U64 * (sigma[0] / s_n) ** 2
+    for kk, th in enumerate(thetas):
+        lhs = (th ** 2 - s_n ** 2) / s_n ** 2
+        assert lhs <= Cc * gap * q ** (2 * kk) + floor, (kk, lhs)
+
+
+# ---------------------------------------------------------------------------------------------
+# Stopping rule on hand-worked histories (Sec. 2.1)
+# ---------------------------------------------------------------------------------------------
+
+def _hist(vals_by_t):
+    return [np.array([v]) for v in vals_by_t]
+
+
+def test_stop_rule_hand_worked():
+    inf = np.inf
+    # residual norms r_0..r_11 and estimates theta_0 (= inf) .. theta_11
+    r = _hist([1.0, .5, .4, .3, .2, .1, 1e-20, 1e-20, 1e-20, 1e-20, 1e-20, 1e-20])
+    th_stag = _hist([inf, 4.0, 3.9, 3.5, 3.2, 3.1, 3.0, 2.8, 2.5, 2.2, 2.1, 2.0])
+    th_conv = _hist([inf, 4.0, 3.0, 2.7, 2.4, 2.2, 2.0, 1.9, 1.8, 1.7, 1.6, 1.5])
+    # i = 10: tol (1e-20 <= 1 * 1e-16), stag1 (1.1e-20 >= r_6 = 1e-20),
+    # stag2: 1.1 (3.0 - 2.0)/2.0 = 0.55 >= (4.0 - 3.0)/3.0 = 0.333 -> stop
+    assert oracle.stop_check(10, r, th_stag, 1.0, 1e-16, True) == (True, True, True)
+    # stag2: 1.1 (2.0 - 1.5)/1.5 = 0.367 < (4.0 - 2.0)/2.0 = 1.0 -> keep going
+    assert oracle.stop_check(10, r, th_conv, 1.0, 1e-16, True) == (True, True, False)
+    # i = 5: theta_{-4} does not exist (+inf) -> stag2 false; r_1 = 0.5 > 1.1 r_6 -> stag1 false
+    assert oracle.stop_check(5, r, th_stag, 1.0, 1e-16, True) == (True, False, False)
+    # tolerance scaled by Sigma~(1,1)^2: 1e-20 > 1e-4^2 * 1e-16
+    assert oracle.stop_check(10, r, th_stag, 1e-4, 1e-16, True)[0] is False
+    # without stagnation checks only the tolerance counts
+    assert oracle.stop_check(0, _hist([1.0, 1e-20]), _hist([inf, 1.0]), 1.0, 1e-16, False) == (True, True, True)
+
+
+def test_earliest_stagnation_stop_is_iteration_10():
+    """With stagnation checks on, no stop can happen before i = 10 (11 iterations)."""
+    A, _, _ = wl.planted_small_gap_free(m=2000, n=30)
+    r = oracle.rlobpcg(A, k=1, seed=1)
+    assert r["iters"] >= 11 and (r["iters"] - 1) % 5 == 0
