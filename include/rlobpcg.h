@@ -1,0 +1,191 @@
+/*
+ * rlobpcg.h -- C ABI of the GB300 (sm_103a) RLOBPCG library.
+ *
+ * RLOBPCG (Epperly, Park & Nakatsukasa, "Fast, high-accuracy, randomized nullspace computations
+ * for tall matrices", arXiv 2602.16797) computes the k smallest singular values of a tall matrix
+ * A (m x n, m >> n >> 1) and their right singular vectors (Sec. 1): a SparseStack sketch SA
+ * (Sec. 2.2) gives a preconditioner and a starting block, then block LOBPCG on A^H A refines them
+ * (Algorithm 2; Algorithm 1 is its b = 1 case).
+ *
+ * Conventions for every entry point:
+ *   - Matrices are dense. A is row-major with leading dimension lda >= n (element (i,j) at
+ *     A[i*lda + j]). Complex data is interleaved (re, im) pairs of doubles (numpy complex128).
+ *   - "device" pointers must be CUDA device (or managed) memory; entry points documented as
+ *     accepting host or device pointers detect which through unified addressing.
+ *   - The caller owns every pointer it passes; the library never frees or keeps them past the
+ *     call, except a plan, which owns its workspace until rlobpcg_plan_destroy.
+ *   - Work is issued on the CUDA stream given at plan time (or per call); entry points return
+ *     after the stream has finished unless stated otherwise.
+ *   - Return value: RLOBPCG_OK (0), a positive warning, or a negative error code.
+ *     rlobpcg_status_string() names it; rlobpcg_last_error() gives the detail of the last error.
+ */
+#ifndef RLOBPCG_H
+#define RLOBPCG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------------------------- */
+#define RLOBPCG_OK 0
+#define RLOBPCG_NOT_CONVERGED 1      /* max_iter reached; outputs hold the last (best) iterate  */
+#define RLOBPCG_ERR_INVALID_ARG (-1) /* bad size, pointer, leading dimension or option           */
+#define RLOBPCG_ERR_OOM (-2)         /* device allocation failed                                  */
+#define RLOBPCG_ERR_CUDA (-3)        /* a CUDA runtime call failed (detail in rlobpcg_last_error) */
+#define RLOBPCG_ERR_NONFINITE (-4)   /* NaN or Inf met in A or in the iteration                   */
+#define RLOBPCG_ERR_TIMEOUT (-5)     /* a bounded device-side wait ran out                        */
+#define RLOBPCG_ERR_UNSUPPORTED (-6) /* shape outside what the kernels handle                     */
+
+/* ---- element types ------------------------------------------------------------------------ */
+#define RLOBPCG_F64 0   /* real double                                */
+#define RLOBPCG_C128 1  /* complex double, interleaved (re, im)       */
+
+/* Precision of the sketch SA, its QR factor R, the SVD of R and R^{-1}. The Gram products,
+ * residuals, Rayleigh-Ritz and orthogonalisation are always FP64 / complex128. */
+#define RLOBPCG_SKETCH_F64 0
+#define RLOBPCG_SKETCH_F32 1
+
+/* Stop reasons reported in rlobpcg_info.stop_reason */
+#define RLOBPCG_STOP_CONVERGED 0   /* sketched tolerance (+ stagnation checks) held (Sec. 2.1)   */
+#define RLOBPCG_STOP_MAX_ITER 1    /* iteration cap (Alg. 1: 200 for b = 1, Alg. 2: 100)         */
+#define RLOBPCG_STOP_FIXED 2       /* fixed_iters iterations were run on request                 */
+
+/* Options. rlobpcg_default_opts fills the paper's defaults (Sec. 2.1-2.2). */
+typedef struct {
+  uint64_t seed;        /* seed of the SparseStack SplitMix64 stream                               */
+  int d;                /* sketch rows; 0 means 4n (Alg. 2 uses 4n, Sec. 2.2 suggests 2n..4n)      */
+  int zeta;             /* nonzeros per column of S (8 by default; Alg. 2 uses 4)                  */
+  int block;            /* block size b >= k; 0 means b = k                                        */
+  int max_iter;         /* 0 means 200 when b = 1 (Alg. 1) and 100 otherwise (Alg. 2)              */
+  int check_every;      /* stop-test period; 0 means 5 with stagnation checks, 1 without           */
+  int use_stagnation;   /* 1: also require the stagnation checks of Sec. 2.1 (default)             */
+  int sketch_prec;      /* RLOBPCG_SKETCH_F64 (default) or RLOBPCG_SKETCH_F32                      */
+  int fixed_iters;      /* > 0: run exactly this many iterations, no stop test (parity runs)       */
+  int residual_refresh_every; /* > 0: every this many iterations recompute A^H (A V) with a pass
+                                 over A instead of the recombined A^H A V (drift control)         */
+  double tau;           /* tolerance of ||R(:,j)|| <= Sigma~(1,1)^2 tau; < 0 means 2 sqrt(n) 2^-52 */
+} rlobpcg_opts;
+
+/* Per-solve report. */
+typedef struct {
+  int iters;            /* LOBPCG iterations run                                                   */
+  int matvecs;          /* columns multiplied by A (b per iteration plus the start block)           */
+  int stop_reason;      /* RLOBPCG_STOP_*                                                           */
+  int block;            /* block size b used                                                       */
+  double sigma11;       /* Sigma~(1,1), the sketch's estimate of ||A|| used by the stop rule         */
+  double ms_sketch;     /* device time of the sketch                                               */
+  double ms_factor;     /* QR of SA, SVD of R, R^{-1}, start block                                 */
+  double ms_iterate;    /* LOBPCG iterations                                                       */
+  double ms_total;      /* whole solve, including host<->device copies done by the call            */
+} rlobpcg_info;
+
+typedef struct rlobpcg_plan_s* rlobpcg_plan_t;
+
+/* Fill *opts with the defaults described above. Returns RLOBPCG_OK, or INVALID_ARG for NULL. */
+int rlobpcg_default_opts(rlobpcg_opts* opts);
+
+/*
+ * Create a plan for solves of m x n matrices (dtype RLOBPCG_F64 or RLOBPCG_C128) asking for the
+ * k smallest singular triplets. Allocates all device workspace the solve needs (its size grows
+ * as (m + n) * 3b plus d * n and n * n elements), so solve() itself allocates nothing unless it
+ * is given host pointers. `stream` is a cudaStream_t (NULL = default stream).
+ * Errors: INVALID_ARG when k < 1, b < k, 3b > n, n > m, d < n, d < zeta or zeta < 1;
+ * OOM when the workspace does not fit; CUDA for runtime failures.
+ */
+int rlobpcg_plan(rlobpcg_plan_t* out, int64_t m, int64_t n, int k, int dtype,
+                 const rlobpcg_opts* opts, void* stream);
+
+/*
+ * Solve (Algorithm 2): sketch, factorise, start block, LOBPCG iterations, outputs.
+ *   A      m x n, leading dimension lda >= n, host or device memory, not modified. Host memory is
+ *          copied to a plan-owned device buffer first (allocated on first use).
+ *   tol    tolerance tau of the sketched stopping rule (Sec. 2.1); tol < 0 keeps the plan's.
+ *   sigma  k doubles, ascending: the k smallest singular value estimates.
+ *   V      n x k (row-major, leading dimension k) right singular vectors in the dtype of A,
+ *          column j belonging to sigma[j].
+ *   U      m x k (row-major, leading dimension k) left vectors A V diag(sigma)^{-1}, or NULL.
+ *          Entries are Inf/NaN-free only when sigma[j] > 0; a sigma at rounding level gives a
+ *          meaningless column.
+ *   resid  k doubles: ||A^H A v_j - sigma_j^2 v_j||, or NULL.
+ *   info   per-solve report, or NULL.
+ * sigma, V, U and resid may each be host or device memory. Returns OK, NOT_CONVERGED (outputs
+ * valid), or an error (outputs undefined).
+ */
+int rlobpcg_solve(rlobpcg_plan_t plan, const void* A, int64_t lda, double tol, double* sigma,
+                  void* V, void* U, double* resid, rlobpcg_info* info);
+
+/* Release a plan and its device workspace. NULL is accepted. */
+int rlobpcg_plan_destroy(rlobpcg_plan_t plan);
+
+/* Static string naming a status code. */
+const char* rlobpcg_status_string(int status);
+
+/* Detail of the most recent error in this thread (static storage, overwritten by the next one). */
+const char* rlobpcg_last_error(void);
+
+/* ---- single steps of the path, for callers that compose their own loop (and for tests) ---- */
+
+/*
+ * Sketch SA = S A with the SparseStack S of Sec. 2.2 (d rows, zeta nonzeros per column, seeded
+ * SplitMix64: entry (row i, piece j) uses output number i*zeta + j; position inside piece j =
+ * floor((h >> 32) * len_j / 2^32) with piece j = rows [floor(j d/zeta), floor((j+1) d/zeta));
+ * sign -1 when bit 0 of h is set; values +-zeta^{-1/2}). Each output entry is summed over its
+ * source rows in ascending order and scaled once at the end, so results are reproducible bit
+ * for bit.
+ *   A   device, m x n row-major (lda), dtype F64 or C128.
+ *   SA  device, d x n COLUMN-major (element (r, j) at SA[j*d + r]); float/complex64 when
+ *       sketch_prec is RLOBPCG_SKETCH_F32, double/complex128 otherwise.
+ * Allocates nothing. Errors: INVALID_ARG (d < zeta, zeta < 1, lda < n, NULL pointers).
+ */
+int rlobpcg_sketch(const void* A, int64_t m, int64_t n, int64_t lda, int dtype, int d, int zeta,
+                   uint64_t seed, int sketch_prec, void* SA, void* stream);
+
+/*
+ * Factorise the sketch (Alg. 2, second and third lines): Householder QR SA = QR (Q discarded),
+ * the SVD R = U~ Sigma~ V~^H by one-sided Jacobi, and R^{-1}. Since SVD(SA) = SVD(R), Sigma~ and
+ * V~ are those of SA, and P P^* = V~ Sigma~^{-2} V~^H = (R^H R)^{-1}.
+ *   SA     device, d x n column-major in the sketch precision (overwritten by the QR).
+ *   R      device, n x n column-major upper triangular (strict lower part zero), or NULL.
+ *   sigma  device, n doubles, Sigma~ descending.
+ *   Vt     device, n x n column-major V~ (column j belongs to sigma[j]) in the sketch precision.
+ *   Rinv   device, n x n row-major R^{-1} in the sketch precision, or NULL.
+ *   work   device scratch of rlobpcg_factor_workspace_size(d, n, dtype, sketch_prec) bytes.
+ * Errors: INVALID_ARG (d < n), TIMEOUT (never in practice: no waits), CUDA.
+ */
+int rlobpcg_factor(void* SA, int64_t d, int64_t n, int dtype, int sketch_prec, void* R,
+                   double* sigma, void* Vt, void* Rinv, void* work, size_t work_bytes,
+                   void* stream);
+size_t rlobpcg_factor_workspace_size(int64_t d, int64_t n, int dtype, int sketch_prec);
+
+/*
+ * Fused Gram pass (the product of Alg. 2 with the trial block): one read of A gives
+ *   AW = A W      (m x b, row-major, leading dimension ldaw)
+ *   G  = A^H AW   (n x b, row-major, leading dimension ldg)
+ * W is n x b row-major (ldw). All device memory, dtype F64 or C128. Rows of A are split over
+ * the SMs and the per-SM partial G's are summed in a fixed order (results are deterministic).
+ *   work  device scratch of rlobpcg_gram_workspace_size(m, n, b, dtype) bytes.
+ * Errors: INVALID_ARG (b < 1, b > 64, leading dimensions too small), UNSUPPORTED (n * b too large
+ * for on-chip accumulation), CUDA.
+ */
+int rlobpcg_gram(const void* A, int64_t m, int64_t n, int64_t lda, int dtype, const void* W, int b,
+                 int64_t ldw, void* AW, int64_t ldaw, void* G, int64_t ldg, void* work,
+                 size_t work_bytes, void* stream);
+size_t rlobpcg_gram_workspace_size(int64_t m, int64_t n, int b, int dtype);
+
+/*
+ * R factor of a tall block (the TSQR used for Rayleigh-Ritz by SVD of A_T, Alg. 2): X is m x c
+ * row-major (ldx), c <= 64; R (c x c, row-major, upper triangular, diag(R) real >= 0) is written
+ * to device memory. Householder reflections per row block, then a fixed-order tree of stacked
+ * R factors.  work: rlobpcg_tsqr_workspace_size(m, c, dtype) bytes of device scratch.
+ */
+int rlobpcg_tsqr(const void* X, int64_t m, int c, int64_t ldx, int dtype, void* R, void* work,
+                 size_t work_bytes, void* stream);
+size_t rlobpcg_tsqr_workspace_size(int64_t m, int c, int dtype);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RLOBPCG_H */

@@ -1,0 +1,722 @@
+// The per-iteration kernels around the Gram pass (Alg. 2 of arXiv 2602.16797):
+//   * TSQR: R factor of A_T = [A_V A_W A_X] (m x c) -- Rayleigh-Ritz needs SVD(A_T), and
+//     SVD(A_T) = SVD(R_T) on the right, without ever forming A_T^H A_T (which would square the
+//     condition number and wipe out sigma ~ 1e-10 ||A||).
+//   * rr_small: one-sided Jacobi SVD of R_T (c x c), Theta descending, and the coefficient block
+//     K = [C_s | C(:, 1:c-b) Q] with Q = Orth(C(1:b, 1:c-b)^H) (the x-trick of Sec. 2.1).
+//   * update: [V X] <- T K, [A_V A_X] <- A_T K, [G_V G_X] <- G_T K in place, row by row.
+//   * residual: R = G_V - V Theta_s^2, its column norms, and R / ||R(:,j)|| in the sketch
+//     precision for the preconditioner.
+//   * precondition: W = R^{-1} (R^{-H} R~) (= P P^* R~ with P = V~ Sigma~^{-1}).
+//   * bcgs2_orth: W <- W - [V X]([V X]^H W) twice, then Orth(W) (thin Householder Q with
+//     diag(R) real non-negative).
+// State layout: T, A_T and G_T are row-major with leading dimension 3b and column blocks
+// [V | W | X] (X absent, i.e. c = 2b, in iteration 0).
+#include "common.cuh"
+
+namespace rl {
+
+namespace {
+
+__device__ inline double sqrt_(double a) { return sqrt(a); }
+__device__ inline float sqrt_(float a) { return sqrtf(a); }
+__device__ inline double hypot_(double a, double b) { return hypot(a, b); }
+__device__ inline double recip_(double a) { return 1.0 / a; }
+__device__ inline cd recip_(cd a) { double s = a.x * a.x + a.y * a.y; return {a.x / s, -a.y / s}; }
+__device__ inline float recip_(float a) { return 1.0f / a; }
+__device__ inline cf recip_(cf a) { float s = a.x * a.x + a.y * a.y; return {a.x / s, -a.y / s}; }
+
+// Householder scalars (LAPACK larfg convention) from alpha = x(0) and ||x(1:)||^2:
+// beta = -sign(Re alpha) ||x||, tau = (beta - alpha)/beta, v = [1; x(1:) / (alpha - beta)].
+// tau = 0 (H = I) when x(1:) = 0 and alpha is real.
+template <class T>
+__device__ inline void householder_scalars(T alpha, double xnorm2, T* tau, T* beta, T* inv_ab) {
+  if (xnorm2 == 0.0 && im_(alpha) == 0.0) {
+    *tau = zero_<T>(); *beta = alpha; *inv_ab = zero_<T>();
+    return;
+  }
+  const double bn = sqrt(abs2_(alpha) + xnorm2);
+  const double bb = re_(alpha) >= 0.0 ? -bn : bn;
+  *beta = from_real<T>(bb);
+  *tau = scale_(sub_(*beta, alpha), 1.0 / bb);
+  *inv_ab = recip_(sub_(alpha, *beta));
+}
+
+// ------------------------------------------------------------------------------------------
+// TSQR level: CTA i reduces rows [i*rpc, min((i+1)*rpc, rows)) of X (row-major, ldx, c cols)
+// to a c x c upper-triangular R by Householder steps on [R_running; next chunk].
+// Thread (column cc, row phase p): cc = tid % CP, p = tid / CP, CP = pow2 >= c.
+// ------------------------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(256) tsqr_level_kernel(const T* __restrict__ X, int64_t rows, int c, int64_t ldx,
+                                                          int64_t rpc, int CH, int CP, T* __restrict__ Rout) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int NT = blockDim.x;
+  const int RP = NT / CP;
+  const int tid = threadIdx.x, cc = tid % CP, p = tid / CP;
+  const int SR = c + CH;                       // stacked rows
+  T* S = reinterpret_cast<T*>(smem_raw);       // SR x c row-major
+  T* part = S + (size_t)SR * c;                // CP x RP partials
+  T* sv = part + (size_t)CP * RP;              // c values s_cc
+  __shared__ T sh_tau, sh_inv;
+
+  const int64_t r_begin = (int64_t)blockIdx.x * rpc;
+  const int64_t r_end = min(rows, r_begin + rpc);
+  for (int i = tid; i < c * c; i += NT) S[i] = zero_<T>();
+  for (int64_t r0 = r_begin; r0 < r_end || r0 == r_begin; r0 += CH) {
+    const int nr = (int)imax<int64_t>(0, imin<int64_t>(CH, r_end - r0));
+    // keep the upper triangle of the running R, load the next chunk below it
+    for (int i = tid; i < c * c; i += NT) {
+      const int r = i / c, q = i % c;
+      if (q < r) S[i] = zero_<T>();
+    }
+    for (int i = tid; i < CH * c; i += NT) {
+      const int r = i / c, q = i % c;
+      S[(size_t)(c + r) * c + q] = (r < nr) ? X[(r0 + r) * ldx + q] : zero_<T>();
+    }
+    __syncthreads();
+    for (int j = 0; j < c; ++j) {
+      // d_cc = sum_{r > j} conj(S[r][j]) S[r][cc] for cc >= j (cc == j gives ||x(1:)||^2)
+      if (cc < c && cc >= j) {
+        T acc = zero_<T>();
+        for (int r = j + 1 + p; r < SR; r += RP) acc = madc_(S[(size_t)r * c + j], S[(size_t)r * c + cc], acc);
+        part[cc * RP + p] = acc;
+      }
+      __syncthreads();
+      if (p == 0 && cc < c && cc >= j) {
+        T dj = part[j * RP];
+        for (int q = 1; q < RP; ++q) dj = add_(dj, part[j * RP + q]);
+        T tau, beta, inv_ab;
+        householder_scalars(S[(size_t)j * c + j], re_(dj), &tau, &beta, &inv_ab);
+        if (cc == j) {
+          sh_tau = tau; sh_inv = inv_ab;
+          sv[j] = beta;
+        } else {
+          T dc = part[cc * RP];
+          for (int q = 1; q < RP; ++q) dc = add_(dc, part[cc * RP + q]);
+          // s = v^H S(:, cc) = S[j][cc] + conj(1/(alpha-beta)) d_cc
+          sv[cc] = add_(S[(size_t)j * c + cc], mul_(conj_(inv_ab), dc));
+        }
+      }
+      __syncthreads();
+      const T tau = sh_tau, inv_ab = sh_inv;
+      if (cc < c && cc > j) {
+        const T f = mul_(conj_(tau), sv[cc]);
+        if (p == 0) S[(size_t)j * c + cc] = sub_(S[(size_t)j * c + cc], f);
+        for (int r = j + 1 + p; r < SR; r += RP) {
+          const T vr = mul_(S[(size_t)r * c + j], inv_ab);
+          S[(size_t)r * c + cc] = sub_(S[(size_t)r * c + cc], mul_(vr, f));
+        }
+      }
+      __syncthreads();
+      if (tid == 0) S[(size_t)j * c + j] = sv[j];
+      // column j below the diagonal is now dead (Q is not formed)
+      for (int r = j + 1 + tid; r < SR; r += NT) S[(size_t)r * c + j] = zero_<T>();
+      __syncthreads();
+    }
+    if (r_end <= r_begin) break;
+  }
+  T* out = Rout + (size_t)blockIdx.x * c * c;
+  for (int i = tid; i < c * c; i += NT) {
+    const int r = i / c, q = i % c;
+    out[i] = (q >= r) ? S[i] : zero_<T>();
+  }
+}
+
+// scale rows of a c x c R so that diag(R) is real and non-negative
+template <class T>
+__global__ void r_phase_fix_kernel(T* R, int c) {
+  const int r = blockIdx.x;
+  const T ph = conj_(phase_(R[(size_t)r * c + r]));
+  for (int q = threadIdx.x; q < c; q += blockDim.x) R[(size_t)r * c + q] = mul_(ph, R[(size_t)r * c + q]);
+}
+
+// ------------------------------------------------------------------------------------------
+// rr_small: one CTA. X = R_T (c x c) column-major in smem, V = I; one-sided Jacobi, one warp
+// per pair (round-robin), __syncthreads per round. Then Theta (descending, stable), C, and
+// K = [C_s | C(:,1:c-b) Q] with Q = Orth(C(1:b,1:c-b)^H).
+// Outputs: theta (c, descending), K (c x 2b row-major), sweeps.
+// ------------------------------------------------------------------------------------------
+__device__ inline int rr_slot(int k, int r, int N) { return k == 0 ? 0 : ((k - 1 + r) % (N - 1)) + 1; }
+
+template <class T>
+__global__ void __launch_bounds__(1024) rr_small_kernel(const T* __restrict__ Rt, int c, int b, double* theta_out,
+                                                         T* K_out, int* info) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* X = reinterpret_cast<T*>(smem_raw);        // c x c col-major
+  T* V = X + c * c;                             // c x c col-major
+  T* C = V + c * c;                             // c x c col-major (sorted)
+  T* Qm = C + c * c;                            // (c-b) x b col-major
+  double* nrm = reinterpret_cast<double*>(Qm + c * b);
+  int* rank = reinterpret_cast<int*>(nrm + c);
+  __shared__ int changed;
+  __shared__ T tau_s[64];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarp = blockDim.x >> 5;
+
+  for (int i = tid; i < c * c; i += blockDim.x) {
+    const int col = i / c, row = i % c;
+    X[i] = Rt[(size_t)row * c + col];
+    V[i] = (row == col) ? from_real<T>(1.0) : zero_<T>();
+  }
+  __syncthreads();
+  const int N = c + (c & 1);
+  const double tol = sqrt((double)c) * 2.220446049250313e-16;
+  int sweep = 0;
+  for (; sweep < 60; ++sweep) {
+    if (tid == 0) changed = 0;
+    __syncthreads();
+    for (int r = 0; r < N - 1; ++r) {
+      for (int i = warp; i < N / 2; i += nwarp) {
+        int pp = rr_slot(i, r, N), qq = rr_slot(N - 1 - i, r, N);
+        if (pp > qq) { int t = pp; pp = qq; qq = t; }
+        if (qq >= c) continue;
+        T* xp = X + pp * c;
+        T* xq = X + qq * c;
+        double a = 0, bb = 0;
+        T g = zero_<T>();
+        for (int rr = lane; rr < c; rr += 32) {
+          a += abs2_(xp[rr]); bb += abs2_(xq[rr]); g = madc_(xp[rr], xq[rr], g);
+        }
+        a = warp_sum(a); bb = warp_sum(bb); g = warp_sum(g);
+        const double ga = sqrt(abs2_(g));
+        if (!(ga > tol * sqrt(a) * sqrt(bb)) || a == 0.0 || bb == 0.0) continue;
+        const T e = scale_(g, 1.0 / ga);
+        const double zeta = (bb - a) / (2.0 * ga);
+        const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + hypot(1.0, zeta));
+        const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+        const T se = scale_(e, sn), sec = conj_(se);
+        for (int rr = lane; rr < c; rr += 32) {
+          const T u = xp[rr], w = xq[rr];
+          xp[rr] = sub_(scale_(u, cs), mul_(sec, w));
+          xq[rr] = add_(mul_(se, u), scale_(w, cs));
+          const T vu = V[pp * c + rr], vw = V[qq * c + rr];
+          V[pp * c + rr] = sub_(scale_(vu, cs), mul_(sec, vw));
+          V[qq * c + rr] = add_(mul_(se, vu), scale_(vw, cs));
+        }
+        if (lane == 0) changed = 1;
+      }
+      __syncthreads();
+    }
+    const int ch = changed;
+    __syncthreads();
+    if (!ch) { ++sweep; break; }
+  }
+  // singular values = column norms; sort descending, ties by index
+  for (int j = warp; j < c; j += nwarp) {
+    double a = 0;
+    for (int rr = lane; rr < c; rr += 32) a += abs2_(X[j * c + rr]);
+    a = warp_sum(a);
+    if (lane == 0) nrm[j] = sqrt(a);
+  }
+  __syncthreads();
+  for (int j = tid; j < c; j += blockDim.x) {
+    int rk = 0;
+    for (int i = 0; i < c; ++i) rk += (nrm[i] > nrm[j]) || (nrm[i] == nrm[j] && i < j);
+    rank[j] = rk;
+  }
+  __syncthreads();
+  for (int i = tid; i < c * c; i += blockDim.x) {
+    const int j = i / c, row = i % c;
+    C[rank[j] * c + row] = V[j * c + row];
+  }
+  for (int j = tid; j < c; j += blockDim.x) theta_out[rank[j]] = nrm[j];
+  __syncthreads();
+
+  // Q = Orth(M), M = C(0:b, 0:p)^H  (p x b, p = c - b >= b); Householder by warp 0 serially.
+  // The initial Rayleigh-Ritz (c == b) has no momentum block: K = [C | 0].
+  const int pdim = c - b;
+  const bool with_x = pdim >= b;
+  for (int i = tid; i < pdim * b; i += blockDim.x) {
+    const int col = i / pdim, row = i % pdim;     // M(row, col) = conj(C(col, row))
+    Qm[col * pdim + row] = conj_(C[row * c + col]);
+  }
+  __syncthreads();
+  if (warp == 0 && with_x) {
+    for (int j = 0; j < b; ++j) {
+      T* x = Qm + j * pdim;
+      double part = 0;
+      for (int r = j + 1 + lane; r < pdim; r += 32) part += abs2_(x[r]);
+      const double xn2 = warp_sum(part);
+      T tau, beta, inv_ab;
+      householder_scalars(x[j], xn2, &tau, &beta, &inv_ab);
+      for (int r = j + 1 + lane; r < pdim; r += 32) x[r] = mul_(x[r], inv_ab);
+      __syncwarp();
+      if (lane == 0) { x[j] = beta; tau_s[j] = tau; }
+      __syncwarp();
+      for (int q = j + 1; q < b; ++q) {
+        T* y = Qm + q * pdim;
+        T s = zero_<T>();
+        for (int r = j + 1 + lane; r < pdim; r += 32) s = madc_(x[r], y[r], s);
+        s = warp_sum(s);
+        s = add_(s, y[j]);
+        const T f = mul_(conj_(tau), s);
+        __syncwarp();
+        if (lane == 0) y[j] = sub_(y[j], f);
+        for (int r = j + 1 + lane; r < pdim; r += 32) y[r] = sub_(y[r], mul_(x[r], f));
+        __syncwarp();
+      }
+    }
+  }
+  __syncthreads();
+  T* E = reinterpret_cast<T*>(rank + c + 4);  // p x b col-major scratch
+  E = reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(E) + 15) & ~(uintptr_t)15);
+  for (int i = tid; i < pdim * b; i += blockDim.x) {
+    const int col = i / pdim, row = i % pdim;
+    E[i] = (row == col) ? from_real<T>(1.0) : zero_<T>();
+  }
+  __syncthreads();
+  // form Q explicitly: E = I(:, 0:b); E <- H_j E for j = b-1 .. 0 (H_j = I - tau_j v_j v_j^H)
+  if (warp == 0 && with_x) {
+    for (int j = b - 1; j >= 0; --j) {
+      const T* v = Qm + j * pdim;
+      const T tau = tau_s[j];
+      for (int q = j; q < b; ++q) {
+        T* y = E + q * pdim;
+        T s = zero_<T>();
+        for (int r = j + 1 + lane; r < pdim; r += 32) s = madc_(v[r], y[r], s);
+        s = warp_sum(s);
+        s = add_(s, y[j]);
+        const T f = mul_(tau, s);
+        __syncwarp();
+        if (lane == 0) y[j] = sub_(y[j], f);
+        for (int r = j + 1 + lane; r < pdim; r += 32) y[r] = sub_(y[r], mul_(v[r], f));
+        __syncwarp();
+      }
+    }
+    // make diag(R) real non-negative: Q(:, j) *= phase(R(j, j))
+    for (int j = 0; j < b; ++j) {
+      const T ph = phase_(Qm[j * pdim + j]);
+      for (int r = lane; r < pdim; r += 32) E[j * pdim + r] = mul_(E[j * pdim + r], ph);
+    }
+  }
+  __syncthreads();
+  // K = [C(:, p:c) | C(:, 0:p) E]  (c x 2b row-major)
+  for (int i = tid; i < c * 2 * b; i += blockDim.x) {
+    const int row = i / (2 * b), col = i % (2 * b);
+    T v;
+    if (col < b) {
+      v = C[(pdim + col) * c + row];
+    } else if (!with_x) {
+      v = zero_<T>();
+    } else {
+      const int q = col - b;
+      v = zero_<T>();
+      for (int l = 0; l < pdim; ++l) v = mad_(C[l * c + row], E[q * pdim + l], v);
+    }
+    K_out[i] = v;
+  }
+  if (tid == 0 && info) info[0] = sweep;
+}
+
+// ------------------------------------------------------------------------------------------
+// update: rows of buf (row-major, ld): x = buf[row, 0:c]; buf[row, 0:b] = x K(:, 0:b),
+// buf[row, 2b:3b] = x K(:, b:2b). Three buffers (T, A_T, G_T) in one launch.
+// ------------------------------------------------------------------------------------------
+template <class T>
+struct UpdSeg { T* buf; int64_t rows; int64_t ld; int blocks; };
+
+template <class T>
+__global__ void __launch_bounds__(256) update_kernel(UpdSeg<T> s0, UpdSeg<T> s1, UpdSeg<T> s2, int c, int b,
+                                                     const T* __restrict__ K) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int TRW = 64;
+  T* Ks = reinterpret_cast<T*>(smem_raw);       // c x 2b
+  T* tile = Ks + c * 2 * b;                     // TRW x c
+  int blk = blockIdx.x;
+  UpdSeg<T> s = s0;
+  if (blk >= s0.blocks) { blk -= s0.blocks; s = s1; if (blk >= s1.blocks) { blk -= s1.blocks; s = s2; } }
+  for (int i = threadIdx.x; i < c * 2 * b; i += blockDim.x) Ks[i] = K[i];
+  const int64_t r0 = (int64_t)blk * TRW;
+  const int nr = (int)imin<int64_t>(TRW, s.rows - r0);
+  for (int i = threadIdx.x; i < nr * c; i += blockDim.x) tile[i] = s.buf[(r0 + i / c) * s.ld + (i % c)];
+  __syncthreads();
+  for (int i = threadIdx.x; i < nr * 2 * b; i += blockDim.x) {
+    const int r = i / (2 * b), o = i % (2 * b);
+    T v = zero_<T>();
+    for (int l = 0; l < c; ++l) v = mad_(tile[r * c + l], Ks[l * 2 * b + o], v);
+    const int col = o < b ? o : (o + b);        // V -> [0,b), X -> [2b,3b)
+    s.buf[(r0 + r) * s.ld + col] = v;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// residual: Res = G_V - V diag(theta_s^2); norms; Rs = Res / ||Res(:,j)|| in precision S.
+// One CTA, one warp per column.
+// ------------------------------------------------------------------------------------------
+template <class T, class S>
+__global__ void __launch_bounds__(1024) residual_kernel(const T* __restrict__ Tbuf, const T* __restrict__ Gbuf,
+                                                         int n, int b, int64_t ld, const double* theta_s,
+                                                         T* Res, double* res_norm, S* Rs, int* err) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  for (int j = warp; j < b; j += nwarp) {
+    const double th2 = theta_s[j] * theta_s[j];
+    double a = 0;
+    for (int k = lane; k < n; k += 32) {
+      const T r = sub_(Gbuf[(int64_t)k * ld + j], scale_(Tbuf[(int64_t)k * ld + j], th2));
+      Res[(int64_t)k * b + j] = r;
+      a += abs2_(r);
+    }
+    a = warp_sum(a);
+    const double nr = sqrt(a);
+    if (lane == 0) {
+      res_norm[j] = nr;
+      if (!isfinite(nr)) atomicOr(err, DEV_ERR_NONFINITE);
+    }
+    const double inv = nr > 0.0 ? 1.0 / nr : 0.0;
+    for (int k = lane; k < n; k += 32) Rs[(int64_t)k * b + j] = cvt_<S, T>(scale_(Res[(int64_t)k * b + j], inv));
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// trimul: Y = L X with L an n x n matrix (row-major, ldl = n, only the triangle l in
+// [lo(k), hi(k)] used) in precision S, X n x b (row-major, ldx) in precision S; Y in precision
+// TO (row-major, ldy). One warp per output row. conj_l conjugates L's entries.
+// ------------------------------------------------------------------------------------------
+template <class S, class TO>
+__global__ void trimul_kernel(const S* __restrict__ L, int n, const S* __restrict__ X, int64_t ldx, int b,
+                              TO* __restrict__ Y, int64_t ldy, int lower, int conj_l) {
+  const int k = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (k >= n) return;
+  const int lo = lower ? 0 : k, hi = lower ? k : n - 1;
+  const S* Lk = L + (int64_t)k * n;
+  for (int c0 = 0; c0 < b; c0 += 8) {
+    S acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = zero_<S>();
+    for (int l = lo + lane; l <= hi; l += 32) {
+      const S lk = conj_l ? conj_(Lk[l]) : Lk[l];
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (c0 + q < b) acc[q] = mad_(lk, X[(int64_t)l * ldx + c0 + q], acc[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      if (c0 + q < b) {
+        const S s = warp_sum(acc[q]);
+        if (lane == 0) Y[(int64_t)k * ldy + c0 + q] = cvt_<TO, S>(s);
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// bcgs2_orth (one CTA): W (n x b at column offset wo of T, ld) is made orthogonal to the
+// columns listed in [0, b) (V) and, when nx > 0, [2b, 3b) (X), twice (BCGS2), then replaced by
+// Orth(W). E is an n x b scratch (row-major).
+// ------------------------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(1024) bcgs2_orth_kernel(T* Tb, int n, int b, int64_t ld, int wo, int nx,
+                                                           T* E, int passes) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* P = reinterpret_cast<T*>(smem_raw);     // q x b, q = b + nx
+  T* tauv = P + 2 * b * b;                   // b
+  T* sv = tauv + b;                          // b (s values)
+  T* dg = sv + b;                            // b diag(R)
+  __shared__ T sh_inv;
+  __shared__ double sh_x2;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarp = blockDim.x >> 5, NT = blockDim.x;
+  const int q = b + nx;
+  auto bcol = [&](int j) { return j < b ? j : (2 * b + (j - b)); };  // basis column -> T column
+  for (int pass = 0; pass < passes && q > 0; ++pass) {
+    for (int o = warp; o < q * b; o += nwarp) {
+      const int j = o / b, cw = o % b;
+      T s = zero_<T>();
+      for (int k = lane; k < n; k += 32) s = madc_(Tb[(int64_t)k * ld + bcol(j)], Tb[(int64_t)k * ld + wo + cw], s);
+      s = warp_sum(s);
+      if (lane == 0) P[o] = s;
+    }
+    __syncthreads();
+    for (int i = tid; i < n * b; i += NT) {
+      const int k = i / b, cw = i % b;
+      T w = Tb[(int64_t)k * ld + wo + cw];
+      for (int j = 0; j < q; ++j) w = sub_(w, mul_(Tb[(int64_t)k * ld + bcol(j)], P[j * b + cw]));
+      Tb[(int64_t)k * ld + wo + cw] = w;
+    }
+    __syncthreads();
+  }
+  // Householder QR of W (n x b) in place; v stored below the diagonal.
+  for (int j = 0; j < b; ++j) {
+    // d_cc = sum_{k > j} conj(W[k][j]) W[k][cc], cc >= j
+    for (int cc = j + warp; cc < b; cc += nwarp) {
+      T s = zero_<T>();
+      for (int k = j + 1 + lane; k < n; k += 32) s = madc_(Tb[(int64_t)k * ld + wo + j], Tb[(int64_t)k * ld + wo + cc], s);
+      s = warp_sum(s);
+      if (lane == 0) sv[cc] = s;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      T tau, beta, inv_ab;
+      const T alpha = Tb[(int64_t)j * ld + wo + j];
+      householder_scalars(alpha, re_(sv[j]), &tau, &beta, &inv_ab);
+      tauv[j] = tau; dg[j] = beta; sh_inv = inv_ab; sh_x2 = re_(sv[j]);
+      for (int cc = j + 1; cc < b; ++cc)
+        sv[cc] = add_(Tb[(int64_t)j * ld + wo + cc], mul_(conj_(inv_ab), sv[cc]));
+    }
+    __syncthreads();
+    const T tau = tauv[j], inv_ab = sh_inv;
+    for (int i = tid; i < (n - j) * b; i += NT) {
+      const int k = j + i / b, cc = i % b;
+      if (cc <= j) continue;
+      const T f = mul_(conj_(tau), sv[cc]);
+      const T vk = (k == j) ? from_real<T>(1.0) : mul_(Tb[(int64_t)k * ld + wo + j], inv_ab);
+      Tb[(int64_t)k * ld + wo + cc] = sub_(Tb[(int64_t)k * ld + wo + cc], mul_(vk, f));
+    }
+    __syncthreads();
+    for (int k = j + 1 + tid; k < n; k += NT) Tb[(int64_t)k * ld + wo + j] = mul_(Tb[(int64_t)k * ld + wo + j], inv_ab);
+    if (tid == 0) Tb[(int64_t)j * ld + wo + j] = dg[j];
+    __syncthreads();
+  }
+  // Q = H_0 ... H_{b-1} I(:, 0:b) into E, phases of diag(R) folded in, copied back to W
+  for (int i = tid; i < n * b; i += NT) {
+    const int k = i / b, cc = i % b;
+    E[i] = (k == cc) ? from_real<T>(1.0) : zero_<T>();
+  }
+  __syncthreads();
+  for (int j = b - 1; j >= 0; --j) {
+    for (int cc = j + warp; cc < b; cc += nwarp) {
+      T s = E[(int64_t)j * b + cc];
+      T part = zero_<T>();
+      for (int k = j + 1 + lane; k < n; k += 32) part = madc_(Tb[(int64_t)k * ld + wo + j], E[(int64_t)k * b + cc], part);
+      part = warp_sum(part);
+      if (lane == 0) sv[cc] = mul_(tauv[j], add_(s, part));
+    }
+    __syncthreads();
+    for (int i = tid; i < (n - j) * b; i += NT) {
+      const int k = j + i / b, cc = i % b;
+      if (cc < j) continue;
+      const T vk = (k == j) ? from_real<T>(1.0) : Tb[(int64_t)k * ld + wo + j];
+      E[(int64_t)k * b + cc] = sub_(E[(int64_t)k * b + cc], mul_(vk, sv[cc]));
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < n * b; i += NT) {
+    const int k = i / b, cc = i % b;
+    Tb[(int64_t)k * ld + wo + cc] = mul_(E[i], phase_(dg[cc]));
+  }
+}
+
+// V0 = Vt(:, n-b:n) (sketch precision, col-major n x n) -> T columns [0, b) in double/complex128
+template <class S, class T>
+__global__ void take_start_kernel(const S* Vt, int n, int b, T* Tb, int64_t ld) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)n * b) return;
+  const int k = (int)(i / b), j = (int)(i % b);
+  Tb[(int64_t)k * ld + j] = cvt_<T, S>(Vt[(int64_t)(n - b + j) * n + k]);
+}
+
+// copy columns [src, src+w) of a row-major buffer to [dst, dst+w) (used to move V0 into the
+// W slot for the first Gram pass and back), or out to a compact row-major array.
+template <class T>
+__global__ void copy_cols_kernel(const T* src, int64_t lds, int so, T* dst, int64_t ldd, int dof, int64_t rows, int w) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows * w) return;
+  const int64_t r = i / w;
+  const int c = (int)(i % w);
+  dst[r * ldd + dof + c] = src[r * lds + so + c];
+}
+
+// outputs: ascending order (reverse of the descending Theta_s block), first k of b
+template <class T>
+__global__ void outputs_kernel(const T* Tb, const T* ATb, int64_t n, int64_t m, int b, int k, int64_t ld,
+                               const double* theta_s, const double* res_norm, double* sigma, T* Vout, T* Uout,
+                               double* resid) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t tot = (n + (Uout ? m : 0)) * k;
+  if (i < k) {
+    sigma[i] = theta_s[b - 1 - i];
+    if (resid) resid[i] = res_norm[b - 1 - i];
+  }
+  if (i >= tot) return;
+  const int64_t r = i / k;
+  const int j = (int)(i % k);
+  const int src = b - 1 - j;
+  if (r < n) {
+    Vout[r * k + j] = Tb[r * ld + src];
+  } else {
+    const int64_t rr = r - n;
+    const double s = theta_s[src];
+    Uout[rr * k + j] = scale_(ATb[rr * ld + src], 1.0 / s);
+  }
+}
+
+template <class T>
+__global__ void nonfinite_scan_kernel(const T* A, int64_t m, int n, int64_t lda, int* err) {
+  int bad = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m * n; i += (int64_t)gridDim.x * blockDim.x)
+    bad |= !finite_(A[(i / n) * lda + (i % n)]);
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(err, DEV_ERR_NONFINITE);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------
+// host launchers
+// ------------------------------------------------------------------------------------------
+static int tsqr_chunk(int c, size_t esz) {
+  int ch = (int)(150 * 1024 / ((size_t)c * esz)) - c;
+  ch = max(32, min(256, ch));
+  return ch;
+}
+
+static int pow2_at_least(int x) { int p = 1; while (p < x) p <<= 1; return p; }
+
+static size_t tsqr_level_smem(int c, int CH, int CP, size_t esz) {
+  const int RP = 256 / CP;
+  return ((size_t)(c + CH) * c + (size_t)CP * RP + c) * esz;
+}
+
+size_t tsqr_workspace_bytes(int64_t m, int c, size_t esz) {
+  const int CH = tsqr_chunk(c, esz);
+  int64_t g1 = imin<int64_t>(num_sms(), imax<int64_t>(1, (m + CH - 1) / CH));
+  // level buffers ping-pong
+  return 2 * (((size_t)g1 * c * c * esz + 255) & ~(size_t)255);
+}
+
+template <class T>
+int tsqr_impl(const T* X, int64_t m, int c, int64_t ldx, T* R, void* work, size_t work_bytes, cudaStream_t st) {
+  if (c < 1 || c > 64) return RLOBPCG_ERR_INVALID_ARG;
+  const size_t esz = sizeof(T);
+  if (work_bytes < tsqr_workspace_bytes(m, c, esz)) return RLOBPCG_ERR_INVALID_ARG;
+  const int CH = tsqr_chunk(c, esz);
+  const int CP = pow2_at_least(c);
+  if (CP > 256) return RLOBPCG_ERR_UNSUPPORTED;
+  const size_t smem = tsqr_level_smem(c, CH, CP, esz);
+  RL_CUDA(cudaFuncSetAttribute(tsqr_level_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int64_t g1 = imin<int64_t>(num_sms(), imax<int64_t>(1, (m + CH - 1) / CH));
+  const size_t half = (((size_t)g1 * c * c * esz + 255) & ~(size_t)255);
+  T* buf[2] = {(T*)work, (T*)((unsigned char*)work + half)};
+  int64_t rpc = (m + g1 - 1) / g1;
+  int64_t grid = (m + rpc - 1) / rpc;
+  if (grid < 1) grid = 1;
+  tsqr_level_kernel<T><<<(int)grid, 256, smem, st>>>(X, m, c, ldx, rpc, CH, CP, buf[0]);
+  RL_CHECK_LAUNCH();
+  int cur = 0;
+  const int FAN = 16;
+  while (grid > 1) {
+    const int64_t rows = grid * c;
+    const int64_t rpc2 = (int64_t)FAN * c;
+    const int64_t g2 = (rows + rpc2 - 1) / rpc2;
+    tsqr_level_kernel<T><<<(int)g2, 256, smem, st>>>(buf[cur], rows, c, c, rpc2, CH, CP, buf[cur ^ 1]);
+    RL_CHECK_LAUNCH();
+    cur ^= 1;
+    grid = g2;
+  }
+  RL_CUDA(cudaMemcpyAsync(R, buf[cur], (size_t)c * c * esz, cudaMemcpyDeviceToDevice, st));
+  r_phase_fix_kernel<T><<<c, 64, 0, st>>>(R, c);
+  RL_CHECK_LAUNCH();
+  return RLOBPCG_OK;
+}
+template int tsqr_impl<double>(const double*, int64_t, int, int64_t, double*, void*, size_t, cudaStream_t);
+template int tsqr_impl<cd>(const cd*, int64_t, int, int64_t, cd*, void*, size_t, cudaStream_t);
+
+template <class T>
+int rr_small_launch(const T* Rt, int c, int b, double* theta, T* K, int* info, cudaStream_t st) {
+  const int pdim = c - b;
+  size_t smem = (size_t)3 * c * c * sizeof(T) + (size_t)c * b * sizeof(T) + c * sizeof(double) +
+                (c + 4) * sizeof(int) + 16 + (size_t)pdim * b * sizeof(T);
+  RL_CUDA(cudaFuncSetAttribute(rr_small_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int threads = min(1024, max(64, ((c + 1) / 2) * 32));
+  rr_small_kernel<T><<<1, threads, smem, st>>>(Rt, c, b, theta, K, info);
+  RL_CHECK_LAUNCH();
+  return RLOBPCG_OK;
+}
+template int rr_small_launch<double>(const double*, int, int, double*, double*, int*, cudaStream_t);
+template int rr_small_launch<cd>(const cd*, int, int, double*, cd*, int*, cudaStream_t);
+
+template <class T>
+int update_launch(T* Tb, int64_t n, T* ATb, int64_t m, T* GTb, int64_t ld, int c, int b, const T* K, cudaStream_t st) {
+  constexpr int TRW = 64;
+  UpdSeg<T> s0{Tb, n, ld, ceil_div(n, TRW)}, s1{ATb, m, ld, ceil_div(m, TRW)}, s2{GTb, n, ld, ceil_div(n, TRW)};
+  const size_t smem = ((size_t)c * 2 * b + (size_t)TRW * c) * sizeof(T);
+  if (smem > 48 * 1024) RL_CUDA(cudaFuncSetAttribute(update_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int blocks = s0.blocks + s1.blocks + s2.blocks;
+  update_kernel<T><<<blocks, 256, smem, st>>>(s0, s1, s2, c, b, K);
+  RL_CHECK_LAUNCH();
+  return RLOBPCG_OK;
+}
+template int update_launch<double>(double*, int64_t, double*, int64_t, double*, int64_t, int, int, const double*, cudaStream_t);
+template int update_launch<cd>(cd*, int64_t, cd*, int64_t, cd*, int64_t, int, int, const cd*, cudaStream_t);
+
+template <class T, class S>
+int residual_launch(const T* Tb, const T* Gb, int n, int b, int64_t ld, const double* theta_s, T* Res, double* res_norm,
+                    S* Rs, int* err, cudaStream_t st) {
+  residual_kernel<T, S><<<1, min(1024, b * 32), 0, st>>>(Tb, Gb, n, b, ld, theta_s, Res, res_norm, Rs, err);
+  RL_CHECK_LAUNCH();
+  return RLOBPCG_OK;
+}
+template int residual_launch<double, double>(const double*, const double*, int, int, int64_t, const double*, double*, double*, double*, int*, cudaStream_t);
+template int residual_launch<double, float>(const double*, const double*, int, int, int64_t, const double*, double*, double*, float*, int*, cudaStream_t);
+template int residual_launch<cd, cd>(const cd*, const cd*, int, int, int64_t, const double*, cd*, double*, cd*, int*, cudaStream_t);
+template int residual_launch<cd, cf>(const cd*, const cd*, int, int, int64_t, const double*, cd*, double*, cf*, int*, cudaStream_t);
+
+// W = Rinv (Rinv^H Rs): Y (n x b, precision S) scratch; W written into T columns [wo, wo+b)
+template <class T, class S>
+int precond_launch(const S* Rinv_r, const S* Rinv_c, int n, int b, const S* Rs, S* Y, T* Tb, int64_t ld, int wo,
+                   cudaStream_t st) {
+  const int blocks = (n * 32 + 255) / 256;
+  // Y(k) = sum_{l <= k} conj(Rinv(l, k)) Rs(l): row k of Rinv^H = conj(column k of Rinv)
+  trimul_kernel<S, S><<<blocks, 256, 0, st>>>(Rinv_c, n, Rs, b, b, Y, b, 1, 1);
+  RL_CHECK_LAUNCH();
+  // W(k) = sum_{l >= k} Rinv(k, l) Y(l)
+  trimul_kernel<S, T><<<blocks, 256, 0, st>>>(Rinv_r, n, Y, b, b, Tb + wo, ld, 0, 0);
+  RL_CHECK_LAUNCH();
+  return RLOBPCG_OK;
+}
+template int precond_launch<double, double>(const double*, const double*, int, int, const double*, double*, double*, int64_t, int, cudaStream_t);
+template int precond_launch<double, float>(const float*, const float*, int, int, const float*, float*, double*, int64_t, int, cudaStream_t);
+template int precond_launch<cd, cd>(const cd*, const cd*, int, int, const cd*, cd*, cd*, int64_t, int, cudaStream_t);
+template int precond_launch<cd, cf>(const cf*, const cf*, int, int, const cf*, cf*, cd*, int64_t, int, cudaStream_t);
+
+template <class T>
+int bcgs2_orth_launch(T* Tb, int n, int b, int64_t ld, int wo, int nx, T* E, int passes, cudaStream_t st) {
+  const size_t smem = ((size_t)2 * b * b + 3 * b) * sizeof(T);
+  bcgs2_orth_kernel<T><<<1, 1024, smem, st>>>(Tb, n, b, ld, wo, nx, E, passes);
+  RL_CHECK_LAUNCH();
+  return RLOBPCG_OK;
+}
+template int bcgs2_orth_launch<double>(double*, int, int, int64_t, int, int, double*, int, cudaStream_t);
+template int bcgs2_orth_launch<cd>(cd*, int, int, int64_t, int, int, cd*, int, cudaStream_t);
+
+template <class S, class T>
+int take_start_launch(const S* Vt, int n, int b, T* Tb, int64_t ld, cudaStream_t st) {
+  take_start_kernel<S, T><<<ceil_div((int64_t)n * b, 256), 256, 0, st>>>(Vt, n, b, Tb, ld);
+  RL_CHECK_LAUNCH();
+  return RLOBPCG_OK;
+}
+template int take_start_launch<double, double>(const double*, int, int, double*, int64_t, cudaStream_t);
+template int take_start_launch<float, double>(const float*, int, int, double*, int64_t, cudaStream_t);
+template int take_start_launch<cd, cd>(const cd*, int, int, cd*, int64_t, cudaStream_t);
+template int take_start_launch<cf, cd>(const cf*, int, int, cd*, int64_t, cudaStream_t);
+
+template <class T>
+int copy_cols_launch(const T* src, int64_t lds, int so, T* dst, int64_t ldd, int dof, int64_t rows, int w, cudaStream_t st) {
+  if (rows * w == 0) return RLOBPCG_OK;
+  copy_cols_kernel<T><<<ceil_div(rows * w, 256), 256, 0, st>>>(src, lds, so, dst, ldd, dof, rows, w);
+  RL_CHECK_LAUNCH();
+  return RLOBPCG_OK;
+}
+template int copy_cols_launch<double>(const double*, int64_t, int, double*, int64_t, int, int64_t, int, cudaStream_t);
+template int copy_cols_launch<cd>(const cd*, int64_t, int, cd*, int64_t, int, int64_t, int, cudaStream_t);
+
+template <class T>
+int outputs_launch(const T* Tb, const T* ATb, int64_t n, int64_t m, int b, int k, int64_t ld, const double* theta_s,
+                   const double* res_norm, double* sigma, T* Vout, T* Uout, double* resid, cudaStream_t st) {
+  const int64_t tot = imax<int64_t>((n + (Uout ? m : 0)) * k, k);
+  outputs_kernel<T><<<ceil_div(tot, 256), 256, 0, st>>>(Tb, ATb, n, m, b, k, ld, theta_s, res_norm, sigma, Vout, Uout, resid);
+  RL_CHECK_LAUNCH();
+  return RLOBPCG_OK;
+}
+template int outputs_launch<double>(const double*, const double*, int64_t, int64_t, int, int, int64_t, const double*, const double*, double*, double*, double*, double*, cudaStream_t);
+template int outputs_launch<cd>(const cd*, const cd*, int64_t, int64_t, int, int, int64_t, const double*, const double*, double*, cd*, cd*, double*, cudaStream_t);
+
+template <class T>
+int nonfinite_scan_launch(const T* A, int64_t m, int n, int64_t lda, int* err, cudaStream_t st) {
+  nonfinite_scan_kernel<T><<<num_sms() * 4, 256, 0, st>>>(A, m, n, lda, err);
+  RL_CHECK_LAUNCH();
+  return RLOBPCG_OK;
+}
+template int nonfinite_scan_launch<double>(const double*, int64_t, int, int64_t, int*, cudaStream_t);
+template int nonfinite_scan_launch<cd>(const cd*, int64_t, int, int64_t, int*, cudaStream_t);
+
+}  // namespace rl

@@ -1,0 +1,401 @@
+// Host driver of one RLOBPCG solve (Algorithm 2 of arXiv 2602.16797) on the GPU.
+//
+// The plan owns every device buffer of a solve; solve() issues the kernels of sketch.cu,
+// factor.cu, gram.cu and small.cu on the plan's stream and reads back only the b residual
+// norms and b Ritz values per iteration, which the host-side stopping rule (Sec. 2.1) needs.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <limits>
+#include <vector>
+
+#include "common.cuh"
+
+namespace rl {
+
+// kernels and launchers defined in the other translation units
+int sketch_dispatch(const void* A, int64_t m, int64_t n, int64_t lda, int dtype, int d, int zeta, uint64_t seed,
+                    int sketch_prec, void* SA, cudaStream_t st);
+size_t factor_workspace_bytes(int64_t d, int64_t n, size_t esz);
+template <class S>
+int factor_impl(S* SA, int d, int n, S* Rout, double* sigma, S* Vt, S* Rinv_r, S* Rinv_c, void* work,
+                size_t work_bytes, cudaStream_t st, int* sweeps_host);
+size_t gram_workspace_bytes(int64_t m, int64_t n, int b, int dtype);
+int gram_dispatch(const void* A, int64_t m, int64_t n, int64_t lda, int dtype, const void* W, int b, int64_t ldw,
+                  void* AW, int64_t ldaw, void* G, int64_t ldg, void* work, size_t work_bytes, int resid_mode,
+                  int* err, cudaStream_t st);
+size_t tsqr_workspace_bytes(int64_t m, int c, size_t esz);
+template <class T>
+int tsqr_impl(const T* X, int64_t m, int c, int64_t ldx, T* R, void* work, size_t work_bytes, cudaStream_t st);
+template <class T>
+int rr_small_launch(const T* Rt, int c, int b, double* theta, T* K, int* info, cudaStream_t st);
+template <class T>
+int update_launch(T* Tb, int64_t n, T* ATb, int64_t m, T* GTb, int64_t ld, int c, int b, const T* K, cudaStream_t st);
+template <class T, class S>
+int residual_launch(const T* Tb, const T* Gb, int n, int b, int64_t ld, const double* theta_s, T* Res,
+                    double* res_norm, S* Rs, int* err, cudaStream_t st);
+template <class T, class S>
+int precond_launch(const S* Rinv_r, const S* Rinv_c, int n, int b, const S* Rs, S* Y, T* Tb, int64_t ld, int wo,
+                   cudaStream_t st);
+template <class T>
+int bcgs2_orth_launch(T* Tb, int n, int b, int64_t ld, int wo, int nx, T* E, int passes, cudaStream_t st);
+template <class S, class T>
+int take_start_launch(const S* Vt, int n, int b, T* Tb, int64_t ld, cudaStream_t st);
+template <class T>
+int outputs_launch(const T* Tb, const T* ATb, int64_t n, int64_t m, int b, int k, int64_t ld, const double* theta_s,
+                   const double* res_norm, double* sigma, T* Vout, T* Uout, double* resid, cudaStream_t st);
+template <class T>
+int nonfinite_scan_launch(const T* A, int64_t m, int n, int64_t lda, int* err, cudaStream_t st);
+
+}  // namespace rl
+
+using namespace rl;
+
+struct rlobpcg_plan_s {
+  int64_t m = 0, n = 0;
+  int k = 0, b = 0, d = 0, dtype = 0;
+  rlobpcg_opts opts{};
+  cudaStream_t st = nullptr;
+  size_t esz = 8, ssz = 8;  // element sizes of the state (T) and of the sketch side (S)
+  // device buffers
+  void* A_dev = nullptr;    // plan-owned copy of a host A (allocated on first use)
+  size_t A_dev_bytes = 0;
+  void* SA = nullptr;
+  double* sk_sigma = nullptr;
+  void* Vt = nullptr;
+  void* Rinv_r = nullptr;
+  void* Rinv_c = nullptr;
+  void* fwork = nullptr;
+  size_t fwork_bytes = 0;
+  void* Tb = nullptr;
+  void* ATb = nullptr;
+  void* GTb = nullptr;
+  void* E = nullptr;
+  void* Res = nullptr;
+  void* Rs = nullptr;
+  void* Y = nullptr;
+  void* Rt = nullptr;
+  void* K = nullptr;
+  double* theta = nullptr;
+  double* res_norm = nullptr;
+  int* err = nullptr;
+  int* info = nullptr;
+  void* gwork = nullptr;
+  size_t gwork_bytes = 0;
+  void* twork = nullptr;
+  size_t twork_bytes = 0;
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  std::vector<void*> owned;
+};
+
+namespace {
+
+int dev_alloc(rlobpcg_plan_s* p, void** out, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(out, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_last_error(cudaGetErrorString(e), __FILE__, __LINE__);
+    return RLOBPCG_ERR_OOM;
+  }
+  p->owned.push_back(*out);
+  return RLOBPCG_OK;
+}
+
+void free_plan(rlobpcg_plan_s* p) {
+  for (void* q : p->owned) cudaFree(q);
+  p->owned.clear();
+  if (p->A_dev) cudaFree(p->A_dev);
+  for (auto& e : p->ev)
+    if (e) cudaEventDestroy(e);
+}
+
+bool is_device_ptr(const void* ptr) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) { cudaGetLastError(); return false; }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Stopping rule of Sec. 2.1 (Alg. 1 / Alg. 2): tolerance on max_j ||R(:,j)|| against
+// Sigma~(1,1)^2 tau, plus (optionally) the two stagnation checks for every column. History
+// that does not exist yet is +inf, so comparisons with it are false.
+struct StopRule {
+  std::vector<std::vector<double>> r, th;  // index t = 0 .. i+1
+  bool check(int i, double sigma11, double tau, bool stag) const {
+    const double inf = std::numeric_limits<double>::infinity();
+    auto rv = [&](int t, int j) { return t >= 0 ? r[t][j] : inf; };
+    auto tv = [&](int t, int j) { return t >= 0 ? th[t][j] : inf; };
+    const int b = (int)r[i + 1].size();
+    double mx = 0;
+    for (int j = 0; j < b; ++j) mx = std::max(mx, r[i + 1][j]);
+    if (!(mx <= sigma11 * sigma11 * tau)) return false;
+    if (!stag) return true;
+    for (int j = 0; j < b; ++j) {
+      if (!(1.1 * rv(i + 1, j) >= rv(i - 4, j))) return false;
+      const double lhs = 1.1 * (tv(i - 4, j) - tv(i + 1, j)) / tv(i + 1, j);
+      const double rhs = (tv(i - 9, j) - tv(i - 4, j)) / tv(i - 4, j);
+      if (!(lhs >= rhs)) return false;
+    }
+    return true;
+  }
+};
+
+template <class T, class S>
+int solve_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, double tau, double* sigma, T* Vout, T* Uout,
+               double* resid, rlobpcg_info* info) {
+  cudaStream_t st = p->st;
+  const int64_t m = p->m;
+  const int n = (int)p->n, b = p->b, k = p->k, d = p->d;
+  const int64_t ld = 3 * b;
+  T* Tb = (T*)p->Tb;
+  T* ATb = (T*)p->ATb;
+  T* GTb = (T*)p->GTb;
+  int rc;
+#define RL_TRY(x) do { rc = (x); if (rc) return rc; } while (0)
+  RL_CUDA(cudaMemsetAsync(p->err, 0, sizeof(int), st));
+  RL_CUDA(cudaEventRecord(p->ev[0], st));
+  RL_TRY(nonfinite_scan_launch<T>(A, m, n, lda, p->err, st));
+  int herr = 0;
+  RL_CUDA(cudaMemcpyAsync(&herr, p->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+
+  // Sketch and factorise (Alg. 2, lines 1-3)
+  RL_TRY(sketch_dispatch(A, m, n, lda, p->dtype, d, p->opts.zeta, p->opts.seed, p->opts.sketch_prec, p->SA, st));
+  RL_CUDA(cudaEventRecord(p->ev[1], st));
+  RL_TRY(factor_impl<S>((S*)p->SA, d, n, nullptr, p->sk_sigma, (S*)p->Vt, (S*)p->Rinv_r, (S*)p->Rinv_c, p->fwork,
+                        p->fwork_bytes, st, nullptr));
+  double sigma11 = 0;
+  RL_CUDA(cudaMemcpyAsync(&sigma11, p->sk_sigma, sizeof(double), cudaMemcpyDeviceToHost, st));
+  RL_CUDA(cudaStreamSynchronize(st));
+  if (herr & DEV_ERR_NONFINITE) return RLOBPCG_ERR_NONFINITE;
+
+  // Sketch-and-solve start and initial Rayleigh-Ritz (Alg. 2, lines 4-7)
+  RL_TRY((take_start_launch<S, T>((const S*)p->Vt, n, b, Tb, ld, st)));
+  RL_TRY(bcgs2_orth_launch<T>(Tb, n, b, ld, 0, 0, (T*)p->E, 0, st));
+  RL_TRY(gram_dispatch(A, m, n, lda, p->dtype, Tb, b, ld, ATb, ld, GTb, ld, p->gwork, p->gwork_bytes, 0, p->err, st));
+  RL_TRY(tsqr_impl<T>(ATb, m, b, ld, (T*)p->Rt, p->twork, p->twork_bytes, st));
+  RL_TRY(rr_small_launch<T>((const T*)p->Rt, b, b, p->theta, (T*)p->K, p->info, st));
+  RL_TRY(update_launch<T>(Tb, n, ATb, m, GTb, ld, b, b, (const T*)p->K, st));
+  RL_TRY((residual_launch<T, S>(Tb, GTb, n, b, ld, p->theta, (T*)p->Res, p->res_norm, (S*)p->Rs, p->err, st)));
+  RL_CUDA(cudaEventRecord(p->ev[2], st));
+
+  StopRule hist;
+  std::vector<double> hr(b), ht(b);
+  RL_CUDA(cudaMemcpyAsync(hr.data(), p->res_norm, b * sizeof(double), cudaMemcpyDeviceToHost, st));
+  RL_CUDA(cudaStreamSynchronize(st));
+  hist.r.push_back(hr);
+  hist.th.push_back(std::vector<double>(b, std::numeric_limits<double>::infinity()));
+
+  const int fixed = p->opts.fixed_iters;
+  const int max_iter = fixed > 0 ? fixed : p->opts.max_iter;
+  const bool stag = p->opts.use_stagnation != 0;
+  const int check_every = std::max(1, p->opts.check_every);
+  const int refresh = p->opts.residual_refresh_every;
+  int nx = 0, it = 0, stop = fixed > 0 ? RLOBPCG_STOP_FIXED : RLOBPCG_STOP_MAX_ITER;
+  int matvecs = b;
+  const double* theta_s = p->theta;
+  for (int i = 0; i < max_iter; ++i) {
+    // W = P (P^* R_i), then BCGS2 against [V X] and Orth
+    RL_TRY((precond_launch<T, S>((const S*)p->Rinv_r, (const S*)p->Rinv_c, n, b, (const S*)p->Rs, (S*)p->Y, Tb, ld, b, st)));
+    RL_TRY(bcgs2_orth_launch<T>(Tb, n, b, ld, b, nx, (T*)p->E, 2, st));
+    // A W and A^H (A W) in one pass over A
+    RL_TRY(gram_dispatch(A, m, n, lda, p->dtype, Tb + b, b, ld, ATb + b, ld, GTb + b, ld, p->gwork, p->gwork_bytes, 0,
+                         p->err, st));
+    matvecs += b;
+    // Rayleigh-Ritz by SVD of A_T (TSQR + Jacobi of R_T)
+    const int c = 2 * b + nx;
+    RL_TRY(tsqr_impl<T>(ATb, m, c, ld, (T*)p->Rt, p->twork, p->twork_bytes, st));
+    RL_TRY(rr_small_launch<T>((const T*)p->Rt, c, b, p->theta, (T*)p->K, p->info, st));
+    theta_s = p->theta + (c - b);
+    RL_TRY(update_launch<T>(Tb, n, ATb, m, GTb, ld, c, b, (const T*)p->K, st));
+    if (refresh > 0 && (i + 1) % refresh == 0) {
+      RL_TRY(gram_dispatch(A, m, n, lda, p->dtype, nullptr, b, ld, ATb, ld, GTb, ld, p->gwork, p->gwork_bytes, 1,
+                           p->err, st));
+      matvecs += b;
+    }
+    RL_TRY((residual_launch<T, S>(Tb, GTb, n, b, ld, theta_s, (T*)p->Res, p->res_norm, (S*)p->Rs, p->err, st)));
+    RL_CUDA(cudaMemcpyAsync(hr.data(), p->res_norm, b * sizeof(double), cudaMemcpyDeviceToHost, st));
+    RL_CUDA(cudaMemcpyAsync(ht.data(), theta_s, b * sizeof(double), cudaMemcpyDeviceToHost, st));
+    RL_CUDA(cudaStreamSynchronize(st));
+    hist.r.push_back(hr);
+    hist.th.push_back(ht);
+    it = i + 1;
+    nx = b;
+    if (fixed <= 0 && i % check_every == 0 && hist.check(i, sigma11, tau, stag)) {
+      stop = RLOBPCG_STOP_CONVERGED;
+      break;
+    }
+  }
+  RL_CUDA(cudaEventRecord(p->ev[3], st));
+  // outputs (ascending sigma): staged in plan scratch, then copied to host or device pointers
+  {
+    double* sig_stage = p->res_norm + b;   // k doubles after the b norms
+    double* res_stage = sig_stage + k;
+    T* V_stage = (T*)p->E;                  // n x k fits in the n x b scratch
+    T* U_dev = (Uout && is_device_ptr(Uout)) ? Uout : nullptr;
+    RL_TRY(outputs_launch<T>(Tb, ATb, n, m, b, k, ld, theta_s, p->res_norm, sig_stage, V_stage, U_dev, res_stage, st));
+    RL_CUDA(cudaMemcpyAsync(sigma, sig_stage, k * sizeof(double), cudaMemcpyDefault, st));
+    if (resid) RL_CUDA(cudaMemcpyAsync(resid, res_stage, k * sizeof(double), cudaMemcpyDefault, st));
+    RL_CUDA(cudaMemcpyAsync(Vout, V_stage, (size_t)n * k * sizeof(T), cudaMemcpyDefault, st));
+    if (Uout && !U_dev) {
+      // host U: a temporary device array (the only allocation of solve() besides a host A copy)
+      T* Ud = nullptr;
+      RL_CUDA(cudaMallocAsync((void**)&Ud, (size_t)m * k * sizeof(T), st));
+      RL_TRY(outputs_launch<T>(Tb, ATb, n, m, b, k, ld, theta_s, p->res_norm, sig_stage, V_stage, Ud, res_stage, st));
+      RL_CUDA(cudaMemcpyAsync(Uout, Ud, (size_t)m * k * sizeof(T), cudaMemcpyDeviceToHost, st));
+      RL_CUDA(cudaFreeAsync(Ud, st));
+    }
+  }
+  RL_CUDA(cudaMemcpyAsync(&herr, p->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  RL_CUDA(cudaEventRecord(p->ev[4], st));
+  RL_CUDA(cudaStreamSynchronize(st));
+  if (info) {
+    info->iters = it;
+    info->matvecs = matvecs;
+    info->stop_reason = stop;
+    info->block = b;
+    info->sigma11 = sigma11;
+    float ms = 0;
+    cudaEventElapsedTime(&ms, p->ev[0], p->ev[1]); info->ms_sketch = ms;
+    cudaEventElapsedTime(&ms, p->ev[1], p->ev[2]); info->ms_factor = ms;
+    cudaEventElapsedTime(&ms, p->ev[2], p->ev[3]); info->ms_iterate = ms;
+    cudaEventElapsedTime(&ms, p->ev[0], p->ev[4]); info->ms_total = ms;
+  }
+  if (herr & DEV_ERR_TIMEOUT) return RLOBPCG_ERR_TIMEOUT;
+  if (herr & DEV_ERR_NONFINITE) return RLOBPCG_ERR_NONFINITE;
+  return stop == RLOBPCG_STOP_MAX_ITER ? RLOBPCG_NOT_CONVERGED : RLOBPCG_OK;
+#undef RL_TRY
+}
+
+}  // namespace
+
+extern "C" int rlobpcg_default_opts(rlobpcg_opts* o) {
+  if (!o) return RLOBPCG_ERR_INVALID_ARG;
+  memset(o, 0, sizeof(*o));
+  o->seed = 0;
+  o->d = 0;
+  o->zeta = 8;
+  o->block = 0;
+  o->max_iter = 0;
+  o->check_every = 0;
+  o->use_stagnation = 1;
+  o->sketch_prec = RLOBPCG_SKETCH_F64;
+  o->fixed_iters = 0;
+  o->residual_refresh_every = 0;
+  o->tau = -1.0;
+  return RLOBPCG_OK;
+}
+
+extern "C" int rlobpcg_plan(rlobpcg_plan_t* out, int64_t m, int64_t n, int k, int dtype, const rlobpcg_opts* opts,
+                            void* stream) {
+  if (!out) return RLOBPCG_ERR_INVALID_ARG;
+  *out = nullptr;
+  rlobpcg_opts o;
+  if (opts) o = *opts; else rlobpcg_default_opts(&o);
+  if (dtype != RLOBPCG_F64 && dtype != RLOBPCG_C128) return RLOBPCG_ERR_INVALID_ARG;
+  const int b = o.block > 0 ? o.block : k;
+  const int64_t d = o.d > 0 ? o.d : 4 * n;
+  if (k < 1 || b < k || 3 * (int64_t)b > n || n > m || o.zeta < 1 || d < n || d < o.zeta || b > 21 ||
+      n > (1 << 20) || (o.sketch_prec != RLOBPCG_SKETCH_F64 && o.sketch_prec != RLOBPCG_SKETCH_F32)) {
+    set_last_error("invalid plan arguments (need 1 <= k <= b <= 21, 3b <= n <= m, n <= d, zeta <= d)", __FILE__, __LINE__);
+    return RLOBPCG_ERR_INVALID_ARG;
+  }
+  auto* p = new rlobpcg_plan_s();
+  p->m = m; p->n = n; p->k = k; p->b = b; p->d = (int)d; p->dtype = dtype;
+  p->st = (cudaStream_t)stream;
+  if (o.max_iter <= 0) o.max_iter = (b == 1) ? 200 : 100;
+  if (o.check_every <= 0) o.check_every = o.use_stagnation ? 5 : 1;
+  if (!(o.tau >= 0)) o.tau = 2.0 * sqrt((double)n) * ldexp(1.0, -52);
+  p->opts = o;
+  const bool cplx = dtype == RLOBPCG_C128;
+  const bool f32 = o.sketch_prec == RLOBPCG_SKETCH_F32;
+  p->esz = cplx ? 16 : 8;
+  p->ssz = (cplx ? 2 : 1) * (f32 ? 4 : 8);
+  const size_t esz = p->esz, ssz = p->ssz;
+  const int64_t ld = 3 * b;
+  int rc = 0;
+#define RL_A(ptr, bytes) do { rc = dev_alloc(p, (void**)&(ptr), (bytes)); if (rc) { free_plan(p); delete p; return rc; } } while (0)
+  RL_A(p->SA, (size_t)d * n * ssz);
+  RL_A(p->sk_sigma, (size_t)n * sizeof(double));
+  RL_A(p->Vt, (size_t)n * n * ssz);
+  RL_A(p->Rinv_r, (size_t)n * n * ssz);
+  RL_A(p->Rinv_c, (size_t)n * n * ssz);
+  p->fwork_bytes = factor_workspace_bytes(d, n, ssz);
+  RL_A(p->fwork, p->fwork_bytes);
+  RL_A(p->Tb, (size_t)n * ld * esz);
+  RL_A(p->ATb, (size_t)m * ld * esz);
+  RL_A(p->GTb, (size_t)n * ld * esz);
+  RL_A(p->E, (size_t)n * b * esz);
+  RL_A(p->Res, (size_t)n * b * esz);
+  RL_A(p->Rs, (size_t)n * b * ssz);
+  RL_A(p->Y, (size_t)std::max<int64_t>(n * b, 64) * std::max(ssz, (size_t)8));
+  RL_A(p->Rt, (size_t)ld * ld * esz);
+  RL_A(p->K, (size_t)ld * 2 * b * esz);
+  RL_A(p->theta, (size_t)ld * sizeof(double));
+  RL_A(p->res_norm, (size_t)(b + 2 * k + 8) * sizeof(double));
+  RL_A(p->err, 64);
+  RL_A(p->info, 64);
+  p->gwork_bytes = gram_workspace_bytes(m, n, b, dtype);
+  if (p->gwork_bytes == 0) { free_plan(p); delete p; set_last_error("Gram kernel: n*b too large for on-chip accumulation", __FILE__, __LINE__); return RLOBPCG_ERR_UNSUPPORTED; }
+  RL_A(p->gwork, p->gwork_bytes);
+  p->twork_bytes = tsqr_workspace_bytes(m, (int)ld, esz);
+  RL_A(p->twork, p->twork_bytes);
+#undef RL_A
+  for (auto& e : p->ev) {
+    if (cudaEventCreate(&e) != cudaSuccess) { free_plan(p); delete p; return RLOBPCG_ERR_CUDA; }
+  }
+  *out = p;
+  return RLOBPCG_OK;
+}
+
+extern "C" int rlobpcg_solve(rlobpcg_plan_t p, const void* A, int64_t lda, double tol, double* sigma, void* V, void* U,
+                             double* resid, rlobpcg_info* info) {
+  if (!p || !A || !sigma || !V || lda < p->n) return RLOBPCG_ERR_INVALID_ARG;
+  const double tau = tol >= 0 ? tol : p->opts.tau;
+  const void* Ause = A;
+  int64_t ldause = lda;
+  cudaEvent_t h0 = nullptr, h1 = nullptr;
+  const bool host_A = !is_device_ptr(A);
+  if (host_A) {
+    // host input: copy into a plan-owned device buffer (compact, lda = n)
+    const size_t bytes = (size_t)p->m * p->n * p->esz;
+    if (p->A_dev_bytes < bytes) {
+      if (p->A_dev) cudaFree(p->A_dev);
+      p->A_dev = nullptr;
+      p->A_dev_bytes = 0;
+      if (cudaMalloc(&p->A_dev, bytes) != cudaSuccess) { cudaGetLastError(); return RLOBPCG_ERR_OOM; }
+      p->A_dev_bytes = bytes;
+    }
+    RL_CUDA(cudaEventCreate(&h0));
+    RL_CUDA(cudaEventCreate(&h1));
+    RL_CUDA(cudaEventRecord(h0, p->st));
+    RL_CUDA(cudaMemcpy2DAsync(p->A_dev, p->n * p->esz, A, lda * p->esz, p->n * p->esz, p->m, cudaMemcpyHostToDevice, p->st));
+    Ause = p->A_dev;
+    ldause = p->n;
+  }
+  int rc;
+  const bool f32 = p->opts.sketch_prec == RLOBPCG_SKETCH_F32;
+  if (p->dtype == RLOBPCG_F64) {
+    rc = f32 ? solve_impl<double, float>(p, (const double*)Ause, ldause, tau, sigma, (double*)V, (double*)U, resid, info)
+             : solve_impl<double, double>(p, (const double*)Ause, ldause, tau, sigma, (double*)V, (double*)U, resid, info);
+  } else {
+    rc = f32 ? solve_impl<cd, cf>(p, (const cd*)Ause, ldause, tau, sigma, (cd*)V, (cd*)U, resid, info)
+             : solve_impl<cd, cd>(p, (const cd*)Ause, ldause, tau, sigma, (cd*)V, (cd*)U, resid, info);
+  }
+  if (host_A) {
+    cudaEventRecord(h1, p->st);
+    cudaEventSynchronize(h1);
+    if (info && rc >= 0) { float ms = 0; cudaEventElapsedTime(&ms, h0, h1); info->ms_total = ms; }
+    cudaEventDestroy(h0);
+    cudaEventDestroy(h1);
+  }
+  return rc;
+}
+
+extern "C" int rlobpcg_plan_destroy(rlobpcg_plan_t p) {
+  if (!p) return RLOBPCG_OK;
+  if (p->st) cudaStreamSynchronize(p->st); else cudaDeviceSynchronize();
+  free_plan(p);
+  delete p;
+  return RLOBPCG_OK;
+}

@@ -1,0 +1,217 @@
+"""Python binding of the C ABI in include/rlobpcg.h (argument marshalling only).
+
+Every entry point keeps the C name. Device buffers are passed as integer addresses (e.g.
+``tensor.data_ptr()`` of a CUDA torch tensor) and streams as ``cudaStream_t`` handles
+(``torch.cuda.current_stream().cuda_stream``). There is no CPU fallback: if the compiled library
+is missing, loading fails with an error that says how to build it.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+c_int, c_int64, c_uint64, c_double, c_size_t, c_void_p, c_char_p = (
+    ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_char_p)
+
+RLOBPCG_OK = 0
+RLOBPCG_NOT_CONVERGED = 1
+RLOBPCG_ERR_INVALID_ARG = -1
+RLOBPCG_ERR_OOM = -2
+RLOBPCG_ERR_CUDA = -3
+RLOBPCG_ERR_NONFINITE = -4
+RLOBPCG_ERR_TIMEOUT = -5
+RLOBPCG_ERR_UNSUPPORTED = -6
+RLOBPCG_F64 = 0
+RLOBPCG_C128 = 1
+RLOBPCG_SKETCH_F64 = 0
+RLOBPCG_SKETCH_F32 = 1
+RLOBPCG_STOP_CONVERGED = 0
+RLOBPCG_STOP_MAX_ITER = 1
+RLOBPCG_STOP_FIXED = 2
+
+
+class rlobpcg_opts(ctypes.Structure):
+    _fields_ = [("seed", c_uint64), ("d", c_int), ("zeta", c_int), ("block", c_int), ("max_iter", c_int),
+                ("check_every", c_int), ("use_stagnation", c_int), ("sketch_prec", c_int), ("fixed_iters", c_int),
+                ("residual_refresh_every", c_int), ("tau", c_double)]
+
+
+class rlobpcg_info(ctypes.Structure):
+    _fields_ = [("iters", c_int), ("matvecs", c_int), ("stop_reason", c_int), ("block", c_int),
+                ("sigma11", c_double), ("ms_sketch", c_double), ("ms_factor", c_double), ("ms_iterate", c_double),
+                ("ms_total", c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class RlobpcgError(RuntimeError):
+    def __init__(self, fn, code):
+        self.code = code
+        super().__init__(f"{fn} failed: {rlobpcg_status_string(code)} ({code}); {rlobpcg_last_error()}")
+
+
+_SIGS = {
+    "rlobpcg_default_opts": (c_int, [ctypes.POINTER(rlobpcg_opts)]),
+    "rlobpcg_plan": (c_int, [ctypes.POINTER(c_void_p), c_int64, c_int64, c_int, c_int, ctypes.POINTER(rlobpcg_opts),
+                             c_void_p]),
+    "rlobpcg_solve": (c_int, [c_void_p, c_void_p, c_int64, c_double, c_void_p, c_void_p, c_void_p, c_void_p,
+                              ctypes.POINTER(rlobpcg_info)]),
+    "rlobpcg_plan_destroy": (c_int, [c_void_p]),
+    "rlobpcg_status_string": (c_char_p, [c_int]),
+    "rlobpcg_last_error": (c_char_p, []),
+    "rlobpcg_sketch": (c_int, [c_void_p, c_int64, c_int64, c_int64, c_int, c_int, c_int, c_uint64, c_int, c_void_p,
+                               c_void_p]),
+    "rlobpcg_factor": (c_int, [c_void_p, c_int64, c_int64, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p,
+                               c_void_p, c_size_t, c_void_p]),
+    "rlobpcg_factor_workspace_size": (c_size_t, [c_int64, c_int64, c_int, c_int]),
+    "rlobpcg_gram": (c_int, [c_void_p, c_int64, c_int64, c_int64, c_int, c_void_p, c_int, c_int64, c_void_p, c_int64,
+                             c_void_p, c_int64, c_void_p, c_size_t, c_void_p]),
+    "rlobpcg_gram_workspace_size": (c_size_t, [c_int64, c_int64, c_int, c_int]),
+    "rlobpcg_tsqr": (c_int, [c_void_p, c_int64, c_int, c_int64, c_int, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "rlobpcg_tsqr_workspace_size": (c_size_t, [c_int64, c_int, c_int]),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False) -> ctypes.CDLL:
+    """Load librlobpcg.so (the in-tree build). Raises if it is missing, unless asked to build."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"{path} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'` "
+                               "or paper_2602_16797_gb300.build.build() (needs nvcc)")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def declared_symbols() -> list[str]:
+    return list(_SIGS)
+
+
+def _check(fn, rc, ok=(RLOBPCG_OK,)):
+    if rc not in ok:
+        raise RlobpcgError(fn, rc)
+    return rc
+
+
+# ---- thin wrappers, one per C entry point ------------------------------------------------------
+
+def rlobpcg_status_string(code: int) -> str:
+    return load().rlobpcg_status_string(code).decode()
+
+
+def rlobpcg_last_error() -> str:
+    return load().rlobpcg_last_error().decode()
+
+
+def rlobpcg_default_opts() -> rlobpcg_opts:
+    o = rlobpcg_opts()
+    _check("rlobpcg_default_opts", load().rlobpcg_default_opts(ctypes.byref(o)))
+    return o
+
+
+def rlobpcg_plan(m: int, n: int, k: int, dtype: int, opts: rlobpcg_opts | None = None, stream: int = 0) -> int:
+    h = c_void_p()
+    rc = load().rlobpcg_plan(ctypes.byref(h), m, n, k, dtype, ctypes.byref(opts) if opts is not None else None, stream)
+    _check("rlobpcg_plan", rc)
+    return h.value
+
+
+def rlobpcg_solve(plan: int, A: int, lda: int, tol: float, sigma: int, V: int, U: int | None = None,
+                  resid: int | None = None, info: rlobpcg_info | None = None) -> int:
+    rc = load().rlobpcg_solve(plan, A, lda, tol, sigma, V, U, resid, ctypes.byref(info) if info is not None else None)
+    return _check("rlobpcg_solve", rc, ok=(RLOBPCG_OK, RLOBPCG_NOT_CONVERGED))
+
+
+def rlobpcg_plan_destroy(plan: int) -> None:
+    _check("rlobpcg_plan_destroy", load().rlobpcg_plan_destroy(plan))
+
+
+def rlobpcg_sketch(A: int, m: int, n: int, lda: int, dtype: int, d: int, zeta: int, seed: int, sketch_prec: int,
+                   SA: int, stream: int = 0) -> None:
+    _check("rlobpcg_sketch", load().rlobpcg_sketch(A, m, n, lda, dtype, d, zeta, seed, sketch_prec, SA, stream))
+
+
+def rlobpcg_factor_workspace_size(d: int, n: int, dtype: int, sketch_prec: int) -> int:
+    return load().rlobpcg_factor_workspace_size(d, n, dtype, sketch_prec)
+
+
+def rlobpcg_factor(SA: int, d: int, n: int, dtype: int, sketch_prec: int, R: int | None, sigma: int, Vt: int,
+                   Rinv: int | None, work: int, work_bytes: int, stream: int = 0) -> None:
+    _check("rlobpcg_factor", load().rlobpcg_factor(SA, d, n, dtype, sketch_prec, R, sigma, Vt, Rinv, work, work_bytes,
+                                                   stream))
+
+
+def rlobpcg_gram_workspace_size(m: int, n: int, b: int, dtype: int) -> int:
+    return load().rlobpcg_gram_workspace_size(m, n, b, dtype)
+
+
+def rlobpcg_gram(A: int, m: int, n: int, lda: int, dtype: int, W: int, b: int, ldw: int, AW: int, ldaw: int, G: int,
+                 ldg: int, work: int, work_bytes: int, stream: int = 0) -> None:
+    _check("rlobpcg_gram", load().rlobpcg_gram(A, m, n, lda, dtype, W, b, ldw, AW, ldaw, G, ldg, work, work_bytes,
+                                               stream))
+
+
+def rlobpcg_tsqr_workspace_size(m: int, c: int, dtype: int) -> int:
+    return load().rlobpcg_tsqr_workspace_size(m, c, dtype)
+
+
+def rlobpcg_tsqr(X: int, m: int, c: int, ldx: int, dtype: int, R: int, work: int, work_bytes: int,
+                 stream: int = 0) -> None:
+    _check("rlobpcg_tsqr", load().rlobpcg_tsqr(X, m, c, ldx, dtype, R, work, work_bytes, stream))
+
+
+# ---- convenience for torch tensors (still only marshalling) -----------------------------------
+
+def _torch_dtype_code(t) -> int:
+    import torch
+    if t.dtype == torch.float64:
+        return RLOBPCG_F64
+    if t.dtype == torch.complex128:
+        return RLOBPCG_C128
+    raise TypeError("A must be float64 or complex128")
+
+
+def solve(A, k: int, *, opts: rlobpcg_opts | None = None, tol: float = -1.0, want_u: bool = False,
+          stream: int | None = None):
+    """Smallest k singular triplets of A (torch tensor, CUDA or CPU-pinned; float64/complex128).
+
+    Returns (sigma [k] float64 CPU tensor, V [n, k], U [m, k] or None, resid [k], info dict).
+    """
+    import torch
+    m, n = A.shape
+    dtype = _torch_dtype_code(A)
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
+    plan = rlobpcg_plan(m, n, k, dtype, opts, stream)
+    try:
+        dev = A.device if A.is_cuda else torch.device("cuda")
+        sigma = torch.empty(k, dtype=torch.float64, device=dev)
+        resid = torch.empty(k, dtype=torch.float64, device=dev)
+        V = torch.empty((n, k), dtype=A.dtype, device=dev)
+        U = torch.empty((m, k), dtype=A.dtype, device=dev) if want_u else None
+        info = rlobpcg_info()
+        rc = rlobpcg_solve(plan, A.data_ptr(), A.stride(0), tol, sigma.data_ptr(), V.data_ptr(),
+                           U.data_ptr() if U is not None else None, resid.data_ptr(), info)
+        out = info.as_dict()
+        out["status"] = rc
+        return sigma, V, U, resid, out
+    finally:
+        rlobpcg_plan_destroy(plan)
