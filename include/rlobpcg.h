@@ -80,6 +80,9 @@ typedef struct {
   double ms_factor;     /* QR of SA, SVD of R, R^{-1}, start block                                 */
   double ms_iterate;    /* LOBPCG iterations                                                       */
   double ms_total;      /* whole solve, including host<->device copies done by the call            */
+  double ms_gram;       /* device time of the fused Gram passes (CUDA events on the plan's stream)  */
+  int gram_passes;      /* number of Gram passes in ms_gram                                         */
+  int kernel_launches;  /* CUDA kernels this solve launched                                         */
 } rlobpcg_info;
 
 typedef struct rlobpcg_plan_s* rlobpcg_plan_t;

@@ -21,6 +21,10 @@ template <class T>
 int tsqr_impl(const T* X, int64_t m, int c, int64_t ldx, T* R, void* work, size_t work_bytes, cudaStream_t st);
 
 static thread_local char g_last_error[512] = "";
+static thread_local long g_launches = 0;
+
+void note_launch() { ++g_launches; }
+long launch_count() { return g_launches; }
 
 void set_last_error(const char* msg, const char* file, int line) {
   const char* base = strrchr(file, '/');

@@ -181,7 +181,11 @@ struct Status {
       return RLOBPCG_ERR_CUDA; }                                                \
   } while (0)
 
-#define RL_CHECK_LAUNCH() RL_CUDA(cudaGetLastError())
+// every kernel launch is followed by RL_CHECK_LAUNCH(), which also counts it
+#define RL_CHECK_LAUNCH() do { ::rl::note_launch(); RL_CUDA(cudaGetLastError()); } while (0)
+
+void note_launch();
+long launch_count();
 
 void set_last_error(const char* msg, const char* file, int line);
 const char* last_error();

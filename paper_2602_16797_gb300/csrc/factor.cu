@@ -169,7 +169,10 @@ __global__ void __launch_bounds__(FQ_THREADS) jacobi_kernel(S* X, S* V, int n, i
   const int NW = gridDim.x * FQ_WARPS;
   const int N = n + (n & 1);
   using R = RealOf<S>;
-  const R tol = sqrt_((R)n) * eps_of<S>();
+  // a pair counts as orthogonal when |x_p^H x_q| <= n eps ||x_p|| ||x_q||: the computed cosine
+  // carries about n u of rounding noise, so a tighter test would never be met and every sweep
+  // would rotate noise
+  const R tol = (R)n * eps_of<S>();
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
     if (blockIdx.x == 0 && threadIdx.x == 0) flags[(sweep + 1) % 3] = 0;
@@ -313,6 +316,7 @@ int factor_impl(S* SA, int d, int n, S* Rout, double* sigma, S* Vt, S* Rinv_r, S
   {
     void* args[] = {(void*)&SA, (void*)&d, (void*)&n, (void*)&tau};
     RL_CUDA(cudaLaunchCooperativeKernel((void*)qr_kernel<S>, dim3(G), dim3(FQ_THREADS), args, 0, st));
+    note_launch();
   }
   const int64_t nn = (int64_t)n * n;
   const int eb = 256, eg = (int)((nn + eb - 1) / eb);
@@ -340,6 +344,7 @@ int factor_impl(S* SA, int d, int n, S* Rout, double* sigma, S* Vt, S* Rinv_r, S
   {
     void* args[] = {(void*)&X, (void*)&V, (void*)&n, (void*)&max_sweeps, (void*)&flags, (void*)&sweeps_dev};
     RL_CUDA(cudaLaunchCooperativeKernel((void*)jacobi_kernel<S>, dim3(G), dim3(FQ_THREADS), args, 0, st));
+    note_launch();
   }
   colnorm_kernel<S><<<(n * 32 + 255) / 256, 256, 0, st>>>(X, n, nrm);
   RL_CHECK_LAUNCH();

@@ -160,7 +160,8 @@ __global__ void __launch_bounds__(1024) rr_small_kernel(const T* __restrict__ Rt
   }
   __syncthreads();
   const int N = c + (c & 1);
-  const double tol = sqrt((double)c) * 2.220446049250313e-16;
+  // orthogonality test |x_p^H x_q| <= c eps ||x_p|| ||x_q|| (the cosine carries ~c u of noise)
+  const double tol = (double)imax(c, 4) * 2.220446049250313e-16;
   int sweep = 0;
   for (; sweep < 60; ++sweep) {
     if (tid == 0) changed = 0;
@@ -340,13 +341,13 @@ __global__ void __launch_bounds__(256) update_kernel(UpdSeg<T> s0, UpdSeg<T> s1,
 }
 
 // ------------------------------------------------------------------------------------------
-// residual: Res = G_V - V diag(theta_s^2); norms; Rs = Res / ||Res(:,j)|| in precision S.
-// One CTA, one warp per column.
+// residual: Res = G_V - V diag(theta_s^2); norms; Rs = Res / ||Res(:,j)|| (the preconditioner
+// input, unit columns). One CTA, one warp per column.
 // ------------------------------------------------------------------------------------------
-template <class T, class S>
+template <class T>
 __global__ void __launch_bounds__(1024) residual_kernel(const T* __restrict__ Tbuf, const T* __restrict__ Gbuf,
                                                          int n, int b, int64_t ld, const double* theta_s,
-                                                         T* Res, double* res_norm, S* Rs, int* err) {
+                                                         T* Res, double* res_norm, T* Rs, int* err) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
   for (int j = warp; j < b; j += nwarp) {
     const double th2 = theta_s[j] * theta_s[j];
@@ -363,29 +364,31 @@ __global__ void __launch_bounds__(1024) residual_kernel(const T* __restrict__ Tb
       if (!isfinite(nr)) atomicOr(err, DEV_ERR_NONFINITE);
     }
     const double inv = nr > 0.0 ? 1.0 / nr : 0.0;
-    for (int k = lane; k < n; k += 32) Rs[(int64_t)k * b + j] = cvt_<S, T>(scale_(Res[(int64_t)k * b + j], inv));
+    for (int k = lane; k < n; k += 32) Rs[(int64_t)k * b + j] = scale_(Res[(int64_t)k * b + j], inv);
   }
 }
 
 // ------------------------------------------------------------------------------------------
-// trimul: Y = L X with L an n x n matrix (row-major, ldl = n, only the triangle l in
-// [lo(k), hi(k)] used) in precision S, X n x b (row-major, ldx) in precision S; Y in precision
-// TO (row-major, ldy). One warp per output row. conj_l conjugates L's entries.
+// trimul: Y = L X with L an n x n matrix (row-major, only the triangle l in [lo(k), hi(k)] used)
+// STORED in precision S (the sketch side: FP32 in the mixed form), X and Y (n x b, row-major) in
+// the working precision T. Every entry of L is widened to T on load and all arithmetic is in T:
+// the factor may be rounded to FP32, its application may not (with kappa(R) >> 1/u_32 an FP32
+// product would lose exactly the directions of the smallest singular values). One warp per row.
 // ------------------------------------------------------------------------------------------
-template <class S, class TO>
-__global__ void trimul_kernel(const S* __restrict__ L, int n, const S* __restrict__ X, int64_t ldx, int b,
-                              TO* __restrict__ Y, int64_t ldy, int lower, int conj_l) {
+template <class S, class T>
+__global__ void trimul_kernel(const S* __restrict__ L, int n, const T* __restrict__ X, int64_t ldx, int b,
+                              T* __restrict__ Y, int64_t ldy, int lower, int conj_l) {
   const int k = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (k >= n) return;
   const int lo = lower ? 0 : k, hi = lower ? k : n - 1;
   const S* Lk = L + (int64_t)k * n;
   for (int c0 = 0; c0 < b; c0 += 8) {
-    S acc[8];
+    T acc[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) acc[q] = zero_<S>();
+    for (int q = 0; q < 8; ++q) acc[q] = zero_<T>();
     for (int l = lo + lane; l <= hi; l += 32) {
-      const S lk = conj_l ? conj_(Lk[l]) : Lk[l];
+      const T lk = cvt_<T, S>(conj_l ? conj_(Lk[l]) : Lk[l]);
 #pragma unroll
       for (int q = 0; q < 8; ++q)
         if (c0 + q < b) acc[q] = mad_(lk, X[(int64_t)l * ldx + c0 + q], acc[q]);
@@ -393,8 +396,8 @@ __global__ void trimul_kernel(const S* __restrict__ L, int n, const S* __restric
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       if (c0 + q < b) {
-        const S s = warp_sum(acc[q]);
-        if (lane == 0) Y[(int64_t)k * ldy + c0 + q] = cvt_<TO, S>(s);
+        const T s = warp_sum(acc[q]);
+        if (lane == 0) Y[(int64_t)k * ldy + c0 + q] = s;
       }
     }
   }
@@ -638,25 +641,24 @@ int update_launch(T* Tb, int64_t n, T* ATb, int64_t m, T* GTb, int64_t ld, int c
 template int update_launch<double>(double*, int64_t, double*, int64_t, double*, int64_t, int, int, const double*, cudaStream_t);
 template int update_launch<cd>(cd*, int64_t, cd*, int64_t, cd*, int64_t, int, int, const cd*, cudaStream_t);
 
-template <class T, class S>
+template <class T>
 int residual_launch(const T* Tb, const T* Gb, int n, int b, int64_t ld, const double* theta_s, T* Res, double* res_norm,
-                    S* Rs, int* err, cudaStream_t st) {
-  residual_kernel<T, S><<<1, min(1024, b * 32), 0, st>>>(Tb, Gb, n, b, ld, theta_s, Res, res_norm, Rs, err);
+                    T* Rs, int* err, cudaStream_t st) {
+  residual_kernel<T><<<1, min(1024, b * 32), 0, st>>>(Tb, Gb, n, b, ld, theta_s, Res, res_norm, Rs, err);
   RL_CHECK_LAUNCH();
   return RLOBPCG_OK;
 }
-template int residual_launch<double, double>(const double*, const double*, int, int, int64_t, const double*, double*, double*, double*, int*, cudaStream_t);
-template int residual_launch<double, float>(const double*, const double*, int, int, int64_t, const double*, double*, double*, float*, int*, cudaStream_t);
-template int residual_launch<cd, cd>(const cd*, const cd*, int, int, int64_t, const double*, cd*, double*, cd*, int*, cudaStream_t);
-template int residual_launch<cd, cf>(const cd*, const cd*, int, int, int64_t, const double*, cd*, double*, cf*, int*, cudaStream_t);
+template int residual_launch<double>(const double*, const double*, int, int, int64_t, const double*, double*, double*, double*, int*, cudaStream_t);
+template int residual_launch<cd>(const cd*, const cd*, int, int, int64_t, const double*, cd*, double*, cd*, int*, cudaStream_t);
 
-// W = Rinv (Rinv^H Rs): Y (n x b, precision S) scratch; W written into T columns [wo, wo+b)
+// W = Rinv (Rinv^H Rs): Rinv stored in precision S, applied in precision T; Y (n x b, T) scratch;
+// W written into T columns [wo, wo+b)
 template <class T, class S>
-int precond_launch(const S* Rinv_r, const S* Rinv_c, int n, int b, const S* Rs, S* Y, T* Tb, int64_t ld, int wo,
+int precond_launch(const S* Rinv_r, const S* Rinv_c, int n, int b, const T* Rs, T* Y, T* Tb, int64_t ld, int wo,
                    cudaStream_t st) {
   const int blocks = (n * 32 + 255) / 256;
   // Y(k) = sum_{l <= k} conj(Rinv(l, k)) Rs(l): row k of Rinv^H = conj(column k of Rinv)
-  trimul_kernel<S, S><<<blocks, 256, 0, st>>>(Rinv_c, n, Rs, b, b, Y, b, 1, 1);
+  trimul_kernel<S, T><<<blocks, 256, 0, st>>>(Rinv_c, n, Rs, b, b, Y, b, 1, 1);
   RL_CHECK_LAUNCH();
   // W(k) = sum_{l >= k} Rinv(k, l) Y(l)
   trimul_kernel<S, T><<<blocks, 256, 0, st>>>(Rinv_r, n, Y, b, b, Tb + wo, ld, 0, 0);
@@ -664,9 +666,9 @@ int precond_launch(const S* Rinv_r, const S* Rinv_c, int n, int b, const S* Rs, 
   return RLOBPCG_OK;
 }
 template int precond_launch<double, double>(const double*, const double*, int, int, const double*, double*, double*, int64_t, int, cudaStream_t);
-template int precond_launch<double, float>(const float*, const float*, int, int, const float*, float*, double*, int64_t, int, cudaStream_t);
+template int precond_launch<double, float>(const float*, const float*, int, int, const double*, double*, double*, int64_t, int, cudaStream_t);
 template int precond_launch<cd, cd>(const cd*, const cd*, int, int, const cd*, cd*, cd*, int64_t, int, cudaStream_t);
-template int precond_launch<cd, cf>(const cf*, const cf*, int, int, const cf*, cf*, cd*, int64_t, int, cudaStream_t);
+template int precond_launch<cd, cf>(const cf*, const cf*, int, int, const cd*, cd*, cd*, int64_t, int, cudaStream_t);
 
 template <class T>
 int bcgs2_orth_launch(T* Tb, int n, int b, int64_t ld, int wo, int nx, T* E, int passes, cudaStream_t st) {

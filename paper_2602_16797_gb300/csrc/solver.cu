@@ -32,11 +32,11 @@ template <class T>
 int rr_small_launch(const T* Rt, int c, int b, double* theta, T* K, int* info, cudaStream_t st);
 template <class T>
 int update_launch(T* Tb, int64_t n, T* ATb, int64_t m, T* GTb, int64_t ld, int c, int b, const T* K, cudaStream_t st);
-template <class T, class S>
+template <class T>
 int residual_launch(const T* Tb, const T* Gb, int n, int b, int64_t ld, const double* theta_s, T* Res,
-                    double* res_norm, S* Rs, int* err, cudaStream_t st);
+                    double* res_norm, T* Rs, int* err, cudaStream_t st);
 template <class T, class S>
-int precond_launch(const S* Rinv_r, const S* Rinv_c, int n, int b, const S* Rs, S* Y, T* Tb, int64_t ld, int wo,
+int precond_launch(const S* Rinv_r, const S* Rinv_c, int n, int b, const T* Rs, T* Y, T* Tb, int64_t ld, int wo,
                    cudaStream_t st);
 template <class T>
 int bcgs2_orth_launch(T* Tb, int n, int b, int64_t ld, int wo, int nx, T* E, int passes, cudaStream_t st);
@@ -85,7 +85,7 @@ struct rlobpcg_plan_s {
   size_t gwork_bytes = 0;
   void* twork = nullptr;
   size_t twork_bytes = 0;
-  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   std::vector<void*> owned;
 };
 
@@ -153,6 +153,9 @@ int solve_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, double tau, double* s
   T* GTb = (T*)p->GTb;
   int rc;
 #define RL_TRY(x) do { rc = (x); if (rc) return rc; } while (0)
+  const long launches0 = launch_count();
+  double gram_ms = 0;
+  int gram_passes = 0;
   RL_CUDA(cudaMemsetAsync(p->err, 0, sizeof(int), st));
   RL_CUDA(cudaEventRecord(p->ev[0], st));
   RL_TRY(nonfinite_scan_launch<T>(A, m, n, lda, p->err, st));
@@ -176,7 +179,7 @@ int solve_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, double tau, double* s
   RL_TRY(tsqr_impl<T>(ATb, m, b, ld, (T*)p->Rt, p->twork, p->twork_bytes, st));
   RL_TRY(rr_small_launch<T>((const T*)p->Rt, b, b, p->theta, (T*)p->K, p->info, st));
   RL_TRY(update_launch<T>(Tb, n, ATb, m, GTb, ld, b, b, (const T*)p->K, st));
-  RL_TRY((residual_launch<T, S>(Tb, GTb, n, b, ld, p->theta, (T*)p->Res, p->res_norm, (S*)p->Rs, p->err, st)));
+  RL_TRY((residual_launch<T>(Tb, GTb, n, b, ld, p->theta, (T*)p->Res, p->res_norm, (T*)p->Rs, p->err, st)));
   RL_CUDA(cudaEventRecord(p->ev[2], st));
 
   StopRule hist;
@@ -196,11 +199,13 @@ int solve_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, double tau, double* s
   const double* theta_s = p->theta;
   for (int i = 0; i < max_iter; ++i) {
     // W = P (P^* R_i), then BCGS2 against [V X] and Orth
-    RL_TRY((precond_launch<T, S>((const S*)p->Rinv_r, (const S*)p->Rinv_c, n, b, (const S*)p->Rs, (S*)p->Y, Tb, ld, b, st)));
+    RL_TRY((precond_launch<T, S>((const S*)p->Rinv_r, (const S*)p->Rinv_c, n, b, (const T*)p->Rs, (T*)p->Y, Tb, ld, b, st)));
     RL_TRY(bcgs2_orth_launch<T>(Tb, n, b, ld, b, nx, (T*)p->E, 2, st));
-    // A W and A^H (A W) in one pass over A
+    // A W and A^H (A W) in one pass over A (timed with events on this stream)
+    RL_CUDA(cudaEventRecord(p->ev[5], st));
     RL_TRY(gram_dispatch(A, m, n, lda, p->dtype, Tb + b, b, ld, ATb + b, ld, GTb + b, ld, p->gwork, p->gwork_bytes, 0,
                          p->err, st));
+    RL_CUDA(cudaEventRecord(p->ev[6], st));
     matvecs += b;
     // Rayleigh-Ritz by SVD of A_T (TSQR + Jacobi of R_T)
     const int c = 2 * b + nx;
@@ -213,10 +218,16 @@ int solve_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, double tau, double* s
                            p->err, st));
       matvecs += b;
     }
-    RL_TRY((residual_launch<T, S>(Tb, GTb, n, b, ld, theta_s, (T*)p->Res, p->res_norm, (S*)p->Rs, p->err, st)));
+    RL_TRY((residual_launch<T>(Tb, GTb, n, b, ld, theta_s, (T*)p->Res, p->res_norm, (T*)p->Rs, p->err, st)));
     RL_CUDA(cudaMemcpyAsync(hr.data(), p->res_norm, b * sizeof(double), cudaMemcpyDeviceToHost, st));
     RL_CUDA(cudaMemcpyAsync(ht.data(), theta_s, b * sizeof(double), cudaMemcpyDeviceToHost, st));
     RL_CUDA(cudaStreamSynchronize(st));
+    {
+      float gms = 0;
+      RL_CUDA(cudaEventElapsedTime(&gms, p->ev[5], p->ev[6]));
+      gram_ms += gms;
+      ++gram_passes;
+    }
     hist.r.push_back(hr);
     hist.th.push_back(ht);
     it = i + 1;
@@ -260,6 +271,9 @@ int solve_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, double tau, double* s
     cudaEventElapsedTime(&ms, p->ev[1], p->ev[2]); info->ms_factor = ms;
     cudaEventElapsedTime(&ms, p->ev[2], p->ev[3]); info->ms_iterate = ms;
     cudaEventElapsedTime(&ms, p->ev[0], p->ev[4]); info->ms_total = ms;
+    info->ms_gram = gram_ms;
+    info->gram_passes = gram_passes;
+    info->kernel_launches = (int)(launch_count() - launches0);
   }
   if (herr & DEV_ERR_TIMEOUT) return RLOBPCG_ERR_TIMEOUT;
   if (herr & DEV_ERR_NONFINITE) return RLOBPCG_ERR_NONFINITE;
@@ -327,8 +341,8 @@ extern "C" int rlobpcg_plan(rlobpcg_plan_t* out, int64_t m, int64_t n, int k, in
   RL_A(p->GTb, (size_t)n * ld * esz);
   RL_A(p->E, (size_t)n * b * esz);
   RL_A(p->Res, (size_t)n * b * esz);
-  RL_A(p->Rs, (size_t)n * b * ssz);
-  RL_A(p->Y, (size_t)std::max<int64_t>(n * b, 64) * std::max(ssz, (size_t)8));
+  RL_A(p->Rs, (size_t)n * b * esz);
+  RL_A(p->Y, (size_t)std::max<int64_t>(n * b, 64) * esz);
   RL_A(p->Rt, (size_t)ld * ld * esz);
   RL_A(p->K, (size_t)ld * 2 * b * esz);
   RL_A(p->theta, (size_t)ld * sizeof(double));
