@@ -179,6 +179,25 @@ int rlobpcg_gram(const void* A, int64_t m, int64_t n, int64_t lda, int dtype, co
 size_t rlobpcg_gram_workspace_size(int64_t m, int64_t n, int b, int dtype);
 
 /*
+ * Allocation-free variant of rlobpcg_gram (the paper has no counterpart; it is an addition of
+ * this library). Same arguments, results and errors as rlobpcg_gram, minus the workspace: the
+ * split-m scratch is a fixed 16 MiB device buffer inside the library (plus 256 bytes for the
+ * error word), held on every GPU that loads the library until the process exits.
+ * For callers that cannot let a library allocate device memory: a serving process that has
+ * budgeted all of HBM at start-up, or a loop that must avoid cudaMalloc/cudaFree because they
+ * synchronise the whole device. This call makes no allocation of any kind.
+ *   - The first call on a device looks up the buffer's device address (once per device, with
+ *     that device current); make that first call before any stream capture.
+ *   - All calls share the one buffer, which keeps the last call's contents: calls that overlap
+ *     on the GPU (other streams, other threads) race and must be serialised by the caller.
+ *   - Problems whose partials need more than 16 MiB (about 152 * n * b * 8 bytes for real A,
+ *     twice that for complex) are rejected with RLOBPCG_ERR_UNSUPPORTED and a message in
+ *     rlobpcg_last_error(); use rlobpcg_gram for those.
+ */
+int rlobpcg_gram_noalloc(const void* A, int64_t m, int64_t n, int64_t lda, int dtype, const void* W, int b,
+                         int64_t ldw, void* AW, int64_t ldaw, void* G, int64_t ldg, void* stream);
+
+/*
  * R factor of a tall block (the TSQR used for Rayleigh-Ritz by SVD of A_T, Alg. 2): X is m x c
  * row-major (ldx), c <= 64; R (c x c, row-major, upper triangular, diag(R) real >= 0) is written
  * to device memory. Householder reflections per row block, then a fixed-order tree of stacked

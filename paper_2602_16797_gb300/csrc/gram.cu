@@ -14,6 +14,8 @@
 // per output). Phase 2: thread k accumulates G[k, :] += conj(A[r, k]) Y[r, :] over the tile
 // into a shared-memory accumulator. Each CTA writes its n x b partial; a second kernel sums the
 // partials in CTA order. Every result is deterministic.
+#include <mutex>
+
 #include "common.cuh"
 
 namespace rl {
@@ -285,4 +287,80 @@ int gram_launch_info(int64_t m, int64_t n, int b, int dtype, int* grid, int* rt,
   return RLOBPCG_OK;
 }
 
+
+// ------------------------------------------------------------------------------------------------
+// Allocation-free entry point of the fused Gram pass.
+//
+// Some callers cannot let a library allocate device memory: a serving process that budgets all
+// of HBM up front and admits work only into memory it already owns, or a real-time loop that
+// must not call cudaMalloc/cudaFree because they synchronise the whole device and stall every
+// other stream's work. rlobpcg_gram_noalloc serves them: its scratch (the per-SM partial
+// sums and the device error word) is a file-scope device array of fixed size, so the call makes
+// no allocation at all. The array lives as long as the library is loaded, on every GPU that uses
+// it, and all calls share it.
+// ------------------------------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoallocPartBytes = (size_t)16 << 20;  // room for the split-m partials: 16 MiB
+constexpr size_t kNoallocHeadBytes = 256;                // the error word, padded to 256 bytes
+
+static __device__ __align__(256) unsigned char g_gram_noalloc_scratch[kNoallocHeadBytes + kNoallocPartBytes];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_base[64] = {};
+
+// Device address of the static scratch on the current device, looked up once per device.
+int noalloc_scratch(void** out) {
+  int dev = 0;
+  RL_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return RLOBPCG_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_base[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_gram_noalloc_scratch);
+    if (e != cudaSuccess || p == nullptr) {
+      cudaGetLastError();
+      set_last_error(e != cudaSuccess ? cudaGetErrorString(e) : "null symbol address", __FILE__, __LINE__);
+      return RLOBPCG_ERR_CUDA;
+    }
+    g_noalloc_base[dev] = p;
+  }
+  *out = g_noalloc_base[dev];
+  return RLOBPCG_OK;
+}
+
+}  // namespace
+
 }  // namespace rl
+
+extern "C" int rlobpcg_gram_noalloc(const void* A, int64_t m, int64_t n, int64_t lda, int dtype, const void* W, int b,
+                                    int64_t ldw, void* AW, int64_t ldaw, void* G, int64_t ldg, void* stream) {
+  using namespace rl;
+  if (!A || !W || !AW || !G || m < 1 || n < 1 || b < 1 || b > 64 || lda < n || ldw < b || ldaw < b || ldg < b ||
+      (dtype != RLOBPCG_F64 && dtype != RLOBPCG_C128))
+    return RLOBPCG_ERR_INVALID_ARG;
+  const size_t need = gram_workspace_bytes(m, n, b, dtype);
+  if (need == 0) {
+    set_last_error("rlobpcg_gram_noalloc: n * b too large for on-chip accumulation", __FILE__, __LINE__);
+    return RLOBPCG_ERR_UNSUPPORTED;
+  }
+  if (need > kNoallocPartBytes) {
+    set_last_error("rlobpcg_gram_noalloc: this m, n, b needs more split-m scratch than its fixed 16 MiB "
+                   "buffer holds; use rlobpcg_gram with caller-provided workspace", __FILE__, __LINE__);
+    return RLOBPCG_ERR_UNSUPPORTED;
+  }
+  void* base = nullptr;
+  int rc = noalloc_scratch(&base);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  int* err = (int*)base;
+  void* part = (unsigned char*)base + kNoallocHeadBytes;
+  // the partials are fully overwritten by every call; only the error word must start at zero
+  RL_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+  rc = gram_dispatch(A, m, n, lda, dtype, W, b, ldw, AW, ldaw, G, ldg, part, kNoallocPartBytes, 0, err, st);
+  if (rc) return rc;
+  int herr = 0;
+  RL_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  RL_CUDA(cudaStreamSynchronize(st));
+  return (herr & DEV_ERR_TIMEOUT) ? RLOBPCG_ERR_TIMEOUT : RLOBPCG_OK;
+}

@@ -70,6 +70,8 @@ _SIGS = {
     "rlobpcg_gram": (c_int, [c_void_p, c_int64, c_int64, c_int64, c_int, c_void_p, c_int, c_int64, c_void_p, c_int64,
                              c_void_p, c_int64, c_void_p, c_size_t, c_void_p]),
     "rlobpcg_gram_workspace_size": (c_size_t, [c_int64, c_int64, c_int, c_int]),
+    "rlobpcg_gram_noalloc": (c_int, [c_void_p, c_int64, c_int64, c_int64, c_int, c_void_p, c_int, c_int64, c_void_p,
+                                     c_int64, c_void_p, c_int64, c_void_p]),
     "rlobpcg_tsqr": (c_int, [c_void_p, c_int64, c_int, c_int64, c_int, c_void_p, c_void_p, c_size_t, c_void_p]),
     "rlobpcg_tsqr_workspace_size": (c_size_t, [c_int64, c_int, c_int]),
 }
@@ -167,6 +169,13 @@ def rlobpcg_gram(A: int, m: int, n: int, lda: int, dtype: int, W: int, b: int, l
                  ldg: int, work: int, work_bytes: int, stream: int = 0) -> None:
     _check("rlobpcg_gram", load().rlobpcg_gram(A, m, n, lda, dtype, W, b, ldw, AW, ldaw, G, ldg, work, work_bytes,
                                                stream))
+
+
+def rlobpcg_gram_noalloc(A: int, m: int, n: int, lda: int, dtype: int, W: int, b: int, ldw: int, AW: int,
+                         ldaw: int, G: int, ldg: int, stream: int = 0) -> None:
+    """rlobpcg_gram without a workspace argument (scratch is the library's fixed device buffer)."""
+    _check("rlobpcg_gram_noalloc", load().rlobpcg_gram_noalloc(A, m, n, lda, dtype, W, b, ldw, AW, ldaw, G, ldg,
+                                                               stream))
 
 
 def rlobpcg_tsqr_workspace_size(m: int, c: int, dtype: int) -> int:
