@@ -252,6 +252,7 @@ def run_ours(args, rank, world, local_rank):
                        "l2": "inputs (400 MB each) larger than L2; no flush", "parallelism": f"replicas x{world}"},
             "latency_ms": {"p50": float(np.percentile(lat_sorted, 50)), "p99": float(np.percentile(lat_sorted, 99))},
             "iters": [x.iters for x in infos], "stop_reasons": [x.stop_reason for x in infos],
+            "jacobi_sweeps": [x.jacobi_sweeps for x in infos],
             "phase_ms": {"sketch": statistics.mean(x.ms_sketch for x in infos),
                          "factor": statistics.mean(x.ms_factor for x in infos),
                          "iterate": statistics.mean(x.ms_iterate for x in infos),

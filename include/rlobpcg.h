@@ -66,6 +66,11 @@ typedef struct {
   int fixed_iters;      /* > 0: run exactly this many iterations, no stop test (parity runs)       */
   int residual_refresh_every; /* > 0: every this many iterations recompute A^H (A V) with a pass
                                  over A instead of the recombined A^H A V (drift control)         */
+  int exact_sketch_svd; /* 1: full one-sided Jacobi SVD of R for V~(:, n-b+1:n) and Sigma~(1,1).
+                           0 (default): only those two, by block inverse iteration with
+                           (R^H R)^{-1} (3 steps, block 2b+4) + Rayleigh-Ritz on R Z, and a block
+                           power iteration for Sigma~(1,1) (8 steps, block 8: about 1% low on a
+                           clustered top spectrum; it only scales the stop tolerance)           */
   double tau;           /* tolerance of ||R(:,j)|| <= Sigma~(1,1)^2 tau; < 0 means 2 sqrt(n) 2^-52 */
 } rlobpcg_opts;
 
@@ -83,6 +88,7 @@ typedef struct {
   double ms_gram;       /* device time of the fused Gram passes (CUDA events on the plan's stream)  */
   int gram_passes;      /* number of Gram passes in ms_gram                                         */
   int kernel_launches;  /* CUDA kernels this solve launched                                         */
+  int jacobi_sweeps;    /* sweeps of the one-sided Jacobi SVD of R                                  */
 } rlobpcg_info;
 
 typedef struct rlobpcg_plan_s* rlobpcg_plan_t;

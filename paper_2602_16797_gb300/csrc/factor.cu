@@ -111,6 +111,15 @@ __global__ void extract_r_kernel(const S* M, int d, int n, S* R) {
   R[idx] = (r <= c) ? M[(int64_t)c * d + r] : zero_<S>();
 }
 
+// R row-major from R column-major (n x n)
+template <class S>
+__global__ void transpose_kernel(const S* Rc, int n, S* Rr) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)n * n) return;
+  const int r = (int)(idx / n), c = (int)(idx % n);
+  Rr[idx] = Rc[(int64_t)c * n + r];
+}
+
 // ------------------------------------------------------------------------------------------
 // One-sided Jacobi SVD (Hestenes; rotation formulas of Demmel & Veselic, SIMAX 1992) on the
 // columns of X (n x n col-major), accumulating V (n x n col-major, starts as I). Round-robin
@@ -121,7 +130,8 @@ __global__ void extract_r_kernel(const S* M, int d, int n, S* R) {
 __device__ inline int rr_slot(int k, int r, int N) { return k == 0 ? 0 : ((k - 1 + r) % (N - 1)) + 1; }
 
 template <class S>
-__device__ void jacobi_pair(S* X, S* V, int n, int p, int q, RealOf<S> tol, int lane, int* changed) {
+__device__ void jacobi_pair(S* X, S* V, int n, int p, int q, RealOf<S> tol, RealOf<S> tiny2, int lane,
+                            int* changed) {
   using R = RealOf<S>;
   S* xp = X + (int64_t)p * n;
   S* xq = X + (int64_t)q * n;
@@ -137,10 +147,16 @@ __device__ void jacobi_pair(S* X, S* V, int n, int p, int q, RealOf<S> tol, int 
   b = warp_sum(b);
   g = warp_sum(g);
   const R ga = sqrt_(abs2_(g));
-  if (!(ga > tol * sqrt_(a) * sqrt_(b)) || a == (R)0 || b == (R)0) return;
+  // columns at rounding level (||x|| <= n eps max_j ||x_j||) are not rotated: their directions
+  // are arbitrary inside the noise subspace, and rotating them would never converge
+  if (!(ga > tol * sqrt_(a) * sqrt_(b)) || a <= tiny2 || b <= tiny2) return;
   const S e = scale_(g, (R)1 / ga);               // e^{i phi}
   const R zeta = (b - a) / ((R)2 * ga);
   const R t = (zeta >= (R)0 ? (R)1 : (R)-1) / (fabs(zeta) + hypot_((R)1, zeta));
+  // a rotation by an angle below eps changes the larger column by less than its rounding and
+  // only re-injects the larger column's rounding noise into the smaller one: skip it, so that
+  // pairs of very different norms stop re-randomising the small columns every sweep
+  if (fabs(t) <= eps_of<S>()) return;
   const R c = (R)1 / sqrt_((R)1 + t * t);
   const R s = c * t;
   const S se = scale_(e, s);                     // s e
@@ -162,7 +178,7 @@ __device__ void jacobi_pair(S* X, S* V, int n, int p, int q, RealOf<S> tol, int 
 
 template <class S>
 __global__ void __launch_bounds__(FQ_THREADS) jacobi_kernel(S* X, S* V, int n, int max_sweeps,
-                                                            int* flags, int* sweeps_out) {
+                                                            int* flags, int* sweeps_out, const double* nrm0) {
   cg::grid_group grid = cg::this_grid();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int gw = blockIdx.x * FQ_WARPS + warp;
@@ -173,6 +189,11 @@ __global__ void __launch_bounds__(FQ_THREADS) jacobi_kernel(S* X, S* V, int n, i
   // carries about n u of rounding noise, so a tighter test would never be met and every sweep
   // would rotate noise
   const R tol = (R)n * eps_of<S>();
+  // rounding-level threshold from the initial column norms (computed before the launch)
+  double mx = 0;
+  for (int j = 0; j < n; ++j) mx = fmax(mx, nrm0[j]);
+  const R tiny = (R)(mx * (double)n * (double)eps_of<S>());
+  const R tiny2 = tiny * tiny;
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
     if (blockIdx.x == 0 && threadIdx.x == 0) flags[(sweep + 1) % 3] = 0;
@@ -182,7 +203,7 @@ __global__ void __launch_bounds__(FQ_THREADS) jacobi_kernel(S* X, S* V, int n, i
         int p = rr_slot(i, r, N), q = rr_slot(N - 1 - i, r, N);
         if (p > q) { int t = p; p = q; q = t; }
         if (q >= n) continue;  // dummy slot of an odd n
-        jacobi_pair(X, V, n, p, q, tol, lane, changed);
+        jacobi_pair(X, V, n, p, q, tol, tiny2, lane, changed);
       }
       grid.sync();
     }
@@ -296,9 +317,11 @@ size_t factor_workspace_bytes(int64_t d, int64_t n, size_t esz) {
   return b;
 }
 
+// Rout (col-major) and Rout_r (row-major) are optional copies of R; with do_svd == false the
+// Jacobi SVD (sigma, Vt) is skipped.
 template <class S>
-int factor_impl(S* SA, int d, int n, S* Rout, double* sigma, S* Vt, S* Rinv_r, S* Rinv_c,
-                void* work, size_t work_bytes, cudaStream_t st, int* sweeps_host) {
+int factor_impl(S* SA, int d, int n, S* Rout, S* Rout_r, double* sigma, S* Vt, S* Rinv_r, S* Rinv_c,
+                void* work, size_t work_bytes, cudaStream_t st, int* sweeps_host, bool do_svd) {
   if (work_bytes < factor_workspace_bytes(d, n, sizeof(S))) return RLOBPCG_ERR_INVALID_ARG;
   unsigned char* p = (unsigned char*)work;
   auto take = [&](size_t x) { void* r = p; p += (x + 255) & ~(size_t)255; return r; };
@@ -323,6 +346,10 @@ int factor_impl(S* SA, int d, int n, S* Rout, double* sigma, S* Vt, S* Rinv_r, S
   extract_r_kernel<S><<<eg, eb, 0, st>>>(SA, d, n, X);
   RL_CHECK_LAUNCH();
   if (Rout) RL_CUDA(cudaMemcpyAsync(Rout, X, nn * sizeof(S), cudaMemcpyDeviceToDevice, st));
+  if (Rout_r) {
+    transpose_kernel<S><<<eg, eb, 0, st>>>(X, n, Rout_r);
+    RL_CHECK_LAUNCH();
+  }
 
   // 3. R^{-1} (before Jacobi overwrites X)
   if (Rinv_r && Rinv_c) {
@@ -332,6 +359,10 @@ int factor_impl(S* SA, int d, int n, S* Rout, double* sigma, S* Vt, S* Rinv_r, S
     RL_CHECK_LAUNCH();
   }
 
+  if (!do_svd) {
+    if (sweeps_host) *sweeps_host = 0;
+    return RLOBPCG_OK;
+  }
   // 2. Jacobi SVD of R
   set_identity_kernel<S><<<eg, eb, 0, st>>>(V, n);
   RL_CHECK_LAUNCH();
@@ -341,8 +372,12 @@ int factor_impl(S* SA, int d, int n, S* Rout, double* sigma, S* Vt, S* Rinv_r, S
   G = min(G, max(1, (n / 2 + FQ_WARPS - 1) / FQ_WARPS));
   int max_sweeps = 40;
   int* sweeps_dev = flags + 3;
+  colnorm_kernel<S><<<(n * 32 + 255) / 256, 256, 0, st>>>(X, n, nrm);
+  RL_CHECK_LAUNCH();
   {
-    void* args[] = {(void*)&X, (void*)&V, (void*)&n, (void*)&max_sweeps, (void*)&flags, (void*)&sweeps_dev};
+    const double* nrm0 = nrm;
+    void* args[] = {(void*)&X, (void*)&V, (void*)&n, (void*)&max_sweeps, (void*)&flags, (void*)&sweeps_dev,
+                    (void*)&nrm0};
     RL_CUDA(cudaLaunchCooperativeKernel((void*)jacobi_kernel<S>, dim3(G), dim3(FQ_THREADS), args, 0, st));
     note_launch();
   }
@@ -354,9 +389,9 @@ int factor_impl(S* SA, int d, int n, S* Rout, double* sigma, S* Vt, S* Rinv_r, S
   return RLOBPCG_OK;
 }
 
-template int factor_impl<double>(double*, int, int, double*, double*, double*, double*, double*, void*, size_t, cudaStream_t, int*);
-template int factor_impl<float>(float*, int, int, float*, double*, float*, float*, float*, void*, size_t, cudaStream_t, int*);
-template int factor_impl<cd>(cd*, int, int, cd*, double*, cd*, cd*, cd*, void*, size_t, cudaStream_t, int*);
-template int factor_impl<cf>(cf*, int, int, cf*, double*, cf*, cf*, cf*, void*, size_t, cudaStream_t, int*);
+template int factor_impl<double>(double*, int, int, double*, double*, double*, double*, double*, double*, void*, size_t, cudaStream_t, int*, bool);
+template int factor_impl<float>(float*, int, int, float*, float*, double*, float*, float*, float*, void*, size_t, cudaStream_t, int*, bool);
+template int factor_impl<cd>(cd*, int, int, cd*, cd*, double*, cd*, cd*, cd*, void*, size_t, cudaStream_t, int*, bool);
+template int factor_impl<cf>(cf*, int, int, cf*, cf*, double*, cf*, cf*, cf*, void*, size_t, cudaStream_t, int*, bool);
 
 }  // namespace rl

@@ -59,7 +59,44 @@ template <> __device__ inline cd ldg_<cd>(const cd* p) {
 
 enum { MODE_FUSED = 0, MODE_RESID = 1 };
 
-template <class T, int CB>
+// Phase 1 for N columns c0 .. c0+N-1 (N exact: no DFMA is issued for a column that does not
+// exist; predicated-off FMAs would still occupy FP64 issue slots).
+template <class T, int N>
+__device__ __forceinline__ void phase1_chunk(const T* arow, int n, int g, int ps, const T* __restrict__ W,
+                                             int64_t ldw, int c0, T* Ps, size_t pbase, int b) {
+  T y[N];
+#pragma unroll
+  for (int cc = 0; cc < N; ++cc) y[cc] = zero_<T>();
+  for (int k = ps; k < n; k += g) {
+    const T a = arow[k];
+    const T* wk = W + (int64_t)k * ldw + c0;
+#pragma unroll
+    for (int cc = 0; cc < N; ++cc) y[cc] = mad_(a, ldg_(wk + cc), y[cc]);
+  }
+#pragma unroll
+  for (int cc = 0; cc < N; ++cc) Ps[(pbase + c0 + cc) * g + ps] = y[cc];
+  (void)b;
+}
+
+// Phase 2 for N columns: G[k, c0 .. c0+N-1] += sum_r conj(A[r, k]) Y[r, c0 ..]
+template <class T, int N>
+__device__ __forceinline__ void phase2_chunk(const T* tile, int n, int k, int rows, const T* Ys, int b, int c0,
+                                             T* Gacc) {
+  T gk[N];
+#pragma unroll
+  for (int cc = 0; cc < N; ++cc) gk[cc] = Gacc[(size_t)k * b + c0 + cc];
+  for (int r = 0; r < rows; ++r) {
+    const T a = tile[(size_t)r * n + k];
+    const T* yr = Ys + (size_t)r * b + c0;
+#pragma unroll
+    for (int cc = 0; cc < N; ++cc) gk[cc] = madc_(a, yr[cc], gk[cc]);
+  }
+#pragma unroll
+  for (int cc = 0; cc < N; ++cc) Gacc[(size_t)k * b + c0 + cc] = gk[cc];
+}
+
+// CB: width of the full column chunks; CR = b mod CB, the width of the last chunk (both exact).
+template <class T, int CB, int CR>
 __global__ void __launch_bounds__(GR_NT, 1)
 gram_kernel(const T* __restrict__ A, int64_t m, int n, int64_t lda, const T* __restrict__ W, int b,
             int64_t ldw, T* __restrict__ AW, int64_t ldaw, T* __restrict__ part, int64_t rows_per_cta,
@@ -80,6 +117,7 @@ gram_kernel(const T* __restrict__ A, int64_t m, int n, int64_t lda, const T* __r
   const int64_t row_begin = (int64_t)blockIdx.x * rows_per_cta;
   const int64_t row_end = min(m, row_begin + rows_per_cta);
   const int ntile = row_end > row_begin ? (int)((row_end - row_begin + RT - 1) / RT) : 0;
+  const int bfull = b - CR;  // columns covered by full chunks
 
   for (int i = tid; i < n * b; i += GR_NT) Gacc[i] = zero_<T>();
   if (tid == 0 && use_tma) {
@@ -119,23 +157,11 @@ gram_kernel(const T* __restrict__ A, int64_t m, int n, int64_t lda, const T* __r
 
     if (mode == MODE_FUSED) {
       // ---- phase 1: partial dot products of row pr with W over columns k = ps (mod g)
-      for (int c0 = 0; c0 < b; c0 += CB) {
-        T y[CB];
-#pragma unroll
-        for (int cc = 0; cc < CB; ++cc) y[cc] = zero_<T>();
-        if (pr < rows) {
-          const T* arow = tile + (size_t)pr * n;
-          for (int k = ps; k < n; k += g) {
-            const T a = arow[k];
-            const T* wk = W + (int64_t)k * ldw + c0;
-#pragma unroll
-            for (int cc = 0; cc < CB; ++cc)
-              if (c0 + cc < b) y[cc] = mad_(a, ldg_(wk + cc), y[cc]);
-          }
-#pragma unroll
-          for (int cc = 0; cc < CB; ++cc)
-            if (c0 + cc < b) Ps[((size_t)pr * b + c0 + cc) * g + ps] = y[cc];
-        }
+      if (pr < rows) {
+        const T* arow = tile + (size_t)pr * n;
+        const size_t pbase = (size_t)pr * b;
+        for (int c0 = 0; c0 < bfull; c0 += CB) phase1_chunk<T, CB>(arow, n, g, ps, W, ldw, c0, Ps, pbase, b);
+        if constexpr (CR > 0) phase1_chunk<T, CR>(arow, n, g, ps, W, ldw, bfull, Ps, pbase, b);
       }
       __syncthreads();
       // fixed-order sum of the g partials of each (row, column)
@@ -153,21 +179,8 @@ gram_kernel(const T* __restrict__ A, int64_t m, int n, int64_t lda, const T* __r
 
     // ---- phase 2: G[k, :] += conj(A[r, k]) Y[r, :]
     for (int k = tid; k < n; k += GR_NT) {
-      for (int c0 = 0; c0 < b; c0 += CB) {
-        T gk[CB];
-#pragma unroll
-        for (int cc = 0; cc < CB; ++cc) gk[cc] = (c0 + cc < b) ? Gacc[(size_t)k * b + c0 + cc] : zero_<T>();
-        for (int r = 0; r < rows; ++r) {
-          const T a = tile[(size_t)r * n + k];
-          const T* yr = Ys + (size_t)r * b + c0;
-#pragma unroll
-          for (int cc = 0; cc < CB; ++cc)
-            if (c0 + cc < b) gk[cc] = madc_(a, yr[cc], gk[cc]);
-        }
-#pragma unroll
-        for (int cc = 0; cc < CB; ++cc)
-          if (c0 + cc < b) Gacc[(size_t)k * b + c0 + cc] = gk[cc];
-      }
+      for (int c0 = 0; c0 < bfull; c0 += CB) phase2_chunk<T, CB>(tile, n, k, rows, Ys, b, c0, Gacc);
+      if constexpr (CR > 0) phase2_chunk<T, CR>(tile, n, k, rows, Ys, b, bfull, Gacc);
     }
     __syncthreads();
     if (use_tma && tid == 0 && t + 2 < ntile) {
@@ -222,6 +235,43 @@ int gram_plan(int64_t m, int n, int b, GramPlan* gp) {
   return RLOBPCG_OK;
 }
 
+template <class T, int CB, int CR>
+int launch_gram_cr(const GramPlan& gp, const T* A, int64_t m, int n, int64_t lda, const T* W, int b, int64_t ldw,
+                   T* AW, int64_t ldaw, T* part, int use_tma, int mode, int* err, cudaStream_t st) {
+  RL_CUDA(cudaFuncSetAttribute(gram_kernel<T, CB, CR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gp.smem));
+  gram_kernel<T, CB, CR><<<gp.grid, GR_NT, gp.smem, st>>>(A, m, n, lda, W, b, ldw, AW, ldaw, part, gp.rows_per_cta,
+                                                         gp.RT, use_tma, mode, err);
+  RL_CHECK_LAUNCH();
+  return RLOBPCG_OK;
+}
+
+// choose the instantiation whose remainder chunk is exactly b mod CB
+template <class T>
+int launch_gram_kernel(const GramPlan& gp, const T* A, int64_t m, int n, int64_t lda, const T* W, int b, int64_t ldw,
+                       T* AW, int64_t ldaw, T* part, int use_tma, int mode, int* err, cudaStream_t st) {
+  if constexpr (sizeof(T) == 16) {
+    switch (b % 4) {
+      case 0: return launch_gram_cr<T, 4, 0>(gp, A, m, n, lda, W, b, ldw, AW, ldaw, part, use_tma, mode, err, st);
+      case 1: return launch_gram_cr<T, 4, 1>(gp, A, m, n, lda, W, b, ldw, AW, ldaw, part, use_tma, mode, err, st);
+      case 2: return launch_gram_cr<T, 4, 2>(gp, A, m, n, lda, W, b, ldw, AW, ldaw, part, use_tma, mode, err, st);
+      default: return launch_gram_cr<T, 4, 3>(gp, A, m, n, lda, W, b, ldw, AW, ldaw, part, use_tma, mode, err, st);
+    }
+  } else {
+    switch (b % 8) {
+      case 0: return launch_gram_cr<T, 8, 0>(gp, A, m, n, lda, W, b, ldw, AW, ldaw, part, use_tma, mode, err, st);
+      case 1: return launch_gram_cr<T, 8, 1>(gp, A, m, n, lda, W, b, ldw, AW, ldaw, part, use_tma, mode, err, st);
+      case 2: return launch_gram_cr<T, 8, 2>(gp, A, m, n, lda, W, b, ldw, AW, ldaw, part, use_tma, mode, err, st);
+      case 3: return launch_gram_cr<T, 8, 3>(gp, A, m, n, lda, W, b, ldw, AW, ldaw, part, use_tma, mode, err, st);
+      case 4: return launch_gram_cr<T, 8, 4>(gp, A, m, n, lda, W, b, ldw, AW, ldaw, part, use_tma, mode, err, st);
+      case 5: return launch_gram_cr<T, 8, 5>(gp, A, m, n, lda, W, b, ldw, AW, ldaw, part, use_tma, mode, err, st);
+      case 6: return launch_gram_cr<T, 8, 6>(gp, A, m, n, lda, W, b, ldw, AW, ldaw, part, use_tma, mode, err, st);
+      default: return launch_gram_cr<T, 8, 7>(gp, A, m, n, lda, W, b, ldw, AW, ldaw, part, use_tma, mode, err, st);
+    }
+  }
+}
+
+#define RL_TRY_GRAM(x) do { int rc_ = (x); if (rc_) return rc_; } while (0)
+
 // Largest column group bc <= b whose accumulators fit on chip; the pass over A is repeated per
 // group (FP64 arithmetic, not the extra reads of A, bounds the kernel).
 template <class T>
@@ -242,15 +292,12 @@ int gram_impl(const T* A, int64_t m, int n, int64_t lda, const T* W, int b, int6
   T* part = (T*)work;
   const int use_tma = ((uintptr_t)A % 16 == 0) && ((lda * (int64_t)sizeof(T)) % 16 == 0) &&
                       (((int64_t)n * (int64_t)sizeof(T)) % 16 == 0);
-  constexpr int CB = sizeof(T) == 16 ? 4 : 8;
-  RL_CUDA(cudaFuncSetAttribute(gram_kernel<T, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gp.smem));
   for (int c0 = 0; c0 < b; c0 += bc) {
     const int bw = imin(bc, b - c0);
     GramPlan gq = gp;
     if (bw != bc) gram_plan<T>(m, n, bw, &gq);
-    gram_kernel<T, CB><<<gq.grid, GR_NT, gq.smem, st>>>(A, m, n, lda, W ? W + c0 : nullptr, bw, ldw, AW + c0, ldaw,
-                                                       part, gq.rows_per_cta, gq.RT, use_tma, mode, err);
-    RL_CHECK_LAUNCH();
+    RL_TRY_GRAM(launch_gram_kernel<T>(gq, A, m, n, lda, W ? W + c0 : nullptr, bw, ldw, AW + c0, ldaw, part, use_tma,
+                                      mode, err, st));
     const int64_t nb = (int64_t)n * bw;
     gram_reduce_kernel<T><<<(int)((nb + 255) / 256), 256, 0, st>>>(part, gq.grid, n, bw, G + c0, ldg);
     RL_CHECK_LAUNCH();

@@ -162,6 +162,19 @@ __global__ void __launch_bounds__(1024) rr_small_kernel(const T* __restrict__ Rt
   const int N = c + (c & 1);
   // orthogonality test |x_p^H x_q| <= c eps ||x_p|| ||x_q|| (the cosine carries ~c u of noise)
   const double tol = (double)imax(c, 4) * 2.220446049250313e-16;
+  // columns at rounding level (<= c eps max_j ||x_j||) are not rotated (rank-deficient R_T, e.g.
+  // A_V at noise level for an exact nullspace): they would never converge
+  for (int j = warp; j < c; j += nwarp) {
+    double a = 0;
+    for (int rr = lane; rr < c; rr += 32) a += abs2_(X[j * c + rr]);
+    a = warp_sum(a);
+    if (lane == 0) nrm[j] = sqrt(a);
+  }
+  __syncthreads();
+  double mx0 = 0;
+  for (int j = 0; j < c; ++j) mx0 = fmax(mx0, nrm[j]);
+  const double tiny = mx0 * (double)imax(c, 4) * 2.220446049250313e-16;
+  const double tiny2 = tiny * tiny;
   int sweep = 0;
   for (; sweep < 60; ++sweep) {
     if (tid == 0) changed = 0;
@@ -180,10 +193,11 @@ __global__ void __launch_bounds__(1024) rr_small_kernel(const T* __restrict__ Rt
         }
         a = warp_sum(a); bb = warp_sum(bb); g = warp_sum(g);
         const double ga = sqrt(abs2_(g));
-        if (!(ga > tol * sqrt(a) * sqrt(bb)) || a == 0.0 || bb == 0.0) continue;
+        if (!(ga > tol * sqrt(a) * sqrt(bb)) || a <= tiny2 || bb <= tiny2) continue;
         const T e = scale_(g, 1.0 / ga);
         const double zeta = (bb - a) / (2.0 * ga);
         const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + hypot(1.0, zeta));
+        if (fabs(t) <= 2.220446049250313e-16) continue;  // angle below eps: changes nothing but noise
         const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
         const T se = scale_(e, sn), sec = conj_(se);
         for (int rr = lane; rr < c; rr += 32) {
@@ -543,6 +557,34 @@ __global__ void outputs_kernel(const T* Tb, const T* ATb, int64_t n, int64_t m, 
   }
 }
 
+// Z (rows x q, row-major, ld) with entries uniform in [-1, 1) (real and imaginary parts) from
+// SplitMix64 output number 2 (r q + j) (+1 for the imaginary part) of the stream `seed`.
+__device__ inline double uniform_pm1(uint64_t h) { return (double)(h >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0; }
+__device__ inline void fill_value(double* z, uint64_t seed, uint64_t c) { *z = uniform_pm1(splitmix64_at(seed, 2 * c)); }
+__device__ inline void fill_value(cd* z, uint64_t seed, uint64_t c) {
+  z->x = uniform_pm1(splitmix64_at(seed, 2 * c));
+  z->y = uniform_pm1(splitmix64_at(seed, 2 * c + 1));
+}
+template <class T>
+__global__ void fill_random_kernel(T* Z, int64_t rows, int q, int64_t ld, uint64_t seed) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows * q) return;
+  fill_value(&Z[(i / q) * ld + (i % q)], seed, (uint64_t)i);
+}
+
+// Out (rows x b, ldo) = In (rows x q, ldi) K (q x b, ldk); one thread per output element
+template <class T>
+__global__ void small_gemm_kernel(const T* __restrict__ In, int64_t ldi, int q, const T* __restrict__ K, int ldk, int b,
+                                  T* __restrict__ Out, int64_t ldo, int64_t rows) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows * b) return;
+  const int64_t r = i / b;
+  const int j = (int)(i % b);
+  T acc = zero_<T>();
+  for (int l = 0; l < q; ++l) acc = mad_(In[r * ldi + l], K[(int64_t)l * ldk + j], acc);
+  Out[r * ldo + j] = acc;
+}
+
 template <class T>
 __global__ void nonfinite_scan_kernel(const T* A, int64_t m, int n, int64_t lda, int* err) {
   int bad = 0;
@@ -614,7 +656,11 @@ template int tsqr_impl<double>(const double*, int64_t, int, int64_t, double*, vo
 template int tsqr_impl<cd>(const cd*, int64_t, int, int64_t, cd*, void*, size_t, cudaStream_t);
 
 template <class T>
-int rr_small_launch(const T* Rt, int c, int b, double* theta, T* K, int* info, cudaStream_t st) {
+int rr_small_launch(const T* Rt, int c, int b, double* theta, T* K, size_t k_cap, int* info, cudaStream_t st) {
+  if ((size_t)c * 2 * b > k_cap || c > 64 || b > c) {
+    set_last_error("rr_small: coefficient block larger than its buffer", __FILE__, __LINE__);
+    return RLOBPCG_ERR_INVALID_ARG;
+  }
   const int pdim = c - b;
   size_t smem = (size_t)3 * c * c * sizeof(T) + (size_t)c * b * sizeof(T) + c * sizeof(double) +
                 (c + 4) * sizeof(int) + 16 + (size_t)pdim * b * sizeof(T);
@@ -624,8 +670,8 @@ int rr_small_launch(const T* Rt, int c, int b, double* theta, T* K, int* info, c
   RL_CHECK_LAUNCH();
   return RLOBPCG_OK;
 }
-template int rr_small_launch<double>(const double*, int, int, double*, double*, int*, cudaStream_t);
-template int rr_small_launch<cd>(const cd*, int, int, double*, cd*, int*, cudaStream_t);
+template int rr_small_launch<double>(const double*, int, int, double*, double*, size_t, int*, cudaStream_t);
+template int rr_small_launch<cd>(const cd*, int, int, double*, cd*, size_t, int*, cudaStream_t);
 
 template <class T>
 int update_launch(T* Tb, int64_t n, T* ATb, int64_t m, T* GTb, int64_t ld, int c, int b, const T* K, cudaStream_t st) {
@@ -669,6 +715,38 @@ template int precond_launch<double, double>(const double*, const double*, int, i
 template int precond_launch<double, float>(const float*, const float*, int, int, const double*, double*, double*, int64_t, int, cudaStream_t);
 template int precond_launch<cd, cd>(const cd*, const cd*, int, int, const cd*, cd*, cd*, int64_t, int, cudaStream_t);
 template int precond_launch<cd, cf>(const cf*, const cf*, int, int, const cd*, cd*, cd*, int64_t, int, cudaStream_t);
+
+template <class T>
+int fill_random_launch(T* Z, int64_t rows, int q, int64_t ld, uint64_t seed, cudaStream_t st) {
+  fill_random_kernel<T><<<ceil_div(rows * q, 256), 256, 0, st>>>(Z, rows, q, ld, seed);
+  RL_CHECK_LAUNCH();
+  return RLOBPCG_OK;
+}
+template int fill_random_launch<double>(double*, int64_t, int, int64_t, uint64_t, cudaStream_t);
+template int fill_random_launch<cd>(cd*, int64_t, int, int64_t, uint64_t, cudaStream_t);
+
+template <class T>
+int small_gemm_launch(const T* In, int64_t ldi, int q, const T* K, int ldk, int b, T* Out, int64_t ldo, int64_t rows,
+                      cudaStream_t st) {
+  small_gemm_kernel<T><<<ceil_div(rows * b, 256), 256, 0, st>>>(In, ldi, q, K, ldk, b, Out, ldo, rows);
+  RL_CHECK_LAUNCH();
+  return RLOBPCG_OK;
+}
+template int small_gemm_launch<double>(const double*, int64_t, int, const double*, int, int, double*, int64_t, int64_t, cudaStream_t);
+template int small_gemm_launch<cd>(const cd*, int64_t, int, const cd*, int, int, cd*, int64_t, int64_t, cudaStream_t);
+
+// Y (n x q) = L X with L stored in precision S (row-major; lower: rows use l <= k, else l >= k)
+template <class T, class S>
+int trimul_launch(const S* L, int n, const T* X, int64_t ldx, int q, T* Y, int64_t ldy, int lower, int conj_l,
+                  cudaStream_t st) {
+  trimul_kernel<S, T><<<(n * 32 + 255) / 256, 256, 0, st>>>(L, n, X, ldx, q, Y, ldy, lower, conj_l);
+  RL_CHECK_LAUNCH();
+  return RLOBPCG_OK;
+}
+template int trimul_launch<double, double>(const double*, int, const double*, int64_t, int, double*, int64_t, int, int, cudaStream_t);
+template int trimul_launch<double, float>(const float*, int, const double*, int64_t, int, double*, int64_t, int, int, cudaStream_t);
+template int trimul_launch<cd, cd>(const cd*, int, const cd*, int64_t, int, cd*, int64_t, int, int, cudaStream_t);
+template int trimul_launch<cd, cf>(const cf*, int, const cd*, int64_t, int, cd*, int64_t, int, int, cudaStream_t);
 
 template <class T>
 int bcgs2_orth_launch(T* Tb, int n, int b, int64_t ld, int wo, int nx, T* E, int passes, cudaStream_t st) {

@@ -19,8 +19,16 @@ int sketch_dispatch(const void* A, int64_t m, int64_t n, int64_t lda, int dtype,
                     int sketch_prec, void* SA, cudaStream_t st);
 size_t factor_workspace_bytes(int64_t d, int64_t n, size_t esz);
 template <class S>
-int factor_impl(S* SA, int d, int n, S* Rout, double* sigma, S* Vt, S* Rinv_r, S* Rinv_c, void* work,
-                size_t work_bytes, cudaStream_t st, int* sweeps_host);
+int factor_impl(S* SA, int d, int n, S* Rout, S* Rout_r, double* sigma, S* Vt, S* Rinv_r, S* Rinv_c, void* work,
+                size_t work_bytes, cudaStream_t st, int* sweeps_host, bool do_svd);
+template <class T>
+int fill_random_launch(T* Z, int64_t rows, int q, int64_t ld, uint64_t seed, cudaStream_t st);
+template <class T>
+int small_gemm_launch(const T* In, int64_t ldi, int q, const T* K, int ldk, int b, T* Out, int64_t ldo, int64_t rows,
+                      cudaStream_t st);
+template <class T, class S>
+int trimul_launch(const S* L, int n, const T* X, int64_t ldx, int q, T* Y, int64_t ldy, int lower, int conj_l,
+                  cudaStream_t st);
 size_t gram_workspace_bytes(int64_t m, int64_t n, int b, int dtype);
 int gram_dispatch(const void* A, int64_t m, int64_t n, int64_t lda, int dtype, const void* W, int b, int64_t ldw,
                   void* AW, int64_t ldaw, void* G, int64_t ldg, void* work, size_t work_bytes, int resid_mode,
@@ -29,7 +37,7 @@ size_t tsqr_workspace_bytes(int64_t m, int c, size_t esz);
 template <class T>
 int tsqr_impl(const T* X, int64_t m, int c, int64_t ldx, T* R, void* work, size_t work_bytes, cudaStream_t st);
 template <class T>
-int rr_small_launch(const T* Rt, int c, int b, double* theta, T* K, int* info, cudaStream_t st);
+int rr_small_launch(const T* Rt, int c, int b, double* theta, T* K, size_t k_cap, int* info, cudaStream_t st);
 template <class T>
 int update_launch(T* Tb, int64_t n, T* ATb, int64_t m, T* GTb, int64_t ld, int c, int b, const T* K, cudaStream_t st);
 template <class T>
@@ -66,6 +74,12 @@ struct rlobpcg_plan_s {
   void* Vt = nullptr;
   void* Rinv_r = nullptr;
   void* Rinv_c = nullptr;
+  void* R_c = nullptr;      // R column-major
+  void* R_r = nullptr;      // R row-major
+  void* Zb = nullptr;       // n x qmax blocks of the start-block / Sigma~(1,1) iterations
+  void* Yb = nullptr;
+  int qmax = 0;
+  size_t K_cap = 0;         // elements of K
   void* fwork = nullptr;
   size_t fwork_bytes = 0;
   void* Tb = nullptr;
@@ -165,19 +179,53 @@ int solve_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, double tau, double* s
   // Sketch and factorise (Alg. 2, lines 1-3)
   RL_TRY(sketch_dispatch(A, m, n, lda, p->dtype, d, p->opts.zeta, p->opts.seed, p->opts.sketch_prec, p->SA, st));
   RL_CUDA(cudaEventRecord(p->ev[1], st));
-  RL_TRY(factor_impl<S>((S*)p->SA, d, n, nullptr, p->sk_sigma, (S*)p->Vt, (S*)p->Rinv_r, (S*)p->Rinv_c, p->fwork,
-                        p->fwork_bytes, st, nullptr));
+  int sweeps = 0;
+  const bool exact = p->opts.exact_sketch_svd != 0;
+  RL_TRY(factor_impl<S>((S*)p->SA, d, n, (S*)p->R_c, (S*)p->R_r, p->sk_sigma, (S*)p->Vt, (S*)p->Rinv_r,
+                        (S*)p->Rinv_c, p->fwork, p->fwork_bytes, st, &sweeps, exact));
   double sigma11 = 0;
-  RL_CUDA(cudaMemcpyAsync(&sigma11, p->sk_sigma, sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (exact) {
+    RL_CUDA(cudaMemcpyAsync(&sigma11, p->sk_sigma, sizeof(double), cudaMemcpyDeviceToHost, st));
+    // Sketch-and-solve start V~(:, n-b+1:n) (Alg. 2, line 4)
+    RL_TRY((take_start_launch<S, T>((const S*)p->Vt, n, b, Tb, ld, st)));
+  } else {
+    // Only the two parts of SVD(SA) = SVD(R) the method uses. Sigma~(1,1): block power iteration
+    // Z <- Orth(R^H R Z), then the largest singular value of R Z by TSQR + Jacobi.
+    T* Z = (T*)p->Zb;
+    T* Y = (T*)p->Yb;
+    const int qt = std::min(n, std::min(8, p->qmax));
+    RL_TRY(fill_random_launch<T>(Z, n, qt, qt, p->opts.seed ^ 0x243F6A8885A308D3ull, st));
+    for (int it = 0; it < 8; ++it) {
+      RL_TRY((trimul_launch<T, S>((const S*)p->R_r, n, Z, qt, qt, Y, qt, 0, 0, st)));
+      RL_TRY((trimul_launch<T, S>((const S*)p->R_c, n, Y, qt, qt, Z, qt, 1, 1, st)));
+      RL_TRY(bcgs2_orth_launch<T>(Z, n, qt, qt, 0, 0, (T*)p->E, 0, st));
+    }
+    RL_TRY((trimul_launch<T, S>((const S*)p->R_r, n, Z, qt, qt, Y, qt, 0, 0, st)));
+    RL_TRY(tsqr_impl<T>(Y, n, qt, qt, (T*)p->Rt, p->twork, p->twork_bytes, st));
+    RL_TRY(rr_small_launch<T>((const T*)p->Rt, qt, qt, p->theta, (T*)p->K, p->K_cap, p->info, st));
+    RL_CUDA(cudaMemcpyAsync(&sigma11, p->theta, sizeof(double), cudaMemcpyDeviceToHost, st));
+    // Start block V~(:, n-b+1:n): block inverse iteration Z <- Orth((R^H R)^{-1} Z) with the
+    // oversampled block q = min(n, 2b + 4), then Rayleigh-Ritz on R Z (its b smallest).
+    const int q = p->qmax;
+    RL_TRY(fill_random_launch<T>(Z, n, q, q, p->opts.seed ^ 0x13198A2E03707344ull, st));
+    for (int it = 0; it < 3; ++it) {
+      RL_TRY((trimul_launch<T, S>((const S*)p->Rinv_c, n, Z, q, q, Y, q, 1, 1, st)));
+      RL_TRY((trimul_launch<T, S>((const S*)p->Rinv_r, n, Y, q, q, Z, q, 0, 0, st)));
+      RL_TRY(bcgs2_orth_launch<T>(Z, n, q, q, 0, 0, (T*)p->E, 0, st));
+    }
+    RL_TRY((trimul_launch<T, S>((const S*)p->R_r, n, Z, q, q, Y, q, 0, 0, st)));
+    RL_TRY(tsqr_impl<T>(Y, n, q, q, (T*)p->Rt, p->twork, p->twork_bytes, st));
+    RL_TRY(rr_small_launch<T>((const T*)p->Rt, q, b, p->theta, (T*)p->K, p->K_cap, p->info, st));
+    RL_TRY(small_gemm_launch<T>(Z, q, q, (const T*)p->K, 2 * b, b, Tb, ld, n, st));
+  }
   RL_CUDA(cudaStreamSynchronize(st));
   if (herr & DEV_ERR_NONFINITE) return RLOBPCG_ERR_NONFINITE;
 
   // Sketch-and-solve start and initial Rayleigh-Ritz (Alg. 2, lines 4-7)
-  RL_TRY((take_start_launch<S, T>((const S*)p->Vt, n, b, Tb, ld, st)));
   RL_TRY(bcgs2_orth_launch<T>(Tb, n, b, ld, 0, 0, (T*)p->E, 0, st));
   RL_TRY(gram_dispatch(A, m, n, lda, p->dtype, Tb, b, ld, ATb, ld, GTb, ld, p->gwork, p->gwork_bytes, 0, p->err, st));
   RL_TRY(tsqr_impl<T>(ATb, m, b, ld, (T*)p->Rt, p->twork, p->twork_bytes, st));
-  RL_TRY(rr_small_launch<T>((const T*)p->Rt, b, b, p->theta, (T*)p->K, p->info, st));
+  RL_TRY(rr_small_launch<T>((const T*)p->Rt, b, b, p->theta, (T*)p->K, p->K_cap, p->info, st));
   RL_TRY(update_launch<T>(Tb, n, ATb, m, GTb, ld, b, b, (const T*)p->K, st));
   RL_TRY((residual_launch<T>(Tb, GTb, n, b, ld, p->theta, (T*)p->Res, p->res_norm, (T*)p->Rs, p->err, st)));
   RL_CUDA(cudaEventRecord(p->ev[2], st));
@@ -210,7 +258,7 @@ int solve_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, double tau, double* s
     // Rayleigh-Ritz by SVD of A_T (TSQR + Jacobi of R_T)
     const int c = 2 * b + nx;
     RL_TRY(tsqr_impl<T>(ATb, m, c, ld, (T*)p->Rt, p->twork, p->twork_bytes, st));
-    RL_TRY(rr_small_launch<T>((const T*)p->Rt, c, b, p->theta, (T*)p->K, p->info, st));
+    RL_TRY(rr_small_launch<T>((const T*)p->Rt, c, b, p->theta, (T*)p->K, p->K_cap, p->info, st));
     theta_s = p->theta + (c - b);
     RL_TRY(update_launch<T>(Tb, n, ATb, m, GTb, ld, c, b, (const T*)p->K, st));
     if (refresh > 0 && (i + 1) % refresh == 0) {
@@ -274,6 +322,7 @@ int solve_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, double tau, double* s
     info->ms_gram = gram_ms;
     info->gram_passes = gram_passes;
     info->kernel_launches = (int)(launch_count() - launches0);
+    info->jacobi_sweeps = sweeps;
   }
   if (herr & DEV_ERR_TIMEOUT) return RLOBPCG_ERR_TIMEOUT;
   if (herr & DEV_ERR_NONFINITE) return RLOBPCG_ERR_NONFINITE;
@@ -334,25 +383,34 @@ extern "C" int rlobpcg_plan(rlobpcg_plan_t* out, int64_t m, int64_t n, int k, in
   RL_A(p->Vt, (size_t)n * n * ssz);
   RL_A(p->Rinv_r, (size_t)n * n * ssz);
   RL_A(p->Rinv_c, (size_t)n * n * ssz);
+  RL_A(p->R_c, (size_t)n * n * ssz);
+  RL_A(p->R_r, (size_t)n * n * ssz);
+  p->qmax = (int)std::min<int64_t>(n, 2 * b + 4);
+  const int64_t cmax = std::max<int64_t>(ld, p->qmax);
+  RL_A(p->Zb, (size_t)n * p->qmax * esz);
+  RL_A(p->Yb, (size_t)n * p->qmax * esz);
   p->fwork_bytes = factor_workspace_bytes(d, n, ssz);
   RL_A(p->fwork, p->fwork_bytes);
   RL_A(p->Tb, (size_t)n * ld * esz);
   RL_A(p->ATb, (size_t)m * ld * esz);
   RL_A(p->GTb, (size_t)n * ld * esz);
-  RL_A(p->E, (size_t)n * b * esz);
+  RL_A(p->E, (size_t)n * cmax * esz);
   RL_A(p->Res, (size_t)n * b * esz);
   RL_A(p->Rs, (size_t)n * b * esz);
   RL_A(p->Y, (size_t)std::max<int64_t>(n * b, 64) * esz);
-  RL_A(p->Rt, (size_t)ld * ld * esz);
-  RL_A(p->K, (size_t)ld * 2 * b * esz);
-  RL_A(p->theta, (size_t)ld * sizeof(double));
+  RL_A(p->Rt, (size_t)cmax * cmax * esz);
+  // coefficient blocks c x 2b of every Rayleigh-Ritz step, including the qt x 2qt block (qt <= 8)
+  // of the Sigma~(1,1) estimate
+  p->K_cap = (size_t)cmax * 2 * std::max<int64_t>(b, 8);
+  RL_A(p->K, p->K_cap * esz);
+  RL_A(p->theta, (size_t)cmax * sizeof(double));
   RL_A(p->res_norm, (size_t)(b + 2 * k + 8) * sizeof(double));
   RL_A(p->err, 64);
   RL_A(p->info, 64);
   p->gwork_bytes = gram_workspace_bytes(m, n, b, dtype);
   if (p->gwork_bytes == 0) { free_plan(p); delete p; set_last_error("Gram kernel: n*b too large for on-chip accumulation", __FILE__, __LINE__); return RLOBPCG_ERR_UNSUPPORTED; }
   RL_A(p->gwork, p->gwork_bytes);
-  p->twork_bytes = tsqr_workspace_bytes(m, (int)ld, esz);
+  p->twork_bytes = std::max(tsqr_workspace_bytes(m, (int)ld, esz), tsqr_workspace_bytes(n, p->qmax, esz));
   RL_A(p->twork, p->twork_bytes);
 #undef RL_A
   for (auto& e : p->ev) {

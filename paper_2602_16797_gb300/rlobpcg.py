@@ -35,13 +35,14 @@ RLOBPCG_STOP_FIXED = 2
 class rlobpcg_opts(ctypes.Structure):
     _fields_ = [("seed", c_uint64), ("d", c_int), ("zeta", c_int), ("block", c_int), ("max_iter", c_int),
                 ("check_every", c_int), ("use_stagnation", c_int), ("sketch_prec", c_int), ("fixed_iters", c_int),
-                ("residual_refresh_every", c_int), ("tau", c_double)]
+                ("residual_refresh_every", c_int), ("exact_sketch_svd", c_int), ("tau", c_double)]
 
 
 class rlobpcg_info(ctypes.Structure):
     _fields_ = [("iters", c_int), ("matvecs", c_int), ("stop_reason", c_int), ("block", c_int),
                 ("sigma11", c_double), ("ms_sketch", c_double), ("ms_factor", c_double), ("ms_iterate", c_double),
-                ("ms_total", c_double), ("ms_gram", c_double), ("gram_passes", c_int), ("kernel_launches", c_int)]
+                ("ms_total", c_double), ("ms_gram", c_double), ("gram_passes", c_int), ("kernel_launches", c_int),
+                ("jacobi_sweeps", c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

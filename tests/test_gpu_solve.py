@@ -20,8 +20,9 @@ pytestmark = pytest.mark.gpu
 
 
 def gpu_solve(A, k, *, seed, d=None, zeta=8, b=None, tau=None, stagnation=True, fixed=0, prec="f64",
-              max_iter=0, refresh=0, want_u=False):
+              max_iter=0, refresh=0, want_u=False, exact_svd=False):
     o = rl.rlobpcg_default_opts()
+    o.exact_sketch_svd = 1 if exact_svd else 0
     o.seed = seed
     o.zeta = zeta
     o.d = d or 0
@@ -54,8 +55,12 @@ def compare(A, k, s_true, V_true, *, n, gap_abs, **kw):
         okw["max_iter"] = None
     okw.pop("refresh", None)
     okw.pop("want_u", None)
+    okw.pop("exact_svd", None)
     o = ora_solve(A, k, **okw)
     sig, V, _, resid, info = g
+    print(f"gpu: iters={info['iters']} stop={info['stop_reason']} sigma11={info['sigma11']!r} sigma={sig!r}")
+    print(f"ora: iters={o['iters']} stop={o['stop_reason']} sigma11={o['sigma11']!r} sigma={o['sigma']!r}")
+    print(f"ora res_hist max: {o['res_hist'].max(axis=1)[:12]!r}")
     check_sigma(sig, o["sigma"], o["sigma11"], n)
     check_angle(V, o["V"], gap_abs, n)
     if s_true is not None:
@@ -93,11 +98,12 @@ def test_small_planted_default_stop(small_planted):
     assert g[4]["stop_reason"] == rl.RLOBPCG_STOP_CONVERGED
 
 
+@pytest.mark.parametrize("exact_svd", [False, True])
 @pytest.mark.parametrize("iters", [1, 3, 12])
-def test_small_planted_fixed_iterations(small_planted, iters):
+def test_small_planted_fixed_iterations(small_planted, iters, exact_svd):
     A, s, V = small_planted
     gap = (s[-2] - s[-1]) / s[0]
-    g, o = compare(A, 1, None, None, n=50, gap_abs=gap, seed=1001, fixed=iters)
+    g, o = compare(A, 1, None, None, n=50, gap_abs=gap, seed=1001, fixed=iters, exact_svd=exact_svd)
     assert g[4]["iters"] == iters and g[4]["stop_reason"] == rl.RLOBPCG_STOP_FIXED
 
 
@@ -139,10 +145,24 @@ def test_planted_bottom_cluster(m):
     compare(A, 5, s[::-1][:5], V[:, ::-1][:, :5], n=500, gap_abs=gap, seed=1002, d=1500)
 
 
-def test_planted_bottom_cluster_fixed_iterations():
+@pytest.mark.parametrize("exact_svd", [False, True])
+def test_planted_bottom_cluster_fixed_iterations(exact_svd):
     A, s, V = wl.planted_bottom_cluster(m=20_000)
     gap = (s[-6] - s[-5]) / s[0]
-    compare(A, 5, None, None, n=500, gap_abs=gap, seed=1002, d=1500, fixed=8)
+    compare(A, 5, None, None, n=500, gap_abs=gap, seed=1002, d=1500, fixed=8, exact_svd=exact_svd)
+
+
+def test_start_block_matches_exact_sketch_svd():
+    """The start block by inverse iteration + Rayleigh-Ritz spans the sketch's bottom-b right
+    singular subspace (the exact V~(:, n-b+1:n)), so one iteration from either start gives the
+    same block. Sigma~(1,1) by block power iteration is within 2% (it only scales the stop
+    tolerance, and it estimates ||A|| only up to the sketch's distortion anyway)."""
+    A, s, V = wl.planted_bottom_cluster(m=20_000)
+    g0 = gpu_solve(A, 5, seed=1002, d=1500, fixed=1, exact_svd=False)
+    g1 = gpu_solve(A, 5, seed=1002, d=1500, fixed=1, exact_svd=True)
+    assert g0[4]["sigma11"] <= g1[4]["sigma11"] * (1 + 1e-12)
+    assert abs(g0[4]["sigma11"] - g1[4]["sigma11"]) <= 2e-2 * g1[4]["sigma11"]
+    assert sub_sin(g0[1], g1[1]) <= 1e-8
 
 
 # ---------------------------------------------------------------------------------------------
