@@ -139,10 +139,10 @@ def gram_traffic_per_element():
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         tag, per = None, None
         for ln in txt.splitlines():
-            if ln.startswith("gram.cu sha256[:16]:"):
-                tag = ln.split(":", 1)[1].strip()
-            if ln.startswith("dram bytes per element of A:"):
-                per = float(ln.split(":", 1)[1].split()[0])
+            if ln.startswith("gram.cu sha256[:16]: "):
+                tag = ln.split(": ", 1)[1].strip()
+            if ln.startswith("dram bytes per element of A: "):
+                per = float(ln.split(": ", 1)[1].split()[0])
         return per if tag == h else None
     except (OSError, ValueError):
         return None
