@@ -31,18 +31,13 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_2602_16797_gb300 import replicas  # noqa: E402
+
 METRIC = "solve time & solves/s at stated σ/angle error; fused AᴴAX GB/s; p50/p99 latency"
 WORKLOAD = "nullspace+planted m=1e5 n=500 k=5 d=3n zeta=8 fp64"
 M, N, K_TRIPLETS, D, ZETA = 100_000, 500, 5, 1500, 8
 SAMPLE_M = 20_000          # row sample for the CPU oracle timings
 FP64_UNITS_PER_SM_CLK = 2  # DFMA per clock per SM: 1.25 TFLOP/s nominal / (152 SMs * 2.07 GHz * 2 flop)
-
-
-def _env_int(name, default):
-    try:
-        return int(os.environ.get(name, default))
-    except ValueError:
-        return default
 
 
 def make_inputs(m):
@@ -175,8 +170,7 @@ def run_ours(args, rank, world, local_rank):
     for i in range(args.warmup):
         step(i, rl.rlobpcg_info())
     torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
+    replicas.barrier(world)
     clocks = ClockSampler(local_rank)
     clocks.start()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
@@ -192,11 +186,8 @@ def run_ours(args, rank, world, local_rank):
     clk = clocks.stop()
     ms_total = ev[0].elapsed_time(ev[-1])
     lat = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
-    if world > 1:
-        t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
-        torch.distributed.barrier()
+    replicas.barrier(world)
+    ms_total = replicas.max_over_ranks(ms_total, world, device=dev)
 
     # e2e: host buffers through the same C-ABI call (H2D of A and D2H of the results inside)
     pinned = [torch.from_numpy(A).pin_memory() for A in As]
@@ -241,7 +232,7 @@ def run_ours(args, rank, world, local_rank):
     out = None
     if rank == 0:
         ms_per = ms_total / args.steps
-        value = world * args.steps / (ms_total * 1e-3)
+        value = replicas.job_rate(args.steps, world, ms_total * 1e-3)
         lat_sorted = sorted(lat)
         result = {
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
@@ -297,23 +288,16 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
-    world = _env_int("WORLD_SIZE", 1)
-    rank = _env_int("RANK", 0)
-    local_rank = _env_int("LOCAL_RANK", 0)
-    if world > 1:
+    rank, world, local_rank = replicas.world_from_env()
+    if world > 1 and args.impl == "ours":
         import torch
-        import torch.distributed as dist
-        if args.impl == "ours":
-            torch.cuda.set_device(local_rank)
-        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+        torch.cuda.set_device(local_rank)
+    replicas.init(world, "nccl" if args.impl == "ours" else "gloo")
     if args.impl == "reference":
         out = run_reference(args, rank, world)
     else:
         out = run_ours(args, rank, world, local_rank)
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
-        dist.destroy_process_group()
+    replicas.finish(world)
     if out is not None:
         print(json.dumps(out))
 
