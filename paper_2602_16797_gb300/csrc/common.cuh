@@ -137,6 +137,62 @@ __host__ __device__ inline bool finite_(float a) { return isfinite(a); }
 __host__ __device__ inline bool finite_(cd a) { return isfinite(a.x) && isfinite(a.y); }
 __host__ __device__ inline bool finite_(cf a) { return isfinite(a.x) && isfinite(a.y); }
 
+// ------------------------------------------------------------------ one-sided Jacobi rotation
+// For columns x_p, x_q with a = ||x_p||^2, b = ||x_q||^2, g = x_p^H x_q: the rotation
+//   x_p' = c x_p - s conj(e) x_q,   x_q' = s e x_p + c x_q       (e = g / |g|)
+// makes x_p'^H x_q' = 0 (Hestenes; the real case is Rutishauser's formula). Its tangent, the
+// smaller root of t^2 + 2 zeta t - 1 = 0 with zeta = (b - a) / (2|g|), is written without the
+// division by |g|:  t = sign(b - a) 2|g| / (|b - a| + sqrt((b - a)^2 + 4|g|^2)),
+// and c = 1/sqrt(1 + t^2), s = c t. On GB300 every dependent FP64 instruction costs ~64 cycles
+// and a divide or square root ~10 of them, so this form (one sqrt, one divide, one rsqrt; the
+// complex case adds one rsqrt for the phase) matters. Returns false -- no rotation -- when the
+// pair is already orthogonal (|g|^2 <= tol^2 a b), when a column is at rounding level (its
+// squared norm <= tiny2), or when the angle is below eps (a rotation that changes nothing but
+// the smaller column's noise).
+__device__ inline double rsqrt_r(double x) { return rsqrt(x); }
+__device__ inline float rsqrt_r(float x) { return rsqrtf(x); }
+__device__ inline double sqrt_r(double x) { return sqrt(x); }
+__device__ inline float sqrt_r(float x) { return sqrtf(x); }
+
+template <class R>
+__device__ inline bool jacobi_tangent(R a, R b, R g2, R ga, R tol, R tiny2, R eps, R* c, R* s) {
+  if (!(g2 > tol * tol * a * b) || a <= tiny2 || b <= tiny2) return false;
+  const R d = b - a;
+  const R den = fabs(d) + sqrt_r(d * d + (R)4 * g2);
+  const R t = (d >= (R)0 ? (R)2 * ga : (R)-2 * ga) / den;
+  if (fabs(t) <= eps) return false;
+  *c = rsqrt_r((R)1 + t * t);
+  *s = *c * t;
+  return true;
+}
+
+__device__ inline bool jacobi_rotation(double a, double b, double g, double tol, double tiny2, double eps, double* c,
+                                       double* s, double* e) {
+  *e = g < 0.0 ? -1.0 : 1.0;
+  return jacobi_tangent(a, b, g * g, fabs(g), tol, tiny2, eps, c, s);
+}
+__device__ inline bool jacobi_rotation(float a, float b, float g, float tol, float tiny2, float eps, float* c,
+                                       float* s, float* e) {
+  *e = g < 0.0f ? -1.0f : 1.0f;
+  return jacobi_tangent(a, b, g * g, fabsf(g), tol, tiny2, eps, c, s);
+}
+__device__ inline bool jacobi_rotation(double a, double b, cd g, double tol, double tiny2, double eps, double* c,
+                                       double* s, cd* e) {
+  const double g2 = abs2_(g);
+  if (!(g2 > 0.0)) return false;
+  const double rg = rsqrt(g2);
+  *e = scale_(g, rg);
+  return jacobi_tangent(a, b, g2, g2 * rg, tol, tiny2, eps, c, s);
+}
+__device__ inline bool jacobi_rotation(float a, float b, cf g, float tol, float tiny2, float eps, float* c, float* s,
+                                       cf* e) {
+  const float g2 = abs2_(g);
+  if (!(g2 > 0.0f)) return false;
+  const float rg = rsqrtf(g2);
+  *e = scale_(g, rg);
+  return jacobi_tangent(a, b, g2, g2 * rg, tol, tiny2, eps, c, s);
+}
+
 // ------------------------------------------------------------------ warp helpers
 __device__ inline double shfl_xor_(double v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
 __device__ inline float shfl_xor_(float v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }

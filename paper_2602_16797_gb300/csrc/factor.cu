@@ -146,19 +146,12 @@ __device__ void jacobi_pair(S* X, S* V, int n, int p, int q, RealOf<S> tol, Real
   a = warp_sum(a);
   b = warp_sum(b);
   g = warp_sum(g);
-  const R ga = sqrt_(abs2_(g));
   // columns at rounding level (||x|| <= n eps max_j ||x_j||) are not rotated: their directions
-  // are arbitrary inside the noise subspace, and rotating them would never converge
-  if (!(ga > tol * sqrt_(a) * sqrt_(b)) || a <= tiny2 || b <= tiny2) return;
-  const S e = scale_(g, (R)1 / ga);               // e^{i phi}
-  const R zeta = (b - a) / ((R)2 * ga);
-  const R t = (zeta >= (R)0 ? (R)1 : (R)-1) / (fabs(zeta) + hypot_((R)1, zeta));
-  // a rotation by an angle below eps changes the larger column by less than its rounding and
-  // only re-injects the larger column's rounding noise into the smaller one: skip it, so that
-  // pairs of very different norms stop re-randomising the small columns every sweep
-  if (fabs(t) <= eps_of<S>()) return;
-  const R c = (R)1 / sqrt_((R)1 + t * t);
-  const R s = c * t;
+  // are arbitrary inside the noise subspace, and rotating them would never converge; neither
+  // are pairs whose rotation angle is below eps (see jacobi_rotation)
+  R c, s;
+  S e;
+  if (!jacobi_rotation(a, b, g, tol, tiny2, eps_of<S>(), &c, &s, &e)) return;
   const S se = scale_(e, s);                     // s e
   const S sec = conj_(se);                       // s conj(e)
   for (int r = lane; r < n; r += 32) {

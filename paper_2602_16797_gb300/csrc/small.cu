@@ -29,6 +29,8 @@ __device__ inline cf recip_(cf a) { float s = a.x * a.x + a.y * a.y; return {a.x
 // Householder scalars (LAPACK larfg convention) from alpha = x(0) and ||x(1:)||^2:
 // beta = -sign(Re alpha) ||x||, tau = (beta - alpha)/beta, v = [1; x(1:) / (alpha - beta)].
 // tau = 0 (H = I) when x(1:) = 0 and alpha is real.
+// One divide instead of two: with r = 1 / (beta (alpha - beta)), 1/beta = (alpha - beta) r and
+// 1/(alpha - beta) = beta r (FP64 divides are ~10 dependent FMAs on GB300).
 template <class T>
 __device__ inline void householder_scalars(T alpha, double xnorm2, T* tau, T* beta, T* inv_ab) {
   if (xnorm2 == 0.0 && im_(alpha) == 0.0) {
@@ -38,30 +40,34 @@ __device__ inline void householder_scalars(T alpha, double xnorm2, T* tau, T* be
   const double bn = sqrt(abs2_(alpha) + xnorm2);
   const double bb = re_(alpha) >= 0.0 ? -bn : bn;
   *beta = from_real<T>(bb);
-  *tau = scale_(sub_(*beta, alpha), 1.0 / bb);
-  *inv_ab = recip_(sub_(alpha, *beta));
+  const T amb = sub_(alpha, *beta);
+  const T r = recip_(scale_(amb, bb));
+  *tau = mul_(sub_(*beta, alpha), mul_(amb, r));
+  *inv_ab = scale_(r, bb);
 }
 
 // ------------------------------------------------------------------------------------------
 // TSQR level: CTA i reduces rows [i*rpc, min((i+1)*rpc, rows)) of X (row-major, ldx, c cols)
-// to a c x c upper-triangular R by Householder steps on [R_running; next chunk].
-// Thread (column cc, row phase p): cc = tid % CP, p = tid / CP, CP = pow2 >= c.
+// to a c x c upper-triangular R by Householder steps on [R_running; next chunk of CH rows].
+// Q is never formed. Thread (column cc, row phase p) with cc = tid / RP, p = tid % RP: the RP
+// lanes of a column are contiguous, so the column sums are shuffle trees. Per column j:
+//   d_cc = sum_{r > j} conj(S[r][j]) S[r][cc]   (cc = j gives ||x(1:)||^2)
+//   reflector scalars from alpha = S[j][j] and d_j (one thread), then for cc > j
+//   s = S[j][cc] + conj(1/(alpha - beta)) d_cc,  f = conj(tau) s,
+//   S[j][cc] -= f,  S[r][cc] -= S[r][j] (f / (alpha - beta))  for r > j.
 // ------------------------------------------------------------------------------------------
 template <class T>
 __global__ void __launch_bounds__(256) tsqr_level_kernel(const T* __restrict__ X, int64_t rows, int c, int64_t ldx,
-                                                          int64_t rpc, int CH, int CP, T* __restrict__ Rout) {
+                                                          int64_t rpc, int CH, int RP, T* __restrict__ Rout) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int NT = blockDim.x;
-  const int RP = NT / CP;
-  const int tid = threadIdx.x, cc = tid % CP, p = tid / CP;
+  const int tid = threadIdx.x, cc = tid / RP, p = tid % RP;
   const int SR = c + CH;                       // stacked rows
   T* S = reinterpret_cast<T*>(smem_raw);       // SR x c row-major
-  T* part = S + (size_t)SR * c;                // CP x RP partials
-  T* sv = part + (size_t)CP * RP;              // c values s_cc
-  __shared__ T sh_tau, sh_inv;
+  __shared__ T sh_tau, sh_inv, sh_beta;
 
   const int64_t r_begin = (int64_t)blockIdx.x * rpc;
-  const int64_t r_end = min(rows, r_begin + rpc);
+  const int64_t r_end = imin<int64_t>(rows, r_begin + rpc);
   for (int i = tid; i < c * c; i += NT) S[i] = zero_<T>();
   for (int64_t r0 = r_begin; r0 < r_end || r0 == r_begin; r0 += CH) {
     const int nr = (int)imax<int64_t>(0, imin<int64_t>(CH, r_end - r0));
@@ -75,43 +81,37 @@ __global__ void __launch_bounds__(256) tsqr_level_kernel(const T* __restrict__ X
       S[(size_t)(c + r) * c + q] = (r < nr) ? X[(r0 + r) * ldx + q] : zero_<T>();
     }
     __syncthreads();
+    const int SRu = c + imax(nr, 1);            // rows that can be nonzero
     for (int j = 0; j < c; ++j) {
-      // d_cc = sum_{r > j} conj(S[r][j]) S[r][cc] for cc >= j (cc == j gives ||x(1:)||^2)
+      T d = zero_<T>();
       if (cc < c && cc >= j) {
-        T acc = zero_<T>();
-        for (int r = j + 1 + p; r < SR; r += RP) acc = madc_(S[(size_t)r * c + j], S[(size_t)r * c + cc], acc);
-        part[cc * RP + p] = acc;
+        T a0 = zero_<T>(), a1 = zero_<T>(), a2 = zero_<T>(), a3 = zero_<T>();
+        int r = j + 1 + p;
+        for (; r + 3 * RP < SRu; r += 4 * RP) {
+          a0 = madc_(S[(size_t)r * c + j], S[(size_t)r * c + cc], a0);
+          a1 = madc_(S[(size_t)(r + RP) * c + j], S[(size_t)(r + RP) * c + cc], a1);
+          a2 = madc_(S[(size_t)(r + 2 * RP) * c + j], S[(size_t)(r + 2 * RP) * c + cc], a2);
+          a3 = madc_(S[(size_t)(r + 3 * RP) * c + j], S[(size_t)(r + 3 * RP) * c + cc], a3);
+        }
+        for (; r < SRu; r += RP) a0 = madc_(S[(size_t)r * c + j], S[(size_t)r * c + cc], a0);
+        d = add_(add_(a0, a1), add_(a2, a3));
       }
-      __syncthreads();
-      if (p == 0 && cc < c && cc >= j) {
-        T dj = part[j * RP];
-        for (int q = 1; q < RP; ++q) dj = add_(dj, part[j * RP + q]);
+      for (int o = RP >> 1; o > 0; o >>= 1) d = add_(d, shfl_xor_(d, o));
+      if (cc == j && p == 0) {
         T tau, beta, inv_ab;
-        householder_scalars(S[(size_t)j * c + j], re_(dj), &tau, &beta, &inv_ab);
-        if (cc == j) {
-          sh_tau = tau; sh_inv = inv_ab;
-          sv[j] = beta;
-        } else {
-          T dc = part[cc * RP];
-          for (int q = 1; q < RP; ++q) dc = add_(dc, part[cc * RP + q]);
-          // s = v^H S(:, cc) = S[j][cc] + conj(1/(alpha-beta)) d_cc
-          sv[cc] = add_(S[(size_t)j * c + cc], mul_(conj_(inv_ab), dc));
-        }
+        householder_scalars(S[(size_t)j * c + j], re_(d), &tau, &beta, &inv_ab);
+        sh_tau = tau; sh_inv = inv_ab; sh_beta = beta;
       }
       __syncthreads();
-      const T tau = sh_tau, inv_ab = sh_inv;
       if (cc < c && cc > j) {
-        const T f = mul_(conj_(tau), sv[cc]);
+        const T inv_ab = sh_inv;
+        const T f = mul_(conj_(sh_tau), add_(S[(size_t)j * c + cc], mul_(conj_(inv_ab), d)));
+        const T fv = mul_(inv_ab, f);            // v_r = S[r][j] / (alpha - beta) folded into f
         if (p == 0) S[(size_t)j * c + cc] = sub_(S[(size_t)j * c + cc], f);
-        for (int r = j + 1 + p; r < SR; r += RP) {
-          const T vr = mul_(S[(size_t)r * c + j], inv_ab);
-          S[(size_t)r * c + cc] = sub_(S[(size_t)r * c + cc], mul_(vr, f));
-        }
+        for (int r = j + 1 + p; r < SRu; r += RP)
+          S[(size_t)r * c + cc] = sub_(S[(size_t)r * c + cc], mul_(S[(size_t)r * c + j], fv));
       }
-      __syncthreads();
-      if (tid == 0) S[(size_t)j * c + j] = sv[j];
-      // column j below the diagonal is now dead (Q is not formed)
-      for (int r = j + 1 + tid; r < SR; r += NT) S[(size_t)r * c + j] = zero_<T>();
+      if (cc == j && p == 0) S[(size_t)j * c + j] = sh_beta;
       __syncthreads();
     }
     if (r_end <= r_begin) break;
@@ -192,13 +192,9 @@ __global__ void __launch_bounds__(1024) rr_small_kernel(const T* __restrict__ Rt
           a += abs2_(xp[rr]); bb += abs2_(xq[rr]); g = madc_(xp[rr], xq[rr], g);
         }
         a = warp_sum(a); bb = warp_sum(bb); g = warp_sum(g);
-        const double ga = sqrt(abs2_(g));
-        if (!(ga > tol * sqrt(a) * sqrt(bb)) || a <= tiny2 || bb <= tiny2) continue;
-        const T e = scale_(g, 1.0 / ga);
-        const double zeta = (bb - a) / (2.0 * ga);
-        const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + hypot(1.0, zeta));
-        if (fabs(t) <= 2.220446049250313e-16) continue;  // angle below eps: changes nothing but noise
-        const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+        double cs, sn;
+        T e;
+        if (!jacobi_rotation(a, bb, g, tol, tiny2, 2.220446049250313e-16, &cs, &sn, &e)) continue;
         const T se = scale_(e, sn), sec = conj_(se);
         for (int rr = lane; rr < c; rr += 32) {
           const T u = xp[rr], w = xq[rr];
@@ -417,6 +413,24 @@ __global__ void trimul_kernel(const S* __restrict__ L, int n, const T* __restric
   }
 }
 
+// Warp-cooperative sum_{k = k0 + lane, step 32} conj(x[k*ldx]) y[k*ldy] for k < n with four
+// independent accumulators per lane (dependent FP64 FMAs cost ~64 cycles each on GB300), then a
+// butterfly over the warp. Every lane returns the total.
+template <class T>
+__device__ inline T warp_dotc(const T* x, int64_t ldx, const T* y, int64_t ldy, int k0, int n) {
+  T a0 = zero_<T>(), a1 = zero_<T>(), a2 = zero_<T>(), a3 = zero_<T>();
+  const int lane = threadIdx.x & 31;
+  int k = k0 + lane;
+  for (; k + 96 < n; k += 128) {
+    a0 = madc_(x[(int64_t)k * ldx], y[(int64_t)k * ldy], a0);
+    a1 = madc_(x[(int64_t)(k + 32) * ldx], y[(int64_t)(k + 32) * ldy], a1);
+    a2 = madc_(x[(int64_t)(k + 64) * ldx], y[(int64_t)(k + 64) * ldy], a2);
+    a3 = madc_(x[(int64_t)(k + 96) * ldx], y[(int64_t)(k + 96) * ldy], a3);
+  }
+  for (; k < n; k += 32) a0 = madc_(x[(int64_t)k * ldx], y[(int64_t)k * ldy], a0);
+  return warp_sum(add_(add_(a0, a1), add_(a2, a3)));
+}
+
 // ------------------------------------------------------------------------------------------
 // bcgs2_orth (one CTA): W (n x b at column offset wo of T, ld) is made orthogonal to the
 // columns listed in [0, b) (V) and, when nx > 0, [2b, 3b) (X), twice (BCGS2), then replaced by
@@ -438,9 +452,7 @@ __global__ void __launch_bounds__(1024) bcgs2_orth_kernel(T* Tb, int n, int b, i
   for (int pass = 0; pass < passes && q > 0; ++pass) {
     for (int o = warp; o < q * b; o += nwarp) {
       const int j = o / b, cw = o % b;
-      T s = zero_<T>();
-      for (int k = lane; k < n; k += 32) s = madc_(Tb[(int64_t)k * ld + bcol(j)], Tb[(int64_t)k * ld + wo + cw], s);
-      s = warp_sum(s);
+      const T s = warp_dotc(Tb + bcol(j), ld, Tb + wo + cw, ld, 0, n);
       if (lane == 0) P[o] = s;
     }
     __syncthreads();
@@ -456,9 +468,7 @@ __global__ void __launch_bounds__(1024) bcgs2_orth_kernel(T* Tb, int n, int b, i
   for (int j = 0; j < b; ++j) {
     // d_cc = sum_{k > j} conj(W[k][j]) W[k][cc], cc >= j
     for (int cc = j + warp; cc < b; cc += nwarp) {
-      T s = zero_<T>();
-      for (int k = j + 1 + lane; k < n; k += 32) s = madc_(Tb[(int64_t)k * ld + wo + j], Tb[(int64_t)k * ld + wo + cc], s);
-      s = warp_sum(s);
+      const T s = warp_dotc(Tb + wo + j, ld, Tb + wo + cc, ld, j + 1, n);
       if (lane == 0) sv[cc] = s;
     }
     __syncthreads();
@@ -492,10 +502,8 @@ __global__ void __launch_bounds__(1024) bcgs2_orth_kernel(T* Tb, int n, int b, i
   __syncthreads();
   for (int j = b - 1; j >= 0; --j) {
     for (int cc = j + warp; cc < b; cc += nwarp) {
-      T s = E[(int64_t)j * b + cc];
-      T part = zero_<T>();
-      for (int k = j + 1 + lane; k < n; k += 32) part = madc_(Tb[(int64_t)k * ld + wo + j], E[(int64_t)k * b + cc], part);
-      part = warp_sum(part);
+      const T s = E[(int64_t)j * b + cc];
+      const T part = warp_dotc(Tb + wo + j, ld, E + cc, b, j + 1, n);
       if (lane == 0) sv[cc] = mul_(tauv[j], add_(s, part));
     }
     __syncthreads();
@@ -599,21 +607,24 @@ __global__ void nonfinite_scan_kernel(const T* A, int64_t m, int n, int64_t lda,
 // host launchers
 // ------------------------------------------------------------------------------------------
 static int tsqr_chunk(int c, size_t esz) {
-  int ch = (int)(150 * 1024 / ((size_t)c * esz)) - c;
-  ch = max(32, min(256, ch));
+  int ch = (int)(64 * 1024 / ((size_t)c * esz)) - c;   // ~64 KB of smem: 3 CTAs per SM
+  ch = imax(32, imin(256, ch));
   return ch;
 }
 
 static int pow2_at_least(int x) { int p = 1; while (p < x) p <<= 1; return p; }
 
-static size_t tsqr_level_smem(int c, int CH, int CP, size_t esz) {
-  const int RP = 256 / CP;
-  return ((size_t)(c + CH) * c + (size_t)CP * RP + c) * esz;
+static int tsqr_rp(int c) { return imin(32, 256 / pow2_at_least(c)); }
+
+static size_t tsqr_level_smem(int c, int CH, size_t esz) { return (size_t)(c + CH) * c * esz; }
+
+static int64_t tsqr_level1_ctas(int64_t m, int c, size_t esz) {
+  const int CH = tsqr_chunk(c, esz);
+  return imin<int64_t>(3 * (int64_t)num_sms(), imax<int64_t>(1, (m + CH - 1) / CH));
 }
 
 size_t tsqr_workspace_bytes(int64_t m, int c, size_t esz) {
-  const int CH = tsqr_chunk(c, esz);
-  int64_t g1 = imin<int64_t>(num_sms(), imax<int64_t>(1, (m + CH - 1) / CH));
+  const int64_t g1 = tsqr_level1_ctas(m, c, esz);
   // level buffers ping-pong
   return 2 * (((size_t)g1 * c * c * esz + 255) & ~(size_t)255);
 }
@@ -624,25 +635,25 @@ int tsqr_impl(const T* X, int64_t m, int c, int64_t ldx, T* R, void* work, size_
   const size_t esz = sizeof(T);
   if (work_bytes < tsqr_workspace_bytes(m, c, esz)) return RLOBPCG_ERR_INVALID_ARG;
   const int CH = tsqr_chunk(c, esz);
-  const int CP = pow2_at_least(c);
-  if (CP > 256) return RLOBPCG_ERR_UNSUPPORTED;
-  const size_t smem = tsqr_level_smem(c, CH, CP, esz);
+  const int RP = tsqr_rp(c);
+  const size_t smem = tsqr_level_smem(c, CH, esz);
   RL_CUDA(cudaFuncSetAttribute(tsqr_level_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  const int64_t g1 = imin<int64_t>(num_sms(), imax<int64_t>(1, (m + CH - 1) / CH));
+  const int64_t g1 = tsqr_level1_ctas(m, c, esz);
   const size_t half = (((size_t)g1 * c * c * esz + 255) & ~(size_t)255);
   T* buf[2] = {(T*)work, (T*)((unsigned char*)work + half)};
   int64_t rpc = (m + g1 - 1) / g1;
   int64_t grid = (m + rpc - 1) / rpc;
   if (grid < 1) grid = 1;
-  tsqr_level_kernel<T><<<(int)grid, 256, smem, st>>>(X, m, c, ldx, rpc, CH, CP, buf[0]);
+  tsqr_level_kernel<T><<<(int)grid, 256, smem, st>>>(X, m, c, ldx, rpc, CH, RP, buf[0]);
   RL_CHECK_LAUNCH();
   int cur = 0;
-  const int FAN = 16;
+  // fixed-order tree: each CTA of the next level stacks the R factors of up to FAN CTAs
+  const int FAN = imax(2, imin(32, CH / c));
   while (grid > 1) {
     const int64_t rows = grid * c;
     const int64_t rpc2 = (int64_t)FAN * c;
     const int64_t g2 = (rows + rpc2 - 1) / rpc2;
-    tsqr_level_kernel<T><<<(int)g2, 256, smem, st>>>(buf[cur], rows, c, c, rpc2, CH, CP, buf[cur ^ 1]);
+    tsqr_level_kernel<T><<<(int)g2, 256, smem, st>>>(buf[cur], rows, c, c, rpc2, CH, RP, buf[cur ^ 1]);
     RL_CHECK_LAUNCH();
     cur ^= 1;
     grid = g2;
