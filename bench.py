@@ -7,7 +7,10 @@ One step = one complete solve (sketch, QR, SVD of R, R^{-1}, start block, LOBPCG
 the paper's stopping rule, outputs). A (400 MB) is larger than the 129 MB L2, so no flush is needed
 between steps.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
+
+--workload selects one of the other configurations of the study (small 4000 x 50, complex
+2e5 x 300 with FP32 or FP64 sketch, 1e6 x 1000 FP64 or mixed); the default is the one above.
 
 Under torchrun each rank solves its own matrices on its own GPU (independent problems, no
 collective on the data path: weak scaling); rank 0 prints the max-over-ranks time.
@@ -34,17 +37,61 @@ sys.path.insert(0, ROOT)
 from paper_2602_16797_gb300 import replicas  # noqa: E402
 
 METRIC = "solve time & solves/s at stated σ/angle error; fused AᴴAX GB/s; p50/p99 latency"
-WORKLOAD = "nullspace+planted m=1e5 n=500 k=5 d=3n zeta=8 fp64"
-M, N, K_TRIPLETS, D, ZETA = 100_000, 500, 5, 1500, 8
-SAMPLE_M = 20_000          # row sample for the CPU oracle timings
+SAMPLE_FRAC = 0.2          # row sample of the CPU oracle timings (m -> 0.2 m)
 FP64_UNITS_PER_SM_CLK = 2  # DFMA per clock per SM: 1.25 TFLOP/s nominal / (152 SMs * 2.07 GHz * 2 flop)
 
 
-def make_inputs(m):
+def _host_pair(m):
     from paper_2602_16797_gb300 import workloads as wl
     A0, _ = wl.exact_nullspace(m=m)
     A1, _, _ = wl.planted_bottom_cluster(m=m)
     return [A0, A1]
+
+
+def _host_small(m):
+    from paper_2602_16797_gb300 import workloads as wl
+    return [wl.planted_small_gap_free(m=m)[0]]
+
+
+def _host_complex(m):
+    from paper_2602_16797_gb300 import workloads as wl
+    return [wl.planted_complex(m=m)[0]]
+
+
+def _device_large(m, device):
+    from paper_2602_16797_gb300 import workloads as wl
+    return [wl.planted_large_device(m=m, device=device)[0]]
+
+
+# Named workloads. The default is the m = 1e5, n = 500, k = 5 configuration; the others are the
+# remaining configurations of the same study (same JSON line, selected with --workload).
+WORKLOADS = {
+    "nullspace_1e5x500": dict(
+        desc="nullspace+planted m=1e5 n=500 k=5 d=3n zeta=8 fp64", m=100_000, n=500, k=5, d=1500, zeta=8,
+        cplx=False, prec=0, host=_host_pair, seeds=(2002, 2003),
+        matrices="exact nullspace A=BC and planted sigma_496..500 in [1e-12,1e-9], alternating"),
+    "small_4000x50": dict(
+        desc="planted m=4000 n=50 k=1 d=4n zeta=8 tau=1e-12 fp64", m=4000, n=50, k=1, d=200, zeta=8, cplx=False,
+        prec=0, host=_host_small, seeds=(1001,), tau=1e-12, stagnation=0,
+        matrices="planted sigma_1..49 logspace(0,-6), sigma_50=1e-10"),
+    "complex_2e5x300_f32sketch": dict(
+        desc="complex planted m=2e5 n=300 k=3 d=4n zeta=8 fp32 sketch", m=200_000, n=300, k=3, d=1200, zeta=8,
+        cplx=True, prec=1, host=_host_complex, seeds=(1003,),
+        matrices="complex planted sigma logspace(0,-8), three smallest 1e-12, 3e-13, 1e-13"),
+    "complex_2e5x300": dict(
+        desc="complex planted m=2e5 n=300 k=3 d=4n zeta=8 fp64 sketch", m=200_000, n=300, k=3, d=1200, zeta=8,
+        cplx=True, prec=0, host=_host_complex, seeds=(1003,),
+        matrices="complex planted sigma logspace(0,-8), three smallest 1e-12, 3e-13, 1e-13"),
+    "large_1e6x1000_mixed": dict(
+        desc="planted m=1e6 n=1000 k=10 d=4n zeta=8 fp32 sketch/R, fp64 Gram", m=1_000_000, n=1000, k=10, d=4000,
+        zeta=8, cplx=False, prec=1, device=_device_large, seeds=(1004,),
+        matrices="planted sigma_1..990 logspace(0,-4), sigma_991..1000 logspace(-9,-10)"),
+    "large_1e6x1000": dict(
+        desc="planted m=1e6 n=1000 k=10 d=4n zeta=8 fp64", m=1_000_000, n=1000, k=10, d=4000, zeta=8,
+        cplx=False, prec=0, device=_device_large, seeds=(1004,),
+        matrices="planted sigma_1..990 logspace(0,-4), sigma_991..1000 logspace(-9,-10)"),
+}
+DEFAULT_WORKLOAD = "nullspace_1e5x500"
 
 
 # ------------------------------------------------------------------------------------------ clocks
@@ -102,20 +149,32 @@ class ClockSampler:
 
 # ------------------------------------------------------------------------------------- oracle timing
 
-def oracle_solves_per_s(n_solves, warmup=0):
-    """The oracle on the row-sampled workload; returns (full-size solves/s estimate, seconds, info)."""
+def oracle_solves_per_s(w, n_solves, warmup=0):
+    """The oracle on a row sample (m -> SAMPLE_FRAC m) of the workload; returns (full-size solves/s
+    estimate, per-solve seconds). Per-solve work is linear in m (the sketch and every iteration
+    stream A once)."""
     import oracle
-    As = make_inputs(SAMPLE_M)
+    ms = int(w["m"] * SAMPLE_FRAC)
+    if "host" in w:
+        As = w["host"](ms)
+    else:
+        from paper_2602_16797_gb300 import workloads as wl
+        sig = np.concatenate([np.logspace(0, -4, w["n"] - w["k"]), np.logspace(-9, -10, w["k"])])
+        As = [wl.planted(np.random.default_rng(w["seeds"][0]), ms, sig)[0]]
+    kw = dict(k=w["k"], d=w["d"], zeta=w["zeta"], sketch_precision="f32" if w["prec"] else "f64")
+    if "tau" in w:
+        kw["tau"] = w["tau"]
+    if w.get("stagnation", 1) == 0:
+        kw["use_stagnation"] = False
     for i in range(warmup):
-        oracle.rlobpcg(As[i % 2], k=K_TRIPLETS, d=D, zeta=ZETA, seed=2002 + (i % 2))
+        oracle.rlobpcg(As[i % len(As)], seed=w["seeds"][i % len(w["seeds"])], **kw)
     times = []
     for i in range(n_solves):
         t0 = time.perf_counter()
-        oracle.rlobpcg(As[i % 2], k=K_TRIPLETS, d=D, zeta=ZETA, seed=2002 + (i % 2))
+        oracle.rlobpcg(As[i % len(As)], seed=w["seeds"][i % len(w["seeds"])], **kw)
         times.append(time.perf_counter() - t0)
     per = sum(times) / len(times)
-    # per-solve work of the method is proportional to m (sketch and every iteration stream A)
-    return (SAMPLE_M / M) / per, times
+    return (ms / w["m"]) / per, times
 
 
 def cpu_cores():
@@ -148,24 +207,40 @@ def run_ours(args, rank, world, local_rank):
 
     from paper_2602_16797_gb300 import rlobpcg as rl
 
+    w = WORKLOADS[args.workload]
+    M, N, K, D = w["m"], w["n"], w["k"], w["d"]
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     rl.load()
-    As = make_inputs(M)
-    Ad = [torch.from_numpy(A).to(dev) for A in As]
+    if "host" in w:
+        hostA = w["host"](M)
+        Ad = [torch.from_numpy(A).to(dev) for A in hostA]
+    else:
+        Ad = w["device"](M, dev)
+        hostA = None
+    dtype = rl.RLOBPCG_C128 if w["cplx"] else rl.RLOBPCG_F64
+    tdt = torch.complex128 if w["cplx"] else torch.float64
+    esz = 16 if w["cplx"] else 8
     stream = torch.cuda.current_stream(dev)
     o = rl.rlobpcg_default_opts()
     o.d = D
-    o.zeta = ZETA
-    plan = rl.rlobpcg_plan(M, N, K_TRIPLETS, rl.RLOBPCG_F64, o, stream.cuda_stream)
-    sigma = torch.empty(K_TRIPLETS, dtype=torch.float64, device=dev)
-    resid = torch.empty(K_TRIPLETS, dtype=torch.float64, device=dev)
-    V = torch.empty((N, K_TRIPLETS), dtype=torch.float64, device=dev)
+    o.zeta = w["zeta"]
+    o.sketch_prec = w["prec"]
+    if "stagnation" in w:
+        o.use_stagnation = w["stagnation"]
+    if "tau" in w:
+        o.tau = w["tau"]
+    plan = rl.rlobpcg_plan(M, N, K, dtype, o, stream.cuda_stream)
+    sigma = torch.empty(K, dtype=torch.float64, device=dev)
+    resid = torch.empty(K, dtype=torch.float64, device=dev)
+    V = torch.empty((N, K), dtype=tdt, device=dev)
+    seeds = w["seeds"]
 
-    def step(i, info):
-        o.seed = 2002 + (i % 2)
-        rl.rlobpcg_solve(plan, Ad[i % 2].data_ptr(), N, -1.0, sigma.data_ptr(), V.data_ptr(), None,
-                         resid.data_ptr(), info)
+    def step(i, info, A_ptr=None, out=None):
+        o.seed = seeds[i % len(seeds)]
+        a = A_ptr if A_ptr is not None else Ad[i % len(Ad)].data_ptr()
+        sg, vv, rs = out if out is not None else (sigma.data_ptr(), V.data_ptr(), resid.data_ptr())
+        rl.rlobpcg_solve(plan, a, N, -1.0, sg, vv, None, rs, info)
 
     for i in range(args.warmup):
         step(i, rl.rlobpcg_info())
@@ -190,41 +265,39 @@ def run_ours(args, rank, world, local_rank):
     ms_total = replicas.max_over_ranks(ms_total, world, device=dev)
 
     # e2e: host buffers through the same C-ABI call (H2D of A and D2H of the results inside)
-    pinned = [torch.from_numpy(A).pin_memory() for A in As]
-    sig_h = torch.empty(K_TRIPLETS, dtype=torch.float64).pin_memory()
-    V_h = torch.empty((N, K_TRIPLETS), dtype=torch.float64).pin_memory()
-    res_h = torch.empty(K_TRIPLETS, dtype=torch.float64).pin_memory()
+    pinned = [torch.from_numpy(A).pin_memory() for A in hostA] if hostA is not None else \
+        [A.cpu().pin_memory() for A in Ad]
+    sig_h = torch.empty(K, dtype=torch.float64).pin_memory()
+    V_h = torch.empty((N, K), dtype=tdt).pin_memory()
+    res_h = torch.empty(K, dtype=torch.float64).pin_memory()
+    hout = (sig_h.data_ptr(), V_h.data_ptr(), res_h.data_ptr())
     e2e_steps = max(2, min(args.steps, 4))
     info = rl.rlobpcg_info()
-    o.seed = 2002
-    rl.rlobpcg_solve(plan, pinned[0].data_ptr(), N, -1.0, sig_h.data_ptr(), V_h.data_ptr(), None, res_h.data_ptr(),
-                     info)  # warm the plan's host-input buffer
+    step(0, info, pinned[0].data_ptr(), hout)  # warm the plan's host-input buffer
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for i in range(e2e_steps):
-        o.seed = 2002 + (i % 2)
-        rl.rlobpcg_solve(plan, pinned[i % 2].data_ptr(), N, -1.0, sig_h.data_ptr(), V_h.data_ptr(), None,
-                         res_h.data_ptr(), info)
+        step(i, info, pinned[i % len(pinned)].data_ptr(), hout)
     e2e_s = time.perf_counter() - t0
     rl.rlobpcg_plan_destroy(plan)
 
     # roofline of the fused Gram pass (FP64 ALU bound): algorithmic flops per pass / event time
     gram_ms = sum(x.ms_gram for x in infos)
     passes = sum(x.gram_passes for x in infos)
-    b = K_TRIPLETS
-    flops_pass = 4.0 * M * N * b
-    bytes_pass = 8.0 * M * N + 8.0 * M * b
+    fl_el = 16.0 if w["cplx"] else 4.0
+    flops_pass = fl_el * M * N * K
+    bytes_pass = esz * (M * N + M * K)
     avg_s = gram_ms / max(passes, 1) * 1e-3
     achieved_tf = flops_pass / avg_s / 1e12 if passes else None
     props = torch.cuda.get_device_properties(dev)
     sm_count = props.multi_processor_count
     max_mhz = clk.get("sm_max_mhz") or 2070.0
     peak_tf = sm_count * FP64_UNITS_PER_SM_CLK * 2 * max_mhz * 1e6 / 1e12
-    per_elem = gram_traffic_per_element()
+    per_elem = gram_traffic_per_element() if args.workload == DEFAULT_WORKLOAD else None
     roofline = {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
                 "frac": (achieved_tf / peak_tf) if achieved_tf else None,
                 "traffic": (per_elem * M * N) if per_elem is not None else None,
-                "kernel": "gram_kernel (fused A W, A^H A W), FP64",
+                "kernel": "gram_kernel (fused A W, A^H A W), " + ("complex128" if w["cplx"] else "FP64"),
                 "peak_source": f"derived: {sm_count} SMs x {FP64_UNITS_PER_SM_CLK} DFMA/clk x 2 flop x {max_mhz:.0f} MHz",
                 "achieved_gbs": bytes_pass / avg_s / 1e9 if passes else None,
                 "passes_timed": passes}
@@ -233,32 +306,34 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0:
         ms_per = ms_total / args.steps
         value = replicas.job_rate(args.steps, world, ms_total * 1e-3)
-        lat_sorted = sorted(lat)
         result = {
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded, paper-shaped; see DESIGN.md)",
-            "config": {"workload": WORKLOAD, "m": M, "n": N, "k": K_TRIPLETS, "d": D, "zeta": ZETA,
-                       "matrices": "exact nullspace A=BC and planted sigma_496..500 in [1e-12,1e-9], alternating",
-                       "l2": "inputs (400 MB each) larger than L2; no flush", "parallelism": f"replicas x{world}"},
-            "latency_ms": {"p50": float(np.percentile(lat_sorted, 50)), "p99": float(np.percentile(lat_sorted, 99))},
+            "vs_baseline": None, "dtype": "c128" if w["cplx"] else "f64",
+            "data": "synthetic (seeded, paper-shaped; see DESIGN.md)",
+            "config": {"workload": w["desc"], "m": M, "n": N, "k": K, "d": D, "zeta": w["zeta"],
+                       "sketch": "fp32" if w["prec"] else "fp64", "matrices": w["matrices"],
+                       "l2": "input larger than L2; no flush" if M * N * esz > 129e6 else
+                             "input smaller than L2 (each step is a full solve)",
+                       "parallelism": f"replicas x{world}"},
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
             "iters": [x.iters for x in infos], "stop_reasons": [x.stop_reason for x in infos],
-            "jacobi_sweeps": [x.jacobi_sweeps for x in infos],
             "phase_ms": {"sketch": statistics.mean(x.ms_sketch for x in infos),
                          "factor": statistics.mean(x.ms_factor for x in infos),
                          "iterate": statistics.mean(x.ms_iterate for x in infos),
                          "gram_per_pass": avg_s * 1e3},
+            "sigma": [float(x) for x in sigma.cpu().numpy()],
             "roofline": roofline, "clocks": clk,
             "gpu_launches": int(sum(x.kernel_launches for x in infos)),
-            "e2e": {"value": e2e_steps / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": 8 * M * N,
-                    "d2h_bytes_per_step": 8 * (K_TRIPLETS + N * K_TRIPLETS + K_TRIPLETS)},
+            "e2e": {"value": e2e_steps / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": esz * M * N,
+                    "d2h_bytes_per_step": 8 * K + esz * N * K + 8 * K},
         }
         if world == 1 and not args.no_cpu_baseline:
-            v, times = oracle_solves_per_s(3)
+            v, times = oracle_solves_per_s(w, 3)
             result["cpu_baseline"] = {"value": v, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
-                                      "sample": f"3 oracle solves of the same two matrix families at m={SAMPLE_M} "
-                                                f"rows ({sum(times):.1f} s), scaled by {SAMPLE_M}/{M} (work is "
-                                                f"linear in m); numpy/LAPACK with all host cores"}
+                                      "sample": f"3 oracle solves of the same matrix families at m={int(M * SAMPLE_FRAC)} "
+                                                f"rows ({sum(times):.1f} s), scaled by {SAMPLE_FRAC} (work is linear "
+                                                f"in m); numpy/LAPACK with all host cores"}
         out = result
     return out
 
@@ -266,17 +341,18 @@ def run_ours(args, rank, world, local_rank):
 def run_reference(args, rank, world):
     if rank != 0:
         return None
-    warm = args.warmup
-    v, times = oracle_solves_per_s(args.steps, warmup=warm)
+    w = WORKLOADS[args.workload]
+    v, times = oracle_solves_per_s(w, args.steps, warmup=args.warmup)
     total = sum(times)
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": world,
-            "steps": args.steps, "warmup": warm, "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (seeded, paper-shaped; see DESIGN.md)",
-            "config": {"workload": WORKLOAD, "m": M, "n": N, "k": K_TRIPLETS, "d": D, "zeta": ZETA,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c128" if w["cplx"] else "f64", "data": "synthetic (seeded, paper-shaped; see DESIGN.md)",
+            "config": {"workload": w["desc"], "m": w["m"], "n": w["n"], "k": w["k"], "d": w["d"], "zeta": w["zeta"],
                        "parallelism": "cpu oracle, rank 0 only"},
             "cpu_baseline": {"value": v, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
-                             "sample": f"each step one oracle solve at m={SAMPLE_M} rows, scaled by {SAMPLE_M}/{M}"},
+                             "sample": f"each step one oracle solve at m={int(w['m'] * SAMPLE_FRAC)} rows, "
+                                       f"scaled by {SAMPLE_FRAC}"},
             "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -287,6 +363,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
     args = ap.parse_args()
     rank, world, local_rank = replicas.world_from_env()
     if world > 1 and args.impl == "ours":

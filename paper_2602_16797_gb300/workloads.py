@@ -175,3 +175,37 @@ def serve_request(r: int):
     sigma = np.concatenate([np.logspace(0, -6, n - k), np.logspace(-9, -10, k)])
     A, _, _ = planted(rng, m, sigma)
     return A, k, "planted"
+
+
+def planted_on_device(seed: int, m: int, sigma: np.ndarray, device="cuda", complex_: bool = False):
+    """A = U diag(sigma) V^H built on a GPU with torch (for sizes where a host QR of the m x n
+    Gaussian takes minutes, e.g. 1e6 x 1000). U: Q of a seeded Gaussian (Philox stream of
+    torch.Generator(device).manual_seed(seed)) with the phases of diag(R) folded back; V: Haar
+    from numpy on the host. Returns (A on the device, sigma sorted descending, V as numpy)."""
+    import torch
+    sigma = np.asarray(sigma, dtype=np.float64)
+    n = sigma.size
+    rng = np.random.default_rng(seed)
+    V = haar_orthonormal(rng, n, n, complex_)
+    gen = torch.Generator(device=device).manual_seed(int(seed))
+    dt = torch.complex128 if complex_ else torch.float64
+    G = torch.randn((m, n), generator=gen, device=device, dtype=dt)
+    Q, R = torch.linalg.qr(G)
+    del G
+    d = torch.diagonal(R)
+    ph = torch.where(d.abs() > 0, d / d.abs(), torch.ones_like(d))
+    Q *= ph[None, :]
+    del R
+    Vd = torch.from_numpy(np.ascontiguousarray(V)).to(device)
+    Q *= torch.from_numpy(sigma).to(device=device, dtype=Q.real.dtype)[None, :].to(dt)
+    A = Q @ Vd.conj().T
+    del Q
+    order = np.argsort(-sigma, kind="stable")
+    return A.contiguous(), sigma[order], V[:, order]
+
+
+def planted_large_device(seed: int = SEED_BASE + 4, m: int = 1_000_000, n: int = 1000, k: int = 10, device="cuda"):
+    """The 1e6 x 1000 planted workload (sigma_1..990 logspace(0,-4), sigma_991..1000 logspace(-9,-10))
+    generated on the device."""
+    sigma = np.concatenate([np.logspace(0, -4, n - k), np.logspace(-9, -10, k)])
+    return planted_on_device(seed, m, sigma, device=device)
