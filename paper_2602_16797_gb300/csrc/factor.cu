@@ -41,62 +41,92 @@ __device__ inline cf recip_(cf a) { float s = a.x * a.x + a.y * a.y; return {a.x
 // ------------------------------------------------------------------------------------------
 // Householder QR (LAPACK geqr2 reflector convention: H = I - tau v v^H, v(0) = 1, H^H x = beta e1)
 // M: d x n column-major (ld = d), overwritten: R in the upper triangle, v below the diagonal.
-// Column c is owned by warp (cta = c % G, warp = (c / G) % FQ_WARPS) of the grid.
+// Column c is owned by CTA c % G; the CTA's 8 warps split its rows, so the dependent FP64 chain
+// of each dot product or update is d/256 long (a dependent FP64 instruction costs ~64 cycles on
+// GB300). One grid barrier per column step.
 // ------------------------------------------------------------------------------------------
+
+// Sum of one value per thread over the CTA (FQ_THREADS threads); every thread gets the total.
+// Fixed order: butterfly inside each warp, then warp 0 combines the 8 warp sums.
 template <class S>
-__device__ void make_reflector(S* col, int j, int d, S* tau, int lane) {
-  using R = RealOf<S>;
-  R part = 0;
-  for (int r = j + 1 + lane; r < d; r += 32) part += abs2_(col[r]);
-  const R xnorm2 = warp_sum(part);
-  const S alpha = col[j];
-  S t = zero_<S>();
-  S beta = alpha;
-  if (!(xnorm2 == (R)0 && im_(alpha) == (R)0)) {
-    const R ar = re_(alpha);
-    R bn = sqrt_(abs2_(alpha) + xnorm2);
-    const R b = ar >= (R)0 ? -bn : bn;
-    beta = from_real<S>(b);
-    // tau = (beta - alpha) / beta ; scale = 1 / (alpha - beta)
-    t = scale_(sub_(beta, alpha), (R)1 / b);
-    const S sc = recip_(sub_(alpha, beta));
-    for (int r = j + 1 + lane; r < d; r += 32) col[r] = mul_(col[r], sc);
+__device__ inline S cta_sum(S v, S* red) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  v = warp_sum(v);
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    S t = lane < FQ_WARPS ? red[lane] : zero_<S>();
+#pragma unroll
+    for (int o = FQ_WARPS / 2; o > 0; o >>= 1) t = add_(t, shfl_xor_(t, o));
+    if (lane == 0) red[FQ_WARPS] = t;
   }
-  __syncwarp();
-  if (lane == 0) { col[j] = beta; tau[j] = t; }
-  __syncwarp();
+  __syncthreads();
+  const S r = red[FQ_WARPS];
+  __syncthreads();
+  return r;
+}
+
+template <class S>
+__device__ void cta_reflector(S* col, int j, int d, S* tau, S* red) {
+  using R = RealOf<S>;
+  R p0 = 0, p1 = 0;
+  int r = j + 1 + threadIdx.x;
+  for (; r + FQ_THREADS < d; r += 2 * FQ_THREADS) { p0 += abs2_(col[r]); p1 += abs2_(col[r + FQ_THREADS]); }
+  if (r < d) p0 += abs2_(col[r]);
+  const R xnorm2 = re_(cta_sum(from_real<S>(p0 + p1), red));
+  __shared__ S sc_s;
+  if (threadIdx.x == 0) {
+    const S alpha = col[j];
+    S t = zero_<S>(), beta = alpha, sc = zero_<S>();
+    if (!(xnorm2 == (R)0 && im_(alpha) == (R)0)) {
+      const R bn = sqrt_(abs2_(alpha) + xnorm2);
+      const R b = re_(alpha) >= (R)0 ? -bn : bn;
+      beta = from_real<S>(b);
+      // one divide: rr = 1 / (beta (alpha - beta)); 1/beta = (alpha - beta) rr, 1/(alpha - beta) = beta rr
+      const S amb = sub_(alpha, beta);
+      const S rr = recip_(scale_(amb, b));
+      t = mul_(sub_(beta, alpha), mul_(amb, rr));
+      sc = scale_(rr, b);
+    }
+    tau[j] = t;
+    col[j] = beta;
+    sc_s = sc;
+  }
+  __syncthreads();
+  const S sc = sc_s;
+  for (int q = j + 1 + threadIdx.x; q < d; q += FQ_THREADS) col[q] = mul_(col[q], sc);
+  __syncthreads();
 }
 
 template <class S>
 __global__ void __launch_bounds__(FQ_THREADS) qr_kernel(S* M, int d, int n, S* tau) {
   cg::grid_group grid = cg::this_grid();
   const int G = gridDim.x;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // column c belongs to CTA c % G and warp (c / G) % FQ_WARPS: c = blockIdx.x + G (warp + 8 t)
-  const int c_first = blockIdx.x + G * warp, c_step = G * FQ_WARPS;
-
-  if (c_first == 0) make_reflector(M, 0, d, tau, lane);
+  __shared__ S red[FQ_WARPS + 1];
+  if (blockIdx.x == 0) cta_reflector(M, 0, d, tau, red);
   grid.sync();
   for (int j = 0; j < n; ++j) {
     const S* v = M + (int64_t)j * d;  // v(j) = 1 implicit, v(r) for r > j stored
     const S tj = tau[j];
-    int c = c_first;
-    if (c <= j) c += ((j - c) / c_step + 1) * c_step;  // first owned column > j
-    for (; c < n; c += c_step) {
+    int c = blockIdx.x;
+    if (c <= j) c += ((j - c) / G + 1) * G;  // first owned column > j
+    for (; c < n; c += G) {
       S* col = M + (int64_t)c * d;
-      S part = zero_<S>();
-      for (int r = j + lane; r < d; r += 32) {
-        const S vr = (r == j) ? from_real<S>((RealOf<S>)1) : v[r];
-        part = madc_(vr, col[r], part);
+      S a0 = zero_<S>(), a1 = zero_<S>();
+      int r = j + 1 + threadIdx.x;
+      for (; r + FQ_THREADS < d; r += 2 * FQ_THREADS) {
+        a0 = madc_(v[r], col[r], a0);
+        a1 = madc_(v[r + FQ_THREADS], col[r + FQ_THREADS], a1);
       }
-      const S s = warp_sum(part);
+      if (r < d) a0 = madc_(v[r], col[r], a0);
+      S part = add_(a0, a1);
+      if (threadIdx.x == 0) part = add_(part, col[j]);   // v(j) = 1
+      const S s = cta_sum(part, red);
       const S f = mul_(conj_(tj), s);   // apply H^H = I - conj(tau) v v^H
-      for (int r = j + lane; r < d; r += 32) {
-        const S vr = (r == j) ? from_real<S>((RealOf<S>)1) : v[r];
-        col[r] = sub_(col[r], mul_(vr, f));
-      }
-      __syncwarp();
-      if (c == j + 1) make_reflector(col, j + 1, d, tau, lane);
+      if (threadIdx.x == 0) col[j] = sub_(col[j], f);
+      for (int q = j + 1 + threadIdx.x; q < d; q += FQ_THREADS) col[q] = sub_(col[q], mul_(v[q], f));
+      __syncthreads();
+      if (c == j + 1) cta_reflector(col, j + 1, d, tau, red);
     }
     grid.sync();
   }

@@ -1,154 +1,129 @@
 // Sketch SA = S A with the SparseStack embedding (Sec. 2.2 of arXiv 2602.16797).
 //
-// Design (GB300): S is never stored. A CTA owns (a block of w columns of A) x (one piece j of
-// the SparseStack columns) x (a sub-range of that piece's destination rows); its accumulator
-// block of SA lives in shared memory. The CTA streams the rows of its column block through a
-// cp.async ring; for each row i it derives the destination row and sign of piece j from
-// SplitMix64 (one hash per row, computed once per CTA). Warp kk owns column kk and its lanes own
-// 32 consecutive rows: lanes that hit the same destination are grouped with match_any and their
-// values are added by the group's first lane in ascending row order. Every SA entry therefore
-// sums its sources in ascending source row -- the same order as a sequential reference -- and
-// only then is scaled by zeta^{-1/2}: the result is reproducible bit for bit.
-// The 8 piece-CTAs of a column block read the same A rows at nearly the same time, so A comes
-// from HBM once and from L2 the other zeta-1 times.
+// Design (GB300): S is never stored. A CTA owns a block of R destination rows of one piece j
+// and a block of up to 256 columns; its slice of SA accumulates in shared memory. The CTA scans
+// all m source rows in chunks: each warp hashes 256 consecutive rows (SplitMix64, integer work
+// only) and keeps, in ascending row order, those whose piece-j destination falls in its block.
+// Then every thread (one column each) walks the kept rows in ascending order and adds +-A[i, k]
+// into its column of the accumulator, loading whole rows of A with coalesced reads. Each SA entry
+// therefore sums its sources in ascending source row -- the order of a sequential reference --
+// and is scaled by zeta^{-1/2} once at the end: the result is reproducible bit for bit. Every row
+// of A is read zeta times in total (once per piece), which costs less than the zeta m n adds.
 #include "common.cuh"
 
 namespace rl {
 
 namespace {
 
-constexpr int SK_TR = 64;      // rows per staged tile
-constexpr int SK_STAGES = 4;   // cp.async ring depth
-
-__device__ inline void cp_async_elem(void* smem, const void* gmem, int bytes) {
-  unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  if (bytes == 16) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-  } else {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
-  }
-}
-__device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N> __device__ inline void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
+constexpr int SK_NT = 256;           // threads per CTA (one column each in the add phase)
+constexpr int SK_WARPS = SK_NT / 32;
+constexpr int SK_GROUPS = 8;         // 32-row groups hashed per warp per chunk
+constexpr int SK_CHUNK = SK_WARPS * SK_GROUPS * 32;   // rows per chunk (2048)
 
 template <class TA, class TS>
-__global__ void __launch_bounds__(1024) sketch_kernel(const TA* __restrict__ A, int64_t m, int n,
-                                                      int64_t lda, int d, int zeta, uint64_t seed,
-                                                      int w, int sub, RealOf<TS> scale,
-                                                      TS* __restrict__ SA) {
+__global__ void __launch_bounds__(SK_NT) sketch_kernel(const TA* __restrict__ A, int64_t m, int n, int64_t lda,
+                                                       int d, int zeta, uint64_t seed, int R, int bpp,
+                                                       RealOf<TS> scale, TS* __restrict__ SA) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int nwarps = blockDim.x >> 5;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int k0 = blockIdx.x * w;
-  const int wcols = min(w, n - k0);
-  const int j = blockIdx.y;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int j = blockIdx.x / bpp;                 // piece
+  const int sblk = blockIdx.x % bpp;              // destination block inside the piece
   const int plo = piece_lo(j, d, zeta);
   const int plen = piece_lo(j + 1, d, zeta) - plo;
-  const int slo = blockIdx.z * sub;
-  const int shi = min(slo + sub, plen);
-  if (slo >= shi) return;  // whole CTA: this piece has no rows in this sub-range
-  const int slen = shi - slo;
+  const int dlo = sblk * R;
+  const int dhi = imin(dlo + R, plen);
+  if (dlo >= dhi) return;                         // whole CTA: empty block
+  const int k0 = blockIdx.y * SK_NT;
+  const int kk = k0 + tid;
+  const bool has_col = kk < n;
 
-  TS* acc = reinterpret_cast<TS*>(smem_raw);                         // [sub][w]
-  size_t off = ((size_t)sub * w * sizeof(TS) + 15) & ~(size_t)15;
-  TA* tiles = reinterpret_cast<TA*>(smem_raw + off);                 // [STAGES][TR][w+1]
-  off += (size_t)SK_STAGES * SK_TR * (w + 1) * sizeof(TA);
-  int* codes = reinterpret_cast<int*>(smem_raw + off);               // [STAGES][TR]
+  TS* acc = reinterpret_cast<TS*>(smem_raw);                       // [R][SK_NT]
+  int* lst = reinterpret_cast<int*>(smem_raw + (size_t)R * SK_NT * sizeof(TS));  // [WARPS][GROUPS*32]
+  int* code = lst + SK_WARPS * SK_GROUPS * 32;                     // matching (dest - dlo) << 1 | sign
+  __shared__ int cnt[SK_WARPS];
+  for (int r = 0; r < dhi - dlo; ++r) acc[r * SK_NT + tid] = zero_<TS>();
 
-  for (int idx = threadIdx.x; idx < slen * w; idx += blockDim.x) acc[idx] = zero_<TS>();
-
-  const int64_t ntiles = (m + SK_TR - 1) / SK_TR;
-  const int rows_per_warp = SK_TR / nwarps;
-
-  auto issue = [&](int64_t t) {
-    int s = (int)(t % SK_STAGES);
-    TA* tile = tiles + (size_t)s * SK_TR * (w + 1);
-    for (int rr = 0; rr < rows_per_warp; ++rr) {
-      int r = warp * rows_per_warp + rr;
-      int64_t i = t * SK_TR + r;
-      if (i < m && lane < wcols) cp_async_elem(&tile[r * (w + 1) + lane], &A[i * lda + k0 + lane], (int)sizeof(TA));
+  for (int64_t c0 = 0; c0 < m; c0 += SK_CHUNK) {
+    // phase 1: warp w hashes rows c0 + w*256 + [0, 256) and keeps its matches in row order
+    int mine = 0;
+    const int64_t wbase = c0 + (int64_t)warp * SK_GROUPS * 32;
+    for (int g = 0; g < SK_GROUPS; ++g) {
+      const int64_t i = wbase + g * 32 + lane;
+      bool hit = false;
+      int cd = 0;
+      if (i < m) {
+        const uint64_t h = splitmix64_at(seed, (uint64_t)i * (uint64_t)zeta + (uint64_t)j);
+        const int pos = (int)(((h >> 32) * (uint64_t)plen) >> 32);
+        hit = pos >= dlo && pos < dhi;
+        cd = ((pos - dlo) << 1) | (int)(h & 1ull);
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, hit);
+      if (hit) {
+        const int slot = mine + __popc(bal & ((1u << lane) - 1u));
+        lst[warp * SK_GROUPS * 32 + slot] = (int)(i - c0);
+        code[warp * SK_GROUPS * 32 + slot] = cd;
+      }
+      mine += __popc(bal);
     }
-    if (warp == 0) {
-      for (int r = lane; r < SK_TR; r += 32) {
-        int64_t i = t * SK_TR + r;
-        int code = -1;
-        if (i < m) {
-          uint64_t h = splitmix64_at(seed, (uint64_t)i * (uint64_t)zeta + (uint64_t)j);
-          int pos = (int)(((h >> 32) * (uint64_t)plen) >> 32);
-          if (pos >= slo && pos < shi) code = ((pos - slo) << 1) | (int)(h & 1ull);
+    if (lane == 0) cnt[warp] = mine;
+    __syncthreads();
+    // phase 2: each thread adds its column of the kept rows, warps' lists in order = row order
+    if (has_col) {
+      for (int w = 0; w < SK_WARPS; ++w) {
+        const int nw = cnt[w];
+        const int* L = lst + w * SK_GROUPS * 32;
+        const int* C = code + w * SK_GROUPS * 32;
+        int e = 0;
+        for (; e + 3 < nw; e += 4) {   // four loads in flight, adds in order
+          const TA v0 = A[(c0 + L[e]) * lda + kk];
+          const TA v1 = A[(c0 + L[e + 1]) * lda + kk];
+          const TA v2 = A[(c0 + L[e + 2]) * lda + kk];
+          const TA v3 = A[(c0 + L[e + 3]) * lda + kk];
+          int q = C[e];
+          acc[(q >> 1) * SK_NT + tid] = (q & 1) ? sub_(acc[(q >> 1) * SK_NT + tid], cvt_<TS, TA>(v0))
+                                                : add_(acc[(q >> 1) * SK_NT + tid], cvt_<TS, TA>(v0));
+          q = C[e + 1];
+          acc[(q >> 1) * SK_NT + tid] = (q & 1) ? sub_(acc[(q >> 1) * SK_NT + tid], cvt_<TS, TA>(v1))
+                                                : add_(acc[(q >> 1) * SK_NT + tid], cvt_<TS, TA>(v1));
+          q = C[e + 2];
+          acc[(q >> 1) * SK_NT + tid] = (q & 1) ? sub_(acc[(q >> 1) * SK_NT + tid], cvt_<TS, TA>(v2))
+                                                : add_(acc[(q >> 1) * SK_NT + tid], cvt_<TS, TA>(v2));
+          q = C[e + 3];
+          acc[(q >> 1) * SK_NT + tid] = (q & 1) ? sub_(acc[(q >> 1) * SK_NT + tid], cvt_<TS, TA>(v3))
+                                                : add_(acc[(q >> 1) * SK_NT + tid], cvt_<TS, TA>(v3));
         }
-        codes[s * SK_TR + r] = code;
+        for (; e < nw; ++e) {
+          const TA v = A[(c0 + L[e]) * lda + kk];
+          const int q = C[e];
+          acc[(q >> 1) * SK_NT + tid] = (q & 1) ? sub_(acc[(q >> 1) * SK_NT + tid], cvt_<TS, TA>(v))
+                                                : add_(acc[(q >> 1) * SK_NT + tid], cvt_<TS, TA>(v));
+        }
       }
     }
-  };
-
-  for (int64_t t = 0; t < SK_STAGES - 1; ++t) {
-    if (t < ntiles) issue(t);
-    cp_async_commit();
-  }
-  for (int64_t t = 0; t < ntiles; ++t) {
-    if (t + SK_STAGES - 1 < ntiles) issue(t + SK_STAGES - 1);
-    cp_async_commit();
-    cp_async_wait<SK_STAGES - 1>();
-    __syncthreads();
-    const int s = (int)(t % SK_STAGES);
-    const TA* tile = tiles + (size_t)s * SK_TR * (w + 1);
-    const int* cd_ = codes + s * SK_TR;
-    if (warp < wcols) {
-      const int kk = warp;
-#pragma unroll
-      for (int h = 0; h < SK_TR / 32; ++h) {
-        const int code = cd_[h * 32 + lane];
-        const int key = code < 0 ? -1 : (code >> 1);
-        const unsigned grp = __match_any_sync(0xffffffffu, key);
-        if (key >= 0 && lane == __ffs(grp) - 1) {
-          TS a = acc[key * w + kk];
-          unsigned mm = grp;
-          while (mm) {
-            const int q = __ffs(mm) - 1;
-            mm &= mm - 1;
-            const TS v = cvt_<TS, TA>(tile[(h * 32 + q) * (w + 1) + kk]);
-            a = (cd_[h * 32 + q] & 1) ? sub_(a, v) : add_(a, v);
-          }
-          acc[key * w + kk] = a;
-        }
-      }
-    }
     __syncthreads();
   }
-  cp_async_wait<0>();
-
   // write out, scaled once by zeta^{-1/2}; SA is column-major (d rows)
-  for (int idx = threadIdx.x; idx < slen * wcols; idx += blockDim.x) {
-    const int kk = idx / slen, p = idx % slen;
-    SA[(int64_t)(k0 + kk) * d + plo + slo + p] = scale_(acc[p * w + kk], scale);
-  }
+  if (has_col)
+    for (int r = 0; r < dhi - dlo; ++r) SA[(int64_t)kk * d + plo + dlo + r] = scale_(acc[r * SK_NT + tid], scale);
 }
 
 template <class TA, class TS>
-int launch_sketch(const TA* A, int64_t m, int n, int64_t lda, int d, int zeta, uint64_t seed,
-                  TS* SA, cudaStream_t st) {
-  const size_t budget = 150 * 1024;
+int launch_sketch(const TA* A, int64_t m, int n, int64_t lda, int d, int zeta, uint64_t seed, TS* SA,
+                  cudaStream_t st) {
   const int maxlen = (d + zeta - 1) / zeta + 1;
-  int w = sizeof(TA) == 16 ? 16 : 32;
-  w = min(w, n);
-  int sub = maxlen;
-  while (w > 8 && (size_t)sub * w * sizeof(TS) > budget) w >>= 1;
-  int nsub = 1;
-  while ((size_t)sub * w * sizeof(TS) > budget) { ++nsub; sub = (maxlen + nsub - 1) / nsub; }
-  // at least 2 warps per CTA so that the 64-row tile load divides evenly
-  int nwarps = max(w, 2);
-  while (SK_TR % nwarps) ++nwarps;
-  size_t smem = (((size_t)sub * w * sizeof(TS) + 15) & ~(size_t)15) +
-                (size_t)SK_STAGES * SK_TR * (w + 1) * sizeof(TA) + (size_t)SK_STAGES * SK_TR * sizeof(int);
+  const int cblocks = (n + SK_NT - 1) / SK_NT;
+  // destination rows per CTA: at most 32 (smem), fewer while that keeps ~2 CTAs per SM busy
+  int R = 32;
+  while (R > 4 && (int64_t)((maxlen + R - 1) / R) * zeta * cblocks < 2 * num_sms()) R >>= 1;
+  R = imin(R, maxlen);
+  const int bpp = (maxlen + R - 1) / R;
+  const size_t smem = (size_t)R * SK_NT * sizeof(TS) + (size_t)2 * SK_WARPS * SK_GROUPS * 32 * sizeof(int);
   if (smem > max_smem_optin()) return RLOBPCG_ERR_UNSUPPORTED;
   RL_CUDA(cudaFuncSetAttribute(sketch_kernel<TA, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  dim3 grid((n + w - 1) / w, zeta, nsub);
-  using R = RealOf<TS>;
-  const R scale = (R)(1.0 / sqrt((double)zeta));
-  sketch_kernel<TA, TS><<<grid, nwarps * 32, smem, st>>>(A, m, n, lda, d, zeta, seed, w, sub, scale, SA);
+  dim3 grid(bpp * zeta, cblocks);
+  using Rl = RealOf<TS>;
+  const Rl scale = (Rl)(1.0 / sqrt((double)zeta));
+  sketch_kernel<TA, TS><<<grid, SK_NT, smem, st>>>(A, m, n, lda, d, zeta, seed, R, bpp, scale, SA);
   RL_CHECK_LAUNCH();
   return RLOBPCG_OK;
 }
