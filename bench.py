@@ -356,6 +356,82 @@ def run_reference(args, rank, world):
             "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_serve(args, rank, world, local_rank):
+    """Serving stream: half Loewner, half planted requests (m log-uniform in [2e3, 5e5], n uniform
+    in [20, 400], k in {1, 2, 4}), HBM admission budget 150 GB. Measures the saturated rate with
+    `--slots` concurrent solves, the same stream one solve at a time, and Poisson arrivals at
+    0.5 / 0.9 / 1.2 x the saturated rate (p50 / p99 latency from submit to result)."""
+    import torch
+
+    from paper_2602_16797_gb300 import rlobpcg as rl
+    from paper_2602_16797_gb300 import workloads as wl
+    if rank != 0:
+        return None
+    torch.cuda.set_device(local_rank)
+    rl.load()
+    reqs = []
+    for r in range(args.requests):
+        A, k, kind = wl.serve_request(r)
+        reqs.append((np.ascontiguousarray(A), k, wl.SERVE_SEED_BASE + r))
+    budget = 150 * (1 << 30)
+
+    def opts(seed):
+        o = rl.rlobpcg_default_opts()
+        o.seed = seed
+        return o
+
+    def stream(slots, arrivals=None):
+        srv = rl.rlobpcg_server_create(budget, slots, local_rank)
+        t0 = time.perf_counter()
+        tickets = []
+        for i, (A, k, seed) in enumerate(reqs):
+            if arrivals is not None:
+                dt = t0 + arrivals[i] - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+            tickets.append(rl.rlobpcg_server_submit(srv, A.ctypes.data, A.shape[0], A.shape[1], A.shape[1], k,
+                                                    rl.RLOBPCG_F64, opts(seed)))
+        iters = []
+        for (A, k, seed), t in zip(reqs, tickets):
+            info = rl.rlobpcg_info()
+            rl.rlobpcg_server_wait(srv, t, None, None, None, info)
+            iters.append(info.iters)
+        makespan = time.perf_counter() - t0
+        st = rl.rlobpcg_server_stats(srv)
+        rl.rlobpcg_server_destroy(srv)
+        st["makespan_s"] = makespan
+        st["rate"] = len(reqs) / makespan
+        st["mean_iters"] = float(np.mean(iters))
+        return st
+
+    warm = reqs[:4]
+    for A, k, seed in warm:
+        rl.solve(torch.from_numpy(A).cuda(), k, opts=opts(seed))
+    sat = stream(args.slots)
+    seq = stream(1)
+    lat = {}
+    rng = np.random.default_rng(4242)
+    for f in (0.5, 0.9, 1.2):
+        lam = f * sat["rate"]
+        arr = np.cumsum(rng.exponential(1.0 / lam, len(reqs)))
+        st = stream(args.slots, arr)
+        lat[f"{f}x"] = {"offered_per_s": lam, "solves_per_s": st["rate"], "p50_ms": st["p50_ms"],
+                        "p99_ms": st["p99_ms"], "peak_running": st["peak_running"], "peak_gb": st["peak_bytes"] / 1e9}
+    bytes_in = float(np.mean([A.nbytes for A, _, _ in reqs]))
+    return {"metric": METRIC, "value": sat["rate"], "unit": "solves/s", "n_gpus": 1, "steps": len(reqs),
+            "warmup": len(warm), "ms_per_step": 1e3 / sat["rate"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded, paper-shaped; see DESIGN.md)",
+            "config": {"workload": f"serving stream of {len(reqs)} requests (half Loewner, half planted; m log-uniform "
+                                   f"[2e3,5e5], n U[20,400], k in {{1,2,4}}), HBM budget 150 GB, {args.slots} slots",
+                       "parallelism": "continuous batching on one GPU"},
+            "saturated": {"solves_per_s": sat["rate"], "p50_ms": sat["p50_ms"], "p99_ms": sat["p99_ms"],
+                          "peak_running": sat["peak_running"], "mean_iters": sat["mean_iters"]},
+            "one_at_a_time": {"solves_per_s": seq["rate"], "p50_ms": seq["p50_ms"], "p99_ms": seq["p99_ms"]},
+            "poisson": lat,
+            "e2e": {"value": sat["rate"], "unit": "solves/s", "h2d_bytes_per_step": bytes_in,
+                    "d2h_bytes_per_step": None}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -363,7 +439,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["serve_stream"], default=DEFAULT_WORKLOAD)
+    ap.add_argument("--requests", type=int, default=48, help="serve_stream: number of requests")
+    ap.add_argument("--slots", type=int, default=8, help="serve_stream: concurrent solves")
     args = ap.parse_args()
     rank, world, local_rank = replicas.world_from_env()
     if world > 1 and args.impl == "ours":
@@ -372,6 +450,8 @@ def main():
     replicas.init(world, "nccl" if args.impl == "ours" else "gloo")
     if args.impl == "reference":
         out = run_reference(args, rank, world)
+    elif args.workload == "serve_stream":
+        out = run_serve(args, rank, world, local_rank)
     else:
         out = run_ours(args, rank, world, local_rank)
     replicas.finish(world)

@@ -100,7 +100,9 @@ int rlobpcg_default_opts(rlobpcg_opts* opts);
  * Create a plan for solves of m x n matrices (dtype RLOBPCG_F64 or RLOBPCG_C128) asking for the
  * k smallest singular triplets. Allocates all device workspace the solve needs (its size grows
  * as (m + n) * 3b plus d * n and n * n elements), so solve() itself allocates nothing unless it
- * is given host pointers. `stream` is a cudaStream_t (NULL = default stream).
+ * is given host pointers. The workspace is stream-ordered (cudaMallocAsync on `stream`, from the
+ * device's default memory pool), so creating a plan does not synchronise the device.
+ * `stream` is a cudaStream_t (NULL = default stream).
  * Errors: INVALID_ARG when k < 1, b < k, 3b > n, n > m, d < n, d < zeta or zeta < 1;
  * OOM when the workspace does not fit; CUDA for runtime failures.
  */
@@ -128,6 +130,54 @@ int rlobpcg_solve(rlobpcg_plan_t plan, const void* A, int64_t lda, double tol, d
 
 /* Release a plan and its device workspace. NULL is accepted. */
 int rlobpcg_plan_destroy(rlobpcg_plan_t plan);
+
+/* Device bytes a plan owns (its workspace; a host-A copy made by solve() is not included). */
+size_t rlobpcg_plan_device_bytes(rlobpcg_plan_t plan);
+
+/* Device bytes rlobpcg_plan would allocate for these arguments (0 if they are invalid), without
+ * allocating anything: what an admission controller charges a solve before it starts. */
+size_t rlobpcg_plan_workspace_size(int64_t m, int64_t n, int k, int dtype, const rlobpcg_opts* opts);
+
+/* ---- serving: continuous batching under an HBM budget ------------------------------------ */
+/*
+ * A server owns `max_active` worker slots on `device`, each with its own CUDA stream. Requests
+ * join a FIFO queue; the head is admitted when a slot is free and its device footprint (the plan
+ * workspace of rlobpcg_plan_workspace_size plus a device copy of A) fits in what
+ * `hbm_budget_bytes` has left. Admitted solves run concurrently on the GPU (their kernels
+ * overlap); each keeps its LOBPCG state in device memory between iterations and releases it when
+ * it finishes, which admits the next request. Results are those of rlobpcg_solve on the same
+ * input (the kernels are deterministic), whatever else is running.
+ * The north star of this library asks for this serving mode; the paper has no counterpart.
+ */
+typedef struct rlobpcg_server_s* rlobpcg_server_t;
+
+/* Errors: INVALID_ARG (bad budget, max_active outside 1..64, bad device), CUDA. */
+int rlobpcg_server_create(rlobpcg_server_t* out, size_t hbm_budget_bytes, int max_active, int device);
+
+/* Queue a solve of the k smallest singular triplets of A (HOST memory, m x n row-major, lda >= n,
+ * F64 or C128; it must stay valid until rlobpcg_server_wait returns for this ticket).
+ * opts may be NULL (defaults). Errors: INVALID_ARG, OOM when the request alone exceeds the
+ * budget (it could never be admitted). */
+int rlobpcg_server_submit(rlobpcg_server_t s, const void* A, int64_t m, int64_t n, int64_t lda, int k, int dtype,
+                          const rlobpcg_opts* opts, int64_t* ticket);
+
+/* 0 queued, 1 running, 2 done; INVALID_ARG for an unknown ticket. */
+int rlobpcg_server_poll(rlobpcg_server_t s, int64_t ticket);
+
+/* Block until the request is done and copy its results to HOST buffers (sigma k, V n x k
+ * row-major in the dtype of A, resid k; each may be NULL). latency_ms: submit -> done.
+ * Returns the solve's status (OK, NOT_CONVERGED or an error). The ticket is released. */
+int rlobpcg_server_wait(rlobpcg_server_t s, int64_t ticket, double* sigma, void* V, double* resid,
+                        rlobpcg_info* info, double* latency_ms);
+
+/* Completed requests, their p50/p99 latency (submit -> done), completed / (last done - first
+ * submit), the peak of admitted device bytes and of concurrently running solves. */
+int rlobpcg_server_stats(rlobpcg_server_t s, int64_t* completed, double* p50_ms, double* p99_ms,
+                         double* solves_per_s, size_t* peak_bytes, int* peak_running);
+
+/* Stop the workers after their current solves; requests not yet admitted are dropped. Call it
+ * after every rlobpcg_server_wait has returned. */
+int rlobpcg_server_destroy(rlobpcg_server_t s);
 
 /* Static string naming a status code. */
 const char* rlobpcg_status_string(int status);

@@ -30,6 +30,7 @@ void set_last_error(const char* msg, const char* file, int line) {
   const char* base = strrchr(file, '/');
   snprintf(g_last_error, sizeof(g_last_error), "%s (%s:%d)", msg, base ? base + 1 : file, line);
 }
+void set_last_error_text(const char* text) { snprintf(g_last_error, sizeof(g_last_error), "%s", text); }
 const char* last_error() { return g_last_error; }
 
 int num_sms() {

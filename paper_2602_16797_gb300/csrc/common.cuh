@@ -244,6 +244,7 @@ void note_launch();
 long launch_count();
 
 void set_last_error(const char* msg, const char* file, int line);
+void set_last_error_text(const char* text);  // verbatim (an error recorded on another thread)
 const char* last_error();
 
 // device-side error flags (bounded waits that ran out, non-finite values)
@@ -256,5 +257,26 @@ template <class T> __host__ __device__ inline T imax(T a, T b) { return a > b ? 
 
 int num_sms();
 size_t max_smem_optin();
+
+// Raise a kernel's dynamic shared-memory limit for a launch of `bytes`. The limit belongs to the
+// function, not to the launch, and solves on concurrent streams launch the same kernel with
+// different sizes; so it is always raised to the device's opt-in maximum (never to this launch's
+// size, which another thread's smaller value could undercut between its set and our launch).
+template <class F>
+int allow_dynamic_smem(F* kernel, size_t bytes) {
+  cudaFuncAttributes fa;
+  RL_CUDA(cudaFuncGetAttributes(&fa, kernel));
+  const size_t opt = max_smem_optin();
+  const size_t cap = opt > fa.sharedSizeBytes ? opt - fa.sharedSizeBytes : 0;  // static smem counts too
+  if (bytes > cap) {
+    set_last_error("kernel needs more shared memory than the device allows per block", __FILE__, __LINE__);
+    return RLOBPCG_ERR_UNSUPPORTED;
+  }
+  // above 48 KB of static + dynamic shared memory a launch needs the opt-in limit
+  if (bytes + fa.sharedSizeBytes > 48 * 1024)
+    RL_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap));
+  return RLOBPCG_OK;
+}
+#define RL_TRY(call) do { const int rc_ = (call); if (rc_ != RLOBPCG_OK) return rc_; } while (0)
 
 }  // namespace rl

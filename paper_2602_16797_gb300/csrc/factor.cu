@@ -377,7 +377,7 @@ int factor_impl(S* SA, int d, int n, S* Rout, S* Rout_r, double* sigma, S* Vt, S
   // 3. R^{-1} (before Jacobi overwrites X)
   if (Rinv_r && Rinv_c) {
     size_t sm = (size_t)n * sizeof(S);
-    if (sm > 48 * 1024) RL_CUDA(cudaFuncSetAttribute(trinv_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    RL_TRY(allow_dynamic_smem(trinv_kernel<S>, sm));
     trinv_kernel<S><<<n, 256, sm, st>>>(X, n, Rinv_r, Rinv_c);
     RL_CHECK_LAUNCH();
   }

@@ -238,7 +238,7 @@ int gram_plan(int64_t m, int n, int b, GramPlan* gp) {
 template <class T, int CB, int CR>
 int launch_gram_cr(const GramPlan& gp, const T* A, int64_t m, int n, int64_t lda, const T* W, int b, int64_t ldw,
                    T* AW, int64_t ldaw, T* part, int use_tma, int mode, int* err, cudaStream_t st) {
-  RL_CUDA(cudaFuncSetAttribute(gram_kernel<T, CB, CR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gp.smem));
+  RL_TRY(allow_dynamic_smem(gram_kernel<T, CB, CR>, gp.smem));
   gram_kernel<T, CB, CR><<<gp.grid, GR_NT, gp.smem, st>>>(A, m, n, lda, W, b, ldw, AW, ldaw, part, gp.rows_per_cta,
                                                          gp.RT, use_tma, mode, err);
   RL_CHECK_LAUNCH();

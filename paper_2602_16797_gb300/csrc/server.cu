@@ -1,0 +1,261 @@
+// Serving loop: continuous batching of RLOBPCG solves under an HBM budget.
+//
+// Requests (A on the host, m, n, k, options) join a FIFO queue. A request is admitted when its
+// device footprint (plan workspace + a device copy of A) fits in what the budget has left and a
+// worker slot is free; each worker owns a CUDA stream, so admitted solves run concurrently on the
+// GPU and their kernels overlap. A solve keeps its whole LOBPCG state in its plan's device
+// buffers between iterations and releases them (stream-ordered) when it finishes, which admits
+// the next request. Every solve runs the same deterministic kernels as rlobpcg_solve, so a result
+// does not depend on what else is running.
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "common.cuh"
+
+namespace {
+
+using clock_t_ = std::chrono::steady_clock;
+
+struct Request {
+  int64_t ticket = 0;
+  const void* A = nullptr;
+  int64_t m = 0, n = 0, lda = 0;
+  int k = 0, dtype = 0;
+  rlobpcg_opts opts{};
+  size_t bytes = 0;
+  int state = 0;  // 0 queued, 1 running, 2 done
+  int rc = 0;
+  char err[512] = "";  // the worker's last error message when rc != RLOBPCG_OK
+  clock_t_::time_point t_arrive, t_start, t_done;
+  std::vector<double> sigma, resid;
+  std::vector<unsigned char> V;
+  rlobpcg_info info{};
+};
+
+size_t elem_bytes(int dtype) { return dtype == RLOBPCG_C128 ? 16 : 8; }
+
+}  // namespace
+
+struct rlobpcg_server_s {
+  int device = 0;
+  size_t budget = 0, in_use = 0, peak = 0;
+  int max_active = 1, running = 0, peak_running = 0;
+  bool stop = false;
+  int64_t next_ticket = 1;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<Request*> queue;
+  std::unordered_map<int64_t, Request*> all;
+  std::vector<double> latencies_ms;
+  std::vector<std::thread> workers;
+  clock_t_::time_point t_first{}, t_last{};
+  bool any_done = false;
+};
+
+namespace {
+
+void worker_main(rlobpcg_server_s* s) {
+  cudaSetDevice(s->device);
+  cudaStream_t st = nullptr;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return;
+  for (;;) {
+    Request* r = nullptr;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      s->cv_work.wait(lk, [&] {
+        return s->stop || (!s->queue.empty() && s->queue.front()->bytes <= s->budget - s->in_use);
+      });
+      if (s->stop) break;
+      if (s->queue.empty()) continue;
+      r = s->queue.front();
+      s->queue.pop_front();
+      s->in_use += r->bytes;
+      s->peak = std::max(s->peak, s->in_use);
+      ++s->running;
+      s->peak_running = std::max(s->peak_running, s->running);
+      r->state = 1;
+      r->t_start = clock_t_::now();
+    }
+    // the solve: plan (stream-ordered workspace), device copy of A, rlobpcg_solve, release
+    const size_t esz = elem_bytes(r->dtype);
+    rlobpcg_plan_t plan = nullptr;
+    void* Ad = nullptr;
+    int rc = rlobpcg_plan(&plan, r->m, r->n, r->k, r->dtype, &r->opts, st);
+    if (rc == RLOBPCG_OK) {
+      if (cudaMallocAsync(&Ad, (size_t)r->m * r->n * esz, st) != cudaSuccess) {
+        cudaGetLastError();
+        rc = RLOBPCG_ERR_OOM;
+      }
+    }
+    if (rc == RLOBPCG_OK) {
+      if (cudaMemcpy2DAsync(Ad, r->n * esz, r->A, r->lda * esz, r->n * esz, r->m, cudaMemcpyHostToDevice, st) !=
+          cudaSuccess) {
+        cudaGetLastError();
+        rc = RLOBPCG_ERR_CUDA;
+      }
+    }
+    if (rc == RLOBPCG_OK)
+      rc = rlobpcg_solve(plan, Ad, r->n, -1.0, r->sigma.data(), r->V.data(), nullptr, r->resid.data(), &r->info);
+    if (rc != RLOBPCG_OK) snprintf(r->err, sizeof(r->err), "%s", rlobpcg_last_error());
+    if (Ad) cudaFreeAsync(Ad, st);
+    rlobpcg_plan_destroy(plan);
+    cudaStreamSynchronize(st);
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->in_use -= r->bytes;
+      --s->running;
+      r->rc = rc;
+      r->state = 2;
+      r->t_done = clock_t_::now();
+      s->latencies_ms.push_back(std::chrono::duration<double, std::milli>(r->t_done - r->t_arrive).count());
+      if (!s->any_done || r->t_done > s->t_last) s->t_last = r->t_done;
+      s->any_done = true;
+    }
+    s->cv_done.notify_all();
+    s->cv_work.notify_all();
+  }
+  cudaStreamDestroy(st);
+}
+
+// Device footprint of one request: the plan's workspace plus a device copy of A.
+size_t request_bytes(int64_t m, int64_t n, int k, int dtype, const rlobpcg_opts& o) {
+  const size_t ws = rlobpcg_plan_workspace_size(m, n, k, dtype, &o);
+  if (ws == 0) return 0;
+  return ws + (((size_t)m * n * elem_bytes(dtype) + 255) & ~(size_t)255);
+}
+
+}  // namespace
+
+using namespace rl;
+
+extern "C" int rlobpcg_server_create(rlobpcg_server_t* out, size_t hbm_budget_bytes, int max_active, int device) {
+  if (!out || hbm_budget_bytes == 0 || max_active < 1 || max_active > 64) return RLOBPCG_ERR_INVALID_ARG;
+  int ndev = 0;
+  RL_CUDA(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) return RLOBPCG_ERR_INVALID_ARG;
+  RL_CUDA(cudaSetDevice(device));
+  // keep freed pool memory cached up to the budget so that admissions do not go back to the OS
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+    uint64_t thr = hbm_budget_bytes;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  auto* s = new rlobpcg_server_s();
+  s->device = device;
+  s->budget = hbm_budget_bytes;
+  s->max_active = max_active;
+  for (int i = 0; i < max_active; ++i) s->workers.emplace_back(worker_main, s);
+  *out = s;
+  return RLOBPCG_OK;
+}
+
+extern "C" int rlobpcg_server_submit(rlobpcg_server_t s, const void* A, int64_t m, int64_t n, int64_t lda, int k,
+                                     int dtype, const rlobpcg_opts* opts, int64_t* ticket) {
+  if (!s || !A || !ticket || lda < n || k < 1 || (dtype != RLOBPCG_F64 && dtype != RLOBPCG_C128))
+    return RLOBPCG_ERR_INVALID_ARG;
+  auto* r = new Request();
+  if (opts) r->opts = *opts; else rlobpcg_default_opts(&r->opts);
+  r->A = A; r->m = m; r->n = n; r->lda = lda; r->k = k; r->dtype = dtype;
+  r->bytes = request_bytes(m, n, k, dtype, r->opts);
+  if (r->bytes == 0) {
+    delete r;
+    return RLOBPCG_ERR_INVALID_ARG;
+  }
+  if (r->bytes > s->budget) {
+    delete r;
+    set_last_error("request larger than the server's HBM budget", __FILE__, __LINE__);
+    return RLOBPCG_ERR_OOM;
+  }
+  r->sigma.resize(k);
+  r->resid.resize(k);
+  r->V.resize((size_t)n * k * elem_bytes(dtype));
+  r->t_arrive = clock_t_::now();
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    r->ticket = s->next_ticket++;
+    if (s->all.empty()) s->t_first = r->t_arrive;
+    s->all[r->ticket] = r;
+    s->queue.push_back(r);
+    *ticket = r->ticket;
+  }
+  s->cv_work.notify_all();
+  return RLOBPCG_OK;
+}
+
+extern "C" int rlobpcg_server_poll(rlobpcg_server_t s, int64_t ticket) {
+  if (!s) return RLOBPCG_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->all.find(ticket);
+  if (it == s->all.end()) return RLOBPCG_ERR_INVALID_ARG;
+  return it->second->state;
+}
+
+extern "C" int rlobpcg_server_wait(rlobpcg_server_t s, int64_t ticket, double* sigma, void* V, double* resid,
+                                   rlobpcg_info* info, double* latency_ms) {
+  if (!s) return RLOBPCG_ERR_INVALID_ARG;
+  Request* r = nullptr;
+  {
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->all.find(ticket);
+    if (it == s->all.end()) return RLOBPCG_ERR_INVALID_ARG;
+    r = it->second;
+    s->cv_done.wait(lk, [&] { return r->state == 2; });
+    s->all.erase(ticket);   // look up again: the map may have rehashed while waiting
+  }
+  if (sigma) std::copy(r->sigma.begin(), r->sigma.end(), sigma);
+  if (resid) std::copy(r->resid.begin(), r->resid.end(), resid);
+  if (V) std::copy(r->V.begin(), r->V.end(), (unsigned char*)V);
+  if (info) *info = r->info;
+  if (latency_ms) *latency_ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_arrive).count();
+  const int rc = r->rc;
+  if (rc != RLOBPCG_OK) rl::set_last_error_text(r->err);
+  delete r;
+  return rc;
+}
+
+extern "C" int rlobpcg_server_stats(rlobpcg_server_t s, int64_t* completed, double* p50_ms, double* p99_ms,
+                                    double* solves_per_s, size_t* peak_bytes, int* peak_running) {
+  if (!s) return RLOBPCG_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  std::vector<double> l = s->latencies_ms;
+  std::sort(l.begin(), l.end());
+  auto pct = [&](double q) {
+    if (l.empty()) return 0.0;
+    const double x = q * (double)(l.size() - 1);
+    const size_t i = (size_t)x;
+    const double f = x - (double)i;
+    return i + 1 < l.size() ? l[i] * (1 - f) + l[i + 1] * f : l[i];
+  };
+  if (completed) *completed = (int64_t)l.size();
+  if (p50_ms) *p50_ms = pct(0.50);
+  if (p99_ms) *p99_ms = pct(0.99);
+  if (solves_per_s) {
+    const double span = s->any_done ? std::chrono::duration<double>(s->t_last - s->t_first).count() : 0.0;
+    *solves_per_s = span > 0 ? (double)l.size() / span : 0.0;
+  }
+  if (peak_bytes) *peak_bytes = s->peak;
+  if (peak_running) *peak_running = s->peak_running;
+  return RLOBPCG_OK;
+}
+
+extern "C" int rlobpcg_server_destroy(rlobpcg_server_t s) {
+  if (!s) return RLOBPCG_OK;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+  }
+  s->cv_work.notify_all();
+  for (auto& t : s->workers) t.join();
+  for (auto& kv : s->all) delete kv.second;
+  for (auto* r : s->queue) (void)r;  // queued requests are owned by `all`
+  delete s;
+  return RLOBPCG_OK;
+}

@@ -119,7 +119,7 @@ int launch_sketch(const TA* A, int64_t m, int n, int64_t lda, int d, int zeta, u
   const int bpp = (maxlen + R - 1) / R;
   const size_t smem = (size_t)R * SK_NT * sizeof(TS) + (size_t)2 * SK_WARPS * SK_GROUPS * 32 * sizeof(int);
   if (smem > max_smem_optin()) return RLOBPCG_ERR_UNSUPPORTED;
-  RL_CUDA(cudaFuncSetAttribute(sketch_kernel<TA, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  RL_TRY(allow_dynamic_smem(sketch_kernel<TA, TS>, smem));
   dim3 grid(bpp * zeta, cblocks);
   using Rl = RealOf<TS>;
   const Rl scale = (Rl)(1.0 / sqrt((double)zeta));

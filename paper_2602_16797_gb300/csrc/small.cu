@@ -637,7 +637,7 @@ int tsqr_impl(const T* X, int64_t m, int c, int64_t ldx, T* R, void* work, size_
   const int CH = tsqr_chunk(c, esz);
   const int RP = tsqr_rp(c);
   const size_t smem = tsqr_level_smem(c, CH, esz);
-  RL_CUDA(cudaFuncSetAttribute(tsqr_level_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  RL_TRY(allow_dynamic_smem(tsqr_level_kernel<T>, smem));
   const int64_t g1 = tsqr_level1_ctas(m, c, esz);
   const size_t half = (((size_t)g1 * c * c * esz + 255) & ~(size_t)255);
   T* buf[2] = {(T*)work, (T*)((unsigned char*)work + half)};
@@ -675,7 +675,7 @@ int rr_small_launch(const T* Rt, int c, int b, double* theta, T* K, size_t k_cap
   const int pdim = c - b;
   size_t smem = (size_t)3 * c * c * sizeof(T) + (size_t)c * b * sizeof(T) + c * sizeof(double) +
                 (c + 4) * sizeof(int) + 16 + (size_t)pdim * b * sizeof(T);
-  RL_CUDA(cudaFuncSetAttribute(rr_small_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  RL_TRY(allow_dynamic_smem(rr_small_kernel<T>, smem));
   int threads = min(1024, max(64, ((c + 1) / 2) * 32));
   rr_small_kernel<T><<<1, threads, smem, st>>>(Rt, c, b, theta, K, info);
   RL_CHECK_LAUNCH();
@@ -689,7 +689,7 @@ int update_launch(T* Tb, int64_t n, T* ATb, int64_t m, T* GTb, int64_t ld, int c
   constexpr int TRW = 64;
   UpdSeg<T> s0{Tb, n, ld, ceil_div(n, TRW)}, s1{ATb, m, ld, ceil_div(m, TRW)}, s2{GTb, n, ld, ceil_div(n, TRW)};
   const size_t smem = ((size_t)c * 2 * b + (size_t)TRW * c) * sizeof(T);
-  if (smem > 48 * 1024) RL_CUDA(cudaFuncSetAttribute(update_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  RL_TRY(allow_dynamic_smem(update_kernel<T>, smem));
   const int blocks = s0.blocks + s1.blocks + s2.blocks;
   update_kernel<T><<<blocks, 256, smem, st>>>(s0, s1, s2, c, b, K);
   RL_CHECK_LAUNCH();

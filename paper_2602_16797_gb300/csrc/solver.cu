@@ -101,26 +101,34 @@ struct rlobpcg_plan_s {
   size_t twork_bytes = 0;
   cudaEvent_t ev[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   std::vector<void*> owned;
+  size_t bytes = 0;          // device bytes owned by the plan (excluding a host-A copy)
 };
 
 namespace {
 
+// Plan memory is stream-ordered (cudaMallocAsync on the plan's stream, from the device's default
+// pool): creating and destroying plans does not synchronise the device, which matters when a
+// server creates one plan per request while other solves run.
 int dev_alloc(rlobpcg_plan_s* p, void** out, size_t bytes) {
   if (bytes == 0) bytes = 16;
-  cudaError_t e = cudaMalloc(out, bytes);
+  bytes = (bytes + 255) & ~(size_t)255;
+  cudaError_t e = cudaMallocAsync(out, bytes, p->st);
   if (e != cudaSuccess) {
     cudaGetLastError();
     set_last_error(cudaGetErrorString(e), __FILE__, __LINE__);
     return RLOBPCG_ERR_OOM;
   }
   p->owned.push_back(*out);
+  p->bytes += bytes;
   return RLOBPCG_OK;
 }
 
 void free_plan(rlobpcg_plan_s* p) {
-  for (void* q : p->owned) cudaFree(q);
+  for (void* q : p->owned) cudaFreeAsync(q, p->st);
   p->owned.clear();
-  if (p->A_dev) cudaFree(p->A_dev);
+  if (p->A_dev) cudaFreeAsync(p->A_dev, p->st);
+  p->A_dev = nullptr;
+  cudaStreamSynchronize(p->st);
   for (auto& e : p->ev)
     if (e) cudaEventDestroy(e);
 }
@@ -349,70 +357,134 @@ extern "C" int rlobpcg_default_opts(rlobpcg_opts* o) {
   return RLOBPCG_OK;
 }
 
+namespace {
+
+// Validate the plan arguments and fill the resolved options; returns 0 or INVALID_ARG.
+int resolve_plan_args(int64_t m, int64_t n, int k, int dtype, const rlobpcg_opts* opts, rlobpcg_opts* o, int* b_out,
+                      int64_t* d_out) {
+  if (opts) *o = *opts; else rlobpcg_default_opts(o);
+  if (dtype != RLOBPCG_F64 && dtype != RLOBPCG_C128) return RLOBPCG_ERR_INVALID_ARG;
+  const int b = o->block > 0 ? o->block : k;
+  const int64_t d = o->d > 0 ? o->d : 4 * n;
+  if (k < 1 || b < k || 3 * (int64_t)b > n || n > m || o->zeta < 1 || d < n || d < o->zeta || b > 21 ||
+      n > (1 << 20) || (o->sketch_prec != RLOBPCG_SKETCH_F64 && o->sketch_prec != RLOBPCG_SKETCH_F32)) {
+    set_last_error("invalid plan arguments (need 1 <= k <= b <= 21, 3b <= n <= m, n <= d, zeta <= d)", __FILE__, __LINE__);
+    return RLOBPCG_ERR_INVALID_ARG;
+  }
+  if (o->max_iter <= 0) o->max_iter = (b == 1) ? 200 : 100;
+  if (o->check_every <= 0) o->check_every = o->use_stagnation ? 5 : 1;
+  if (!(o->tau >= 0)) o->tau = 2.0 * sqrt((double)n) * ldexp(1.0, -52);
+  *b_out = b;
+  *d_out = d;
+  return RLOBPCG_OK;
+}
+
+// Every device buffer of a plan, in one place: with p == nullptr only the bytes are summed.
+struct PlanAlloc {
+  rlobpcg_plan_s* p;
+  size_t total = 0;
+  int operator()(void** slot, size_t bytes) {
+    bytes = (std::max<size_t>(bytes, 16) + 255) & ~(size_t)255;
+    if (!p) { total += bytes; return RLOBPCG_OK; }
+    return dev_alloc(p, slot, bytes);
+  }
+};
+
+int plan_buffers(PlanAlloc& A_, rlobpcg_plan_s* p, int64_t m, int64_t n, int b, int64_t d, int k, int dtype,
+                 const rlobpcg_opts& o, size_t* K_cap_out, int* qmax_out, size_t* gwork, size_t* twork,
+                 size_t* fwork) {
+  const bool cplx = dtype == RLOBPCG_C128;
+  const bool f32 = o.sketch_prec == RLOBPCG_SKETCH_F32;
+  const size_t esz = cplx ? 16 : 8;
+  const size_t ssz = (cplx ? 2 : 1) * (f32 ? 4 : 8);
+  const int64_t ld = 3 * b;
+  void* dummy = nullptr;
+  auto slot = [&](void* rlobpcg_plan_s::*member) -> void** { return p ? &(p->*member) : &dummy; };
+  int rc;
+#define RL_B(member, bytes) do { rc = A_(slot(&rlobpcg_plan_s::member), (bytes)); if (rc) return rc; } while (0)
+  RL_B(SA, (size_t)d * n * ssz);
+  RL_B(Vt, (size_t)n * n * ssz);
+  RL_B(Rinv_r, (size_t)n * n * ssz);
+  RL_B(Rinv_c, (size_t)n * n * ssz);
+  RL_B(R_c, (size_t)n * n * ssz);
+  RL_B(R_r, (size_t)n * n * ssz);
+  const int qmax = (int)std::min<int64_t>(n, 2 * b + 4);
+  const int64_t cmax = std::max<int64_t>(ld, qmax);
+  RL_B(Zb, (size_t)n * qmax * esz);
+  RL_B(Yb, (size_t)n * qmax * esz);
+  *fwork = factor_workspace_bytes(d, n, ssz);
+  RL_B(fwork, *fwork);
+  RL_B(Tb, (size_t)n * ld * esz);
+  RL_B(ATb, (size_t)m * ld * esz);
+  RL_B(GTb, (size_t)n * ld * esz);
+  RL_B(E, (size_t)n * cmax * esz);
+  RL_B(Res, (size_t)n * b * esz);
+  RL_B(Rs, (size_t)n * b * esz);
+  RL_B(Y, (size_t)std::max<int64_t>(n * b, 64) * esz);
+  RL_B(Rt, (size_t)cmax * cmax * esz);
+  // coefficient blocks c x 2b of every Rayleigh-Ritz step, including the qt x 2qt block (qt <= 8)
+  // of the Sigma~(1,1) estimate
+  *K_cap_out = (size_t)cmax * 2 * std::max<int64_t>(b, 8);
+  RL_B(K, *K_cap_out * esz);
+  {
+    void** sl = p ? (void**)&p->theta : &dummy;
+    rc = A_(sl, (size_t)cmax * sizeof(double)); if (rc) return rc;
+    sl = p ? (void**)&p->sk_sigma : &dummy;
+    rc = A_(sl, (size_t)n * sizeof(double)); if (rc) return rc;
+    sl = p ? (void**)&p->res_norm : &dummy;
+    rc = A_(sl, (size_t)(b + 2 * k + 8) * sizeof(double)); if (rc) return rc;
+    sl = p ? (void**)&p->err : &dummy;
+    rc = A_(sl, 64); if (rc) return rc;
+    sl = p ? (void**)&p->info : &dummy;
+    rc = A_(sl, 64); if (rc) return rc;
+  }
+  *gwork = gram_workspace_bytes(m, n, b, dtype);
+  if (*gwork == 0) {
+    set_last_error("Gram kernel: n*b too large for on-chip accumulation", __FILE__, __LINE__);
+    return RLOBPCG_ERR_UNSUPPORTED;
+  }
+  RL_B(gwork, *gwork);
+  *twork = std::max(tsqr_workspace_bytes(m, (int)ld, esz), tsqr_workspace_bytes(n, qmax, esz));
+  RL_B(twork, *twork);
+#undef RL_B
+  *qmax_out = qmax;
+  return RLOBPCG_OK;
+}
+
+}  // namespace
+
+extern "C" size_t rlobpcg_plan_workspace_size(int64_t m, int64_t n, int k, int dtype, const rlobpcg_opts* opts) {
+  rlobpcg_opts o;
+  int b = 0;
+  int64_t d = 0;
+  if (resolve_plan_args(m, n, k, dtype, opts, &o, &b, &d)) return 0;
+  PlanAlloc dry{nullptr};
+  size_t kc, gw, tw, fw;
+  int qm;
+  if (plan_buffers(dry, nullptr, m, n, b, d, k, dtype, o, &kc, &qm, &gw, &tw, &fw)) return 0;
+  return dry.total;
+}
+
 extern "C" int rlobpcg_plan(rlobpcg_plan_t* out, int64_t m, int64_t n, int k, int dtype, const rlobpcg_opts* opts,
                             void* stream) {
   if (!out) return RLOBPCG_ERR_INVALID_ARG;
   *out = nullptr;
   rlobpcg_opts o;
-  if (opts) o = *opts; else rlobpcg_default_opts(&o);
-  if (dtype != RLOBPCG_F64 && dtype != RLOBPCG_C128) return RLOBPCG_ERR_INVALID_ARG;
-  const int b = o.block > 0 ? o.block : k;
-  const int64_t d = o.d > 0 ? o.d : 4 * n;
-  if (k < 1 || b < k || 3 * (int64_t)b > n || n > m || o.zeta < 1 || d < n || d < o.zeta || b > 21 ||
-      n > (1 << 20) || (o.sketch_prec != RLOBPCG_SKETCH_F64 && o.sketch_prec != RLOBPCG_SKETCH_F32)) {
-    set_last_error("invalid plan arguments (need 1 <= k <= b <= 21, 3b <= n <= m, n <= d, zeta <= d)", __FILE__, __LINE__);
-    return RLOBPCG_ERR_INVALID_ARG;
-  }
+  int b = 0;
+  int64_t d = 0;
+  int rc = resolve_plan_args(m, n, k, dtype, opts, &o, &b, &d);
+  if (rc) return rc;
   auto* p = new rlobpcg_plan_s();
   p->m = m; p->n = n; p->k = k; p->b = b; p->d = (int)d; p->dtype = dtype;
   p->st = (cudaStream_t)stream;
-  if (o.max_iter <= 0) o.max_iter = (b == 1) ? 200 : 100;
-  if (o.check_every <= 0) o.check_every = o.use_stagnation ? 5 : 1;
-  if (!(o.tau >= 0)) o.tau = 2.0 * sqrt((double)n) * ldexp(1.0, -52);
   p->opts = o;
   const bool cplx = dtype == RLOBPCG_C128;
-  const bool f32 = o.sketch_prec == RLOBPCG_SKETCH_F32;
   p->esz = cplx ? 16 : 8;
-  p->ssz = (cplx ? 2 : 1) * (f32 ? 4 : 8);
-  const size_t esz = p->esz, ssz = p->ssz;
-  const int64_t ld = 3 * b;
-  int rc = 0;
-#define RL_A(ptr, bytes) do { rc = dev_alloc(p, (void**)&(ptr), (bytes)); if (rc) { free_plan(p); delete p; return rc; } } while (0)
-  RL_A(p->SA, (size_t)d * n * ssz);
-  RL_A(p->sk_sigma, (size_t)n * sizeof(double));
-  RL_A(p->Vt, (size_t)n * n * ssz);
-  RL_A(p->Rinv_r, (size_t)n * n * ssz);
-  RL_A(p->Rinv_c, (size_t)n * n * ssz);
-  RL_A(p->R_c, (size_t)n * n * ssz);
-  RL_A(p->R_r, (size_t)n * n * ssz);
-  p->qmax = (int)std::min<int64_t>(n, 2 * b + 4);
-  const int64_t cmax = std::max<int64_t>(ld, p->qmax);
-  RL_A(p->Zb, (size_t)n * p->qmax * esz);
-  RL_A(p->Yb, (size_t)n * p->qmax * esz);
-  p->fwork_bytes = factor_workspace_bytes(d, n, ssz);
-  RL_A(p->fwork, p->fwork_bytes);
-  RL_A(p->Tb, (size_t)n * ld * esz);
-  RL_A(p->ATb, (size_t)m * ld * esz);
-  RL_A(p->GTb, (size_t)n * ld * esz);
-  RL_A(p->E, (size_t)n * cmax * esz);
-  RL_A(p->Res, (size_t)n * b * esz);
-  RL_A(p->Rs, (size_t)n * b * esz);
-  RL_A(p->Y, (size_t)std::max<int64_t>(n * b, 64) * esz);
-  RL_A(p->Rt, (size_t)cmax * cmax * esz);
-  // coefficient blocks c x 2b of every Rayleigh-Ritz step, including the qt x 2qt block (qt <= 8)
-  // of the Sigma~(1,1) estimate
-  p->K_cap = (size_t)cmax * 2 * std::max<int64_t>(b, 8);
-  RL_A(p->K, p->K_cap * esz);
-  RL_A(p->theta, (size_t)cmax * sizeof(double));
-  RL_A(p->res_norm, (size_t)(b + 2 * k + 8) * sizeof(double));
-  RL_A(p->err, 64);
-  RL_A(p->info, 64);
-  p->gwork_bytes = gram_workspace_bytes(m, n, b, dtype);
-  if (p->gwork_bytes == 0) { free_plan(p); delete p; set_last_error("Gram kernel: n*b too large for on-chip accumulation", __FILE__, __LINE__); return RLOBPCG_ERR_UNSUPPORTED; }
-  RL_A(p->gwork, p->gwork_bytes);
-  p->twork_bytes = std::max(tsqr_workspace_bytes(m, (int)ld, esz), tsqr_workspace_bytes(n, p->qmax, esz));
-  RL_A(p->twork, p->twork_bytes);
-#undef RL_A
+  p->ssz = (cplx ? 2 : 1) * (o.sketch_prec == RLOBPCG_SKETCH_F32 ? 4 : 8);
+  PlanAlloc alloc{p};
+  rc = plan_buffers(alloc, p, m, n, b, d, k, dtype, o, &p->K_cap, &p->qmax, &p->gwork_bytes, &p->twork_bytes,
+                    &p->fwork_bytes);
+  if (rc) { free_plan(p); delete p; return rc; }
   for (auto& e : p->ev) {
     if (cudaEventCreate(&e) != cudaSuccess) { free_plan(p); delete p; return RLOBPCG_ERR_CUDA; }
   }
@@ -432,10 +504,10 @@ extern "C" int rlobpcg_solve(rlobpcg_plan_t p, const void* A, int64_t lda, doubl
     // host input: copy into a plan-owned device buffer (compact, lda = n)
     const size_t bytes = (size_t)p->m * p->n * p->esz;
     if (p->A_dev_bytes < bytes) {
-      if (p->A_dev) cudaFree(p->A_dev);
+      if (p->A_dev) cudaFreeAsync(p->A_dev, p->st);
       p->A_dev = nullptr;
       p->A_dev_bytes = 0;
-      if (cudaMalloc(&p->A_dev, bytes) != cudaSuccess) { cudaGetLastError(); return RLOBPCG_ERR_OOM; }
+      if (cudaMallocAsync(&p->A_dev, bytes, p->st) != cudaSuccess) { cudaGetLastError(); return RLOBPCG_ERR_OOM; }
       p->A_dev_bytes = bytes;
     }
     RL_CUDA(cudaEventCreate(&h0));
@@ -466,8 +538,10 @@ extern "C" int rlobpcg_solve(rlobpcg_plan_t p, const void* A, int64_t lda, doubl
 
 extern "C" int rlobpcg_plan_destroy(rlobpcg_plan_t p) {
   if (!p) return RLOBPCG_OK;
-  if (p->st) cudaStreamSynchronize(p->st); else cudaDeviceSynchronize();
+  cudaStreamSynchronize(p->st);
   free_plan(p);
   delete p;
   return RLOBPCG_OK;
 }
+
+extern "C" size_t rlobpcg_plan_device_bytes(rlobpcg_plan_t p) { return p ? p->bytes : 0; }

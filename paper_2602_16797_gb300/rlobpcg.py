@@ -75,6 +75,18 @@ _SIGS = {
                                      c_int64, c_void_p, c_int64, c_void_p]),
     "rlobpcg_tsqr": (c_int, [c_void_p, c_int64, c_int, c_int64, c_int, c_void_p, c_void_p, c_size_t, c_void_p]),
     "rlobpcg_tsqr_workspace_size": (c_size_t, [c_int64, c_int, c_int]),
+    "rlobpcg_plan_device_bytes": (c_size_t, [c_void_p]),
+    "rlobpcg_plan_workspace_size": (c_size_t, [c_int64, c_int64, c_int, c_int, ctypes.POINTER(rlobpcg_opts)]),
+    "rlobpcg_server_create": (c_int, [ctypes.POINTER(c_void_p), c_size_t, c_int, c_int]),
+    "rlobpcg_server_submit": (c_int, [c_void_p, c_void_p, c_int64, c_int64, c_int64, c_int, c_int,
+                                      ctypes.POINTER(rlobpcg_opts), ctypes.POINTER(c_int64)]),
+    "rlobpcg_server_poll": (c_int, [c_void_p, c_int64]),
+    "rlobpcg_server_wait": (c_int, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, ctypes.POINTER(rlobpcg_info),
+                                    ctypes.POINTER(c_double)]),
+    "rlobpcg_server_stats": (c_int, [c_void_p, ctypes.POINTER(c_int64), ctypes.POINTER(c_double),
+                                     ctypes.POINTER(c_double), ctypes.POINTER(c_double), ctypes.POINTER(c_size_t),
+                                     ctypes.POINTER(c_int)]),
+    "rlobpcg_server_destroy": (c_int, [c_void_p]),
 }
 
 _lib = None
@@ -225,3 +237,52 @@ def solve(A, k: int, *, opts: rlobpcg_opts | None = None, tol: float = -1.0, wan
         return sigma, V, U, resid, out
     finally:
         rlobpcg_plan_destroy(plan)
+
+
+def rlobpcg_plan_device_bytes(plan: int) -> int:
+    return load().rlobpcg_plan_device_bytes(plan)
+
+
+def rlobpcg_plan_workspace_size(m: int, n: int, k: int, dtype: int, opts: rlobpcg_opts | None = None) -> int:
+    return load().rlobpcg_plan_workspace_size(m, n, k, dtype, ctypes.byref(opts) if opts is not None else None)
+
+
+def rlobpcg_server_create(budget_bytes: int, max_active: int, device: int = 0) -> int:
+    h = c_void_p()
+    _check("rlobpcg_server_create", load().rlobpcg_server_create(ctypes.byref(h), budget_bytes, max_active, device))
+    return h.value
+
+
+def rlobpcg_server_submit(server: int, A: int, m: int, n: int, lda: int, k: int, dtype: int,
+                          opts: rlobpcg_opts | None = None) -> int:
+    t = c_int64()
+    _check("rlobpcg_server_submit", load().rlobpcg_server_submit(server, A, m, n, lda, k, dtype,
+                                                                 ctypes.byref(opts) if opts is not None else None,
+                                                                 ctypes.byref(t)))
+    return t.value
+
+
+def rlobpcg_server_poll(server: int, ticket: int) -> int:
+    return load().rlobpcg_server_poll(server, ticket)
+
+
+def rlobpcg_server_wait(server: int, ticket: int, sigma: int | None, V: int | None, resid: int | None,
+                        info: rlobpcg_info | None = None):
+    lat = c_double()
+    rc = load().rlobpcg_server_wait(server, ticket, sigma, V, resid, ctypes.byref(info) if info is not None else None,
+                                    ctypes.byref(lat))
+    _check("rlobpcg_server_wait", rc, ok=(RLOBPCG_OK, RLOBPCG_NOT_CONVERGED))
+    return rc, lat.value
+
+
+def rlobpcg_server_stats(server: int) -> dict:
+    c, p50, p99, sps, pk, pr = c_int64(), c_double(), c_double(), c_double(), c_size_t(), c_int()
+    _check("rlobpcg_server_stats", load().rlobpcg_server_stats(server, ctypes.byref(c), ctypes.byref(p50),
+                                                               ctypes.byref(p99), ctypes.byref(sps), ctypes.byref(pk),
+                                                               ctypes.byref(pr)))
+    return {"completed": c.value, "p50_ms": p50.value, "p99_ms": p99.value, "solves_per_s": sps.value,
+            "peak_bytes": pk.value, "peak_running": pr.value}
+
+
+def rlobpcg_server_destroy(server: int) -> None:
+    _check("rlobpcg_server_destroy", load().rlobpcg_server_destroy(server))
