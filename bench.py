@@ -177,6 +177,14 @@ def oracle_solves_per_s(w, n_solves, warmup=0):
     return (ms / w["m"]) / per, times
 
 
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
 def cpu_cores():
     return os.cpu_count() or 1
 
@@ -200,6 +208,46 @@ def gram_traffic_per_element():
         return per if tag == h else None
     except (OSError, ValueError):
         return None
+
+
+def split_traffic_per_launch(m, n, k):
+    """DRAM bytes per launch of the two split-Gram kernels (A W and A^T (A W)) from the committed ncu
+    summary, scaled to (m, n) by the digit bytes, if that summary was taken on the current
+    gram_tc.cu (else None)."""
+    path = os.path.join(ROOT, "profiles", "gram_split_ncu_summary.md")
+    src = os.path.join(ROOT, "paper_2602_16797_gb300", "csrc", "gram_tc.cu")
+    try:
+        txt = open(path).read()
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        tag, per = None, {}
+        for ln in txt.splitlines():
+            if ln.startswith("gram_tc.cu sha256[:16]: "):
+                tag = ln.split(": ", 1)[1].strip()
+            for key in ("ab", "atb"):
+                pre = f"dram bytes per digit byte ({key}): "
+                if ln.startswith(pre):
+                    per[key] = float(ln.split(": ", 1)[1].split()[0])
+        if tag != h or len(per) != 2:
+            return None
+        alg = split_algorithmic_bytes(m, n, k)
+        return {key: per[key] * alg[key + "_digits"] for key in ("ab", "atb")}
+    except (OSError, ValueError):
+        return None
+
+
+def split_algorithmic_bytes(m, n, b):
+    """Bytes each split-Gram kernel must move per launch (layouts of gram_tc.cu): the digits of A
+    (8 bf16 digits per element of the padded matrix: 16 bytes), plus A W (FP64) and the digits of
+    A W (8 x 8 or 8 x 16 bf16 per row) written by the first, read by the second once per 128-column
+    tile."""
+    cd = lambda a, q: -(-a // q)  # noqa: E731
+    R1, NKB, CT = cd(m, 128), cd(n, 16), cd(n, 128)
+    N = 8 * (8 if b <= 8 else 16)
+    ab_digits = R1 * NKB * 8 * 4096
+    atb_digits = CT * R1 * 8 * 8 * 4096
+    y_digits = R1 * 128 * N * 2
+    return {"ab_digits": ab_digits, "atb_digits": atb_digits,
+            "ab": ab_digits + 8 * m * b + y_digits, "atb": atb_digits + CT * y_digits}
 
 
 def run_ours(args, rank, world, local_rank):
@@ -226,6 +274,8 @@ def run_ours(args, rank, world, local_rank):
     o.d = D
     o.zeta = w["zeta"]
     o.sketch_prec = w["prec"]
+    o.gram_split = 1 if args.gram == "split" else 0
+    split = args.gram == "split" and not w["cplx"] and K <= 16
     if "stagnation" in w:
         o.use_stagnation = w["stagnation"]
     if "tau" in w:
@@ -293,14 +343,37 @@ def run_ours(args, rank, world, local_rank):
     sm_count = props.multi_processor_count
     max_mhz = clk.get("sm_max_mhz") or 2070.0
     peak_tf = sm_count * FP64_UNITS_PER_SM_CLK * 2 * max_mhz * 1e6 / 1e12
-    per_elem = gram_traffic_per_element() if args.workload == DEFAULT_WORKLOAD else None
-    roofline = {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
-                "frac": (achieved_tf / peak_tf) if achieved_tf else None,
-                "traffic": (per_elem * M * N) if per_elem is not None else None,
-                "kernel": "gram_kernel (fused A W, A^H A W), " + ("complex128" if w["cplx"] else "FP64"),
-                "peak_source": f"derived: {sm_count} SMs x {FP64_UNITS_PER_SM_CLK} DFMA/clk x 2 flop x {max_mhz:.0f} MHz",
-                "achieved_gbs": bytes_pass / avg_s / 1e9 if passes else None,
-                "passes_timed": passes}
+    if split:
+        # split-bf16 Gram: two HBM-bound tensor-core kernels per pass; the roofline is that of the
+        # slower one (bytes it must move per launch / its event-timed duration) against the measured
+        # copy bandwidth
+        alg = split_algorithmic_bytes(M, N, K)
+        t_ab = sum(x.ms_gram_ab for x in infos) / max(passes, 1) * 1e-3
+        t_atb = sum(x.ms_gram_atb for x in infos) / max(passes, 1) * 1e-3
+        key, t_k = ("atb", t_atb) if t_atb >= t_ab else ("ab", t_ab)
+        peaks = measured_peaks()
+        peak_gbs = peaks.get("hbm_gbs") or 6800.0
+        achieved_gbs = alg[key] / t_k / 1e9 if passes else None
+        tr = split_traffic_per_launch(M, N, K)
+        roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": peak_gbs, "unit": "GB/s",
+                    "frac": (achieved_gbs / peak_gbs) if achieved_gbs else None,
+                    "traffic": tr[key] if tr else None,
+                    "kernel": ("split_pass_kernel<8,1> (A^T (A W) from bf16 digits, tcgen05)" if key == "atb" else
+                               "split_pass_kernel<8,0> (A W from bf16 digits, tcgen05)"),
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks.get("hbm_gbs") else
+                                   "fallback 6.8 TB/s",
+                    "bytes_per_launch": alg[key], "ms_per_launch": t_k * 1e3,
+                    "other_kernel_ms": (t_ab if key == "atb" else t_atb) * 1e3,
+                    "gram_pass_fp64_equiv_tflops": achieved_tf, "passes_timed": passes}
+    else:
+        per_elem = gram_traffic_per_element() if args.workload == DEFAULT_WORKLOAD else None
+        roofline = {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
+                    "frac": (achieved_tf / peak_tf) if achieved_tf else None,
+                    "traffic": (per_elem * M * N) if per_elem is not None else None,
+                    "kernel": "gram_kernel (fused A W, A^H A W), " + ("complex128" if w["cplx"] else "FP64"),
+                    "peak_source": f"derived: {sm_count} SMs x {FP64_UNITS_PER_SM_CLK} DFMA/clk x 2 flop x {max_mhz:.0f} MHz",
+                    "achieved_gbs": bytes_pass / avg_s / 1e9 if passes else None,
+                    "passes_timed": passes}
 
     out = None
     if rank == 0:
@@ -310,9 +383,11 @@ def run_ours(args, rank, world, local_rank):
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "c128" if w["cplx"] else "f64",
-            "data": "synthetic (seeded, paper-shaped; see DESIGN.md)",
+            "data": "synthetic (seeded; the paper's matrix families)",
             "config": {"workload": w["desc"], "m": M, "n": N, "k": K, "d": D, "zeta": w["zeta"],
                        "sketch": "fp32" if w["prec"] else "fp64", "matrices": w["matrices"],
+                       "gram": "split-bf16 tensor cores" if split else ("fp64 CUDA cores" if not w["cplx"]
+                                                                         else "complex128 CUDA cores"),
                        "l2": "input larger than L2; no flush" if M * N * esz > 129e6 else
                              "input smaller than L2 (each step is a full solve)",
                        "parallelism": f"replicas x{world}"},
@@ -321,7 +396,8 @@ def run_ours(args, rank, world, local_rank):
             "phase_ms": {"sketch": statistics.mean(x.ms_sketch for x in infos),
                          "factor": statistics.mean(x.ms_factor for x in infos),
                          "iterate": statistics.mean(x.ms_iterate for x in infos),
-                         "gram_per_pass": avg_s * 1e3},
+                         "gram_per_pass": avg_s * 1e3,
+                         "split_a": statistics.mean(x.ms_split_a for x in infos)},
             "sigma": [float(x) for x in sigma.cpu().numpy()],
             "roofline": roofline, "clocks": clk,
             "gpu_launches": int(sum(x.kernel_launches for x in infos)),
@@ -347,7 +423,7 @@ def run_reference(args, rank, world):
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "c128" if w["cplx"] else "f64", "data": "synthetic (seeded, paper-shaped; see DESIGN.md)",
+            "dtype": "c128" if w["cplx"] else "f64", "data": "synthetic (seeded; the paper's matrix families)",
             "config": {"workload": w["desc"], "m": w["m"], "n": w["n"], "k": w["k"], "d": w["d"], "zeta": w["zeta"],
                        "parallelism": "cpu oracle, rank 0 only"},
             "cpu_baseline": {"value": v, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
@@ -420,7 +496,7 @@ def run_serve(args, rank, world, local_rank):
     bytes_in = float(np.mean([A.nbytes for A, _, _ in reqs]))
     return {"metric": METRIC, "value": sat["rate"], "unit": "solves/s", "n_gpus": 1, "steps": len(reqs),
             "warmup": len(warm), "ms_per_step": 1e3 / sat["rate"], "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded, paper-shaped; see DESIGN.md)",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded; the paper's matrix families)",
             "config": {"workload": f"serving stream of {len(reqs)} requests (half Loewner, half planted; m log-uniform "
                                    f"[2e3,5e5], n U[20,400], k in {{1,2,4}}), HBM budget 150 GB, {args.slots} slots",
                        "parallelism": "continuous batching on one GPU"},
@@ -440,6 +516,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["serve_stream"], default=DEFAULT_WORKLOAD)
+    ap.add_argument("--gram", choices=["split", "fp64"], default="split",
+                    help="Gram products: split-bf16 on the tensor cores (default) or FP64 CUDA cores")
     ap.add_argument("--requests", type=int, default=48, help="serve_stream: number of requests")
     ap.add_argument("--slots", type=int, default=8, help="serve_stream: concurrent solves")
     args = ap.parse_args()

@@ -71,6 +71,11 @@ typedef struct {
                            (R^H R)^{-1} (3 steps, block 2b+4) + Rayleigh-Ritz on R Z, and a block
                            power iteration for Sigma~(1,1) (8 steps, block 8: about 1% low on a
                            clustered top spectrum; it only scales the stop tolerance)           */
+  int gram_split;       /* 1 (default): run the Gram products on the tensor cores by an exact split
+                           of A, W and A W into bf16 digits (rlobpcg_gram_split; about FP64
+                           accuracy). Real FP64 and b <= 16 only (ignored otherwise); A is split
+                           once per solve into about 32 bytes of device memory per element of A.
+                           0: the FP64 CUDA-core Gram pass (rlobpcg_gram).                    */
   double tau;           /* tolerance of ||R(:,j)|| <= Sigma~(1,1)^2 tau; < 0 means 2 sqrt(n) 2^-52 */
 } rlobpcg_opts;
 
@@ -89,6 +94,9 @@ typedef struct {
   int gram_passes;      /* number of Gram passes in ms_gram                                         */
   int kernel_launches;  /* CUDA kernels this solve launched                                         */
   int jacobi_sweeps;    /* sweeps of the one-sided Jacobi SVD of R                                  */
+  double ms_gram_ab;    /* split Gram plans: device time of the A W kernels (W split + first product) */
+  double ms_gram_atb;   /* split Gram plans: device time of the A^T (A W) kernels (+ partial sums)     */
+  double ms_split_a;    /* split Gram plans: device time of splitting A into digits (once per solve)   */
 } rlobpcg_info;
 
 typedef struct rlobpcg_plan_s* rlobpcg_plan_t;
@@ -252,6 +260,32 @@ size_t rlobpcg_gram_workspace_size(int64_t m, int64_t n, int b, int dtype);
  */
 int rlobpcg_gram_noalloc(const void* A, int64_t m, int64_t n, int64_t lda, int dtype, const void* W, int b,
                          int64_t ldw, void* AW, int64_t ldaw, void* G, int64_t ldg, void* stream);
+
+/*
+ * Split-bf16 Gram pass on the tensor cores (real FP64). The paper forms these products in FP64;
+ * this is an addition of this library with the same results up to FP64-level rounding: the same
+ * AW = A W (m x b) and G = A^T AW (n x b) as rlobpcg_gram, with every operand split exactly into
+ * eight signed 7-bit digits (exact in bf16) under a power-of-two scale per group -- a row of A for
+ * A W, a column of A within each 128-row chunk for A^T AW, a column of W, a column of AW within
+ * each chunk (the Ozaki scheme). Digit products accumulate exactly (as integers below 2^24) in the
+ * tensor cores' f32 accumulators and are recombined in FP64. Per product term the error is about
+ * 2^-55 times the product of the two group maxima.
+ *   rlobpcg_gram_split_prepare: split A (m x n, row-major, lda) once -- it is constant through a
+ *     solve -- into prep, rlobpcg_gram_split_prepare_size(m, n) bytes of device memory (about 32
+ *     bytes per element of A).
+ *   rlobpcg_gram_split: one pass; W (n x b, ldw), AW (m x b, ldaw), G (n x b, ldg) row-major,
+ *     1 <= b <= 16; work: rlobpcg_gram_split_workspace_size(m, n, b) bytes of device scratch.
+ * All pointers are device memory owned by the caller; calls are asynchronous on `stream` and
+ * synchronise it before returning. Errors: INVALID_ARG (sizes, NULL, buffers too small),
+ * UNSUPPORTED (n above 1,048,560), NONFINITE (W holds Inf or NaN), TIMEOUT (a bounded device wait
+ * ran out), CUDA.
+ */
+size_t rlobpcg_gram_split_prepare_size(int64_t m, int64_t n);
+int rlobpcg_gram_split_prepare(const double* A, int64_t m, int64_t n, int64_t lda, void* prep, size_t prep_bytes,
+                               void* stream);
+size_t rlobpcg_gram_split_workspace_size(int64_t m, int64_t n, int b);
+int rlobpcg_gram_split(const void* prep, int64_t m, int64_t n, const double* W, int b, int64_t ldw, double* AW,
+                       int64_t ldaw, double* G, int64_t ldg, void* work, size_t work_bytes, void* stream);
 
 /*
  * R factor of a tall block (the TSQR used for Rayleigh-Ritz by SVD of A_T, Alg. 2): X is m x c

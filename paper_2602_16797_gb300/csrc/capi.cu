@@ -17,6 +17,12 @@ int gram_dispatch(const void* A, int64_t m, int64_t n, int64_t lda, int dtype, c
                   void* AW, int64_t ldaw, void* G, int64_t ldg, void* work, size_t work_bytes, int resid_mode,
                   int* err, cudaStream_t st);
 size_t tsqr_workspace_bytes(int64_t m, int c, size_t esz);
+size_t split_prep_bytes(int64_t m, int64_t n);
+size_t split_work_bytes(int64_t m, int64_t n, int b);
+int split_prepare(const double* A, int64_t m, int64_t n, int64_t lda, void* prep, size_t prep_bytes, cudaStream_t st);
+int split_gram(const void* prep, int64_t m, int64_t n, const double* W, int b, int64_t ldw, double* AW, int64_t ldaw,
+               double* G, int64_t ldg, void* work, size_t work_bytes, int resid_mode, int* err, cudaEvent_t mid,
+               cudaStream_t st);
 template <class T>
 int tsqr_impl(const T* X, int64_t m, int c, int64_t ldx, T* R, void* work, size_t work_bytes, cudaStream_t st);
 
@@ -77,6 +83,7 @@ static int finish(cudaStream_t st, int* err) {
   if (err) RL_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
   RL_CUDA(cudaStreamSynchronize(st));
   if (herr & DEV_ERR_TIMEOUT) return RLOBPCG_ERR_TIMEOUT;
+  if (herr & DEV_ERR_NONFINITE) return RLOBPCG_ERR_NONFINITE;
   return RLOBPCG_OK;
 }
 
@@ -164,6 +171,30 @@ extern "C" int rlobpcg_gram(const void* A, int64_t m, int64_t n, int64_t lda, in
   int* err = step_err_word(st);
   if (!err) return RLOBPCG_ERR_OOM;
   int rc = gram_dispatch(A, m, n, lda, dtype, W, b, ldw, AW, ldaw, G, ldg, work, work_bytes, 0, err, st);
+  if (rc) return rc;
+  return finish(st, err);
+}
+
+extern "C" size_t rlobpcg_gram_split_prepare_size(int64_t m, int64_t n) { return split_prep_bytes(m, n); }
+
+extern "C" int rlobpcg_gram_split_prepare(const double* A, int64_t m, int64_t n, int64_t lda, void* prep,
+                                          size_t prep_bytes, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  const int rc = split_prepare(A, m, n, lda, prep, prep_bytes, st);
+  if (rc) return rc;
+  return finish(st, nullptr);
+}
+
+extern "C" size_t rlobpcg_gram_split_workspace_size(int64_t m, int64_t n, int b) { return split_work_bytes(m, n, b); }
+
+extern "C" int rlobpcg_gram_split(const void* prep, int64_t m, int64_t n, const double* W, int b, int64_t ldw,
+                                  double* AW, int64_t ldaw, double* G, int64_t ldg, void* work, size_t work_bytes,
+                                  void* stream) {
+  if (!W) return RLOBPCG_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  int* err = step_err_word(st);
+  if (!err) return RLOBPCG_ERR_OOM;
+  const int rc = split_gram(prep, m, n, W, b, ldw, AW, ldaw, G, ldg, work, work_bytes, 0, err, nullptr, st);
   if (rc) return rc;
   return finish(st, err);
 }

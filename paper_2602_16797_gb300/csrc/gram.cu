@@ -1,5 +1,6 @@
-// Fused Gram pass: the one product with A per LOBPCG iteration (Alg. 2 of arXiv 2602.16797,
-// "only W is multiplied"), extended so that the same read of A also gives A^H (A W):
+// Fused Gram pass: the one product with A per LOBPCG iteration (Alg. 2 of arXiv 2602.16797 keeps
+// A V and A X from earlier products and multiplies only the new block W), extended so that the
+// same read of A also gives A^H (A W):
 //     AW = A W            (m x b)     -- the new columns of A_T
 //     G  = A^H AW         (n x b)     -- keeps G_T = A^H A T current, so the residual
 //                                        A^H A_V - V Theta^2 needs no second pass over A.

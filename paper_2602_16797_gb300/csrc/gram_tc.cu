@@ -1,0 +1,684 @@
+// Split-bf16 Gram pass on the 5th-generation tensor cores: the products of the Gram pass of
+// Alg. 2 (arXiv 2602.16797; per iteration only the new block W is multiplied by A), real FP64,
+//     AW = A W      (m x b)   and   G = A^T AW   (n x b),
+// computed as an error-free split of every FP64 operand into bf16 digits (the Ozaki scheme:
+// Ozaki, Ogita, Oishi, Rump, "Error-free transformations of matrix multiplication by using fast
+// routines of matrix multiplication", Numer. Algorithms 59, 2012; on tensor cores: Mukunoki,
+// Ozaki, Ogita, Imamura, "DGEMM using Tensor Cores, and Its Accurate and Reproducible Versions",
+// ISC 2020).
+//
+// Split. A group of FP64 values (a row of A for the first product, a column of A within a
+// 128-row chunk for the second, a column of W, a column of AW within a 128-row chunk) shares one
+// exponent E with max |x| < 2^E. Each x becomes V = rint(x 2^(55-E)) (|V| <= 2^55) and V is
+// written in balanced base 128, most significant digit first:
+//     x ~= 2^(E+1) sum_{p=0}^{7} d_p 2^(-7(p+1)),   d_p integers in [-64, 64],
+// with |error| <= 2^(E-56). A digit is exact in bf16 and a digit product (|.| <= 2^12) is exact.
+//
+// Products. For a digit pair (p, q) the tensor core forms sum_k a_p[k] b_q[k] in f32. Pairs of
+// the same level l = p + q share one accumulator: the MMA for A-digit p writes its N = 8 x BP
+// output columns (B-digits q = 0..7, BP columns each) at TMEM column offset BP * p, so pair
+// (p, q) lands on columns BP * l + j. A level holds at most 8 pairs, so with at most 512 terms
+// per accumulation |L_l| <= 8 * 512 * 2^12 = 2^24 and the f32 accumulator is exact (integers).
+// The result is then
+//     2^(E+F-12) sum_{l=0}^{14} 2^(-7 l) L_l,
+// evaluated by Horner's rule: levels 14..5 in f32 (their weight is below 2^-35 of level 0, so
+// f32 rounding there stays below 2^-59 of the leading term) and levels 4..0 in FP64. The error
+// is that of the digit truncation, about 2^-55 of the group maxima per term, which is the size
+// of an FP64 dot product's own rounding. Tensor cores do the O(m n b) work; FP64 does O((m+n) b).
+//
+// Layouts (bf16 digits, no-swizzle K-major core-matrix order of tc.cuh, 4 KB per 128 x 16
+// digit tile): A_rt[r][kb][p] -- row tile r (128 rows), column block kb (16 columns), digit p --
+// for the first product; A_ct[ct][rc][kb][p] -- column tile ct (128 columns) as the M side,
+// row chunk rc (128 rows = 8 blocks of 16) as the K side -- for the second. Every pipeline stage
+// is then one contiguous 32 KB bulk copy of A digits plus the matching B digits. A is constant
+// through a solve, so it is split once per solve; W and AW are split once per pass.
+//
+// Kernel shape: one CTA per SM, 192 threads: warp 0 issues the bulk copies (5-stage ring of
+// mbarriers), warp 1 owns TMEM and issues the MMAs from one thread, warps 2-5 read the
+// accumulators (two TMEM buffers, so reading one unit overlaps the MMAs of the next), zero them,
+// and do the FP64 recombination. Every wait is bounded and reports DEV_ERR_TIMEOUT.
+#include "common.cuh"
+#include "tc.cuh"
+
+namespace rl {
+
+namespace {
+
+constexpr int SL = 8;                  // digits per FP64 value
+constexpr int TM = 128;                // MMA M: rows (first product) or columns (second) per tile
+constexpr int TK = 16;                 // MMA K and pipeline stage depth
+constexpr int KC_KB = 32;              // k-blocks per exact accumulation: 32 x 16 = 512 terms
+constexpr int CH_KB = TM / TK;         // k-blocks per 128-row chunk of the second product
+constexpr int NST = 5;                 // pipeline stages
+constexpr int SLICE_BYTES = TM * TK * 2;
+constexpr int NTH = 192;
+
+__host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+inline size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Dims {
+  int64_t R1, NKB, CT, NC;
+};
+Dims dims_of(int64_t m, int64_t n) { return {cdiv(m, TM), cdiv(n, TK), cdiv(n, TM), cdiv(n, TM) * TM}; }
+
+struct PrepLayout {
+  size_t art, act, erow, ecol, total;
+};
+PrepLayout prep_layout(int64_t m, int64_t n) {
+  const Dims d = dims_of(m, n);
+  PrepLayout L;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { const size_t o = off; off += a256(bytes); return o; };
+  L.art = take((size_t)d.R1 * d.NKB * SL * SLICE_BYTES);
+  L.act = take((size_t)d.CT * d.R1 * CH_KB * SL * SLICE_BYTES);
+  L.erow = take((size_t)d.R1 * TM * sizeof(int));
+  L.ecol = take((size_t)d.R1 * d.NC * sizeof(int));
+  L.total = off;
+  return L;
+}
+
+struct WorkLayout {
+  int BP, NR;
+  size_t wsl, f, ysl, h, part, total;
+};
+WorkLayout work_layout(int64_t m, int64_t n, int b) {
+  const Dims d = dims_of(m, n);
+  WorkLayout L;
+  L.BP = b <= 8 ? 8 : 16;
+  const int N = SL * L.BP;
+  L.NR = (int)std::max<int64_t>(1, std::min<int64_t>(d.R1, num_sms() / std::max<int64_t>(1, d.CT)));
+  size_t off = 0;
+  auto take = [&](size_t bytes) { const size_t o = off; off += a256(bytes); return o; };
+  L.wsl = take((size_t)d.NKB * N * TK * 2);
+  L.f = take(64 * sizeof(int));
+  L.ysl = take((size_t)d.R1 * CH_KB * N * TK * 2);
+  L.h = take((size_t)d.R1 * L.BP * sizeof(int));
+  L.part = take((size_t)L.NR * d.NC * L.BP * sizeof(double));
+  L.total = off;
+  return L;
+}
+
+// ---- digits --------------------------------------------------------------------------------------
+__device__ __forceinline__ int group_exp(double amax) {
+  int e = 0;
+  frexp(amax, &e);   // amax = f 2^e with f in [0.5, 1), so every |x| <= amax is < 2^e
+  return amax > 0 ? e : 0;
+}
+
+__device__ __forceinline__ void split8(double x, int E, int (&d)[SL]) {
+  long long V = __double2ll_rn(scalbn(x, 55 - E));
+#pragma unroll
+  for (int p = SL - 1; p > 0; --p) {
+    const int r = (int)(V & 127);
+    const int dd = r - ((r & 64) << 1);   // balanced remainder in [-64, 63]
+    d[p] = dd;
+    V = (V - dd) >> 7;                    // exact: V - dd is a multiple of 128
+  }
+  d[0] = (int)V;                          // |V| <= 64 here since |V| <= 2^55 at the start
+}
+
+__device__ __forceinline__ uint16_t bf16_of(int v) { return (uint16_t)(__float_as_uint((float)v) >> 16); }
+
+// element (row, kk) of an R-row x 16 digit tile in core-matrix order
+__device__ __forceinline__ int core_off(int row, int kk, int R) {
+  return (kk >> 3) * (R * 8) + (row >> 3) * 64 + (row & 7) * 8 + (kk & 7);
+}
+// inverse for R = 128: position o -> (row, kk), so that consecutive threads write consecutive digits
+__device__ __forceinline__ void core_pos128(int o, int& row, int& kk) {
+  kk = ((o >> 10) << 3) | (o & 7);
+  row = (((o & 1023) >> 6) << 3) | ((o & 63) >> 3);
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// ---- one-time split of A ---------------------------------------------------------------------------
+__global__ void row_exp_kernel(const double* __restrict__ A, int64_t m, int n, int64_t lda, int64_t mpad,
+                               int* __restrict__ erow) {
+  const int64_t i = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (i >= mpad) return;
+  double mx = 0;
+  if (i < m)
+    for (int k = lane; k < n; k += 32) mx = fmax(mx, fabs(A[i * lda + k]));
+  mx = warp_max(mx);
+  if (lane == 0) erow[i] = group_exp(mx);
+}
+
+__global__ void __launch_bounds__(256) rt_digits_kernel(const double* __restrict__ A, int64_t m, int n, int64_t lda,
+                                                        const int* __restrict__ erow, int64_t NKB,
+                                                        uint16_t* __restrict__ Art) {
+  const int64_t r = blockIdx.x, kb = blockIdx.y;
+  uint16_t* out = Art + (size_t)((r * NKB + kb) * SL) * (TM * TK);
+  for (int o = threadIdx.x; o < TM * TK; o += 256) {
+    int row, kk;
+    core_pos128(o, row, kk);
+    const int64_t i = r * TM + row, k = kb * TK + kk;
+    double x = 0;
+    int E = 0;
+    if (i < m) {
+      E = erow[i];
+      if (k < n) x = A[i * lda + k];
+    }
+    int d[SL];
+    split8(x, E, d);
+#pragma unroll
+    for (int p = 0; p < SL; ++p) out[p * (TM * TK) + o] = bf16_of(d[p]);
+  }
+}
+
+__global__ void col_exp_kernel(const double* __restrict__ A, int64_t m, int n, int64_t lda, int64_t NC,
+                               int* __restrict__ ecol) {
+  const int64_t rc = blockIdx.x;
+  const int64_t c = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
+  if (c >= NC) return;
+  double mx = 0;
+  if (c < n) {
+    const int64_t i1 = min(m, rc * TM + TM);
+    for (int64_t i = rc * TM; i < i1; ++i) mx = fmax(mx, fabs(A[i * lda + c]));
+  }
+  ecol[rc * NC + c] = group_exp(mx);
+}
+
+__global__ void __launch_bounds__(256) ct_digits_kernel(const double* __restrict__ A, int64_t m, int n, int64_t lda,
+                                                        const int* __restrict__ ecol, int64_t NC, int64_t R1,
+                                                        uint16_t* __restrict__ Act) {
+  __shared__ double tile[TK][TM + 1];
+  const int64_t rc = blockIdx.x / CH_KB;
+  const int kb = (int)(blockIdx.x % CH_KB);
+  const int64_t ct = blockIdx.y;
+  const int64_t i0 = rc * TM + kb * TK, c0 = ct * TM;
+  for (int e = threadIdx.x; e < TK * TM; e += 256) {
+    const int rr = e >> 7, cc = e & 127;
+    const int64_t i = i0 + rr, c = c0 + cc;
+    tile[rr][cc] = (i < m && c < n) ? A[i * lda + c] : 0.0;
+  }
+  __syncthreads();
+  uint16_t* out = Act + (size_t)(((ct * R1 + rc) * CH_KB + kb) * SL) * (TM * TK);
+  for (int o = threadIdx.x; o < TM * TK; o += 256) {
+    int cc, kk;
+    core_pos128(o, cc, kk);   // M index = column, K index = row within the block
+    int d[SL];
+    split8(tile[kk][cc], ecol[rc * NC + c0 + cc], d);
+#pragma unroll
+    for (int p = 0; p < SL; ++p) out[p * (TM * TK) + o] = bf16_of(d[p]);
+  }
+}
+
+// ---- per-pass split of W (one CTA) ---------------------------------------------------------------
+template <int BP>
+__global__ void __launch_bounds__(512) w_digits_kernel(const double* __restrict__ W, int n, int b, int64_t ldw,
+                                                       int64_t NKB, uint16_t* __restrict__ Wsl, int* __restrict__ F,
+                                                       int* err) {
+  constexpr int N = SL * BP;
+  __shared__ double red[16][BP];
+  __shared__ int Fs[BP];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double mx[BP];
+  bool bad = false;
+#pragma unroll
+  for (int j = 0; j < BP; ++j) mx[j] = 0;
+  for (int k = threadIdx.x; k < n; k += 512)
+#pragma unroll
+    for (int j = 0; j < BP; ++j)
+      if (j < b) {
+        const double a = fabs(W[(int64_t)k * ldw + j]);
+        bad |= !(a <= 1.7976931348623157e308);
+        mx[j] = fmax(mx[j], a);
+      }
+#pragma unroll
+  for (int j = 0; j < BP; ++j) {
+    const double v = warp_max(mx[j]);
+    if (lane == 0) red[warp][j] = v;
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(err, DEV_ERR_NONFINITE);
+  if (threadIdx.x < BP) {
+    double v = 0;
+    for (int w = 0; w < 16; ++w) v = fmax(v, red[w][threadIdx.x]);
+    Fs[threadIdx.x] = group_exp(v);
+    F[threadIdx.x] = Fs[threadIdx.x];
+  }
+  __syncthreads();
+  const int64_t total = NKB * TK * BP;
+  for (int64_t e = threadIdx.x; e < total; e += 512) {
+    const int j = (int)(e % BP);
+    const int64_t k = e / BP;
+    const double x = (k < n && j < b) ? W[k * ldw + j] : 0.0;
+    int d[SL];
+    split8(x, Fs[j], d);
+    uint16_t* out = Wsl + (size_t)(k / TK) * (N * TK);
+    const int kk = (int)(k % TK);
+#pragma unroll
+    for (int q = 0; q < SL; ++q) out[core_off(q * BP + j, kk, N)] = bf16_of(d[q]);
+  }
+}
+
+// Digits of one 128-row chunk of Y = AW (B operand of the second product): the chunk's column
+// maxima set H_j, then row `row` writes its digits. `bar` synchronises the 128 threads of the chunk.
+template <int BP, class Bar>
+__device__ __forceinline__ void emit_y_digits(const double (&y)[BP], int b, int row, int lane, int quarter,
+                                              double* red, int64_t rc, uint16_t* __restrict__ Ysl,
+                                              int* __restrict__ H, Bar bar) {
+  constexpr int N = SL * BP;
+#pragma unroll
+  for (int j = 0; j < BP; ++j) {
+    const double v = warp_max(j < b ? fabs(y[j]) : 0.0);
+    if (lane == 0) red[quarter * BP + j] = v;
+  }
+  bar();
+  int Hj[BP];
+#pragma unroll
+  for (int j = 0; j < BP; ++j)
+    Hj[j] = group_exp(fmax(fmax(red[j], red[BP + j]), fmax(red[2 * BP + j], red[3 * BP + j])));
+  if (row == 0)
+#pragma unroll
+    for (int j = 0; j < BP; ++j) H[rc * BP + j] = j < b ? Hj[j] : 0;
+  uint16_t* out = Ysl + (size_t)(rc * CH_KB + (row >> 4)) * (N * TK);
+  const int kk = row & 15;
+#pragma unroll
+  for (int j = 0; j < BP; ++j) {
+    int d[SL];
+    split8(j < b ? y[j] : 0.0, Hj[j], d);
+#pragma unroll
+    for (int q = 0; q < SL; ++q) out[core_off(q * BP + j, kk, N)] = bf16_of(d[q]);
+  }
+}
+
+// Y given (the residual refresh: G = A^T A_V for a stored A_V): one CTA of 128 threads per chunk
+template <int BP>
+__global__ void __launch_bounds__(128) y_digits_kernel(const double* __restrict__ Y, int64_t m, int b, int64_t ldy,
+                                                       uint16_t* __restrict__ Ysl, int* __restrict__ H, int* err) {
+  __shared__ double red[4 * BP];
+  const int64_t rc = blockIdx.x;
+  const int row = threadIdx.x;
+  const int64_t i = rc * TM + row;
+  double y[BP];
+  bool bad = false;
+#pragma unroll
+  for (int j = 0; j < BP; ++j) {
+    y[j] = (i < m && j < b) ? Y[i * ldy + j] : 0.0;
+    bad |= !(fabs(y[j]) <= 1.7976931348623157e308);
+  }
+  if (bad) atomicOr(err, DEV_ERR_NONFINITE);
+  emit_y_digits<BP>(y, b, row, row & 31, row >> 5, red, rc, Ysl, H, [] { __syncthreads(); });
+}
+
+// ---- the tensor-core pass ---------------------------------------------------------------------
+struct PassArgs {
+  const uint16_t* Aop;   // A_rt (first product) or A_ct (second)
+  const uint16_t* Bop;   // W digits or AW digits
+  const int* eA;         // row exponents of A, or column exponents per chunk
+  const int* eB;         // W column exponents, or AW column exponents per chunk
+  int64_t m, R1, NKB, CT, NC;
+  int b, NR;
+  double* AW;            // first product: output (m x b, ldaw)
+  int64_t ldaw;
+  uint16_t* Ysl;         // first product: digits of AW for the second product (or null)
+  int* H;
+  double* part;          // second product: partials [NR][NC][BP]
+  int* err;
+};
+
+// Bounded wait by the four epilogue warps; the outcome is made uniform over all 128 threads, so
+// that they either all go on (and meet every later named barrier) or all stop.
+__device__ __forceinline__ bool epi_wait(uint64_t* bar, uint32_t parity) {
+  return tc::named_bar_and<2>(128, tc::mbar_wait(bar, parity));
+}
+
+template <int BP>
+__device__ __forceinline__ void ld_level8(uint32_t taddr, uint32_t (&r)[BP], int h) {
+  tc::tmem_ld8(taddr, r[h], r[h + 1], r[h + 2], r[h + 3], r[h + 4], r[h + 5], r[h + 6], r[h + 7]);
+}
+
+// Reads one accumulator buffer (levels 0..14 of BP columns), zeroes it for reuse, releases it,
+// and returns s_j = sum_l 2^(-7 l) L_l[j].
+template <int BP>
+__device__ __forceinline__ void drain_levels(uint32_t ta, uint64_t* release, int b, double (&s)[BP]) {
+  float t[BP];
+  uint32_t r[5][BP];
+  // levels 14..10
+#pragma unroll
+  for (int l = 0; l < 5; ++l)
+#pragma unroll
+    for (int h = 0; h < BP; h += 8) ld_level8(ta + BP * (14 - l) + h, r[l], h);
+  tc::tmem_ld_wait();
+#pragma unroll
+  for (int j = 0; j < BP; ++j) {
+    t[j] = __uint_as_float(r[0][j]);
+#pragma unroll
+    for (int l = 1; l < 5; ++l) t[j] = fmaf(t[j], 0x1p-7f, __uint_as_float(r[l][j]));
+  }
+  // levels 9..5
+#pragma unroll
+  for (int l = 0; l < 5; ++l)
+#pragma unroll
+    for (int h = 0; h < BP; h += 8) ld_level8(ta + BP * (9 - l) + h, r[l], h);
+  tc::tmem_ld_wait();
+#pragma unroll
+  for (int j = 0; j < BP; ++j)
+#pragma unroll
+    for (int l = 0; l < 5; ++l) t[j] = fmaf(t[j], 0x1p-7f, __uint_as_float(r[l][j]));
+  // levels 4..0
+#pragma unroll
+  for (int l = 0; l < 5; ++l)
+#pragma unroll
+    for (int h = 0; h < BP; h += 8) ld_level8(ta + BP * (4 - l) + h, r[l], h);
+  tc::tmem_ld_wait();
+  // the buffer is free again once it is zero
+  constexpr uint32_t ACCW = BP == 8 ? 128 : 256;
+#pragma unroll
+  for (uint32_t c = 0; c < ACCW; c += 8) tc::tmem_st8_zero(ta + c);
+  tc::tmem_st_wait();
+  tc::fence_before_sync();
+  tc::mbar_arrive(release);
+#pragma unroll
+  for (int j = 0; j < BP; ++j) {
+    if (j < b) {
+      double v = (double)t[j];
+#pragma unroll
+      for (int l = 0; l < 5; ++l) v = fma(v, 0x1p-7, (double)__uint_as_float(r[l][j]));
+      s[j] = v;
+    } else {
+      s[j] = 0;
+    }
+  }
+}
+
+// MODE 0: AW = A W (+ digits of AW). MODE 1: partial G = A^T AW over each CTA's row chunks.
+template <int BP, int MODE>
+__global__ void __launch_bounds__(NTH, 1) split_pass_kernel(PassArgs g) {
+  constexpr int N = SL * BP;
+  constexpr uint32_t ACCW = BP == 8 ? 128 : 256;
+  constexpr uint32_t BBYTES = N * TK * 2;
+  constexpr uint32_t ABYTES = SL * SLICE_BYTES;
+  constexpr uint32_t STG = ABYTES + BBYTES;
+  constexpr uint32_t IDESC = tc::idesc_bf16_f32(TM, N);
+  extern __shared__ __align__(1024) unsigned char sm[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + NST * STG);
+  uint64_t* empty = full + NST;
+  uint64_t* accf = empty + NST;
+  uint64_t* acce = accf + 2;
+  uint64_t* done = acce + 2;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+  double* red = reinterpret_cast<double*>(sm + NST * STG + 256);   // [2][4][BP]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NST; ++s) {
+      tc::mbar_init(full + s, 1);
+      tc::mbar_init(empty + s, 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      tc::mbar_init(accf + a, 1);
+      tc::mbar_init(acce + a, 128);
+    }
+    tc::mbar_init(done, 1);
+    tc::fence_mbar_init();
+  }
+  if (warp == 1) tc::tmem_alloc(tslot, 2 * ACCW);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tslot;
+
+  // work of this CTA: MODE 0 -- row tiles r = blockIdx.x (+ gridDim.x ...), each ceil(NKB / 32)
+  // units of up to 32 k-blocks; MODE 1 -- column tile ct and row chunks [rc0, rc1), one unit each
+  const int64_t ct = MODE == 1 ? blockIdx.x % g.CT : 0;
+  const int64_t rng = MODE == 1 ? blockIdx.x / g.CT : 0;
+  const int64_t rc0 = MODE == 1 ? rng * g.R1 / g.NR : 0;
+  const int64_t rc1 = MODE == 1 ? (rng + 1) * g.R1 / g.NR : 0;
+  const int64_t NKC = cdiv(g.NKB, KC_KB);
+
+  if (warp == 0) {
+    if (lane == 0) {
+      uint32_t u = 0;
+      bool ok = true;
+      auto load = [&](const uint16_t* srcA, const uint16_t* srcB) {
+        const int s = (int)(u % NST);
+        if (!tc::mbar_wait(empty + s, ((u / NST) & 1) ^ 1)) return false;
+        unsigned char* stg = sm + (size_t)s * STG;
+        tc::mbar_expect_tx(full + s, STG);
+        tc::bulk_g2s(stg, srcA, ABYTES, full + s);
+        tc::bulk_g2s(stg + ABYTES, srcB, BBYTES, full + s);
+        ++u;
+        return true;
+      };
+      if (MODE == 0) {
+        for (int64_t r = blockIdx.x; ok && r < g.R1; r += gridDim.x)
+          for (int64_t kb = 0; ok && kb < g.NKB; ++kb)
+            ok = load(g.Aop + (size_t)((r * g.NKB + kb) * SL) * (TM * TK), g.Bop + (size_t)kb * (N * TK));
+      } else {
+        for (int64_t rc = rc0; ok && rc < rc1; ++rc)
+          for (int kb = 0; ok && kb < CH_KB; ++kb)
+            ok = load(g.Aop + (size_t)(((ct * g.R1 + rc) * CH_KB + kb) * SL) * (TM * TK),
+                      g.Bop + (size_t)(rc * CH_KB + kb) * (N * TK));
+      }
+      if (!ok) atomicOr(g.err, DEV_ERR_TIMEOUT);
+      // copies into the last NST stages have landed before the CTA may finish
+      for (uint32_t w = u > (uint32_t)NST ? u - NST : 0; w < u; ++w) tc::mbar_wait(full + (w % NST), (w / NST) & 1);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      uint32_t u = 0, v = 0;
+      bool ok = true;
+      auto unit = [&](int nkb) {
+        const int a = (int)(v & 1);
+        if (!tc::mbar_wait(acce + a, (v >> 1) & 1)) return false;
+        tc::fence_after_sync();
+        const uint32_t dbase = tmem + (uint32_t)a * ACCW;
+        for (int kb = 0; kb < nkb; ++kb) {
+          const int s = (int)(u % NST);
+          if (!tc::mbar_wait(full + s, (u / NST) & 1)) return false;
+          tc::fence_after_sync();
+          unsigned char* stg = sm + (size_t)s * STG;
+          const uint64_t bdesc = tc::smem_desc(stg + ABYTES, (N / 8) * 128, 128);
+#pragma unroll
+          for (int p = 0; p < SL; ++p)
+            tc::mma_bf16(dbase + (uint32_t)(BP * p), tc::smem_desc(stg + p * SLICE_BYTES, 2048, 128), bdesc, IDESC, 1u);
+          tc::mma_commit(empty + s);
+          ++u;
+        }
+        tc::mma_commit(accf + a);
+        ++v;
+        return true;
+      };
+      if (MODE == 0) {
+        for (int64_t r = blockIdx.x; ok && r < g.R1; r += gridDim.x)
+          for (int64_t kc = 0; ok && kc < NKC; ++kc) ok = unit((int)std::min<int64_t>(KC_KB, g.NKB - kc * KC_KB));
+      } else {
+        for (int64_t rc = rc0; ok && rc < rc1; ++rc) ok = unit(CH_KB);
+      }
+      if (!ok) atomicOr(g.err, DEV_ERR_TIMEOUT);
+      // every MMA issued here has finished before TMEM is released
+      tc::mma_commit(done);
+      tc::mbar_wait(done, 0);
+    }
+  } else {
+    const int quarter = warp & 3;                 // TMEM lanes 32 * quarter .. + 31
+    const int row = 32 * quarter + lane;          // MODE 0: row of the tile; MODE 1: column
+    const uint32_t tq = tmem + ((uint32_t)(32 * quarter) << 16);
+#pragma unroll
+    for (uint32_t c = 0; c < 2 * ACCW; c += 8) tc::tmem_st8_zero(tq + c);
+    tc::tmem_st_wait();
+    tc::fence_before_sync();
+    tc::mbar_arrive(acce + 0);
+    tc::mbar_arrive(acce + 1);
+    uint32_t v = 0;
+    bool ok = true;
+    if (MODE == 0) {
+      int Fj[BP];
+#pragma unroll
+      for (int j = 0; j < BP; ++j) Fj[j] = g.eB[j];
+      int t = 0;
+      for (int64_t r = blockIdx.x; ok && r < g.R1; r += gridDim.x, ++t) {
+        const int64_t i = r * TM + row;
+        const int Ei = g.eA[i];
+        double y[BP];
+#pragma unroll
+        for (int j = 0; j < BP; ++j) y[j] = 0;
+        for (int64_t kc = 0; kc < NKC; ++kc) {
+          const int a = (int)(v & 1);
+          ok = epi_wait(accf + a, (v >> 1) & 1);
+          if (!ok) break;
+          tc::fence_after_sync();
+          double s[BP];
+          drain_levels<BP>(tq + (uint32_t)a * ACCW, acce + a, g.b, s);
+          ++v;
+#pragma unroll
+          for (int j = 0; j < BP; ++j)
+            if (j < g.b) y[j] += scalbn(s[j], Ei + Fj[j] - 12);
+        }
+        if (!ok) break;
+        if (i < g.m)
+#pragma unroll
+          for (int j = 0; j < BP; ++j)
+            if (j < g.b) g.AW[i * g.ldaw + j] = y[j];
+        if (g.Ysl)
+          emit_y_digits<BP>(y, g.b, row, lane, quarter, red + (t & 1) * 4 * BP, r, g.Ysl, g.H,
+                            [] { tc::named_bar<1>(128); });
+      }
+    } else {
+      const int64_t c = ct * TM + row;
+      double acc[BP];
+#pragma unroll
+      for (int j = 0; j < BP; ++j) acc[j] = 0;
+      for (int64_t rc = rc0; ok && rc < rc1; ++rc) {
+        const int a = (int)(v & 1);
+        ok = epi_wait(accf + a, (v >> 1) & 1);
+        if (!ok) break;
+        tc::fence_after_sync();
+        double s[BP];
+        drain_levels<BP>(tq + (uint32_t)a * ACCW, acce + a, g.b, s);
+        ++v;
+        const int Ec = g.eA[rc * g.NC + c];
+#pragma unroll
+        for (int j = 0; j < BP; ++j)
+          if (j < g.b) acc[j] += scalbn(s[j], Ec + g.eB[rc * BP + j] - 12);
+      }
+      double* out = g.part + (size_t)(rng * g.NC + c) * BP;
+#pragma unroll
+      for (int j = 0; j < BP; ++j) out[j] = (ok && j < g.b) ? acc[j] : 0.0;
+    }
+    if (!ok) atomicOr(g.err, DEV_ERR_TIMEOUT);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 1) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, 2 * ACCW);
+  }
+}
+
+__global__ void split_reduce_kernel(const double* __restrict__ part, int NR, int64_t NC, int BP, int64_t n, int b,
+                                    double* __restrict__ G, int64_t ldg) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * b) return;
+  const int64_t k = e / b;
+  const int j = (int)(e % b);
+  double s = 0;
+  for (int r = 0; r < NR; ++r) s += part[((int64_t)r * NC + k) * BP + j];   // fixed order
+  G[k * ldg + j] = s;
+}
+
+template <int BP, int MODE>
+int launch_pass(const PassArgs& a, int grid, cudaStream_t st) {
+  constexpr uint32_t STG = SL * SLICE_BYTES + SL * BP * TK * 2;
+  const size_t smem = (size_t)NST * STG + 256 + 2 * 4 * BP * sizeof(double);
+  RL_TRY(allow_dynamic_smem(split_pass_kernel<BP, MODE>, smem));
+  split_pass_kernel<BP, MODE><<<grid, NTH, smem, st>>>(a);
+  RL_CHECK_LAUNCH();
+  return RLOBPCG_OK;
+}
+
+template <int BP>
+int split_gram_bp(const unsigned char* prep, int64_t m, int64_t n, const double* W, int b, int64_t ldw, double* AW,
+                  int64_t ldaw, double* G, int64_t ldg, unsigned char* work, int resid_mode, int* err,
+                  cudaEvent_t mid, cudaStream_t st) {
+  const Dims d = dims_of(m, n);
+  const PrepLayout P = prep_layout(m, n);
+  const WorkLayout L = work_layout(m, n, b);
+  uint16_t* Ysl = (uint16_t*)(work + L.ysl);
+  int* H = (int*)(work + L.h);
+  if (!resid_mode) {
+    w_digits_kernel<BP><<<1, 512, 0, st>>>(W, (int)n, b, ldw, d.NKB, (uint16_t*)(work + L.wsl), (int*)(work + L.f), err);
+    RL_CHECK_LAUNCH();
+    PassArgs a{};
+    a.Aop = (const uint16_t*)(prep + P.art);
+    a.Bop = (const uint16_t*)(work + L.wsl);
+    a.eA = (const int*)(prep + P.erow);
+    a.eB = (const int*)(work + L.f);
+    a.m = m; a.R1 = d.R1; a.NKB = d.NKB; a.CT = d.CT; a.NC = d.NC;
+    a.b = b; a.NR = L.NR;
+    a.AW = AW; a.ldaw = ldaw; a.Ysl = Ysl; a.H = H; a.err = err;
+    RL_TRY((launch_pass<BP, 0>(a, (int)std::min<int64_t>(d.R1, num_sms()), st)));
+  } else {
+    y_digits_kernel<BP><<<(unsigned)d.R1, 128, 0, st>>>(AW, m, b, ldaw, Ysl, H, err);
+    RL_CHECK_LAUNCH();
+  }
+  if (mid) RL_CUDA(cudaEventRecord(mid, st));
+  PassArgs a{};
+  a.Aop = (const uint16_t*)(prep + P.act);
+  a.Bop = Ysl;
+  a.eA = (const int*)(prep + P.ecol);
+  a.eB = H;
+  a.m = m; a.R1 = d.R1; a.NKB = d.NKB; a.CT = d.CT; a.NC = d.NC;
+  a.b = b; a.NR = L.NR;
+  a.part = (double*)(work + L.part);
+  a.err = err;
+  RL_TRY((launch_pass<BP, 1>(a, (int)(d.CT * L.NR), st)));
+  const int64_t tot = n * b;
+  split_reduce_kernel<<<(unsigned)cdiv(tot, 256), 256, 0, st>>>((const double*)(work + L.part), L.NR, d.NC, BP, n, b,
+                                                                 G, ldg);
+  RL_CHECK_LAUNCH();
+  return RLOBPCG_OK;
+}
+
+}  // namespace
+
+size_t split_prep_bytes(int64_t m, int64_t n) { return (m < 1 || n < 1) ? 0 : prep_layout(m, n).total; }
+
+size_t split_work_bytes(int64_t m, int64_t n, int b) {
+  return (m < 1 || n < 1 || b < 1 || b > 16) ? 0 : work_layout(m, n, b).total;
+}
+
+int split_prepare(const double* A, int64_t m, int64_t n, int64_t lda, void* prep, size_t prep_bytes, cudaStream_t st) {
+  if (!A || !prep || m < 1 || n < 1 || lda < n) return RLOBPCG_ERR_INVALID_ARG;
+  const PrepLayout P = prep_layout(m, n);
+  if (prep_bytes < P.total) return RLOBPCG_ERR_INVALID_ARG;
+  const Dims d = dims_of(m, n);
+  if (d.NKB > 65535 || cdiv(d.NC, 256) > 65535) return RLOBPCG_ERR_UNSUPPORTED;
+  unsigned char* base = (unsigned char*)prep;
+  int* erow = (int*)(base + P.erow);
+  int* ecol = (int*)(base + P.ecol);
+  const int64_t mpad = d.R1 * TM;
+  row_exp_kernel<<<(unsigned)cdiv(mpad, 8), 256, 0, st>>>(A, m, (int)n, lda, mpad, erow);
+  RL_CHECK_LAUNCH();
+  rt_digits_kernel<<<dim3((unsigned)d.R1, (unsigned)d.NKB), 256, 0, st>>>(A, m, (int)n, lda, erow, d.NKB,
+                                                                         (uint16_t*)(base + P.art));
+  RL_CHECK_LAUNCH();
+  col_exp_kernel<<<dim3((unsigned)d.R1, (unsigned)cdiv(d.NC, 256)), 256, 0, st>>>(A, m, (int)n, lda, d.NC, ecol);
+  RL_CHECK_LAUNCH();
+  ct_digits_kernel<<<dim3((unsigned)(d.R1 * CH_KB), (unsigned)d.CT), 256, 0, st>>>(A, m, (int)n, lda, ecol, d.NC, d.R1,
+                                                                                  (uint16_t*)(base + P.act));
+  RL_CHECK_LAUNCH();
+  return RLOBPCG_OK;
+}
+
+int split_gram(const void* prep, int64_t m, int64_t n, const double* W, int b, int64_t ldw, double* AW, int64_t ldaw,
+               double* G, int64_t ldg, void* work, size_t work_bytes, int resid_mode, int* err, cudaEvent_t mid,
+               cudaStream_t st) {
+  if (!prep || !AW || !G || !work || m < 1 || n < 1 || b < 1 || b > 16 || ldaw < b || ldg < b ||
+      (!resid_mode && (!W || ldw < b)))
+    return RLOBPCG_ERR_INVALID_ARG;
+  if (work_bytes < split_work_bytes(m, n, b)) return RLOBPCG_ERR_INVALID_ARG;
+  if (b <= 8)
+    return split_gram_bp<8>((const unsigned char*)prep, m, n, W, b, ldw, AW, ldaw, G, ldg, (unsigned char*)work,
+                            resid_mode, err, mid, st);
+  return split_gram_bp<16>((const unsigned char*)prep, m, n, W, b, ldw, AW, ldaw, G, ldg, (unsigned char*)work,
+                           resid_mode, err, mid, st);
+}
+
+}  // namespace rl

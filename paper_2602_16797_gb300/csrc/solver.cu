@@ -33,6 +33,12 @@ size_t gram_workspace_bytes(int64_t m, int64_t n, int b, int dtype);
 int gram_dispatch(const void* A, int64_t m, int64_t n, int64_t lda, int dtype, const void* W, int b, int64_t ldw,
                   void* AW, int64_t ldaw, void* G, int64_t ldg, void* work, size_t work_bytes, int resid_mode,
                   int* err, cudaStream_t st);
+size_t split_prep_bytes(int64_t m, int64_t n);
+size_t split_work_bytes(int64_t m, int64_t n, int b);
+int split_prepare(const double* A, int64_t m, int64_t n, int64_t lda, void* prep, size_t prep_bytes, cudaStream_t st);
+int split_gram(const void* prep, int64_t m, int64_t n, const double* W, int b, int64_t ldw, double* AW, int64_t ldaw,
+               double* G, int64_t ldg, void* work, size_t work_bytes, int resid_mode, int* err, cudaEvent_t mid,
+               cudaStream_t st);
 size_t tsqr_workspace_bytes(int64_t m, int c, size_t esz);
 template <class T>
 int tsqr_impl(const T* X, int64_t m, int c, int64_t ldx, T* R, void* work, size_t work_bytes, cudaStream_t st);
@@ -97,9 +103,14 @@ struct rlobpcg_plan_s {
   int* info = nullptr;
   void* gwork = nullptr;
   size_t gwork_bytes = 0;
+  bool split = false;       // Gram products on the tensor cores (split-bf16)
+  void* sprep = nullptr;    // digits of A (split once per solve)
+  size_t sprep_bytes = 0;
+  void* swork = nullptr;
+  size_t swork_bytes = 0;
   void* twork = nullptr;
   size_t twork_bytes = 0;
-  cudaEvent_t ev[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev[10] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   std::vector<void*> owned;
   size_t bytes = 0;          // device bytes owned by the plan (excluding a host-A copy)
 };
@@ -163,6 +174,19 @@ struct StopRule {
   }
 };
 
+// One Gram pass: AW = A W and G = A^H AW (resid_mode: G = A^H AW for the given AW), on the FP64
+// CUDA cores or, for plans with gram_split, on the tensor cores from the digits of A.
+template <class T>
+int gram_pass(rlobpcg_plan_s* p, const T* A, int64_t lda, const T* W, T* AW, T* G, int resid_mode,
+              cudaEvent_t mid = nullptr) {
+  const int64_t ld = 3 * p->b;
+  if (p->split)
+    return split_gram(p->sprep, p->m, p->n, (const double*)W, p->b, ld, (double*)AW, ld, (double*)G, ld, p->swork,
+                      p->swork_bytes, resid_mode, p->err, mid, p->st);
+  return gram_dispatch(A, p->m, p->n, lda, p->dtype, W, p->b, ld, AW, ld, G, ld, p->gwork, p->gwork_bytes, resid_mode,
+                       p->err, p->st);
+}
+
 template <class T, class S>
 int solve_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, double tau, double* sigma, T* Vout, T* Uout,
                double* resid, rlobpcg_info* info) {
@@ -173,10 +197,8 @@ int solve_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, double tau, double* s
   T* Tb = (T*)p->Tb;
   T* ATb = (T*)p->ATb;
   T* GTb = (T*)p->GTb;
-  int rc;
-#define RL_TRY(x) do { rc = (x); if (rc) return rc; } while (0)
   const long launches0 = launch_count();
-  double gram_ms = 0;
+  double gram_ms = 0, gram_ab_ms = 0, gram_atb_ms = 0;
   int gram_passes = 0;
   RL_CUDA(cudaMemsetAsync(p->err, 0, sizeof(int), st));
   RL_CUDA(cudaEventRecord(p->ev[0], st));
@@ -231,7 +253,12 @@ int solve_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, double tau, double* s
 
   // Sketch-and-solve start and initial Rayleigh-Ritz (Alg. 2, lines 4-7)
   RL_TRY(bcgs2_orth_launch<T>(Tb, n, b, ld, 0, 0, (T*)p->E, 0, st));
-  RL_TRY(gram_dispatch(A, m, n, lda, p->dtype, Tb, b, ld, ATb, ld, GTb, ld, p->gwork, p->gwork_bytes, 0, p->err, st));
+  if (p->split) {
+    RL_CUDA(cudaEventRecord(p->ev[8], st));
+    RL_TRY(split_prepare((const double*)A, m, n, lda, p->sprep, p->sprep_bytes, st));
+    RL_CUDA(cudaEventRecord(p->ev[9], st));
+  }
+  RL_TRY(gram_pass<T>(p, A, lda, Tb, ATb, GTb, 0));
   RL_TRY(tsqr_impl<T>(ATb, m, b, ld, (T*)p->Rt, p->twork, p->twork_bytes, st));
   RL_TRY(rr_small_launch<T>((const T*)p->Rt, b, b, p->theta, (T*)p->K, p->K_cap, p->info, st));
   RL_TRY(update_launch<T>(Tb, n, ATb, m, GTb, ld, b, b, (const T*)p->K, st));
@@ -259,8 +286,7 @@ int solve_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, double tau, double* s
     RL_TRY(bcgs2_orth_launch<T>(Tb, n, b, ld, b, nx, (T*)p->E, 2, st));
     // A W and A^H (A W) in one pass over A (timed with events on this stream)
     RL_CUDA(cudaEventRecord(p->ev[5], st));
-    RL_TRY(gram_dispatch(A, m, n, lda, p->dtype, Tb + b, b, ld, ATb + b, ld, GTb + b, ld, p->gwork, p->gwork_bytes, 0,
-                         p->err, st));
+    RL_TRY(gram_pass<T>(p, A, lda, Tb + b, ATb + b, GTb + b, 0, p->split ? p->ev[7] : nullptr));
     RL_CUDA(cudaEventRecord(p->ev[6], st));
     matvecs += b;
     // Rayleigh-Ritz by SVD of A_T (TSQR + Jacobi of R_T)
@@ -270,8 +296,7 @@ int solve_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, double tau, double* s
     theta_s = p->theta + (c - b);
     RL_TRY(update_launch<T>(Tb, n, ATb, m, GTb, ld, c, b, (const T*)p->K, st));
     if (refresh > 0 && (i + 1) % refresh == 0) {
-      RL_TRY(gram_dispatch(A, m, n, lda, p->dtype, nullptr, b, ld, ATb, ld, GTb, ld, p->gwork, p->gwork_bytes, 1,
-                           p->err, st));
+      RL_TRY(gram_pass<T>(p, A, lda, nullptr, ATb, GTb, 1));
       matvecs += b;
     }
     RL_TRY((residual_launch<T>(Tb, GTb, n, b, ld, theta_s, (T*)p->Res, p->res_norm, (T*)p->Rs, p->err, st)));
@@ -283,6 +308,12 @@ int solve_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, double tau, double* s
       RL_CUDA(cudaEventElapsedTime(&gms, p->ev[5], p->ev[6]));
       gram_ms += gms;
       ++gram_passes;
+      if (p->split) {
+        RL_CUDA(cudaEventElapsedTime(&gms, p->ev[5], p->ev[7]));
+        gram_ab_ms += gms;
+        RL_CUDA(cudaEventElapsedTime(&gms, p->ev[7], p->ev[6]));
+        gram_atb_ms += gms;
+      }
     }
     hist.r.push_back(hr);
     hist.th.push_back(ht);
@@ -331,11 +362,17 @@ int solve_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, double tau, double* s
     info->gram_passes = gram_passes;
     info->kernel_launches = (int)(launch_count() - launches0);
     info->jacobi_sweeps = sweeps;
+    info->ms_gram_ab = gram_ab_ms;
+    info->ms_gram_atb = gram_atb_ms;
+    info->ms_split_a = 0;
+    if (p->split) {
+      cudaEventElapsedTime(&ms, p->ev[8], p->ev[9]);
+      info->ms_split_a = ms;
+    }
   }
   if (herr & DEV_ERR_TIMEOUT) return RLOBPCG_ERR_TIMEOUT;
   if (herr & DEV_ERR_NONFINITE) return RLOBPCG_ERR_NONFINITE;
   return stop == RLOBPCG_STOP_MAX_ITER ? RLOBPCG_NOT_CONVERGED : RLOBPCG_OK;
-#undef RL_TRY
 }
 
 }  // namespace
@@ -353,6 +390,7 @@ extern "C" int rlobpcg_default_opts(rlobpcg_opts* o) {
   o->sketch_prec = RLOBPCG_SKETCH_F64;
   o->fixed_iters = 0;
   o->residual_refresh_every = 0;
+  o->gram_split = 1;
   o->tau = -1.0;
   return RLOBPCG_OK;
 }
@@ -378,6 +416,8 @@ int resolve_plan_args(int64_t m, int64_t n, int k, int dtype, const rlobpcg_opts
   *d_out = d;
   return RLOBPCG_OK;
 }
+
+bool uses_split(const rlobpcg_opts& o, int dtype, int b) { return o.gram_split && dtype == RLOBPCG_F64 && b <= 16; }
 
 // Every device buffer of a plan, in one place: with p == nullptr only the bytes are summed.
 struct PlanAlloc {
@@ -438,12 +478,21 @@ int plan_buffers(PlanAlloc& A_, rlobpcg_plan_s* p, int64_t m, int64_t n, int b, 
     sl = p ? (void**)&p->info : &dummy;
     rc = A_(sl, 64); if (rc) return rc;
   }
-  *gwork = gram_workspace_bytes(m, n, b, dtype);
-  if (*gwork == 0) {
-    set_last_error("Gram kernel: n*b too large for on-chip accumulation", __FILE__, __LINE__);
-    return RLOBPCG_ERR_UNSUPPORTED;
+  if (uses_split(o, dtype, b)) {
+    const size_t sp = split_prep_bytes(m, n), sw = split_work_bytes(m, n, b);
+    if (sp == 0 || sw == 0) return RLOBPCG_ERR_INVALID_ARG;
+    RL_B(sprep, sp);
+    RL_B(swork, sw);
+    if (p) { p->split = true; p->sprep_bytes = sp; p->swork_bytes = sw; }
+    *gwork = 0;
+  } else {
+    *gwork = gram_workspace_bytes(m, n, b, dtype);
+    if (*gwork == 0) {
+      set_last_error("Gram kernel: n*b too large for on-chip accumulation", __FILE__, __LINE__);
+      return RLOBPCG_ERR_UNSUPPORTED;
+    }
+    RL_B(gwork, *gwork);
   }
-  RL_B(gwork, *gwork);
   *twork = std::max(tsqr_workspace_bytes(m, (int)ld, esz), tsqr_workspace_bytes(n, qmax, esz));
   RL_B(twork, *twork);
 #undef RL_B

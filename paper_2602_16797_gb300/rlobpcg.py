@@ -35,14 +35,15 @@ RLOBPCG_STOP_FIXED = 2
 class rlobpcg_opts(ctypes.Structure):
     _fields_ = [("seed", c_uint64), ("d", c_int), ("zeta", c_int), ("block", c_int), ("max_iter", c_int),
                 ("check_every", c_int), ("use_stagnation", c_int), ("sketch_prec", c_int), ("fixed_iters", c_int),
-                ("residual_refresh_every", c_int), ("exact_sketch_svd", c_int), ("tau", c_double)]
+                ("residual_refresh_every", c_int), ("exact_sketch_svd", c_int), ("gram_split", c_int),
+                ("tau", c_double)]
 
 
 class rlobpcg_info(ctypes.Structure):
     _fields_ = [("iters", c_int), ("matvecs", c_int), ("stop_reason", c_int), ("block", c_int),
                 ("sigma11", c_double), ("ms_sketch", c_double), ("ms_factor", c_double), ("ms_iterate", c_double),
                 ("ms_total", c_double), ("ms_gram", c_double), ("gram_passes", c_int), ("kernel_launches", c_int),
-                ("jacobi_sweeps", c_int)]
+                ("jacobi_sweeps", c_int), ("ms_gram_ab", c_double), ("ms_gram_atb", c_double), ("ms_split_a", c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -73,6 +74,11 @@ _SIGS = {
     "rlobpcg_gram_workspace_size": (c_size_t, [c_int64, c_int64, c_int, c_int]),
     "rlobpcg_gram_noalloc": (c_int, [c_void_p, c_int64, c_int64, c_int64, c_int, c_void_p, c_int, c_int64, c_void_p,
                                      c_int64, c_void_p, c_int64, c_void_p]),
+    "rlobpcg_gram_split_prepare_size": (c_size_t, [c_int64, c_int64]),
+    "rlobpcg_gram_split_prepare": (c_int, [c_void_p, c_int64, c_int64, c_int64, c_void_p, c_size_t, c_void_p]),
+    "rlobpcg_gram_split_workspace_size": (c_size_t, [c_int64, c_int64, c_int]),
+    "rlobpcg_gram_split": (c_int, [c_void_p, c_int64, c_int64, c_void_p, c_int, c_int64, c_void_p, c_int64, c_void_p,
+                                   c_int64, c_void_p, c_size_t, c_void_p]),
     "rlobpcg_tsqr": (c_int, [c_void_p, c_int64, c_int, c_int64, c_int, c_void_p, c_void_p, c_size_t, c_void_p]),
     "rlobpcg_tsqr_workspace_size": (c_size_t, [c_int64, c_int, c_int]),
     "rlobpcg_plan_device_bytes": (c_size_t, [c_void_p]),
@@ -189,6 +195,24 @@ def rlobpcg_gram_noalloc(A: int, m: int, n: int, lda: int, dtype: int, W: int, b
     """rlobpcg_gram without a workspace argument (scratch is the library's fixed device buffer)."""
     _check("rlobpcg_gram_noalloc", load().rlobpcg_gram_noalloc(A, m, n, lda, dtype, W, b, ldw, AW, ldaw, G, ldg,
                                                                stream))
+
+
+def rlobpcg_gram_split_prepare_size(m: int, n: int) -> int:
+    return load().rlobpcg_gram_split_prepare_size(m, n)
+
+
+def rlobpcg_gram_split_prepare(A: int, m: int, n: int, lda: int, prep: int, prep_bytes: int, stream: int = 0) -> None:
+    _check("rlobpcg_gram_split_prepare", load().rlobpcg_gram_split_prepare(A, m, n, lda, prep, prep_bytes, stream))
+
+
+def rlobpcg_gram_split_workspace_size(m: int, n: int, b: int) -> int:
+    return load().rlobpcg_gram_split_workspace_size(m, n, b)
+
+
+def rlobpcg_gram_split(prep: int, m: int, n: int, W: int, b: int, ldw: int, AW: int, ldaw: int, G: int, ldg: int,
+                       work: int, work_bytes: int, stream: int = 0) -> None:
+    _check("rlobpcg_gram_split", load().rlobpcg_gram_split(prep, m, n, W, b, ldw, AW, ldaw, G, ldg, work, work_bytes,
+                                                           stream))
 
 
 def rlobpcg_tsqr_workspace_size(m: int, c: int, dtype: int) -> int:

@@ -20,8 +20,10 @@ pytestmark = pytest.mark.gpu
 
 
 def gpu_solve(A, k, *, seed, d=None, zeta=8, b=None, tau=None, stagnation=True, fixed=0, prec="f64",
-              max_iter=0, refresh=0, want_u=False, exact_svd=False):
+              max_iter=0, refresh=0, want_u=False, exact_svd=False, gram=None):
     o = rl.rlobpcg_default_opts()
+    if gram is not None:
+        o.gram_split = 1 if gram == "split" else 0
     o.exact_sketch_svd = 1 if exact_svd else 0
     o.seed = seed
     o.zeta = zeta
@@ -56,6 +58,7 @@ def compare(A, k, s_true, V_true, *, n, gap_abs, **kw):
     okw.pop("refresh", None)
     okw.pop("want_u", None)
     okw.pop("exact_svd", None)
+    okw.pop("gram", None)
     o = ora_solve(A, k, **okw)
     sig, V, _, resid, info = g
     print(f"gpu: iters={info['iters']} stop={info['stop_reason']} sigma11={info['sigma11']!r} sigma={sig!r}")
@@ -123,12 +126,13 @@ def test_well_conditioned_literal_bars():
 # exact nullspace and planted bottom cluster, n = 500, k = 5, d = 3n (reduced m for speed)
 # ---------------------------------------------------------------------------------------------
 
+@pytest.mark.parametrize("gram", ["split", "fp64"])
 @pytest.mark.parametrize("m", [20_000, 100_000])
-def test_exact_nullspace(m):
+def test_exact_nullspace(m, gram):
     A, C = wl.exact_nullspace(m=m)
     _, _, Vh = np.linalg.svd(C)
     null = Vh.conj().T[:, 495:]
-    g = gpu_solve(A, 5, seed=1002, d=1500)
+    g = gpu_solve(A, 5, seed=1002, d=1500, gram=gram)
     o = ora_solve(A, 5, seed=1002, d=1500)
     nA = o["sigma11"]
     # sigma is at rounding level: absolute bar only
@@ -138,11 +142,12 @@ def test_exact_nullspace(m):
     assert np.linalg.norm(A @ g[1], 2) <= 100 * np.sqrt(500) * U * nA
 
 
+@pytest.mark.parametrize("gram", ["split", "fp64"])
 @pytest.mark.parametrize("m", [20_000, 100_000])
-def test_planted_bottom_cluster(m):
+def test_planted_bottom_cluster(m, gram):
     A, s, V = wl.planted_bottom_cluster(m=m)
     gap = (s[-6] - s[-5]) / s[0]
-    compare(A, 5, s[::-1][:5], V[:, ::-1][:, :5], n=500, gap_abs=gap, seed=1002, d=1500)
+    compare(A, 5, s[::-1][:5], V[:, ::-1][:, :5], n=500, gap_abs=gap, seed=1002, d=1500, gram=gram)
 
 
 @pytest.mark.parametrize("exact_svd", [False, True])
