@@ -393,6 +393,7 @@ def run_ours(args, rank, world, local_rank):
                        "parallelism": f"replicas x{world}"},
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
             "iters": [x.iters for x in infos], "stop_reasons": [x.stop_reason for x in infos],
+            "rr_sweeps_per_svd": round(sum(x.rr_sweeps for x in infos) / max(1, sum(x.rr_calls for x in infos)), 2),
             "phase_ms": {"sketch": statistics.mean(x.ms_sketch for x in infos),
                          "factor": statistics.mean(x.ms_factor for x in infos),
                          "iterate": statistics.mean(x.ms_iterate for x in infos),

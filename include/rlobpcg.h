@@ -97,6 +97,8 @@ typedef struct {
   double ms_gram_ab;    /* split Gram plans: device time of the A W kernels (W split + first product) */
   double ms_gram_atb;   /* split Gram plans: device time of the A^T (A W) kernels (+ partial sums)     */
   double ms_split_a;    /* split Gram plans: device time of splitting A into digits (once per solve)   */
+  int rr_sweeps;        /* Jacobi sweeps of all Rayleigh-Ritz SVDs of the solve (R_T and the start) */
+  int rr_calls;         /* number of those SVDs                                                      */
 } rlobpcg_info;
 
 typedef struct rlobpcg_plan_s* rlobpcg_plan_t;
@@ -276,7 +278,8 @@ int rlobpcg_gram_noalloc(const void* A, int64_t m, int64_t n, int64_t lda, int d
  *   rlobpcg_gram_split: one pass; W (n x b, ldw), AW (m x b, ldaw), G (n x b, ldg) row-major,
  *     1 <= b <= 16; work: rlobpcg_gram_split_workspace_size(m, n, b) bytes of device scratch.
  * All pointers are device memory owned by the caller; calls are asynchronous on `stream` and
- * synchronise it before returning. Errors: INVALID_ARG (sizes, NULL, buffers too small),
+ * synchronise it before returning. prep also holds a few counters that each pass uses and leaves
+ * at zero, so passes on one prep must not overlap. Errors: INVALID_ARG (sizes, NULL, buffers too small),
  * UNSUPPORTED (n above 1,048,560), NONFINITE (W holds Inf or NaN), TIMEOUT (a bounded device wait
  * ran out), CUDA.
  */

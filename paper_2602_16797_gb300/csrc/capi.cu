@@ -21,7 +21,7 @@ size_t split_prep_bytes(int64_t m, int64_t n);
 size_t split_work_bytes(int64_t m, int64_t n, int b);
 int split_prepare(const double* A, int64_t m, int64_t n, int64_t lda, void* prep, size_t prep_bytes, cudaStream_t st);
 int split_gram(const void* prep, int64_t m, int64_t n, const double* W, int b, int64_t ldw, double* AW, int64_t ldaw,
-               double* G, int64_t ldg, void* work, size_t work_bytes, int resid_mode, int* err, cudaEvent_t mid,
+               double* G, int64_t ldg, void* work, size_t work_bytes, int flags, int* err, cudaEvent_t mid,
                cudaStream_t st);
 template <class T>
 int tsqr_impl(const T* X, int64_t m, int c, int64_t ldx, T* R, void* work, size_t work_bytes, cudaStream_t st);

@@ -158,11 +158,17 @@ template <class R>
 __device__ inline bool jacobi_tangent(R a, R b, R g2, R ga, R tol, R tiny2, R eps, R* c, R* s) {
   if (!(g2 > tol * tol * a * b) || a <= tiny2 || b <= tiny2) return false;
   const R d = b - a;
-  const R den = fabs(d) + sqrt_r(d * d + (R)4 * g2);
-  const R t = (d >= (R)0 ? (R)2 * ga : (R)-2 * ga) / den;
-  if (fabs(t) <= eps) return false;
-  *c = rsqrt_r((R)1 + t * t);
-  *s = *c * t;
+  // With r = sqrt(d^2 + 4 g^2): cos(2 theta) = |d| / r, cos(theta)^2 = (1 + cos(2 theta)) / 2 and
+  // sin(theta) = |g| / (r cos(theta)). Two reciprocal square roots and no square root or division
+  // on the dependent chain (FP64 latency); tan(theta) = 2|g| / (|d| + r) as in the usual formula.
+  const R q = rsqrt_r(d * d + (R)4 * g2);
+  const R u = (R)0.5 + (R)0.5 * (fabs(d) * q);
+  const R w = rsqrt_r(u);
+  const R cc = u * w;
+  const R ss = (ga * q) * w;
+  if (ss <= eps * cc) return false;
+  *c = cc;
+  *s = d >= (R)0 ? ss : -ss;
   return true;
 }
 

@@ -36,17 +36,25 @@
 // Kernel shape: one CTA per SM, 192 threads: warp 0 issues the bulk copies (5-stage ring of
 // mbarriers), warp 1 owns TMEM and issues the MMAs from one thread, warps 2-5 read the
 // accumulators (two TMEM buffers, so reading one unit overlaps the MMAs of the next), zero them,
-// and do the FP64 recombination. Every wait is bounded and reports DEV_ERR_TIMEOUT.
+// and do the FP64 recombination; the last CTA of each column tile of the second product sums
+// the per-CTA partials in a fixed order. Every wait is bounded and reports DEV_ERR_TIMEOUT.
 #include "common.cuh"
+#include "split.cuh"
 #include "tc.cuh"
 
 namespace rl {
 
 namespace {
 
-constexpr int SL = 8;                  // digits per FP64 value
+using split::SL;
+using split::TK;
+using split::core_off;
+using split::group_exp;
+using split::split8;
+using split::bf16_of;
+using split::SPLIT_RESID;
+using split::SPLIT_W_READY;
 constexpr int TM = 128;                // MMA M: rows (first product) or columns (second) per tile
-constexpr int TK = 16;                 // MMA K and pipeline stage depth
 constexpr int KC_KB = 32;              // k-blocks per exact accumulation: 32 x 16 = 512 terms
 constexpr int CH_KB = TM / TK;         // k-blocks per 128-row chunk of the second product
 constexpr int NST = 5;                 // pipeline stages
@@ -62,7 +70,7 @@ struct Dims {
 Dims dims_of(int64_t m, int64_t n) { return {cdiv(m, TM), cdiv(n, TK), cdiv(n, TM), cdiv(n, TM) * TM}; }
 
 struct PrepLayout {
-  size_t art, act, erow, ecol, total;
+  size_t art, act, erow, ecol, cnt, total;
 };
 PrepLayout prep_layout(int64_t m, int64_t n) {
   const Dims d = dims_of(m, n);
@@ -73,6 +81,7 @@ PrepLayout prep_layout(int64_t m, int64_t n) {
   L.act = take((size_t)d.CT * d.R1 * CH_KB * SL * SLICE_BYTES);
   L.erow = take((size_t)d.R1 * TM * sizeof(int));
   L.ecol = take((size_t)d.R1 * d.NC * sizeof(int));
+  L.cnt = take((size_t)d.CT * sizeof(int));   // finished-CTA counters of the second product
   L.total = off;
   return L;
 }
@@ -98,32 +107,8 @@ WorkLayout work_layout(int64_t m, int64_t n, int b) {
   return L;
 }
 
-// ---- digits --------------------------------------------------------------------------------------
-__device__ __forceinline__ int group_exp(double amax) {
-  int e = 0;
-  frexp(amax, &e);   // amax = f 2^e with f in [0.5, 1), so every |x| <= amax is < 2^e
-  return amax > 0 ? e : 0;
-}
-
-__device__ __forceinline__ void split8(double x, int E, int (&d)[SL]) {
-  long long V = __double2ll_rn(scalbn(x, 55 - E));
-#pragma unroll
-  for (int p = SL - 1; p > 0; --p) {
-    const int r = (int)(V & 127);
-    const int dd = r - ((r & 64) << 1);   // balanced remainder in [-64, 63]
-    d[p] = dd;
-    V = (V - dd) >> 7;                    // exact: V - dd is a multiple of 128
-  }
-  d[0] = (int)V;                          // |V| <= 64 here since |V| <= 2^55 at the start
-}
-
-__device__ __forceinline__ uint16_t bf16_of(int v) { return (uint16_t)(__float_as_uint((float)v) >> 16); }
-
-// element (row, kk) of an R-row x 16 digit tile in core-matrix order
-__device__ __forceinline__ int core_off(int row, int kk, int R) {
-  return (kk >> 3) * (R * 8) + (row >> 3) * 64 + (row & 7) * 8 + (kk & 7);
-}
-// inverse for R = 128: position o -> (row, kk), so that consecutive threads write consecutive digits
+// inverse of core_off for R = 128: position o -> (row, kk), so that consecutive threads write
+// consecutive digits
 __device__ __forceinline__ void core_pos128(int o, int& row, int& kk) {
   kk = ((o >> 10) << 3) | (o & 7);
   row = (((o & 1023) >> 6) << 3) | ((o & 63) >> 3);
@@ -319,6 +304,9 @@ struct PassArgs {
   uint16_t* Ysl;         // first product: digits of AW for the second product (or null)
   int* H;
   double* part;          // second product: partials [NR][NC][BP]
+  double* G;             // second product: output (n x b, ldg), summed by the last CTA per column tile
+  int64_t ldg, n;
+  int* cnt;              // per column tile: CTAs finished (zero between launches)
   int* err;
 };
 
@@ -529,7 +517,7 @@ __global__ void __launch_bounds__(NTH, 1) split_pass_kernel(PassArgs g) {
           ++v;
 #pragma unroll
           for (int j = 0; j < BP; ++j)
-            if (j < g.b) y[j] += scalbn(s[j], Ei + Fj[j] - 12);
+            if (j < g.b) y[j] += split::mul_pow2(s[j], Ei + Fj[j] - 12);
         }
         if (!ok) break;
         if (i < g.m)
@@ -556,11 +544,49 @@ __global__ void __launch_bounds__(NTH, 1) split_pass_kernel(PassArgs g) {
         const int Ec = g.eA[rc * g.NC + c];
 #pragma unroll
         for (int j = 0; j < BP; ++j)
-          if (j < g.b) acc[j] += scalbn(s[j], Ec + g.eB[rc * BP + j] - 12);
+          if (j < g.b) acc[j] += split::mul_pow2(s[j], Ec + g.eB[rc * BP + j] - 12);
       }
       double* out = g.part + (size_t)(rng * g.NC + c) * BP;
 #pragma unroll
       for (int j = 0; j < BP; ++j) out[j] = (ok && j < g.b) ? acc[j] : 0.0;
+      // the last CTA of this column tile to finish sums the NR partials in range order
+      // (deterministic); the counter is left at zero for the next launch
+      __shared__ int s_last;
+      __threadfence();
+      tc::named_bar<1>(128);
+      if (row == 0) s_last = atomicAdd(g.cnt + ct, 1) == g.NR - 1;
+      tc::named_bar<1>(128);
+      if (s_last) {
+        __threadfence();
+        if (c < g.n) {
+          // 4 interleaved accumulators per column keep several L2 loads in flight; the
+          // combination order is fixed
+          double sum[4][BP];
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int j = 0; j < BP; ++j) sum[u][j] = 0;
+          int r = 0;
+          for (; r + 3 < g.NR; r += 4)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const double* pr = g.part + (size_t)((r + u) * g.NC + c) * BP;
+#pragma unroll
+              for (int j = 0; j < BP; ++j)
+                if (j < g.b) sum[u][j] += __ldcg(pr + j);
+            }
+          for (; r < g.NR; ++r) {
+            const double* pr = g.part + (size_t)(r * g.NC + c) * BP;
+#pragma unroll
+            for (int j = 0; j < BP; ++j)
+              if (j < g.b) sum[0][j] += __ldcg(pr + j);
+          }
+#pragma unroll
+          for (int j = 0; j < BP; ++j)
+            if (j < g.b) g.G[c * g.ldg + j] = (sum[0][j] + sum[1][j]) + (sum[2][j] + sum[3][j]);
+        }
+        if (row == 0) g.cnt[ct] = 0;
+      }
     }
     if (!ok) atomicOr(g.err, DEV_ERR_TIMEOUT);
   }
@@ -570,17 +596,6 @@ __global__ void __launch_bounds__(NTH, 1) split_pass_kernel(PassArgs g) {
     tc::fence_after_sync();
     tc::tmem_dealloc(tmem, 2 * ACCW);
   }
-}
-
-__global__ void split_reduce_kernel(const double* __restrict__ part, int NR, int64_t NC, int BP, int64_t n, int b,
-                                    double* __restrict__ G, int64_t ldg) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= n * b) return;
-  const int64_t k = e / b;
-  const int j = (int)(e % b);
-  double s = 0;
-  for (int r = 0; r < NR; ++r) s += part[((int64_t)r * NC + k) * BP + j];   // fixed order
-  G[k * ldg + j] = s;
 }
 
 template <int BP, int MODE>
@@ -595,16 +610,20 @@ int launch_pass(const PassArgs& a, int grid, cudaStream_t st) {
 
 template <int BP>
 int split_gram_bp(const unsigned char* prep, int64_t m, int64_t n, const double* W, int b, int64_t ldw, double* AW,
-                  int64_t ldaw, double* G, int64_t ldg, unsigned char* work, int resid_mode, int* err,
+                  int64_t ldaw, double* G, int64_t ldg, unsigned char* work, int flags, int* err,
                   cudaEvent_t mid, cudaStream_t st) {
+  const bool resid_mode = (flags & SPLIT_RESID) != 0;
   const Dims d = dims_of(m, n);
   const PrepLayout P = prep_layout(m, n);
   const WorkLayout L = work_layout(m, n, b);
   uint16_t* Ysl = (uint16_t*)(work + L.ysl);
   int* H = (int*)(work + L.h);
   if (!resid_mode) {
-    w_digits_kernel<BP><<<1, 512, 0, st>>>(W, (int)n, b, ldw, d.NKB, (uint16_t*)(work + L.wsl), (int*)(work + L.f), err);
-    RL_CHECK_LAUNCH();
+    if (!(flags & SPLIT_W_READY)) {
+      w_digits_kernel<BP><<<1, 512, 0, st>>>(W, (int)n, b, ldw, d.NKB, (uint16_t*)(work + L.wsl), (int*)(work + L.f),
+                                            err);
+      RL_CHECK_LAUNCH();
+    }
     PassArgs a{};
     a.Aop = (const uint16_t*)(prep + P.art);
     a.Bop = (const uint16_t*)(work + L.wsl);
@@ -627,12 +646,12 @@ int split_gram_bp(const unsigned char* prep, int64_t m, int64_t n, const double*
   a.m = m; a.R1 = d.R1; a.NKB = d.NKB; a.CT = d.CT; a.NC = d.NC;
   a.b = b; a.NR = L.NR;
   a.part = (double*)(work + L.part);
+  a.G = G;
+  a.ldg = ldg;
+  a.n = n;
+  a.cnt = (int*)(prep + P.cnt);
   a.err = err;
   RL_TRY((launch_pass<BP, 1>(a, (int)(d.CT * L.NR), st)));
-  const int64_t tot = n * b;
-  split_reduce_kernel<<<(unsigned)cdiv(tot, 256), 256, 0, st>>>((const double*)(work + L.part), L.NR, d.NC, BP, n, b,
-                                                                 G, ldg);
-  RL_CHECK_LAUNCH();
   return RLOBPCG_OK;
 }
 
@@ -654,6 +673,7 @@ int split_prepare(const double* A, int64_t m, int64_t n, int64_t lda, void* prep
   int* erow = (int*)(base + P.erow);
   int* ecol = (int*)(base + P.ecol);
   const int64_t mpad = d.R1 * TM;
+  RL_CUDA(cudaMemsetAsync(base + P.cnt, 0, (size_t)d.CT * sizeof(int), st));
   row_exp_kernel<<<(unsigned)cdiv(mpad, 8), 256, 0, st>>>(A, m, (int)n, lda, mpad, erow);
   RL_CHECK_LAUNCH();
   rt_digits_kernel<<<dim3((unsigned)d.R1, (unsigned)d.NKB), 256, 0, st>>>(A, m, (int)n, lda, erow, d.NKB,
@@ -667,18 +687,29 @@ int split_prepare(const double* A, int64_t m, int64_t n, int64_t lda, void* prep
   return RLOBPCG_OK;
 }
 
+split::WDigits split_w_digits(void* work, int64_t m, int64_t n, int b) {
+  const WorkLayout L = work_layout(m, n, b);
+  split::WDigits w;
+  w.Wsl = (uint16_t*)((unsigned char*)work + L.wsl);
+  w.F = (int*)((unsigned char*)work + L.f);
+  w.NKB = dims_of(m, n).NKB;
+  w.BP = L.BP;
+  return w;
+}
+
 int split_gram(const void* prep, int64_t m, int64_t n, const double* W, int b, int64_t ldw, double* AW, int64_t ldaw,
-               double* G, int64_t ldg, void* work, size_t work_bytes, int resid_mode, int* err, cudaEvent_t mid,
+               double* G, int64_t ldg, void* work, size_t work_bytes, int flags, int* err, cudaEvent_t mid,
                cudaStream_t st) {
+  const bool resid_mode = (flags & SPLIT_RESID) != 0;
   if (!prep || !AW || !G || !work || m < 1 || n < 1 || b < 1 || b > 16 || ldaw < b || ldg < b ||
       (!resid_mode && (!W || ldw < b)))
     return RLOBPCG_ERR_INVALID_ARG;
   if (work_bytes < split_work_bytes(m, n, b)) return RLOBPCG_ERR_INVALID_ARG;
   if (b <= 8)
     return split_gram_bp<8>((const unsigned char*)prep, m, n, W, b, ldw, AW, ldaw, G, ldg, (unsigned char*)work,
-                            resid_mode, err, mid, st);
+                            flags, err, mid, st);
   return split_gram_bp<16>((const unsigned char*)prep, m, n, W, b, ldw, AW, ldaw, G, ldg, (unsigned char*)work,
-                           resid_mode, err, mid, st);
+                           flags, err, mid, st);
 }
 
 }  // namespace rl

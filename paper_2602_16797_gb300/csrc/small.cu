@@ -12,7 +12,10 @@
 //     diag(R) real non-negative).
 // State layout: T, A_T and G_T are row-major with leading dimension 3b and column blocks
 // [V | W | X] (X absent, i.e. c = 2b, in iteration 0).
+#include <type_traits>
+
 #include "common.cuh"
+#include "split.cuh"
 
 namespace rl {
 
@@ -123,6 +126,68 @@ __global__ void __launch_bounds__(256) tsqr_level_kernel(const T* __restrict__ X
   }
 }
 
+// Upper levels of the TSQR tree: merge F stacked c x c upper-triangular R factors into one.
+// Block 0 is the running R; the reflector of column j touches row j of block 0 and rows 0..j of
+// blocks 1..F-1 only (every other entry of the column is zero and stays zero), so both the FP64
+// work and the rows per thread of column j shrink with j (half the work of a dense stack).
+// Thread (column cc, row phase p) as in tsqr_level_kernel; the reflector is applied with its
+// 1/(alpha - beta) scaling folded into the update, and Q is never formed.
+template <class T>
+__global__ void __launch_bounds__(256) tsqr_merge_kernel(const T* __restrict__ Rin, int nblk, int c, int F, int RP,
+                                                         T* __restrict__ Rout) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* S = reinterpret_cast<T*>(smem_raw);   // F c rows x c, row-major
+  __shared__ T sh_tau, sh_inv, sh_beta;
+  const int tid = threadIdx.x, NT = blockDim.x, cc = tid / RP, p = tid % RP;
+  const int b0 = blockIdx.x * F;
+  const int nb = imin(F, nblk - b0);
+  for (int i = tid; i < nb * c * c; i += NT) S[i] = Rin[(size_t)b0 * c * c + i];
+  __syncthreads();
+  for (int j = 0; j < c; ++j) {
+    const int jr = j + 1;
+    const int act = (nb - 1) * jr;   // rows of blocks 1.. that can be nonzero in column j
+    T d = zero_<T>();
+    if (cc < c && cc >= j) {
+      T a0 = zero_<T>(), a1 = zero_<T>();
+      int t = p;
+      for (; t + RP < act; t += 2 * RP) {
+        const int r0 = (1 + t / jr) * c + t % jr, r1 = (1 + (t + RP) / jr) * c + (t + RP) % jr;
+        a0 = madc_(S[(size_t)r0 * c + j], S[(size_t)r0 * c + cc], a0);
+        a1 = madc_(S[(size_t)r1 * c + j], S[(size_t)r1 * c + cc], a1);
+      }
+      if (t < act) {
+        const int r0 = (1 + t / jr) * c + t % jr;
+        a0 = madc_(S[(size_t)r0 * c + j], S[(size_t)r0 * c + cc], a0);
+      }
+      d = add_(a0, a1);
+    }
+    for (int o = RP >> 1; o > 0; o >>= 1) d = add_(d, shfl_xor_(d, o));
+    if (cc == j && p == 0) {
+      T tau, beta, inv_ab;
+      householder_scalars(S[(size_t)j * c + j], re_(d), &tau, &beta, &inv_ab);
+      sh_tau = tau; sh_inv = inv_ab; sh_beta = beta;
+    }
+    __syncthreads();
+    if (cc < c && cc > j) {
+      const T inv_ab = sh_inv;
+      const T f = mul_(conj_(sh_tau), add_(S[(size_t)j * c + cc], mul_(conj_(inv_ab), d)));
+      const T fv = mul_(inv_ab, f);
+      if (p == 0) S[(size_t)j * c + cc] = sub_(S[(size_t)j * c + cc], f);
+      for (int t = p; t < act; t += RP) {
+        const int r = (1 + t / jr) * c + t % jr;
+        S[(size_t)r * c + cc] = sub_(S[(size_t)r * c + cc], mul_(S[(size_t)r * c + j], fv));
+      }
+    }
+    if (cc == j && p == 0) S[(size_t)j * c + j] = sh_beta;
+    __syncthreads();
+  }
+  T* out = Rout + (size_t)blockIdx.x * c * c;
+  for (int i = tid; i < c * c; i += NT) {
+    const int r = i / c, q = i % c;
+    out[i] = (q >= r) ? S[i] : zero_<T>();
+  }
+}
+
 // scale rows of a c x c R so that diag(R) is real and non-negative
 template <class T>
 __global__ void r_phase_fix_kernel(T* R, int c) {
@@ -138,6 +203,189 @@ __global__ void r_phase_fix_kernel(T* R, int c) {
 // Outputs: theta (c, descending), K (c x 2b row-major), sweeps.
 // ------------------------------------------------------------------------------------------
 __device__ inline int rr_slot(int k, int r, int N) { return k == 0 ? 0 : ((k - 1 + r) % (N - 1)) + 1; }
+
+// One-sided Jacobi on c <= 16 real columns (X, V column-major c x c in shared memory) with two
+// disjoint pairs per warp (a half-warp each, lane = row): on GB300 every FP64 warp instruction
+// costs its sub-partition ~64 cycles whatever the number of active lanes, so packing two pairs per
+// instruction halves the FP64 time of a round. A half-warp forms its pair's three sums with a
+// 4-level butterfly. The rotation test is the FP64 one of jacobi_tangent; the angle comes from an
+// FP32 evaluation of tan(theta) = sign(d) 2|g| / (|d| + sqrt(d^2 + 4 g^2)) on d = b - a and g
+// taken in FP64 and scaled by a power of two, and (c, s) = (1, t) / sqrt(1 + t^2) in FP64, which
+// is orthogonal to FP64 rounding for any t; an FP32-accurate angle leaves ~1e-7 of the pair's
+// cosine, which the next sweep removes. A pair that needs no rotation uses (c, s) = (1, 0), so
+// both halves execute the same instructions. Returns the number of sweeps.
+__device__ int jacobi_pairs16(double* X, double* V, int c, int N, double tol, double tiny2) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
+  const int half = lane >> 4, row = lane & 15;
+  const double tol2 = tol * tol;
+  int sweep = 0;
+  for (; sweep < 60; ++sweep) {
+    int rotated = 0;
+    for (int r = 0; r < N - 1; ++r) {
+      for (int p0 = 2 * warp; p0 < N / 2; p0 += 2 * nw) {   // warp-uniform
+        const int pi = p0 + half;
+        int pp = 0, qq = 0;
+        bool valid = pi < N / 2;
+        if (valid) {
+          pp = rr_slot(pi, r, N);
+          qq = rr_slot(N - 1 - pi, r, N);
+          if (pp > qq) { const int t = pp; pp = qq; qq = t; }
+          valid = qq < c;
+        }
+        const bool live = valid && row < c;
+        const double xp = live ? X[pp * c + row] : 0.0, xq = live ? X[qq * c + row] : 0.0;
+        double a = xp * xp, bb = xq * xq, g = xp * xq;
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) {
+          a += __shfl_xor_sync(0xffffffffu, a, o);
+          bb += __shfl_xor_sync(0xffffffffu, bb, o);
+          g += __shfl_xor_sync(0xffffffffu, g, o);
+        }
+        bool rot = valid && (g * g > tol2 * a * bb) && a > tiny2 && bb > tiny2;
+        double cs = 1.0, se = 0.0;
+        {
+          const double mx = rot ? fmax(a, bb) : 1.0;
+          const int ex = (int)((__double_as_longlong(mx) >> 52) & 0x7ff) - 1023;
+          const double sc = __longlong_as_double((long long)(1023 - imax(-1022, imin(1022, ex))) << 52);
+          const float df = (float)((bb - a) * sc), gf = fabsf((float)(g * sc));
+          const float tf = copysignf(2.0f * gf, df) / (fabsf(df) + sqrtf(df * df + 4.0f * gf * gf));
+          rot = rot && fabsf(tf) > 2.220446049250313e-16f;
+          const double t = rot ? (double)tf : 0.0;
+          cs = rsqrt(fma(t, t, 1.0));
+          const double sn = cs * t;
+          se = g < 0.0 ? -sn : sn;
+        }
+        if (live) {
+          const double vp = V[pp * c + row], vq = V[qq * c + row];
+          X[pp * c + row] = cs * xp - se * xq;
+          X[qq * c + row] = se * xp + cs * xq;
+          V[pp * c + row] = cs * vp - se * vq;
+          V[qq * c + row] = se * vp + cs * vq;
+        }
+        rotated |= rot;
+      }
+      __syncthreads();
+    }
+    if (!__syncthreads_or(rotated)) { ++sweep; break; }
+  }
+  return sweep;
+}
+
+// The same sweeps in FP32 (on GB300 the FP32 pipe issues ~64x the FP64 rate): used on a scaled
+// FP32 copy of R_T to find a V that nearly diagonalises it (cosines ~ c u_32).
+__device__ int jacobi_pairs16_f32(float* X, float* V, int c, int N, float tol, float tiny2) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
+  const int half = lane >> 4, row = lane & 15;
+  const float tol2 = tol * tol;
+  int sweep = 0;
+  for (; sweep < 40; ++sweep) {
+    int rotated = 0;
+    for (int r = 0; r < N - 1; ++r) {
+      for (int p0 = 2 * warp; p0 < N / 2; p0 += 2 * nw) {
+        const int pi = p0 + half;
+        int pp = 0, qq = 0;
+        bool valid = pi < N / 2;
+        if (valid) {
+          pp = rr_slot(pi, r, N);
+          qq = rr_slot(N - 1 - pi, r, N);
+          if (pp > qq) { const int t = pp; pp = qq; qq = t; }
+          valid = qq < c;
+        }
+        const bool live = valid && row < c;
+        const float xp = live ? X[pp * c + row] : 0.0f, xq = live ? X[qq * c + row] : 0.0f;
+        float a = xp * xp, bb = xq * xq, g = xp * xq;
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) {
+          a += __shfl_xor_sync(0xffffffffu, a, o);
+          bb += __shfl_xor_sync(0xffffffffu, bb, o);
+          g += __shfl_xor_sync(0xffffffffu, g, o);
+        }
+        const float d = bb - a, ga = fabsf(g);
+        const float tf = copysignf(2.0f * ga, d) / (fabsf(d) + sqrtf(d * d + 4.0f * ga * ga));
+        const bool rot = valid && (g * g > tol2 * a * bb) && a > tiny2 && bb > tiny2 && fabsf(tf) > 1.0e-12f;
+        const float t = rot ? tf : 0.0f;
+        const float cs = rsqrtf(fmaf(t, t, 1.0f));
+        const float sn = cs * t;
+        const float se = g < 0.0f ? -sn : sn;
+        if (live) {
+          const float vp = V[pp * c + row], vq = V[qq * c + row];
+          X[pp * c + row] = cs * xp - se * xq;
+          X[qq * c + row] = se * xp + cs * xq;
+          V[pp * c + row] = cs * vp - se * vq;
+          V[qq * c + row] = se * vp + cs * vq;
+        }
+        rotated |= rot;
+      }
+      __syncthreads();
+    }
+    if (!__syncthreads_or(rotated)) { ++sweep; break; }
+  }
+  return sweep;
+}
+
+// Out = In * M for c x c column-major matrices in shared memory (all threads; result in Out).
+__device__ void small_matmul(const double* In, const double* M, double* Out, int c) {
+  for (int o = threadIdx.x; o < c * c; o += blockDim.x) {
+    const int j = o / c, r = o % c;
+    double s0 = 0, s1 = 0;
+    int i = 0;
+    for (; i + 1 < c; i += 2) {
+      s0 = fma(In[i * c + r], M[j * c + i], s0);
+      s1 = fma(In[(i + 1) * c + r], M[j * c + i + 1], s1);
+    }
+    if (i < c) s0 = fma(In[i * c + r], M[j * c + i], s0);
+    Out[o] = s0 + s1;
+  }
+}
+
+// Preconditioned one-sided Jacobi for real c <= 16 (X = R_T, V = I on entry, column-major):
+//   1. FP32 sweeps on X scaled by a power of two -> Vf with X Vf nearly column-orthogonal;
+//   2. V = Vf made orthonormal in FP64 by two Newton-Schulz steps V <- V (3 I - V^T V) / 2
+//      (orthogonality error ~1e-6 -> ~1e-12 -> rounding level);
+//   3. X <- X V in FP64 and FP64 sweeps from there (usually one with rotations, one to confirm).
+// The FP64 stage runs to the same convergence test as the plain FP64 sweeps, on X V with V
+// orthonormal to rounding; the FP32 stage only changes where it starts (and saves FP64 sweeps).
+__device__ int jacobi_mixed16(double* X, double* V, int c, int N, double tol, double tiny2, double mx0, float* Xf,
+                              float* Vf, double* Ms, double* Ws) {
+  const int tid = threadIdx.x, NT = blockDim.x;
+  // power-of-two scale so that the largest column norm is about 1 in FP32
+  const int ex = (int)((__double_as_longlong(fmax(mx0, 1e-300)) >> 52) & 0x7ff) - 1023;
+  const double sc = __longlong_as_double((long long)(1023 - imax(-1022, imin(1022, ex))) << 52);
+  for (int i = tid; i < c * c; i += NT) {
+    Xf[i] = (float)(X[i] * sc);
+    Vf[i] = (i / c == i % c) ? 1.0f : 0.0f;
+  }
+  __syncthreads();
+  const float tol32 = (float)imax(c, 4) * 1.1920929e-7f;
+  const float tiny32 = (float)(tiny2 * sc * sc);
+  jacobi_pairs16_f32(Xf, Vf, c, N, tol32, tiny32);
+  for (int i = tid; i < c * c; i += NT) V[i] = (double)Vf[i];
+  __syncthreads();
+  for (int step = 0; step < 2; ++step) {
+    // Ms = (3 I - V^T V) / 2
+    for (int o = tid; o < c * c; o += NT) {
+      const int i = o / c, j = o % c;
+      double s0 = 0, s1 = 0;
+      int k = 0;
+      for (; k + 1 < c; k += 2) {
+        s0 = fma(V[i * c + k], V[j * c + k], s0);
+        s1 = fma(V[i * c + k + 1], V[j * c + k + 1], s1);
+      }
+      if (k < c) s0 = fma(V[i * c + k], V[j * c + k], s0);
+      Ms[o] = (i == j ? 1.5 : 0.0) - 0.5 * (s0 + s1);
+    }
+    __syncthreads();
+    small_matmul(V, Ms, Ws, c);
+    __syncthreads();
+    for (int i = tid; i < c * c; i += NT) V[i] = Ws[i];
+    __syncthreads();
+  }
+  small_matmul(X, V, Ws, c);
+  __syncthreads();
+  for (int i = tid; i < c * c; i += NT) X[i] = Ws[i];
+  __syncthreads();
+  return jacobi_pairs16(X, V, c, N, tol, tiny2);
+}
 
 template <class T>
 __global__ void __launch_bounds__(1024) rr_small_kernel(const T* __restrict__ Rt, int c, int b, double* theta_out,
@@ -176,7 +424,16 @@ __global__ void __launch_bounds__(1024) rr_small_kernel(const T* __restrict__ Rt
   const double tiny = mx0 * (double)imax(c, 4) * 2.220446049250313e-16;
   const double tiny2 = tiny * tiny;
   int sweep = 0;
-  for (; sweep < 60; ++sweep) {
+  bool fast = false;
+  if constexpr (std::is_same<T, double>::value) {
+    if (c <= 16) {
+      __shared__ float Xf[256], Vf[256];
+      __shared__ double Ms[256], Ws2[256];
+      sweep = jacobi_mixed16(X, V, c, N, tol, tiny2, mx0, Xf, Vf, Ms, Ws2);
+      fast = true;
+    }
+  }
+  for (; !fast && sweep < 60; ++sweep) {
     if (tid == 0) changed = 0;
     __syncthreads();
     for (int r = 0; r < N - 1; ++r) {
@@ -316,7 +573,7 @@ __global__ void __launch_bounds__(1024) rr_small_kernel(const T* __restrict__ Rt
     }
     K_out[i] = v;
   }
-  if (tid == 0 && info) info[0] = sweep;
+  if (tid == 0 && info) { info[0] += sweep; info[1] += 1; }   // totals over the solve
 }
 
 // ------------------------------------------------------------------------------------------
@@ -521,6 +778,179 @@ __global__ void __launch_bounds__(1024) bcgs2_orth_kernel(T* Tb, int n, int b, i
   }
 }
 
+// BCGS2 + Orth with the rows of [V X] and W staged in shared memory (one CTA of 256 threads,
+// used whenever n (q + b) elements fit; the kernel above is the fallback). Shared-memory operands
+// avoid the L2 latency of every dependent step; the FP64 work (2 passes x 2 n q b FMAs, then
+// 2 n b^2 for Householder and Q) runs at the single SM's DFMA rate. With wd.Wsl set (real FP64),
+// the final W is also written as bf16 digits for the split Gram pass (see split.cuh).
+template <class T>
+__global__ void __launch_bounds__(256) bcgs2_orth_smem_kernel(T* __restrict__ Tb, int n, int b, int64_t ld, int wo,
+                                                              int nx, int passes, split::WDigits wd, int* err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int NT = 256, NW = NT / 32;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int q = b + nx;
+  const int QB = q * b;
+  T* Bs = reinterpret_cast<T*>(smem_raw);   // n x q: V then X (row-major); later E = Q (n x b)
+  T* Ws = Bs + (size_t)n * q;               // n x b
+  T* Pp = Ws + (size_t)n * b;               // up to 4 x q x b partial projections
+  T* P = Pp + 4 * (size_t)QB;               // q x b
+  T* tauv = P + QB;
+  T* dg = tauv + b;
+  T* sv = dg + b;
+  double* red = reinterpret_cast<double*>(sv + b);   // NW x 16 column maxima
+  __shared__ T sh_inv;
+  __shared__ int Fs[16];
+  auto bcol = [&](int j) { return j < b ? j : (2 * b + (j - b)); };
+  for (int e = tid; e < n * b; e += NT) {
+    const int k = e / b, cw = e % b;
+    Ws[e] = Tb[(int64_t)k * ld + wo + cw];
+  }
+  if (passes > 0)
+    for (int e = tid; e < n * q; e += NT) {
+      const int k = e / q, j = e % q;
+      Bs[e] = Tb[(int64_t)k * ld + bcol(j)];
+    }
+  __syncthreads();
+  const int G = QB >= NT ? 1 : imin(4, NT / QB);
+  for (int pass = 0; pass < passes; ++pass) {
+    // P = [V X]^H W, rows split into G groups per output
+    for (int t = tid; t < G * QB; t += NT) {
+      const int o = t % QB, g = t / QB;
+      const int j = o / b, cw = o % b;
+      const int r0 = (int)((int64_t)g * n / G), r1 = (int)((int64_t)(g + 1) * n / G);
+      T a0 = zero_<T>(), a1 = zero_<T>(), a2 = zero_<T>(), a3 = zero_<T>();
+      int r = r0;
+      for (; r + 3 < r1; r += 4) {
+        a0 = madc_(Bs[(size_t)r * q + j], Ws[(size_t)r * b + cw], a0);
+        a1 = madc_(Bs[(size_t)(r + 1) * q + j], Ws[(size_t)(r + 1) * b + cw], a1);
+        a2 = madc_(Bs[(size_t)(r + 2) * q + j], Ws[(size_t)(r + 2) * b + cw], a2);
+        a3 = madc_(Bs[(size_t)(r + 3) * q + j], Ws[(size_t)(r + 3) * b + cw], a3);
+      }
+      for (; r < r1; ++r) a0 = madc_(Bs[(size_t)r * q + j], Ws[(size_t)r * b + cw], a0);
+      Pp[(size_t)g * QB + o] = add_(add_(a0, a1), add_(a2, a3));
+    }
+    __syncthreads();
+    for (int o = tid; o < QB; o += NT) {
+      T sum = Pp[o];
+      for (int g = 1; g < G; ++g) sum = add_(sum, Pp[(size_t)g * QB + o]);
+      P[o] = sum;
+    }
+    __syncthreads();
+    // W -= [V X] P
+    for (int e = tid; e < n * b; e += NT) {
+      const int k = e / b, cw = e % b;
+      T w = Ws[e];
+      for (int j = 0; j < q; ++j) w = sub_(w, mul_(Bs[(size_t)k * q + j], P[j * b + cw]));
+      Ws[e] = w;
+    }
+    __syncthreads();
+  }
+  // Householder QR of W (n x b) in place; v (scaled by 1/(alpha - beta)) stored below the diagonal
+  for (int j = 0; j < b; ++j) {
+    for (int cc = j + warp; cc < b; cc += NW) {
+      T a0 = zero_<T>(), a1 = zero_<T>();
+      int k = j + 1 + lane;
+      for (; k + 32 < n; k += 64) {
+        a0 = madc_(Ws[(size_t)k * b + j], Ws[(size_t)k * b + cc], a0);
+        a1 = madc_(Ws[(size_t)(k + 32) * b + j], Ws[(size_t)(k + 32) * b + cc], a1);
+      }
+      if (k < n) a0 = madc_(Ws[(size_t)k * b + j], Ws[(size_t)k * b + cc], a0);
+      const T s = warp_sum(add_(a0, a1));
+      if (lane == 0) sv[cc] = s;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      T tau, beta, inv_ab;
+      householder_scalars(Ws[(size_t)j * b + j], re_(sv[j]), &tau, &beta, &inv_ab);
+      tauv[j] = tau;
+      dg[j] = beta;
+      sh_inv = inv_ab;
+      for (int cc = j + 1; cc < b; ++cc) sv[cc] = add_(Ws[(size_t)j * b + cc], mul_(conj_(inv_ab), sv[cc]));
+    }
+    __syncthreads();
+    const T tau = tauv[j], inv_ab = sh_inv;
+    for (int e = tid; e < (n - j) * b; e += NT) {
+      const int k = j + e / b, cc = e % b;
+      if (cc <= j) continue;
+      const T f = mul_(conj_(tau), sv[cc]);
+      const T vk = (k == j) ? from_real<T>(1.0) : mul_(Ws[(size_t)k * b + j], inv_ab);
+      Ws[(size_t)k * b + cc] = sub_(Ws[(size_t)k * b + cc], mul_(vk, f));
+    }
+    __syncthreads();
+    for (int k = j + 1 + tid; k < n; k += NT) Ws[(size_t)k * b + j] = mul_(Ws[(size_t)k * b + j], inv_ab);
+    if (tid == 0) Ws[(size_t)j * b + j] = dg[j];
+    __syncthreads();
+  }
+  // Q = H_0 ... H_{b-1} I(:, 0:b) into E (the space of [V X]), phases of diag(R) folded in
+  T* E = Bs;
+  for (int e = tid; e < n * b; e += NT) {
+    const int k = e / b, cc = e % b;
+    E[e] = (k == cc) ? from_real<T>(1.0) : zero_<T>();
+  }
+  __syncthreads();
+  for (int j = b - 1; j >= 0; --j) {
+    for (int cc = j + warp; cc < b; cc += NW) {
+      T a0 = zero_<T>(), a1 = zero_<T>();
+      int k = j + 1 + lane;
+      for (; k + 32 < n; k += 64) {
+        a0 = madc_(Ws[(size_t)k * b + j], E[(size_t)k * b + cc], a0);
+        a1 = madc_(Ws[(size_t)(k + 32) * b + j], E[(size_t)(k + 32) * b + cc], a1);
+      }
+      if (k < n) a0 = madc_(Ws[(size_t)k * b + j], E[(size_t)k * b + cc], a0);
+      const T s = warp_sum(add_(a0, a1));
+      if (lane == 0) sv[cc] = mul_(tauv[j], add_(E[(size_t)j * b + cc], s));
+    }
+    __syncthreads();
+    for (int e = tid; e < (n - j) * b; e += NT) {
+      const int k = j + e / b, cc = e % b;
+      if (cc < j) continue;
+      const T vk = (k == j) ? from_real<T>(1.0) : Ws[(size_t)k * b + j];
+      E[(size_t)k * b + cc] = sub_(E[(size_t)k * b + cc], mul_(vk, sv[cc]));
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < n * b; e += NT) {
+    const int k = e / b, cc = e % b;
+    const T v = mul_(E[e], phase_(dg[cc]));
+    E[e] = v;
+    Tb[(int64_t)k * ld + wo + cc] = v;
+  }
+  if (wd.Wsl == nullptr) return;
+  // digits of the final W (real FP64 only): column exponents, then digit tiles
+  __syncthreads();
+  const int BP = wd.BP, N = split::SL * BP;
+  bool bad = false;
+  for (int cc = warp; cc < BP; cc += NW) {
+    double mx = 0;
+    if (cc < b)
+      for (int k = lane; k < n; k += 32) {
+        const double a = fabs(re_(E[(size_t)k * b + cc]));
+        bad |= !(a <= 1.7976931348623157e308);
+        mx = fmax(mx, a);
+      }
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) {
+      Fs[cc] = split::group_exp(mx);
+      wd.F[cc] = Fs[cc];
+    }
+  }
+  if (__syncthreads_or(bad) && tid == 0) atomicOr(err, DEV_ERR_NONFINITE);
+  const int64_t total = wd.NKB * split::TK * BP;
+  for (int64_t e = tid; e < total; e += NT) {
+    const int j = (int)(e % BP);
+    const int64_t k = e / BP;
+    const double x = (k < n && j < b) ? re_(E[(size_t)k * b + j]) : 0.0;
+    int d[split::SL];
+    split::split8(x, Fs[j], d);
+    uint16_t* out = wd.Wsl + (size_t)(k / split::TK) * (N * split::TK);
+    const int kk = (int)(k % split::TK);
+#pragma unroll
+    for (int qd = 0; qd < split::SL; ++qd) out[split::core_off(qd * BP + j, kk, N)] = split::bf16_of(d[qd]);
+  }
+  (void)red;
+}
+
 // V0 = Vt(:, n-b:n) (sketch precision, col-major n x n) -> T columns [0, b) in double/complex128
 template <class S, class T>
 __global__ void take_start_kernel(const S* Vt, int n, int b, T* Tb, int64_t ld) {
@@ -618,10 +1048,14 @@ static int tsqr_rp(int c) { return imin(32, 256 / pow2_at_least(c)); }
 
 static size_t tsqr_level_smem(int c, int CH, size_t esz) { return (size_t)(c + CH) * c * esz; }
 
+// Level 1: up to three CTAs per SM (one chunk each when m allows): the level is bound by FP64
+// issue (about 2 m c^2 FMAs), so all SMs' FP64 pipes take part.
 static int64_t tsqr_level1_ctas(int64_t m, int c, size_t esz) {
   const int CH = tsqr_chunk(c, esz);
   return imin<int64_t>(3 * (int64_t)num_sms(), imax<int64_t>(1, (m + CH - 1) / CH));
 }
+
+static constexpr int kTsqrFan = 20;   // R factors merged per CTA in the upper levels
 
 size_t tsqr_workspace_bytes(int64_t m, int c, size_t esz) {
   const int64_t g1 = tsqr_level1_ctas(m, c, esz);
@@ -647,13 +1081,14 @@ int tsqr_impl(const T* X, int64_t m, int c, int64_t ldx, T* R, void* work, size_
   tsqr_level_kernel<T><<<(int)grid, 256, smem, st>>>(X, m, c, ldx, rpc, CH, RP, buf[0]);
   RL_CHECK_LAUNCH();
   int cur = 0;
-  // fixed-order tree: each CTA of the next level stacks the R factors of up to FAN CTAs
-  const int FAN = imax(2, imin(32, CH / c));
+  // fixed-order tree of triangular merges, up to kTsqrFan factors per CTA (balanced)
+  const int fan = (int)imax<int64_t>(2, imin<int64_t>(kTsqrFan, (int64_t)(max_smem_optin() * 9 / 10) / ((int64_t)c * c * esz)));
   while (grid > 1) {
-    const int64_t rows = grid * c;
-    const int64_t rpc2 = (int64_t)FAN * c;
-    const int64_t g2 = (rows + rpc2 - 1) / rpc2;
-    tsqr_level_kernel<T><<<(int)g2, 256, smem, st>>>(buf[cur], rows, c, c, rpc2, CH, RP, buf[cur ^ 1]);
+    const int64_t g2 = (grid + fan - 1) / fan;
+    const int F = (int)((grid + g2 - 1) / g2);
+    const size_t msmem = (size_t)F * c * c * esz;
+    RL_TRY(allow_dynamic_smem(tsqr_merge_kernel<T>, msmem));
+    tsqr_merge_kernel<T><<<(int)g2, 256, msmem, st>>>(buf[cur], (int)grid, c, F, RP, buf[cur ^ 1]);
     RL_CHECK_LAUNCH();
     cur ^= 1;
     grid = g2;
@@ -677,6 +1112,7 @@ int rr_small_launch(const T* Rt, int c, int b, double* theta, T* K, size_t k_cap
                 (c + 4) * sizeof(int) + 16 + (size_t)pdim * b * sizeof(T);
   RL_TRY(allow_dynamic_smem(rr_small_kernel<T>, smem));
   int threads = min(1024, max(64, ((c + 1) / 2) * 32));
+  if (std::is_same<T, double>::value && c <= 16) threads = 128;   // two Jacobi pairs per warp
   rr_small_kernel<T><<<1, threads, smem, st>>>(Rt, c, b, theta, K, info);
   RL_CHECK_LAUNCH();
   return RLOBPCG_OK;
@@ -760,14 +1196,29 @@ template int trimul_launch<cd, cd>(const cd*, int, const cd*, int64_t, int, cd*,
 template int trimul_launch<cd, cf>(const cf*, int, const cd*, int64_t, int, cd*, int64_t, int, int, cudaStream_t);
 
 template <class T>
-int bcgs2_orth_launch(T* Tb, int n, int b, int64_t ld, int wo, int nx, T* E, int passes, cudaStream_t st) {
+int bcgs2_orth_launch(T* Tb, int n, int b, int64_t ld, int wo, int nx, T* E, int passes, cudaStream_t st,
+                      const split::WDigits* wd, int* err, bool* digits_done) {
+  if (digits_done) *digits_done = false;
+  const int q = b + nx;
+  const size_t smem_s = ((size_t)n * (q + b) + 5 * (size_t)q * b + 3 * b) * sizeof(T) + 16 * 8 * sizeof(double) + 64;
+  if (smem_s <= max_smem_optin() - 1024) {
+    split::WDigits w{};
+    if (wd && wd->Wsl && sizeof(T) == sizeof(double) && b <= wd->BP) w = *wd;
+    RL_TRY(allow_dynamic_smem(bcgs2_orth_smem_kernel<T>, smem_s));
+    bcgs2_orth_smem_kernel<T><<<1, 256, smem_s, st>>>(Tb, n, b, ld, wo, nx, passes, w, err);
+    RL_CHECK_LAUNCH();
+    if (digits_done) *digits_done = w.Wsl != nullptr;
+    return RLOBPCG_OK;
+  }
   const size_t smem = ((size_t)2 * b * b + 3 * b) * sizeof(T);
   bcgs2_orth_kernel<T><<<1, 1024, smem, st>>>(Tb, n, b, ld, wo, nx, E, passes);
   RL_CHECK_LAUNCH();
   return RLOBPCG_OK;
 }
-template int bcgs2_orth_launch<double>(double*, int, int, int64_t, int, int, double*, int, cudaStream_t);
-template int bcgs2_orth_launch<cd>(cd*, int, int, int64_t, int, int, cd*, int, cudaStream_t);
+template int bcgs2_orth_launch<double>(double*, int, int, int64_t, int, int, double*, int, cudaStream_t,
+                                       const split::WDigits*, int*, bool*);
+template int bcgs2_orth_launch<cd>(cd*, int, int, int64_t, int, int, cd*, int, cudaStream_t, const split::WDigits*,
+                                   int*, bool*);
 
 template <class S, class T>
 int take_start_launch(const S* Vt, int n, int b, T* Tb, int64_t ld, cudaStream_t st) {

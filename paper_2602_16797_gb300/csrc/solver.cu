@@ -1,8 +1,10 @@
 // Host driver of one RLOBPCG solve (Algorithm 2 of arXiv 2602.16797) on the GPU.
 //
 // The plan owns every device buffer of a solve; solve() issues the kernels of sketch.cu,
-// factor.cu, gram.cu and small.cu on the plan's stream and reads back only the b residual
-// norms and b Ritz values per iteration, which the host-side stopping rule (Sec. 2.1) needs.
+// factor.cu, gram.cu / gram_tc.cu and small.cu on the plan's stream. Per iteration it copies
+// back only the b residual norms and b Ritz values the host-side stopping rule (Sec. 2.1) needs,
+// asynchronously into a pinned history; the host waits for the GPU only on the iterations where
+// the rule is tested (every check_every iterations), so it queues the iterations in between.
 #include <math.h>
 #include <string.h>
 
@@ -11,6 +13,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "split.cuh"
 
 namespace rl {
 
@@ -37,7 +40,7 @@ size_t split_prep_bytes(int64_t m, int64_t n);
 size_t split_work_bytes(int64_t m, int64_t n, int b);
 int split_prepare(const double* A, int64_t m, int64_t n, int64_t lda, void* prep, size_t prep_bytes, cudaStream_t st);
 int split_gram(const void* prep, int64_t m, int64_t n, const double* W, int b, int64_t ldw, double* AW, int64_t ldaw,
-               double* G, int64_t ldg, void* work, size_t work_bytes, int resid_mode, int* err, cudaEvent_t mid,
+               double* G, int64_t ldg, void* work, size_t work_bytes, int flags, int* err, cudaEvent_t mid,
                cudaStream_t st);
 size_t tsqr_workspace_bytes(int64_t m, int c, size_t esz);
 template <class T>
@@ -53,7 +56,9 @@ template <class T, class S>
 int precond_launch(const S* Rinv_r, const S* Rinv_c, int n, int b, const T* Rs, T* Y, T* Tb, int64_t ld, int wo,
                    cudaStream_t st);
 template <class T>
-int bcgs2_orth_launch(T* Tb, int n, int b, int64_t ld, int wo, int nx, T* E, int passes, cudaStream_t st);
+int bcgs2_orth_launch(T* Tb, int n, int b, int64_t ld, int wo, int nx, T* E, int passes, cudaStream_t st,
+                      const split::WDigits* wd = nullptr, int* err = nullptr, bool* digits_done = nullptr);
+split::WDigits split_w_digits(void* work, int64_t m, int64_t n, int b);
 template <class S, class T>
 int take_start_launch(const S* Vt, int n, int b, T* Tb, int64_t ld, cudaStream_t st);
 template <class T>
@@ -111,6 +116,11 @@ struct rlobpcg_plan_s {
   void* twork = nullptr;
   size_t twork_bytes = 0;
   cudaEvent_t ev[10] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  // Per-iteration Gram timing events (3 per slot, a ring) and the pinned history of residual
+  // norms and Ritz values, copied asynchronously; the host synchronises only to test the stop rule.
+  std::vector<cudaEvent_t> gev;
+  double* hist_h = nullptr;
+  int hist_slots = 0;
   std::vector<void*> owned;
   size_t bytes = 0;          // device bytes owned by the plan (excluding a host-A copy)
 };
@@ -142,7 +152,14 @@ void free_plan(rlobpcg_plan_s* p) {
   cudaStreamSynchronize(p->st);
   for (auto& e : p->ev)
     if (e) cudaEventDestroy(e);
+  for (auto& e : p->gev)
+    if (e) cudaEventDestroy(e);
+  p->gev.clear();
+  if (p->hist_h) cudaFreeHost(p->hist_h);
+  p->hist_h = nullptr;
 }
+
+constexpr int kRing = 16;   // slots of per-iteration timing events
 
 bool is_device_ptr(const void* ptr) {
   cudaPointerAttributes a;
@@ -178,11 +195,12 @@ struct StopRule {
 // CUDA cores or, for plans with gram_split, on the tensor cores from the digits of A.
 template <class T>
 int gram_pass(rlobpcg_plan_s* p, const T* A, int64_t lda, const T* W, T* AW, T* G, int resid_mode,
-              cudaEvent_t mid = nullptr) {
+              cudaEvent_t mid = nullptr, bool w_ready = false) {
   const int64_t ld = 3 * p->b;
   if (p->split)
     return split_gram(p->sprep, p->m, p->n, (const double*)W, p->b, ld, (double*)AW, ld, (double*)G, ld, p->swork,
-                      p->swork_bytes, resid_mode, p->err, mid, p->st);
+                      p->swork_bytes, (resid_mode ? split::SPLIT_RESID : 0) | (w_ready ? split::SPLIT_W_READY : 0),
+                      p->err, mid, p->st);
   return gram_dispatch(A, p->m, p->n, lda, p->dtype, W, p->b, ld, AW, ld, G, ld, p->gwork, p->gwork_bytes, resid_mode,
                        p->err, p->st);
 }
@@ -201,6 +219,7 @@ int solve_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, double tau, double* s
   double gram_ms = 0, gram_ab_ms = 0, gram_atb_ms = 0;
   int gram_passes = 0;
   RL_CUDA(cudaMemsetAsync(p->err, 0, sizeof(int), st));
+  RL_CUDA(cudaMemsetAsync(p->info, 0, 2 * sizeof(int), st));
   RL_CUDA(cudaEventRecord(p->ev[0], st));
   RL_TRY(nonfinite_scan_launch<T>(A, m, n, lda, p->err, st));
   int herr = 0;
@@ -252,13 +271,16 @@ int solve_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, double tau, double* s
   if (herr & DEV_ERR_NONFINITE) return RLOBPCG_ERR_NONFINITE;
 
   // Sketch-and-solve start and initial Rayleigh-Ritz (Alg. 2, lines 4-7)
-  RL_TRY(bcgs2_orth_launch<T>(Tb, n, b, ld, 0, 0, (T*)p->E, 0, st));
+  split::WDigits wd{};
+  if (p->split) wd = split_w_digits(p->swork, m, n, b);
+  bool w_ready = false;
+  RL_TRY(bcgs2_orth_launch<T>(Tb, n, b, ld, 0, 0, (T*)p->E, 0, st, p->split ? &wd : nullptr, p->err, &w_ready));
   if (p->split) {
     RL_CUDA(cudaEventRecord(p->ev[8], st));
     RL_TRY(split_prepare((const double*)A, m, n, lda, p->sprep, p->sprep_bytes, st));
     RL_CUDA(cudaEventRecord(p->ev[9], st));
   }
-  RL_TRY(gram_pass<T>(p, A, lda, Tb, ATb, GTb, 0));
+  RL_TRY(gram_pass<T>(p, A, lda, Tb, ATb, GTb, 0, nullptr, w_ready));
   RL_TRY(tsqr_impl<T>(ATb, m, b, ld, (T*)p->Rt, p->twork, p->twork_bytes, st));
   RL_TRY(rr_small_launch<T>((const T*)p->Rt, b, b, p->theta, (T*)p->K, p->K_cap, p->info, st));
   RL_TRY(update_launch<T>(Tb, n, ATb, m, GTb, ld, b, b, (const T*)p->K, st));
@@ -266,11 +288,13 @@ int solve_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, double tau, double* s
   RL_CUDA(cudaEventRecord(p->ev[2], st));
 
   StopRule hist;
-  std::vector<double> hr(b), ht(b);
-  RL_CUDA(cudaMemcpyAsync(hr.data(), p->res_norm, b * sizeof(double), cudaMemcpyDeviceToHost, st));
-  RL_CUDA(cudaStreamSynchronize(st));
-  hist.r.push_back(hr);
-  hist.th.push_back(std::vector<double>(b, std::numeric_limits<double>::infinity()));
+  {
+    std::vector<double> hr(b);
+    RL_CUDA(cudaMemcpyAsync(hr.data(), p->res_norm, b * sizeof(double), cudaMemcpyDeviceToHost, st));
+    RL_CUDA(cudaStreamSynchronize(st));
+    hist.r.push_back(hr);
+    hist.th.push_back(std::vector<double>(b, std::numeric_limits<double>::infinity()));
+  }
 
   const int fixed = p->opts.fixed_iters;
   const int max_iter = fixed > 0 ? fixed : p->opts.max_iter;
@@ -280,19 +304,42 @@ int solve_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, double tau, double* s
   int nx = 0, it = 0, stop = fixed > 0 ? RLOBPCG_STOP_FIXED : RLOBPCG_STOP_MAX_ITER;
   int matvecs = b;
   const double* theta_s = p->theta;
+  int drained = 0;   // iterations whose history and timings the host has read
+  auto drain = [&](int upto) -> int {
+    for (int t = drained; t < upto; ++t) {
+      const double* slot = p->hist_h + (size_t)(t + 1) * 2 * b;
+      hist.r.emplace_back(slot, slot + b);
+      hist.th.emplace_back(slot + b, slot + 2 * b);
+      cudaEvent_t* e = &p->gev[(size_t)(t % kRing) * 3];
+      float gms = 0;
+      RL_CUDA(cudaEventElapsedTime(&gms, e[0], e[2]));
+      gram_ms += gms;
+      ++gram_passes;
+      if (p->split) {
+        RL_CUDA(cudaEventElapsedTime(&gms, e[0], e[1]));
+        gram_ab_ms += gms;
+        RL_CUDA(cudaEventElapsedTime(&gms, e[1], e[2]));
+        gram_atb_ms += gms;
+      }
+    }
+    drained = upto;
+    return RLOBPCG_OK;
+  };
   for (int i = 0; i < max_iter; ++i) {
     // W = P (P^* R_i), then BCGS2 against [V X] and Orth
     RL_TRY((precond_launch<T, S>((const S*)p->Rinv_r, (const S*)p->Rinv_c, n, b, (const T*)p->Rs, (T*)p->Y, Tb, ld, b, st)));
-    RL_TRY(bcgs2_orth_launch<T>(Tb, n, b, ld, b, nx, (T*)p->E, 2, st));
-    // A W and A^H (A W) in one pass over A (timed with events on this stream)
-    RL_CUDA(cudaEventRecord(p->ev[5], st));
-    RL_TRY(gram_pass<T>(p, A, lda, Tb + b, ATb + b, GTb + b, 0, p->split ? p->ev[7] : nullptr));
-    RL_CUDA(cudaEventRecord(p->ev[6], st));
-    matvecs += b;
-    // Rayleigh-Ritz by SVD of A_T (TSQR + Jacobi of R_T)
+    RL_TRY(bcgs2_orth_launch<T>(Tb, n, b, ld, b, nx, (T*)p->E, 2, st, p->split ? &wd : nullptr, p->err, &w_ready));
     const int c = 2 * b + nx;
+    cudaEvent_t* e = &p->gev[(size_t)(i % kRing) * 3];
+    RL_CUDA(cudaEventRecord(e[0], st));
+    // A W and A^H (A W) (the split path records the boundary between its two kernels in e[1])
+    RL_TRY(gram_pass<T>(p, A, lda, Tb + b, ATb + b, GTb + b, 0, p->split ? e[1] : nullptr, w_ready));
+    RL_CUDA(cudaEventRecord(e[2], st));
+    // Rayleigh-Ritz by SVD of A_T (TSQR + Jacobi of R_T). Running it on a second stream beside
+    // the A^T (A W) kernel was measured slower on GB300 (both contend for the FP64 pipes).
     RL_TRY(tsqr_impl<T>(ATb, m, c, ld, (T*)p->Rt, p->twork, p->twork_bytes, st));
     RL_TRY(rr_small_launch<T>((const T*)p->Rt, c, b, p->theta, (T*)p->K, p->K_cap, p->info, st));
+    matvecs += b;
     theta_s = p->theta + (c - b);
     RL_TRY(update_launch<T>(Tb, n, ATb, m, GTb, ld, c, b, (const T*)p->K, st));
     if (refresh > 0 && (i + 1) % refresh == 0) {
@@ -300,28 +347,19 @@ int solve_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, double tau, double* s
       matvecs += b;
     }
     RL_TRY((residual_launch<T>(Tb, GTb, n, b, ld, theta_s, (T*)p->Res, p->res_norm, (T*)p->Rs, p->err, st)));
-    RL_CUDA(cudaMemcpyAsync(hr.data(), p->res_norm, b * sizeof(double), cudaMemcpyDeviceToHost, st));
-    RL_CUDA(cudaMemcpyAsync(ht.data(), theta_s, b * sizeof(double), cudaMemcpyDeviceToHost, st));
-    RL_CUDA(cudaStreamSynchronize(st));
-    {
-      float gms = 0;
-      RL_CUDA(cudaEventElapsedTime(&gms, p->ev[5], p->ev[6]));
-      gram_ms += gms;
-      ++gram_passes;
-      if (p->split) {
-        RL_CUDA(cudaEventElapsedTime(&gms, p->ev[5], p->ev[7]));
-        gram_ab_ms += gms;
-        RL_CUDA(cudaEventElapsedTime(&gms, p->ev[7], p->ev[6]));
-        gram_atb_ms += gms;
-      }
-    }
-    hist.r.push_back(hr);
-    hist.th.push_back(ht);
+    double* slot = p->hist_h + (size_t)(i + 1) * 2 * b;
+    RL_CUDA(cudaMemcpyAsync(slot, p->res_norm, b * sizeof(double), cudaMemcpyDeviceToHost, st));
+    RL_CUDA(cudaMemcpyAsync(slot + b, theta_s, b * sizeof(double), cudaMemcpyDeviceToHost, st));
     it = i + 1;
     nx = b;
-    if (fixed <= 0 && i % check_every == 0 && hist.check(i, sigma11, tau, stag)) {
-      stop = RLOBPCG_STOP_CONVERGED;
-      break;
+    const bool check = fixed <= 0 && i % check_every == 0;
+    if (check || i + 1 == max_iter || i + 1 - drained >= kRing - 1) {
+      RL_CUDA(cudaStreamSynchronize(st));
+      RL_TRY(drain(i + 1));
+      if (check && hist.check(i, sigma11, tau, stag)) {
+        stop = RLOBPCG_STOP_CONVERGED;
+        break;
+      }
     }
   }
   RL_CUDA(cudaEventRecord(p->ev[3], st));
@@ -345,6 +383,8 @@ int solve_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, double tau, double* s
     }
   }
   RL_CUDA(cudaMemcpyAsync(&herr, p->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  int rr_stats[2] = {0, 0};
+  RL_CUDA(cudaMemcpyAsync(rr_stats, p->info, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
   RL_CUDA(cudaEventRecord(p->ev[4], st));
   RL_CUDA(cudaStreamSynchronize(st));
   if (info) {
@@ -362,6 +402,8 @@ int solve_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, double tau, double* s
     info->gram_passes = gram_passes;
     info->kernel_launches = (int)(launch_count() - launches0);
     info->jacobi_sweeps = sweeps;
+    info->rr_sweeps = rr_stats[0];
+    info->rr_calls = rr_stats[1];
     info->ms_gram_ab = gram_ab_ms;
     info->ms_gram_atb = gram_atb_ms;
     info->ms_split_a = 0;
@@ -536,6 +578,21 @@ extern "C" int rlobpcg_plan(rlobpcg_plan_t* out, int64_t m, int64_t n, int k, in
   if (rc) { free_plan(p); delete p; return rc; }
   for (auto& e : p->ev) {
     if (cudaEventCreate(&e) != cudaSuccess) { free_plan(p); delete p; return RLOBPCG_ERR_CUDA; }
+  }
+  p->gev.assign((size_t)kRing * 3, nullptr);
+  for (auto& e : p->gev) {
+    if (cudaEventCreate(&e) != cudaSuccess) { free_plan(p); delete p; return RLOBPCG_ERR_CUDA; }
+  }
+  {
+    const int iters = std::max(o.max_iter, o.fixed_iters);
+    p->hist_slots = iters + 2;
+    if (cudaMallocHost((void**)&p->hist_h, (size_t)p->hist_slots * 2 * b * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      set_last_error("plan: pinned host buffer for the stop-rule history", __FILE__, __LINE__);
+      free_plan(p);
+      delete p;
+      return RLOBPCG_ERR_CUDA;
+    }
   }
   *out = p;
   return RLOBPCG_OK;

@@ -1,0 +1,60 @@
+// Digit split of FP64 values for the tensor-core Gram pass (the Ozaki scheme of gram_tc.cu):
+// a group of values with max |x| < 2^E is written as rint(x 2^(55-E)) in balanced base 128,
+//     x ~= 2^(E+1) sum_{p=0}^{7} d_p 2^(-7(p+1)),   d_p integers in [-64, 64],
+// each digit exact in bf16. Shared by gram_tc.cu (A, A W) and small.cu (W, at the end of the
+// BCGS2 + Orth kernel that produces it).
+#pragma once
+#include <cstdint>
+
+namespace rl {
+namespace split {
+
+constexpr int SL = 8;   // digits per FP64 value
+constexpr int TK = 16;  // K depth of one MMA / one digit tile
+
+__device__ __forceinline__ int group_exp(double amax) {
+  int e = 0;
+  frexp(amax, &e);   // amax = f 2^e with f in [0.5, 1), so every |x| <= amax is < 2^e
+  return amax > 0 ? e : 0;
+}
+
+// x 2^k: one exact multiply by a power of two built from its bits (FP64 instructions are the
+// scarce resource on GB300); scalbn only for k outside the normal exponent range
+__device__ __forceinline__ double mul_pow2(double x, int k) {
+  return (k >= -1022 && k <= 1023) ? x * __longlong_as_double((long long)(k + 1023) << 52) : scalbn(x, k);
+}
+
+__device__ __forceinline__ void split8(double x, int E, int (&d)[SL]) {
+  long long V = __double2ll_rn(mul_pow2(x, 55 - E));
+#pragma unroll
+  for (int p = SL - 1; p > 0; --p) {
+    const int r = (int)(V & 127);
+    const int dd = r - ((r & 64) << 1);   // balanced remainder in [-64, 63]
+    d[p] = dd;
+    V = (V - dd) >> 7;                    // exact: V - dd is a multiple of 128
+  }
+  d[0] = (int)V;                          // |V| <= 64 here since |V| <= 2^55 at the start
+}
+
+__device__ __forceinline__ uint16_t bf16_of(int v) { return (uint16_t)(__float_as_uint((float)v) >> 16); }
+
+// element (row, kk) of an R-row x 16 digit tile in tcgen05's no-swizzle K-major core-matrix order
+__device__ __forceinline__ int core_off(int row, int kk, int R) {
+  return (kk >> 3) * (R * 8) + (row >> 3) * 64 + (row & 7) * 8 + (kk & 7);
+}
+
+// Where the digits of W (n x b) go: Wsl[kb][N x 16 tile], N = 8 x BP, row q * BP + j of the tile
+// holding digit q of W[kb * 16 + kk][j]; F[j] the exponent of column j. NKB = ceil(n / 16).
+struct WDigits {
+  uint16_t* Wsl = nullptr;
+  int* F = nullptr;
+  int64_t NKB = 0;
+  int BP = 0;
+};
+
+// flags of split_gram
+constexpr int SPLIT_RESID = 1;    // G = A^T Y for the given Y = AW (no first product)
+constexpr int SPLIT_W_READY = 2;  // the digits of W are already in the work buffer
+
+}  // namespace split
+}  // namespace rl

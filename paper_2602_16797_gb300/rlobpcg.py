@@ -43,7 +43,8 @@ class rlobpcg_info(ctypes.Structure):
     _fields_ = [("iters", c_int), ("matvecs", c_int), ("stop_reason", c_int), ("block", c_int),
                 ("sigma11", c_double), ("ms_sketch", c_double), ("ms_factor", c_double), ("ms_iterate", c_double),
                 ("ms_total", c_double), ("ms_gram", c_double), ("gram_passes", c_int), ("kernel_launches", c_int),
-                ("jacobi_sweeps", c_int), ("ms_gram_ab", c_double), ("ms_gram_atb", c_double), ("ms_split_a", c_double)]
+                ("jacobi_sweeps", c_int), ("ms_gram_ab", c_double), ("ms_gram_atb", c_double), ("ms_split_a", c_double),
+                ("rr_sweeps", c_int), ("rr_calls", c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
