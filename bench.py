@@ -398,6 +398,7 @@ def run_ours(args, rank, world, local_rank):
                          "factor": statistics.mean(x.ms_factor for x in infos),
                          "iterate": statistics.mean(x.ms_iterate for x in infos),
                          "gram_per_pass": avg_s * 1e3,
+                         "per_iteration": statistics.mean(x.ms_iterate / max(x.iters, 1) for x in infos),
                          "split_a": statistics.mean(x.ms_split_a for x in infos)},
             "sigma": [float(x) for x in sigma.cpu().numpy()],
             "roofline": roofline, "clocks": clk,

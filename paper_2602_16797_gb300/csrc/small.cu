@@ -12,6 +12,7 @@
 //     diag(R) real non-negative).
 // State layout: T, A_T and G_T are row-major with leading dimension 3b and column blocks
 // [V | W | X] (X absent, i.e. c = 2b, in iteration 0).
+#include <cooperative_groups.h>
 #include <type_traits>
 
 #include "common.cuh"
@@ -214,24 +215,20 @@ __device__ inline int rr_slot(int k, int r, int N) { return k == 0 ? 0 : ((k - 1
 // is orthogonal to FP64 rounding for any t; an FP32-accurate angle leaves ~1e-7 of the pair's
 // cosine, which the next sweep removes. A pair that needs no rotation uses (c, s) = (1, 0), so
 // both halves execute the same instructions. Returns the number of sweeps.
-__device__ int jacobi_pairs16(double* X, double* V, int c, int N, double tol, double tiny2) {
+__device__ int jacobi_pairs16(double* X, double* V, int c, int N, double tol, double tiny2, const uint8_t* sched,
+                              int max_sweeps) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
   const int half = lane >> 4, row = lane & 15;
   const double tol2 = tol * tol;
   int sweep = 0;
-  for (; sweep < 60; ++sweep) {
+  for (; sweep < max_sweeps; ++sweep) {
     int rotated = 0;
     for (int r = 0; r < N - 1; ++r) {
       for (int p0 = 2 * warp; p0 < N / 2; p0 += 2 * nw) {   // warp-uniform
         const int pi = p0 + half;
-        int pp = 0, qq = 0;
-        bool valid = pi < N / 2;
-        if (valid) {
-          pp = rr_slot(pi, r, N);
-          qq = rr_slot(N - 1 - pi, r, N);
-          if (pp > qq) { const int t = pp; pp = qq; qq = t; }
-          valid = qq < c;
-        }
+        const int code = pi < N / 2 ? sched[r * 8 + pi] : 0xFF;
+        const int pp = code & 15, qq = code >> 4;
+        const bool valid = code != 0xFF;
         const bool live = valid && row < c;
         const double xp = live ? X[pp * c + row] : 0.0, xq = live ? X[qq * c + row] : 0.0;
         double a = xp * xp, bb = xq * xq, g = xp * xq;
@@ -271,54 +268,81 @@ __device__ int jacobi_pairs16(double* X, double* V, int c, int N, double tol, do
   return sweep;
 }
 
+// Does any column pair of X (c x c, column-major) still fail the Jacobi test? One pass over all
+// pairs (c (c - 1) / 2 dot products of length c) instead of a whole confirming sweep.
+__device__ bool jacobi_pending(const double* X, int c, double tol, double tiny2) {
+  const double tol2 = tol * tol;
+  int bad = 0;
+  for (int e = threadIdx.x; e < c * c; e += blockDim.x) {
+    const int i = e / c, j = e % c;
+    if (j <= i) continue;
+    double a = 0, bb = 0, g = 0;
+    for (int r = 0; r < c; ++r) {
+      const double x = X[i * c + r], y = X[j * c + r];
+      a = fma(x, x, a);
+      bb = fma(y, y, bb);
+      g = fma(x, y, g);
+    }
+    bad |= (g * g > tol2 * a * bb) && a > tiny2 && bb > tiny2;
+  }
+  return __syncthreads_or(bad) != 0;
+}
+
 // The same sweeps in FP32 (on GB300 the FP32 pipe issues ~64x the FP64 rate): used on a scaled
 // FP32 copy of R_T to find a V that nearly diagonalises it (cosines ~ c u_32).
-__device__ int jacobi_pairs16_f32(float* X, float* V, int c, int N, float tol, float tiny2) {
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
-  const int half = lane >> 4, row = lane & 15;
+__device__ int jacobi_pairs16_f32(float* X, float* V, int c, int N, float tol, float tiny2, const uint8_t* sched) {
+  // one warp: eight pairs per round, four lanes per pair, rows ql, ql + 4, ql + 8, ql + 12
+  const int lane = threadIdx.x & 31, pi = lane >> 2, ql = lane & 3;
   const float tol2 = tol * tol;
   int sweep = 0;
-  for (; sweep < 40; ++sweep) {
+  for (; sweep < 12; ++sweep) {
     int rotated = 0;
     for (int r = 0; r < N - 1; ++r) {
-      for (int p0 = 2 * warp; p0 < N / 2; p0 += 2 * nw) {
-        const int pi = p0 + half;
-        int pp = 0, qq = 0;
-        bool valid = pi < N / 2;
-        if (valid) {
-          pp = rr_slot(pi, r, N);
-          qq = rr_slot(N - 1 - pi, r, N);
-          if (pp > qq) { const int t = pp; pp = qq; qq = t; }
-          valid = qq < c;
-        }
-        const bool live = valid && row < c;
-        const float xp = live ? X[pp * c + row] : 0.0f, xq = live ? X[qq * c + row] : 0.0f;
-        float a = xp * xp, bb = xq * xq, g = xp * xq;
+      const int code = pi < N / 2 ? sched[r * 8 + pi] : 0xFF;
+      const int pp = code & 15, qq = code >> 4;
+      const bool valid = code != 0xFF;
+      float xp[4], xq[4];
+      float a = 0.f, bb = 0.f, g = 0.f;
 #pragma unroll
-        for (int o = 8; o > 0; o >>= 1) {
-          a += __shfl_xor_sync(0xffffffffu, a, o);
-          bb += __shfl_xor_sync(0xffffffffu, bb, o);
-          g += __shfl_xor_sync(0xffffffffu, g, o);
-        }
-        const float d = bb - a, ga = fabsf(g);
-        const float tf = copysignf(2.0f * ga, d) / (fabsf(d) + sqrtf(d * d + 4.0f * ga * ga));
-        const bool rot = valid && (g * g > tol2 * a * bb) && a > tiny2 && bb > tiny2 && fabsf(tf) > 1.0e-12f;
-        const float t = rot ? tf : 0.0f;
-        const float cs = rsqrtf(fmaf(t, t, 1.0f));
-        const float sn = cs * t;
-        const float se = g < 0.0f ? -sn : sn;
-        if (live) {
-          const float vp = V[pp * c + row], vq = V[qq * c + row];
-          X[pp * c + row] = cs * xp - se * xq;
-          X[qq * c + row] = se * xp + cs * xq;
-          V[pp * c + row] = cs * vp - se * vq;
-          V[qq * c + row] = se * vp + cs * vq;
-        }
-        rotated |= rot;
+      for (int k = 0; k < 4; ++k) {
+        const int rr = ql + 4 * k;
+        const bool live = valid && rr < c;
+        xp[k] = live ? X[pp * c + rr] : 0.f;
+        xq[k] = live ? X[qq * c + rr] : 0.f;
+        a = fmaf(xp[k], xp[k], a);
+        bb = fmaf(xq[k], xq[k], bb);
+        g = fmaf(xp[k], xq[k], g);
       }
-      __syncthreads();
+#pragma unroll
+      for (int o = 2; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        bb += __shfl_xor_sync(0xffffffffu, bb, o);
+        g += __shfl_xor_sync(0xffffffffu, g, o);
+      }
+      const float d = bb - a, ga = fabsf(g);
+      const float tf = copysignf(2.0f * ga, d) / (fabsf(d) + sqrtf(d * d + 4.0f * ga * ga));
+      const bool rot = valid && (g * g > tol2 * a * bb) && a > tiny2 && bb > tiny2 && fabsf(tf) > 1.0e-12f;
+      const float t = rot ? tf : 0.0f;
+      const float cs = rsqrtf(fmaf(t, t, 1.0f));
+      const float sn = cs * t;
+      const float se = g < 0.0f ? -sn : sn;
+      if (rot) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int rr = ql + 4 * k;
+          if (rr < c) {
+            const float vp = V[pp * c + rr], vq = V[qq * c + rr];
+            X[pp * c + rr] = cs * xp[k] - se * xq[k];
+            X[qq * c + rr] = se * xp[k] + cs * xq[k];
+            V[pp * c + rr] = cs * vp - se * vq;
+            V[qq * c + rr] = se * vp + cs * vq;
+          }
+        }
+      }
+      rotated |= rot;
+      __syncwarp();
     }
-    if (!__syncthreads_or(rotated)) { ++sweep; break; }
+    if (!__any_sync(0xffffffffu, rotated)) { ++sweep; break; }
   }
   return sweep;
 }
@@ -358,7 +382,22 @@ __device__ int jacobi_mixed16(double* X, double* V, int c, int N, double tol, do
   __syncthreads();
   const float tol32 = (float)imax(c, 4) * 1.1920929e-7f;
   const float tiny32 = (float)(tiny2 * sc * sc);
-  jacobi_pairs16_f32(Xf, Vf, c, N, tol32, tiny32);
+  // round-robin schedule: pair i of round r is (slot(i), slot(N - 1 - i)), ordered, 0xFF if a
+  // member is the padding column c (odd c)
+  __shared__ uint8_t sched[15 * 8];
+  for (int e = tid; e < (N - 1) * 8; e += NT) {
+    const int r = e / 8, i = e % 8;
+    uint8_t code = 0xFF;
+    if (i < N / 2) {
+      int pp = rr_slot(i, r, N), qq = rr_slot(N - 1 - i, r, N);
+      if (pp > qq) { const int t = pp; pp = qq; qq = t; }
+      if (qq < c) code = (uint8_t)(pp | (qq << 4));
+    }
+    sched[e] = code;
+  }
+  __syncthreads();
+  if ((tid >> 5) == 0) jacobi_pairs16_f32(Xf, Vf, c, N, tol32, tiny32, sched);
+  __syncthreads();
   for (int i = tid; i < c * c; i += NT) V[i] = (double)Vf[i];
   __syncthreads();
   for (int step = 0; step < 2; ++step) {
@@ -384,7 +423,15 @@ __device__ int jacobi_mixed16(double* X, double* V, int c, int N, double tol, do
   __syncthreads();
   for (int i = tid; i < c * c; i += NT) X[i] = Ws[i];
   __syncthreads();
-  return jacobi_pairs16(X, V, c, N, tol, tiny2);
+  // FP64 sweeps while they rotate; after two, a single check of all pairs replaces the sweep
+  // that would only confirm convergence
+  int sweeps = 0;
+  for (int round = 0; round < 30; ++round) {
+    const int s2 = jacobi_pairs16(X, V, c, N, tol, tiny2, sched, 2);
+    sweeps += s2;
+    if (s2 < 2 || !jacobi_pending(X, c, tol, tiny2)) break;
+  }
+  return sweeps;
 }
 
 template <class T>
@@ -499,9 +546,10 @@ __global__ void __launch_bounds__(1024) rr_small_kernel(const T* __restrict__ Rt
     Qm[col * pdim + row] = conj_(C[row * c + col]);
   }
   __syncthreads();
-  if (warp == 0 && with_x) {
-    for (int j = 0; j < b; ++j) {
-      T* x = Qm + j * pdim;
+  // (warp 0 forms each reflector; the columns it updates are spread over the warps)
+  for (int j = 0; with_x && j < b; ++j) {
+    T* x = Qm + j * pdim;
+    if (warp == 0) {
       double part = 0;
       for (int r = j + 1 + lane; r < pdim; r += 32) part += abs2_(x[r]);
       const double xn2 = warp_sum(part);
@@ -510,22 +558,22 @@ __global__ void __launch_bounds__(1024) rr_small_kernel(const T* __restrict__ Rt
       for (int r = j + 1 + lane; r < pdim; r += 32) x[r] = mul_(x[r], inv_ab);
       __syncwarp();
       if (lane == 0) { x[j] = beta; tau_s[j] = tau; }
-      __syncwarp();
-      for (int q = j + 1; q < b; ++q) {
-        T* y = Qm + q * pdim;
-        T s = zero_<T>();
-        for (int r = j + 1 + lane; r < pdim; r += 32) s = madc_(x[r], y[r], s);
-        s = warp_sum(s);
-        s = add_(s, y[j]);
-        const T f = mul_(conj_(tau), s);
-        __syncwarp();
-        if (lane == 0) y[j] = sub_(y[j], f);
-        for (int r = j + 1 + lane; r < pdim; r += 32) y[r] = sub_(y[r], mul_(x[r], f));
-        __syncwarp();
-      }
     }
+    __syncthreads();
+    const T tau = tau_s[j];
+    for (int q = j + 1 + warp; q < b; q += nwarp) {
+      T* y = Qm + q * pdim;
+      T s = zero_<T>();
+      for (int r = j + 1 + lane; r < pdim; r += 32) s = madc_(x[r], y[r], s);
+      s = warp_sum(s);
+      s = add_(s, y[j]);
+      const T f = mul_(conj_(tau), s);
+      __syncwarp();
+      if (lane == 0) y[j] = sub_(y[j], f);
+      for (int r = j + 1 + lane; r < pdim; r += 32) y[r] = sub_(y[r], mul_(x[r], f));
+    }
+    __syncthreads();
   }
-  __syncthreads();
   T* E = reinterpret_cast<T*>(rank + c + 4);  // p x b col-major scratch
   E = reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(E) + 15) & ~(uintptr_t)15);
   for (int i = tid; i < pdim * b; i += blockDim.x) {
@@ -534,29 +582,28 @@ __global__ void __launch_bounds__(1024) rr_small_kernel(const T* __restrict__ Rt
   }
   __syncthreads();
   // form Q explicitly: E = I(:, 0:b); E <- H_j E for j = b-1 .. 0 (H_j = I - tau_j v_j v_j^H)
-  if (warp == 0 && with_x) {
-    for (int j = b - 1; j >= 0; --j) {
-      const T* v = Qm + j * pdim;
-      const T tau = tau_s[j];
-      for (int q = j; q < b; ++q) {
-        T* y = E + q * pdim;
-        T s = zero_<T>();
-        for (int r = j + 1 + lane; r < pdim; r += 32) s = madc_(v[r], y[r], s);
-        s = warp_sum(s);
-        s = add_(s, y[j]);
-        const T f = mul_(tau, s);
-        __syncwarp();
-        if (lane == 0) y[j] = sub_(y[j], f);
-        for (int r = j + 1 + lane; r < pdim; r += 32) y[r] = sub_(y[r], mul_(v[r], f));
-        __syncwarp();
-      }
+  for (int j = b - 1; with_x && j >= 0; --j) {
+    const T* v = Qm + j * pdim;
+    const T tau = tau_s[j];
+    for (int q = j + warp; q < b; q += nwarp) {
+      T* y = E + q * pdim;
+      T s = zero_<T>();
+      for (int r = j + 1 + lane; r < pdim; r += 32) s = madc_(v[r], y[r], s);
+      s = warp_sum(s);
+      s = add_(s, y[j]);
+      const T f = mul_(tau, s);
+      __syncwarp();
+      if (lane == 0) y[j] = sub_(y[j], f);
+      for (int r = j + 1 + lane; r < pdim; r += 32) y[r] = sub_(y[r], mul_(v[r], f));
     }
-    // make diag(R) real non-negative: Q(:, j) *= phase(R(j, j))
-    for (int j = 0; j < b; ++j) {
-      const T ph = phase_(Qm[j * pdim + j]);
-      for (int r = lane; r < pdim; r += 32) E[j * pdim + r] = mul_(E[j * pdim + r], ph);
-    }
+    __syncthreads();
   }
+  // make diag(R) real non-negative: Q(:, j) *= phase(R(j, j))
+  if (with_x)
+    for (int e = tid; e < pdim * b; e += blockDim.x) {
+      const int j = e / pdim;
+      E[e] = mul_(E[e], phase_(Qm[j * pdim + j]));
+    }
   __syncthreads();
   // K = [C(:, p:c) | C(:, 0:p) E]  (c x 2b row-major)
   for (int i = tid; i < c * 2 * b; i += blockDim.x) {
@@ -951,6 +998,231 @@ __global__ void __launch_bounds__(256) bcgs2_orth_smem_kernel(T* __restrict__ Tb
   (void)red;
 }
 
+// L2-coherent load (data written by other CTAs of a cooperative grid)
+__device__ __forceinline__ double ldcg_(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ cd ldcg_(const cd* p) {
+  const double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+  return {v.x, v.y};
+}
+
+// Householder QR of a rows x b block (row-major, ld b) in shared memory by one CTA: on return the
+// upper triangle holds R (diag = beta), the strict lower part the reflector vectors scaled by
+// 1/(alpha - beta) (v_j = 1 implicit) and tau[j] their scalars; H_j = I - tau_j v_j v_j^H and the
+// block equals H_0 ... H_{b-1} [R; 0]. dgo[j] = beta_j.
+template <class T>
+__device__ void cta_householder(T* Wm, int rows, int b, T* tau, T* dgo, T* sv, T* sh_inv) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, NT = blockDim.x, NW = NT >> 5;
+  for (int j = 0; j < b; ++j) {
+    for (int cc = j + warp; cc < b; cc += NW) {
+      T a0 = zero_<T>(), a1 = zero_<T>();
+      int k = j + 1 + lane;
+      for (; k + 32 < rows; k += 64) {
+        a0 = madc_(Wm[(size_t)k * b + j], Wm[(size_t)k * b + cc], a0);
+        a1 = madc_(Wm[(size_t)(k + 32) * b + j], Wm[(size_t)(k + 32) * b + cc], a1);
+      }
+      if (k < rows) a0 = madc_(Wm[(size_t)k * b + j], Wm[(size_t)k * b + cc], a0);
+      const T sum = warp_sum(add_(a0, a1));
+      if (lane == 0) sv[cc] = sum;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      T t, beta, inv_ab;
+      householder_scalars(Wm[(size_t)j * b + j], re_(sv[j]), &t, &beta, &inv_ab);
+      tau[j] = t;
+      dgo[j] = beta;
+      *sh_inv = inv_ab;
+      for (int cc = j + 1; cc < b; ++cc) sv[cc] = add_(Wm[(size_t)j * b + cc], mul_(conj_(inv_ab), sv[cc]));
+    }
+    __syncthreads();
+    const T tj = tau[j], inv_ab = *sh_inv;
+    for (int e = tid; e < (rows - j) * b; e += NT) {
+      const int k = j + e / b, cc = e % b;
+      if (cc <= j) continue;
+      const T f = mul_(conj_(tj), sv[cc]);
+      const T vk = (k == j) ? from_real<T>(1.0) : mul_(Wm[(size_t)k * b + j], inv_ab);
+      Wm[(size_t)k * b + cc] = sub_(Wm[(size_t)k * b + cc], mul_(vk, f));
+    }
+    __syncthreads();
+    for (int k = j + 1 + tid; k < rows; k += NT) Wm[(size_t)k * b + j] = mul_(Wm[(size_t)k * b + j], inv_ab);
+    if (tid == 0) Wm[(size_t)j * b + j] = dgo[j];
+    __syncthreads();
+  }
+}
+
+// E (rows x b) <- H_0 ... H_{b-1} E with the reflectors stored by cta_householder in Vm (rows x b).
+// from_identity: E = [I; 0] on entry, so H_j only touches columns >= j.
+template <class T>
+__device__ void cta_apply_q(const T* Vm, const T* tau, int rows, int b, T* E, T* sv, bool from_identity) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, NT = blockDim.x, NW = NT >> 5;
+  for (int j = b - 1; j >= 0; --j) {
+    const int c0 = from_identity ? j : 0;
+    for (int cc = c0 + warp; cc < b; cc += NW) {
+      T a0 = zero_<T>(), a1 = zero_<T>();
+      int k = j + 1 + lane;
+      for (; k + 32 < rows; k += 64) {
+        a0 = madc_(Vm[(size_t)k * b + j], E[(size_t)k * b + cc], a0);
+        a1 = madc_(Vm[(size_t)(k + 32) * b + j], E[(size_t)(k + 32) * b + cc], a1);
+      }
+      if (k < rows) a0 = madc_(Vm[(size_t)k * b + j], E[(size_t)k * b + cc], a0);
+      const T sum = warp_sum(add_(a0, a1));
+      if (lane == 0) sv[cc] = mul_(tau[j], add_(E[(size_t)j * b + cc], sum));
+    }
+    __syncthreads();
+    for (int e = tid; e < (rows - j) * b; e += NT) {
+      const int k = j + e / b, cc = e % b;
+      if (cc < c0) continue;
+      const T vk = (k == j) ? from_real<T>(1.0) : Vm[(size_t)k * b + j];
+      E[(size_t)k * b + cc] = sub_(E[(size_t)k * b + cc], mul_(vk, sv[cc]));
+    }
+    __syncthreads();
+  }
+}
+
+// BCGS2 + Orth over G cooperating CTAs, CTA g owning rows [g n / G, (g+1) n / G). The projections
+// [V X]^H W are summed from per-CTA partials in CTA order after a grid barrier (two alternating
+// global buffers, one barrier per pass). Orth(W) is a one-level TSQR: each CTA reduces its rows
+// to R_g by Householder steps, every CTA then factors the same stack [R_0; ...; R_{G-1}] (same
+// arithmetic, so all hold the same R and stack Q_s) and applies its local reflectors to its
+// b x b block of Q_s. Q = blockdiag(Q_g) Q_s is the thin Householder Q of W (diag(R) made real
+// non-negative as in the single-CTA kernel). With wd.Wsl set, the column maxima go through one
+// more barrier and every CTA writes the bf16 digits of its rows.
+template <class T>
+__global__ void __launch_bounds__(256) bcgs2_orth_coop_kernel(T* __restrict__ Tb, int n, int b, int64_t ld, int wo,
+                                                              int nx, int passes, T* __restrict__ gs,
+                                                              split::WDigits wd, int* err) {
+  namespace cg = cooperative_groups;
+  cg::grid_group grid = cg::this_grid();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, NT = blockDim.x, NW = NT >> 5;
+  const int G = gridDim.x, g = blockIdx.x;
+  const int q = b + nx, QB = q * b, SB = G * b;
+  const int r0 = (int)((int64_t)g * n / G), r1 = (int)((int64_t)(g + 1) * n / G), rows = r1 - r0;
+  const int rmax = (n + G - 1) / G;
+  T* Bs = reinterpret_cast<T*>(smem_raw);   // rmax x q (V, X); later this CTA's rows of Q
+  T* Ws = Bs + (size_t)rmax * imax(q, b);   // rmax x b
+  T* P = Ws + (size_t)rmax * b;             // q x b
+  T* S = P + QB;                            // SB x b: the stack of R factors, then its reflectors
+  T* E = S + (size_t)SB * b;                // SB x b: Q_s
+  T* tl = E + (size_t)SB * b;               // local taus
+  T* ts = tl + b;                           // stack taus
+  T* sv = ts + b;
+  T* dl = sv + b;                           // local betas (unused after the stack)
+  T* dg = dl + b;                           // stack betas = diag(R)
+  __shared__ T sh_inv;
+  __shared__ int Fs[16];
+  T* gP0 = gs;
+  T* gP1 = gP0 + (size_t)G * QB;
+  T* gR = gP1 + (size_t)G * QB;
+  double* gmx = reinterpret_cast<double*>(gR + (size_t)G * b * b);
+  auto bcol = [&](int j) { return j < b ? j : (2 * b + (j - b)); };
+
+  for (int e = tid; e < rows * b; e += NT) {
+    const int k = e / b, cw = e % b;
+    Ws[e] = Tb[(int64_t)(r0 + k) * ld + wo + cw];
+  }
+  if (passes > 0)
+    for (int e = tid; e < rows * q; e += NT) {
+      const int k = e / q, j = e % q;
+      Bs[e] = Tb[(int64_t)(r0 + k) * ld + bcol(j)];
+    }
+  __syncthreads();
+  for (int pass = 0; pass < passes; ++pass) {
+    T* gP = (pass & 1) ? gP1 : gP0;
+    for (int o = tid; o < QB; o += NT) {
+      const int j = o / b, cw = o % b;
+      T a0 = zero_<T>(), a1 = zero_<T>();
+      int k = 0;
+      for (; k + 1 < rows; k += 2) {
+        a0 = madc_(Bs[(size_t)k * q + j], Ws[(size_t)k * b + cw], a0);
+        a1 = madc_(Bs[(size_t)(k + 1) * q + j], Ws[(size_t)(k + 1) * b + cw], a1);
+      }
+      if (k < rows) a0 = madc_(Bs[(size_t)k * q + j], Ws[(size_t)k * b + cw], a0);
+      gP[(size_t)g * QB + o] = add_(a0, a1);
+    }
+    grid.sync();
+    for (int o = tid; o < QB; o += NT) {
+      T sum = ldcg_(gP + o);
+      for (int h = 1; h < G; ++h) sum = add_(sum, ldcg_(gP + (size_t)h * QB + o));
+      P[o] = sum;
+    }
+    __syncthreads();
+    for (int e = tid; e < rows * b; e += NT) {
+      const int k = e / b, cw = e % b;
+      T w = Ws[e];
+      for (int j = 0; j < q; ++j) w = sub_(w, mul_(Bs[(size_t)k * q + j], P[j * b + cw]));
+      Ws[e] = w;
+    }
+    __syncthreads();
+  }
+  // local R_g
+  cta_householder<T>(Ws, rows, b, tl, dl, sv, &sh_inv);
+  for (int e = tid; e < b * b; e += NT) {
+    const int r = e / b, cc = e % b;
+    gR[(size_t)g * b * b + e] = (cc >= r) ? Ws[e] : zero_<T>();
+  }
+  grid.sync();
+  for (int e = tid; e < SB * b; e += NT) S[e] = ldcg_(gR + e);
+  __syncthreads();
+  cta_householder<T>(S, SB, b, ts, dg, sv, &sh_inv);
+  for (int e = tid; e < SB * b; e += NT) {
+    const int k = e / b, cc = e % b;
+    E[e] = (k == cc) ? from_real<T>(1.0) : zero_<T>();
+  }
+  __syncthreads();
+  cta_apply_q<T>(S, ts, SB, b, E, sv, true);
+  // this CTA's rows of Q: H_local [Q_s block g; 0]
+  T* QL = Bs;
+  for (int e = tid; e < rows * b; e += NT) {
+    const int k = e / b, cc = e % b;
+    QL[e] = (k < b) ? E[(size_t)(g * b + k) * b + cc] : zero_<T>();
+  }
+  __syncthreads();
+  cta_apply_q<T>(Ws, tl, rows, b, QL, sv, false);
+  for (int e = tid; e < rows * b; e += NT) {
+    const int k = e / b, cc = e % b;
+    const T v = mul_(QL[e], phase_(dg[cc]));
+    QL[e] = v;
+    Tb[(int64_t)(r0 + k) * ld + wo + cc] = v;
+  }
+  if (wd.Wsl == nullptr) return;
+  const int BP = wd.BP, N = split::SL * BP;
+  __syncthreads();
+  bool bad = false;
+  for (int cc = warp; cc < BP; cc += NW) {
+    double mx = 0;
+    if (cc < b)
+      for (int k = lane; k < rows; k += 32) {
+        const double a = fabs(re_(QL[(size_t)k * b + cc]));
+        bad |= !(a <= 1.7976931348623157e308);
+        mx = fmax(mx, a);
+      }
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) gmx[(size_t)g * 16 + cc] = mx;
+  }
+  if (__syncthreads_or(bad) && tid == 0) atomicOr(err, DEV_ERR_NONFINITE);
+  grid.sync();
+  if (tid < BP) {
+    double mx = 0;
+    for (int h = 0; h < G; ++h) mx = fmax(mx, __ldcg(gmx + (size_t)h * 16 + tid));
+    Fs[tid] = split::group_exp(mx);
+    if (g == 0) wd.F[tid] = Fs[tid];
+  }
+  __syncthreads();
+  const int64_t k_end = (g == G - 1) ? wd.NKB * split::TK : r1;   // the last CTA writes the padding rows
+  const int64_t total = (k_end - r0) * BP;
+  for (int64_t e = tid; e < total; e += NT) {
+    const int j = (int)(e % BP);
+    const int64_t k = r0 + e / BP;
+    const double x = (k < n && j < b) ? re_(QL[(size_t)(k - r0) * b + j]) : 0.0;
+    int d[split::SL];
+    split::split8(x, Fs[j], d);
+    uint16_t* out = wd.Wsl + (size_t)(k / split::TK) * (N * split::TK);
+    const int kk = (int)(k % split::TK);
+#pragma unroll
+    for (int qd = 0; qd < split::SL; ++qd) out[split::core_off(qd * BP + j, kk, N)] = split::bf16_of(d[qd]);
+  }
+}
+
 // V0 = Vt(:, n-b:n) (sketch precision, col-major n x n) -> T columns [0, b) in double/complex128
 template <class S, class T>
 __global__ void take_start_kernel(const S* Vt, int n, int b, T* Tb, int64_t ld) {
@@ -1195,11 +1467,32 @@ template int trimul_launch<double, float>(const float*, int, const double*, int6
 template int trimul_launch<cd, cd>(const cd*, int, const cd*, int64_t, int, cd*, int64_t, int, int, cudaStream_t);
 template int trimul_launch<cd, cf>(const cf*, int, const cd*, int64_t, int, cd*, int64_t, int, int, cudaStream_t);
 
+size_t bcgs2_coop_bytes(int64_t n, int qmax, int b, size_t esz);
+
 template <class T>
 int bcgs2_orth_launch(T* Tb, int n, int b, int64_t ld, int wo, int nx, T* E, int passes, cudaStream_t st,
-                      const split::WDigits* wd, int* err, bool* digits_done) {
+                      const split::WDigits* wd, int* err, bool* digits_done, void* coop, size_t coop_bytes) {
   if (digits_done) *digits_done = false;
   const int q = b + nx;
+  {
+    // cooperative version over G CTAs when every CTA keeps at least max(32, b) rows
+    const int G = imin(16, n / imax(32, b));
+    if (G >= 2 && coop && coop_bytes >= bcgs2_coop_bytes(n, b + imax(nx, 0), b, sizeof(T))) {
+      const int rmax = (n + G - 1) / G, SB = G * b;
+      const size_t smem = ((size_t)rmax * (imax(q, b) + b) + (size_t)q * b + 2 * (size_t)SB * b + 6 * b) * sizeof(T);
+      if (smem <= max_smem_optin() - 2048) {
+        split::WDigits w{};
+        if (wd && wd->Wsl && sizeof(T) == sizeof(double) && b <= wd->BP) w = *wd;
+        RL_TRY(allow_dynamic_smem(bcgs2_orth_coop_kernel<T>, smem));
+        T* gsp = (T*)coop;
+        void* args[] = {&Tb, &n, &b, &ld, &wo, &nx, &passes, &gsp, &w, &err};
+        RL_CUDA(cudaLaunchCooperativeKernel((void*)bcgs2_orth_coop_kernel<T>, dim3(G), dim3(256), args, smem, st));
+        note_launch();
+        if (digits_done) *digits_done = w.Wsl != nullptr;
+        return RLOBPCG_OK;
+      }
+    }
+  }
   const size_t smem_s = ((size_t)n * (q + b) + 5 * (size_t)q * b + 3 * b) * sizeof(T) + 16 * 8 * sizeof(double) + 64;
   if (smem_s <= max_smem_optin() - 1024) {
     split::WDigits w{};
@@ -1216,9 +1509,16 @@ int bcgs2_orth_launch(T* Tb, int n, int b, int64_t ld, int wo, int nx, T* E, int
   return RLOBPCG_OK;
 }
 template int bcgs2_orth_launch<double>(double*, int, int, int64_t, int, int, double*, int, cudaStream_t,
-                                       const split::WDigits*, int*, bool*);
+                                       const split::WDigits*, int*, bool*, void*, size_t);
 template int bcgs2_orth_launch<cd>(cd*, int, int, int64_t, int, int, cd*, int, cudaStream_t, const split::WDigits*,
-                                   int*, bool*);
+                                   int*, bool*, void*, size_t);
+
+// global scratch of the cooperative BCGS2 + Orth kernel for up to qmax basis columns and b columns
+size_t bcgs2_coop_bytes(int64_t n, int qmax, int b, size_t esz) {
+  const int64_t G = 16;
+  (void)n;
+  return ((size_t)2 * G * qmax * b + (size_t)G * b * b) * esz + (size_t)G * 16 * sizeof(double) + 256;
+}
 
 template <class S, class T>
 int take_start_launch(const S* Vt, int n, int b, T* Tb, int64_t ld, cudaStream_t st) {

@@ -57,7 +57,8 @@ int precond_launch(const S* Rinv_r, const S* Rinv_c, int n, int b, const T* Rs, 
                    cudaStream_t st);
 template <class T>
 int bcgs2_orth_launch(T* Tb, int n, int b, int64_t ld, int wo, int nx, T* E, int passes, cudaStream_t st,
-                      const split::WDigits* wd = nullptr, int* err = nullptr, bool* digits_done = nullptr);
+                      const split::WDigits* wd, int* err, bool* digits_done, void* coop, size_t coop_bytes);
+size_t bcgs2_coop_bytes(int64_t n, int qmax, int b, size_t esz);
 split::WDigits split_w_digits(void* work, int64_t m, int64_t n, int b);
 template <class S, class T>
 int take_start_launch(const S* Vt, int n, int b, T* Tb, int64_t ld, cudaStream_t st);
@@ -115,6 +116,8 @@ struct rlobpcg_plan_s {
   size_t swork_bytes = 0;
   void* twork = nullptr;
   size_t twork_bytes = 0;
+  void* coop = nullptr;     // global scratch of the cooperative BCGS2 + Orth kernel
+  size_t coop_bytes = 0;
   cudaEvent_t ev[10] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   // Per-iteration Gram timing events (3 per slot, a ring) and the pinned history of residual
   // norms and Ritz values, copied asynchronously; the host synchronises only to test the stop rule.
@@ -247,7 +250,7 @@ int solve_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, double tau, double* s
     for (int it = 0; it < 8; ++it) {
       RL_TRY((trimul_launch<T, S>((const S*)p->R_r, n, Z, qt, qt, Y, qt, 0, 0, st)));
       RL_TRY((trimul_launch<T, S>((const S*)p->R_c, n, Y, qt, qt, Z, qt, 1, 1, st)));
-      RL_TRY(bcgs2_orth_launch<T>(Z, n, qt, qt, 0, 0, (T*)p->E, 0, st));
+      RL_TRY(bcgs2_orth_launch<T>(Z, n, qt, qt, 0, 0, (T*)p->E, 0, st, nullptr, p->err, nullptr, p->coop, p->coop_bytes));
     }
     RL_TRY((trimul_launch<T, S>((const S*)p->R_r, n, Z, qt, qt, Y, qt, 0, 0, st)));
     RL_TRY(tsqr_impl<T>(Y, n, qt, qt, (T*)p->Rt, p->twork, p->twork_bytes, st));
@@ -260,7 +263,7 @@ int solve_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, double tau, double* s
     for (int it = 0; it < 3; ++it) {
       RL_TRY((trimul_launch<T, S>((const S*)p->Rinv_c, n, Z, q, q, Y, q, 1, 1, st)));
       RL_TRY((trimul_launch<T, S>((const S*)p->Rinv_r, n, Y, q, q, Z, q, 0, 0, st)));
-      RL_TRY(bcgs2_orth_launch<T>(Z, n, q, q, 0, 0, (T*)p->E, 0, st));
+      RL_TRY(bcgs2_orth_launch<T>(Z, n, q, q, 0, 0, (T*)p->E, 0, st, nullptr, p->err, nullptr, p->coop, p->coop_bytes));
     }
     RL_TRY((trimul_launch<T, S>((const S*)p->R_r, n, Z, q, q, Y, q, 0, 0, st)));
     RL_TRY(tsqr_impl<T>(Y, n, q, q, (T*)p->Rt, p->twork, p->twork_bytes, st));
@@ -274,7 +277,8 @@ int solve_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, double tau, double* s
   split::WDigits wd{};
   if (p->split) wd = split_w_digits(p->swork, m, n, b);
   bool w_ready = false;
-  RL_TRY(bcgs2_orth_launch<T>(Tb, n, b, ld, 0, 0, (T*)p->E, 0, st, p->split ? &wd : nullptr, p->err, &w_ready));
+  RL_TRY(bcgs2_orth_launch<T>(Tb, n, b, ld, 0, 0, (T*)p->E, 0, st, p->split ? &wd : nullptr, p->err, &w_ready,
+                              p->coop, p->coop_bytes));
   if (p->split) {
     RL_CUDA(cudaEventRecord(p->ev[8], st));
     RL_TRY(split_prepare((const double*)A, m, n, lda, p->sprep, p->sprep_bytes, st));
@@ -328,7 +332,8 @@ int solve_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, double tau, double* s
   for (int i = 0; i < max_iter; ++i) {
     // W = P (P^* R_i), then BCGS2 against [V X] and Orth
     RL_TRY((precond_launch<T, S>((const S*)p->Rinv_r, (const S*)p->Rinv_c, n, b, (const T*)p->Rs, (T*)p->Y, Tb, ld, b, st)));
-    RL_TRY(bcgs2_orth_launch<T>(Tb, n, b, ld, b, nx, (T*)p->E, 2, st, p->split ? &wd : nullptr, p->err, &w_ready));
+    RL_TRY(bcgs2_orth_launch<T>(Tb, n, b, ld, b, nx, (T*)p->E, 2, st, p->split ? &wd : nullptr, p->err, &w_ready,
+                                p->coop, p->coop_bytes));
     const int c = 2 * b + nx;
     cudaEvent_t* e = &p->gev[(size_t)(i % kRing) * 3];
     RL_CUDA(cudaEventRecord(e[0], st));
@@ -537,6 +542,11 @@ int plan_buffers(PlanAlloc& A_, rlobpcg_plan_s* p, int64_t m, int64_t n, int b, 
   }
   *twork = std::max(tsqr_workspace_bytes(m, (int)ld, esz), tsqr_workspace_bytes(n, qmax, esz));
   RL_B(twork, *twork);
+  {
+    const size_t cb = bcgs2_coop_bytes(n, (int)std::max<int64_t>(ld, qmax), std::max(b, qmax), esz);
+    RL_B(coop, cb);
+    if (p) p->coop_bytes = cb;
+  }
 #undef RL_B
   *qmax_out = qmax;
   return RLOBPCG_OK;
