@@ -1475,9 +1475,10 @@ int bcgs2_orth_launch(T* Tb, int n, int b, int64_t ld, int wo, int nx, T* E, int
   if (digits_done) *digits_done = false;
   const int q = b + nx;
   {
-    // cooperative version over G CTAs when every CTA keeps at least max(32, b) rows
+    // cooperative version over G CTAs when n is large enough for the grid barriers to pay (every
+    // CTA keeps at least max(32, b) rows; below n = 256 the one-CTA kernel is faster)
     const int G = imin(16, n / imax(32, b));
-    if (G >= 2 && coop && coop_bytes >= bcgs2_coop_bytes(n, b + imax(nx, 0), b, sizeof(T))) {
+    if (n >= 256 && G >= 2 && coop && coop_bytes >= bcgs2_coop_bytes(n, b + imax(nx, 0), b, sizeof(T))) {
       const int rmax = (n + G - 1) / G, SB = G * b;
       const size_t smem = ((size_t)rmax * (imax(q, b) + b) + (size_t)q * b + 2 * (size_t)SB * b + 6 * b) * sizeof(T);
       if (smem <= max_smem_optin() - 2048) {
