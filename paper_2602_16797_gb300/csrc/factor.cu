@@ -286,23 +286,29 @@ template <class S>
 __global__ void trinv_kernel(const S* Rm, int n, S* Xr, S* Xc) {
   using Rl = RealOf<S>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  S* acc = reinterpret_cast<S*>(smem_raw);
-  __shared__ Rl diag_max;
+  S* acc = reinterpret_cast<S*>(smem_raw);   // n entries, then n pivot reciprocals
+  S* rdiag = acc + n;
+  __shared__ Rl red[32];
   const int j = blockIdx.x;
-  if (threadIdx.x == 0) {
-    Rl mx = 0;
-    for (int i = 0; i < n; ++i) mx = fmax(mx, sqrt_(abs2_(Rm[(int64_t)i * n + i])));
-    diag_max = mx;
-  }
+  // max |R_ii| (parallel), the floor for zero pivots, and the pivot reciprocals 1/R_ll, l <= j,
+  // all before the dependent back substitution
+  Rl mx = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) mx = fmax(mx, sqrt_(abs2_(Rm[(int64_t)i * n + i])));
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
   for (int i = threadIdx.x; i <= j; i += blockDim.x) acc[i] = (i == j) ? from_real<S>((Rl)1) : zero_<S>();
   __syncthreads();
-  const Rl floor_ = eps_of<S>() * diag_max;
+  mx = 0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, red[w]);
+  const Rl floor_ = eps_of<S>() * mx;
+  for (int l = threadIdx.x; l <= j; l += blockDim.x) {
+    S piv = Rm[(int64_t)l * n + l];
+    if (abs2_(piv) == (Rl)0) piv = from_real<S>(floor_ > (Rl)0 ? floor_ : (Rl)1);
+    rdiag[l] = recip_(piv);
+  }
+  __syncthreads();
   for (int l = j; l >= 0; --l) {
-    if (threadIdx.x == 0) {
-      S piv = Rm[(int64_t)l * n + l];
-      if (abs2_(piv) == (Rl)0) piv = from_real<S>(floor_ > (Rl)0 ? floor_ : (Rl)1);
-      acc[l] = mul_(acc[l], recip_(piv));
-    }
+    if (threadIdx.x == 0) acc[l] = mul_(acc[l], rdiag[l]);
     __syncthreads();
     const S xl = acc[l];
     const S* col = Rm + (int64_t)l * n;
@@ -321,7 +327,7 @@ int coop_grid(K kernel, int threads, size_t smem, int* grid) {
   int per_sm = 0;
   RL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem));
   if (per_sm < 1) return RLOBPCG_ERR_UNSUPPORTED;
-  *grid = num_sms() * min(per_sm, 2);
+  *grid = num_sms();   // one CTA per SM: measured faster than two (cheaper grid barriers)
   return RLOBPCG_OK;
 }
 
@@ -376,7 +382,7 @@ int factor_impl(S* SA, int d, int n, S* Rout, S* Rout_r, double* sigma, S* Vt, S
 
   // 3. R^{-1} (before Jacobi overwrites X)
   if (Rinv_r && Rinv_c) {
-    size_t sm = (size_t)n * sizeof(S);
+    size_t sm = (size_t)2 * n * sizeof(S);
     RL_TRY(allow_dynamic_smem(trinv_kernel<S>, sm));
     trinv_kernel<S><<<n, 256, sm, st>>>(X, n, Rinv_r, Rinv_c);
     RL_CHECK_LAUNCH();
