@@ -268,8 +268,9 @@ __device__ int jacobi_pairs16(double* X, double* V, int c, int N, double tol, do
   return sweep;
 }
 
-// Does any column pair of X (c x c, column-major) still fail the Jacobi test? One pass over all
-// pairs (c (c - 1) / 2 dot products of length c) instead of a whole confirming sweep.
+// Would a sweep still rotate any column pair of X (c x c, column-major)? The same two tests as
+// the sweep -- the cosine test and a rotation angle above eps (a pair whose angle is below eps is
+// never rotated) -- in one pass over all pairs instead of a whole confirming sweep.
 __device__ bool jacobi_pending(const double* X, int c, double tol, double tiny2) {
   const double tol2 = tol * tol;
   int bad = 0;
@@ -283,7 +284,11 @@ __device__ bool jacobi_pending(const double* X, int c, double tol, double tiny2)
       bb = fma(y, y, bb);
       g = fma(x, y, g);
     }
-    bad |= (g * g > tol2 * a * bb) && a > tiny2 && bb > tiny2;
+    if ((g * g > tol2 * a * bb) && a > tiny2 && bb > tiny2) {
+      const double d = bb - a;
+      const double t = 2.0 * fabs(g) / (fabs(d) + sqrt(d * d + 4.0 * g * g));
+      bad |= t > 2.220446049250313e-16;
+    }
   }
   return __syncthreads_or(bad) != 0;
 }
