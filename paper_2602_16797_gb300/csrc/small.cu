@@ -296,58 +296,47 @@ __device__ bool jacobi_pending(const double* X, int c, double tol, double tiny2)
 // The same sweeps in FP32 (on GB300 the FP32 pipe issues ~64x the FP64 rate): used on a scaled
 // FP32 copy of R_T to find a V that nearly diagonalises it (cosines ~ c u_32).
 __device__ int jacobi_pairs16_f32(float* X, float* V, int c, int N, float tol, float tiny2, const uint8_t* sched) {
-  // one warp: eight pairs per round, four lanes per pair, rows ql, ql + 4, ql + 8, ql + 12
-  const int lane = threadIdx.x & 31, pi = lane >> 2, ql = lane & 3;
+  // same layout as the FP64 sweeps: two pairs per warp, a half-warp per pair, lane = row
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
+  const int half = lane >> 4, row = lane & 15;
   const float tol2 = tol * tol;
   int sweep = 0;
   for (; sweep < 12; ++sweep) {
     int rotated = 0;
     for (int r = 0; r < N - 1; ++r) {
-      const int code = pi < N / 2 ? sched[r * 8 + pi] : 0xFF;
-      const int pp = code & 15, qq = code >> 4;
-      const bool valid = code != 0xFF;
-      float xp[4], xq[4];
-      float a = 0.f, bb = 0.f, g = 0.f;
+      for (int p0 = 2 * warp; p0 < N / 2; p0 += 2 * nw) {   // warp-uniform
+        const int pi = p0 + half;
+        const int code = pi < N / 2 ? sched[r * 8 + pi] : 0xFF;
+        const int pp = code & 15, qq = code >> 4;
+        const bool valid = code != 0xFF;
+        const bool live = valid && row < c;
+        const float xp = live ? X[pp * c + row] : 0.f, xq = live ? X[qq * c + row] : 0.f;
+        float a = xp * xp, bb = xq * xq, g = xp * xq;
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int rr = ql + 4 * k;
-        const bool live = valid && rr < c;
-        xp[k] = live ? X[pp * c + rr] : 0.f;
-        xq[k] = live ? X[qq * c + rr] : 0.f;
-        a = fmaf(xp[k], xp[k], a);
-        bb = fmaf(xq[k], xq[k], bb);
-        g = fmaf(xp[k], xq[k], g);
-      }
-#pragma unroll
-      for (int o = 2; o > 0; o >>= 1) {
-        a += __shfl_xor_sync(0xffffffffu, a, o);
-        bb += __shfl_xor_sync(0xffffffffu, bb, o);
-        g += __shfl_xor_sync(0xffffffffu, g, o);
-      }
-      const float d = bb - a, ga = fabsf(g);
-      const float tf = copysignf(2.0f * ga, d) / (fabsf(d) + sqrtf(d * d + 4.0f * ga * ga));
-      const bool rot = valid && (g * g > tol2 * a * bb) && a > tiny2 && bb > tiny2 && fabsf(tf) > 1.0e-12f;
-      const float t = rot ? tf : 0.0f;
-      const float cs = rsqrtf(fmaf(t, t, 1.0f));
-      const float sn = cs * t;
-      const float se = g < 0.0f ? -sn : sn;
-      if (rot) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const int rr = ql + 4 * k;
-          if (rr < c) {
-            const float vp = V[pp * c + rr], vq = V[qq * c + rr];
-            X[pp * c + rr] = cs * xp[k] - se * xq[k];
-            X[qq * c + rr] = se * xp[k] + cs * xq[k];
-            V[pp * c + rr] = cs * vp - se * vq;
-            V[qq * c + rr] = se * vp + cs * vq;
-          }
+        for (int o = 8; o > 0; o >>= 1) {
+          a += __shfl_xor_sync(0xffffffffu, a, o);
+          bb += __shfl_xor_sync(0xffffffffu, bb, o);
+          g += __shfl_xor_sync(0xffffffffu, g, o);
         }
+        const float d = bb - a, ga = fabsf(g);
+        const float tf = copysignf(2.0f * ga, d) / (fabsf(d) + sqrtf(d * d + 4.0f * ga * ga));
+        const bool rot = valid && (g * g > tol2 * a * bb) && a > tiny2 && bb > tiny2 && fabsf(tf) > 1.0e-12f;
+        const float t = rot ? tf : 0.0f;
+        const float cs = rsqrtf(fmaf(t, t, 1.0f));
+        const float sn = cs * t;
+        const float se = g < 0.0f ? -sn : sn;
+        if (live && rot) {
+          const float vp = V[pp * c + row], vq = V[qq * c + row];
+          X[pp * c + row] = cs * xp - se * xq;
+          X[qq * c + row] = se * xp + cs * xq;
+          V[pp * c + row] = cs * vp - se * vq;
+          V[qq * c + row] = se * vp + cs * vq;
+        }
+        rotated |= rot;
       }
-      rotated |= rot;
-      __syncwarp();
+      __syncthreads();
     }
-    if (!__any_sync(0xffffffffu, rotated)) { ++sweep; break; }
+    if (!__syncthreads_or(rotated)) { ++sweep; break; }
   }
   return sweep;
 }
@@ -401,8 +390,7 @@ __device__ int jacobi_mixed16(double* X, double* V, int c, int N, double tol, do
     sched[e] = code;
   }
   __syncthreads();
-  if ((tid >> 5) == 0) jacobi_pairs16_f32(Xf, Vf, c, N, tol32, tiny32, sched);
-  __syncthreads();
+  jacobi_pairs16_f32(Xf, Vf, c, N, tol32, tiny32, sched);
   for (int i = tid; i < c * c; i += NT) V[i] = (double)Vf[i];
   __syncthreads();
   for (int step = 0; step < 2; ++step) {
@@ -521,12 +509,17 @@ __global__ void __launch_bounds__(1024) rr_small_kernel(const T* __restrict__ Rt
     __syncthreads();
     if (!ch) { ++sweep; break; }
   }
-  // singular values = column norms; sort descending, ties by index
-  for (int j = warp; j < c; j += nwarp) {
-    double a = 0;
-    for (int rr = lane; rr < c; rr += 32) a += abs2_(X[j * c + rr]);
-    a = warp_sum(a);
-    if (lane == 0) nrm[j] = sqrt(a);
+  // singular values = column norms (a thread per column: no reductions on the dependent chain);
+  // sort descending, ties by index
+  for (int j = tid; j < c; j += blockDim.x) {
+    double a0 = 0, a1 = 0;
+    int rr = 0;
+    for (; rr + 1 < c; rr += 2) {
+      a0 += abs2_(X[j * c + rr]);
+      a1 += abs2_(X[j * c + rr + 1]);
+    }
+    if (rr < c) a0 += abs2_(X[j * c + rr]);
+    nrm[j] = sqrt(a0 + a1);
   }
   __syncthreads();
   for (int j = tid; j < c; j += blockDim.x) {
