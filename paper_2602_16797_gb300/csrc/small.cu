@@ -148,17 +148,24 @@ __global__ void __launch_bounds__(256) tsqr_merge_kernel(const T* __restrict__ R
     const int jr = j + 1;
     const int act = (nb - 1) * jr;   // rows of blocks 1.. that can be nonzero in column j
     T d = zero_<T>();
+    // active row t = (block 1 + t / jr, local row t % jr), walked incrementally (no divides)
     if (cc < c && cc >= j) {
       T a0 = zero_<T>(), a1 = zero_<T>();
-      int t = p;
-      for (; t + RP < act; t += 2 * RP) {
-        const int r0 = (1 + t / jr) * c + t % jr, r1 = (1 + (t + RP) / jr) * c + (t + RP) % jr;
+      int f = 1 + p / jr, lr = p % jr;
+      const int df = RP / jr, dl = RP % jr;
+      for (int t = p; t < act; t += 2 * RP) {
+        const int r0 = f * c + lr;
         a0 = madc_(S[(size_t)r0 * c + j], S[(size_t)r0 * c + cc], a0);
-        a1 = madc_(S[(size_t)r1 * c + j], S[(size_t)r1 * c + cc], a1);
-      }
-      if (t < act) {
-        const int r0 = (1 + t / jr) * c + t % jr;
-        a0 = madc_(S[(size_t)r0 * c + j], S[(size_t)r0 * c + cc], a0);
+        f += df;
+        lr += dl;
+        if (lr >= jr) { lr -= jr; ++f; }
+        if (t + RP < act) {
+          const int r1 = f * c + lr;
+          a1 = madc_(S[(size_t)r1 * c + j], S[(size_t)r1 * c + cc], a1);
+        }
+        f += df;
+        lr += dl;
+        if (lr >= jr) { lr -= jr; ++f; }
       }
       d = add_(a0, a1);
     }
@@ -174,9 +181,14 @@ __global__ void __launch_bounds__(256) tsqr_merge_kernel(const T* __restrict__ R
       const T f = mul_(conj_(sh_tau), add_(S[(size_t)j * c + cc], mul_(conj_(inv_ab), d)));
       const T fv = mul_(inv_ab, f);
       if (p == 0) S[(size_t)j * c + cc] = sub_(S[(size_t)j * c + cc], f);
+      int fb = 1 + p / jr, lr = p % jr;
+      const int df = RP / jr, dl = RP % jr;
       for (int t = p; t < act; t += RP) {
-        const int r = (1 + t / jr) * c + t % jr;
+        const int r = fb * c + lr;
         S[(size_t)r * c + cc] = sub_(S[(size_t)r * c + cc], mul_(S[(size_t)r * c + j], fv));
+        fb += df;
+        lr += dl;
+        if (lr >= jr) { lr -= jr; ++fb; }
       }
     }
     if (cc == j && p == 0) S[(size_t)j * c + j] = sh_beta;
