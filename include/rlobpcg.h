@@ -222,7 +222,8 @@ int rlobpcg_sketch(const void* A, int64_t m, int64_t n, int64_t lda, int dtype, 
  *   Vt     device, n x n column-major V~ (column j belongs to sigma[j]) in the sketch precision.
  *   Rinv   device, n x n row-major R^{-1} in the sketch precision, or NULL.
  *   work   device scratch of rlobpcg_factor_workspace_size(d, n, dtype, sketch_prec) bytes.
- * Errors: INVALID_ARG (d < n), TIMEOUT (never in practice: no waits), CUDA.
+ * Errors: INVALID_ARG (d < n), TIMEOUT (a bounded wait between the QR's CTAs ran out: not seen
+ * in normal runs), CUDA.
  */
 int rlobpcg_factor(void* SA, int64_t d, int64_t n, int dtype, int sketch_prec, void* R,
                    double* sigma, void* Vt, void* Rinv, void* work, size_t work_bytes,

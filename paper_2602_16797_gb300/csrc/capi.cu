@@ -11,7 +11,7 @@ int sketch_dispatch(const void* A, int64_t m, int64_t n, int64_t lda, int dtype,
 size_t factor_workspace_bytes(int64_t d, int64_t n, size_t esz);
 template <class S>
 int factor_impl(S* SA, int d, int n, S* Rout, S* Rout_r, double* sigma, S* Vt, S* Rinv_r, S* Rinv_c, void* work,
-                size_t work_bytes, cudaStream_t st, int* sweeps_host, bool do_svd);
+                size_t work_bytes, cudaStream_t st, int* sweeps_host, bool do_svd, int* err);
 size_t gram_workspace_bytes(int64_t m, int64_t n, int b, int dtype);
 int gram_dispatch(const void* A, int64_t m, int64_t n, int64_t lda, int dtype, const void* W, int b, int64_t ldw,
                   void* AW, int64_t ldaw, void* G, int64_t ldg, void* work, size_t work_bytes, int resid_mode,
@@ -140,21 +140,23 @@ extern "C" int rlobpcg_factor(void* SA, int64_t d, int64_t n, int dtype, int ske
   const size_t fbytes = factor_workspace_bytes(d, n, esz);
   void* Rinv_c = Rinv ? (void*)((unsigned char*)work + fbytes) : nullptr;
   work_bytes = fbytes;
+  int* err = step_err_word(st);
+  if (!err) return RLOBPCG_ERR_OOM;
   int rc;
   const bool f32 = sketch_prec == RLOBPCG_SKETCH_F32;
   if (dtype == RLOBPCG_F64) {
     rc = f32 ? factor_impl<float>((float*)SA, (int)d, (int)n, (float*)R, nullptr, sigma, (float*)Vt, (float*)Rinv,
-                                  (float*)Rinv_c, work, work_bytes, st, nullptr, true)
+                                  (float*)Rinv_c, work, work_bytes, st, nullptr, true, err)
              : factor_impl<double>((double*)SA, (int)d, (int)n, (double*)R, nullptr, sigma, (double*)Vt, (double*)Rinv,
-                                   (double*)Rinv_c, work, work_bytes, st, nullptr, true);
+                                   (double*)Rinv_c, work, work_bytes, st, nullptr, true, err);
   } else {
     rc = f32 ? factor_impl<cf>((cf*)SA, (int)d, (int)n, (cf*)R, nullptr, sigma, (cf*)Vt, (cf*)Rinv, (cf*)Rinv_c, work,
-                               work_bytes, st, nullptr, true)
+                               work_bytes, st, nullptr, true, err)
              : factor_impl<cd>((cd*)SA, (int)d, (int)n, (cd*)R, nullptr, sigma, (cd*)Vt, (cd*)Rinv, (cd*)Rinv_c, work,
-                               work_bytes, st, nullptr, true);
+                               work_bytes, st, nullptr, true, err);
   }
   if (rc) return rc;
-  return finish(st, nullptr);
+  return finish(st, err);
 }
 
 extern "C" size_t rlobpcg_gram_workspace_size(int64_t m, int64_t n, int b, int dtype) {

@@ -5,9 +5,11 @@
 //      as two triangular products.
 // All three run in the sketch precision S (float/cf in the mixed form, double/cd otherwise).
 //
-// GB300 mapping: QR and Jacobi are persistent cooperative kernels (one launch each, grid-wide
-// barriers between the dependent steps) with one warp per column (QR) or per column pair
-// (Jacobi); the matrices stay L2-resident (n <= a few thousand). R^{-1} uses one CTA per column.
+// GB300 mapping: QR and Jacobi are persistent cooperative kernels (one launch each). The QR runs
+// as a dataflow: each reflector is published through a flag and every CTA applies it to its own
+// columns when it arrives, so only the chain "update column j+1, form reflector j+1" is serial.
+// Jacobi uses grid-wide barriers between rounds, one warp per column pair. The matrices stay
+// L2-resident (n <= a few thousand). R^{-1} uses one CTA per column.
 #include <cooperative_groups.h>
 
 #include "common.cuh"
@@ -129,6 +131,231 @@ __global__ void __launch_bounds__(FQ_THREADS) qr_kernel(S* M, int d, int n, S* t
       if (c == j + 1) cta_reflector(col, j + 1, d, tau, red);
     }
     grid.sync();
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Dataflow Householder QR (the reflectors of qr_kernel, LAPACK geqr2 convention) for
+// d <= 32 * NR * 8 rows. Column c is owned by CTA c % G; row r of every column by thread r % NT
+// (NT = blockDim.x, a multiple of 32 with NT * NR >= d), slot r / NT of its registers, so a
+// thread only rereads rows of its own columns that it wrote itself. Reflector j is published
+// through two flags:
+//   ready1[j]: u = column j below the diagonal is in memory (unscaled: v = [1; sc_j u]);
+//   ready2[j]: tau_j and sc_j = 1 / (alpha - beta) are in memory.
+// A reader starts its dot products u^H x on ready1 and needs tau_j, sc_j only after the
+// reduction, so forming reflector j (a norm reduction, a square root, a divide) overlaps the
+// readers' loads and reductions. The CTA that owns column j+1 updates it first at step j and
+// publishes it at once; the strict lower part of M ends up holding u unscaled (only R is used).
+// On GB300 an SM retires about one 32-lane FP64 instruction per 16 cycles, so the cross-thread
+// sums and the reflector's scalars run in one warp (or one thread), not redundantly in all.
+// Waits are bounded: on timeout the CTA sets DEV_ERR_TIMEOUT and returns.
+// ------------------------------------------------------------------------------------------
+constexpr long kQrSpin = 1L << 22;
+constexpr int kQrMaxThreads = 256;
+constexpr int kQrBatch = 2;   // non-critical columns updated per reduction
+
+__device__ __forceinline__ double ldcg_s(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ float ldcg_s(const float* p) { return __ldcg(p); }
+__device__ __forceinline__ cd ldcg_s(const cd* p) {
+  const double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+  return {v.x, v.y};
+}
+__device__ __forceinline__ cf ldcg_s(const cf* p) {
+  const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+  return {v.x, v.y};
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+// Release store: orders this thread's earlier writes, and through a preceding __syncthreads()
+// those of the whole CTA, before the flag.
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ inline bool qr_poll(const unsigned* flag) {
+  for (long it = 0; it < kQrSpin; ++it) {
+    if (ld_acquire(flag) != 0u) return true;
+    if (it > 32) __nanosleep(32);
+  }
+  return false;
+}
+
+// Called by warp 0 only: sums NV blocks of nt partials (block q at part + q * kQrMaxThreads) in
+// a fixed order; the lanes of group q = lane / (32 / NV) all return the total of block q.
+template <class S, int NV>
+__device__ inline S qr_warp_sum(const S* part, int nt, int lane) {
+  constexpr int LPV = 32 / NV;
+  const int q = lane / LPV, l = lane % LPV, per = nt / LPV;
+  const S* p = part + q * kQrMaxThreads + l * per;
+  S a0 = zero_<S>(), a1 = zero_<S>();
+  int i = 0;
+  for (; i + 1 < per; i += 2) { a0 = add_(a0, p[i]); a1 = add_(a1, p[i + 1]); }
+  if (i < per) a0 = add_(a0, p[i]);
+  S s = add_(a0, a1);
+#pragma unroll
+  for (int o = LPV / 2; o > 0; o >>= 1) s = add_(s, shfl_xor_(s, o));
+  return s;
+}
+
+template <class S>
+struct QrShared {
+  S part[2][kQrBatch][kQrMaxThreads];   // per-thread partial sums, two phases used alternately
+  S xj[2][kQrBatch];                    // x(j) of the reduced columns, or alpha
+  S f[kQrBatch], fs[kQrBatch];          // f = conj(tau_j) v^H x and f sc_j
+  S tj, scj;
+  int stop[2];                          // stage-1 / stage-2 wait outcome
+};
+
+// Reflector c of the column held in x (every reflector before c applied): the partial norms go
+// through phase ph of the shared buffers; thread 0 writes beta, tau_c, sc_c and sets ready2[c].
+template <class S, int NR>
+__device__ inline void qr_form(const S (&x)[NR], S* col, int d, int c, S* tau, S* scv, unsigned* ready2,
+                               QrShared<S>& sh, int& ph) {
+  using R = RealOf<S>;
+  const int nt = blockDim.x, tid = threadIdx.x;
+  R p = 0;
+#pragma unroll
+  for (int i = 0; i < NR; ++i) {
+    const int r = tid + i * nt;
+    if (r > c && r < d) p += abs2_(x[i]);
+    if (r == c) sh.xj[ph][0] = x[i];
+  }
+  sh.part[ph][0][tid] = from_real<S>(p);
+  __syncthreads();
+  if (tid < 32) {
+    const R xnorm2 = re_(qr_warp_sum<S, 1>(sh.part[ph][0], nt, tid));
+    if (tid == 0) {
+      const S alpha = sh.xj[ph][0];
+      S t = zero_<S>(), beta = alpha, sc = zero_<S>();
+      if (!(xnorm2 == (R)0 && im_(alpha) == (R)0)) {
+        const R bn = sqrt_(abs2_(alpha) + xnorm2);
+        const R b = re_(alpha) >= (R)0 ? -bn : bn;
+        beta = from_real<S>(b);
+        const S amb = sub_(alpha, beta);
+        const S rr = recip_(scale_(amb, b));   // 1 / (beta (alpha - beta))
+        t = mul_(sub_(beta, alpha), mul_(amb, rr));
+        sc = scale_(rr, b);
+      }
+      col[c] = beta;
+      tau[c] = t;
+      scv[c] = sc;
+      st_release(ready2 + c, 1u);
+    }
+  }
+  ph ^= 1;
+}
+
+template <class S, int NR>
+__global__ void __launch_bounds__(kQrMaxThreads) qr_flow_kernel(S* M, int d, int n, S* tau, S* scv,
+                                                               unsigned* ready, int* err) {
+  __shared__ QrShared<S> sh;
+  unsigned* ready1 = ready;
+  unsigned* ready2 = ready + n;
+  const int G = gridDim.x, b0 = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  if (b0 >= n) return;
+  const int lastc = b0 + ((n - 1 - b0) / G) * G;
+  int ph = 0;
+  S u[NR];
+  if (b0 == 0) {   // reflector 0: the sketch itself is in memory, so ready1[0] holds at launch
+    S x[NR];
+#pragma unroll
+    for (int i = 0; i < NR; ++i) {
+      const int r = tid + i * nt;
+      x[i] = r < d ? M[r] : zero_<S>();
+    }
+    if (tid == 0) st_release(ready1, 1u);
+    qr_form<S, NR>(x, M, d, 0, tau, scv, ready2, sh, ph);
+  }
+  for (int j = 0; j < lastc; ++j) {
+    if (tid == 0) {
+      const bool ok = qr_poll(ready1 + j);
+      sh.stop[0] = ok ? 0 : 1;
+      if (!ok) atomicOr(err, DEV_ERR_TIMEOUT);
+    }
+    __syncthreads();
+    if (sh.stop[0]) return;
+    const S* uj = M + (int64_t)j * d;
+#pragma unroll
+    for (int i = 0; i < NR; ++i) {
+      const int r = tid + i * nt;
+      u[i] = (r > j && r < d) ? ldcg_s(uj + r) : zero_<S>();
+    }
+    bool have_tau = false;
+    int c = b0 > j ? b0 : b0 + ((j - b0) / G + 1) * G;   // first owned column > j
+    while (c < n) {
+      // the next pivot column j+1 alone (it is then published at once), else up to kQrBatch
+      const int kb = (c == j + 1) ? 1 : min(kQrBatch, (n - 1 - c) / G + 1);
+      S x[kQrBatch][NR];
+#pragma unroll
+      for (int k = 0; k < kQrBatch; ++k) {
+        S a0 = zero_<S>(), a1 = zero_<S>();
+        if (k < kb) {
+          const S* col = M + (int64_t)(c + k * G) * d;
+#pragma unroll
+          for (int i = 0; i < NR; ++i) {
+            const int r = tid + i * nt;
+            x[k][i] = (r >= j && r < d) ? col[r] : zero_<S>();
+            if (i & 1) a1 = madc_(u[i], x[k][i], a1);   // conj(u) x
+            else a0 = madc_(u[i], x[k][i], a0);
+            if (r == j) sh.xj[ph][k] = x[k][i];
+          }
+        }
+        sh.part[ph][k][tid] = add_(a0, a1);
+      }
+      __syncthreads();
+      if (tid < 32) {
+        const S s = kb == 1 ? qr_warp_sum<S, 1>(sh.part[ph][0], nt, tid) : qr_warp_sum<S, 2>(sh.part[ph][0], nt, tid);
+        if (!have_tau && tid == 0) {
+          const bool ok = qr_poll(ready2 + j);
+          sh.stop[1] = ok ? 0 : 1;
+          if (!ok) atomicOr(err, DEV_ERR_TIMEOUT);
+          sh.tj = ldcg_s(tau + j);
+          sh.scj = ldcg_s(scv + j);
+        }
+        __syncwarp();
+        const int lpv = kb == 1 ? 32 : 16;
+        if (tid % lpv == 0) {
+          // H_j^H x = x - f v,  f = conj(tau_j) (x(j) + conj(sc_j) u^H x(j+1:)),  v = [1; sc_j u]
+          const int q = tid / lpv;
+          const S tj = sh.tj, scj = sh.scj;
+          const S f = mul_(conj_(tj), add_(sh.xj[ph][q], mul_(conj_(scj), s)));
+          sh.f[q] = f;
+          sh.fs[q] = mul_(f, scj);
+        }
+      }
+      __syncthreads();
+      if (sh.stop[1]) return;
+      have_tau = true;
+#pragma unroll
+      for (int k = 0; k < kQrBatch; ++k) {
+        if (k < kb) {
+          S* col = M + (int64_t)(c + k * G) * d;
+          const S f = sh.f[k], fs = sh.fs[k];
+#pragma unroll
+          for (int i = 0; i < NR; ++i) {
+            const int r = tid + i * nt;
+            if (r > j && r < d) {
+              x[k][i] = sub_(x[k][i], mul_(fs, u[i]));
+              col[r] = x[k][i];
+            } else if (r == j) {
+              x[k][i] = sub_(x[k][i], f);
+              col[r] = x[k][i];
+            }
+          }
+        }
+      }
+      ph ^= 1;
+      if (c == j + 1) {
+        __syncthreads();   // every thread's rows of u_{j+1} are stored
+        if (tid == 0) st_release(ready1 + c, 1u);
+        qr_form<S, NR>(x[0], M + (int64_t)c * d, d, c, tau, scv, ready2, sh, ph);
+      }
+      c += kb * G;
+    }
   }
 }
 
@@ -333,39 +560,64 @@ int coop_grid(K kernel, int threads, size_t smem, int* grid) {
 
 }  // namespace
 
-// workspace: tau (n), X copy (n*n), V (n*n), norms (n doubles), flags (4 ints)
+// workspace: tau (n), sc (n), X copy (n*n), V (n*n), norms (n doubles), flags (4 ints),
+// reflector ready flags (2n)
 size_t factor_workspace_bytes(int64_t d, int64_t n, size_t esz) {
   (void)d;
   size_t b = 0;
   auto add = [&](size_t x) { b += (x + 255) & ~(size_t)255; };
   add(n * esz);
+  add(n * esz);
   add(n * n * esz);
   add(n * n * esz);
   add(n * sizeof(double));
   add(4 * sizeof(int));
+  add(2 * n * sizeof(unsigned));
   return b;
 }
 
-// Rout (col-major) and Rout_r (row-major) are optional copies of R; with do_svd == false the
-// Jacobi SVD (sigma, Vt) is skipped.
+template <class S, int NR>
+int qr_flow_launch(S* SA, int d, int n, S* tau, S* scv, unsigned* ready, int* err, cudaStream_t st) {
+  const int nt = 32 * ((d + 32 * NR - 1) / (32 * NR));   // NT * NR >= d, fewer than 32 * NR idle rows
+  int per_sm = 0;
+  RL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, qr_flow_kernel<S, NR>, nt, 0));
+  if (per_sm < 1) return RLOBPCG_ERR_UNSUPPORTED;
+  // two CTAs per SM measured faster than one (a CTA's backlog of non-pivot columns no longer
+  // delays its next pivot) and than more (the SM's FP64 pipe is shared)
+  const int G = (int)min((int64_t)min(per_sm, 2) * num_sms(), (int64_t)n);
+  RL_CUDA(cudaMemsetAsync(ready, 0, (size_t)2 * n * sizeof(unsigned), st));
+  void* args[] = {(void*)&SA, (void*)&d, (void*)&n, (void*)&tau, (void*)&scv, (void*)&ready, (void*)&err};
+  RL_CUDA(cudaLaunchCooperativeKernel((void*)qr_flow_kernel<S, NR>, dim3(G), dim3(nt), args, 0, st));
+  note_launch();
+  return RLOBPCG_OK;
+}
+
+// err: device word that receives DEV_ERR_TIMEOUT if a bounded wait of the QR runs out.
 template <class S>
 int factor_impl(S* SA, int d, int n, S* Rout, S* Rout_r, double* sigma, S* Vt, S* Rinv_r, S* Rinv_c,
-                void* work, size_t work_bytes, cudaStream_t st, int* sweeps_host, bool do_svd) {
-  if (work_bytes < factor_workspace_bytes(d, n, sizeof(S))) return RLOBPCG_ERR_INVALID_ARG;
+                void* work, size_t work_bytes, cudaStream_t st, int* sweeps_host, bool do_svd, int* err) {
+  if (work_bytes < factor_workspace_bytes(d, n, sizeof(S)) || !err) return RLOBPCG_ERR_INVALID_ARG;
   unsigned char* p = (unsigned char*)work;
   auto take = [&](size_t x) { void* r = p; p += (x + 255) & ~(size_t)255; return r; };
   S* tau = (S*)take((size_t)n * sizeof(S));
+  S* scv = (S*)take((size_t)n * sizeof(S));
   S* X = (S*)take((size_t)n * n * sizeof(S));
   S* V = (S*)take((size_t)n * n * sizeof(S));
   double* nrm = (double*)take((size_t)n * sizeof(double));
   int* flags = (int*)take(4 * sizeof(int));
+  unsigned* ready = (unsigned*)take((size_t)2 * n * sizeof(unsigned));
 
-  // 1. Householder QR
-  int G = 0;
-  int rc = coop_grid(qr_kernel<S>, FQ_THREADS, 0, &G);
-  if (rc) return rc;
-  G = min(G, max(1, n));
-  {
+  // 1. Householder QR: the dataflow kernel holds each thread's rows of a column in registers
+  // (d <= 4096); taller sketches take the kernel with one grid barrier per column.
+  int G = 0, rc = 0;
+  if (d <= 8 * kQrMaxThreads) {
+    RL_TRY((qr_flow_launch<S, 8>(SA, d, n, tau, scv, ready, err, st)));
+  } else if (d <= 16 * kQrMaxThreads) {
+    RL_TRY((qr_flow_launch<S, 16>(SA, d, n, tau, scv, ready, err, st)));
+  } else {
+    rc = coop_grid(qr_kernel<S>, FQ_THREADS, 0, &G);
+    if (rc) return rc;
+    G = min(G, max(1, n));
     void* args[] = {(void*)&SA, (void*)&d, (void*)&n, (void*)&tau};
     RL_CUDA(cudaLaunchCooperativeKernel((void*)qr_kernel<S>, dim3(G), dim3(FQ_THREADS), args, 0, st));
     note_launch();
@@ -418,9 +670,9 @@ int factor_impl(S* SA, int d, int n, S* Rout, S* Rout_r, double* sigma, S* Vt, S
   return RLOBPCG_OK;
 }
 
-template int factor_impl<double>(double*, int, int, double*, double*, double*, double*, double*, double*, void*, size_t, cudaStream_t, int*, bool);
-template int factor_impl<float>(float*, int, int, float*, float*, double*, float*, float*, float*, void*, size_t, cudaStream_t, int*, bool);
-template int factor_impl<cd>(cd*, int, int, cd*, cd*, double*, cd*, cd*, cd*, void*, size_t, cudaStream_t, int*, bool);
-template int factor_impl<cf>(cf*, int, int, cf*, cf*, double*, cf*, cf*, cf*, void*, size_t, cudaStream_t, int*, bool);
+template int factor_impl<double>(double*, int, int, double*, double*, double*, double*, double*, double*, void*, size_t, cudaStream_t, int*, bool, int*);
+template int factor_impl<float>(float*, int, int, float*, float*, double*, float*, float*, float*, void*, size_t, cudaStream_t, int*, bool, int*);
+template int factor_impl<cd>(cd*, int, int, cd*, cd*, double*, cd*, cd*, cd*, void*, size_t, cudaStream_t, int*, bool, int*);
+template int factor_impl<cf>(cf*, int, int, cf*, cf*, double*, cf*, cf*, cf*, void*, size_t, cudaStream_t, int*, bool, int*);
 
 }  // namespace rl

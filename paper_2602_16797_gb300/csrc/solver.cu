@@ -23,7 +23,7 @@ int sketch_dispatch(const void* A, int64_t m, int64_t n, int64_t lda, int dtype,
 size_t factor_workspace_bytes(int64_t d, int64_t n, size_t esz);
 template <class S>
 int factor_impl(S* SA, int d, int n, S* Rout, S* Rout_r, double* sigma, S* Vt, S* Rinv_r, S* Rinv_c, void* work,
-                size_t work_bytes, cudaStream_t st, int* sweeps_host, bool do_svd);
+                size_t work_bytes, cudaStream_t st, int* sweeps_host, bool do_svd, int* err);
 template <class T>
 int fill_random_launch(T* Z, int64_t rows, int q, int64_t ld, uint64_t seed, cudaStream_t st);
 template <class T>
@@ -234,7 +234,7 @@ int solve_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, double tau, double* s
   int sweeps = 0;
   const bool exact = p->opts.exact_sketch_svd != 0;
   RL_TRY(factor_impl<S>((S*)p->SA, d, n, (S*)p->R_c, (S*)p->R_r, p->sk_sigma, (S*)p->Vt, (S*)p->Rinv_r,
-                        (S*)p->Rinv_c, p->fwork, p->fwork_bytes, st, &sweeps, exact));
+                        (S*)p->Rinv_c, p->fwork, p->fwork_bytes, st, &sweeps, exact, p->err));
   double sigma11 = 0;
   if (exact) {
     RL_CUDA(cudaMemcpyAsync(&sigma11, p->sk_sigma, sizeof(double), cudaMemcpyDeviceToHost, st));

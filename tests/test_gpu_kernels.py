@@ -199,7 +199,10 @@ def _sub_sin(V1, V2):
     return np.linalg.norm(Q1 - Q2 @ (Q2.conj().T @ Q1), 2)
 
 
-@pytest.mark.parametrize("d,n", [(200, 50), (37, 36), (1500, 500), (400, 101)])
+# (1900, 700): more columns than resident CTAs, so CTAs own several; (2500, 300): 16 rows per
+# thread; (4500, 120): taller than the register-resident QR, the grid-barrier kernel
+@pytest.mark.parametrize("d,n", [(200, 50), (37, 36), (1500, 500), (400, 101), (1900, 700), (2500, 300),
+                                 (4500, 120), (1, 1), (257, 257)])
 @pytest.mark.parametrize("cplx", [False, True])
 def test_factor_parity_f64(d, n, cplx):
     rng = np.random.default_rng(d + n)
@@ -216,12 +219,31 @@ def test_factor_parity_f64(d, n, cplx):
     assert np.all(np.abs(sig - s0) <= 50 * n * U * s0[0])
     assert np.all(np.diff(sig) <= 0)
     # the bottom 3 right singular vectors (the start block) span the same subspace
-    gap = (s0[-4] - s0[-3]) / s0[0]
-    assert _sub_sin(Vt[:, -3:], V0[:, -3:]) <= max(1e-10, 1e3 * n * U / gap)
+    if n >= 4:
+        gap = (s0[-4] - s0[-3]) / s0[0]
+        assert _sub_sin(Vt[:, -3:], V0[:, -3:]) <= max(1e-10, 1e3 * n * U / gap)
     assert np.allclose(Vt.conj().T @ Vt, np.eye(n), atol=1e3 * n * U)
     # R^{-1} R = I to kappa u
     kappa = s0[0] / s0[-1]
     assert np.allclose(Rinv @ R, np.eye(n), atol=1e2 * n * U * kappa)
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_factor_rank_deficient_sketch(cplx):
+    # exact zero columns keep tau = 0 and R(j, j) = 0 exactly; a repeated column gives a diagonal
+    # entry at rounding level; R^H R = SA^H SA still holds to rounding
+    rng = np.random.default_rng(11)
+    d, n = 900, 300
+    SA = _rand(rng, (d, n), cplx)
+    SA[:, 5:9] = 0
+    SA[:, 40] = SA[:, 3]
+    R, sig, Vt, Rinv = gpu_factor(SA, "f64")
+    s0 = np.linalg.svd(SA, compute_uv=False)
+    assert np.all(np.tril(R, -1) == 0)
+    assert np.all(R[5:9, 5:9] == 0) and np.all(R[:, 5:9] == 0)
+    assert abs(R[40, 40]) <= 1e2 * n * U * s0[0]
+    assert np.allclose(R.conj().T @ R, SA.conj().T @ SA, rtol=0, atol=100 * n * U * s0[0] ** 2)
+    assert np.all(np.abs(sig - s0) <= 50 * n * U * s0[0])
 
 
 @pytest.mark.parametrize("cplx", [False, True])
