@@ -26,18 +26,27 @@
 // is that of the digit truncation, about 2^-55 of the group maxima per term, which is the size
 // of an FP64 dot product's own rounding. Tensor cores do the O(m n b) work; FP64 does O((m+n) b).
 //
-// Layouts (bf16 digits, no-swizzle K-major core-matrix order of tc.cuh, 4 KB per 128 x 16
-// digit tile): A_rt[r][kb][p] -- row tile r (128 rows), column block kb (16 columns), digit p --
-// for the first product; A_ct[ct][rc][kb][p] -- column tile ct (128 columns) as the M side,
-// row chunk rc (128 rows = 8 blocks of 16) as the K side -- for the second. Every pipeline stage
-// is then one contiguous 32 KB bulk copy of A digits plus the matching B digits. A is constant
-// through a solve, so it is split once per solve; W and AW are split once per pass.
+// Layouts. A is split once per solve and kept as one BYTE per digit, u_p = d_p + 64 in [0, 127]
+// (8 bytes per element, as many as the FP64 value itself); the kernel expands them to bf16 on
+// chip: a byte permute puts 0x43 above each byte, giving the bf16 128 + u_p, and one bf16x2 add
+// of -192 leaves d_p, exactly (two digits per two instructions). Digits in [-64, 63] need
+// |rint(x 2^(55-E))| below 0.992 * 2^55, so an A group takes E with max |x| * 65/64 < 2^E. A
+// digit tile is 128 x 16 elements: 256 units of (M index i, K half h), each 64 bytes [p][8 k]
+// stored as four 16-byte chunks at 4096 c + 16 u (unit u = 128 h + i), so that a warp of
+// converter threads reads 512 consecutive bytes per chunk and writes 32 consecutive 16-byte rows of
+// the no-swizzle K-major core-matrix order of tc.cuh (row i of K half h sits at byte
+// 2048 h + 16 i of each 4 KB bf16 digit tile). A_rt[r][kb] -- row tile r (128 rows), column
+// block kb (16 columns) -- for the first product; A_ct[ct][rc][kb] -- column tile ct (128
+// columns) as the M side, row chunk rc (128 rows = 8 blocks of 16) as the K side -- for the
+// second. W and AW are split once per pass, straight into bf16 digit tiles.
 //
-// Kernel shape: one CTA per SM, 192 threads: warp 0 issues the bulk copies (5-stage ring of
-// mbarriers), warp 1 owns TMEM and issues the MMAs from one thread, warps 2-5 read the
-// accumulators (two TMEM buffers, so reading one unit overlaps the MMAs of the next), zero them,
-// and do the FP64 recombination; the last CTA of each column tile of the second product sums
-// the per-CTA partials in a fixed order. Every wait is bounded and reports DEV_ERR_TIMEOUT.
+// Kernel shape: one CTA per SM, 448 threads: warp 0 issues the bulk copies of the B digits
+// (5-stage ring of mbarriers), warp 1 owns TMEM and issues the MMAs from one thread, warps 2-5
+// read the accumulators (two TMEM buffers, so reading one unit overlaps the MMAs of the next),
+// zero them, and do the FP64 recombination, and warps 6-13 load the A digit bytes (four stages
+// ahead, in registers) and write each stage's eight bf16 digit tiles; the last CTA of each
+// column tile of the second product sums the per-CTA partials in a fixed order. Every wait is
+// bounded and reports DEV_ERR_TIMEOUT.
 #include "common.cuh"
 #include "split.cuh"
 #include "tc.cuh"
@@ -57,9 +66,12 @@ using split::SPLIT_W_READY;
 constexpr int TM = 128;                // MMA M: rows (first product) or columns (second) per tile
 constexpr int KC_KB = 32;              // k-blocks per exact accumulation: 32 x 16 = 512 terms
 constexpr int CH_KB = TM / TK;         // k-blocks per 128-row chunk of the second product
-constexpr int NST = 5;                 // pipeline stages
-constexpr int SLICE_BYTES = TM * TK * 2;
-constexpr int NTH = 192;
+constexpr int NST = 3;                 // bf16 digit stages (MMA operands)
+constexpr int NSB = 7;                 // byte-digit staging slots (bulk copies in flight)
+constexpr int SLICE_BYTES = TM * TK * 2;   // one bf16 digit tile
+constexpr int TILE_U8 = TM * TK * SL;      // the byte digits of one 128 x 16 tile (all 8 digits)
+constexpr int NCW = 8;                     // converter warps (one 64-byte unit per thread per stage)
+constexpr int NTH = 192 + 32 * NCW;
 
 __host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 inline size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -77,8 +89,8 @@ PrepLayout prep_layout(int64_t m, int64_t n) {
   PrepLayout L;
   size_t off = 0;
   auto take = [&](size_t bytes) { const size_t o = off; off += a256(bytes); return o; };
-  L.art = take((size_t)d.R1 * d.NKB * SL * SLICE_BYTES);
-  L.act = take((size_t)d.CT * d.R1 * CH_KB * SL * SLICE_BYTES);
+  L.art = take((size_t)d.R1 * d.NKB * TILE_U8);
+  L.act = take((size_t)d.CT * d.R1 * CH_KB * TILE_U8);
   L.erow = take((size_t)d.R1 * TM * sizeof(int));
   L.ecol = take((size_t)d.R1 * d.NC * sizeof(int));
   L.cnt = take((size_t)d.CT * sizeof(int));   // finished-CTA counters of the second product
@@ -107,13 +119,6 @@ WorkLayout work_layout(int64_t m, int64_t n, int b) {
   return L;
 }
 
-// inverse of core_off for R = 128: position o -> (row, kk), so that consecutive threads write
-// consecutive digits
-__device__ __forceinline__ void core_pos128(int o, int& row, int& kk) {
-  kk = ((o >> 10) << 3) | (o & 7);
-  row = (((o & 1023) >> 6) << 3) | ((o & 63) >> 3);
-}
-
 __device__ __forceinline__ double warp_max(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -121,6 +126,34 @@ __device__ __forceinline__ double warp_max(double v) {
 }
 
 // ---- one-time split of A ---------------------------------------------------------------------------
+// Exponent of a group of A: max |x| * 65/64 < 2^E (see the byte form above).
+__device__ __forceinline__ int group_exp_a(double amax) { return group_exp(amax * 1.015625); }
+
+// Byte digits of 8 values sharing exponent E: w[2p + kk/4] holds u_p of value kk in byte kk%4,
+// u_p the base-128 digits of V + OFF, V = rint(x 2^(55-E)), OFF = 64 sum_p 128^p, so that
+// V = sum_p (u_p - 64) 128^(7-p) with every u_p in [0, 127].
+__device__ __forceinline__ void digit_bytes(const double (&x)[8], int E, uint32_t (&w)[16]) {
+  constexpr long long OFF = (64LL * ((1LL << 56) - 1)) / 127;
+#pragma unroll
+  for (int q = 0; q < 16; ++q) w[q] = 0;
+#pragma unroll
+  for (int kk = 0; kk < 8; ++kk) {
+    const unsigned long long Y =
+        (unsigned long long)(__double2ll_rn(split::mul_pow2(x[kk], 55 - E)) + OFF);
+#pragma unroll
+    for (int p = 0; p < SL; ++p)
+      w[2 * p + (kk >> 2)] |= (uint32_t)((Y >> (7 * (SL - 1 - p))) & 127u) << (8 * (kk & 3));
+  }
+}
+
+// 16-byte chunk c of unit t (digits 2c and 2c + 1) lives at byte 4096 c + 16 t of the tile, so
+// that a warp reading chunk c of 32 consecutive units touches 512 consecutive bytes
+__device__ __forceinline__ void store_unit(unsigned char* tile, int t, const uint32_t (&w)[16]) {
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+    *reinterpret_cast<uint4*>(tile + c * 4096 + t * 16) = make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
+}
+
 __global__ void row_exp_kernel(const double* __restrict__ A, int64_t m, int n, int64_t lda, int64_t mpad,
                                int* __restrict__ erow) {
   const int64_t i = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
@@ -130,29 +163,24 @@ __global__ void row_exp_kernel(const double* __restrict__ A, int64_t m, int n, i
   if (i < m)
     for (int k = lane; k < n; k += 32) mx = fmax(mx, fabs(A[i * lda + k]));
   mx = warp_max(mx);
-  if (lane == 0) erow[i] = group_exp(mx);
+  if (lane == 0) erow[i] = group_exp_a(mx);
 }
 
+// one CTA per 128 x 16 tile (r, kb); thread t writes unit t (row t % 128, K half t / 128)
 __global__ void __launch_bounds__(256) rt_digits_kernel(const double* __restrict__ A, int64_t m, int n, int64_t lda,
                                                         const int* __restrict__ erow, int64_t NKB,
-                                                        uint16_t* __restrict__ Art) {
+                                                        unsigned char* __restrict__ Art) {
   const int64_t r = blockIdx.x, kb = blockIdx.y;
-  uint16_t* out = Art + (size_t)((r * NKB + kb) * SL) * (TM * TK);
-  for (int o = threadIdx.x; o < TM * TK; o += 256) {
-    int row, kk;
-    core_pos128(o, row, kk);
-    const int64_t i = r * TM + row, k = kb * TK + kk;
-    double x = 0;
-    int E = 0;
-    if (i < m) {
-      E = erow[i];
-      if (k < n) x = A[i * lda + k];
-    }
-    int d[SL];
-    split8(x, E, d);
+  const int t = threadIdx.x, row = t & 127, h = t >> 7;
+  const int64_t i = r * TM + row, k0 = kb * TK + h * 8;
+  double x[8];
+  int E = 0;
+  if (i < m) E = erow[i];
 #pragma unroll
-    for (int p = 0; p < SL; ++p) out[p * (TM * TK) + o] = bf16_of(d[p]);
-  }
+  for (int kk = 0; kk < 8; ++kk) x[kk] = (i < m && k0 + kk < n) ? A[i * lda + k0 + kk] : 0.0;
+  uint32_t w[16];
+  digit_bytes(x, E, w);
+  store_unit(Art + (size_t)(r * NKB + kb) * TILE_U8, t, w);
 }
 
 __global__ void col_exp_kernel(const double* __restrict__ A, int64_t m, int n, int64_t lda, int64_t NC,
@@ -165,12 +193,15 @@ __global__ void col_exp_kernel(const double* __restrict__ A, int64_t m, int n, i
     const int64_t i1 = min(m, rc * TM + TM);
     for (int64_t i = rc * TM; i < i1; ++i) mx = fmax(mx, fabs(A[i * lda + c]));
   }
-  ecol[rc * NC + c] = group_exp(mx);
+  ecol[rc * NC + c] = group_exp_a(mx);
 }
 
+// one CTA per tile (ct, rc, kb): rows rc * 128 + kb * 16 + [0, 16) of columns ct * 128 + [0, 128),
+// staged through shared memory so that the loads are coalesced; thread t writes unit t
+// (column t % 128 as the M index, K half t / 128)
 __global__ void __launch_bounds__(256) ct_digits_kernel(const double* __restrict__ A, int64_t m, int n, int64_t lda,
                                                         const int* __restrict__ ecol, int64_t NC, int64_t R1,
-                                                        uint16_t* __restrict__ Act) {
+                                                        unsigned char* __restrict__ Act) {
   __shared__ double tile[TK][TM + 1];
   const int64_t rc = blockIdx.x / CH_KB;
   const int kb = (int)(blockIdx.x % CH_KB);
@@ -182,14 +213,34 @@ __global__ void __launch_bounds__(256) ct_digits_kernel(const double* __restrict
     tile[rr][cc] = (i < m && c < n) ? A[i * lda + c] : 0.0;
   }
   __syncthreads();
-  uint16_t* out = Act + (size_t)(((ct * R1 + rc) * CH_KB + kb) * SL) * (TM * TK);
-  for (int o = threadIdx.x; o < TM * TK; o += 256) {
-    int cc, kk;
-    core_pos128(o, cc, kk);   // M index = column, K index = row within the block
-    int d[SL];
-    split8(tile[kk][cc], ecol[rc * NC + c0 + cc], d);
+  const int t = threadIdx.x, cc = t & 127, h = t >> 7;
+  double x[8];
 #pragma unroll
-    for (int p = 0; p < SL; ++p) out[p * (TM * TK) + o] = bf16_of(d[p]);
+  for (int kk = 0; kk < 8; ++kk) x[kk] = tile[h * 8 + kk][cc];
+  uint32_t w[16];
+  digit_bytes(x, ecol[rc * NC + c0 + cc], w);
+  store_unit(Act + (size_t)(((ct * R1 + rc) * CH_KB + kb)) * TILE_U8, t, w);
+}
+
+// Expands one 64-byte unit (8 digits of 8 values) into the bf16 digit tiles of a stage: digit p
+// goes to the 16-byte row at dst + p * SLICE_BYTES.
+__device__ __forceinline__ uint32_t bf16x2_minus192(uint32_t v) {
+  uint32_t r;
+  asm("add.rn.bf16x2 %0, %1, %2;" : "=r"(r) : "r"(v), "r"(0xC340C340u));
+  return r;
+}
+__device__ __forceinline__ void expand_unit(const uint4 (&b)[4], unsigned char* dst) {
+  const uint32_t w[16] = {b[0].x, b[0].y, b[0].z, b[0].w, b[1].x, b[1].y, b[1].z, b[1].w,
+                          b[2].x, b[2].y, b[2].z, b[2].w, b[3].x, b[3].y, b[3].z, b[3].w};
+  constexpr uint32_t HI = 0x43434343u;   // bf16 0x43uu = 128 + uu for uu < 128
+#pragma unroll
+  for (int p = 0; p < SL; ++p) {
+    uint4 o;
+    o.x = bf16x2_minus192(__byte_perm(w[2 * p], HI, 0x4140));
+    o.y = bf16x2_minus192(__byte_perm(w[2 * p], HI, 0x4342));
+    o.z = bf16x2_minus192(__byte_perm(w[2 * p + 1], HI, 0x4140));
+    o.w = bf16x2_minus192(__byte_perm(w[2 * p + 1], HI, 0x4342));
+    *reinterpret_cast<uint4*>(dst + p * SLICE_BYTES) = o;
   }
 }
 
@@ -293,7 +344,7 @@ __global__ void __launch_bounds__(128) y_digits_kernel(const double* __restrict_
 
 // ---- the tensor-core pass ---------------------------------------------------------------------
 struct PassArgs {
-  const uint16_t* Aop;   // A_rt (first product) or A_ct (second)
+  const unsigned char* Aop;   // byte digits A_rt (first product) or A_ct (second)
   const uint16_t* Bop;   // W digits or AW digits
   const int* eA;         // row exponents of A, or column exponents per chunk
   const int* eB;         // W column exponents, or AW column exponents per chunk
@@ -385,19 +436,26 @@ __global__ void __launch_bounds__(NTH, 1) split_pass_kernel(PassArgs g) {
   constexpr uint32_t STG = ABYTES + BBYTES;
   constexpr uint32_t IDESC = tc::idesc_bf16_f32(TM, N);
   extern __shared__ __align__(1024) unsigned char sm[];
-  uint64_t* full = reinterpret_cast<uint64_t*>(sm + NST * STG);
+  unsigned char* bring = sm + NST * STG;   // byte-digit staging slots, TILE_U8 each
+  uint64_t* full = reinterpret_cast<uint64_t*>(bring + NSB * TILE_U8);
   uint64_t* empty = full + NST;
-  uint64_t* accf = empty + NST;
+  uint64_t* bfull = empty + NST;
+  uint64_t* bempty = bfull + NSB;
+  uint64_t* accf = bempty + NSB;
   uint64_t* acce = accf + 2;
   uint64_t* done = acce + 2;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
-  double* red = reinterpret_cast<double*>(sm + NST * STG + 256);   // [2][4][BP]
+  double* red = reinterpret_cast<double*>(bring + NSB * TILE_U8 + 512);   // [2][4][BP]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NST; ++s) {
-      tc::mbar_init(full + s, 1);
+      tc::mbar_init(full + s, 1 + NCW);   // the B copy (with its bytes) and the converter warps
       tc::mbar_init(empty + s, 1);
+    }
+    for (int s = 0; s < NSB; ++s) {
+      tc::mbar_init(bfull + s, 1);
+      tc::mbar_init(bempty + s, NCW);
     }
     for (int a = 0; a < 2; ++a) {
       tc::mbar_init(accf + a, 1);
@@ -421,32 +479,29 @@ __global__ void __launch_bounds__(NTH, 1) split_pass_kernel(PassArgs g) {
   const int64_t NKC = cdiv(g.NKB, KC_KB);
 
   if (warp == 0) {
+    // the A digit bytes of every stage, NSB tiles ahead of the converters
     if (lane == 0) {
       uint32_t u = 0;
       bool ok = true;
-      auto load = [&](const uint16_t* srcA, const uint16_t* srcB) {
-        const int s = (int)(u % NST);
-        if (!tc::mbar_wait(empty + s, ((u / NST) & 1) ^ 1)) return false;
-        unsigned char* stg = sm + (size_t)s * STG;
-        tc::mbar_expect_tx(full + s, STG);
-        tc::bulk_g2s(stg, srcA, ABYTES, full + s);
-        tc::bulk_g2s(stg + ABYTES, srcB, BBYTES, full + s);
+      auto load = [&](const unsigned char* srcA) {
+        const int s = (int)(u % NSB);
+        if (!tc::mbar_wait(bempty + s, ((u / NSB) & 1) ^ 1)) return false;
+        tc::mbar_expect_tx(bfull + s, TILE_U8);
+        tc::bulk_g2s(bring + (size_t)s * TILE_U8, srcA, TILE_U8, bfull + s);
         ++u;
         return true;
       };
       if (MODE == 0) {
         for (int64_t r = blockIdx.x; ok && r < g.R1; r += gridDim.x)
-          for (int64_t kb = 0; ok && kb < g.NKB; ++kb)
-            ok = load(g.Aop + (size_t)((r * g.NKB + kb) * SL) * (TM * TK), g.Bop + (size_t)kb * (N * TK));
+          for (int64_t kb = 0; ok && kb < g.NKB; ++kb) ok = load(g.Aop + (size_t)(r * g.NKB + kb) * TILE_U8);
       } else {
         for (int64_t rc = rc0; ok && rc < rc1; ++rc)
           for (int kb = 0; ok && kb < CH_KB; ++kb)
-            ok = load(g.Aop + (size_t)(((ct * g.R1 + rc) * CH_KB + kb) * SL) * (TM * TK),
-                      g.Bop + (size_t)(rc * CH_KB + kb) * (N * TK));
+            ok = load(g.Aop + (size_t)((ct * g.R1 + rc) * CH_KB + kb) * TILE_U8);
       }
       if (!ok) atomicOr(g.err, DEV_ERR_TIMEOUT);
-      // copies into the last NST stages have landed before the CTA may finish
-      for (uint32_t w = u > (uint32_t)NST ? u - NST : 0; w < u; ++w) tc::mbar_wait(full + (w % NST), (w / NST) & 1);
+      // copies into the last NSB slots have landed before the CTA may finish
+      for (uint32_t w = u > (uint32_t)NSB ? u - NSB : 0; w < u; ++w) tc::mbar_wait(bfull + (w % NSB), (w / NSB) & 1);
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -484,7 +539,7 @@ __global__ void __launch_bounds__(NTH, 1) split_pass_kernel(PassArgs g) {
       tc::mma_commit(done);
       tc::mbar_wait(done, 0);
     }
-  } else {
+  } else if (warp < 6) {
     const int quarter = warp & 3;                 // TMEM lanes 32 * quarter .. + 31
     const int row = 32 * quarter + lane;          // MODE 0: row of the tile; MODE 1: column
     const uint32_t tq = tmem + ((uint32_t)(32 * quarter) << 16);
@@ -589,6 +644,52 @@ __global__ void __launch_bounds__(NTH, 1) split_pass_kernel(PassArgs g) {
       }
     }
     if (!ok) atomicOr(g.err, DEV_ERR_TIMEOUT);
+  } else {
+    // converter warps: thread ci expands unit ci (M index ci % 128, K half ci / 128) of each
+    // stage's A tile from the staging slot into the bf16 digit tiles; the first converter warp
+    // also issues the stage's B copy
+    const int ci = threadIdx.x - 192;
+    const uint32_t soff = (uint32_t)((ci >> 7) * 2048 + (ci & 127) * 16);
+    const int64_t nrt = MODE == 0 ? (blockIdx.x < g.R1 ? (g.R1 - 1 - blockIdx.x) / gridDim.x + 1 : 0) : 0;
+    const uint32_t U = (uint32_t)(MODE == 0 ? nrt * g.NKB : (rc1 - rc0) * CH_KB);
+    const bool issuer = warp == 6 && lane == 0;
+    int64_t cur = MODE == 0 ? 0 : rc0, ckb = 0;   // (row chunk,) k-block of stage u, for B
+    bool ok = true;
+    for (uint32_t u = 0; ok && u < U; ++u) {
+      const int ds = (int)(u % NSB), s = (int)(u % NST);
+      ok = __all_sync(0xffffffffu, tc::mbar_wait(bfull + ds, (u / NSB) & 1));
+      if (!ok) break;
+      uint4 b[4];
+      const unsigned char* sp = bring + (size_t)ds * TILE_U8 + (size_t)ci * 16;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) b[c] = *reinterpret_cast<const uint4*>(sp + c * 4096);
+      ok = __all_sync(0xffffffffu, tc::mbar_wait(empty + s, ((u / NST) & 1) ^ 1));
+      if (!ok) break;
+      unsigned char* stg = sm + (size_t)s * STG;
+      if (issuer) {
+        const uint16_t* srcB = MODE == 0 ? g.Bop + (size_t)ckb * (N * TK) : g.Bop + (size_t)(cur * CH_KB + ckb) * (N * TK);
+        tc::mbar_expect_tx(full + s, BBYTES);
+        tc::bulk_g2s(stg + ABYTES, srcB, BBYTES, full + s);
+      }
+      if (++ckb == (MODE == 0 ? g.NKB : CH_KB)) {
+        ckb = 0;
+        ++cur;
+      }
+      expand_unit(b, stg + soff);
+      // the staging slot is free once every lane's bytes are in registers (expand_unit consumed
+      // them), and the bulk copy that refills it writes through the async proxy; so do the
+      // tensor core's reads of the tiles just written
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      __syncwarp();
+      if (lane == 0) {
+        tc::mbar_arrive(bempty + ds);
+        tc::mbar_arrive(full + s);
+      }
+    }
+    if (!ok && lane == 0) atomicOr(g.err, DEV_ERR_TIMEOUT);
+    // the B copies issued here have landed before the CTA may finish (bounded)
+    if (issuer)
+      for (uint32_t w = U > (uint32_t)NST ? U - NST : 0; w < U; ++w) tc::mbar_wait(full + (w % NST), (w / NST) & 1);
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -601,7 +702,7 @@ __global__ void __launch_bounds__(NTH, 1) split_pass_kernel(PassArgs g) {
 template <int BP, int MODE>
 int launch_pass(const PassArgs& a, int grid, cudaStream_t st) {
   constexpr uint32_t STG = SL * SLICE_BYTES + SL * BP * TK * 2;
-  const size_t smem = (size_t)NST * STG + 256 + 2 * 4 * BP * sizeof(double);
+  const size_t smem = (size_t)NST * STG + (size_t)NSB * TILE_U8 + 512 + 2 * 4 * BP * sizeof(double);
   RL_TRY(allow_dynamic_smem(split_pass_kernel<BP, MODE>, smem));
   split_pass_kernel<BP, MODE><<<grid, NTH, smem, st>>>(a);
   RL_CHECK_LAUNCH();
@@ -625,7 +726,7 @@ int split_gram_bp(const unsigned char* prep, int64_t m, int64_t n, const double*
       RL_CHECK_LAUNCH();
     }
     PassArgs a{};
-    a.Aop = (const uint16_t*)(prep + P.art);
+    a.Aop = prep + P.art;
     a.Bop = (const uint16_t*)(work + L.wsl);
     a.eA = (const int*)(prep + P.erow);
     a.eB = (const int*)(work + L.f);
@@ -639,7 +740,7 @@ int split_gram_bp(const unsigned char* prep, int64_t m, int64_t n, const double*
   }
   if (mid) RL_CUDA(cudaEventRecord(mid, st));
   PassArgs a{};
-  a.Aop = (const uint16_t*)(prep + P.act);
+  a.Aop = prep + P.act;
   a.Bop = Ysl;
   a.eA = (const int*)(prep + P.ecol);
   a.eB = H;
@@ -677,12 +778,12 @@ int split_prepare(const double* A, int64_t m, int64_t n, int64_t lda, void* prep
   row_exp_kernel<<<(unsigned)cdiv(mpad, 8), 256, 0, st>>>(A, m, (int)n, lda, mpad, erow);
   RL_CHECK_LAUNCH();
   rt_digits_kernel<<<dim3((unsigned)d.R1, (unsigned)d.NKB), 256, 0, st>>>(A, m, (int)n, lda, erow, d.NKB,
-                                                                         (uint16_t*)(base + P.art));
+                                                                         base + P.art);
   RL_CHECK_LAUNCH();
   col_exp_kernel<<<dim3((unsigned)d.R1, (unsigned)cdiv(d.NC, 256)), 256, 0, st>>>(A, m, (int)n, lda, d.NC, ecol);
   RL_CHECK_LAUNCH();
   ct_digits_kernel<<<dim3((unsigned)(d.R1 * CH_KB), (unsigned)d.CT), 256, 0, st>>>(A, m, (int)n, lda, ecol, d.NC, d.R1,
-                                                                                  (uint16_t*)(base + P.act));
+                                                                                  base + P.act);
   RL_CHECK_LAUNCH();
   return RLOBPCG_OK;
 }
