@@ -274,8 +274,9 @@ int rlobpcg_gram_noalloc(const void* A, int64_t m, int64_t n, int64_t lda, int d
  * tensor cores' f32 accumulators and are recombined in FP64. Per product term the error is about
  * 2^-55 times the product of the two group maxima.
  *   rlobpcg_gram_split_prepare: split A (m x n, row-major, lda) once -- it is constant through a
- *     solve -- into prep, rlobpcg_gram_split_prepare_size(m, n) bytes of device memory (about 32
- *     bytes per element of A).
+ *     solve -- into prep, rlobpcg_gram_split_prepare_size(m, n) bytes of device memory (about 16
+ *     bytes per element of A: one byte per digit, in the layouts of both products). Errors as
+ *     below; NONFINITE when A holds Inf or NaN.
  *   rlobpcg_gram_split: one pass; W (n x b, ldw), AW (m x b, ldaw), G (n x b, ldg) row-major,
  *     1 <= b <= 16; work: rlobpcg_gram_split_workspace_size(m, n, b) bytes of device scratch.
  * All pointers are device memory owned by the caller; calls are asynchronous on `stream` and

@@ -19,7 +19,8 @@ int gram_dispatch(const void* A, int64_t m, int64_t n, int64_t lda, int dtype, c
 size_t tsqr_workspace_bytes(int64_t m, int c, size_t esz);
 size_t split_prep_bytes(int64_t m, int64_t n);
 size_t split_work_bytes(int64_t m, int64_t n, int b);
-int split_prepare(const double* A, int64_t m, int64_t n, int64_t lda, void* prep, size_t prep_bytes, cudaStream_t st);
+int split_prepare(const double* A, int64_t m, int64_t n, int64_t lda, void* prep, size_t prep_bytes, int* err,
+                  cudaStream_t st);
 int split_gram(const void* prep, int64_t m, int64_t n, const double* W, int b, int64_t ldw, double* AW, int64_t ldaw,
                double* G, int64_t ldg, void* work, size_t work_bytes, int flags, int* err, cudaEvent_t mid,
                cudaStream_t st);
@@ -182,9 +183,11 @@ extern "C" size_t rlobpcg_gram_split_prepare_size(int64_t m, int64_t n) { return
 extern "C" int rlobpcg_gram_split_prepare(const double* A, int64_t m, int64_t n, int64_t lda, void* prep,
                                           size_t prep_bytes, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
-  const int rc = split_prepare(A, m, n, lda, prep, prep_bytes, st);
+  int* err = step_err_word(st);
+  if (!err) return RLOBPCG_ERR_OOM;
+  const int rc = split_prepare(A, m, n, lda, prep, prep_bytes, err, st);
   if (rc) return rc;
-  return finish(st, nullptr);
+  return finish(st, err);
 }
 
 extern "C" size_t rlobpcg_gram_split_workspace_size(int64_t m, int64_t n, int b) { return split_work_bytes(m, n, b); }

@@ -129,41 +129,108 @@ __device__ __forceinline__ double warp_max(double v) {
 // Exponent of a group of A: max |x| * 65/64 < 2^E (see the byte form above).
 __device__ __forceinline__ int group_exp_a(double amax) { return group_exp(amax * 1.015625); }
 
+// rint(x 2^(55-E)) (ties away from zero) for |x| < 2^E, from the bits of x with integer
+// instructions only (the FP64 pipe is the scarce one on GB300)
+__device__ __forceinline__ long long scaled_int(double x, int E) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((bits >> 52) & 0x7ff);
+  unsigned long long M = bits & 0xfffffffffffffull;
+  int eb = 1;                     // x = M 2^(eb - 1075); subnormals keep eb = 1
+  if (e) {
+    M |= 1ull << 52;
+    eb = e;
+  }
+  const int sh = eb - 1020 - E;   // x 2^(55-E) = M 2^sh, sh <= 2 since |x| < 2^E
+  unsigned long long X = 0;
+  if (sh >= 0) {
+    X = M << sh;
+  } else if (sh > -64) {
+    const int r = -sh;
+    X = (M + (1ull << (r - 1))) >> r;   // M + 2^62 < 2^63: no overflow
+  }
+  return (bits >> 63) ? -(long long)X : (long long)X;
+}
+
 // Byte digits of 8 values sharing exponent E: w[2p + kk/4] holds u_p of value kk in byte kk%4,
 // u_p the base-128 digits of V + OFF, V = rint(x 2^(55-E)), OFF = 64 sum_p 128^p, so that
 // V = sum_p (u_p - 64) 128^(7-p) with every u_p in [0, 127].
 __device__ __forceinline__ void digit_bytes(const double (&x)[8], int E, uint32_t (&w)[16]) {
-  constexpr long long OFF = (64LL * ((1LL << 56) - 1)) / 127;
+  constexpr unsigned long long OFF = (64ull * ((1ull << 56) - 1)) / 127;
 #pragma unroll
   for (int q = 0; q < 16; ++q) w[q] = 0;
 #pragma unroll
   for (int kk = 0; kk < 8; ++kk) {
-    const unsigned long long Y =
-        (unsigned long long)(__double2ll_rn(split::mul_pow2(x[kk], 55 - E)) + OFF);
+    const unsigned long long Y = (unsigned long long)scaled_int(x[kk], E) + OFF;
+    const uint32_t lo = (uint32_t)Y, hi = (uint32_t)(Y >> 32);
+    // digit p holds bits [7 (7 - p), 7 (7 - p) + 7) of Y
+    const uint32_t d[SL] = {(hi >> 17) & 127u, (hi >> 10) & 127u, (hi >> 3) & 127u, __funnelshift_r(lo, hi, 28) & 127u,
+                            (lo >> 21) & 127u, (lo >> 14) & 127u, (lo >> 7) & 127u, lo & 127u};
 #pragma unroll
-    for (int p = 0; p < SL; ++p)
-      w[2 * p + (kk >> 2)] |= (uint32_t)((Y >> (7 * (SL - 1 - p))) & 127u) << (8 * (kk & 3));
+    for (int p = 0; p < SL; ++p) w[2 * p + (kk >> 2)] |= d[p] << (8 * (kk & 3));
   }
 }
 
-// 16-byte chunk c of unit t (digits 2c and 2c + 1) lives at byte 4096 c + 16 t of the tile, so
-// that a warp reading chunk c of 32 consecutive units touches 512 consecutive bytes
 __device__ __forceinline__ void store_unit(unsigned char* tile, int t, const uint32_t (&w)[16]) {
 #pragma unroll
   for (int c = 0; c < 4; ++c)
     *reinterpret_cast<uint4*>(tile + c * 4096 + t * 16) = make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
 }
 
-__global__ void row_exp_kernel(const double* __restrict__ A, int64_t m, int n, int64_t lda, int64_t mpad,
-                               int* __restrict__ erow) {
-  const int64_t i = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-  const int lane = threadIdx.x & 31;
-  if (i >= mpad) return;
-  double mx = 0;
-  if (i < m)
-    for (int k = lane; k < n; k += 32) mx = fmax(mx, fabs(A[i * lda + k]));
-  mx = warp_max(mx);
-  if (lane == 0) erow[i] = group_exp_a(mx);
+// One CTA per 128-row chunk rc: the row exponents of its rows and the column exponents of the
+// chunk (the groups of the two products), from one read of A; maxima are taken on the bit
+// patterns of |x| (ordered like the values), which also flags NaN and infinity.
+__global__ void __launch_bounds__(256) exp_scan_kernel(const double* __restrict__ A, int64_t m, int n, int64_t lda,
+                                                       int64_t NC, int* __restrict__ erow, int* __restrict__ ecol,
+                                                       int* err) {
+  constexpr unsigned long long ABS = 0x7fffffffffffffffull, INF = 0x7ff0000000000000ull;
+  __shared__ unsigned long long cmax[8][512];
+  __shared__ unsigned long long rmax[TM];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t rc = blockIdx.x, i0 = rc * TM;
+  const int nrow = (int)min((int64_t)TM, m - i0);
+  bool bad = false;
+  for (int r = threadIdx.x; r < TM; r += 256) rmax[r] = 0;
+  __syncthreads();
+  for (int64_t c0 = 0; c0 < NC; c0 += 512) {
+    unsigned long long cm[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) cm[q] = 0;
+    for (int r = warp; r < nrow; r += 8) {
+      const double* row = A + (i0 + r) * lda;
+      unsigned long long rm = 0;
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int64_t c = c0 + q * 32 + lane;
+        if (c < n) {
+          const unsigned long long key = (unsigned long long)__double_as_longlong(row[c]) & ABS;
+          rm = max(rm, key);
+          cm[q] = max(cm[q], key);
+        }
+      }
+      const unsigned hi = __reduce_max_sync(0xffffffffu, (unsigned)(rm >> 32));
+      const unsigned lo = __reduce_max_sync(0xffffffffu, (unsigned)(rm >> 32) == hi ? (unsigned)rm : 0u);
+      if (lane == 0) rmax[r] = max(rmax[r], ((unsigned long long)hi << 32) | lo);
+    }
+#pragma unroll
+    for (int q = 0; q < 16; ++q) cmax[warp][q * 32 + lane] = cm[q];
+    __syncthreads();
+    for (int c = threadIdx.x; c < 512; c += 256) {
+      unsigned long long v = 0;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) v = max(v, cmax[w][c]);
+      if (c0 + c < NC) {
+        bad |= v >= INF;
+        ecol[rc * NC + c0 + c] = group_exp_a(__longlong_as_double((long long)v));
+      }
+    }
+    __syncthreads();
+  }
+  for (int r = threadIdx.x; r < TM; r += 256) {
+    const unsigned long long v = rmax[r];
+    bad |= v >= INF;
+    erow[i0 + r] = group_exp_a(__longlong_as_double((long long)v));
+  }
+  if (bad && err) atomicOr(err, DEV_ERR_NONFINITE);
 }
 
 // one CTA per 128 x 16 tile (r, kb); thread t writes unit t (row t % 128, K half t / 128)
@@ -181,19 +248,6 @@ __global__ void __launch_bounds__(256) rt_digits_kernel(const double* __restrict
   uint32_t w[16];
   digit_bytes(x, E, w);
   store_unit(Art + (size_t)(r * NKB + kb) * TILE_U8, t, w);
-}
-
-__global__ void col_exp_kernel(const double* __restrict__ A, int64_t m, int n, int64_t lda, int64_t NC,
-                               int* __restrict__ ecol) {
-  const int64_t rc = blockIdx.x;
-  const int64_t c = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
-  if (c >= NC) return;
-  double mx = 0;
-  if (c < n) {
-    const int64_t i1 = min(m, rc * TM + TM);
-    for (int64_t i = rc * TM; i < i1; ++i) mx = fmax(mx, fabs(A[i * lda + c]));
-  }
-  ecol[rc * NC + c] = group_exp_a(mx);
 }
 
 // one CTA per tile (ct, rc, kb): rows rc * 128 + kb * 16 + [0, 16) of columns ct * 128 + [0, 128),
@@ -764,23 +818,21 @@ size_t split_work_bytes(int64_t m, int64_t n, int b) {
   return (m < 1 || n < 1 || b < 1 || b > 16) ? 0 : work_layout(m, n, b).total;
 }
 
-int split_prepare(const double* A, int64_t m, int64_t n, int64_t lda, void* prep, size_t prep_bytes, cudaStream_t st) {
+int split_prepare(const double* A, int64_t m, int64_t n, int64_t lda, void* prep, size_t prep_bytes, int* err,
+                  cudaStream_t st) {
   if (!A || !prep || m < 1 || n < 1 || lda < n) return RLOBPCG_ERR_INVALID_ARG;
   const PrepLayout P = prep_layout(m, n);
   if (prep_bytes < P.total) return RLOBPCG_ERR_INVALID_ARG;
   const Dims d = dims_of(m, n);
-  if (d.NKB > 65535 || cdiv(d.NC, 256) > 65535) return RLOBPCG_ERR_UNSUPPORTED;
+  if (d.NKB > 65535 || d.R1 * CH_KB > 2147483647LL) return RLOBPCG_ERR_UNSUPPORTED;
   unsigned char* base = (unsigned char*)prep;
   int* erow = (int*)(base + P.erow);
   int* ecol = (int*)(base + P.ecol);
-  const int64_t mpad = d.R1 * TM;
   RL_CUDA(cudaMemsetAsync(base + P.cnt, 0, (size_t)d.CT * sizeof(int), st));
-  row_exp_kernel<<<(unsigned)cdiv(mpad, 8), 256, 0, st>>>(A, m, (int)n, lda, mpad, erow);
+  exp_scan_kernel<<<(unsigned)d.R1, 256, 0, st>>>(A, m, (int)n, lda, d.NC, erow, ecol, err);
   RL_CHECK_LAUNCH();
   rt_digits_kernel<<<dim3((unsigned)d.R1, (unsigned)d.NKB), 256, 0, st>>>(A, m, (int)n, lda, erow, d.NKB,
                                                                          base + P.art);
-  RL_CHECK_LAUNCH();
-  col_exp_kernel<<<dim3((unsigned)d.R1, (unsigned)cdiv(d.NC, 256)), 256, 0, st>>>(A, m, (int)n, lda, d.NC, ecol);
   RL_CHECK_LAUNCH();
   ct_digits_kernel<<<dim3((unsigned)(d.R1 * CH_KB), (unsigned)d.CT), 256, 0, st>>>(A, m, (int)n, lda, ecol, d.NC, d.R1,
                                                                                   base + P.act);

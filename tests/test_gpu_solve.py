@@ -276,11 +276,13 @@ def test_loewner_backward_error():
     assert np.allclose(g[1].T @ g[1], np.eye(2), atol=1e-12)
 
 
-def test_nonfinite_input_is_reported():
+@pytest.mark.parametrize("gram", ["split", "fp64"])
+@pytest.mark.parametrize("bad", [np.nan, np.inf])
+def test_nonfinite_input_is_reported(gram, bad):
     A = np.random.default_rng(0).standard_normal((500, 20))
-    A[123, 7] = np.nan
+    A[123, 7] = bad
     with pytest.raises(rl.RlobpcgError) as e:
-        gpu_solve(A, 1, seed=1)
+        gpu_solve(A, 1, seed=1, gram=gram)
     assert e.value.code == rl.RLOBPCG_ERR_NONFINITE
 
 

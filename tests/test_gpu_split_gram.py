@@ -144,6 +144,12 @@ def test_invalid_and_nonfinite():
     with pytest.raises(rl.RlobpcgError) as e:
         rl.rlobpcg_gram_split_prepare(A.data_ptr(), m, n, n, prep.data_ptr(), ps - 1, _stream())
     assert e.value.code == rl.RLOBPCG_ERR_INVALID_ARG
+    for bad in (np.nan, np.inf, -np.inf):
+        Ab = np.ones((m, n))
+        Ab[m - 1, n - 1] = bad
+        with pytest.raises(rl.RlobpcgError) as e:
+            rl.rlobpcg_gram_split_prepare(_dev(Ab).data_ptr(), m, n, n, prep.data_ptr(), ps, _stream())
+        assert e.value.code == rl.RLOBPCG_ERR_NONFINITE
 
 
 # ------------------------------------------------------------------------------- whole solves
