@@ -40,13 +40,15 @@
 // columns) as the M side, row chunk rc (128 rows = 8 blocks of 16) as the K side -- for the
 // second. W and AW are split once per pass, straight into bf16 digit tiles.
 //
-// Kernel shape: one CTA per SM, 448 threads: warp 0 issues the bulk copies of the B digits
-// (5-stage ring of mbarriers), warp 1 owns TMEM and issues the MMAs from one thread, warps 2-5
-// read the accumulators (two TMEM buffers, so reading one unit overlaps the MMAs of the next),
-// zero them, and do the FP64 recombination, and warps 6-13 load the A digit bytes (four stages
-// ahead, in registers) and write each stage's eight bf16 digit tiles; the last CTA of each
-// column tile of the second product sums the per-CTA partials in a fixed order. Every wait is
-// bounded and reports DEV_ERR_TIMEOUT.
+// Kernel shape: one CTA per SM, 448 threads. Warp 0 streams the A digit bytes and the B digits
+// of each stage into a ring of staging slots (12 when A goes through TMEM, else 6) with bulk
+// copies; warps 6-13 expand each stage's bytes into the eight bf16 digit tiles -- in TMEM beside
+// the accumulators for b <= 8 (the MMAs then read A without shared-memory traffic), else in
+// shared memory; warp 1 owns TMEM and issues the MMAs from one thread, B read in the staging
+// slot; warps 2-5 read the accumulators (two TMEM buffers, so reading one unit overlaps the MMAs
+// of the next), zero them, and do the FP64 recombination. The last CTA of each column tile of
+// the second product sums the per-CTA partials in a fixed order. Every wait is bounded and
+// reports DEV_ERR_TIMEOUT.
 #include "common.cuh"
 #include "split.cuh"
 #include "tc.cuh"
@@ -66,8 +68,12 @@ using split::SPLIT_W_READY;
 constexpr int TM = 128;                // MMA M: rows (first product) or columns (second) per tile
 constexpr int KC_KB = 32;              // k-blocks per exact accumulation: 32 x 16 = 512 terms
 constexpr int CH_KB = TM / TK;         // k-blocks per 128-row chunk of the second product
-constexpr int NST = 3;                 // bf16 digit stages (MMA operands)
-constexpr int NSB = 7;                 // byte-digit staging slots (bulk copies in flight)
+// bf16 digit stages (MMA operands): in TMEM (b <= 8) four fit beside the two accumulator buffers
+template <bool TA> constexpr int nst() { return TA ? 4 : 3; }
+// staging slots (bulk copies in flight), each the A digit bytes of a stage and its B digits: the
+// bf16 A stages take 32 KB of shared memory each when the MMAs read A from there, none when A
+// goes through TMEM (b <= 8)
+template <bool TA> constexpr int nsb() { return TA ? 12 : 6; }
 constexpr int SLICE_BYTES = TM * TK * 2;   // one bf16 digit tile
 constexpr int TILE_U8 = TM * TK * SL;      // the byte digits of one 128 x 16 tile (all 8 digits)
 constexpr int NCW = 8;                     // converter warps (one 64-byte unit per thread per stage)
@@ -283,19 +289,20 @@ __device__ __forceinline__ uint32_t bf16x2_minus192(uint32_t v) {
   asm("add.rn.bf16x2 %0, %1, %2;" : "=r"(r) : "r"(v), "r"(0xC340C340u));
   return r;
 }
-__device__ __forceinline__ void expand_unit(const uint4 (&b)[4], unsigned char* dst) {
+template <class Put>
+__device__ __forceinline__ void expand_unit_to(const uint4 (&b)[4], Put put) {
   const uint32_t w[16] = {b[0].x, b[0].y, b[0].z, b[0].w, b[1].x, b[1].y, b[1].z, b[1].w,
                           b[2].x, b[2].y, b[2].z, b[2].w, b[3].x, b[3].y, b[3].z, b[3].w};
   constexpr uint32_t HI = 0x43434343u;   // bf16 0x43uu = 128 + uu for uu < 128
 #pragma unroll
-  for (int p = 0; p < SL; ++p) {
-    uint4 o;
-    o.x = bf16x2_minus192(__byte_perm(w[2 * p], HI, 0x4140));
-    o.y = bf16x2_minus192(__byte_perm(w[2 * p], HI, 0x4342));
-    o.z = bf16x2_minus192(__byte_perm(w[2 * p + 1], HI, 0x4140));
-    o.w = bf16x2_minus192(__byte_perm(w[2 * p + 1], HI, 0x4342));
-    *reinterpret_cast<uint4*>(dst + p * SLICE_BYTES) = o;
-  }
+  for (int p = 0; p < SL; ++p)
+    put(p, bf16x2_minus192(__byte_perm(w[2 * p], HI, 0x4140)), bf16x2_minus192(__byte_perm(w[2 * p], HI, 0x4342)),
+        bf16x2_minus192(__byte_perm(w[2 * p + 1], HI, 0x4140)), bf16x2_minus192(__byte_perm(w[2 * p + 1], HI, 0x4342)));
+}
+__device__ __forceinline__ void expand_unit(const uint4 (&b)[4], unsigned char* dst) {
+  expand_unit_to(b, [&](int p, uint32_t x, uint32_t y, uint32_t z, uint32_t w) {
+    *reinterpret_cast<uint4*>(dst + p * SLICE_BYTES) = make_uint4(x, y, z, w);
+  });
 }
 
 // ---- per-pass split of W (one CTA) ---------------------------------------------------------------
@@ -486,12 +493,19 @@ __global__ void __launch_bounds__(NTH, 1) split_pass_kernel(PassArgs g) {
   constexpr int N = SL * BP;
   constexpr uint32_t ACCW = BP == 8 ? 128 : 256;
   constexpr uint32_t BBYTES = N * TK * 2;
-  constexpr uint32_t ABYTES = SL * SLICE_BYTES;
-  constexpr uint32_t STG = ABYTES + BBYTES;
+  // b <= 8: the A digits of a stage go to TMEM (8 columns per digit, after the two accumulator
+  // buffers), so shared memory holds only B and the MMAs read A without shared-memory traffic
+  constexpr bool TA = BP == 8;
+  constexpr uint32_t STG = TA ? 0 : SL * SLICE_BYTES;   // bf16 A stage in shared memory
+  constexpr uint32_t SLOT = TILE_U8 + BBYTES;           // staging slot: A bytes, then B digits
+  constexpr int NSB = nsb<TA>();
+  constexpr int NST = nst<TA>();
+  constexpr uint32_t TCOLS = TA ? 512 : 2 * ACCW;
+  constexpr uint32_t ACOL0 = 2 * ACCW;   // TMEM column of the A digits of stage 0 (TA)
   constexpr uint32_t IDESC = tc::idesc_bf16_f32(TM, N);
   extern __shared__ __align__(1024) unsigned char sm[];
-  unsigned char* bring = sm + NST * STG;   // byte-digit staging slots, TILE_U8 each
-  uint64_t* full = reinterpret_cast<uint64_t*>(bring + NSB * TILE_U8);
+  unsigned char* bring = sm + NST * STG;   // staging slots, SLOT bytes each
+  uint64_t* full = reinterpret_cast<uint64_t*>(bring + NSB * SLOT);
   uint64_t* empty = full + NST;
   uint64_t* bfull = empty + NST;
   uint64_t* bempty = bfull + NSB;
@@ -499,17 +513,17 @@ __global__ void __launch_bounds__(NTH, 1) split_pass_kernel(PassArgs g) {
   uint64_t* acce = accf + 2;
   uint64_t* done = acce + 2;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
-  double* red = reinterpret_cast<double*>(bring + NSB * TILE_U8 + 512);   // [2][4][BP]
+  double* red = reinterpret_cast<double*>(bring + NSB * SLOT + 512);   // [2][4][BP]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NST; ++s) {
-      tc::mbar_init(full + s, 1 + NCW);   // the B copy (with its bytes) and the converter warps
-      tc::mbar_init(empty + s, 1);
+      tc::mbar_init(full + s, NCW);       // the converter warps
+      tc::mbar_init(empty + s, 1);        // the MMAs of the stage
     }
     for (int s = 0; s < NSB; ++s) {
-      tc::mbar_init(bfull + s, 1);
-      tc::mbar_init(bempty + s, NCW);
+      tc::mbar_init(bfull + s, 1);        // the two copies (with their bytes)
+      tc::mbar_init(bempty + s, NCW + 1); // the converter warps and the MMAs (which read B there)
     }
     for (int a = 0; a < 2; ++a) {
       tc::mbar_init(accf + a, 1);
@@ -518,7 +532,7 @@ __global__ void __launch_bounds__(NTH, 1) split_pass_kernel(PassArgs g) {
     tc::mbar_init(done, 1);
     tc::fence_mbar_init();
   }
-  if (warp == 1) tc::tmem_alloc(tslot, 2 * ACCW);
+  if (warp == 1) tc::tmem_alloc(tslot, TCOLS);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
@@ -533,25 +547,29 @@ __global__ void __launch_bounds__(NTH, 1) split_pass_kernel(PassArgs g) {
   const int64_t NKC = cdiv(g.NKB, KC_KB);
 
   if (warp == 0) {
-    // the A digit bytes of every stage, NSB tiles ahead of the converters
+    // the A digit bytes and the B digits of every stage, NSB stages ahead of the converters
     if (lane == 0) {
       uint32_t u = 0;
       bool ok = true;
-      auto load = [&](const unsigned char* srcA) {
+      auto load = [&](const unsigned char* srcA, const uint16_t* srcB) {
         const int s = (int)(u % NSB);
         if (!tc::mbar_wait(bempty + s, ((u / NSB) & 1) ^ 1)) return false;
-        tc::mbar_expect_tx(bfull + s, TILE_U8);
-        tc::bulk_g2s(bring + (size_t)s * TILE_U8, srcA, TILE_U8, bfull + s);
+        unsigned char* slot = bring + (size_t)s * SLOT;
+        tc::mbar_expect_tx(bfull + s, SLOT);
+        tc::bulk_g2s(slot, srcA, TILE_U8, bfull + s);
+        tc::bulk_g2s(slot + TILE_U8, srcB, BBYTES, bfull + s);
         ++u;
         return true;
       };
       if (MODE == 0) {
         for (int64_t r = blockIdx.x; ok && r < g.R1; r += gridDim.x)
-          for (int64_t kb = 0; ok && kb < g.NKB; ++kb) ok = load(g.Aop + (size_t)(r * g.NKB + kb) * TILE_U8);
+          for (int64_t kb = 0; ok && kb < g.NKB; ++kb)
+            ok = load(g.Aop + (size_t)(r * g.NKB + kb) * TILE_U8, g.Bop + (size_t)kb * (N * TK));
       } else {
         for (int64_t rc = rc0; ok && rc < rc1; ++rc)
           for (int kb = 0; ok && kb < CH_KB; ++kb)
-            ok = load(g.Aop + (size_t)((ct * g.R1 + rc) * CH_KB + kb) * TILE_U8);
+            ok = load(g.Aop + (size_t)((ct * g.R1 + rc) * CH_KB + kb) * TILE_U8,
+                      g.Bop + (size_t)(rc * CH_KB + kb) * (N * TK));
       }
       if (!ok) atomicOr(g.err, DEV_ERR_TIMEOUT);
       // copies into the last NSB slots have landed before the CTA may finish
@@ -567,15 +585,21 @@ __global__ void __launch_bounds__(NTH, 1) split_pass_kernel(PassArgs g) {
         tc::fence_after_sync();
         const uint32_t dbase = tmem + (uint32_t)a * ACCW;
         for (int kb = 0; kb < nkb; ++kb) {
-          const int s = (int)(u % NST);
+          const int s = (int)(u % NST), ds = (int)(u % NSB);
           if (!tc::mbar_wait(full + s, (u / NST) & 1)) return false;
           tc::fence_after_sync();
           unsigned char* stg = sm + (size_t)s * STG;
-          const uint64_t bdesc = tc::smem_desc(stg + ABYTES, (N / 8) * 128, 128);
+          const uint64_t bdesc = tc::smem_desc(bring + (size_t)ds * SLOT + TILE_U8, (N / 8) * 128, 128);
 #pragma unroll
-          for (int p = 0; p < SL; ++p)
-            tc::mma_bf16(dbase + (uint32_t)(BP * p), tc::smem_desc(stg + p * SLICE_BYTES, 2048, 128), bdesc, IDESC, 1u);
+          for (int p = 0; p < SL; ++p) {
+            if (TA)
+              tc::mma_bf16_ta(dbase + (uint32_t)(BP * p), tmem + ACOL0 + (uint32_t)(64 * s + 8 * p), bdesc, IDESC, 1u);
+            else
+              tc::mma_bf16(dbase + (uint32_t)(BP * p), tc::smem_desc(stg + p * SLICE_BYTES, 2048, 128), bdesc, IDESC,
+                           1u);
+          }
           tc::mma_commit(empty + s);
+          tc::mma_commit(bempty + ds);
           ++u;
         }
         tc::mma_commit(accf + a);
@@ -702,38 +726,37 @@ __global__ void __launch_bounds__(NTH, 1) split_pass_kernel(PassArgs g) {
     // converter warps: thread ci expands unit ci (M index ci % 128, K half ci / 128) of each
     // stage's A tile from the staging slot into the bf16 digit tiles; the first converter warp
     // also issues the stage's B copy
-    const int ci = threadIdx.x - 192;
-    const uint32_t soff = (uint32_t)((ci >> 7) * 2048 + (ci & 127) * 16);
+    // warp w covers rows 32 (w % 4) .. + 31 (its TMEM lane quarter) of K half (w - 6) / 4
+    const int quarter = warp & 3, h = (warp - 6) >> 2, row = 32 * quarter + lane;
+    const int ci = 128 * h + row;
+    const uint32_t soff = (uint32_t)(h * 2048 + row * 16);
+    const uint32_t tq = tmem + ((uint32_t)(32 * quarter) << 16) + ACOL0 + 4 * h;
     const int64_t nrt = MODE == 0 ? (blockIdx.x < g.R1 ? (g.R1 - 1 - blockIdx.x) / gridDim.x + 1 : 0) : 0;
     const uint32_t U = (uint32_t)(MODE == 0 ? nrt * g.NKB : (rc1 - rc0) * CH_KB);
-    const bool issuer = warp == 6 && lane == 0;
-    int64_t cur = MODE == 0 ? 0 : rc0, ckb = 0;   // (row chunk,) k-block of stage u, for B
     bool ok = true;
     for (uint32_t u = 0; ok && u < U; ++u) {
       const int ds = (int)(u % NSB), s = (int)(u % NST);
       ok = __all_sync(0xffffffffu, tc::mbar_wait(bfull + ds, (u / NSB) & 1));
       if (!ok) break;
       uint4 b[4];
-      const unsigned char* sp = bring + (size_t)ds * TILE_U8 + (size_t)ci * 16;
+      const unsigned char* sp = bring + (size_t)ds * SLOT + (size_t)ci * 16;
 #pragma unroll
       for (int c = 0; c < 4; ++c) b[c] = *reinterpret_cast<const uint4*>(sp + c * 4096);
       ok = __all_sync(0xffffffffu, tc::mbar_wait(empty + s, ((u / NST) & 1) ^ 1));
       if (!ok) break;
       unsigned char* stg = sm + (size_t)s * STG;
-      if (issuer) {
-        const uint16_t* srcB = MODE == 0 ? g.Bop + (size_t)ckb * (N * TK) : g.Bop + (size_t)(cur * CH_KB + ckb) * (N * TK);
-        tc::mbar_expect_tx(full + s, BBYTES);
-        tc::bulk_g2s(stg + ABYTES, srcB, BBYTES, full + s);
+      // the staging slot is free once every lane's bytes are in registers (the expansion consumed
+      // them); the tensor core reads the digits just written through TMEM or the async proxy
+      if (TA) {
+        expand_unit_to(b, [&](int p, uint32_t x, uint32_t y, uint32_t z, uint32_t w) {
+          tc::tmem_st4(tq + (uint32_t)(64 * s + 8 * p), x, y, z, w);
+        });
+        tc::tmem_st_wait();
+        tc::fence_before_sync();
+      } else {
+        expand_unit(b, stg + soff);
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
       }
-      if (++ckb == (MODE == 0 ? g.NKB : CH_KB)) {
-        ckb = 0;
-        ++cur;
-      }
-      expand_unit(b, stg + soff);
-      // the staging slot is free once every lane's bytes are in registers (expand_unit consumed
-      // them), and the bulk copy that refills it writes through the async proxy; so do the
-      // tensor core's reads of the tiles just written
-      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
       __syncwarp();
       if (lane == 0) {
         tc::mbar_arrive(bempty + ds);
@@ -741,22 +764,21 @@ __global__ void __launch_bounds__(NTH, 1) split_pass_kernel(PassArgs g) {
       }
     }
     if (!ok && lane == 0) atomicOr(g.err, DEV_ERR_TIMEOUT);
-    // the B copies issued here have landed before the CTA may finish (bounded)
-    if (issuer)
-      for (uint32_t w = U > (uint32_t)NST ? U - NST : 0; w < U; ++w) tc::mbar_wait(full + (w % NST), (w / NST) & 1);
   }
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 1) {
     tc::fence_after_sync();
-    tc::tmem_dealloc(tmem, 2 * ACCW);
+    tc::tmem_dealloc(tmem, TCOLS);
   }
 }
 
 template <int BP, int MODE>
 int launch_pass(const PassArgs& a, int grid, cudaStream_t st) {
-  constexpr uint32_t STG = SL * SLICE_BYTES + SL * BP * TK * 2;
-  const size_t smem = (size_t)NST * STG + (size_t)NSB * TILE_U8 + 512 + 2 * 4 * BP * sizeof(double);
+  constexpr bool TA = BP == 8;
+  constexpr uint32_t STG = TA ? 0 : SL * SLICE_BYTES;
+  constexpr uint32_t SLOT = TILE_U8 + SL * BP * TK * 2;
+  const size_t smem = (size_t)nst<TA>() * STG + (size_t)nsb<TA>() * SLOT + 512 + 2 * 4 * BP * sizeof(double);
   RL_TRY(allow_dynamic_smem(split_pass_kernel<BP, MODE>, smem));
   split_pass_kernel<BP, MODE><<<grid, NTH, smem, st>>>(a);
   RL_CHECK_LAUNCH();
