@@ -237,14 +237,15 @@ def split_traffic_per_launch(m, n, k):
 
 def split_algorithmic_bytes(m, n, b):
     """Bytes each split-Gram kernel must move per launch (layouts of gram_tc.cu): the digits of A
-    (8 bf16 digits per element of the padded matrix: 16 bytes), plus A W (FP64) and the digits of
-    A W (8 x 8 or 8 x 16 bf16 per row) written by the first, read by the second once per 128-column
-    tile."""
+    (8 one-byte digits per element of the padded matrix, as many bytes as the FP64 value), plus
+    A W (FP64) and the bf16 digits of A W (8 x 8 or 8 x 16 per row) written by the first, read by
+    the second once per 128-column tile."""
     cd = lambda a, q: -(-a // q)  # noqa: E731
     R1, NKB, CT = cd(m, 128), cd(n, 16), cd(n, 128)
     N = 8 * (8 if b <= 8 else 16)
-    ab_digits = R1 * NKB * 8 * 4096
-    atb_digits = CT * R1 * 8 * 8 * 4096
+    tile = 128 * 16 * 8
+    ab_digits = R1 * NKB * tile
+    atb_digits = CT * R1 * 8 * tile
     y_digits = R1 * 128 * N * 2
     return {"ab_digits": ab_digits, "atb_digits": atb_digits,
             "ab": ab_digits + 8 * m * b + y_digits, "atb": atb_digits + CT * y_digits}
@@ -344,9 +345,9 @@ def run_ours(args, rank, world, local_rank):
     max_mhz = clk.get("sm_max_mhz") or 2070.0
     peak_tf = sm_count * FP64_UNITS_PER_SM_CLK * 2 * max_mhz * 1e6 / 1e12
     if split:
-        # split-bf16 Gram: two HBM-bound tensor-core kernels per pass; the roofline is that of the
-        # slower one (bytes it must move per launch / its event-timed duration) against the measured
-        # copy bandwidth
+        # split-bf16 Gram: two tensor-core kernels per pass that stream the byte digits of A; the
+        # roofline is that of the slower one (bytes it must move per launch / its event-timed
+        # duration) against the measured copy bandwidth
         alg = split_algorithmic_bytes(M, N, K)
         t_ab = sum(x.ms_gram_ab for x in infos) / max(passes, 1) * 1e-3
         t_atb = sum(x.ms_gram_atb for x in infos) / max(passes, 1) * 1e-3
@@ -358,8 +359,9 @@ def run_ours(args, rank, world, local_rank):
         roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": peak_gbs, "unit": "GB/s",
                     "frac": (achieved_gbs / peak_gbs) if achieved_gbs else None,
                     "traffic": tr[key] if tr else None,
-                    "kernel": ("split_pass_kernel<8,1> (A^T (A W) from bf16 digits, tcgen05)" if key == "atb" else
-                               "split_pass_kernel<8,0> (A W from bf16 digits, tcgen05)"),
+                    "kernel": ("split_pass_kernel<8,1> (A^T (A W), byte digits expanded to bf16 in TMEM, tcgen05)"
+                               if key == "atb" else
+                               "split_pass_kernel<8,0> (A W, byte digits expanded to bf16 in TMEM, tcgen05)"),
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks.get("hbm_gbs") else
                                    "fallback 6.8 TB/s",
                     "bytes_per_launch": alg[key], "ms_per_launch": t_k * 1e3,

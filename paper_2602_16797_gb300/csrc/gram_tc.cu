@@ -41,8 +41,8 @@
 // second. W and AW are split once per pass, straight into bf16 digit tiles.
 //
 // Kernel shape: one CTA per SM, 448 threads. Warp 0 streams the A digit bytes and the B digits
-// of each stage into a ring of staging slots (12 when A goes through TMEM, else 6) with bulk
-// copies; warps 6-13 expand each stage's bytes into the eight bf16 digit tiles -- in TMEM beside
+// of each stage (two k-blocks when A goes through TMEM, else one) into a ring of six staging
+// slots with bulk copies; warps 6-13 expand each stage's bytes into the eight bf16 digit tiles -- in TMEM beside
 // the accumulators for b <= 8 (the MMAs then read A without shared-memory traffic), else in
 // shared memory; warp 1 owns TMEM and issues the MMAs from one thread, B read in the staging
 // slot; warps 2-5 read the accumulators (two TMEM buffers, so reading one unit overlaps the MMAs
@@ -68,12 +68,14 @@ using split::SPLIT_W_READY;
 constexpr int TM = 128;                // MMA M: rows (first product) or columns (second) per tile
 constexpr int KC_KB = 32;              // k-blocks per exact accumulation: 32 x 16 = 512 terms
 constexpr int CH_KB = TM / TK;         // k-blocks per 128-row chunk of the second product
-// bf16 digit stages (MMA operands): in TMEM (b <= 8) four fit beside the two accumulator buffers
-template <bool TA> constexpr int nst() { return TA ? 4 : 3; }
+// bf16 digit stages (MMA operands): in TMEM (b <= 8) two stages of two k-blocks fit beside the two
+// accumulator buffers; in shared memory three stages of one k-block
+template <bool TA> constexpr int nst() { return TA ? 2 : 3; }
+template <bool TA> constexpr int kps() { return TA ? 2 : 1; }   // k-blocks per stage
 // staging slots (bulk copies in flight), each the A digit bytes of a stage and its B digits: the
 // bf16 A stages take 32 KB of shared memory each when the MMAs read A from there, none when A
 // goes through TMEM (b <= 8)
-template <bool TA> constexpr int nsb() { return TA ? 12 : 6; }
+template <bool TA> constexpr int nsb() { return TA ? 6 : 6; }
 constexpr int SLICE_BYTES = TM * TK * 2;   // one bf16 digit tile
 constexpr int TILE_U8 = TM * TK * SL;      // the byte digits of one 128 x 16 tile (all 8 digits)
 constexpr int NCW = 8;                     // converter warps (one 64-byte unit per thread per stage)
@@ -496,12 +498,16 @@ __global__ void __launch_bounds__(NTH, 1) split_pass_kernel(PassArgs g) {
   // b <= 8: the A digits of a stage go to TMEM (8 columns per digit, after the two accumulator
   // buffers), so shared memory holds only B and the MMAs read A without shared-memory traffic
   constexpr bool TA = BP == 8;
-  constexpr uint32_t STG = TA ? 0 : SL * SLICE_BYTES;   // bf16 A stage in shared memory
-  constexpr uint32_t SLOT = TILE_U8 + BBYTES;           // staging slot: A bytes, then B digits
+  // A stage covers KPS k-blocks (a unit of KC_KB or CH_KB k-blocks -- both even -- never splits
+  // a stage; the last stage of a unit may hold one k-block)
+  constexpr int KPS = kps<TA>();
+  constexpr uint32_t STG = TA ? 0 : SL * SLICE_BYTES;      // bf16 A stage in shared memory
+  constexpr uint32_t SLOT = KPS * (TILE_U8 + BBYTES);      // staging slot: KPS A byte tiles, KPS B tiles
   constexpr int NSB = nsb<TA>();
   constexpr int NST = nst<TA>();
   constexpr uint32_t TCOLS = TA ? 512 : 2 * ACCW;
   constexpr uint32_t ACOL0 = 2 * ACCW;   // TMEM column of the A digits of stage 0 (TA)
+  constexpr uint32_t ASTW = 64 * KPS;    // TMEM columns of one A stage (TA)
   constexpr uint32_t IDESC = tc::idesc_bf16_f32(TM, N);
   extern __shared__ __align__(1024) unsigned char sm[];
   unsigned char* bring = sm + NST * STG;   // staging slots, SLOT bytes each
@@ -522,7 +528,7 @@ __global__ void __launch_bounds__(NTH, 1) split_pass_kernel(PassArgs g) {
       tc::mbar_init(empty + s, 1);        // the MMAs of the stage
     }
     for (int s = 0; s < NSB; ++s) {
-      tc::mbar_init(bfull + s, 1);        // the two copies (with their bytes)
+      tc::mbar_init(bfull + s, 1);        // the copies (with their bytes)
       tc::mbar_init(bempty + s, NCW + 1); // the converter warps and the MMAs (which read B there)
     }
     for (int a = 0; a < 2; ++a) {
@@ -551,25 +557,27 @@ __global__ void __launch_bounds__(NTH, 1) split_pass_kernel(PassArgs g) {
     if (lane == 0) {
       uint32_t u = 0;
       bool ok = true;
-      auto load = [&](const unsigned char* srcA, const uint16_t* srcB) {
+      // the nk tiles of a stage are consecutive in both digit layouts
+      auto load = [&](const unsigned char* srcA, const uint16_t* srcB, int nk) {
         const int s = (int)(u % NSB);
         if (!tc::mbar_wait(bempty + s, ((u / NSB) & 1) ^ 1)) return false;
         unsigned char* slot = bring + (size_t)s * SLOT;
-        tc::mbar_expect_tx(bfull + s, SLOT);
-        tc::bulk_g2s(slot, srcA, TILE_U8, bfull + s);
-        tc::bulk_g2s(slot + TILE_U8, srcB, BBYTES, bfull + s);
+        tc::mbar_expect_tx(bfull + s, (uint32_t)nk * (TILE_U8 + BBYTES));
+        tc::bulk_g2s(slot, srcA, (uint32_t)nk * TILE_U8, bfull + s);
+        tc::bulk_g2s(slot + KPS * TILE_U8, srcB, (uint32_t)nk * BBYTES, bfull + s);
         ++u;
         return true;
       };
       if (MODE == 0) {
         for (int64_t r = blockIdx.x; ok && r < g.R1; r += gridDim.x)
-          for (int64_t kb = 0; ok && kb < g.NKB; ++kb)
-            ok = load(g.Aop + (size_t)(r * g.NKB + kb) * TILE_U8, g.Bop + (size_t)kb * (N * TK));
+          for (int64_t kb = 0; ok && kb < g.NKB; kb += KPS)
+            ok = load(g.Aop + (size_t)(r * g.NKB + kb) * TILE_U8, g.Bop + (size_t)kb * (N * TK),
+                      (int)std::min<int64_t>(KPS, g.NKB - kb));
       } else {
         for (int64_t rc = rc0; ok && rc < rc1; ++rc)
-          for (int kb = 0; ok && kb < CH_KB; ++kb)
+          for (int kb = 0; ok && kb < CH_KB; kb += KPS)
             ok = load(g.Aop + (size_t)((ct * g.R1 + rc) * CH_KB + kb) * TILE_U8,
-                      g.Bop + (size_t)(rc * CH_KB + kb) * (N * TK));
+                      g.Bop + (size_t)(rc * CH_KB + kb) * (N * TK), KPS);
       }
       if (!ok) atomicOr(g.err, DEV_ERR_TIMEOUT);
       // copies into the last NSB slots have landed before the CTA may finish
@@ -584,19 +592,24 @@ __global__ void __launch_bounds__(NTH, 1) split_pass_kernel(PassArgs g) {
         if (!tc::mbar_wait(acce + a, (v >> 1) & 1)) return false;
         tc::fence_after_sync();
         const uint32_t dbase = tmem + (uint32_t)a * ACCW;
-        for (int kb = 0; kb < nkb; ++kb) {
+        for (int kb = 0; kb < nkb; kb += KPS) {
           const int s = (int)(u % NST), ds = (int)(u % NSB);
           if (!tc::mbar_wait(full + s, (u / NST) & 1)) return false;
           tc::fence_after_sync();
           unsigned char* stg = sm + (size_t)s * STG;
-          const uint64_t bdesc = tc::smem_desc(bring + (size_t)ds * SLOT + TILE_U8, (N / 8) * 128, 128);
+          const int nk = nkb - kb < KPS ? nkb - kb : KPS;
+          for (int q = 0; q < nk; ++q) {
+            const uint64_t bdesc =
+                tc::smem_desc(bring + (size_t)ds * SLOT + KPS * TILE_U8 + q * BBYTES, (N / 8) * 128, 128);
 #pragma unroll
-          for (int p = 0; p < SL; ++p) {
-            if (TA)
-              tc::mma_bf16_ta(dbase + (uint32_t)(BP * p), tmem + ACOL0 + (uint32_t)(64 * s + 8 * p), bdesc, IDESC, 1u);
-            else
-              tc::mma_bf16(dbase + (uint32_t)(BP * p), tc::smem_desc(stg + p * SLICE_BYTES, 2048, 128), bdesc, IDESC,
-                           1u);
+            for (int p = 0; p < SL; ++p) {
+              if (TA)
+                tc::mma_bf16_ta(dbase + (uint32_t)(BP * p), tmem + ACOL0 + (uint32_t)(ASTW * s + 64 * q + 8 * p), bdesc,
+                                IDESC, 1u);
+              else
+                tc::mma_bf16(dbase + (uint32_t)(BP * p), tc::smem_desc(stg + p * SLICE_BYTES, 2048, 128), bdesc, IDESC,
+                             1u);
+            }
           }
           tc::mma_commit(empty + s);
           tc::mma_commit(bempty + ds);
@@ -723,38 +736,38 @@ __global__ void __launch_bounds__(NTH, 1) split_pass_kernel(PassArgs g) {
     }
     if (!ok) atomicOr(g.err, DEV_ERR_TIMEOUT);
   } else {
-    // converter warps: thread ci expands unit ci (M index ci % 128, K half ci / 128) of each
-    // stage's A tile from the staging slot into the bf16 digit tiles; the first converter warp
-    // also issues the stage's B copy
-    // warp w covers rows 32 (w % 4) .. + 31 (its TMEM lane quarter) of K half (w - 6) / 4
+    // converter warps: thread ci expands unit ci (M index ci % 128, K half ci / 128) of each of
+    // the stage's nk A tiles from the staging slot into the bf16 digit tiles; warp w covers rows
+    // 32 (w % 4) .. + 31 (its TMEM lane quarter) of K half (w - 6) / 4
     const int quarter = warp & 3, h = (warp - 6) >> 2, row = 32 * quarter + lane;
     const int ci = 128 * h + row;
     const uint32_t soff = (uint32_t)(h * 2048 + row * 16);
     const uint32_t tq = tmem + ((uint32_t)(32 * quarter) << 16) + ACOL0 + 4 * h;
-    const int64_t nrt = MODE == 0 ? (blockIdx.x < g.R1 ? (g.R1 - 1 - blockIdx.x) / gridDim.x + 1 : 0) : 0;
-    const uint32_t U = (uint32_t)(MODE == 0 ? nrt * g.NKB : (rc1 - rc0) * CH_KB);
-    bool ok = true;
-    for (uint32_t u = 0; ok && u < U; ++u) {
+    uint32_t u = 0;
+    auto stage = [&](int nk) {
       const int ds = (int)(u % NSB), s = (int)(u % NST);
-      ok = __all_sync(0xffffffffu, tc::mbar_wait(bfull + ds, (u / NSB) & 1));
-      if (!ok) break;
-      uint4 b[4];
+      if (!__all_sync(0xffffffffu, tc::mbar_wait(bfull + ds, (u / NSB) & 1))) return false;
+      uint4 b[KPS][4];
       const unsigned char* sp = bring + (size_t)ds * SLOT + (size_t)ci * 16;
 #pragma unroll
-      for (int c = 0; c < 4; ++c) b[c] = *reinterpret_cast<const uint4*>(sp + c * 4096);
-      ok = __all_sync(0xffffffffu, tc::mbar_wait(empty + s, ((u / NST) & 1) ^ 1));
-      if (!ok) break;
-      unsigned char* stg = sm + (size_t)s * STG;
+      for (int q = 0; q < KPS; ++q)
+        if (q < nk)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) b[q][c] = *reinterpret_cast<const uint4*>(sp + q * TILE_U8 + c * 4096);
+      if (!__all_sync(0xffffffffu, tc::mbar_wait(empty + s, ((u / NST) & 1) ^ 1))) return false;
       // the staging slot is free once every lane's bytes are in registers (the expansion consumed
       // them); the tensor core reads the digits just written through TMEM or the async proxy
       if (TA) {
-        expand_unit_to(b, [&](int p, uint32_t x, uint32_t y, uint32_t z, uint32_t w) {
-          tc::tmem_st4(tq + (uint32_t)(64 * s + 8 * p), x, y, z, w);
-        });
+#pragma unroll
+        for (int q = 0; q < KPS; ++q)
+          if (q < nk)
+            expand_unit_to(b[q], [&](int p, uint32_t x, uint32_t y, uint32_t z, uint32_t w) {
+              tc::tmem_st4(tq + (uint32_t)(ASTW * s + 64 * q + 8 * p), x, y, z, w);
+            });
         tc::tmem_st_wait();
         tc::fence_before_sync();
       } else {
-        expand_unit(b, stg + soff);
+        expand_unit(b[0], sm + (size_t)s * STG + soff);
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
       }
       __syncwarp();
@@ -762,6 +775,16 @@ __global__ void __launch_bounds__(NTH, 1) split_pass_kernel(PassArgs g) {
         tc::mbar_arrive(bempty + ds);
         tc::mbar_arrive(full + s);
       }
+      ++u;
+      return true;
+    };
+    bool ok = true;
+    if (MODE == 0) {
+      for (int64_t r = blockIdx.x; ok && r < g.R1; r += gridDim.x)
+        for (int64_t kb = 0; ok && kb < g.NKB; kb += KPS) ok = stage((int)std::min<int64_t>(KPS, g.NKB - kb));
+    } else {
+      for (int64_t rc = rc0; ok && rc < rc1; ++rc)
+        for (int kb = 0; ok && kb < CH_KB; kb += KPS) ok = stage(KPS);
     }
     if (!ok && lane == 0) atomicOr(g.err, DEV_ERR_TIMEOUT);
   }
@@ -777,7 +800,7 @@ template <int BP, int MODE>
 int launch_pass(const PassArgs& a, int grid, cudaStream_t st) {
   constexpr bool TA = BP == 8;
   constexpr uint32_t STG = TA ? 0 : SL * SLICE_BYTES;
-  constexpr uint32_t SLOT = TILE_U8 + SL * BP * TK * 2;
+  constexpr uint32_t SLOT = kps<TA>() * (TILE_U8 + SL * BP * TK * 2);
   const size_t smem = (size_t)nst<TA>() * STG + (size_t)nsb<TA>() * SLOT + 512 + 2 * 4 * BP * sizeof(double);
   RL_TRY(allow_dynamic_smem(split_pass_kernel<BP, MODE>, smem));
   split_pass_kernel<BP, MODE><<<grid, NTH, smem, st>>>(a);
