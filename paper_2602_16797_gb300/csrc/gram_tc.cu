@@ -436,7 +436,10 @@ __device__ __forceinline__ void ld_level8(uint32_t taddr, uint32_t (&r)[BP], int
 }
 
 // Reads one accumulator buffer (levels 0..14 of BP columns), zeroes it for reuse, releases it,
-// and returns s_j = sum_l 2^(-7 l) L_l[j].
+// and returns s_j = 2^28 sum_l 2^(-7 l) L_l[j]. Levels 4..0 are integers below 2^24 held exactly
+// in f32, so S = sum_{l<=4} L_l 2^(7 (4 - l)) is an exact int64 below 2^53 and converts to FP64
+// exactly: three FP64-pipe instructions per column instead of a five-step FP64 Horner with its
+// conversions (the FP64 pipe is the scarce one in the epilogue).
 template <int BP>
 __device__ __forceinline__ void drain_levels(uint32_t ta, uint64_t* release, int b, double (&s)[BP]) {
   float t[BP];
@@ -479,10 +482,11 @@ __device__ __forceinline__ void drain_levels(uint32_t ta, uint64_t* release, int
 #pragma unroll
   for (int j = 0; j < BP; ++j) {
     if (j < b) {
-      double v = (double)t[j];
+      // r[l] holds level 4 - l
+      long long S = __float2int_rn(__uint_as_float(r[4][j]));
 #pragma unroll
-      for (int l = 0; l < 5; ++l) v = fma(v, 0x1p-7, (double)__uint_as_float(r[l][j]));
-      s[j] = v;
+      for (int l = 3; l >= 0; --l) S = S * 128 + __float2int_rn(__uint_as_float(r[l][j]));
+      s[j] = fma((double)t[j], 0x1p-7, __ll2double_rn(S));
     } else {
       s[j] = 0;
     }
@@ -663,7 +667,7 @@ __global__ void __launch_bounds__(NTH, 1) split_pass_kernel(PassArgs g) {
           ++v;
 #pragma unroll
           for (int j = 0; j < BP; ++j)
-            if (j < g.b) y[j] += split::mul_pow2(s[j], Ei + Fj[j] - 12);
+            if (j < g.b) y[j] += split::mul_pow2(s[j], Ei + Fj[j] - 40);
         }
         if (!ok) break;
         if (i < g.m)
@@ -690,7 +694,7 @@ __global__ void __launch_bounds__(NTH, 1) split_pass_kernel(PassArgs g) {
         const int Ec = g.eA[rc * g.NC + c];
 #pragma unroll
         for (int j = 0; j < BP; ++j)
-          if (j < g.b) acc[j] += split::mul_pow2(s[j], Ec + g.eB[rc * BP + j] - 12);
+          if (j < g.b) acc[j] += split::mul_pow2(s[j], Ec + g.eB[rc * BP + j] - 40);
       }
       double* out = g.part + (size_t)(rng * g.NC + c) * BP;
 #pragma unroll
