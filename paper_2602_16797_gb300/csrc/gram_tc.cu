@@ -21,8 +21,9 @@
 // per accumulation |L_l| <= 8 * 512 * 2^12 = 2^24 and the f32 accumulator is exact (integers).
 // The result is then
 //     2^(E+F-12) sum_{l=0}^{14} 2^(-7 l) L_l,
-// evaluated by Horner's rule: levels 14..5 in f32 (their weight is below 2^-35 of level 0, so
-// f32 rounding there stays below 2^-59 of the leading term) and levels 4..0 in FP64. The error
+// evaluated as: levels 14..5 by Horner's rule in f32 (their weight is below 2^-35 of level 0,
+// so f32 rounding there stays below 2^-59 of the leading term), levels 4..0 exactly as one int64
+// (sum L_l 2^(7 (4 - l)) < 2^53), the two joined and scaled in FP64. The error
 // is that of the digit truncation, about 2^-55 of the group maxima per term, which is the size
 // of an FP64 dot product's own rounding. Tensor cores do the O(m n b) work; FP64 does O((m+n) b).
 //
@@ -137,28 +138,6 @@ __device__ __forceinline__ double warp_max(double v) {
 // Exponent of a group of A: max |x| * 65/64 < 2^E (see the byte form above).
 __device__ __forceinline__ int group_exp_a(double amax) { return group_exp(amax * 1.015625); }
 
-// rint(x 2^(55-E)) (ties away from zero) for |x| < 2^E, from the bits of x with integer
-// instructions only (the FP64 pipe is the scarce one on GB300)
-__device__ __forceinline__ long long scaled_int(double x, int E) {
-  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
-  const int e = (int)((bits >> 52) & 0x7ff);
-  unsigned long long M = bits & 0xfffffffffffffull;
-  int eb = 1;                     // x = M 2^(eb - 1075); subnormals keep eb = 1
-  if (e) {
-    M |= 1ull << 52;
-    eb = e;
-  }
-  const int sh = eb - 1020 - E;   // x 2^(55-E) = M 2^sh, sh <= 2 since |x| < 2^E
-  unsigned long long X = 0;
-  if (sh >= 0) {
-    X = M << sh;
-  } else if (sh > -64) {
-    const int r = -sh;
-    X = (M + (1ull << (r - 1))) >> r;   // M + 2^62 < 2^63: no overflow
-  }
-  return (bits >> 63) ? -(long long)X : (long long)X;
-}
-
 // Byte digits of 8 values sharing exponent E: w[2p + kk/4] holds u_p of value kk in byte kk%4,
 // u_p the base-128 digits of V + OFF, V = rint(x 2^(55-E)), OFF = 64 sum_p 128^p, so that
 // V = sum_p (u_p - 64) 128^(7-p) with every u_p in [0, 127].
@@ -168,7 +147,7 @@ __device__ __forceinline__ void digit_bytes(const double (&x)[8], int E, uint32_
   for (int q = 0; q < 16; ++q) w[q] = 0;
 #pragma unroll
   for (int kk = 0; kk < 8; ++kk) {
-    const unsigned long long Y = (unsigned long long)scaled_int(x[kk], E) + OFF;
+    const unsigned long long Y = (unsigned long long)split::scaled_int(x[kk], E) + OFF;
     const uint32_t lo = (uint32_t)Y, hi = (uint32_t)(Y >> 32);
     // digit p holds bits [7 (7 - p), 7 (7 - p) + 7) of Y
     const uint32_t d[SL] = {(hi >> 17) & 127u, (hi >> 10) & 127u, (hi >> 3) & 127u, __funnelshift_r(lo, hi, 28) & 127u,
@@ -362,16 +341,19 @@ __device__ __forceinline__ void emit_y_digits(const double (&y)[BP], int b, int 
                                               double* red, int64_t rc, uint16_t* __restrict__ Ysl,
                                               int* __restrict__ H, Bar bar) {
   constexpr int N = SL * BP;
+  // group maxima on the bit patterns of |y| (integer instructions; red holds the bits)
+  unsigned long long* redb = reinterpret_cast<unsigned long long*>(red);
 #pragma unroll
   for (int j = 0; j < BP; ++j) {
-    const double v = warp_max(j < b ? fabs(y[j]) : 0.0);
-    if (lane == 0) red[quarter * BP + j] = v;
+    const unsigned long long v = split::warp_max_abs_bits(j < b ? y[j] : 0.0);
+    if (lane == 0) redb[quarter * BP + j] = v;
   }
   bar();
   int Hj[BP];
 #pragma unroll
   for (int j = 0; j < BP; ++j)
-    Hj[j] = group_exp(fmax(fmax(red[j], red[BP + j]), fmax(red[2 * BP + j], red[3 * BP + j])));
+    Hj[j] = group_exp(__longlong_as_double(
+        (long long)max(max(redb[j], redb[BP + j]), max(redb[2 * BP + j], redb[3 * BP + j]))));
   if (row == 0)
 #pragma unroll
     for (int j = 0; j < BP; ++j) H[rc * BP + j] = j < b ? Hj[j] : 0;

@@ -24,8 +24,38 @@ __device__ __forceinline__ double mul_pow2(double x, int k) {
   return (k >= -1022 && k <= 1023) ? x * __longlong_as_double((long long)(k + 1023) << 52) : scalbn(x, k);
 }
 
+// rint(x 2^(55-E)) (ties away from zero) for |x| < 2^E, from the bits of x with integer
+// instructions only (the FP64 pipe is the scarce one on GB300)
+__device__ __forceinline__ long long scaled_int(double x, int E) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((bits >> 52) & 0x7ff);
+  unsigned long long M = bits & 0xfffffffffffffull;
+  int eb = 1;                     // x = M 2^(eb - 1075); subnormals keep eb = 1
+  if (e) {
+    M |= 1ull << 52;
+    eb = e;
+  }
+  const int sh = eb - 1020 - E;   // x 2^(55-E) = M 2^sh, sh <= 2 since |x| < 2^E
+  unsigned long long X = 0;
+  if (sh >= 0) {
+    X = M << sh;
+  } else if (sh > -64) {
+    const int r = -sh;
+    X = (M + (1ull << (r - 1))) >> r;   // M + 2^62 < 2^63: no overflow
+  }
+  return (bits >> 63) ? -(long long)X : (long long)X;
+}
+
+// largest |x| of a warp's values, on the bit patterns (ordered like the values for |x|)
+__device__ __forceinline__ unsigned long long warp_max_abs_bits(double x) {
+  const unsigned long long k = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+  const unsigned hi = __reduce_max_sync(0xffffffffu, (unsigned)(k >> 32));
+  const unsigned lo = __reduce_max_sync(0xffffffffu, (unsigned)(k >> 32) == hi ? (unsigned)k : 0u);
+  return ((unsigned long long)hi << 32) | lo;
+}
+
 __device__ __forceinline__ void split8(double x, int E, int (&d)[SL]) {
-  long long V = __double2ll_rn(mul_pow2(x, 55 - E));
+  long long V = scaled_int(x, E);
 #pragma unroll
   for (int p = SL - 1; p > 0; --p) {
     const int r = (int)(V & 127);
