@@ -240,7 +240,8 @@ def solve(A, k: int, *, opts: rlobpcg_opts | None = None, tol: float = -1.0, wan
           stream: int | None = None):
     """Smallest k singular triplets of A (torch tensor, CUDA or CPU-pinned; float64/complex128).
 
-    Returns (sigma [k] float64 CPU tensor, V [n, k], U [m, k] or None, resid [k], info dict).
+    Returns (sigma [k] float64, V [n, k], U [m, k] or None, resid [k] -- all on the GPU -- and the
+    info dict).
     """
     import torch
     m, n = A.shape
