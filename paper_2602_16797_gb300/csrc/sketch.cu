@@ -20,6 +20,16 @@ constexpr int SK_WARPS = SK_NT / 32;
 constexpr int SK_GROUPS = 8;         // 32-row groups hashed per warp per chunk
 constexpr int SK_CHUNK = SK_WARPS * SK_GROUPS * 32;   // rows per chunk (2048)
 
+// x with its sign flipped when s = 1, by an integer XOR on the sign bit(s): acc + flip(v, 1) is
+// exactly acc - v, and the FP64 pipe (the sketch's bound) sees one add instead of an add and a
+// subtract with a select
+__device__ __forceinline__ double flip_(double x, int s) {
+  return __longlong_as_double(__double_as_longlong(x) ^ ((long long)s << 63));
+}
+__device__ __forceinline__ float flip_(float x, int s) { return __int_as_float(__float_as_int(x) ^ (s << 31)); }
+__device__ __forceinline__ cd flip_(cd x, int s) { return {flip_(x.x, s), flip_(x.y, s)}; }
+__device__ __forceinline__ cf flip_(cf x, int s) { return {flip_(x.x, s), flip_(x.y, s)}; }
+
 template <class TA, class TS>
 __global__ void __launch_bounds__(SK_NT) sketch_kernel(const TA* __restrict__ A, int64_t m, int n, int64_t lda,
                                                        int d, int zeta, uint64_t seed, int R, int bpp,
@@ -80,23 +90,18 @@ __global__ void __launch_bounds__(SK_NT) sketch_kernel(const TA* __restrict__ A,
           const TA v2 = A[(c0 + L[e + 2]) * lda + kk];
           const TA v3 = A[(c0 + L[e + 3]) * lda + kk];
           int q = C[e];
-          acc[(q >> 1) * SK_NT + tid] = (q & 1) ? sub_(acc[(q >> 1) * SK_NT + tid], cvt_<TS, TA>(v0))
-                                                : add_(acc[(q >> 1) * SK_NT + tid], cvt_<TS, TA>(v0));
+          acc[(q >> 1) * SK_NT + tid] = add_(acc[(q >> 1) * SK_NT + tid], flip_(cvt_<TS, TA>(v0), q & 1));
           q = C[e + 1];
-          acc[(q >> 1) * SK_NT + tid] = (q & 1) ? sub_(acc[(q >> 1) * SK_NT + tid], cvt_<TS, TA>(v1))
-                                                : add_(acc[(q >> 1) * SK_NT + tid], cvt_<TS, TA>(v1));
+          acc[(q >> 1) * SK_NT + tid] = add_(acc[(q >> 1) * SK_NT + tid], flip_(cvt_<TS, TA>(v1), q & 1));
           q = C[e + 2];
-          acc[(q >> 1) * SK_NT + tid] = (q & 1) ? sub_(acc[(q >> 1) * SK_NT + tid], cvt_<TS, TA>(v2))
-                                                : add_(acc[(q >> 1) * SK_NT + tid], cvt_<TS, TA>(v2));
+          acc[(q >> 1) * SK_NT + tid] = add_(acc[(q >> 1) * SK_NT + tid], flip_(cvt_<TS, TA>(v2), q & 1));
           q = C[e + 3];
-          acc[(q >> 1) * SK_NT + tid] = (q & 1) ? sub_(acc[(q >> 1) * SK_NT + tid], cvt_<TS, TA>(v3))
-                                                : add_(acc[(q >> 1) * SK_NT + tid], cvt_<TS, TA>(v3));
+          acc[(q >> 1) * SK_NT + tid] = add_(acc[(q >> 1) * SK_NT + tid], flip_(cvt_<TS, TA>(v3), q & 1));
         }
         for (; e < nw; ++e) {
           const TA v = A[(c0 + L[e]) * lda + kk];
           const int q = C[e];
-          acc[(q >> 1) * SK_NT + tid] = (q & 1) ? sub_(acc[(q >> 1) * SK_NT + tid], cvt_<TS, TA>(v))
-                                                : add_(acc[(q >> 1) * SK_NT + tid], cvt_<TS, TA>(v));
+          acc[(q >> 1) * SK_NT + tid] = add_(acc[(q >> 1) * SK_NT + tid], flip_(cvt_<TS, TA>(v), q & 1));
         }
       }
     }
