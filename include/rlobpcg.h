@@ -213,7 +213,7 @@ int rlobpcg_sketch(const void* A, int64_t m, int64_t n, int64_t lda, int dtype, 
                    uint64_t seed, int sketch_prec, void* SA, void* stream);
 
 /*
- * Factorise the sketch (Alg. 2, second and third lines): Householder QR SA = QR (Q discarded),
+ * Factorise the sketch (the factorisation step of Alg. 2): Householder QR SA = QR (Q discarded),
  * the SVD R = U~ Sigma~ V~^H by one-sided Jacobi, and R^{-1}. Since SVD(SA) = SVD(R), Sigma~ and
  * V~ are those of SA, and P P^* = V~ Sigma~^{-2} V~^H = (R^H R)^{-1}.
  *   SA     device, d x n column-major in the sketch precision (overwritten by the QR).

@@ -147,8 +147,8 @@ def sketch(A: np.ndarray, d: int, zeta: int, seed: int, precision: str = "f64") 
 
 
 def sketch_svd(SA: np.ndarray):
-    """[~, Sigma~, V~] = SVD(SA) (Alg. 2, second line): Sigma~ descending, V~ (n x n) with the
-    right singular vectors as columns. LAPACK gesdd in the precision of SA."""
+    """[~, Sigma~, V~] = SVD(SA) (the SVD of the sketch in Alg. 2): Sigma~ descending, V~ (n x n)
+    with the right singular vectors as columns. LAPACK gesdd in the precision of SA."""
     _, s, Vh = np.linalg.svd(SA, full_matrices=False)
     return s, Vh.conj().T
 
@@ -250,7 +250,7 @@ def rlobpcg(A: np.ndarray, k: int, b: int | None = None, d: int | None = None, z
     A = A.astype(wt, copy=False)
     AH = A.conj().T
 
-    # Sketch and factorise (Alg. 2, lines 1-3): P = V~ Sigma~^{-1}
+    # Sketch and factorise (the first steps of Alg. 2): P = V~ Sigma~^{-1}
     SA = sketch(A, d, zeta, seed, sketch_precision)
     s, Vt = sketch_svd(SA)
     s = s.astype(np.float64)
@@ -258,7 +258,7 @@ def rlobpcg(A: np.ndarray, k: int, b: int | None = None, d: int | None = None, z
     sigma11 = float(s[0])
     P = Vt / s[None, :]
 
-    # Sketch-and-solve start and initial Rayleigh-Ritz (Alg. 2, lines 4-7)
+    # Sketch-and-solve start and the initial Rayleigh-Ritz step (Alg. 2)
     V = orth(Vt[:, n - b:])
     AV = A @ V
     theta, C = rayleigh_ritz(AV)
@@ -311,7 +311,7 @@ def rlobpcg(A: np.ndarray, k: int, b: int | None = None, d: int | None = None, z
 
     if fixed_iters is not None:
         stop_reason = "fixed_iters"
-    # Outputs (Alg. 2, last lines), returned in ascending order of sigma
+    # Outputs (the end of Alg. 2), returned in ascending order of sigma
     order = np.arange(b - 1, b - 1 - k, -1)
     sig = theta_s[order] if i >= 0 else theta[order]
     Vk = V[:, order]

@@ -1,4 +1,4 @@
-// Factorisation of the sketch (Alg. 2, second and third lines of arXiv 2602.16797):
+// Factorisation of the sketch (the factorisation step of Alg. 2 of arXiv 2602.16797):
 //   1. Householder QR  SA = QR  (the QR route that the footnote in Sec. 1 names as the usual one);
 //   2. one-sided Jacobi SVD  R = U~ Sigma~ V~^H  (SVD(SA) = SVD(R): same Sigma~ and V~);
 //   3. R^{-1}, so that the preconditioner P P^* = V~ Sigma~^{-2} V~^H = (R^H R)^{-1} is applied

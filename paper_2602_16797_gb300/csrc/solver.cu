@@ -236,7 +236,7 @@ int solve_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, double tau, double* s
   int herr = 0;
   RL_CUDA(cudaMemcpyAsync(&herr, p->err, sizeof(int), cudaMemcpyDeviceToHost, st));
 
-  // Sketch and factorise (Alg. 2, lines 1-3)
+  // Sketch and factorise (the first steps of Alg. 2)
   RL_TRY(sketch_dispatch(A, m, n, lda, p->dtype, d, p->opts.zeta, p->opts.seed, p->opts.sketch_prec, p->SA, st));
   RL_CUDA(cudaEventRecord(p->ev[1], st));
   int sweeps = 0;
@@ -246,7 +246,7 @@ int solve_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, double tau, double* s
   double sigma11 = 0;
   if (exact) {
     RL_CUDA(cudaMemcpyAsync(&sigma11, p->sk_sigma, sizeof(double), cudaMemcpyDeviceToHost, st));
-    // Sketch-and-solve start V~(:, n-b+1:n) (Alg. 2, line 4)
+    // Sketch-and-solve start V~(:, n-b+1:n) (Alg. 2)
     RL_TRY((take_start_launch<S, T>((const S*)p->Vt, n, b, Tb, ld, st)));
   } else {
     // Only the two parts of SVD(SA) = SVD(R) the method uses. Sigma~(1,1): block power iteration
@@ -281,7 +281,7 @@ int solve_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, double tau, double* s
   RL_CUDA(cudaStreamSynchronize(st));
   if (herr & DEV_ERR_NONFINITE) return RLOBPCG_ERR_NONFINITE;
 
-  // Sketch-and-solve start and initial Rayleigh-Ritz (Alg. 2, lines 4-7)
+  // Sketch-and-solve start and the initial Rayleigh-Ritz step (Alg. 2)
   split::WDigits wd{};
   if (p->split) wd = split_w_digits(p->swork, m, n, b);
   bool w_ready = false;
