@@ -66,9 +66,12 @@ size_t max_smem_optin() {
   return (size_t)cached[dev];
 }
 
-// Scratch error word shared by the step entry points (bounded device waits report here).
+// Scratch error word of the step entry points (bounded device waits report here). One per host
+// thread and device: a thread's calls are sequential (each synchronises its stream before it
+// returns), so calls from different threads on different streams never share a word. The word
+// lives as long as the process.
 static int* step_err_word(cudaStream_t st) {
-  static int* w[64] = {nullptr};
+  static thread_local int* w[64] = {nullptr};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) dev = 0;
