@@ -189,6 +189,24 @@ def cpu_cores():
     return os.cpu_count() or 1
 
 
+def oracle_rate_one_thread(workload, n_solves=1, timeout=300):
+    """The same oracle sample with every BLAS/OpenMP pool at one thread, in a fresh interpreter
+    (the pools of this process are already sized); None if it cannot be measured."""
+    env = dict(os.environ)
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS",
+                "VECLIB_MAXIMUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[var] = "1"
+    code = ("import json, bench; v, t = bench.oracle_solves_per_s(bench.WORKLOADS[%r], %d); "
+            "print(json.dumps([v, sum(t)]))" % (workload, n_solves))
+    try:
+        r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                           timeout=timeout)
+        v, secs = json.loads(r.stdout.strip().splitlines()[-1])
+        return float(v), float(secs)
+    except (subprocess.SubprocessError, ValueError, IndexError, OSError):
+        return None
+
+
 # --------------------------------------------------------------------------------------- our arm
 
 def gram_traffic_per_element():
@@ -414,6 +432,10 @@ def run_ours(args, rank, world, local_rank):
                                       "sample": f"3 oracle solves of the same matrix families at m={int(M * SAMPLE_FRAC)} "
                                                 f"rows ({sum(times):.1f} s), scaled by {SAMPLE_FRAC} (work is linear "
                                                 f"in m); numpy/LAPACK with all host cores"}
+            one = oracle_rate_one_thread(args.workload)
+            if one is not None:
+                result["cpu_baseline"]["value_1_thread"] = one[0]
+                result["cpu_baseline"]["sample"] += f"; value_1_thread: one such solve with one thread ({one[1]:.1f} s)"
         out = result
     return out
 

@@ -54,3 +54,9 @@ def test_traffic_is_null_once_the_kernel_changed(tmp_path, monkeypatch):
     _fake_tree(tmp_path, "// kernel source, edited\n", "0123456789abcdef")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench.split_traffic_per_launch(100000, 500, 5) is None
+
+
+def test_single_thread_oracle_sample_runs_in_a_fresh_interpreter():
+    one = bench.oracle_rate_one_thread("small_4000x50", timeout=240)
+    assert one is not None and one[0] > 0 and one[1] > 0
+    assert bench.oracle_rate_one_thread("no_such_workload", timeout=120) is None
