@@ -38,6 +38,7 @@ extern "C" {
 #define RLOBPCG_ERR_NONFINITE (-4)   /* NaN or Inf met in A or in the iteration                   */
 #define RLOBPCG_ERR_TIMEOUT (-5)     /* a bounded device-side wait ran out                        */
 #define RLOBPCG_ERR_UNSUPPORTED (-6) /* shape outside what the kernels handle                     */
+#define RLOBPCG_ERR_CANCELLED (-7)   /* a queued request dropped by rlobpcg_server_destroy          */
 
 /* ---- element types ------------------------------------------------------------------------ */
 #define RLOBPCG_F64 0   /* real double                                */
@@ -74,7 +75,7 @@ typedef struct {
   int gram_split;       /* 1 (default): run the Gram products on the tensor cores by an exact split
                            of A, W and A W into bf16 digits (rlobpcg_gram_split; about FP64
                            accuracy). Real FP64 and b <= 16 only (ignored otherwise); A is split
-                           once per solve into about 32 bytes of device memory per element of A.
+                           once per solve into about 16 bytes of device memory per element of A.
                            0: the FP64 CUDA-core Gram pass (rlobpcg_gram).                    */
   double tau;           /* tolerance of ||R(:,j)|| <= Sigma~(1,1)^2 tau; < 0 means 2 sqrt(n) 2^-52 */
 } rlobpcg_opts;
@@ -161,7 +162,9 @@ size_t rlobpcg_plan_workspace_size(int64_t m, int64_t n, int k, int dtype, const
  */
 typedef struct rlobpcg_server_s* rlobpcg_server_t;
 
-/* Errors: INVALID_ARG (bad budget, max_active outside 1..64, bad device), CUDA. */
+/* Creates the max_active worker streams up front; a server is created with all its slots or not
+ * at all. Errors: INVALID_ARG (bad budget, max_active outside 1..64, bad device), CUDA (a
+ * stream could not be created; nothing is left behind). */
 int rlobpcg_server_create(rlobpcg_server_t* out, size_t hbm_budget_bytes, int max_active, int device);
 
 /* Queue a solve of the k smallest singular triplets of A (HOST memory, m x n row-major, lda >= n,
@@ -176,7 +179,9 @@ int rlobpcg_server_poll(rlobpcg_server_t s, int64_t ticket);
 
 /* Block until the request is done and copy its results to HOST buffers (sigma k, V n x k
  * row-major in the dtype of A, resid k; each may be NULL). latency_ms: submit -> done.
- * Returns the solve's status (OK, NOT_CONVERGED or an error). The ticket is released. */
+ * Returns the solve's status (OK, NOT_CONVERGED, CANCELLED when the server was destroyed before
+ * the request was admitted, or an error). The ticket is released. One thread waits per ticket:
+ * a second wait on a ticket that already has a waiter returns INVALID_ARG at once. */
 int rlobpcg_server_wait(rlobpcg_server_t s, int64_t ticket, double* sigma, void* V, double* resid,
                         rlobpcg_info* info, double* latency_ms);
 
@@ -185,8 +190,10 @@ int rlobpcg_server_wait(rlobpcg_server_t s, int64_t ticket, double* sigma, void*
 int rlobpcg_server_stats(rlobpcg_server_t s, int64_t* completed, double* p50_ms, double* p99_ms,
                          double* solves_per_s, size_t* peak_bytes, int* peak_running);
 
-/* Stop the workers after their current solves; requests not yet admitted are dropped. Call it
- * after every rlobpcg_server_wait has returned. */
+/* Stop the server: requests not yet admitted are cancelled (their waiters return
+ * RLOBPCG_ERR_CANCELLED), running solves finish, and the call returns once every worker has
+ * stopped and every thread inside rlobpcg_server_wait for this server has returned. No other call
+ * on this server may start during or after it. */
 int rlobpcg_server_destroy(rlobpcg_server_t s);
 
 /* Static string naming a status code. */
@@ -253,6 +260,8 @@ size_t rlobpcg_gram_workspace_size(int64_t m, int64_t n, int b, int dtype);
  * For callers that cannot let a library allocate device memory: a serving process that has
  * budgeted all of HBM at start-up, or a loop that must avoid cudaMalloc/cudaFree because they
  * synchronise the whole device. This call makes no allocation of any kind.
+ *   - The call is synchronous: it reads the device error word back and synchronises `stream`
+ *     before it returns.
  *   - The first call on a device looks up the buffer's device address (once per device, with
  *     that device current); make that first call before any stream capture.
  *   - All calls share the one buffer, which keeps the last call's contents: calls that overlap

@@ -3,13 +3,23 @@
 TEST INFRASTRUCTURE ONLY: tests/, __graft_entry__.smoke() and bench.py's CPU baseline may import
 it; the GPU library shares no code with it and never calls it.
 
-What it computes: Epperly, Park & Nakatsukasa, "Fast, high-accuracy, randomized nullspace
-computations for tall matrices" (arXiv 2602.16797), Algorithm 2 (block RLOBPCG; Algorithm 1 is
-its b = 1 case), step by step and in the paper's notation. The only building blocks are numpy /
-LAPACK primitives (matmul, SVD, Householder QR); there is no blocking, fusion or reordering
-beyond what the algorithm states. Arithmetic is float64 (complex128 for complex A); the optional
-FP32 sketch rounds A to float32 and sums in float32, as the mixed-precision form of the method
-does, and everything after the sketch SVD is float64 again.
+What it computes: the k smallest singular values of a tall A and their right singular vectors,
+by the method of Epperly, Park & Nakatsukasa, "Fast, high-accuracy, randomized nullspace
+computations for tall matrices" (arXiv 2602.16797): a SparseStack sketch SA (Sec. 2.2) whose SVD
+gives the preconditioner P = V~ Sigma~^{-1} (Sec. 2.1) and the sketch-and-solve start block
+V~(:, n-b+1:n) (Sec. 3.1); then block LOBPCG on A^H A (Sec. 2.1, 2.3): each iteration forms the
+preconditioned residual direction W = P P^* (A^H A V - V Theta^2), makes it orthonormal and
+orthogonal to the current block V and momentum block X (two block Gram-Schmidt passes, then a
+Householder Orth), and replaces V by the b right singular vectors of A T, T = [V X W], that belong
+to its b smallest singular values (Rayleigh-Ritz by energy minimisation: the SVD of A T instead
+of an eigenproblem of T^H A^H A T, which would square the small singular values). The momentum
+block is the part of the new trial space orthogonal to the new V (Sec. 2.1, the x-defining
+equation). Stopping follows Sec. 2.1 (the sketched tolerance on the residual, with the
+stagnation checks). Only numpy / LAPACK primitives are used (matmul, SVD, Householder QR); each
+quantity is formed the plain way its definition states, with no blocking, fusion or
+reordering, so that it can be checked against the paper by eye. Arithmetic is float64
+(complex128 for complex A); the optional FP32 sketch rounds A to float32 and sums in float32, as
+the mixed-precision form of the method does, and everything after the sketch SVD is float64.
 
 Readings taken where the paper is silent, ambiguous or inconsistent:
   * SparseStack randomness (Sec. 2.2 says "uniformly random"): entry (i, j) -- source row i, piece

@@ -86,9 +86,7 @@ static int finish(cudaStream_t st, int* err) {
   int herr = 0;
   if (err) RL_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
   RL_CUDA(cudaStreamSynchronize(st));
-  if (herr & DEV_ERR_TIMEOUT) return RLOBPCG_ERR_TIMEOUT;
-  if (herr & DEV_ERR_NONFINITE) return RLOBPCG_ERR_NONFINITE;
-  return RLOBPCG_OK;
+  return dev_err_status(herr);
 }
 
 }  // namespace rl
@@ -105,6 +103,7 @@ extern "C" const char* rlobpcg_status_string(int s) {
     case RLOBPCG_ERR_NONFINITE: return "non-finite value in input or iteration";
     case RLOBPCG_ERR_TIMEOUT: return "bounded device wait ran out";
     case RLOBPCG_ERR_UNSUPPORTED: return "shape not supported by the kernels";
+    case RLOBPCG_ERR_CANCELLED: return "request cancelled before it ran";
     default: return "unknown status";
   }
 }

@@ -256,6 +256,14 @@ const char* last_error();
 // device-side error flags (bounded waits that ran out, non-finite values)
 enum : int { DEV_ERR_TIMEOUT = 1, DEV_ERR_NONFINITE = 2, DEV_ERR_BOUNDS = 4 };
 
+// Status of an entry point from the device error word it read back (one mapping for all of them)
+inline int dev_err_status(int herr) {
+  if (herr & DEV_ERR_TIMEOUT) return RLOBPCG_ERR_TIMEOUT;
+  if (herr & DEV_ERR_NONFINITE) return RLOBPCG_ERR_NONFINITE;
+  if (herr & DEV_ERR_BOUNDS) return RLOBPCG_ERR_INVALID_ARG;
+  return RLOBPCG_OK;
+}
+
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
 template <class T> __host__ __device__ inline T imin(T a, T b) { return a < b ? a : b; }

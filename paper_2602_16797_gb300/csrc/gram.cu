@@ -410,5 +410,5 @@ extern "C" int rlobpcg_gram_noalloc(const void* A, int64_t m, int64_t n, int64_t
   int herr = 0;
   RL_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
   RL_CUDA(cudaStreamSynchronize(st));
-  return (herr & DEV_ERR_TIMEOUT) ? RLOBPCG_ERR_TIMEOUT : RLOBPCG_OK;
+  return dev_err_status(herr);
 }

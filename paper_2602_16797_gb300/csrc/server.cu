@@ -32,6 +32,7 @@ struct Request {
   rlobpcg_opts opts{};
   size_t bytes = 0;
   int state = 0;  // 0 queued, 1 running, 2 done
+  bool claimed = false;  // a thread is in rlobpcg_server_wait for this ticket
   int rc = 0;
   char err[512] = "";  // the worker's last error message when rc != RLOBPCG_OK
   clock_t_::time_point t_arrive, t_start, t_done;
@@ -56,16 +57,16 @@ struct rlobpcg_server_s {
   std::unordered_map<int64_t, Request*> all;
   std::vector<double> latencies_ms;
   std::vector<std::thread> workers;
+  std::vector<cudaStream_t> streams;  // one per worker, created by rlobpcg_server_create
+  int waiters = 0;                    // threads inside rlobpcg_server_wait
   clock_t_::time_point t_first{}, t_last{};
   bool any_done = false;
 };
 
 namespace {
 
-void worker_main(rlobpcg_server_s* s) {
+void worker_main(rlobpcg_server_s* s, cudaStream_t st) {
   cudaSetDevice(s->device);
-  cudaStream_t st = nullptr;
-  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return;
   for (;;) {
     Request* r = nullptr;
     {
@@ -104,7 +105,7 @@ void worker_main(rlobpcg_server_s* s) {
     }
     if (rc == RLOBPCG_OK)
       rc = rlobpcg_solve(plan, Ad, r->n, -1.0, r->sigma.data(), r->V.data(), nullptr, r->resid.data(), &r->info);
-    if (rc != RLOBPCG_OK) snprintf(r->err, sizeof(r->err), "%s", rlobpcg_last_error());
+    if (rc < 0) snprintf(r->err, sizeof(r->err), "%s", rlobpcg_last_error());
     if (Ad) cudaFreeAsync(Ad, st);
     rlobpcg_plan_destroy(plan);
     cudaStreamSynchronize(st);
@@ -122,7 +123,6 @@ void worker_main(rlobpcg_server_s* s) {
     s->cv_done.notify_all();
     s->cv_work.notify_all();
   }
-  cudaStreamDestroy(st);
 }
 
 // Device footprint of one request: the plan's workspace plus a device copy of A.
@@ -152,7 +152,21 @@ extern "C" int rlobpcg_server_create(rlobpcg_server_t* out, size_t hbm_budget_by
   s->device = device;
   s->budget = hbm_budget_bytes;
   s->max_active = max_active;
-  for (int i = 0; i < max_active; ++i) s->workers.emplace_back(worker_main, s);
+  // every worker's stream exists before any worker starts: a server either has all its slots or
+  // is not created
+  for (int i = 0; i < max_active; ++i) {
+    cudaStream_t st = nullptr;
+    const cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      set_last_error(cudaGetErrorString(e), __FILE__, __LINE__);
+      for (cudaStream_t q : s->streams) cudaStreamDestroy(q);
+      delete s;
+      return RLOBPCG_ERR_CUDA;
+    }
+    s->streams.push_back(st);
+  }
+  for (int i = 0; i < max_active; ++i) s->workers.emplace_back(worker_main, s, s->streams[i]);
   *out = s;
   return RLOBPCG_OK;
 }
@@ -205,10 +219,17 @@ extern "C" int rlobpcg_server_wait(rlobpcg_server_t s, int64_t ticket, double* s
   {
     std::unique_lock<std::mutex> lk(s->mu);
     auto it = s->all.find(ticket);
-    if (it == s->all.end()) return RLOBPCG_ERR_INVALID_ARG;
+    // an unknown ticket, or one another thread is already waiting for
+    if (it == s->all.end() || it->second->claimed) return RLOBPCG_ERR_INVALID_ARG;
     r = it->second;
+    r->claimed = true;
+    ++s->waiters;
     s->cv_done.wait(lk, [&] { return r->state == 2; });
     s->all.erase(ticket);   // look up again: the map may have rehashed while waiting
+    --s->waiters;
+    // rlobpcg_server_destroy may be waiting for the last waiter to leave; notified under the
+    // lock, so that the server cannot be deleted before this thread is done with it
+    s->cv_done.notify_all();
   }
   if (sigma) std::copy(r->sigma.begin(), r->sigma.end(), sigma);
   if (resid) std::copy(r->resid.begin(), r->resid.end(), resid);
@@ -216,7 +237,7 @@ extern "C" int rlobpcg_server_wait(rlobpcg_server_t s, int64_t ticket, double* s
   if (info) *info = r->info;
   if (latency_ms) *latency_ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_arrive).count();
   const int rc = r->rc;
-  if (rc != RLOBPCG_OK) rl::set_last_error_text(r->err);
+  if (rc < 0) rl::set_last_error_text(r->err);
   delete r;
   return rc;
 }
@@ -249,13 +270,30 @@ extern "C" int rlobpcg_server_stats(rlobpcg_server_t s, int64_t* completed, doub
 extern "C" int rlobpcg_server_destroy(rlobpcg_server_t s) {
   if (!s) return RLOBPCG_OK;
   {
+    // requests not yet admitted are cancelled: done, with RLOBPCG_ERR_CANCELLED, so that a thread
+    // waiting for one of them returns instead of waiting for a worker that will never run it
     std::lock_guard<std::mutex> lk(s->mu);
     s->stop = true;
+    const auto now = clock_t_::now();
+    for (Request* r : s->queue) {
+      r->state = 2;
+      r->rc = RLOBPCG_ERR_CANCELLED;
+      r->t_done = now;
+      snprintf(r->err, sizeof(r->err), "request cancelled by rlobpcg_server_destroy before it was admitted");
+    }
+    s->queue.clear();
   }
+  s->cv_done.notify_all();
   s->cv_work.notify_all();
+  // running solves finish and wake their waiters
   for (auto& t : s->workers) t.join();
+  {
+    // every waiter has left rlobpcg_server_wait before the server's memory goes away
+    std::unique_lock<std::mutex> lk(s->mu);
+    s->cv_done.wait(lk, [&] { return s->waiters == 0; });
+  }
   for (auto& kv : s->all) delete kv.second;
-  for (auto* r : s->queue) (void)r;  // queued requests are owned by `all`
+  for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
   delete s;
   return RLOBPCG_OK;
 }

@@ -420,8 +420,7 @@ int solve_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, double tau, double* s
       info->ms_split_a = ms;
     }
   }
-  if (herr & DEV_ERR_TIMEOUT) return RLOBPCG_ERR_TIMEOUT;
-  if (herr & DEV_ERR_NONFINITE) return RLOBPCG_ERR_NONFINITE;
+  if (dev_err_status(herr) != RLOBPCG_OK) return dev_err_status(herr);
   return stop == RLOBPCG_STOP_MAX_ITER ? RLOBPCG_NOT_CONVERGED : RLOBPCG_OK;
 }
 

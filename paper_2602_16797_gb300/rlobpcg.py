@@ -23,6 +23,7 @@ RLOBPCG_ERR_CUDA = -3
 RLOBPCG_ERR_NONFINITE = -4
 RLOBPCG_ERR_TIMEOUT = -5
 RLOBPCG_ERR_UNSUPPORTED = -6
+RLOBPCG_ERR_CANCELLED = -7
 RLOBPCG_F64 = 0
 RLOBPCG_C128 = 1
 RLOBPCG_SKETCH_F64 = 0

@@ -1,5 +1,8 @@
 """Serving with continuous batching (rlobpcg_server_*): each result is the same alone and in the
-mix, the HBM budget is respected, and requests beyond it are refused."""
+mix, the HBM budget is respected, requests beyond it are refused, queued requests are cancelled
+(and their waiters woken) by destroy, and one ticket has one waiter."""
+import threading
+
 import numpy as np
 import pytest
 
@@ -71,5 +74,59 @@ def test_server_refuses_request_beyond_budget():
         with pytest.raises(rl.RlobpcgError) as e:
             rl.rlobpcg_server_submit(srv, A.ctypes.data, 5000, 40, 40, 1, rl.RLOBPCG_F64, None)
         assert e.value.code == rl.RLOBPCG_ERR_OOM
+    finally:
+        rl.rlobpcg_server_destroy(srv)
+
+
+def _waiter(srv, ticket, n, k, out):
+    """Wait for one ticket on a thread; records the status code (0, 1 or the error raised)."""
+    sig = np.zeros(k)
+    V = np.zeros((n, k))
+    try:
+        rc, _ = rl.rlobpcg_server_wait(srv, ticket, sig.ctypes.data, V.ctypes.data, None)
+        out.append(rc)
+    except rl.RlobpcgError as e:
+        out.append(e.code)
+
+
+def test_destroy_cancels_queued_requests_and_wakes_waiters():
+    reqs = _requests(count=5, max_m=60_000)
+    srv = rl.rlobpcg_server_create(1 << 36, 1, 0)    # one slot: all but the first request queue
+    tickets = [rl.rlobpcg_server_submit(srv, A.ctypes.data, A.shape[0], A.shape[1], A.shape[1], k,
+                                        rl.RLOBPCG_F64, _opts(seed)) for A, k, seed in reqs]
+    results = [[] for _ in reqs]
+    threads = [threading.Thread(target=_waiter, args=(srv, t, A.shape[1], k, res))
+               for (A, k, _), t, res in zip(reqs, tickets, results)]
+    for th in threads:
+        th.start()
+    rl.rlobpcg_server_destroy(srv)                   # returns only after every waiter has left
+    for th in threads:
+        th.join(timeout=60)
+        assert not th.is_alive()
+    codes = [r[0] for r in results]
+    assert all(c in (rl.RLOBPCG_OK, rl.RLOBPCG_NOT_CONVERGED, rl.RLOBPCG_ERR_CANCELLED) for c in codes), codes
+    # the last request cannot have started before destroy (one slot, four ahead of it)
+    assert codes[-1] == rl.RLOBPCG_ERR_CANCELLED
+
+
+def test_one_waiter_per_ticket():
+    reqs = _requests(count=3, max_m=60_000)
+    srv = rl.rlobpcg_server_create(1 << 36, 1, 0)
+    try:
+        tickets = [rl.rlobpcg_server_submit(srv, A.ctypes.data, A.shape[0], A.shape[1], A.shape[1], k,
+                                            rl.RLOBPCG_F64, _opts(seed)) for A, k, seed in reqs]
+        A, k, _ = reqs[-1]
+        out = []
+        th = [threading.Thread(target=_waiter, args=(srv, tickets[-1], A.shape[1], k, out)) for _ in range(2)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join(timeout=120)
+            assert not t.is_alive()
+        # whichever thread claimed the ticket first gets the result; the other is refused
+        assert len(out) == 2 and out.count(rl.RLOBPCG_ERR_INVALID_ARG) == 1, out
+        assert all(c in (rl.RLOBPCG_OK, rl.RLOBPCG_NOT_CONVERGED, rl.RLOBPCG_ERR_INVALID_ARG) for c in out), out
+        for t, (A, k, _) in zip(tickets[:-1], reqs[:-1]):
+            rl.rlobpcg_server_wait(srv, t, None, None, None)
     finally:
         rl.rlobpcg_server_destroy(srv)

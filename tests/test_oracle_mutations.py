@@ -88,3 +88,20 @@ def test_wrong_stagnation_index_is_caught(monkeypatch):
         return orig(i - 1, res_hist, theta_hist, sigma11, tau, use_stagnation)
     _patch(monkeypatch, "stop_check", bad)
     _expect_failure(pins.test_stop_rule_hand_worked)
+
+
+def test_gram_pass_without_conjugate_is_caught(monkeypatch):
+    def bad(A, W):
+        AW = A @ W
+        return AW, A.T @ AW                                  # A^T instead of A^H
+    _patch(monkeypatch, "gram_pass", bad)
+    _expect_failure(lambda: pins.test_gram_pass_exact_on_integers(True))
+
+
+def test_gram_pass_dropping_a_row_is_caught(monkeypatch):
+    def bad(A, W):
+        AW = A @ W
+        return AW, A[1:].conj().T @ AW[1:]                   # first row missing from the sum
+    _patch(monkeypatch, "gram_pass", bad)
+    _expect_failure(lambda: pins.test_gram_pass_exact_on_integers(False))
+    _expect_failure(pins.test_gram_pass_within_rounding_of_exact_rationals)

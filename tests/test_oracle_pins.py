@@ -32,6 +32,83 @@ def _distortion(A, S):
 
 
 # ---------------------------------------------------------------------------------------------
+# The two products of one iteration: A W and A^H (A W) (Alg. 2)
+# ---------------------------------------------------------------------------------------------
+
+def _int_matrix(rng, rows, cols, complex_, lim=60):
+    re = rng.integers(-lim, lim + 1, size=(rows, cols))
+    if not complex_:
+        return re.astype(np.int64)
+    return re + 1j * rng.integers(-lim, lim + 1, size=(rows, cols))
+
+
+def _exact_products(A, W):
+    """A W and A^H (A W) by definition, in Python integers (Gaussian integers for complex data):
+    (A W)_ij = sum_k a_ik w_kj and (A^H Y)_kj = sum_i conj(a_ik) y_ij, with no rounding at all."""
+    m, n = A.shape
+    b = W.shape[1]
+    cplx = np.iscomplexobj(A)
+    to = (lambda z: (int(z.real), int(z.imag))) if cplx else (lambda z: (int(z), 0))
+    a = [[to(A[i, k]) for k in range(n)] for i in range(m)]
+    w = [[to(W[k, j]) for j in range(b)] for k in range(n)]
+    mul = lambda x, y: (x[0] * y[0] - x[1] * y[1], x[0] * y[1] + x[1] * y[0])  # noqa: E731
+    Y = [[(sum(mul(a[i][k], w[k][j])[0] for k in range(n)), sum(mul(a[i][k], w[k][j])[1] for k in range(n)))
+          for j in range(b)] for i in range(m)]
+    G = [[(sum(mul((a[i][k][0], -a[i][k][1]), Y[i][j])[0] for i in range(m)),
+           sum(mul((a[i][k][0], -a[i][k][1]), Y[i][j])[1] for i in range(m))) for j in range(b)] for k in range(n)]
+    return Y, G
+
+
+@pytest.mark.parametrize("complex_", [False, True])
+def test_gram_pass_exact_on_integers(complex_):
+    """On small integer (Gaussian-integer) data every product and partial sum of A W and
+    A^H (A W) is an integer below 2^53, so float64 arithmetic is exact and the oracle must agree
+    bit for bit with the definition of the two products (conjugate transpose in the second)."""
+    rng = np.random.default_rng(31)
+    A = _int_matrix(rng, 29, 11, complex_)
+    W = _int_matrix(rng, 11, 3, complex_)
+    Y, G = _exact_products(A, W)
+    AW, GW = oracle.gram_pass(A.astype(np.complex128 if complex_ else np.float64),
+                              W.astype(np.complex128 if complex_ else np.float64))
+    assert max(abs(v) for row in Y for c in row for v in c) < 2 ** 53
+    assert max(abs(v) for row in G for c in row for v in c) < 2 ** 53
+    for i in range(A.shape[0]):
+        for j in range(W.shape[1]):
+            assert AW[i, j].real == Y[i][j][0] and np.imag(AW[i, j]) == Y[i][j][1], (i, j)
+    for k in range(A.shape[1]):
+        for j in range(W.shape[1]):
+            assert GW[k, j].real == G[k][j][0] and np.imag(GW[k, j]) == G[k][j][1], (k, j)
+
+
+def test_gram_pass_within_rounding_of_exact_rationals():
+    """Non-integer data: the exact products in rational arithmetic (every float64 is a dyadic
+    rational) against the oracle's float64 products, within the standard dot-product bound
+    gamma_n |A| |W| (Higham, Accuracy and Stability of Numerical Algorithms, Sec. 3.1), and for
+    the second product gamma_m |A|^T |A W| plus the first product's error carried through A^T."""
+    from fractions import Fraction
+    rng = np.random.default_rng(32)
+    m, n, b = 13, 7, 2
+    A = rng.standard_normal((m, n)) * np.exp(rng.uniform(-3, 3, (m, n)))
+    W = rng.standard_normal((n, b))
+    AW, GW = oracle.gram_pass(A, W)
+    Af = [[Fraction(float(x)) for x in row] for row in A]
+    Wf = [[Fraction(float(x)) for x in row] for row in W]
+    Yf = [[sum(Af[i][k] * Wf[k][j] for k in range(n)) for j in range(b)] for i in range(m)]
+    Gf = [[sum(Af[i][k] * Yf[i][j] for i in range(m)) for j in range(b)] for k in range(n)]
+    u = 2.0 ** -53
+    gam = lambda p: p * u / (1 - p * u)  # noqa: E731
+    absA = np.abs(A)
+    bY = gam(n) * (absA @ np.abs(W))
+    bG = gam(m) * (absA.T @ np.abs(AW)) + absA.T @ bY * (1 + gam(m))
+    for i in range(m):
+        for j in range(b):
+            assert abs(Fraction(float(AW[i, j])) - Yf[i][j]) <= Fraction(float(bY[i, j])) * Fraction(101, 100)
+    for k in range(n):
+        for j in range(b):
+            assert abs(Fraction(float(GW[k, j])) - Gf[k][j]) <= Fraction(float(bG[k, j])) * Fraction(101, 100)
+
+
+# ---------------------------------------------------------------------------------------------
 # SplitMix64 and the SparseStack pattern (Sec. 2.2)
 # ---------------------------------------------------------------------------------------------
 

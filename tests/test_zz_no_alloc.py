@@ -6,7 +6,8 @@ or let it allocate one. The allocation-free entry point keeps its split-m scratc
 device buffer inside the library. These tests call it through the C ABI and check that two
 calls in a row (different inputs, so the second cannot pass by reusing the first one's scratch)
 give the same results as rlobpcg_gram with a caller-provided workspace, within the bounds the
-other Gram tests use, and that an oversized problem is refused cleanly.
+other Gram tests use, that warm calls leave the device's free memory and torch's reserved pool
+unchanged, and that an oversized problem is refused cleanly.
 
 The file sorts last so that a run stopping at the first failure has already run everything else.
 """
@@ -82,3 +83,29 @@ def test_noalloc_refuses_problems_beyond_its_buffer():
     assert rc == rl.RLOBPCG_ERR_UNSUPPORTED
     assert "16 MiB" in rl.rlobpcg_last_error()
     assert rl.load().rlobpcg_gram_noalloc(None, 10, 10, 10, 0, p, 1, 1, p, 1, p, 1, None) == rl.RLOBPCG_ERR_INVALID_ARG
+
+
+def test_noalloc_calls_leave_device_memory_unchanged():
+    """After one warm-up call (which may load the kernels), further calls allocate nothing: the
+    driver's free-memory count and torch's reserved pool are the same before and after them."""
+    rng = np.random.default_rng(5)
+    m, n, b = 20_000, 200, 4
+    Ad = torch.from_numpy(rng.standard_normal((m, n))).cuda()
+    Wd = torch.from_numpy(rng.standard_normal((n, b))).cuda()
+    AW = torch.empty((m, b), dtype=torch.float64, device="cuda")
+    G = torch.empty((n, b), dtype=torch.float64, device="cuda")
+
+    def call():
+        rl.rlobpcg_gram_noalloc(Ad.data_ptr(), m, n, n, rl.RLOBPCG_F64, Wd.data_ptr(), b, b, AW.data_ptr(), b,
+                                G.data_ptr(), b, _stream())
+
+    call()
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    reserved0 = torch.cuda.memory_reserved()
+    for _ in range(4):
+        call()
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.cuda.memory_reserved() == reserved0
