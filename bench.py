@@ -1,21 +1,25 @@
 """Benchmark: RLOBPCG solves/s on GB300 (one JSON line on rank 0).
 
-Workload (default): m = 1e5, n = 500, k = 5, d = 3n, zeta = 8, FP64. Two seeded synthetic matrices
-of the paper's structure, solved alternately: A = B C with an exact 5-dimensional nullspace, and a
-planted spectrum with sigma_496..500 in [1e-12, 1e-9] below sigma_495 = 1e-4 (Haar U, V).
-One step = one complete solve (sketch, QR, SVD of R, R^{-1}, start block, LOBPCG iterations with
-the paper's stopping rule, outputs). A (400 MB) is larger than the 129 MB L2, so no flush is needed
-between steps.
+Workload (default): the large planted configuration m = 1e6, n = 1000, k = 10, d = 4n, zeta = 8,
+FP64 A of 8 GB (sigma_1..990 logspace(0,-4), sigma_991..1000 logspace(-9,-10), Haar U and V; built
+on the GPU from a seeded Philox Gaussian). One step = one complete solve (sketch, QR, start block,
+LOBPCG iterations with the paper's stopping rule, outputs). A (8 GB) is far larger than the
+129 MB L2, so no flush is needed between steps. The line also carries the mixed-precision form
+(`mixed`: FP32 sketch and R refined once in FP64) timed on the same matrix.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
+                  [--fixed-iters I]
 
---workload selects one of the other configurations of the study (small 4000 x 50, complex
-2e5 x 300 with FP32 or FP64 sketch, 1e6 x 1000 FP64 or mixed); the default is the one above.
+--workload selects one of the other configurations of the study (4000 x 50, 1e5 x 500 exact
+nullspace + planted cluster, complex 2e5 x 300, the clustered 1e6 x 2000 block-size study, the
+serving stream); --fixed-iters runs exactly I LOBPCG iterations per solve (no stop test), which
+makes the per-iteration time independent of where the stopping rule fires.
 
 Under torchrun each rank solves its own matrices on its own GPU (independent problems, no
 collective on the data path: weak scaling); rank 0 prints the max-over-ranks time.
 `--impl reference` times the CPU oracle (the plain numpy implementation of Algorithm 2 that the
-tests check the GPU against) on a bounded row sample of the same workload.
+tests check the GPU against) per phase on a bounded row sample of the same matrix family and
+scales it to the full size.
 """
 from __future__ import annotations
 
@@ -37,61 +41,77 @@ sys.path.insert(0, ROOT)
 from paper_2602_16797_gb300 import replicas  # noqa: E402
 
 METRIC = "solve time & solves/s at stated σ/angle error; fused AᴴAX GB/s; p50/p99 latency"
-SAMPLE_FRAC = 0.2          # row sample of the CPU oracle timings (m -> 0.2 m)
 FP64_UNITS_PER_SM_CLK = 2  # DFMA per clock per SM: 1.25 TFLOP/s nominal / (152 SMs * 2.07 GHz * 2 flop)
+DIGIT_PAIRS = 64           # digit pairs per product of the split-bf16 Gram pass (8 x 8 digits)
 
 
 def _host_pair(m):
     from paper_2602_16797_gb300 import workloads as wl
     A0, _ = wl.exact_nullspace(m=m)
-    A1, _, _ = wl.planted_bottom_cluster(m=m)
-    return [A0, A1]
+    A1, s1, _ = wl.planted_bottom_cluster(m=m)
+    return [A0, A1], [np.zeros(5), np.sort(s1)[:5]]
 
 
 def _host_small(m):
     from paper_2602_16797_gb300 import workloads as wl
-    return [wl.planted_small_gap_free(m=m)[0]]
+    A, s, _ = wl.planted_small_gap_free(m=m)
+    return [A], [np.sort(s)[:1]]
 
 
 def _host_complex(m):
     from paper_2602_16797_gb300 import workloads as wl
-    return [wl.planted_complex(m=m)[0]]
+    A, s, _ = wl.planted_complex(m=m)
+    return [A], [np.sort(s)[:3]]
+
+
+def _large_sigma(n=1000, k=10):
+    return np.concatenate([np.logspace(0, -4, n - k), np.logspace(-9, -10, k)])
 
 
 def _device_large(m, device):
     from paper_2602_16797_gb300 import workloads as wl
-    return [wl.planted_large_device(m=m, device=device)[0]]
+    A, s, _ = wl.planted_large_device(m=m, device=device)
+    return [A], [np.sort(s)[:10]]
 
 
-# Named workloads. The default is the m = 1e5, n = 500, k = 5 configuration; the others are the
-# remaining configurations of the same study (same JSON line, selected with --workload).
+def _host_large_sample(m):
+    """The same spectrum as the 1e6 x 1000 matrix on a row sample (host, for the CPU oracle)."""
+    from paper_2602_16797_gb300 import workloads as wl
+    A, s, _ = wl.planted_large(m=m)
+    return [A], [np.sort(s)[:10]]
+
+
+def _host_complex_sample(m):
+    return _host_complex(m)
+
+
+# Named workloads: the configurations of the study (same JSON line, selected with --workload).
+# `sample_m` is the row count of the CPU oracle's sample; `host_sample` builds it.
 WORKLOADS = {
+    "large_1e6x1000": dict(
+        desc="planted m=1e6 n=1000 k=10 d=4n zeta=8 fp64", m=1_000_000, n=1000, k=10, d=4000,
+        zeta=8, cplx=False, prec=0, device=_device_large, seeds=(1004,), mixed_prec=1,
+        host_sample=_host_large_sample, sample_m=100_000,
+        matrices="planted sigma_1..990 logspace(0,-4), sigma_991..1000 logspace(-9,-10), Haar U, V"),
     "nullspace_1e5x500": dict(
         desc="nullspace+planted m=1e5 n=500 k=5 d=3n zeta=8 fp64", m=100_000, n=500, k=5, d=1500, zeta=8,
-        cplx=False, prec=0, host=_host_pair, seeds=(2002, 2003),
+        cplx=False, prec=0, host=_host_pair, seeds=(2002, 2003), sample_m=20_000,
         matrices="exact nullspace A=BC and planted sigma_496..500 in [1e-12,1e-9], alternating"),
     "small_4000x50": dict(
         desc="planted m=4000 n=50 k=1 d=4n zeta=8 tau=1e-12 fp64", m=4000, n=50, k=1, d=200, zeta=8, cplx=False,
-        prec=0, host=_host_small, seeds=(1001,), tau=1e-12, stagnation=0,
+        prec=0, host=_host_small, seeds=(1001,), tau=1e-12, stagnation=0, sample_m=4000,
         matrices="planted sigma_1..49 logspace(0,-6), sigma_50=1e-10"),
-    "complex_2e5x300_f32sketch": dict(
-        desc="complex planted m=2e5 n=300 k=3 d=4n zeta=8 fp32 sketch", m=200_000, n=300, k=3, d=1200, zeta=8,
-        cplx=True, prec=1, host=_host_complex, seeds=(1003,),
-        matrices="complex planted sigma logspace(0,-8), three smallest 1e-12, 3e-13, 1e-13"),
     "complex_2e5x300": dict(
         desc="complex planted m=2e5 n=300 k=3 d=4n zeta=8 fp64 sketch", m=200_000, n=300, k=3, d=1200, zeta=8,
-        cplx=True, prec=0, host=_host_complex, seeds=(1003,),
+        cplx=True, prec=0, host=_host_complex, seeds=(1003,), mixed_prec=1, sample_m=40_000,
+        host_sample=_host_complex_sample,
         matrices="complex planted sigma logspace(0,-8), three smallest 1e-12, 3e-13, 1e-13"),
-    "large_1e6x1000_mixed": dict(
-        desc="planted m=1e6 n=1000 k=10 d=4n zeta=8 fp32 sketch/R, fp64 Gram", m=1_000_000, n=1000, k=10, d=4000,
-        zeta=8, cplx=False, prec=1, device=_device_large, seeds=(1004,),
-        matrices="planted sigma_1..990 logspace(0,-4), sigma_991..1000 logspace(-9,-10)"),
-    "large_1e6x1000": dict(
-        desc="planted m=1e6 n=1000 k=10 d=4n zeta=8 fp64", m=1_000_000, n=1000, k=10, d=4000, zeta=8,
-        cplx=False, prec=0, device=_device_large, seeds=(1004,),
-        matrices="planted sigma_1..990 logspace(0,-4), sigma_991..1000 logspace(-9,-10)"),
+    "complex_2e5x300_f32sketch": dict(
+        desc="complex planted m=2e5 n=300 k=3 d=4n zeta=8 fp32 sketch", m=200_000, n=300, k=3, d=1200, zeta=8,
+        cplx=True, prec=1, host=_host_complex, seeds=(1003,), sample_m=40_000, host_sample=_host_complex_sample,
+        matrices="complex planted sigma logspace(0,-8), three smallest 1e-12, 3e-13, 1e-13"),
 }
-DEFAULT_WORKLOAD = "nullspace_1e5x500"
+DEFAULT_WORKLOAD = "large_1e6x1000"
 
 
 # ------------------------------------------------------------------------------------------ clocks
@@ -149,32 +169,60 @@ class ClockSampler:
 
 # ------------------------------------------------------------------------------------- oracle timing
 
-def oracle_solves_per_s(w, n_solves, warmup=0):
-    """The oracle on a row sample (m -> SAMPLE_FRAC m) of the workload; returns (full-size solves/s
-    estimate, per-solve seconds). Per-solve work is linear in m (the sketch and every iteration
-    stream A once)."""
-    import oracle
-    ms = int(w["m"] * SAMPLE_FRAC)
-    if "host" in w:
-        As = w["host"](ms)
-    else:
-        from paper_2602_16797_gb300 import workloads as wl
-        sig = np.concatenate([np.logspace(0, -4, w["n"] - w["k"]), np.logspace(-9, -10, w["k"])])
-        As = [wl.planted(np.random.default_rng(w["seeds"][0]), ms, sig)[0]]
-    kw = dict(k=w["k"], d=w["d"], zeta=w["zeta"], sketch_precision="f32" if w["prec"] else "f64")
+def _oracle_kwargs(w):
+    kw = dict(k=w["k"], d=w["d"], zeta=w["zeta"], sketch_precision="f32" if w["prec"] == 1 else "f64")
     if "tau" in w:
         kw["tau"] = w["tau"]
     if w.get("stagnation", 1) == 0:
         kw["use_stagnation"] = False
-    for i in range(warmup):
-        oracle.rlobpcg(As[i % len(As)], seed=w["seeds"][i % len(w["seeds"])], **kw)
-    times = []
-    for i in range(n_solves):
+    return kw
+
+
+def oracle_sample_phases(w, run_to_stop=True):
+    """Time the CPU oracle, as it stands, on a row sample of the workload (m -> sample_m rows of the
+    same matrix family and spectrum). Returns the seconds of its one-time part (sketch, SVD of the
+    sketch, start block) split into the part that streams A (scales with m) and the SVD of the
+    d x n sketch (does not), the seconds per LOBPCG iteration (every iteration streams A: scales
+    with m), and the iteration count at which the oracle's own stopping rule fires on the sample."""
+    import oracle
+    ms = min(w["sample_m"], w["m"])
+    build = w.get("host_sample") or w["host"]
+    As, _ = build(ms)
+    A = As[0]
+    seed = w["seeds"][0]
+    kw = _oracle_kwargs(w)
+    t0 = time.perf_counter()
+    SA = oracle.sketch(A.astype(np.complex128 if w["cplx"] else np.float64), w["d"], w["zeta"], seed,
+                       kw["sketch_precision"])
+    t1 = time.perf_counter()
+    oracle.sketch_svd(SA)
+    t_svd = time.perf_counter() - t1
+    t0 = time.perf_counter()
+    oracle.rlobpcg(A, seed=seed, fixed_iters=1, **kw)
+    t_fix1 = time.perf_counter() - t0
+    t_fix3 = None
+    stop_iters = None
+    if run_to_stop:
         t0 = time.perf_counter()
-        oracle.rlobpcg(As[i % len(As)], seed=w["seeds"][i % len(w["seeds"])], **kw)
-        times.append(time.perf_counter() - t0)
-    per = sum(times) / len(times)
-    return (ms / w["m"]) / per, times
+        r = oracle.rlobpcg(A, seed=seed, **kw)
+        t_stop = time.perf_counter() - t0
+        stop_iters = int(r["iters"])
+        t_iter = (t_stop - t_fix1) / max(stop_iters - 1, 1)
+    else:
+        t0 = time.perf_counter()
+        oracle.rlobpcg(A, seed=seed, fixed_iters=3, **kw)
+        t_fix3 = time.perf_counter() - t0
+        t_iter = (t_fix3 - t_fix1) / 2.0
+    t_once = max(t_fix1 - t_iter, t_svd)
+    return {"sample_m": ms, "t_svd": t_svd, "t_once_stream": max(t_once - t_svd, 0.0), "t_iter": max(t_iter, 0.0),
+            "stop_iters": stop_iters, "cpu_seconds": None}
+
+
+def oracle_full_solve_seconds(w, ph, iters):
+    """Full-size oracle solve time estimated from the sample's phases: the parts that stream A
+    scale with m / sample_m, the SVD of the d x n sketch does not."""
+    f = w["m"] / ph["sample_m"]
+    return ph["t_once_stream"] * f + ph["t_svd"] + iters * ph["t_iter"] * f
 
 
 def measured_peaks():
@@ -189,29 +237,63 @@ def cpu_cores():
     return os.cpu_count() or 1
 
 
-def oracle_rate_one_thread(workload, n_solves=1, timeout=300):
+def oracle_rate_one_thread(workload, iters, timeout=300):
     """The same oracle sample with every BLAS/OpenMP pool at one thread, in a fresh interpreter
-    (the pools of this process are already sized); None if it cannot be measured."""
+    (the pools of this process are already sized): estimated full-size solves/s at `iters`
+    iterations and the seconds the sample took; None if it cannot be measured in time."""
     env = dict(os.environ)
     for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS",
                 "VECLIB_MAXIMUM_THREADS", "NUMEXPR_NUM_THREADS"):
         env[var] = "1"
-    code = ("import json, bench; v, t = bench.oracle_solves_per_s(bench.WORKLOADS[%r], %d); "
-            "print(json.dumps([v, sum(t)]))" % (workload, n_solves))
+    code = ("import json, time, bench; w = bench.WORKLOADS[%r]; t0 = time.perf_counter(); "
+            "ph = bench.oracle_sample_phases(w, run_to_stop=False); "
+            "print(json.dumps([1.0 / bench.oracle_full_solve_seconds(w, ph, %d), time.perf_counter() - t0]))"
+            % (workload, iters))
     try:
         r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
                            timeout=timeout)
         v, secs = json.loads(r.stdout.strip().splitlines()[-1])
         return float(v), float(secs)
-    except (subprocess.SubprocessError, ValueError, IndexError, OSError):
+    except (subprocess.SubprocessError, ValueError, IndexError, OSError, KeyError):
         return None
 
 
-# --------------------------------------------------------------------------------------- our arm
+# --------------------------------------------------------------------------------- roofline helpers
 
-def gram_traffic_per_element():
-    """DRAM bytes per element of A per Gram pass from the committed ncu summary, if that summary
-    was taken on the current gram.cu (else None)."""
+def pass_algorithmic_bytes(m, n, b, cplx):
+    """Bytes one Gram pass must move at least: A once (m n elements) and A W written once (m b)."""
+    esz = 16 if cplx else 8
+    return esz * (m * n + m * b)
+
+
+def pass_tensor_flops(m, n, b):
+    """Tensor-core work of one split-bf16 Gram pass: two products (A W and A^T (A W)), each over
+    DIGIT_PAIRS digit pairs of 2 m n b multiply-adds (the unpadded block width b)."""
+    return 2 * DIGIT_PAIRS * 2 * m * n * b
+
+
+def pass_traffic(m, n):
+    """DRAM bytes per Gram pass from the committed ncu summary of the split Gram kernels, scaled
+    by m n from the bytes per element of A it states, if that summary was taken on the current
+    gram_tc.cu (else None: the counters belong to another kernel)."""
+    path = os.path.join(ROOT, "profiles", "gram_split_ncu_summary.md")
+    src = os.path.join(ROOT, "paper_2602_16797_gb300", "csrc", "gram_tc.cu")
+    try:
+        txt = open(path).read()
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        tag, per = None, None
+        for ln in txt.splitlines():
+            if ln.startswith("gram_tc.cu sha256[:16]: "):
+                tag = ln.split(": ", 1)[1].strip()
+            if ln.startswith("dram bytes per element of A per pass: "):
+                per = float(ln.split(": ", 1)[1].split()[0])
+        return per * m * n if (tag == h and per is not None) else None
+    except (OSError, ValueError):
+        return None
+
+
+def fp64_traffic(m, n):
+    """DRAM bytes per FP64 Gram pass from the committed ncu summary of gram.cu, if current."""
     path = os.path.join(ROOT, "profiles", "gram_fused_ncu_summary.md")
     src = os.path.join(ROOT, "paper_2602_16797_gb300", "csrc", "gram.cu")
     try:
@@ -223,50 +305,82 @@ def gram_traffic_per_element():
                 tag = ln.split(": ", 1)[1].strip()
             if ln.startswith("dram bytes per element of A: "):
                 per = float(ln.split(": ", 1)[1].split()[0])
-        return per if tag == h else None
+        return per * m * n if (tag == h and per is not None) else None
     except (OSError, ValueError):
         return None
 
 
-def split_traffic_per_launch(m, n, k):
-    """DRAM bytes per launch of the two split-Gram kernels (A W and A^T (A W)) from the committed ncu
-    summary, scaled to (m, n) by the digit bytes, if that summary was taken on the current
-    gram_tc.cu (else None)."""
-    path = os.path.join(ROOT, "profiles", "gram_split_ncu_summary.md")
-    src = os.path.join(ROOT, "paper_2602_16797_gb300", "csrc", "gram_tc.cu")
-    try:
-        txt = open(path).read()
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        tag, per = None, {}
-        for ln in txt.splitlines():
-            if ln.startswith("gram_tc.cu sha256[:16]: "):
-                tag = ln.split(": ", 1)[1].strip()
-            for key in ("ab", "atb"):
-                pre = f"dram bytes per digit byte ({key}): "
-                if ln.startswith(pre):
-                    per[key] = float(ln.split(": ", 1)[1].split()[0])
-        if tag != h or len(per) != 2:
-            return None
-        alg = split_algorithmic_bytes(m, n, k)
-        return {key: per[key] * alg[key + "_digits"] for key in ("ab", "atb")}
-    except (OSError, ValueError):
-        return None
+def gram_roofline(m, n, b, cplx, split, t_pass_s, peaks, fp64_peak_tf, fp64_peak_src):
+    """Roofline object of the Gram pass (the dominant kernel pair) from its event-timed duration.
+
+    Split path: the pass must move pass_algorithmic_bytes through HBM and run pass_tensor_flops
+    on the tensor cores; the bound is whichever takes longer at its measured peak (HBM copy
+    bandwidth; bf16 tensor throughput sustained, since the pass runs inside a long solve), and
+    the other is reported beside it. FP64 path: 4 m n b (16 m n b complex) flops against the
+    FP64 peak derived from the unit count and clock."""
+    hbm = peaks.get("hbm_gbs") or 6800.0
+    hbm_src = "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks.get("hbm_gbs") else "fallback 6.8 TB/s"
+    tc = peaks.get("bf16_tflops_sustained") or 1700.0
+    tc_src = ("MEASURED_PEAKS.json bf16_tflops_sustained (of measured)" if peaks.get("bf16_tflops_sustained")
+              else "fallback 1.7 PFLOP/s sustained")
+    by = pass_algorithmic_bytes(m, n, b, cplx)
+    hbm_obj = {"bound": "hbm", "achieved": by / t_pass_s / 1e9, "peak": hbm, "unit": "GB/s",
+               "frac": by / t_pass_s / 1e9 / hbm, "traffic": None, "bytes_per_pass": by,
+               "peak_source": hbm_src}
+    if not split:
+        fl = (16.0 if cplx else 4.0) * m * n * b
+        tf = fl / t_pass_s / 1e12
+        hbm_obj["traffic"] = fp64_traffic(m, n)
+        return {"bound": "alu", "achieved": tf, "peak": fp64_peak_tf, "unit": "TFLOP/s", "frac": tf / fp64_peak_tf,
+                "traffic": hbm_obj["traffic"], "flops_per_pass": fl, "peak_source": fp64_peak_src,
+                "kernel": "gram_kernel (fused A W, A^H A W), " + ("complex128" if cplx else "FP64"),
+                "ms_per_pass": t_pass_s * 1e3, "hbm": hbm_obj}
+    fl = pass_tensor_flops(m, n, b)
+    tc_obj = {"bound": "tensor", "achieved": fl / t_pass_s / 1e12, "peak": tc, "unit": "TFLOP/s",
+              "frac": fl / t_pass_s / 1e12 / tc, "traffic": None, "flops_per_pass": fl, "peak_source": tc_src}
+    hbm_obj["traffic"] = pass_traffic(m, n)
+    t_hbm, t_tc = by / (hbm * 1e9), fl / (tc * 1e12)
+    main, other = (tc_obj, hbm_obj) if t_tc > t_hbm else (hbm_obj, tc_obj)
+    out = dict(main)
+    out.update({"kernel": "split-bf16 Gram pass (gram_tc.cu: split of W, A W and A^T (A W) on tcgen05)",
+                "ms_per_pass": t_pass_s * 1e3, "roof_ms": max(t_hbm, t_tc) * 1e3,
+                "other": other})
+    return out
 
 
-def split_algorithmic_bytes(m, n, b):
-    """Bytes each split-Gram kernel must move per launch (layouts of gram_tc.cu): the digits of A
-    (8 one-byte digits per element of the padded matrix, as many bytes as the FP64 value), plus
-    A W (FP64) and the bf16 digits of A W (8 x 8 or 8 x 16 per row) written by the first, read by
-    the second once per 128-column tile."""
-    cd = lambda a, q: -(-a // q)  # noqa: E731
-    R1, NKB, CT = cd(m, 128), cd(n, 16), cd(n, 128)
-    N = 8 * (8 if b <= 8 else 16)
-    tile = 128 * 16 * 8
-    ab_digits = R1 * NKB * tile
-    atb_digits = CT * R1 * 8 * tile
-    y_digits = R1 * 128 * N * 2
-    return {"ab_digits": ab_digits, "atb_digits": atb_digits,
-            "ab": ab_digits + 8 * m * b + y_digits, "atb": atb_digits + CT * y_digits}
+# --------------------------------------------------------------------------------------- our arm
+
+def _opts(rl, w, seed, prec, fixed_iters, gram):
+    o = rl.rlobpcg_default_opts()
+    o.d = w["d"]
+    o.zeta = w["zeta"]
+    o.sketch_prec = prec
+    o.seed = seed
+    o.gram_split = 1 if gram == "split" else 0
+    if "stagnation" in w:
+        o.use_stagnation = w["stagnation"]
+    if "tau" in w:
+        o.tau = w["tau"]
+    if fixed_iters:
+        o.fixed_iters = fixed_iters
+    return o
+
+
+def _timed_solves(rl, torch, plans, Ad, steps, stream, outs):
+    """`steps` solves (matrix i % len, its seed's plan) between CUDA events on the plans' stream."""
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    infos = []
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for i in range(steps):
+        info = rl.rlobpcg_info()
+        rl.rlobpcg_solve(plans[i % len(plans)], Ad[i % len(Ad)].data_ptr(), Ad[i % len(Ad)].shape[1], -1.0,
+                         *outs, info)
+        ev[i + 1].record(stream)
+        infos.append(info)
+    torch.cuda.synchronize()
+    lat = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
+    return ev[0].elapsed_time(ev[-1]), lat, infos
 
 
 def run_ours(args, rank, world, local_rank):
@@ -280,58 +394,58 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     rl.load()
     if "host" in w:
-        hostA = w["host"](M)
+        hostA, truth = w["host"](M)
         Ad = [torch.from_numpy(A).to(dev) for A in hostA]
     else:
-        Ad = w["device"](M, dev)
+        Ad, truth = w["device"](M, dev)
         hostA = None
     dtype = rl.RLOBPCG_C128 if w["cplx"] else rl.RLOBPCG_F64
     tdt = torch.complex128 if w["cplx"] else torch.float64
     esz = 16 if w["cplx"] else 8
     stream = torch.cuda.current_stream(dev)
-    o = rl.rlobpcg_default_opts()
-    o.d = D
-    o.zeta = w["zeta"]
-    o.sketch_prec = w["prec"]
-    o.gram_split = 1 if args.gram == "split" else 0
     split = args.gram == "split" and not w["cplx"] and K <= 16
-    if "stagnation" in w:
-        o.use_stagnation = w["stagnation"]
-    if "tau" in w:
-        o.tau = w["tau"]
-    plan = rl.rlobpcg_plan(M, N, K, dtype, o, stream.cuda_stream)
+    seeds = w["seeds"]
+    # one plan per seed: a plan keeps the options it was made with (the seed of S among them)
+    plans = [rl.rlobpcg_plan(M, N, K, dtype, _opts(rl, w, sd, w["prec"], args.fixed_iters, args.gram),
+                             stream.cuda_stream) for sd in seeds]
     sigma = torch.empty(K, dtype=torch.float64, device=dev)
     resid = torch.empty(K, dtype=torch.float64, device=dev)
     V = torch.empty((N, K), dtype=tdt, device=dev)
-    seeds = w["seeds"]
-
-    def step(i, info, A_ptr=None, out=None):
-        o.seed = seeds[i % len(seeds)]
-        a = A_ptr if A_ptr is not None else Ad[i % len(Ad)].data_ptr()
-        sg, vv, rs = out if out is not None else (sigma.data_ptr(), V.data_ptr(), resid.data_ptr())
-        rl.rlobpcg_solve(plan, a, N, -1.0, sg, vv, None, rs, info)
+    outs = (sigma.data_ptr(), V.data_ptr(), None, resid.data_ptr())
 
     for i in range(args.warmup):
-        step(i, rl.rlobpcg_info())
+        rl.rlobpcg_solve(plans[i % len(plans)], Ad[i % len(Ad)].data_ptr(), N, -1.0, *outs, rl.rlobpcg_info())
     torch.cuda.synchronize()
     replicas.barrier(world)
     clocks = ClockSampler(local_rank)
     clocks.start()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-    infos = []
-    torch.cuda.synchronize()
-    ev[0].record(stream)
-    for i in range(args.steps):
-        info = rl.rlobpcg_info()
-        step(i, info)
-        ev[i + 1].record(stream)
-        infos.append(info)
-    torch.cuda.synchronize()
+    ms_total, lat, infos = _timed_solves(rl, torch, plans, Ad, args.steps, stream, outs)
     clk = clocks.stop()
-    ms_total = ev[0].elapsed_time(ev[-1])
-    lat = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
     replicas.barrier(world)
     ms_total = replicas.max_over_ranks(ms_total, world, device=dev)
+    sig_last = sigma.cpu().numpy().copy()
+    err_truth = float(np.max(np.abs(sig_last - truth[(args.steps - 1) % len(truth)]) /
+                             np.maximum(truth[(args.steps - 1) % len(truth)], 1e-300)))
+
+    # mixed-precision form (FP32 sketch and R) on the same matrices, beside the plain form
+    mixed = None
+    if "mixed_prec" in w and not args.no_mixed:
+        mplans = [rl.rlobpcg_plan(M, N, K, dtype, _opts(rl, w, sd, w["mixed_prec"], args.fixed_iters, args.gram),
+                                  stream.cuda_stream) for sd in seeds]
+        rl.rlobpcg_solve(mplans[0], Ad[0].data_ptr(), N, -1.0, *outs, rl.rlobpcg_info())
+        msteps = max(2, args.steps // 3)
+        mms, _, minfos = _timed_solves(rl, torch, mplans, Ad, msteps, stream, outs)
+        ms_sig = sigma.cpu().numpy().copy()
+        tr = truth[(msteps - 1) % len(truth)]
+        mixed = {"sketch_prec": {1: "fp32", 2: "fp32 + fp64 refinement"}.get(w["mixed_prec"], "?"),
+                 "solves_per_s": msteps / (mms * 1e-3), "ms_per_solve": mms / msteps, "steps": msteps,
+                 "iters": [x.iters for x in minfos],
+                 "per_iteration_ms": statistics.mean(x.ms_iterate / max(x.iters, 1) for x in minfos),
+                 "phase_ms": {"sketch": statistics.mean(x.ms_sketch for x in minfos),
+                              "factor": statistics.mean(x.ms_factor for x in minfos)},
+                 "sigma_rel_err_vs_planted": float(np.max(np.abs(ms_sig - tr) / np.maximum(tr, 1e-300)))}
+        for p in mplans:
+            rl.rlobpcg_plan_destroy(p)
 
     # e2e: host buffers through the same C-ABI call (H2D of A and D2H of the results inside)
     pinned = [torch.from_numpy(A).pin_memory() for A in hostA] if hostA is not None else \
@@ -339,113 +453,107 @@ def run_ours(args, rank, world, local_rank):
     sig_h = torch.empty(K, dtype=torch.float64).pin_memory()
     V_h = torch.empty((N, K), dtype=tdt).pin_memory()
     res_h = torch.empty(K, dtype=torch.float64).pin_memory()
-    hout = (sig_h.data_ptr(), V_h.data_ptr(), res_h.data_ptr())
+    hout = (sig_h.data_ptr(), V_h.data_ptr(), None, res_h.data_ptr())
     e2e_steps = max(2, min(args.steps, 4))
-    info = rl.rlobpcg_info()
-    step(0, info, pinned[0].data_ptr(), hout)  # warm the plan's host-input buffer
+    rl.rlobpcg_solve(plans[0], pinned[0].data_ptr(), N, -1.0, *hout, rl.rlobpcg_info())  # warm the host-A buffer
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for i in range(e2e_steps):
-        step(i, info, pinned[i % len(pinned)].data_ptr(), hout)
+        rl.rlobpcg_solve(plans[i % len(plans)], pinned[i % len(pinned)].data_ptr(), N, -1.0, *hout, rl.rlobpcg_info())
     e2e_s = time.perf_counter() - t0
-    rl.rlobpcg_plan_destroy(plan)
+    for p in plans:
+        rl.rlobpcg_plan_destroy(p)
 
-    # roofline of the fused Gram pass (FP64 ALU bound): algorithmic flops per pass / event time
     gram_ms = sum(x.ms_gram for x in infos)
     passes = sum(x.gram_passes for x in infos)
-    fl_el = 16.0 if w["cplx"] else 4.0
-    flops_pass = fl_el * M * N * K
-    bytes_pass = esz * (M * N + M * K)
-    avg_s = gram_ms / max(passes, 1) * 1e-3
-    achieved_tf = flops_pass / avg_s / 1e12 if passes else None
+    t_pass = gram_ms / max(passes, 1) * 1e-3
     props = torch.cuda.get_device_properties(dev)
-    sm_count = props.multi_processor_count
     max_mhz = clk.get("sm_max_mhz") or 2070.0
-    peak_tf = sm_count * FP64_UNITS_PER_SM_CLK * 2 * max_mhz * 1e6 / 1e12
-    if split:
-        # split-bf16 Gram: two tensor-core kernels per pass that stream the byte digits of A; the
-        # roofline is that of the slower one (bytes it must move per launch / its event-timed
-        # duration) against the measured copy bandwidth
-        alg = split_algorithmic_bytes(M, N, K)
-        t_ab = sum(x.ms_gram_ab for x in infos) / max(passes, 1) * 1e-3
-        t_atb = sum(x.ms_gram_atb for x in infos) / max(passes, 1) * 1e-3
-        key, t_k = ("atb", t_atb) if t_atb >= t_ab else ("ab", t_ab)
-        peaks = measured_peaks()
-        peak_gbs = peaks.get("hbm_gbs") or 6800.0
-        achieved_gbs = alg[key] / t_k / 1e9 if passes else None
-        tr = split_traffic_per_launch(M, N, K)
-        roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": peak_gbs, "unit": "GB/s",
-                    "frac": (achieved_gbs / peak_gbs) if achieved_gbs else None,
-                    "traffic": tr[key] if tr else None,
-                    "kernel": ("split_pass_kernel<8,1> (A^T (A W), byte digits expanded to bf16 in TMEM, tcgen05)"
-                               if key == "atb" else
-                               "split_pass_kernel<8,0> (A W, byte digits expanded to bf16 in TMEM, tcgen05)"),
-                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks.get("hbm_gbs") else
-                                   "fallback 6.8 TB/s",
-                    "bytes_per_launch": alg[key], "ms_per_launch": t_k * 1e3,
-                    "other_kernel_ms": (t_ab if key == "atb" else t_atb) * 1e3,
-                    "gram_pass_fp64_equiv_tflops": achieved_tf, "passes_timed": passes}
-    else:
-        per_elem = gram_traffic_per_element() if args.workload == DEFAULT_WORKLOAD else None
-        roofline = {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
-                    "frac": (achieved_tf / peak_tf) if achieved_tf else None,
-                    "traffic": (per_elem * M * N) if per_elem is not None else None,
-                    "kernel": "gram_kernel (fused A W, A^H A W), " + ("complex128" if w["cplx"] else "FP64"),
-                    "peak_source": f"derived: {sm_count} SMs x {FP64_UNITS_PER_SM_CLK} DFMA/clk x 2 flop x {max_mhz:.0f} MHz",
-                    "achieved_gbs": bytes_pass / avg_s / 1e9 if passes else None,
-                    "passes_timed": passes}
+    fp64_peak = props.multi_processor_count * FP64_UNITS_PER_SM_CLK * 2 * max_mhz * 1e6 / 1e12
+    roofline = gram_roofline(M, N, K, w["cplx"], split, t_pass, measured_peaks(), fp64_peak,
+                             f"derived: {props.multi_processor_count} SMs x {FP64_UNITS_PER_SM_CLK} DFMA/clk x 2 flop x "
+                             f"{max_mhz:.0f} MHz")
+    roofline["passes_timed"] = passes
 
     out = None
     if rank == 0:
         ms_per = ms_total / args.steps
         value = replicas.job_rate(args.steps, world, ms_total * 1e-3)
+        iters = [x.iters for x in infos]
         result = {
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "c128" if w["cplx"] else "f64",
             "data": "synthetic (seeded; the paper's matrix families)",
             "config": {"workload": w["desc"], "m": M, "n": N, "k": K, "d": D, "zeta": w["zeta"],
-                       "sketch": "fp32" if w["prec"] else "fp64", "matrices": w["matrices"],
+                       "sketch": "fp32" if w["prec"] == 1 else "fp64", "matrices": w["matrices"],
                        "gram": "split-bf16 tensor cores" if split else ("fp64 CUDA cores" if not w["cplx"]
                                                                          else "complex128 CUDA cores"),
+                       "fixed_iters": args.fixed_iters or None,
                        "l2": "input larger than L2; no flush" if M * N * esz > 129e6 else
                              "input smaller than L2 (each step is a full solve)",
                        "parallelism": f"replicas x{world}"},
+            "per_iteration_ms": statistics.mean(x.ms_iterate / max(x.iters, 1) for x in infos),
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
-            "iters": [x.iters for x in infos], "stop_reasons": [x.stop_reason for x in infos],
+            "iters": iters, "stop_reasons": [x.stop_reason for x in infos],
+            "sigma_rel_err_vs_planted": err_truth,
             "rr_sweeps_per_svd": round(sum(x.rr_sweeps for x in infos) / max(1, sum(x.rr_calls for x in infos)), 2),
             "phase_ms": {"sketch": statistics.mean(x.ms_sketch for x in infos),
                          "factor": statistics.mean(x.ms_factor for x in infos),
                          "iterate": statistics.mean(x.ms_iterate for x in infos),
-                         "gram_per_pass": avg_s * 1e3,
-                         "per_iteration": statistics.mean(x.ms_iterate / max(x.iters, 1) for x in infos),
+                         "gram_per_pass": t_pass * 1e3,
+                         "gram_ab_per_pass": sum(x.ms_gram_ab for x in infos) / max(passes, 1),
+                         "gram_atb_per_pass": sum(x.ms_gram_atb for x in infos) / max(passes, 1),
                          "split_a": statistics.mean(x.ms_split_a for x in infos)},
-            "sigma": [float(x) for x in sigma.cpu().numpy()],
+            "sigma": [float(x) for x in sig_last],
             "roofline": roofline, "clocks": clk,
             "gpu_launches": int(sum(x.kernel_launches for x in infos)),
             "e2e": {"value": e2e_steps / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": esz * M * N,
                     "d2h_bytes_per_step": 8 * K + esz * N * K + 8 * K},
         }
+        if mixed is not None:
+            result["mixed"] = mixed
         if world == 1 and not args.no_cpu_baseline:
-            v, times = oracle_solves_per_s(w, 3)
-            result["cpu_baseline"] = {"value": v, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
-                                      "sample": f"3 oracle solves of the same matrix families at m={int(M * SAMPLE_FRAC)} "
-                                                f"rows ({sum(times):.1f} s), scaled by {SAMPLE_FRAC} (work is linear "
-                                                f"in m); numpy/LAPACK with all host cores"}
-            one = oracle_rate_one_thread(args.workload)
+            t0 = time.perf_counter()
+            ph = oracle_sample_phases(w, run_to_stop=True)
+            secs = time.perf_counter() - t0
+            gi = statistics.mean(iters)
+            est = oracle_full_solve_seconds(w, ph, gi)
+            result["cpu_baseline"] = {
+                "value": 1.0 / est, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
+                "sample": (f"oracle (numpy/LAPACK, all host cores) on a {ph['sample_m']}-row sample of the same matrix "
+                           f"family ({secs:.1f} s): one run to its own stop ({ph['stop_iters']} iterations) and one "
+                           f"with 1 iteration give {ph['t_iter']:.3f} s per iteration and {ph['t_once_stream']:.2f} s "
+                           f"of one-time work that streams A (both x {M / ph['sample_m']:g} for m = {M}), plus the "
+                           f"SVD of the d x n sketch ({ph['t_svd']:.2f} s, size-independent), at the GPU's "
+                           f"{gi:g} iterations"),
+                "oracle_iters_on_sample": ph["stop_iters"], "gpu_iters": gi,
+                "per_iteration_s_full_size": ph["t_iter"] * M / ph["sample_m"]}
+            one = oracle_rate_one_thread(args.workload, int(round(gi)))
             if one is not None:
                 result["cpu_baseline"]["value_1_thread"] = one[0]
-                result["cpu_baseline"]["sample"] += f"; value_1_thread: one such solve with one thread ({one[1]:.1f} s)"
+                result["cpu_baseline"]["sample"] += (f"; value_1_thread: the same estimate from a 1- and 3-iteration "
+                                                     f"sample with every BLAS pool at one thread ({one[1]:.1f} s)")
         out = result
     return out
 
 
 def run_reference(args, rank, world):
+    """The CPU oracle, as it stands, on the host cores: each step times it per phase on a row sample
+    of the workload and scales it to the full size at the iteration count the oracle's own
+    stopping rule reaches on that sample (measured once, before the timed steps)."""
     if rank != 0:
         return None
     w = WORKLOADS[args.workload]
-    v, times = oracle_solves_per_s(w, args.steps, warmup=args.warmup)
-    total = sum(times)
+    ph0 = oracle_sample_phases(w, run_to_stop=True)
+    iters = ph0["stop_iters"]
+    per = []
+    for i in range(args.warmup + args.steps):
+        ph = ph0 if i == 0 else oracle_sample_phases(w, run_to_stop=False)
+        if i >= args.warmup:
+            per.append(oracle_full_solve_seconds(w, ph, iters))
+    total = sum(per)
+    v = args.steps / total
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -453,8 +561,9 @@ def run_reference(args, rank, world):
             "config": {"workload": w["desc"], "m": w["m"], "n": w["n"], "k": w["k"], "d": w["d"], "zeta": w["zeta"],
                        "parallelism": "cpu oracle, rank 0 only"},
             "cpu_baseline": {"value": v, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
-                             "sample": f"each step one oracle solve at m={int(w['m'] * SAMPLE_FRAC)} rows, "
-                                       f"scaled by {SAMPLE_FRAC}"},
+                             "sample": f"each step: the oracle on a {ph0['sample_m']}-row sample of the same matrix "
+                                       f"family, 1 and 3 fixed iterations, scaled to m = {w['m']} (the parts that stream "
+                                       f"A) at the {iters} iterations its stopping rule takes on the sample"},
             "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -544,7 +653,10 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["serve_stream"], default=DEFAULT_WORKLOAD)
     ap.add_argument("--gram", choices=["split", "fp64"], default="split",
                     help="Gram products: split-bf16 on the tensor cores (default) or FP64 CUDA cores")
-    ap.add_argument("--requests", type=int, default=48, help="serve_stream: number of requests")
+    ap.add_argument("--fixed-iters", type=int, default=0,
+                    help="run exactly this many LOBPCG iterations per solve (no stop test)")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision form beside the plain one")
+    ap.add_argument("--requests", type=int, default=2000, help="serve_stream: number of requests")
     ap.add_argument("--slots", type=int, default=8, help="serve_stream: concurrent solves")
     args = ap.parse_args()
     rank, world, local_rank = replicas.world_from_env()

@@ -1,9 +1,11 @@
-"""Host-side helpers of bench.py that feed the roofline object (no GPU needed).
+"""Host-side helpers of bench.py that feed the roofline and CPU-baseline objects (no GPU needed).
 
-The split Gram kernels must move the byte digits of A (one byte per digit, eight digits per
-element of the row- and column-padded matrix) plus A W and its bf16 digits; the DRAM traffic
-reported beside it is scaled from the committed ncu summary only when that summary was taken on
-the current kernel source.
+The Gram pass must move A once and write A W once (its algorithmic bytes); the split-bf16 form
+also runs a fixed number of digit-pair products on the tensor cores. The roofline takes the
+slower of the two roofs as the bound and reports the other beside it. DRAM traffic is scaled
+from the committed ncu summary only when that summary was taken on the current kernel source.
+The CPU baseline scales a row sample of the oracle: the parts that stream A by m / sample_m, the
+SVD of the d x n sketch not at all.
 """
 import hashlib
 import os
@@ -16,19 +18,36 @@ sys.path.insert(0, ROOT)
 import bench  # noqa: E402
 
 
-@pytest.mark.parametrize("m,n,b", [(100000, 500, 5), (1, 1, 1), (129, 17, 9), (1000000, 1000, 10)])
-def test_split_algorithmic_bytes_count_the_padded_byte_digits(m, n, b):
-    a = bench.split_algorithmic_bytes(m, n, b)
-    mp, npad16, npad128 = -(-m // 128) * 128, -(-n // 16) * 16, -(-n // 128) * 128
-    assert a["ab_digits"] == 8 * mp * npad16            # row tiles x 16-column blocks
-    assert a["atb_digits"] == 8 * mp * npad128          # column tiles x row chunks
-    N = 8 * (8 if b <= 8 else 16)
-    y = mp * N * 2                                       # bf16 digits of A W per padded row
-    assert a["ab"] == a["ab_digits"] + 8 * m * b + y
-    assert a["atb"] == a["atb_digits"] + (npad128 // 128) * y
+@pytest.mark.parametrize("m,n,b,cplx", [(100000, 500, 5, False), (1, 1, 1, False), (200000, 300, 3, True),
+                                         (1000000, 1000, 10, False)])
+def test_pass_algorithmic_bytes_are_one_read_of_A_and_one_write_of_AW(m, n, b, cplx):
+    esz = 16 if cplx else 8
+    assert bench.pass_algorithmic_bytes(m, n, b, cplx) == esz * m * n + esz * m * b
 
 
-def _fake_tree(tmp_path, src_text, summary_sha, ab=1.04, atb=1.02):
+def test_pass_tensor_flops_count_both_products_over_all_digit_pairs():
+    m, n, b = 1000000, 1000, 10
+    assert bench.pass_tensor_flops(m, n, b) == 2 * bench.DIGIT_PAIRS * 2 * m * n * b
+
+
+def test_roofline_takes_the_slower_roof_as_the_bound():
+    peaks = {"hbm_gbs": 6779.0, "bf16_tflops_sustained": 1710.4}
+    m, n = 1000000, 1000
+    # b = 10: tensor work 2.56e12 flop (1.50 ms) against 8.08 GB (1.19 ms): tensor-bound
+    r = bench.gram_roofline(m, n, 10, False, True, 3.0e-3, peaks, 1.26, "derived")
+    assert r["bound"] == "tensor" and r["other"]["bound"] == "hbm"
+    assert r["frac"] == pytest.approx(bench.pass_tensor_flops(m, n, 10) / 3.0e-3 / 1e12 / 1710.4)
+    assert r["other"]["frac"] == pytest.approx(bench.pass_algorithmic_bytes(m, n, 10, False) / 3.0e-3 / 1e9 / 6779.0)
+    # b = 1: 0.26e12 flop (0.15 ms) against 8.01 GB (1.18 ms): HBM-bound
+    r = bench.gram_roofline(m, n, 1, False, True, 2.0e-3, peaks, 1.26, "derived")
+    assert r["bound"] == "hbm" and r["other"]["bound"] == "tensor"
+    assert r["roof_ms"] == pytest.approx(bench.pass_algorithmic_bytes(m, n, 1, False) / 6779.0e9 * 1e3)
+    # FP64 path: FP64 flops against the derived FP64 peak
+    r = bench.gram_roofline(200000, 300, 3, True, False, 3.0e-3, peaks, 1.259, "derived")
+    assert r["bound"] == "alu" and r["frac"] == pytest.approx(16 * 200000 * 300 * 3 / 3.0e-3 / 1e12 / 1.259)
+
+
+def _fake_tree(tmp_path, src_text, summary_sha, per=8.2):
     (tmp_path / "profiles").mkdir()
     csrc = tmp_path / "paper_2602_16797_gb300" / "csrc"
     csrc.mkdir(parents=True)
@@ -36,8 +55,7 @@ def _fake_tree(tmp_path, src_text, summary_sha, ab=1.04, atb=1.02):
     (tmp_path / "profiles" / "gram_split_ncu_summary.md").write_text(
         "# summary\n\n"
         f"gram_tc.cu sha256[:16]: {summary_sha}\n"
-        f"dram bytes per digit byte (ab): {ab}\n"
-        f"dram bytes per digit byte (atb): {atb}\n")
+        f"dram bytes per element of A per pass: {per}\n")
 
 
 def test_traffic_scales_the_summary_when_it_matches_the_source(tmp_path, monkeypatch):
@@ -45,18 +63,22 @@ def test_traffic_scales_the_summary_when_it_matches_the_source(tmp_path, monkeyp
     sha = hashlib.sha256(src.encode()).hexdigest()[:16]
     _fake_tree(tmp_path, src, sha)
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    tr = bench.split_traffic_per_launch(100000, 500, 5)
-    alg = bench.split_algorithmic_bytes(100000, 500, 5)
-    assert tr == pytest.approx({"ab": 1.04 * alg["ab_digits"], "atb": 1.02 * alg["atb_digits"]})
+    assert bench.pass_traffic(100000, 500) == pytest.approx(8.2 * 100000 * 500)
 
 
 def test_traffic_is_null_once_the_kernel_changed(tmp_path, monkeypatch):
     _fake_tree(tmp_path, "// kernel source, edited\n", "0123456789abcdef")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    assert bench.split_traffic_per_launch(100000, 500, 5) is None
+    assert bench.pass_traffic(100000, 500) is None
+
+
+def test_full_size_estimate_scales_only_what_streams_A():
+    w = {"m": 1000000}
+    ph = {"sample_m": 100000, "t_svd": 2.0, "t_once_stream": 0.5, "t_iter": 0.1}
+    assert bench.oracle_full_solve_seconds(w, ph, 40) == pytest.approx(0.5 * 10 + 2.0 + 40 * 0.1 * 10)
 
 
 def test_single_thread_oracle_sample_runs_in_a_fresh_interpreter():
-    one = bench.oracle_rate_one_thread("small_4000x50", timeout=240)
+    one = bench.oracle_rate_one_thread("small_4000x50", 5, timeout=240)
     assert one is not None and one[0] > 0 and one[1] > 0
-    assert bench.oracle_rate_one_thread("no_such_workload", timeout=120) is None
+    assert bench.oracle_rate_one_thread("no_such_workload", 5, timeout=120) is None

@@ -1,7 +1,8 @@
 """Full-size configurations, in the launch configuration bench.py times.
 
 - complex128 2e5 x 300, k = 3: parity with the oracle at full size.
-- 1e6 x 1000 (8 GB) Gram pass: the oracle's products A W (sampled rows) and A^H (A W) (all of it).
+- 1e6 x 1000 (8 GB) Gram pass, FP64 and split-bf16 tensor-core forms, b = 10 (the block the
+  1e6 x 1000, k = 10 solve uses): the oracle's products A W and A^H (A W), elementwise.
 - 1e6 x 1000, k = 10 solves, FP64 sketch and FP32 sketch/R: the oracle is too slow at this size,
   so the results are checked against what holds at any size: the planted singular values and
   subspace (within the backward-stable floors of Sec. 4), ||A v_j|| = sigma_j and V^H V = I.
@@ -73,6 +74,37 @@ def test_large_gram_pass_against_oracle_products(large):
     absA = np.abs(Ah)
     b2 = absA.T @ ((n + 2) * U * (absA @ np.abs(W))) + (m + 2) * U * (absA.T @ np.abs(AWfull))
     assert np.all(np.abs(G_h - G0) <= b2)
+
+
+def test_large_split_gram_pass_against_oracle_products(large):
+    """The tensor-core Gram pass at the full 1e6 x 1000 size with b = 10, in the launch
+    configuration a solve of that matrix uses, against the oracle's products elementwise under
+    the split's error bound (tests/test_gpu_split_gram.py)."""
+    from tests.test_gpu_split_gram import bounds
+    A, s, V = large
+    m, n = A.shape
+    b = 10
+    rng = np.random.default_rng(12)
+    W = np.linalg.qr(rng.standard_normal((n, b)))[0]
+    Wd = torch.from_numpy(W).cuda()
+    st = torch.cuda.current_stream().cuda_stream
+    ps = rl.rlobpcg_gram_split_prepare_size(m, n)
+    ws = rl.rlobpcg_gram_split_workspace_size(m, n, b)
+    prep = torch.empty(ps, dtype=torch.uint8, device="cuda")
+    work = torch.empty(ws, dtype=torch.uint8, device="cuda")
+    AW = torch.full((m, b), np.nan, dtype=torch.float64, device="cuda")
+    G = torch.full((n, b), np.nan, dtype=torch.float64, device="cuda")
+    rl.rlobpcg_gram_split_prepare(A.data_ptr(), m, n, n, prep.data_ptr(), ps, st)
+    rl.rlobpcg_gram_split(prep.data_ptr(), m, n, Wd.data_ptr(), b, b, AW.data_ptr(), b, G.data_ptr(), b,
+                          work.data_ptr(), ws, st)
+    torch.cuda.synchronize()
+    del prep, work
+    Ah = A.cpu().numpy()
+    AW_h, G_h = AW.cpu().numpy(), G.cpu().numpy()
+    AW0, G0 = oracle.gram_pass(Ah, W)
+    tAW, tG = bounds(Ah, W, AW0)
+    assert np.all(np.abs(AW_h - AW0) <= tAW)
+    assert np.all(np.abs(G_h - G0) <= tG)
 
 
 @pytest.mark.parametrize("prec", [0, 1])
