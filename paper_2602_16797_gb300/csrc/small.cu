@@ -439,6 +439,192 @@ __device__ int jacobi_mixed16(double* X, double* V, int c, int N, double tol, do
   return sweeps;
 }
 
+// ---- real c in (16, 32]: the same preconditioned scheme with one pair per warp -------------
+// Round-robin schedule for N <= 32 slots: pair i of round r is coded pp | qq << 8 (pp < qq), or
+// 0xFFFF when a member is the padding column c (odd c).
+__device__ void rr_schedule32(uint16_t* sched, int c, int N) {
+  for (int e = threadIdx.x; e < (N - 1) * 16; e += blockDim.x) {
+    const int r = e / 16, i = e % 16;
+    uint16_t code = 0xFFFF;
+    if (i < N / 2) {
+      int pp = rr_slot(i, r, N), qq = rr_slot(N - 1 - i, r, N);
+      if (pp > qq) { const int t = pp; pp = qq; qq = t; }
+      if (qq < c) code = (uint16_t)(pp | (qq << 8));
+    }
+    sched[e] = code;
+  }
+}
+
+// FP32 sweeps for c <= 32: a warp per pair, lane = row, the three sums by a 5-level butterfly
+// (FP32 work runs on the fast pipe). Same rotation rule as jacobi_pairs16_f32.
+__device__ int jacobi_sweeps32_f32(float* X, float* V, int c, int N, float tol, float tiny2, const uint16_t* sched) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
+  const float tol2 = tol * tol;
+  int sweep = 0;
+  for (; sweep < 15; ++sweep) {
+    int rotated = 0;
+    for (int r = 0; r < N - 1; ++r) {
+      for (int pi = warp; pi < N / 2; pi += nw) {   // warp-uniform
+        const int code = sched[r * 16 + pi];
+        const bool valid = code != 0xFFFF;
+        const int pp = code & 0xFF, qq = code >> 8;
+        const bool live = valid && lane < c;
+        const float xp = live ? X[pp * c + lane] : 0.f, xq = live ? X[qq * c + lane] : 0.f;
+        float a = xp * xp, bb = xq * xq, g = xp * xq;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          a += __shfl_xor_sync(0xffffffffu, a, o);
+          bb += __shfl_xor_sync(0xffffffffu, bb, o);
+          g += __shfl_xor_sync(0xffffffffu, g, o);
+        }
+        const float d = bb - a, ga = fabsf(g);
+        const float tf = copysignf(2.0f * ga, d) / (fabsf(d) + sqrtf(d * d + 4.0f * ga * ga));
+        const bool rot = valid && (g * g > tol2 * a * bb) && a > tiny2 && bb > tiny2 && fabsf(tf) > 1.0e-12f;
+        const float t = rot ? tf : 0.0f;
+        const float cs = rsqrtf(fmaf(t, t, 1.0f));
+        const float sn = cs * t;
+        const float se = g < 0.0f ? -sn : sn;
+        if (live && rot) {
+          const float vp = V[pp * c + lane], vq = V[qq * c + lane];
+          X[pp * c + lane] = cs * xp - se * xq;
+          X[qq * c + lane] = se * xp + cs * xq;
+          V[pp * c + lane] = cs * vp - se * vq;
+          V[qq * c + lane] = se * vp + cs * vq;
+        }
+        rotated |= rot;
+      }
+      __syncthreads();
+    }
+    if (!__syncthreads_or(rotated)) { ++sweep; break; }
+  }
+  return sweep;
+}
+
+// FP64 sweeps for c <= 32, in three phases per round so that few FP64 warp instructions are
+// issued (each costs an SM sub-partition ~64 cycles however many lanes are active):
+//   1. the 3 sums of each of the <= 16 pairs, 8 lanes per sum (4 rows each, 3 butterfly levels);
+//   2. the rotations, one lane of warp 0 per pair (same rule as jacobi_pairs16);
+//   3. a warp per pair applies its rotation to X and V, lane = row.
+// Needs blockDim.x >= 384. dots: 48 doubles, rot: 32 doubles, rflag: 16 ints (shared).
+__device__ int jacobi_sweeps32_f64(double* X, double* V, int c, int N, double tol, double tiny2,
+                                   const uint16_t* sched, int max_sweeps, double* dots, double* rotp, int* rflag) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
+  const double tol2 = tol * tol;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    int rotated = 0;
+    for (int r = 0; r < N - 1; ++r) {
+      const uint16_t* sr = sched + r * 16;
+      if (tid < 384) {
+        const int t = tid >> 3, sub = tid & 7, pi = t / 3, kind = t % 3;
+        const int code = pi < N / 2 ? sr[pi] : 0xFFFF;
+        double sum = 0.0;
+        if (code != 0xFFFF) {
+          const int pp = code & 0xFF, qq = code >> 8;
+          const double* u = X + (kind == 1 ? qq : pp) * c;
+          const double* v = X + (kind == 0 ? pp : qq) * c;
+          for (int row = sub; row < c; row += 8) sum = fma(u[row], v[row], sum);
+        }
+        sum += __shfl_xor_sync(0xffffffffu, sum, 4);
+        sum += __shfl_xor_sync(0xffffffffu, sum, 2);
+        sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+        if (sub == 0) dots[t] = sum;
+      }
+      __syncthreads();
+      if (tid < 16) {
+        const int pi = tid;
+        const int code = pi < N / 2 ? sr[pi] : 0xFFFF;
+        const double a = dots[3 * pi], bb = dots[3 * pi + 1], g = dots[3 * pi + 2];
+        bool rot = code != 0xFFFF && (g * g > tol2 * a * bb) && a > tiny2 && bb > tiny2;
+        double cs = 1.0, se = 0.0;
+        if (rot) {
+          const double mx = fmax(a, bb);
+          const int ex = (int)((__double_as_longlong(mx) >> 52) & 0x7ff) - 1023;
+          const double sc = __longlong_as_double((long long)(1023 - imax(-1022, imin(1022, ex))) << 52);
+          const float df = (float)((bb - a) * sc), gf = fabsf((float)(g * sc));
+          const float tf = copysignf(2.0f * gf, df) / (fabsf(df) + sqrtf(df * df + 4.0f * gf * gf));
+          rot = fabsf(tf) > 2.220446049250313e-16f;
+          const double t = rot ? (double)tf : 0.0;
+          cs = rsqrt(fma(t, t, 1.0));
+          const double sn = cs * t;
+          se = g < 0.0 ? -sn : sn;
+        }
+        rotp[2 * pi] = cs;
+        rotp[2 * pi + 1] = se;
+        rflag[pi] = rot;
+        rotated |= rot;
+      }
+      __syncthreads();
+      for (int pi = warp; pi < N / 2; pi += nw) {   // warp-uniform
+        if (!rflag[pi] || lane >= c) continue;
+        const int code = sr[pi];
+        const int pp = code & 0xFF, qq = code >> 8;
+        const double cs = rotp[2 * pi], se = rotp[2 * pi + 1];
+        const double xp = X[pp * c + lane], xq = X[qq * c + lane];
+        const double vp = V[pp * c + lane], vq = V[qq * c + lane];
+        X[pp * c + lane] = cs * xp - se * xq;
+        X[qq * c + lane] = se * xp + cs * xq;
+        V[pp * c + lane] = cs * vp - se * vq;
+        V[qq * c + lane] = se * vp + cs * vq;
+      }
+      __syncthreads();
+    }
+    if (!__syncthreads_or(rotated)) { ++sweep; break; }
+  }
+  return sweep;
+}
+
+// Preconditioned one-sided Jacobi for real 16 < c <= 32, as jacobi_mixed16: FP32 sweeps on a
+// power-of-two scaled copy, V made orthonormal in FP64 by two Newton-Schulz steps, X <- X V, and
+// FP64 sweeps from there to the n eps test (confirmed by one pass over all pairs).
+__device__ int jacobi_mixed32(double* X, double* V, int c, int N, double tol, double tiny2, double mx0, float* Xf,
+                              float* Vf, double* Ms, double* Ws, uint16_t* sched, double* dots, double* rotp,
+                              int* rflag) {
+  const int tid = threadIdx.x, NT = blockDim.x;
+  const int ex = (int)((__double_as_longlong(fmax(mx0, 1e-300)) >> 52) & 0x7ff) - 1023;
+  const double sc = __longlong_as_double((long long)(1023 - imax(-1022, imin(1022, ex))) << 52);
+  for (int i = tid; i < c * c; i += NT) {
+    Xf[i] = (float)(X[i] * sc);
+    Vf[i] = (i / c == i % c) ? 1.0f : 0.0f;
+  }
+  rr_schedule32(sched, c, N);
+  __syncthreads();
+  const float tol32 = (float)imax(c, 4) * 1.1920929e-7f;
+  const float tiny32 = (float)(tiny2 * sc * sc);
+  jacobi_sweeps32_f32(Xf, Vf, c, N, tol32, tiny32, sched);
+  for (int i = tid; i < c * c; i += NT) V[i] = (double)Vf[i];
+  __syncthreads();
+  for (int step = 0; step < 2; ++step) {
+    for (int o = tid; o < c * c; o += NT) {
+      const int i = o / c, j = o % c;
+      double s0 = 0, s1 = 0;
+      int k = 0;
+      for (; k + 1 < c; k += 2) {
+        s0 = fma(V[i * c + k], V[j * c + k], s0);
+        s1 = fma(V[i * c + k + 1], V[j * c + k + 1], s1);
+      }
+      if (k < c) s0 = fma(V[i * c + k], V[j * c + k], s0);
+      Ms[o] = (i == j ? 1.5 : 0.0) - 0.5 * (s0 + s1);
+    }
+    __syncthreads();
+    small_matmul(V, Ms, Ws, c);
+    __syncthreads();
+    for (int i = tid; i < c * c; i += NT) V[i] = Ws[i];
+    __syncthreads();
+  }
+  small_matmul(X, V, Ws, c);
+  __syncthreads();
+  for (int i = tid; i < c * c; i += NT) X[i] = Ws[i];
+  __syncthreads();
+  int sweeps = 0;
+  for (int round = 0; round < 30; ++round) {
+    const int s2 = jacobi_sweeps32_f64(X, V, c, N, tol, tiny2, sched, 2, dots, rotp, rflag);
+    sweeps += s2;
+    if (s2 < 2 || !jacobi_pending(X, c, tol, tiny2)) break;
+  }
+  return sweeps;
+}
+
 template <class T>
 __global__ void __launch_bounds__(1024) rr_small_kernel(const T* __restrict__ Rt, int c, int b, double* theta_out,
                                                          T* K_out, int* info) {
@@ -478,10 +664,17 @@ __global__ void __launch_bounds__(1024) rr_small_kernel(const T* __restrict__ Rt
   int sweep = 0;
   bool fast = false;
   if constexpr (std::is_same<T, double>::value) {
-    if (c <= 16) {
-      __shared__ float Xf[256], Vf[256];
-      __shared__ double Ms[256], Ws2[256];
-      sweep = jacobi_mixed16(X, V, c, N, tol, tiny2, mx0, Xf, Vf, Ms, Ws2);
+    if (c <= 32) {
+      __shared__ float Xf[1024], Vf[1024];
+      __shared__ double Ms[1024], Ws2[1024];
+      if (c <= 16) {
+        sweep = jacobi_mixed16(X, V, c, N, tol, tiny2, mx0, Xf, Vf, Ms, Ws2);
+      } else {
+        __shared__ uint16_t sched32[31 * 16];
+        __shared__ double dots[48], rotp[32];
+        __shared__ int rflag[16];
+        sweep = jacobi_mixed32(X, V, c, N, tol, tiny2, mx0, Xf, Vf, Ms, Ws2, sched32, dots, rotp, rflag);
+      }
       fast = true;
     }
   }
@@ -1395,6 +1588,7 @@ int rr_small_launch(const T* Rt, int c, int b, double* theta, T* K, size_t k_cap
   RL_TRY(allow_dynamic_smem(rr_small_kernel<T>, smem));
   int threads = min(1024, max(64, ((c + 1) / 2) * 32));
   if (std::is_same<T, double>::value && c <= 16) threads = 128;   // two Jacobi pairs per warp
+  else if (std::is_same<T, double>::value && c <= 32) threads = 512;   // a warp per pair, 16 pairs
   rr_small_kernel<T><<<1, threads, smem, st>>>(Rt, c, b, theta, K, info);
   RL_CHECK_LAUNCH();
   return RLOBPCG_OK;
