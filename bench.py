@@ -90,8 +90,8 @@ def _host_complex_sample(m):
 WORKLOADS = {
     "large_1e6x1000": dict(
         desc="planted m=1e6 n=1000 k=10 d=4n zeta=8 fp64", m=1_000_000, n=1000, k=10, d=4000,
-        zeta=8, cplx=False, prec=0, device=_device_large, seeds=(1004,), mixed_prec=1,
-        host_sample=_host_large_sample, sample_m=100_000,
+        zeta=8, cplx=False, prec=0, device=_device_large, seeds=(1004,), mixed_prec=2,
+        host_sample=_host_large_sample, sample_m=100_000, ref_sample_m=20_000,
         matrices="planted sigma_1..990 logspace(0,-4), sigma_991..1000 logspace(-9,-10), Haar U, V"),
     "nullspace_1e5x500": dict(
         desc="nullspace+planted m=1e5 n=500 k=5 d=3n zeta=8 fp64", m=100_000, n=500, k=5, d=1500, zeta=8,
@@ -103,7 +103,7 @@ WORKLOADS = {
         matrices="planted sigma_1..49 logspace(0,-6), sigma_50=1e-10"),
     "complex_2e5x300": dict(
         desc="complex planted m=2e5 n=300 k=3 d=4n zeta=8 fp64 sketch", m=200_000, n=300, k=3, d=1200, zeta=8,
-        cplx=True, prec=0, host=_host_complex, seeds=(1003,), mixed_prec=1, sample_m=40_000,
+        cplx=True, prec=0, host=_host_complex, seeds=(1003,), mixed_prec=2, sample_m=40_000,
         host_sample=_host_complex_sample,
         matrices="complex planted sigma logspace(0,-8), three smallest 1e-12, 3e-13, 1e-13"),
     "complex_2e5x300_f32sketch": dict(
@@ -178,17 +178,28 @@ def _oracle_kwargs(w):
     return kw
 
 
-def oracle_sample_phases(w, run_to_stop=True):
+_SAMPLE_CACHE = {}
+
+
+def _sample_matrix(w, ms):
+    """The row sample (ms rows of the workload's matrix family), built once per process."""
+    key = (w["desc"], ms)
+    if key not in _SAMPLE_CACHE:
+        build = w.get("host_sample") or w["host"]
+        As, _ = build(ms)
+        _SAMPLE_CACHE[key] = As[0]
+    return _SAMPLE_CACHE[key]
+
+
+def oracle_sample_phases(w, run_to_stop=True, sample_m=None):
     """Time the CPU oracle, as it stands, on a row sample of the workload (m -> sample_m rows of the
     same matrix family and spectrum). Returns the seconds of its one-time part (sketch, SVD of the
     sketch, start block) split into the part that streams A (scales with m) and the SVD of the
     d x n sketch (does not), the seconds per LOBPCG iteration (every iteration streams A: scales
     with m), and the iteration count at which the oracle's own stopping rule fires on the sample."""
     import oracle
-    ms = min(w["sample_m"], w["m"])
-    build = w.get("host_sample") or w["host"]
-    As, _ = build(ms)
-    A = As[0]
+    ms = min(sample_m or w["sample_m"], w["m"])
+    A = _sample_matrix(w, ms)
     seed = w["seeds"][0]
     kw = _oracle_kwargs(w)
     t0 = time.perf_counter()
@@ -545,11 +556,12 @@ def run_reference(args, rank, world):
     if rank != 0:
         return None
     w = WORKLOADS[args.workload]
-    ph0 = oracle_sample_phases(w, run_to_stop=True)
+    ms = w.get("ref_sample_m", w["sample_m"])
+    ph0 = oracle_sample_phases(w, run_to_stop=True, sample_m=ms)
     iters = ph0["stop_iters"]
     per = []
     for i in range(args.warmup + args.steps):
-        ph = ph0 if i == 0 else oracle_sample_phases(w, run_to_stop=False)
+        ph = oracle_sample_phases(w, run_to_stop=False, sample_m=ms)
         if i >= args.warmup:
             per.append(oracle_full_solve_seconds(w, ph, iters))
     total = sum(per)

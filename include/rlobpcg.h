@@ -45,9 +45,19 @@ extern "C" {
 #define RLOBPCG_C128 1  /* complex double, interleaved (re, im)       */
 
 /* Precision of the sketch SA, its QR factor R, the SVD of R and R^{-1}. The Gram products,
- * residuals, Rayleigh-Ritz and orthogonalisation are always FP64 / complex128. */
+ * residuals, Rayleigh-Ritz and orthogonalisation are always FP64 / complex128.
+ *   F64:        SA, its QR and R in FP64 (the paper's form).
+ *   F32:        SA summed in FP32 and its QR in FP32. Enough when kappa(A) << 1/u_32 ~ 1.7e7; above
+ *               that the FP32 factor cannot see the bottom singular directions (Fact 2 of Sec. 3.1
+ *               then gives kappa(A P) ~ u_32 kappa(A)) and LOBPCG needs more iterations.
+ *   F32_REFINE: SA in FP64, its QR in FP32 (R_32), then one FP64 Cholesky-QR correction on SA:
+ *               Y = SA R_32^{-1}, R_c = chol(Y^H Y + s I) with s = n u max_i (Y^H Y)_ii,
+ *               R = R_c R_32. R, R^{-1} and the SVD of R are FP64 and as good a preconditioner as
+ *               the F64 form's (kappa(Y) ~ u_32 kappa(SA) stays far below 1/sqrt(u)). An addition
+ *               of this library; the paper factors in FP64. */
 #define RLOBPCG_SKETCH_F64 0
 #define RLOBPCG_SKETCH_F32 1
+#define RLOBPCG_SKETCH_F32_REFINE 2
 
 /* Stop reasons reported in rlobpcg_info.stop_reason */
 #define RLOBPCG_STOP_CONVERGED 0   /* sketched tolerance (+ stagnation checks) held (Sec. 2.1)   */
@@ -63,7 +73,7 @@ typedef struct {
   int max_iter;         /* 0 means 200 when b = 1 (Alg. 1) and 100 otherwise (Alg. 2)              */
   int check_every;      /* stop-test period; 0 means 5 with stagnation checks, 1 without           */
   int use_stagnation;   /* 1: also require the stagnation checks of Sec. 2.1 (default)             */
-  int sketch_prec;      /* RLOBPCG_SKETCH_F64 (default) or RLOBPCG_SKETCH_F32                      */
+  int sketch_prec;      /* RLOBPCG_SKETCH_F64 (default), _F32 or _F32_REFINE (see above)           */
   int fixed_iters;      /* > 0: run exactly this many iterations, no stop test (parity runs)       */
   int residual_refresh_every; /* > 0: every this many iterations recompute A^H (A V) with a pass
                                  over A instead of the recombined A^H A V (drift control)         */
@@ -213,7 +223,8 @@ const char* rlobpcg_last_error(void);
  * for bit.
  *   A   device, m x n row-major (lda), dtype F64 or C128.
  *   SA  device, d x n COLUMN-major (element (r, j) at SA[j*d + r]); float/complex64 when
- *       sketch_prec is RLOBPCG_SKETCH_F32, double/complex128 otherwise.
+ *       sketch_prec is RLOBPCG_SKETCH_F32, double/complex128 otherwise (F32_REFINE keeps the
+ *       sketch in FP64).
  * Allocates nothing. Errors: INVALID_ARG (d < zeta, zeta < 1, lda < n, NULL pointers).
  */
 int rlobpcg_sketch(const void* A, int64_t m, int64_t n, int64_t lda, int dtype, int d, int zeta,
@@ -222,7 +233,9 @@ int rlobpcg_sketch(const void* A, int64_t m, int64_t n, int64_t lda, int dtype, 
 /*
  * Factorise the sketch (the factorisation step of Alg. 2): Householder QR SA = QR (Q discarded),
  * the SVD R = U~ Sigma~ V~^H by one-sided Jacobi, and R^{-1}. Since SVD(SA) = SVD(R), Sigma~ and
- * V~ are those of SA, and P P^* = V~ Sigma~^{-2} V~^H = (R^H R)^{-1}.
+ * V~ are those of SA, and P P^* = V~ Sigma~^{-2} V~^H = (R^H R)^{-1}. With
+ * RLOBPCG_SKETCH_F32_REFINE, SA is FP64, the QR runs in FP32 and R is corrected once in FP64 (see
+ * the precision constants); R, sigma, V~ and R^{-1} are then FP64.
  *   SA     device, d x n column-major in the sketch precision (overwritten by the QR).
  *   R      device, n x n column-major upper triangular (strict lower part zero), or NULL.
  *   sigma  device, n doubles, Sigma~ descending.

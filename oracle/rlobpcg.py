@@ -19,7 +19,9 @@ stagnation checks). Only numpy / LAPACK primitives are used (matmul, SVD, Househ
 quantity is formed the plain way its definition states, with no blocking, fusion or
 reordering, so that it can be checked against the paper by eye. Arithmetic is float64
 (complex128 for complex A); the optional FP32 sketch rounds A to float32 and sums in float32, as
-the mixed-precision form of the method does, and everything after the sketch SVD is float64.
+the mixed-precision form of the method does, and everything after the sketch SVD is float64. The
+'f32_refine' sketch precision (an addition of this library, not in the paper) keeps SA in float64,
+factors it in float32 and corrects the factor once by a float64 Cholesky QR (refined_factor).
 
 Readings taken where the paper is silent, ambiguous or inconsistent:
   * SparseStack randomness (Sec. 2.2 says "uniformly random"): entry (i, j) -- source row i, piece
@@ -60,7 +62,7 @@ import numpy as np
 
 __all__ = [
     "splitmix64", "piece_bounds", "sparse_stack", "sketch_dense_matrix", "sketch", "sketch_svd",
-    "orth", "rayleigh_ritz", "gram_pass", "householder_r", "stop_check", "rlobpcg",
+    "orth", "rayleigh_ritz", "gram_pass", "householder_r", "stop_check", "rlobpcg", "refined_factor",
     "default_tau", "EPS",
 ]
 
@@ -154,6 +156,26 @@ def sketch(A: np.ndarray, d: int, zeta: int, seed: int, precision: str = "f64") 
         np.add.at(acc, dest[:, j], sign[:, j, None].astype(real) * Aw)
     scale = real(1.0 / np.sqrt(float(zeta)))
     return acc * scale
+
+
+def refined_factor(SA: np.ndarray) -> np.ndarray:
+    """R factor of the FP64 sketch SA from an FP32 Householder QR corrected once in FP64 (the
+    sketch precision 'f32_refine', an addition of this library; the paper factors in FP64).
+
+    R_32 = R of QR(SA rounded to float32), computed in float32 (LAPACK geqrf); M = R_32^{-1} in
+    float64; Y = SA M; H = Y^H Y; s = n u max_i Re H_ii (u = 2^-53); R_c = the upper Cholesky
+    factor of H + s I (H + s I = R_c^H R_c); R = R_c R_32. In exact arithmetic, and without the
+    shift, R^H R = SA^H SA: R is a QR factor of SA.
+    """
+    n = SA.shape[1]
+    low = np.complex64 if np.iscomplexobj(SA) else np.float32
+    R32 = np.linalg.qr(SA.astype(low), mode="r").astype(SA.dtype)
+    M = np.linalg.solve(R32, np.eye(n, dtype=SA.dtype))
+    Y = SA @ M
+    H = Y.conj().T @ Y
+    shift = n * 2.0 ** -53 * float(np.max(np.real(np.diagonal(H))))
+    Rc = np.linalg.cholesky(H + shift * np.eye(n)).conj().T
+    return Rc @ R32
 
 
 def sketch_svd(SA: np.ndarray):
@@ -260,9 +282,14 @@ def rlobpcg(A: np.ndarray, k: int, b: int | None = None, d: int | None = None, z
     A = A.astype(wt, copy=False)
     AH = A.conj().T
 
-    # Sketch and factorise (the first steps of Alg. 2): P = V~ Sigma~^{-1}
-    SA = sketch(A, d, zeta, seed, sketch_precision)
-    s, Vt = sketch_svd(SA)
+    # Sketch and factorise (the first steps of Alg. 2): P = V~ Sigma~^{-1}. The refined form
+    # keeps SA in FP64 and takes V~, Sigma~ from its refined QR factor (SVD(SA) = SVD(R)).
+    if sketch_precision == "f32_refine":
+        SA = sketch(A, d, zeta, seed, "f64")
+        s, Vt = sketch_svd(refined_factor(SA))
+    else:
+        SA = sketch(A, d, zeta, seed, sketch_precision)
+        s, Vt = sketch_svd(SA)
     s = s.astype(np.float64)
     Vt = Vt.astype(wt)
     sigma11 = float(s[0])

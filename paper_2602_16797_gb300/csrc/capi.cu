@@ -12,6 +12,10 @@ size_t factor_workspace_bytes(int64_t d, int64_t n, size_t esz);
 template <class S>
 int factor_impl(S* SA, int d, int n, S* Rout, S* Rout_r, double* sigma, S* Vt, S* Rinv_r, S* Rinv_c, void* work,
                 size_t work_bytes, cudaStream_t st, int* sweeps_host, bool do_svd, int* err);
+size_t refine_workspace_bytes(int64_t d, int64_t n, int dtype);
+template <class T>
+int factor_refine_impl(T* SA, int d, int n, T* Rout, T* Rout_r, double* sigma, T* Vt, T* Rinv_r, T* Rinv_c,
+                       void* work, size_t work_bytes, cudaStream_t st, int* sweeps_host, bool do_svd, int* err);
 size_t gram_workspace_bytes(int64_t m, int64_t n, int b, int dtype);
 int gram_dispatch(const void* A, int64_t m, int64_t n, int64_t lda, int dtype, const void* W, int b, int64_t ldw,
                   void* AW, int64_t ldaw, void* G, int64_t ldg, void* work, size_t work_bytes, int resid_mode,
@@ -114,10 +118,13 @@ extern "C" int rlobpcg_sketch(const void* A, int64_t m, int64_t n, int64_t lda, 
                               uint64_t seed, int sketch_prec, void* SA, void* stream) {
   if (!A || !SA || m < 1 || n < 1 || lda < n || zeta < 1 || d < zeta || d > (1 << 28) || n > (1 << 28) ||
       (dtype != RLOBPCG_F64 && dtype != RLOBPCG_C128) ||
-      (sketch_prec != RLOBPCG_SKETCH_F64 && sketch_prec != RLOBPCG_SKETCH_F32))
+      (sketch_prec != RLOBPCG_SKETCH_F64 && sketch_prec != RLOBPCG_SKETCH_F32 &&
+       sketch_prec != RLOBPCG_SKETCH_F32_REFINE))
     return RLOBPCG_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
-  int rc = sketch_dispatch(A, m, n, lda, dtype, d, zeta, seed, sketch_prec, SA, st);
+  // the refined form keeps the sketch in FP64 (its QR input is rounded to FP32 inside the factor)
+  const int sp = sketch_prec == RLOBPCG_SKETCH_F32 ? RLOBPCG_SKETCH_F32 : RLOBPCG_SKETCH_F64;
+  int rc = sketch_dispatch(A, m, n, lda, dtype, d, zeta, seed, sp, SA, st);
   if (rc) return rc;
   return finish(st, nullptr);
 }
@@ -126,28 +133,39 @@ static size_t sketch_elem(int dtype, int prec) {
   return (dtype == RLOBPCG_C128 ? 2 : 1) * (prec == RLOBPCG_SKETCH_F32 ? 4 : 8);
 }
 
+static size_t factor_scratch_bytes(int64_t d, int64_t n, int dtype, int sketch_prec) {
+  if (sketch_prec == RLOBPCG_SKETCH_F32_REFINE) return refine_workspace_bytes(d, n, dtype);
+  return factor_workspace_bytes(d, n, sketch_elem(dtype, sketch_prec));
+}
+
 // factorisation scratch plus a column-major copy of R^{-1} (the caller receives the row-major one)
 extern "C" size_t rlobpcg_factor_workspace_size(int64_t d, int64_t n, int dtype, int sketch_prec) {
   const size_t esz = sketch_elem(dtype, sketch_prec);
-  return factor_workspace_bytes(d, n, esz) + (((size_t)n * n * esz + 255) & ~(size_t)255);
+  return factor_scratch_bytes(d, n, dtype, sketch_prec) + (((size_t)n * n * esz + 255) & ~(size_t)255);
 }
 
 extern "C" int rlobpcg_factor(void* SA, int64_t d, int64_t n, int dtype, int sketch_prec, void* R, double* sigma,
                               void* Vt, void* Rinv, void* work, size_t work_bytes, void* stream) {
   if (!SA || !sigma || !Vt || !work || n < 1 || d < n || (dtype != RLOBPCG_F64 && dtype != RLOBPCG_C128) ||
-      (sketch_prec != RLOBPCG_SKETCH_F64 && sketch_prec != RLOBPCG_SKETCH_F32))
+      (sketch_prec != RLOBPCG_SKETCH_F64 && sketch_prec != RLOBPCG_SKETCH_F32 &&
+       sketch_prec != RLOBPCG_SKETCH_F32_REFINE))
     return RLOBPCG_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
-  const size_t esz = sketch_elem(dtype, sketch_prec);
   if (work_bytes < rlobpcg_factor_workspace_size(d, n, dtype, sketch_prec)) return RLOBPCG_ERR_INVALID_ARG;
-  const size_t fbytes = factor_workspace_bytes(d, n, esz);
+  const size_t fbytes = factor_scratch_bytes(d, n, dtype, sketch_prec);
   void* Rinv_c = Rinv ? (void*)((unsigned char*)work + fbytes) : nullptr;
   work_bytes = fbytes;
   int* err = step_err_word(st);
   if (!err) return RLOBPCG_ERR_OOM;
   int rc;
   const bool f32 = sketch_prec == RLOBPCG_SKETCH_F32;
-  if (dtype == RLOBPCG_F64) {
+  if (sketch_prec == RLOBPCG_SKETCH_F32_REFINE) {
+    rc = dtype == RLOBPCG_F64
+             ? factor_refine_impl<double>((double*)SA, (int)d, (int)n, (double*)R, nullptr, sigma, (double*)Vt,
+                                          (double*)Rinv, (double*)Rinv_c, work, work_bytes, st, nullptr, true, err)
+             : factor_refine_impl<cd>((cd*)SA, (int)d, (int)n, (cd*)R, nullptr, sigma, (cd*)Vt, (cd*)Rinv,
+                                      (cd*)Rinv_c, work, work_bytes, st, nullptr, true, err);
+  } else if (dtype == RLOBPCG_F64) {
     rc = f32 ? factor_impl<float>((float*)SA, (int)d, (int)n, (float*)R, nullptr, sigma, (float*)Vt, (float*)Rinv,
                                   (float*)Rinv_c, work, work_bytes, st, nullptr, true, err)
              : factor_impl<double>((double*)SA, (int)d, (int)n, (double*)R, nullptr, sigma, (double*)Vt, (double*)Rinv,

@@ -34,11 +34,25 @@ __device__ inline float sqrt_(float a) { return sqrtf(a); }
 __device__ inline double hypot_(double a, double b) { return hypot(a, b); }
 __device__ inline float hypot_(float a, float b) { return hypotf(a, b); }
 
-// 1 / z
+// 1 / z. The complex forms scale z by a power of two first (exact), so that |z|^2 neither
+// underflows nor overflows: the reflector's 1 / (beta (alpha - beta)) is about |x|^-2 for a
+// column of norm |x|, and |z|^2 ~ |x|^4 underflows in FP32 already for |x| ~ 1e-10.
 __device__ inline double recip_(double a) { return 1.0 / a; }
 __device__ inline float recip_(float a) { return 1.0f / a; }
-__device__ inline cd recip_(cd a) { double s = a.x * a.x + a.y * a.y; return {a.x / s, -a.y / s}; }
-__device__ inline cf recip_(cf a) { float s = a.x * a.x + a.y * a.y; return {a.x / s, -a.y / s}; }
+__device__ inline cd recip_(cd a) {
+  int e = 0;
+  frexp(fmax(fabs(a.x), fabs(a.y)), &e);
+  const double x = ldexp(a.x, -e), y = ldexp(a.y, -e);
+  const double s = x * x + y * y;
+  return {ldexp(x / s, -e), ldexp(-y / s, -e)};
+}
+__device__ inline cf recip_(cf a) {
+  int e = 0;
+  frexpf(fmaxf(fabsf(a.x), fabsf(a.y)), &e);
+  const float x = ldexpf(a.x, -e), y = ldexpf(a.y, -e);
+  const float s = x * x + y * y;
+  return {ldexpf(x / s, -e), ldexpf(-y / s, -e)};
+}
 
 // ------------------------------------------------------------------------------------------
 // Householder QR (LAPACK geqr2 reflector convention: H = I - tau v v^H, v(0) = 1, H^H x = beta e1)
@@ -592,87 +606,146 @@ int qr_flow_launch(S* SA, int d, int n, S* tau, S* scv, unsigned* ready, int* er
   return RLOBPCG_OK;
 }
 
-// err: device word that receives DEV_ERR_TIMEOUT if a bounded wait of the QR runs out.
+namespace {
+// Pointers of the factor workspace (layout of factor_workspace_bytes)
 template <class S>
-int factor_impl(S* SA, int d, int n, S* Rout, S* Rout_r, double* sigma, S* Vt, S* Rinv_r, S* Rinv_c,
-                void* work, size_t work_bytes, cudaStream_t st, int* sweeps_host, bool do_svd, int* err) {
-  if (work_bytes < factor_workspace_bytes(d, n, sizeof(S)) || !err) return RLOBPCG_ERR_INVALID_ARG;
-  unsigned char* p = (unsigned char*)work;
-  auto take = [&](size_t x) { void* r = p; p += (x + 255) & ~(size_t)255; return r; };
-  S* tau = (S*)take((size_t)n * sizeof(S));
-  S* scv = (S*)take((size_t)n * sizeof(S));
-  S* X = (S*)take((size_t)n * n * sizeof(S));
-  S* V = (S*)take((size_t)n * n * sizeof(S));
-  double* nrm = (double*)take((size_t)n * sizeof(double));
-  int* flags = (int*)take(4 * sizeof(int));
-  unsigned* ready = (unsigned*)take((size_t)2 * n * sizeof(unsigned));
+struct FactorWs {
+  S *tau, *scv, *X, *V;
+  double* nrm;
+  int* flags;
+  unsigned* ready;
+  FactorWs(void* work, int n) {
+    unsigned char* p = (unsigned char*)work;
+    auto take = [&](size_t x) { void* r = p; p += (x + 255) & ~(size_t)255; return r; };
+    tau = (S*)take((size_t)n * sizeof(S));
+    scv = (S*)take((size_t)n * sizeof(S));
+    X = (S*)take((size_t)n * n * sizeof(S));
+    V = (S*)take((size_t)n * n * sizeof(S));
+    nrm = (double*)take((size_t)n * sizeof(double));
+    flags = (int*)take(4 * sizeof(int));
+    ready = (unsigned*)take((size_t)2 * n * sizeof(unsigned));
+  }
+};
+}  // namespace
 
-  // 1. Householder QR: the dataflow kernel holds each thread's rows of a column in registers
-  // (d <= 4096); taller sketches take the kernel with one grid barrier per column.
+// Householder QR of SA (d x n col-major, overwritten); R (n x n col-major, zero below the
+// diagonal) is left in the workspace's X (factor_r_of). err: device word that receives
+// DEV_ERR_TIMEOUT if a bounded wait of the QR runs out.
+template <class S>
+int factor_qr(S* SA, int d, int n, void* work, size_t work_bytes, cudaStream_t st, int* err) {
+  if (work_bytes < factor_workspace_bytes(d, n, sizeof(S)) || !err) return RLOBPCG_ERR_INVALID_ARG;
+  FactorWs<S> w(work, n);
+  // the dataflow kernel holds each thread's rows of a column in registers (d <= 4096); taller
+  // sketches take the kernel with one grid barrier per column
   int G = 0, rc = 0;
   if (d <= 8 * kQrMaxThreads) {
-    RL_TRY((qr_flow_launch<S, 8>(SA, d, n, tau, scv, ready, err, st)));
+    RL_TRY((qr_flow_launch<S, 8>(SA, d, n, w.tau, w.scv, w.ready, err, st)));
   } else if (d <= 16 * kQrMaxThreads) {
-    RL_TRY((qr_flow_launch<S, 16>(SA, d, n, tau, scv, ready, err, st)));
+    RL_TRY((qr_flow_launch<S, 16>(SA, d, n, w.tau, w.scv, w.ready, err, st)));
   } else {
     rc = coop_grid(qr_kernel<S>, FQ_THREADS, 0, &G);
     if (rc) return rc;
     G = min(G, max(1, n));
-    void* args[] = {(void*)&SA, (void*)&d, (void*)&n, (void*)&tau};
+    void* args[] = {(void*)&SA, (void*)&d, (void*)&n, (void*)&w.tau};
     RL_CUDA(cudaLaunchCooperativeKernel((void*)qr_kernel<S>, dim3(G), dim3(FQ_THREADS), args, 0, st));
     note_launch();
   }
   const int64_t nn = (int64_t)n * n;
   const int eb = 256, eg = (int)((nn + eb - 1) / eb);
-  extract_r_kernel<S><<<eg, eb, 0, st>>>(SA, d, n, X);
+  extract_r_kernel<S><<<eg, eb, 0, st>>>(SA, d, n, w.X);
   RL_CHECK_LAUNCH();
+  return RLOBPCG_OK;
+}
+
+// X = R^{-1} for an upper-triangular R (n x n col-major), row- and column-major outputs.
+template <class S>
+int trinv_launch(const S* R, int n, S* Xr, S* Xc, cudaStream_t st) {
+  const size_t sm = (size_t)2 * n * sizeof(S);
+  RL_TRY(allow_dynamic_smem(trinv_kernel<S>, sm));
+  trinv_kernel<S><<<n, 256, sm, st>>>(R, n, Xr, Xc);
+  RL_CHECK_LAUNCH();
+  return RLOBPCG_OK;
+}
+
+// Where factor_qr leaves R, and where factor_post reads it (the workspace's X).
+template <class S>
+S* factor_r_of(void* work, int n) { return FactorWs<S>(work, n).X; }
+
+// From R in the workspace's X (n x n col-major, consumed): copies of R (col- and row-major),
+// R^{-1} (row- and col-major), and the one-sided Jacobi SVD of R (sigma descending, V~).
+template <class S>
+int factor_post(int n, S* Rout, S* Rout_r, double* sigma, S* Vt, S* Rinv_r, S* Rinv_c, void* work, cudaStream_t st,
+                int* sweeps_host, bool do_svd) {
+  FactorWs<S> w(work, n);
+  S* X = w.X;
+  const int64_t nn = (int64_t)n * n;
+  const int eb = 256, eg = (int)((nn + eb - 1) / eb);
   if (Rout) RL_CUDA(cudaMemcpyAsync(Rout, X, nn * sizeof(S), cudaMemcpyDeviceToDevice, st));
   if (Rout_r) {
     transpose_kernel<S><<<eg, eb, 0, st>>>(X, n, Rout_r);
     RL_CHECK_LAUNCH();
   }
-
-  // 3. R^{-1} (before Jacobi overwrites X)
+  // R^{-1} (before Jacobi overwrites X)
   if (Rinv_r && Rinv_c) {
     size_t sm = (size_t)2 * n * sizeof(S);
     RL_TRY(allow_dynamic_smem(trinv_kernel<S>, sm));
     trinv_kernel<S><<<n, 256, sm, st>>>(X, n, Rinv_r, Rinv_c);
     RL_CHECK_LAUNCH();
   }
-
   if (!do_svd) {
     if (sweeps_host) *sweeps_host = 0;
     return RLOBPCG_OK;
   }
-  // 2. Jacobi SVD of R
-  set_identity_kernel<S><<<eg, eb, 0, st>>>(V, n);
+  // Jacobi SVD of R
+  set_identity_kernel<S><<<eg, eb, 0, st>>>(w.V, n);
   RL_CHECK_LAUNCH();
-  RL_CUDA(cudaMemsetAsync(flags, 0, 4 * sizeof(int), st));
-  rc = coop_grid(jacobi_kernel<S>, FQ_THREADS, 0, &G);
+  RL_CUDA(cudaMemsetAsync(w.flags, 0, 4 * sizeof(int), st));
+  int G = 0;
+  const int rc = coop_grid(jacobi_kernel<S>, FQ_THREADS, 0, &G);
   if (rc) return rc;
   G = min(G, max(1, (n / 2 + FQ_WARPS - 1) / FQ_WARPS));
   int max_sweeps = 40;
-  int* sweeps_dev = flags + 3;
-  colnorm_kernel<S><<<(n * 32 + 255) / 256, 256, 0, st>>>(X, n, nrm);
+  int* sweeps_dev = w.flags + 3;
+  colnorm_kernel<S><<<(n * 32 + 255) / 256, 256, 0, st>>>(X, n, w.nrm);
   RL_CHECK_LAUNCH();
   {
-    const double* nrm0 = nrm;
+    const double* nrm0 = w.nrm;
+    S* V = w.V;
+    int* flags = w.flags;
     void* args[] = {(void*)&X, (void*)&V, (void*)&n, (void*)&max_sweeps, (void*)&flags, (void*)&sweeps_dev,
                     (void*)&nrm0};
     RL_CUDA(cudaLaunchCooperativeKernel((void*)jacobi_kernel<S>, dim3(G), dim3(FQ_THREADS), args, 0, st));
     note_launch();
   }
-  colnorm_kernel<S><<<(n * 32 + 255) / 256, 256, 0, st>>>(X, n, nrm);
+  colnorm_kernel<S><<<(n * 32 + 255) / 256, 256, 0, st>>>(X, n, w.nrm);
   RL_CHECK_LAUNCH();
-  sort_svd_kernel<S><<<n, 256, 0, st>>>(nrm, V, n, sigma, Vt);
+  sort_svd_kernel<S><<<n, 256, 0, st>>>(w.nrm, w.V, n, sigma, Vt);
   RL_CHECK_LAUNCH();
   if (sweeps_host) RL_CUDA(cudaMemcpyAsync(sweeps_host, sweeps_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
   return RLOBPCG_OK;
+}
+
+// The factorisation step of Alg. 2: QR of SA, then R, R^{-1} and (optionally) the SVD of R.
+template <class S>
+int factor_impl(S* SA, int d, int n, S* Rout, S* Rout_r, double* sigma, S* Vt, S* Rinv_r, S* Rinv_c,
+                void* work, size_t work_bytes, cudaStream_t st, int* sweeps_host, bool do_svd, int* err) {
+  RL_TRY(factor_qr<S>(SA, d, n, work, work_bytes, st, err));
+  return factor_post<S>(n, Rout, Rout_r, sigma, Vt, Rinv_r, Rinv_c, work, st, sweeps_host, do_svd);
 }
 
 template int factor_impl<double>(double*, int, int, double*, double*, double*, double*, double*, double*, void*, size_t, cudaStream_t, int*, bool, int*);
 template int factor_impl<float>(float*, int, int, float*, float*, double*, float*, float*, float*, void*, size_t, cudaStream_t, int*, bool, int*);
 template int factor_impl<cd>(cd*, int, int, cd*, cd*, double*, cd*, cd*, cd*, void*, size_t, cudaStream_t, int*, bool, int*);
 template int factor_impl<cf>(cf*, int, int, cf*, cf*, double*, cf*, cf*, cf*, void*, size_t, cudaStream_t, int*, bool, int*);
+template int factor_qr<float>(float*, int, int, void*, size_t, cudaStream_t, int*);
+template int factor_qr<cf>(cf*, int, int, void*, size_t, cudaStream_t, int*);
+template int trinv_launch<double>(const double*, int, double*, double*, cudaStream_t);
+template int trinv_launch<cd>(const cd*, int, cd*, cd*, cudaStream_t);
+template float* factor_r_of<float>(void*, int);
+template cf* factor_r_of<cf>(void*, int);
+template double* factor_r_of<double>(void*, int);
+template cd* factor_r_of<cd>(void*, int);
+template int factor_post<double>(int, double*, double*, double*, double*, double*, double*, void*, cudaStream_t, int*, bool);
+template int factor_post<cd>(int, cd*, cd*, double*, cd*, cd*, cd*, void*, cudaStream_t, int*, bool);
 
 }  // namespace rl

@@ -10,6 +10,7 @@
 
 #include <algorithm>
 #include <limits>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -21,6 +22,10 @@ namespace rl {
 int sketch_dispatch(const void* A, int64_t m, int64_t n, int64_t lda, int dtype, int d, int zeta, uint64_t seed,
                     int sketch_prec, void* SA, cudaStream_t st);
 size_t factor_workspace_bytes(int64_t d, int64_t n, size_t esz);
+size_t refine_workspace_bytes(int64_t d, int64_t n, int dtype);
+template <class T>
+int factor_refine_impl(T* SA, int d, int n, T* Rout, T* Rout_r, double* sigma, T* Vt, T* Rinv_r, T* Rinv_c,
+                       void* work, size_t work_bytes, cudaStream_t st, int* sweeps_host, bool do_svd, int* err);
 template <class S>
 int factor_impl(S* SA, int d, int n, S* Rout, S* Rout_r, double* sigma, S* Vt, S* Rinv_r, S* Rinv_c, void* work,
                 size_t work_bytes, cudaStream_t st, int* sweeps_host, bool do_svd, int* err);
@@ -237,12 +242,21 @@ int solve_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, double tau, double* s
   RL_CUDA(cudaMemcpyAsync(&herr, p->err, sizeof(int), cudaMemcpyDeviceToHost, st));
 
   // Sketch and factorise (the first steps of Alg. 2)
-  RL_TRY(sketch_dispatch(A, m, n, lda, p->dtype, d, p->opts.zeta, p->opts.seed, p->opts.sketch_prec, p->SA, st));
+  // the refined form keeps SA in FP64; its QR input is rounded to FP32 inside the factor step
+  const bool refine = p->opts.sketch_prec == RLOBPCG_SKETCH_F32_REFINE;
+  RL_TRY(sketch_dispatch(A, m, n, lda, p->dtype, d, p->opts.zeta, p->opts.seed,
+                         refine ? RLOBPCG_SKETCH_F64 : p->opts.sketch_prec, p->SA, st));
   RL_CUDA(cudaEventRecord(p->ev[1], st));
   int sweeps = 0;
   const bool exact = p->opts.exact_sketch_svd != 0;
-  RL_TRY(factor_impl<S>((S*)p->SA, d, n, (S*)p->R_c, (S*)p->R_r, p->sk_sigma, (S*)p->Vt, (S*)p->Rinv_r,
-                        (S*)p->Rinv_c, p->fwork, p->fwork_bytes, st, &sweeps, exact, p->err));
+  if constexpr (std::is_same<S, T>::value) {
+    if (refine)
+      RL_TRY(factor_refine_impl<S>((S*)p->SA, d, n, (S*)p->R_c, (S*)p->R_r, p->sk_sigma, (S*)p->Vt, (S*)p->Rinv_r,
+                                   (S*)p->Rinv_c, p->fwork, p->fwork_bytes, st, &sweeps, exact, p->err));
+  }
+  if (!refine)
+    RL_TRY(factor_impl<S>((S*)p->SA, d, n, (S*)p->R_c, (S*)p->R_r, p->sk_sigma, (S*)p->Vt, (S*)p->Rinv_r,
+                          (S*)p->Rinv_c, p->fwork, p->fwork_bytes, st, &sweeps, exact, p->err));
   double sigma11 = 0;
   if (exact) {
     RL_CUDA(cudaMemcpyAsync(&sigma11, p->sk_sigma, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -454,7 +468,8 @@ int resolve_plan_args(int64_t m, int64_t n, int k, int dtype, const rlobpcg_opts
   const int b = o->block > 0 ? o->block : k;
   const int64_t d = o->d > 0 ? o->d : 4 * n;
   if (k < 1 || b < k || 3 * (int64_t)b > n || n > m || o->zeta < 1 || d < n || d < o->zeta || b > 21 ||
-      n > (1 << 20) || (o->sketch_prec != RLOBPCG_SKETCH_F64 && o->sketch_prec != RLOBPCG_SKETCH_F32)) {
+      n > (1 << 20) || (o->sketch_prec != RLOBPCG_SKETCH_F64 && o->sketch_prec != RLOBPCG_SKETCH_F32 &&
+                        o->sketch_prec != RLOBPCG_SKETCH_F32_REFINE)) {
     set_last_error("invalid plan arguments (need 1 <= k <= b <= 21, 3b <= n <= m, n <= d, zeta <= d)", __FILE__, __LINE__);
     return RLOBPCG_ERR_INVALID_ARG;
   }
@@ -501,7 +516,8 @@ int plan_buffers(PlanAlloc& A_, rlobpcg_plan_s* p, int64_t m, int64_t n, int b, 
   const int64_t cmax = std::max<int64_t>(ld, qmax);
   RL_B(Zb, (size_t)n * qmax * esz);
   RL_B(Yb, (size_t)n * qmax * esz);
-  *fwork = factor_workspace_bytes(d, n, ssz);
+  *fwork = o.sketch_prec == RLOBPCG_SKETCH_F32_REFINE ? refine_workspace_bytes(d, n, dtype)
+                                                     : factor_workspace_bytes(d, n, ssz);
   RL_B(fwork, *fwork);
   RL_B(Tb, (size_t)n * ld * esz);
   RL_B(ATb, (size_t)m * ld * esz);

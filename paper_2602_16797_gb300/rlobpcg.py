@@ -28,6 +28,7 @@ RLOBPCG_F64 = 0
 RLOBPCG_C128 = 1
 RLOBPCG_SKETCH_F64 = 0
 RLOBPCG_SKETCH_F32 = 1
+RLOBPCG_SKETCH_F32_REFINE = 2
 RLOBPCG_STOP_CONVERGED = 0
 RLOBPCG_STOP_MAX_ITER = 1
 RLOBPCG_STOP_FIXED = 2

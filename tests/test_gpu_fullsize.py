@@ -30,6 +30,23 @@ def _opts(seed, d, prec=0, **kw):
     return o
 
 
+def test_complex_full_size_refined_sketch():
+    """The complex 2e5 x 300, k = 3 configuration with its FP32 factor (refined once in FP64 so
+    that kappa = 1e13 is resolved): converges (no max_iter) and matches the oracle's refined run
+    and the planted truth at full size."""
+    A, s, V = wl.planted_complex()
+    n, k = 300, 3
+    sig, Vg, _, _, info = rl.solve(torch.from_numpy(A).cuda(), k,
+                                   opts=_opts(1003, 4 * n, rl.RLOBPCG_SKETCH_F32_REFINE))
+    assert info["stop_reason"] == rl.RLOBPCG_STOP_CONVERGED
+    sig, Vg = sig.cpu().numpy(), Vg.cpu().numpy()
+    o = oracle.rlobpcg(A, k=k, d=4 * n, zeta=8, seed=1003, sketch_precision="f32_refine")
+    gap = (s[-4] - s[-3]) / s[0]
+    check_sigma(sig, o["sigma"], o["sigma11"], n)
+    check_angle(Vg, o["V"], gap, n)
+    check_truth(sig, o["sigma"], s[::-1][:k], o["sigma11"], n)
+
+
 def test_complex_full_size_parity():
     A, s, V = wl.planted_complex()
     n, k = 300, 3
@@ -107,7 +124,7 @@ def test_large_split_gram_pass_against_oracle_products(large):
     assert np.all(np.abs(G_h - G0) <= tG)
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_large_solve_against_planted_truth(large, prec):
     A, s, V = large
     m, n = A.shape

@@ -176,9 +176,11 @@ def gpu_factor(SA, prec):
     d, n = SA.shape
     cplx = np.iscomplexobj(SA)
     dt = rl.RLOBPCG_C128 if cplx else rl.RLOBPCG_F64
-    sp = rl.RLOBPCG_SKETCH_F32 if prec == "f32" else rl.RLOBPCG_SKETCH_F64
-    tdt = {(False, "f64"): torch.float64, (False, "f32"): torch.float32,
-           (True, "f64"): torch.complex128, (True, "f32"): torch.complex64}[(cplx, prec)]
+    sp = {"f32": rl.RLOBPCG_SKETCH_F32, "f64": rl.RLOBPCG_SKETCH_F64,
+          "f32_refine": rl.RLOBPCG_SKETCH_F32_REFINE}[prec]
+    low = prec == "f32"
+    tdt = {(False, False): torch.float64, (False, True): torch.float32,
+           (True, False): torch.complex128, (True, True): torch.complex64}[(cplx, low)]
     SAd = torch.from_numpy(np.ascontiguousarray(SA.T)).to(tdt).cuda()   # column-major d x n
     R = torch.empty((n, n), dtype=tdt, device="cuda")
     Vt = torch.empty((n, n), dtype=tdt, device="cuda")
@@ -247,6 +249,22 @@ def test_factor_rank_deficient_sketch(cplx):
 
 
 @pytest.mark.parametrize("cplx", [False, True])
+def test_factor_f32_graded_columns(cplx):
+    """FP32 factor of a sketch whose columns fall to 1e-13 of the largest: every output finite
+    (the complex reflector scalar is formed without squaring a product of two small numbers), and
+    R^H R = SA^H SA to FP32 rounding of the column scales."""
+    rng = np.random.default_rng(9)
+    d, n = 1200, 300
+    SA = (_rand(rng, (d, n), cplx) @ np.diag(np.logspace(0, -13, n))).astype(np.complex64 if cplx else np.float32)
+    R, sig, Vt, Rinv = gpu_factor(SA, "f32")
+    assert np.isfinite(R).all() and np.isfinite(sig).all() and np.isfinite(Rinv).all()
+    SA64 = SA.astype(np.complex128 if cplx else np.float64)
+    R64 = R.astype(SA64.dtype)
+    G = SA64.conj().T @ SA64
+    assert np.linalg.norm(R64.conj().T @ R64 - G, 2) <= 50 * n * 2.0 ** -24 * np.linalg.norm(G, 2)
+
+
+@pytest.mark.parametrize("cplx", [False, True])
 def test_factor_f32_sketch(cplx):
     rng = np.random.default_rng(5)
     d, n = 400, 100
@@ -258,3 +276,26 @@ def test_factor_f32_sketch(cplx):
     assert np.allclose(Vt.conj().T @ Vt, np.eye(n), atol=1e2 * n * u32)
     assert np.allclose(Rinv.astype(np.complex128 if cplx else np.float64) @ R, np.eye(n),
                        atol=1e2 * n * u32 * s0[0] / s0[-1])
+
+
+@pytest.mark.parametrize("d,n,kappa", [(400, 100, 1e10), (1200, 300, 1e13), (4000, 1000, 1e10), (37, 36, 1e6),
+                                       (257, 130, 1e12)])
+@pytest.mark.parametrize("cplx", [False, True])
+def test_factor_refined_parity(d, n, kappa, cplx):
+    """FP32 QR of the FP64 sketch corrected once in FP64 (RLOBPCG_SKETCH_F32_REFINE): R^H R equals
+    SA^H SA to FP64 rounding and the shift (where the FP32 factor alone is off by u_32 ||SA||^2),
+    sigma~ matches the FP64 SVD of SA, and R^{-1} R = I; both the oracle's refined factor and the
+    GPU's are QR factors of the same SA. Sizes span several Cholesky panels and ragged tiles."""
+    rng = np.random.default_rng(d + n)
+    SA = _rand(rng, (d, n), cplx) @ np.diag(np.logspace(0, -np.log10(kappa), n))
+    R, sig, Vt, Rinv = gpu_factor(SA, "f32_refine")
+    G = SA.conj().T @ SA
+    s0, V0 = oracle.sketch_svd(SA)
+    nrm = s0[0] ** 2
+    assert np.allclose(np.tril(R, -1), 0)
+    assert np.linalg.norm(R.conj().T @ R - G, 2) <= 100 * n * U * nrm
+    Ro = oracle.refined_factor(SA)
+    assert np.linalg.norm(Ro.conj().T @ Ro - G, 2) <= 100 * n * U * nrm
+    assert np.all(np.abs(sig - s0) <= 50 * n * U * s0[0])
+    assert np.all(np.diff(sig) <= 0)
+    assert np.allclose(Rinv @ R, np.eye(n), atol=1e2 * n * U * s0[0] / s0[-1])

@@ -33,7 +33,8 @@ def gpu_solve(A, k, *, seed, d=None, zeta=8, b=None, tau=None, stagnation=True, 
     o.fixed_iters = fixed
     o.max_iter = max_iter
     o.residual_refresh_every = refresh
-    o.sketch_prec = rl.RLOBPCG_SKETCH_F32 if prec == "f32" else rl.RLOBPCG_SKETCH_F64
+    o.sketch_prec = {"f32": rl.RLOBPCG_SKETCH_F32, "f64": rl.RLOBPCG_SKETCH_F64,
+                     "f32_refine": rl.RLOBPCG_SKETCH_F32_REFINE}[prec]
     if tau is not None:
         o.tau = tau
     Ad = torch.from_numpy(np.ascontiguousarray(A)).cuda()
@@ -196,6 +197,39 @@ def test_complex_fp64_sketch_fixed():
     A, s, V = wl.planted_complex(m=20_000)
     gap = (s[-4] - s[-3]) / s[0]
     compare(A, 3, None, None, n=300, gap_abs=gap, seed=1003, fixed=10)
+
+
+@pytest.mark.parametrize("fixed", [0, 3, 12])
+def test_refined_sketch_small(small_planted, fixed):
+    """FP32 factor refined once in FP64, kappa = 1e10: parity with the oracle's refined run, in
+    adaptive and fixed-iteration mode; adaptive stops after as many iterations as the oracle."""
+    A, s, V = small_planted
+    gap = (s[-2] - s[-1]) / s[0]
+    g, o = compare(A, 1, None if fixed else s[-1:], None if fixed else V[:, -1:], n=50, gap_abs=gap, seed=1001,
+                   prec="f32_refine", fixed=fixed, tau=1e-12, stagnation=False)
+    if not fixed:
+        assert g[4]["iters"] == o["iters"]
+
+
+@pytest.mark.parametrize("fixed", [0, 10])
+def test_complex_refined_sketch(fixed):
+    """complex128 with the three smallest singular values 1e-13..1e-12 (kappa = 1e13), FP32
+    factor refined in FP64: parity with the oracle's refined run and with the planted truth."""
+    A, s, V = wl.planted_complex(m=20_000)
+    gap = (s[-4] - s[-3]) / s[0]
+    compare(A, 3, None if fixed else s[::-1][:3], None, n=300, gap_abs=gap, seed=1003, prec="f32_refine",
+            fixed=fixed)
+
+
+def test_refined_nullspace():
+    """Exactly rank-deficient sketch (A = B C): the shifted Cholesky keeps the refined factor
+    defined; the nullspace is found like with the FP64 factor."""
+    A, C = wl.exact_nullspace(m=20_000)
+    Q = np.linalg.svd(C)[2].T[:, -5:]
+    sig, V, _, _, info = gpu_solve(A, 5, seed=2002, d=1500, prec="f32_refine")
+    assert info["stop_reason"] == rl.RLOBPCG_STOP_CONVERGED
+    assert np.all(sig <= 100 * np.sqrt(500) * U * info["sigma11"])
+    assert sub_sin(V, Q) <= 1e-8
 
 
 def test_mixed_precision_sketch_small(small_planted):

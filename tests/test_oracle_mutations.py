@@ -105,3 +105,21 @@ def test_gram_pass_dropping_a_row_is_caught(monkeypatch):
     _patch(monkeypatch, "gram_pass", bad)
     _expect_failure(lambda: pins.test_gram_pass_exact_on_integers(False))
     _expect_failure(pins.test_gram_pass_within_rounding_of_exact_rationals)
+
+
+def test_refinement_dropped_is_caught(monkeypatch):
+    def bad(SA):
+        low = np.complex64 if np.iscomplexobj(SA) else np.float32
+        return np.linalg.qr(SA.astype(low), mode="r").astype(SA.dtype)   # the FP32 factor alone
+    _patch(monkeypatch, "refined_factor", bad)
+    _expect_failure(lambda: pins.test_refined_factor_is_a_qr_factor_of_the_sketch(False, 1e10))
+    _expect_failure(lambda: pins.test_refined_factor_satisfies_the_preconditioning_fact(False))
+
+
+def test_refinement_without_conjugate_is_caught(monkeypatch):
+    orig = MOD.refined_factor
+
+    def bad(SA):
+        return orig(SA).conj()                                              # a transposed-only Gram
+    _patch(monkeypatch, "refined_factor", bad)
+    _expect_failure(lambda: pins.test_refined_factor_is_a_qr_factor_of_the_sketch(True, 1e13))

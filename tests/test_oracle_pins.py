@@ -229,6 +229,58 @@ def test_randomized_preconditioning_fact(complex_):
     np.testing.assert_allclose(np.sort(sv), np.sort(1.0 / ssq), rtol=1e-6)
 
 
+@pytest.mark.parametrize("complex_,kappa", [(False, 1e10), (True, 1e13)])
+def test_refined_factor_is_a_qr_factor_of_the_sketch(complex_, kappa):
+    """The FP32 factor corrected once in FP64 (sketch precision 'f32_refine') is an FP64-quality
+    QR factor of the sketch: R^H R = (SA)^H (SA) up to the Cholesky shift s = n u max_i H_ii
+    times ||R_32||^2 and FP64 rounding, where the FP32 factor alone is off by u_32 ||SA||^2."""
+    rng = np.random.default_rng(41)
+    m, n, zeta = 3000, 40, 8
+    sigma = np.logspace(0, -np.log10(kappa), n)
+    A, _, _ = wl.planted(rng, m, sigma, complex_=complex_)
+    SA = oracle.sketch(A, 4 * n, zeta, seed=22)
+    R = oracle.refined_factor(SA)
+    G = SA.conj().T @ SA
+    nrm = np.linalg.norm(SA, 2) ** 2
+    assert np.allclose(np.tril(R, -1), 0)
+    assert np.linalg.norm(R.conj().T @ R - G, 2) <= 100 * n * U64 * nrm
+    low = np.complex64 if complex_ else np.float32
+    R32 = np.linalg.qr(SA.astype(low), mode="r").astype(SA.dtype)
+    assert np.linalg.norm(R32.conj().T @ R32 - G, 2) > 1000 * n * U64 * nrm   # what the FP64 step removes
+
+
+@pytest.mark.parametrize("complex_", [False, True])
+def test_refined_factor_satisfies_the_preconditioning_fact(complex_):
+    """Fact (randomized preconditioning, Sec. 3.1) for P = R^{-1} with the refined factor, at
+    kappa(A) = 1e10 where an FP32 factor alone leaves kappa(A R_32^{-1}) ~ u_32 kappa(A)."""
+    rng = np.random.default_rng(42)
+    m, n, zeta = 3000, 40, 8
+    sigma = np.logspace(0, -10, n)
+    A, _, _ = wl.planted(rng, m, sigma, complex_=complex_)
+    d = 16 * n
+    S = oracle.sketch_dense_matrix(m, d, zeta, seed=23)
+    eta = _distortion(A, S)
+    assert 0 < eta < 1
+    R = oracle.refined_factor(oracle.sketch(A, d, zeta, seed=23))
+    sv = np.linalg.svd(A @ np.linalg.inv(R), compute_uv=False)
+    slack = 1e-4
+    assert sv.max() ** 2 <= 1.0 / (1.0 - eta) + slack
+    assert sv.min() ** 2 >= 1.0 / (1.0 + eta) - slack
+
+
+def test_refined_solve_matches_the_fp64_solve():
+    """The whole method with the refined factor behaves like the FP64 form on a kappa = 1e10
+    planted problem (tolerance 1e-12 of the 4000 x 50 configuration): the same number of
+    iterations and the same sigma to 1e-10 relative, where the FP32 factor alone needs more."""
+    A, s, V = wl.planted_small_gap_free(m=4000, n=50)
+    r64 = oracle.rlobpcg(A, k=1, seed=3, tau=1e-12, use_stagnation=False)
+    rrf = oracle.rlobpcg(A, k=1, seed=3, tau=1e-12, use_stagnation=False, sketch_precision="f32_refine")
+    r32 = oracle.rlobpcg(A, k=1, seed=3, tau=1e-12, use_stagnation=False, sketch_precision="f32")
+    assert rrf["iters"] == r64["iters"]
+    assert abs(rrf["sigma"][0] - r64["sigma"][0]) <= 1e-10 * r64["sigma"][0]
+    assert rrf["iters"] < r32["iters"]
+
+
 def test_sketch_and_solve_fact():
     """Fact (sketch-and-solve, Sec. 3.1): v0 = P e_n / ||P e_n|| satisfies
     ||A v0||^2 <= (1+eta)/(1-eta) sigma_min(A)^2."""
