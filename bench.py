@@ -579,6 +579,75 @@ def run_reference(args, rank, world):
             "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_block_study(args, rank, world, local_rank):
+    """Block sizes b in {1, 3, 5, 10, 20} on the clustered 1e6 x 2000 matrix of Sec. 4.2 (16 GB
+    FP64, Haar U and V, sigma_i = exp(-log(1e10) ((i-1)/(n-1))^(1/256))), one triplet (k = 1)
+    wanted: per block size the iterations, matrix-vector products (b per iteration), device
+    time of the solve, the relative error of the smallest singular value against the planted one
+    and the sine of the angle of its vector to the planted one, and the per-iteration relative
+    error of the smallest Ritz value. Block sizes up to 16 run the Gram products on the tensor
+    cores, b = 20 on the FP64 CUDA cores."""
+    import torch
+
+    from paper_2602_16797_gb300 import rlobpcg as rl
+    from paper_2602_16797_gb300 import workloads as wl
+    if rank != 0:
+        return None
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    rl.load()
+    m, n = args.study_m, args.study_n
+    A, s_true, V_true = wl.clustered_large_device(m=m, n=n, device=dev)
+    smin, vmin = s_true[-1], V_true[:, -1]
+    gap = (s_true[-2] ** 2 - s_true[-1] ** 2) / s_true[-1] ** 2
+    stream = torch.cuda.current_stream(dev)
+    sigma = torch.empty(1, dtype=torch.float64, device=dev)
+    resid = torch.empty(1, dtype=torch.float64, device=dev)
+    V = torch.empty((n, 1), dtype=torch.float64, device=dev)
+    rows = []
+    blocks = [int(x) for x in args.blocks.split(",")]
+    for i, b in enumerate(blocks):
+        o = rl.rlobpcg_default_opts()
+        o.seed = 1006
+        o.block = b
+        o.max_iter = args.study_max_iter
+        plan = rl.rlobpcg_plan(m, n, 1, rl.RLOBPCG_F64, o, stream.cuda_stream)
+        if i == 0:
+            rl.rlobpcg_solve(plan, A.data_ptr(), n, -1.0, sigma.data_ptr(), V.data_ptr(), None, resid.data_ptr(),
+                             rl.rlobpcg_info())   # warm-up (kernels, clocks)
+        info = rl.rlobpcg_info()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        rl.rlobpcg_solve(plan, A.data_ptr(), n, -1.0, sigma.data_ptr(), V.data_ptr(), None, resid.data_ptr(), info)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        th, rs = rl.rlobpcg_history(plan)
+        rl.rlobpcg_plan_destroy(plan)
+        v = V.cpu().numpy()[:, 0]
+        sin = float(np.sqrt(max(0.0, 1.0 - abs(float(v @ vmin)) ** 2)))
+        err_hist = [float(abs(t - smin) / smin) for t in th[:, -1]]
+        ms_it = info.ms_iterate / max(info.iters, 1)
+        once = info.ms_sketch + info.ms_factor + info.ms_split_a
+        # cost to first reach each relative sigma error: iterations, matvecs (b per iteration plus
+        # the start block), device time (one-time part + iterations at the measured rate)
+        reach = {}
+        for thr in (1e-2, 1e-3, 1e-4, 1e-5, 1e-6, 1e-7, 1e-8):
+            it = next((t for t, e in enumerate(err_hist) if e <= thr), None)
+            reach[f"{thr:g}"] = None if it is None else {"iters": it, "matvecs": b * (it + 1),
+                                                         "ms": once + it * ms_it}
+        rows.append({"b": b, "gram": "split-bf16 tensor cores" if b <= 16 else "fp64 CUDA cores",
+                     "iters": info.iters, "matvecs": info.matvecs, "stop_reason": info.stop_reason,
+                     "ms": e0.elapsed_time(e1), "ms_per_iteration": ms_it, "ms_one_time": once,
+                     "sigma_rel_err": float(abs(sigma.item() - smin) / smin), "vector_sin_angle": sin,
+                     "reach": reach, "sigma_rel_err_history": err_hist})
+    return {"metric": "block-size study (Sec. 4.2): iterations, matvecs, wall-clock and accuracy per block size",
+            "value": None, "unit": None, "n_gpus": 1, "dtype": "f64", "data": "synthetic (seeded; Sec. 4.2 recipe)",
+            "config": {"workload": f"clustered m={m} n={n} k=1, sigma_i = exp(-log(1e10) ((i-1)/(n-1))^(1/256))",
+                       "d": 4 * n, "zeta": 8, "gap_rel": float(gap), "sigma_min": float(smin)},
+            "blocks": rows}
+
+
 def run_serve(args, rank, world, local_rank):
     """Serving stream: half Loewner, half planted requests (m log-uniform in [2e3, 5e5], n uniform
     in [20, 400], k in {1, 2, 4}), HBM admission budget 150 GB. Measures the saturated rate with
@@ -662,7 +731,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["serve_stream"], default=DEFAULT_WORKLOAD)
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["serve_stream", "block_study"], default=DEFAULT_WORKLOAD)
+    ap.add_argument("--blocks", default="1,3,5,10,20", help="block_study: block sizes")
+    ap.add_argument("--study-m", type=int, default=1_000_000, help="block_study: rows")
+    ap.add_argument("--study-n", type=int, default=2000, help="block_study: columns")
+    ap.add_argument("--study-max-iter", type=int, default=0,
+                    help="block_study: iteration cap (0: the paper's, 200 for b = 1 and 100 otherwise)")
     ap.add_argument("--gram", choices=["split", "fp64"], default="split",
                     help="Gram products: split-bf16 on the tensor cores (default) or FP64 CUDA cores")
     ap.add_argument("--fixed-iters", type=int, default=0,
@@ -680,6 +754,8 @@ def main():
         out = run_reference(args, rank, world)
     elif args.workload == "serve_stream":
         out = run_serve(args, rank, world, local_rank)
+    elif args.workload == "block_study":
+        out = run_block_study(args, rank, world, local_rank)
     else:
         out = run_ours(args, rank, world, local_rank)
     replicas.finish(world)

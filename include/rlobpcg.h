@@ -152,6 +152,15 @@ int rlobpcg_solve(rlobpcg_plan_t plan, const void* A, int64_t lda, double tol, d
 /* Release a plan and its device workspace. NULL is accepted. */
 int rlobpcg_plan_destroy(rlobpcg_plan_t plan);
 
+/* Per-iteration history of the plan's last solve (host memory, row-major, b columns, b = the block
+ * size, returned in *block): row 0 holds the Ritz values of the start block's Rayleigh-Ritz step
+ * and its residual norms, row t >= 1 those after iteration t; within a row, the b smallest Ritz
+ * values in descending order (the last is the smallest) and their residual column norms
+ * ||A^H A v_j - theta_j^2 v_j|| -- the quantities the stopping rule of Sec. 2.1 reads. *rows
+ * receives iterations + 1; at most cap_rows rows are copied into theta and resnorm (either may be
+ * NULL). Errors: INVALID_ARG (NULL plan or rows, cap_rows < 0). */
+int rlobpcg_history(rlobpcg_plan_t plan, double* theta, double* resnorm, int cap_rows, int* rows, int* block);
+
 /* Device bytes a plan owns (its workspace; a host-A copy made by solve() is not included). */
 size_t rlobpcg_plan_device_bytes(rlobpcg_plan_t plan);
 

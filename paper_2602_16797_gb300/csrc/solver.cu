@@ -132,6 +132,10 @@ struct rlobpcg_plan_s {
   int hist_slots = 0;
   std::vector<void*> owned;
   size_t bytes = 0;          // device bytes owned by the plan (excluding a host-A copy)
+  // history of the last solve: per iteration t = 0 .. iters, the b Ritz values (the b smallest,
+  // descending; t = 0 is the start block's Rayleigh-Ritz) and the b residual column norms
+  std::vector<double> last_theta, last_res;
+  int last_rows = 0;
 };
 
 namespace {
@@ -309,9 +313,11 @@ int solve_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, double tau, double* s
   RL_CUDA(cudaEventRecord(p->ev[2], st));
 
   StopRule hist;
+  std::vector<double> theta0(b);
   {
     std::vector<double> hr(b);
     RL_CUDA(cudaMemcpyAsync(hr.data(), p->res_norm, b * sizeof(double), cudaMemcpyDeviceToHost, st));
+    RL_CUDA(cudaMemcpyAsync(theta0.data(), p->theta, b * sizeof(double), cudaMemcpyDeviceToHost, st));
     RL_CUDA(cudaStreamSynchronize(st));
     hist.r.push_back(hr);
     hist.th.push_back(std::vector<double>(b, std::numeric_limits<double>::infinity()));
@@ -385,6 +391,15 @@ int solve_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, double tau, double* s
     }
   }
   RL_CUDA(cudaEventRecord(p->ev[3], st));
+  // keep the history for rlobpcg_history (row 0: the start block's Ritz values)
+  p->last_rows = (int)hist.r.size();
+  p->last_theta.assign((size_t)p->last_rows * b, 0.0);
+  p->last_res.assign((size_t)p->last_rows * b, 0.0);
+  for (int t = 0; t < p->last_rows; ++t)
+    for (int j = 0; j < b; ++j) {
+      p->last_res[(size_t)t * b + j] = hist.r[t][j];
+      p->last_theta[(size_t)t * b + j] = t == 0 ? theta0[j] : hist.th[t][j];
+    }
   // outputs (ascending sigma): staged in plan scratch, then copied to host or device pointers
   {
     double* sig_stage = p->res_norm + b;   // k doubles after the b norms
@@ -679,3 +694,13 @@ extern "C" int rlobpcg_plan_destroy(rlobpcg_plan_t p) {
 }
 
 extern "C" size_t rlobpcg_plan_device_bytes(rlobpcg_plan_t p) { return p ? p->bytes : 0; }
+
+extern "C" int rlobpcg_history(rlobpcg_plan_t p, double* theta, double* resnorm, int cap_rows, int* rows, int* block) {
+  if (!p || !rows || cap_rows < 0) return RLOBPCG_ERR_INVALID_ARG;
+  *rows = p->last_rows;
+  if (block) *block = p->b;
+  const int n = std::min(cap_rows, p->last_rows);
+  if (theta) memcpy(theta, p->last_theta.data(), (size_t)n * p->b * sizeof(double));
+  if (resnorm) memcpy(resnorm, p->last_res.data(), (size_t)n * p->b * sizeof(double));
+  return RLOBPCG_OK;
+}

@@ -85,6 +85,7 @@ _SIGS = {
     "rlobpcg_tsqr": (c_int, [c_void_p, c_int64, c_int, c_int64, c_int, c_void_p, c_void_p, c_size_t, c_void_p]),
     "rlobpcg_tsqr_workspace_size": (c_size_t, [c_int64, c_int, c_int]),
     "rlobpcg_plan_device_bytes": (c_size_t, [c_void_p]),
+    "rlobpcg_history": (c_int, [c_void_p, c_void_p, c_void_p, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
     "rlobpcg_plan_workspace_size": (c_size_t, [c_int64, c_int64, c_int, c_int, ctypes.POINTER(rlobpcg_opts)]),
     "rlobpcg_server_create": (c_int, [ctypes.POINTER(c_void_p), c_size_t, c_int, c_int]),
     "rlobpcg_server_submit": (c_int, [c_void_p, c_void_p, c_int64, c_int64, c_int64, c_int, c_int,
@@ -265,6 +266,18 @@ def solve(A, k: int, *, opts: rlobpcg_opts | None = None, tol: float = -1.0, wan
         return sigma, V, U, resid, out
     finally:
         rlobpcg_plan_destroy(plan)
+
+
+def rlobpcg_history(plan: int):
+    """(theta, resnorm) of the plan's last solve as numpy arrays [iterations + 1, b]."""
+    import numpy as np
+    rows, b = c_int(), c_int()
+    _check("rlobpcg_history", load().rlobpcg_history(plan, None, None, 0, ctypes.byref(rows), ctypes.byref(b)))
+    th = np.zeros((rows.value, b.value))
+    rs = np.zeros((rows.value, b.value))
+    _check("rlobpcg_history", load().rlobpcg_history(plan, th.ctypes.data, rs.ctypes.data, rows.value,
+                                                     ctypes.byref(rows), ctypes.byref(b)))
+    return th, rs
 
 
 def rlobpcg_plan_device_bytes(plan: int) -> int:

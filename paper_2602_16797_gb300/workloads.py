@@ -127,12 +127,21 @@ def condition_sweep(seed: int, kappa: float, m: int = 10_000, n: int = 100):
     return planted(rng, m, sigma)
 
 
-def clustered(seed: int, m: int, n: int, a: float = 1.0 / 256.0):
+def clustered_sigma(n: int, a: float = 1.0 / 256.0) -> np.ndarray:
     """Sec. 4.2: sigma_i = exp(-log(1e10) ((i-1)/(n-1))^a), i = 1..n (clustered near the bottom)."""
-    rng = np.random.default_rng(seed)
     i = np.arange(1, n + 1)
-    sigma = np.exp(-np.log(1e10) * ((i - 1) / (n - 1)) ** a)
-    return planted(rng, m, sigma)
+    return np.exp(-np.log(1e10) * ((i - 1) / (n - 1)) ** a)
+
+
+def clustered(seed: int, m: int, n: int, a: float = 1.0 / 256.0):
+    """Sec. 4.2 block-test matrix: Haar U, V and the clustered spectrum of clustered_sigma."""
+    rng = np.random.default_rng(seed)
+    return planted(rng, m, clustered_sigma(n, a))
+
+
+def clustered_large_device(seed: int = SEED_BASE + 6, m: int = 1_000_000, n: int = 2000, device="cuda"):
+    """The 1e6 x 2000 clustered block-test matrix of Sec. 4.2 (16 GB FP64), built on the GPU."""
+    return planted_on_device(seed, m, clustered_sigma(n), device=device)
 
 
 def easy_coherent(seed: int, m: int, n: int):
