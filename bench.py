@@ -414,7 +414,7 @@ def run_ours(args, rank, world, local_rank):
     tdt = torch.complex128 if w["cplx"] else torch.float64
     esz = 16 if w["cplx"] else 8
     stream = torch.cuda.current_stream(dev)
-    split = args.gram == "split" and not w["cplx"] and K <= 16
+    split = args.gram == "split" and not w["cplx"] and K <= 24
     seeds = w["seeds"]
     # one plan per seed: a plan keeps the options it was made with (the seed of S among them)
     plans = [rl.rlobpcg_plan(M, N, K, dtype, _opts(rl, w, sd, w["prec"], args.fixed_iters, args.gram),
@@ -585,8 +585,8 @@ def run_block_study(args, rank, world, local_rank):
     wanted: per block size the iterations, matrix-vector products (b per iteration), device
     time of the solve, the relative error of the smallest singular value against the planted one
     and the sine of the angle of its vector to the planted one, and the per-iteration relative
-    error of the smallest Ritz value. Block sizes up to 16 run the Gram products on the tensor
-    cores, b = 20 on the FP64 CUDA cores."""
+    error of the smallest Ritz value. Every block size runs the Gram products on the tensor
+    cores (split-bf16 digits, b <= 24)."""
     import torch
 
     from paper_2602_16797_gb300 import rlobpcg as rl
@@ -636,7 +636,7 @@ def run_block_study(args, rank, world, local_rank):
             it = next((t for t, e in enumerate(err_hist) if e <= thr), None)
             reach[f"{thr:g}"] = None if it is None else {"iters": it, "matvecs": b * (it + 1),
                                                          "ms": once + it * ms_it}
-        rows.append({"b": b, "gram": "split-bf16 tensor cores" if b <= 16 else "fp64 CUDA cores",
+        rows.append({"b": b, "gram": "split-bf16 tensor cores" if b <= 24 else "fp64 CUDA cores",
                      "iters": info.iters, "matvecs": info.matvecs, "stop_reason": info.stop_reason,
                      "ms": e0.elapsed_time(e1), "ms_per_iteration": ms_it, "ms_one_time": once,
                      "sigma_rel_err": float(abs(sigma.item() - smin) / smin), "vector_sin_angle": sin,

@@ -84,7 +84,7 @@ typedef struct {
                            clustered top spectrum; it only scales the stop tolerance)           */
   int gram_split;       /* 1 (default): run the Gram products on the tensor cores by an exact split
                            of A, W and A W into bf16 digits (rlobpcg_gram_split; about FP64
-                           accuracy). Real FP64 and b <= 16 only (ignored otherwise); A is split
+                           accuracy). Real FP64 and b <= 24 only (ignored otherwise); A is split
                            once per solve into about 16 bytes of device memory per element of A.
                            0: the FP64 CUDA-core Gram pass (rlobpcg_gram).                    */
   double tau;           /* tolerance of ||R(:,j)|| <= Sigma~(1,1)^2 tau; < 0 means 2 sqrt(n) 2^-52 */
@@ -302,14 +302,15 @@ int rlobpcg_gram_noalloc(const void* A, int64_t m, int64_t n, int64_t lda, int d
  * eight signed 7-bit digits (exact in bf16) under a power-of-two scale per group -- a row of A for
  * A W, a column of A within each 128-row chunk for A^T AW, a column of W, a column of AW within
  * each chunk (the Ozaki scheme). Digit products accumulate exactly (as integers below 2^24) in the
- * tensor cores' f32 accumulators and are recombined in FP64. Per product term the error is about
- * 2^-55 times the product of the two group maxima.
+ * tensor cores' f32 accumulators and are recombined in FP64; the 43 digit pairs of levels
+ * p + q <= 8 are formed (the others weigh below 2^-60 of the leading term). Per product term the
+ * error is about 2^-55 times the product of the two group maxima.
  *   rlobpcg_gram_split_prepare: split A (m x n, row-major, lda) once -- it is constant through a
  *     solve -- into prep, rlobpcg_gram_split_prepare_size(m, n) bytes of device memory (about 16
  *     bytes per element of A: one byte per digit, in the layouts of both products). Errors as
  *     below; NONFINITE when A holds Inf or NaN.
  *   rlobpcg_gram_split: one pass; W (n x b, ldw), AW (m x b, ldaw), G (n x b, ldg) row-major,
- *     1 <= b <= 16; work: rlobpcg_gram_split_workspace_size(m, n, b) bytes of device scratch.
+ *     1 <= b <= 24; work: rlobpcg_gram_split_workspace_size(m, n, b) bytes of device scratch.
  * All pointers are device memory owned by the caller; calls are asynchronous on `stream` and
  * synchronise it before returning. prep also holds a few counters that each pass uses and leaves
  * at zero, so passes on one prep must not overlap. Errors: INVALID_ARG (sizes, NULL, buffers too small),

@@ -15,17 +15,25 @@
 // with |error| <= 2^(E-56). A digit is exact in bf16 and a digit product (|.| <= 2^12) is exact.
 //
 // Products. For a digit pair (p, q) the tensor core forms sum_k a_p[k] b_q[k] in f32. Pairs of
-// the same level l = p + q share one accumulator: the MMA for A-digit p writes its N = 8 x BP
-// output columns (B-digits q = 0..7, BP columns each) at TMEM column offset BP * p, so pair
-// (p, q) lands on columns BP * l + j. A level holds at most 8 pairs, so with at most 512 terms
-// per accumulation |L_l| <= 8 * 512 * 2^12 = 2^24 and the f32 accumulator is exact (integers).
+// the same level l = p + q share one accumulator: the MMA for A-digit p writes its output
+// columns (B-digits q, BP columns each) at TMEM column offset BP * p, so pair (p, q) lands on
+// columns BP * l + j. Only levels l <= 8 are kept: a level-9 term is at most 2^12 2^(-7 * 11)
+// = 2^-65 of 2^(E+F+2) and the six of them (with everything above) stay below 2^-60 of the
+// leading term, far under the 2^-55 of the digit truncation itself. The MMA of A-digit p
+// therefore spans only the B-digits q <= 8 - p (N = BP min(8, 9 - p), rounded up to the MMA's
+// granularity of 16: the rounding adds a few level >= 9 products in columns that are never
+// read), 43 of the 64 pairs. A level holds at most 8 pairs, so with at most 512 terms per
+// accumulation |L_l| <= 8 * 512 * 2^12 = 2^24 and the f32 accumulator is exact (integers).
 // The result is then
-//     2^(E+F-12) sum_{l=0}^{14} 2^(-7 l) L_l,
-// evaluated as: levels 14..5 by Horner's rule in f32 (their weight is below 2^-35 of level 0,
+//     2^(E+F-12) sum_{l=0}^{8} 2^(-7 l) L_l,
+// evaluated as: levels 8..5 by Horner's rule in f32 (their weight is below 2^-35 of level 0,
 // so f32 rounding there stays below 2^-59 of the leading term), levels 4..0 exactly as one int64
 // (sum L_l 2^(7 (4 - l)) < 2^53), the two joined and scaled in FP64. The error
 // is that of the digit truncation, about 2^-55 of the group maxima per term, which is the size
 // of an FP64 dot product's own rounding. Tensor cores do the O(m n b) work; FP64 does O((m+n) b).
+// BP, the block width of the digits of W and A W, is 8, 12, 16 or 24 (b <= 24): levels 0..8
+// of BP columns take 128 TMEM columns for BP <= 12 (two accumulator buffers and two A stages fit
+// in TMEM) and 256 above.
 //
 // Layouts. A is split once per solve and kept as one BYTE per digit, u_p = d_p + 64 in [0, 127]
 // (8 bytes per element, as many as the FP64 value itself); the kernel expands them to bf16 on
@@ -42,9 +50,9 @@
 // second. W and AW are split once per pass, straight into bf16 digit tiles.
 //
 // Kernel shape: one CTA per SM, 448 threads. Warp 0 streams the A digit bytes and the B digits
-// of each stage (two k-blocks when A goes through TMEM, else one) into a ring of six staging
+// of each stage (two k-blocks when A goes through TMEM, else one) into a ring of five or six staging
 // slots with bulk copies; warps 6-13 expand each stage's bytes into the eight bf16 digit tiles -- in TMEM beside
-// the accumulators for b <= 8 (the MMAs then read A without shared-memory traffic), else in
+// the accumulators for BP <= 12 (the MMAs then read A without shared-memory traffic), else in
 // shared memory; warp 1 owns TMEM and issues the MMAs from one thread, B read in the staging
 // slot; warps 2-5 read the accumulators (two TMEM buffers, so reading one unit overlaps the MMAs
 // of the next), zero them, and do the FP64 recombination. The last CTA of each column tile of
@@ -69,14 +77,39 @@ using split::SPLIT_W_READY;
 constexpr int TM = 128;                // MMA M: rows (first product) or columns (second) per tile
 constexpr int KC_KB = 32;              // k-blocks per exact accumulation: 32 x 16 = 512 terms
 constexpr int CH_KB = TM / TK;         // k-blocks per 128-row chunk of the second product
-// bf16 digit stages (MMA operands): in TMEM (b <= 8) two stages of two k-blocks fit beside the two
-// accumulator buffers; in shared memory three stages of one k-block
+constexpr int NLEV = 9;                // digit-pair levels kept (l = p + q <= 8)
+// TMEM columns of one accumulator buffer, and whether the A digits go through TMEM (BP <= 12:
+// two stages of two k-blocks fit beside the two buffers) or shared memory
+template <int BP> constexpr uint32_t accw() { return NLEV * BP <= 128 ? 128u : 256u; }
+template <int BP> constexpr bool ta_of() { return accw<BP>() == 128u; }
+// B rows (digits x BP) the MMA of A-digit p reads: the digits q <= 8 - p, rounded up to 16
+__host__ __device__ constexpr int np_of(int BP, int p) {
+  return ((((9 - p) < 8 ? (9 - p) : 8) * BP + 15) / 16) * 16;
+}
+// every MMA's output columns [BP p, BP p + np_of(BP, p)) lie inside one accumulator buffer, and
+// its B rows inside the 8 BP rows of the B tile
+template <int BP>
+constexpr bool mma_cols_fit() {
+  for (int p = 0; p < SL; ++p)
+    if (BP * p + np_of(BP, p) > (int)accw<BP>() || np_of(BP, p) > SL * BP || np_of(BP, p) < 16) return false;
+  return true;
+}
+// bf16 digit stages (MMA operands): in TMEM two stages of two k-blocks; in shared memory three
+// stages of one k-block
 template <bool TA> constexpr int nst() { return TA ? 2 : 3; }
 template <bool TA> constexpr int kps() { return TA ? 2 : 1; }   // k-blocks per stage
 // staging slots (bulk copies in flight), each the A digit bytes of a stage and its B digits: the
 // bf16 A stages take 32 KB of shared memory each when the MMAs read A from there, none when A
-// goes through TMEM (b <= 8)
-template <bool TA> constexpr int nsb() { return TA ? 6 : 6; }
+// goes through TMEM; as many slots as fit in 227 KB, at most six
+constexpr size_t kSmemMax = 227 * 1024;
+template <int BP> constexpr size_t slot_bytes() { return (size_t)kps<ta_of<BP>()>() * (TM * TK * SL + SL * BP * TK * 2); }
+template <int BP> constexpr size_t fixed_smem() {
+  return (size_t)nst<ta_of<BP>()>() * (ta_of<BP>() ? 0 : SL * TM * TK * 2) + 512 + 2 * 4 * BP * sizeof(double);
+}
+template <int BP> constexpr int nsb() {
+  return (int)((kSmemMax - fixed_smem<BP>()) / slot_bytes<BP>() < 6 ? (kSmemMax - fixed_smem<BP>()) / slot_bytes<BP>() : 6);
+}
+template <int BP> constexpr size_t pass_smem() { return fixed_smem<BP>() + (size_t)nsb<BP>() * slot_bytes<BP>(); }
 constexpr int SLICE_BYTES = TM * TK * 2;   // one bf16 digit tile
 constexpr int TILE_U8 = TM * TK * SL;      // the byte digits of one 128 x 16 tile (all 8 digits)
 constexpr int NCW = 8;                     // converter warps (one 64-byte unit per thread per stage)
@@ -114,7 +147,7 @@ struct WorkLayout {
 WorkLayout work_layout(int64_t m, int64_t n, int b) {
   const Dims d = dims_of(m, n);
   WorkLayout L;
-  L.BP = b <= 8 ? 8 : 16;
+  L.BP = b <= 8 ? 8 : b <= 12 ? 12 : b <= 16 ? 16 : 24;
   const int N = SL * L.BP;
   L.NR = (int)std::max<int64_t>(1, std::min<int64_t>(d.R1, num_sms() / std::max<int64_t>(1, d.CT)));
   size_t off = 0;
@@ -417,84 +450,75 @@ __device__ __forceinline__ void ld_level8(uint32_t taddr, uint32_t (&r)[BP], int
   tc::tmem_ld8(taddr, r[h], r[h + 1], r[h + 2], r[h + 3], r[h + 4], r[h + 5], r[h + 6], r[h + 7]);
 }
 
-// Reads one accumulator buffer (levels 0..14 of BP columns), zeroes it for reuse, releases it,
-// and returns s_j = 2^28 sum_l 2^(-7 l) L_l[j]. Levels 4..0 are integers below 2^24 held exactly
-// in f32, so S = sum_{l<=4} L_l 2^(7 (4 - l)) is an exact int64 below 2^53 and converts to FP64
-// exactly: three FP64-pipe instructions per column instead of a five-step FP64 Horner with its
-// conversions (the FP64 pipe is the scarce one in the epilogue).
-template <int BP>
-__device__ __forceinline__ void drain_levels(uint32_t ta, uint64_t* release, int b, double (&s)[BP]) {
-  float t[BP];
-  uint32_t r[5][BP];
-  // levels 14..10
+// Reads one accumulator buffer (levels 0..8 of BP columns) eight columns at a time, hands
+// s_j = 2^28 sum_l 2^(-7 l) L_l[j] of every column j < b to put(j, s_j), then zeroes the buffer
+// for reuse and releases it. Levels 4..0 are integers below 2^24 held exactly in f32, so
+// S = sum_{l<=4} L_l 2^(7 (4 - l)) is an exact int64 below 2^53 and converts to FP64 exactly;
+// levels 8..5 by Horner's rule in f32: three FP64-pipe instructions per column (the FP64 pipe is
+// the scarce one in the epilogue).
+template <int BP, class Put>
+__device__ __forceinline__ void drain_levels(uint32_t ta, uint64_t* release, int b, Put put) {
+  constexpr int BR = (BP + 7) / 8 * 8;
 #pragma unroll
-  for (int l = 0; l < 5; ++l)
+  for (int h = 0; h < BR; h += 8) {
+    // levels 8..5 (Horner in f32), then levels 0..4 (exact int64): two waits, a smaller peak
+    uint32_t r[5][8];
+    float t[8];
 #pragma unroll
-    for (int h = 0; h < BP; h += 8) ld_level8(ta + BP * (14 - l) + h, r[l], h);
-  tc::tmem_ld_wait();
+    for (int l = 0; l < 4; ++l)
+      tc::tmem_ld8(ta + BP * (8 - l) + h, r[l][0], r[l][1], r[l][2], r[l][3], r[l][4], r[l][5], r[l][6], r[l][7]);
+    tc::tmem_ld_wait();
 #pragma unroll
-  for (int j = 0; j < BP; ++j) {
-    t[j] = __uint_as_float(r[0][j]);
+    for (int jj = 0; jj < 8; ++jj) {
+      t[jj] = __uint_as_float(r[0][jj]);
 #pragma unroll
-    for (int l = 1; l < 5; ++l) t[j] = fmaf(t[j], 0x1p-7f, __uint_as_float(r[l][j]));
+      for (int l = 1; l < 4; ++l) t[jj] = fmaf(t[jj], 0x1p-7f, __uint_as_float(r[l][jj]));
+    }
+#pragma unroll
+    for (int l = 0; l < 5; ++l)
+      tc::tmem_ld8(ta + BP * l + h, r[l][0], r[l][1], r[l][2], r[l][3], r[l][4], r[l][5], r[l][6], r[l][7]);
+    tc::tmem_ld_wait();
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) {
+      const int j = h + jj;
+      if (j < BP && j < b) {
+        long long S = __float2int_rn(__uint_as_float(r[0][jj]));
+#pragma unroll
+        for (int l = 1; l <= 4; ++l) S = S * 128 + __float2int_rn(__uint_as_float(r[l][jj]));
+        put(j, fma((double)t[jj], 0x1p-7, __ll2double_rn(S)));
+      }
+    }
   }
-  // levels 9..5
-#pragma unroll
-  for (int l = 0; l < 5; ++l)
-#pragma unroll
-    for (int h = 0; h < BP; h += 8) ld_level8(ta + BP * (9 - l) + h, r[l], h);
-  tc::tmem_ld_wait();
-#pragma unroll
-  for (int j = 0; j < BP; ++j)
-#pragma unroll
-    for (int l = 0; l < 5; ++l) t[j] = fmaf(t[j], 0x1p-7f, __uint_as_float(r[l][j]));
-  // levels 4..0
-#pragma unroll
-  for (int l = 0; l < 5; ++l)
-#pragma unroll
-    for (int h = 0; h < BP; h += 8) ld_level8(ta + BP * (4 - l) + h, r[l], h);
-  tc::tmem_ld_wait();
   // the buffer is free again once it is zero
-  constexpr uint32_t ACCW = BP == 8 ? 128 : 256;
+  constexpr uint32_t ACCW = accw<BP>();
 #pragma unroll
   for (uint32_t c = 0; c < ACCW; c += 8) tc::tmem_st8_zero(ta + c);
   tc::tmem_st_wait();
   tc::fence_before_sync();
   tc::mbar_arrive(release);
-#pragma unroll
-  for (int j = 0; j < BP; ++j) {
-    if (j < b) {
-      // r[l] holds level 4 - l
-      long long S = __float2int_rn(__uint_as_float(r[4][j]));
-#pragma unroll
-      for (int l = 3; l >= 0; --l) S = S * 128 + __float2int_rn(__uint_as_float(r[l][j]));
-      s[j] = fma((double)t[j], 0x1p-7, __ll2double_rn(S));
-    } else {
-      s[j] = 0;
-    }
-  }
 }
 
 // MODE 0: AW = A W (+ digits of AW). MODE 1: partial G = A^T AW over each CTA's row chunks.
 template <int BP, int MODE>
 __global__ void __launch_bounds__(NTH, 1) split_pass_kernel(PassArgs g) {
   constexpr int N = SL * BP;
-  constexpr uint32_t ACCW = BP == 8 ? 128 : 256;
+  constexpr uint32_t ACCW = accw<BP>();
   constexpr uint32_t BBYTES = N * TK * 2;
-  // b <= 8: the A digits of a stage go to TMEM (8 columns per digit, after the two accumulator
+  static_assert(BP % 4 == 0 && mma_cols_fit<BP>(), "digit block width outside the TMEM layout");
+  static_assert(nsb<BP>() >= 4 && pass_smem<BP>() <= kSmemMax, "staging ring does not fit in shared memory");
+  // BP <= 12: the A digits of a stage go to TMEM (8 columns per digit, after the two accumulator
   // buffers), so shared memory holds only B and the MMAs read A without shared-memory traffic
-  constexpr bool TA = BP == 8;
+  constexpr bool TA = ta_of<BP>();
   // A stage covers KPS k-blocks (a unit of KC_KB or CH_KB k-blocks -- both even -- never splits
   // a stage; the last stage of a unit may hold one k-block)
   constexpr int KPS = kps<TA>();
   constexpr uint32_t STG = TA ? 0 : SL * SLICE_BYTES;      // bf16 A stage in shared memory
   constexpr uint32_t SLOT = KPS * (TILE_U8 + BBYTES);      // staging slot: KPS A byte tiles, KPS B tiles
-  constexpr int NSB = nsb<TA>();
+  constexpr int NSB = nsb<BP>();
   constexpr int NST = nst<TA>();
   constexpr uint32_t TCOLS = TA ? 512 : 2 * ACCW;
   constexpr uint32_t ACOL0 = 2 * ACCW;   // TMEM column of the A digits of stage 0 (TA)
   constexpr uint32_t ASTW = 64 * KPS;    // TMEM columns of one A stage (TA)
-  constexpr uint32_t IDESC = tc::idesc_bf16_f32(TM, N);
   extern __shared__ __align__(1024) unsigned char sm[];
   unsigned char* bring = sm + NST * STG;   // staging slots, SLOT bytes each
   uint64_t* full = reinterpret_cast<uint64_t*>(bring + NSB * SLOT);
@@ -589,11 +613,13 @@ __global__ void __launch_bounds__(NTH, 1) split_pass_kernel(PassArgs g) {
                 tc::smem_desc(bring + (size_t)ds * SLOT + KPS * TILE_U8 + q * BBYTES, (N / 8) * 128, 128);
 #pragma unroll
             for (int p = 0; p < SL; ++p) {
+              // A-digit p against the B-digits of levels p + q <= 8 only
+              const uint32_t idesc = tc::idesc_bf16_f32(TM, np_of(BP, p));
               if (TA)
                 tc::mma_bf16_ta(dbase + (uint32_t)(BP * p), tmem + ACOL0 + (uint32_t)(ASTW * s + 64 * q + 8 * p), bdesc,
-                                IDESC, 1u);
+                                idesc, 1u);
               else
-                tc::mma_bf16(dbase + (uint32_t)(BP * p), tc::smem_desc(stg + p * SLICE_BYTES, 2048, 128), bdesc, IDESC,
+                tc::mma_bf16(dbase + (uint32_t)(BP * p), tc::smem_desc(stg + p * SLICE_BYTES, 2048, 128), bdesc, idesc,
                              1u);
             }
           }
@@ -644,12 +670,9 @@ __global__ void __launch_bounds__(NTH, 1) split_pass_kernel(PassArgs g) {
           ok = epi_wait(accf + a, (v >> 1) & 1);
           if (!ok) break;
           tc::fence_after_sync();
-          double s[BP];
-          drain_levels<BP>(tq + (uint32_t)a * ACCW, acce + a, g.b, s);
+          drain_levels<BP>(tq + (uint32_t)a * ACCW, acce + a, g.b,
+                           [&](int j, double sj) { y[j] += split::mul_pow2(sj, Ei + Fj[j] - 40); });
           ++v;
-#pragma unroll
-          for (int j = 0; j < BP; ++j)
-            if (j < g.b) y[j] += split::mul_pow2(s[j], Ei + Fj[j] - 40);
         }
         if (!ok) break;
         if (i < g.m)
@@ -670,13 +693,11 @@ __global__ void __launch_bounds__(NTH, 1) split_pass_kernel(PassArgs g) {
         ok = epi_wait(accf + a, (v >> 1) & 1);
         if (!ok) break;
         tc::fence_after_sync();
-        double s[BP];
-        drain_levels<BP>(tq + (uint32_t)a * ACCW, acce + a, g.b, s);
-        ++v;
         const int Ec = g.eA[rc * g.NC + c];
-#pragma unroll
-        for (int j = 0; j < BP; ++j)
-          if (j < g.b) acc[j] += split::mul_pow2(s[j], Ec + g.eB[rc * BP + j] - 40);
+        const int* eBr = g.eB + rc * BP;
+        drain_levels<BP>(tq + (uint32_t)a * ACCW, acce + a, g.b,
+                         [&](int j, double sj) { acc[j] += split::mul_pow2(sj, Ec + eBr[j] - 40); });
+        ++v;
       }
       double* out = g.part + (size_t)(rng * g.NC + c) * BP;
 #pragma unroll
@@ -784,10 +805,7 @@ __global__ void __launch_bounds__(NTH, 1) split_pass_kernel(PassArgs g) {
 
 template <int BP, int MODE>
 int launch_pass(const PassArgs& a, int grid, cudaStream_t st) {
-  constexpr bool TA = BP == 8;
-  constexpr uint32_t STG = TA ? 0 : SL * SLICE_BYTES;
-  constexpr uint32_t SLOT = kps<TA>() * (TILE_U8 + SL * BP * TK * 2);
-  const size_t smem = (size_t)nst<TA>() * STG + (size_t)nsb<TA>() * SLOT + 512 + 2 * 4 * BP * sizeof(double);
+  const size_t smem = pass_smem<BP>();
   RL_TRY(allow_dynamic_smem(split_pass_kernel<BP, MODE>, smem));
   split_pass_kernel<BP, MODE><<<grid, NTH, smem, st>>>(a);
   RL_CHECK_LAUNCH();
@@ -846,7 +864,7 @@ int split_gram_bp(const unsigned char* prep, int64_t m, int64_t n, const double*
 size_t split_prep_bytes(int64_t m, int64_t n) { return (m < 1 || n < 1) ? 0 : prep_layout(m, n).total; }
 
 size_t split_work_bytes(int64_t m, int64_t n, int b) {
-  return (m < 1 || n < 1 || b < 1 || b > 16) ? 0 : work_layout(m, n, b).total;
+  return (m < 1 || n < 1 || b < 1 || b > 24) ? 0 : work_layout(m, n, b).total;
 }
 
 int split_prepare(const double* A, int64_t m, int64_t n, int64_t lda, void* prep, size_t prep_bytes, int* err,
@@ -885,15 +903,16 @@ int split_gram(const void* prep, int64_t m, int64_t n, const double* W, int b, i
                double* G, int64_t ldg, void* work, size_t work_bytes, int flags, int* err, cudaEvent_t mid,
                cudaStream_t st) {
   const bool resid_mode = (flags & SPLIT_RESID) != 0;
-  if (!prep || !AW || !G || !work || m < 1 || n < 1 || b < 1 || b > 16 || ldaw < b || ldg < b ||
+  if (!prep || !AW || !G || !work || m < 1 || n < 1 || b < 1 || b > 24 || ldaw < b || ldg < b ||
       (!resid_mode && (!W || ldw < b)))
     return RLOBPCG_ERR_INVALID_ARG;
   if (work_bytes < split_work_bytes(m, n, b)) return RLOBPCG_ERR_INVALID_ARG;
-  if (b <= 8)
-    return split_gram_bp<8>((const unsigned char*)prep, m, n, W, b, ldw, AW, ldaw, G, ldg, (unsigned char*)work,
-                            flags, err, mid, st);
-  return split_gram_bp<16>((const unsigned char*)prep, m, n, W, b, ldw, AW, ldaw, G, ldg, (unsigned char*)work,
-                           flags, err, mid, st);
+  const unsigned char* pp = (const unsigned char*)prep;
+  unsigned char* wk = (unsigned char*)work;
+  if (b <= 8) return split_gram_bp<8>(pp, m, n, W, b, ldw, AW, ldaw, G, ldg, wk, flags, err, mid, st);
+  if (b <= 12) return split_gram_bp<12>(pp, m, n, W, b, ldw, AW, ldaw, G, ldg, wk, flags, err, mid, st);
+  if (b <= 16) return split_gram_bp<16>(pp, m, n, W, b, ldw, AW, ldaw, G, ldg, wk, flags, err, mid, st);
+  return split_gram_bp<24>(pp, m, n, W, b, ldw, AW, ldaw, G, ldg, wk, flags, err, mid, st);
 }
 
 }  // namespace rl

@@ -1050,7 +1050,7 @@ __global__ void __launch_bounds__(256) bcgs2_orth_smem_kernel(T* __restrict__ Tb
   T* sv = dg + b;
   double* red = reinterpret_cast<double*>(sv + b);   // NW x 16 column maxima
   __shared__ T sh_inv;
-  __shared__ int Fs[16];
+  __shared__ int Fs[32];   // digit-block width of the split Gram pass, <= 32
   auto bcol = [&](int j) { return j < b ? j : (2 * b + (j - b)); };
   for (int e = tid; e < n * b; e += NT) {
     const int k = e / b, cw = e % b;
@@ -1312,7 +1312,7 @@ __global__ void __launch_bounds__(256) bcgs2_orth_coop_kernel(T* __restrict__ Tb
   T* dl = sv + b;                           // local betas (unused after the stack)
   T* dg = dl + b;                           // stack betas = diag(R)
   __shared__ T sh_inv;
-  __shared__ int Fs[16];
+  __shared__ int Fs[32];   // digit-block width of the split Gram pass, <= 32
   T* gP0 = gs;
   T* gP1 = gP0 + (size_t)G * QB;
   T* gR = gP1 + (size_t)G * QB;
@@ -1400,13 +1400,13 @@ __global__ void __launch_bounds__(256) bcgs2_orth_coop_kernel(T* __restrict__ Tb
         mx = fmax(mx, a);
       }
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (lane == 0) gmx[(size_t)g * 16 + cc] = mx;
+    if (lane == 0) gmx[(size_t)g * 32 + cc] = mx;
   }
   if (__syncthreads_or(bad) && tid == 0) atomicOr(err, DEV_ERR_NONFINITE);
   grid.sync();
   if (tid < BP) {
     double mx = 0;
-    for (int h = 0; h < G; ++h) mx = fmax(mx, __ldcg(gmx + (size_t)h * 16 + tid));
+    for (int h = 0; h < G; ++h) mx = fmax(mx, __ldcg(gmx + (size_t)h * 32 + tid));
     Fs[tid] = split::group_exp(mx);
     if (g == 0) wd.F[tid] = Fs[tid];
   }
@@ -1722,7 +1722,7 @@ template int bcgs2_orth_launch<cd>(cd*, int, int, int64_t, int, int, cd*, int, c
 size_t bcgs2_coop_bytes(int64_t n, int qmax, int b, size_t esz) {
   const int64_t G = 16;
   (void)n;
-  return ((size_t)2 * G * qmax * b + (size_t)G * b * b) * esz + (size_t)G * 16 * sizeof(double) + 256;
+  return ((size_t)2 * G * qmax * b + (size_t)G * b * b) * esz + (size_t)G * 32 * sizeof(double) + 256;
 }
 
 template <class S, class T>

@@ -496,7 +496,7 @@ int resolve_plan_args(int64_t m, int64_t n, int k, int dtype, const rlobpcg_opts
   return RLOBPCG_OK;
 }
 
-bool uses_split(const rlobpcg_opts& o, int dtype, int b) { return o.gram_split && dtype == RLOBPCG_F64 && b <= 16; }
+bool uses_split(const rlobpcg_opts& o, int dtype, int b) { return o.gram_split && dtype == RLOBPCG_F64 && b <= 24; }
 
 // Every device buffer of a plan, in one place: with p == nullptr only the bytes are summed.
 struct PlanAlloc {

@@ -4,8 +4,8 @@ one wanted triplet (k = 1), on a row-reduced copy that the oracle runs in second
 Per block size, in fixed-iteration mode: the smallest Ritz value after every iteration (the
 history the study reports, read back with rlobpcg_history) against the oracle's, the final
 triplet against the oracle's (bars of tests/parity.py), the matrix-vector count b (iterations + 1)
-of Sec. 4.2's cost model, and the history's last row against the returned sigma. b = 20 runs the
-Gram products on the FP64 CUDA cores (the tensor-core path takes b <= 16).
+of Sec. 4.2's cost model, and the history's last row against the returned sigma. Every block size
+runs the Gram products on the tensor cores (digit-block widths 8, 12 and 24).
 """
 import numpy as np
 import pytest

@@ -3,7 +3,9 @@
 The products are those of the Gram pass of Alg. 2 (A W and A^T (A W)). Bounds: a split operand
 is exact to 2^-56 of its group maximum (E of the group, |x| < 2^E, error <= 2^(E-56) <= 2^-55
 max), so a product term a w carries at most 2^-55 (max_a |w| + |a| max_w) plus FP64 rounding of
-the recombination; the oracle's own product adds the usual n u |A||W|.
+the recombination; the digit pairs of levels above 8, which the pass does not form, weigh below
+2^-58 of max_a max_w per term; the oracle's own product adds the usual n u |A||W|. Block widths
+cover every digit-block width of the pass (8, 12, 16, 24).
 """
 import numpy as np
 import pytest
@@ -84,7 +86,9 @@ def test_integer_operands_give_exact_products():
 
 
 @pytest.mark.parametrize("m,n,b", [(1, 1, 1), (127, 16, 3), (129, 17, 5), (2999, 500, 5), (5000, 700, 10),
-                                   (3001, 300, 8), (2048, 128, 9), (4097, 1000, 16), (1000, 40, 2)])
+                                   (3001, 300, 8), (2048, 128, 9), (4097, 1000, 16), (1000, 40, 2),
+                                   (3000, 257, 11), (2500, 600, 12), (129, 33, 13), (4097, 300, 17),
+                                   (3000, 1030, 20), (1500, 96, 24)])
 def test_products_against_oracle(m, n, b):
     rng = np.random.default_rng(m * 7 + n + b)
     A = rng.standard_normal((m, n))
@@ -125,16 +129,16 @@ def test_invalid_and_nonfinite():
     ps = rl.rlobpcg_gram_split_prepare_size(m, n)
     prep = torch.empty(ps, dtype=torch.uint8, device="cuda")
     rl.rlobpcg_gram_split_prepare(A.data_ptr(), m, n, n, prep.data_ptr(), ps, _stream())
-    assert rl.rlobpcg_gram_split_workspace_size(m, n, 17) == 0
+    assert rl.rlobpcg_gram_split_workspace_size(m, n, 25) == 0
     ws = rl.rlobpcg_gram_split_workspace_size(m, n, 4)
     work = torch.empty(ws, dtype=torch.uint8, device="cuda")
     W = np.ones((n, 4))
     W[3, 2] = np.nan
     Wd = _dev(W)
-    AW = torch.empty((m, 17), dtype=torch.float64, device="cuda")
-    G = torch.empty((n, 17), dtype=torch.float64, device="cuda")
+    AW = torch.empty((m, 25), dtype=torch.float64, device="cuda")
+    G = torch.empty((n, 25), dtype=torch.float64, device="cuda")
     with pytest.raises(rl.RlobpcgError) as e:
-        rl.rlobpcg_gram_split(prep.data_ptr(), m, n, Wd.data_ptr(), 17, 17, AW.data_ptr(), 17, G.data_ptr(), 17,
+        rl.rlobpcg_gram_split(prep.data_ptr(), m, n, Wd.data_ptr(), 25, 25, AW.data_ptr(), 25, G.data_ptr(), 25,
                               work.data_ptr(), ws, _stream())
     assert e.value.code == rl.RLOBPCG_ERR_INVALID_ARG
     with pytest.raises(rl.RlobpcgError) as e:
