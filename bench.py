@@ -42,7 +42,7 @@ from paper_2602_16797_gb300 import replicas  # noqa: E402
 
 METRIC = "solve time & solves/s at stated σ/angle error; fused AᴴAX GB/s; p50/p99 latency"
 FP64_UNITS_PER_SM_CLK = 2  # DFMA per clock per SM: 1.25 TFLOP/s nominal / (152 SMs * 2.07 GHz * 2 flop)
-DIGIT_PAIRS = 64           # digit pairs per product of the split-bf16 Gram pass (8 x 8 digits)
+DIGIT_PAIRS = 43           # digit pairs per product of the split-bf16 Gram pass (levels p + q <= 8 of 8 x 8)
 
 
 def _host_pair(m):

@@ -33,11 +33,11 @@ def test_pass_tensor_flops_count_both_products_over_all_digit_pairs():
 def test_roofline_takes_the_slower_roof_as_the_bound():
     peaks = {"hbm_gbs": 6779.0, "bf16_tflops_sustained": 1710.4}
     m, n = 1000000, 1000
-    # b = 10: tensor work 2.56e12 flop (1.50 ms) against 8.08 GB (1.19 ms): tensor-bound
-    r = bench.gram_roofline(m, n, 10, False, True, 3.0e-3, peaks, 1.26, "derived")
+    # b = 20: tensor work 3.44e12 flop (2.01 ms) against 8.16 GB (1.20 ms): tensor-bound
+    r = bench.gram_roofline(m, n, 20, False, True, 3.0e-3, peaks, 1.26, "derived")
     assert r["bound"] == "tensor" and r["other"]["bound"] == "hbm"
-    assert r["frac"] == pytest.approx(bench.pass_tensor_flops(m, n, 10) / 3.0e-3 / 1e12 / 1710.4)
-    assert r["other"]["frac"] == pytest.approx(bench.pass_algorithmic_bytes(m, n, 10, False) / 3.0e-3 / 1e9 / 6779.0)
+    assert r["frac"] == pytest.approx(bench.pass_tensor_flops(m, n, 20) / 3.0e-3 / 1e12 / 1710.4)
+    assert r["other"]["frac"] == pytest.approx(bench.pass_algorithmic_bytes(m, n, 20, False) / 3.0e-3 / 1e9 / 6779.0)
     # b = 1: 0.26e12 flop (0.15 ms) against 8.01 GB (1.18 ms): HBM-bound
     r = bench.gram_roofline(m, n, 1, False, True, 2.0e-3, peaks, 1.26, "derived")
     assert r["bound"] == "hbm" and r["other"]["bound"] == "tensor"
