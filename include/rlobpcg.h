@@ -215,6 +215,18 @@ int rlobpcg_server_stats(rlobpcg_server_t s, int64_t* completed, double* p50_ms,
  * on this server may start during or after it. */
 int rlobpcg_server_destroy(rlobpcg_server_t s);
 
+/*
+ * Health check of the bounded-wait path (an addition of this library; the paper has no
+ * counterpart). Every device-side wait of the library gives up after a bounded number of tries,
+ * records the timeout, releases what its kernel holds and returns, so that a lost arrival surfaces
+ * as RLOBPCG_ERR_TIMEOUT instead of a hung GPU. This call runs a kernel that holds TMEM and waits,
+ * at most `spins` tries (1 .. 2^24), on an mbarrier nothing arrives at (kind 0) or on a global
+ * flag nothing sets (kind 1). Returns RLOBPCG_ERR_TIMEOUT when the path works (the kernel gave up,
+ * released its TMEM and exited; the stream stays usable), INVALID_ARG for a bad kind or spins,
+ * CUDA for a runtime failure. Synchronous on `stream`.
+ */
+int rlobpcg_check_bounded_wait(int kind, int spins, void* stream);
+
 /* Static string naming a status code. */
 const char* rlobpcg_status_string(int status);
 

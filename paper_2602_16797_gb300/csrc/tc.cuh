@@ -27,11 +27,12 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
 }
-// Bounded wait for the phase of the given parity to complete. Returns false when the bound ran
-// out; callers record a device error and stop issuing work, so no wait is ever unbounded.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Bounded wait for the phase of the given parity to complete (at most `spins` tries). Returns
+// false when the bound ran out; callers record a device error and stop issuing work, so no wait
+// is ever unbounded.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int spins) {
   const uint32_t a = smem_addr(bar);
-  for (int it = 0; it < (1 << 24); ++it) {
+  for (int it = 0; it < spins; ++it) {
     uint32_t done;
     asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
                  : "=r"(done) : "r"(a), "r"(parity) : "memory");
@@ -39,6 +40,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   }
   return false;
 }
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) { return mbar_wait_bounded(bar, parity, 1 << 24); }
 
 // ---- bulk copy (TMA engine, untiled): 16-byte aligned addresses, size a multiple of 16 --------
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {

@@ -97,6 +97,7 @@ _SIGS = {
                                      ctypes.POINTER(c_double), ctypes.POINTER(c_double), ctypes.POINTER(c_size_t),
                                      ctypes.POINTER(c_int)]),
     "rlobpcg_server_destroy": (c_int, [c_void_p]),
+    "rlobpcg_check_bounded_wait": (c_int, [c_int, c_int, c_void_p]),
 }
 
 _lib = None
@@ -327,3 +328,8 @@ def rlobpcg_server_stats(server: int) -> dict:
 
 def rlobpcg_server_destroy(server: int) -> None:
     _check("rlobpcg_server_destroy", load().rlobpcg_server_destroy(server))
+
+
+def rlobpcg_check_bounded_wait(kind: int, spins: int, stream: int | None = None) -> int:
+    """Status of the bounded-wait health check (RLOBPCG_ERR_TIMEOUT when the path works)."""
+    return load().rlobpcg_check_bounded_wait(kind, spins, stream)
