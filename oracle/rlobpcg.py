@@ -62,7 +62,8 @@ import numpy as np
 
 __all__ = [
     "splitmix64", "piece_bounds", "sparse_stack", "sketch_dense_matrix", "sketch", "sketch_svd",
-    "orth", "rayleigh_ritz", "gram_pass", "householder_r", "stop_check", "rlobpcg", "refined_factor",
+    "orth", "rayleigh_ritz", "gram_pass", "householder_r", "stop_check", "rlobpcg", "refined_factor", "svqb",
+    "projection_set",
     "default_tau", "EPS",
 ]
 
@@ -200,6 +201,30 @@ def orth(M: np.ndarray) -> np.ndarray:
     return Q * ph[None, :]
 
 
+def svqb(W: np.ndarray, tau: float = EPS) -> np.ndarray:
+    """SVQB orthonormalisation of the columns of W (Stathopoulos & Wu, "A block orthogonalization
+    procedure with constant synchronization requirements", SISC 2002), the faster alternative to
+    Orth that Sec. 2.1 names: S = W^H W, D = diag(S)^{-1/2} (zero columns keep D = 0), the
+    eigendecomposition D S D = Z Theta Z^H, every eigenvalue below tau max(Theta) raised to it,
+    and W D Z Theta^{-1/2}. It spans the columns of W (for full-rank W) with orthonormal columns
+    to about u kappa(W D)^2; Theta ascending (LAPACK heevd)."""
+    S = W.conj().T @ W
+    dg = np.real(np.diagonal(S)).copy()
+    D = np.zeros_like(dg)
+    D[dg > 0] = 1.0 / np.sqrt(dg[dg > 0])
+    M = (S * D[:, None]) * D[None, :]
+    theta, Z = np.linalg.eigh(M)
+    top = float(np.max(theta)) if theta.size else 0.0
+    theta = np.maximum(theta, tau * top) if top > 0 else np.ones_like(theta)
+    return ((W * D[None, :]) @ Z) / np.sqrt(theta)[None, :]
+
+
+def projection_set(V: np.ndarray, X: np.ndarray, act: np.ndarray) -> np.ndarray:
+    """The columns W is made orthogonal to (Alg. 2): all of V -- with locking, the converged
+    columns too, which keeps the trial space orthogonal to them (Sec. 2.3) -- and X."""
+    return np.concatenate([V, X], axis=1)
+
+
 def rayleigh_ritz(AT: np.ndarray):
     """[~, Theta, C] = SVD(A_T) (Alg. 2, Rayleigh-Ritz by energy minimisation, Sec. 2.1): Theta
     descending, C square with the right singular vectors of A_T as columns."""
@@ -257,11 +282,17 @@ def rlobpcg(A: np.ndarray, k: int, b: int | None = None, d: int | None = None, z
             seed: int = 0, tau: float | None = None, max_iter: int | None = None,
             check_every: int | None = None, use_stagnation: bool = True,
             sketch_precision: str = "f64", fixed_iters: int | None = None,
-            keep_iterates: bool = False) -> dict:
+            keep_iterates: bool = False, orth_mode: str = "householder", locking: bool = False) -> dict:
     """Block RLOBPCG (Alg. 2) for the k smallest singular triplets of a tall A (m x n).
 
     b is the block size (default k), d the sketch rows (default 4n), zeta the SparseStack
     sparsity. fixed_iters runs exactly that many iterations with no stopping test.
+    orth_mode: "householder" (Orth of Alg. 2 after the two block Gram-Schmidt passes) or "svqb"
+    (SVQB in its place, the alternative Sec. 2.1 names). locking: deflate converged columns
+    (Sec. 2.3): a column whose residual meets the tolerance sigma11^2 tau is locked -- kept in V
+    with its value frozen, while X and W lose its column, W is made orthogonal to all of V, and
+    Rayleigh-Ritz runs on the active columns only, so the trial space stays orthogonal to the
+    converged vectors; the solve also ends when every column is locked.
     Returns a dict with sigma (k, ascending), V (n x k), U = A V diag(sigma)^{-1} (m x k),
     resid (k residual column norms), iters, stop_reason, sigma11 (= Sigma~(1,1)) and the
     per-iteration history of the b estimates and residual norms.
@@ -306,32 +337,43 @@ def rlobpcg(A: np.ndarray, k: int, b: int | None = None, d: int | None = None, z
     X = np.zeros((n, 0), dtype=wt)
     AX = np.zeros((m, 0), dtype=wt)
 
-    res_hist = [np.linalg.norm(Res, axis=0)]
+    if orth_mode not in ("householder", "svqb"):
+        raise ValueError(f"unknown orth_mode {orth_mode!r}")
+    normalise = orth if orth_mode == "householder" else svqb
+    rnorm = np.linalg.norm(Res, axis=0)
+    res_hist = [rnorm.copy()]
     theta_hist = [np.full(b, np.inf)]
+    theta_s = theta.copy()
+    locked = np.zeros(b, dtype=bool)
+    act = np.arange(b)                  # active columns (all of them without locking)
+    matvecs = b
     it_hist = []
     stop_reason = "max_iter"
     n_iter = fixed_iters if fixed_iters is not None else max_iter
     i = -1
     for i in range(n_iter):
-        # Search direction (Alg. 2): W = P (P^* R_i)
-        W = P @ (P.conj().T @ Res)
-        # BCGS2 against [V X], then Orth
-        VX = np.concatenate([V, X], axis=1)
+        a = act.size
+        # Search direction (Alg. 2): W = P (P^* R_i), for the active columns
+        W = P @ (P.conj().T @ Res[:, act])
+        # BCGS2 against [V X] (all of V: locked columns too), then Orth (or SVQB)
+        VX = projection_set(V, X, act)
         W = W - VX @ (VX.conj().T @ W)
-        W = orth(W - VX @ (VX.conj().T @ W))
+        W = normalise(W - VX @ (VX.conj().T @ W))
         # Trial space and its image: only W is multiplied by A
-        T = np.concatenate([V, X, W], axis=1)
-        AT = np.concatenate([AV, AX, A @ W], axis=1)
+        T = np.concatenate([V[:, act], X, W], axis=1)
+        AT = np.concatenate([AV[:, act], AX, A @ W], axis=1)
+        matvecs += a
         # Rayleigh-Ritz by SVD of A_T
         theta, C = rayleigh_ritz(AT)
         ncol = T.shape[1]
-        Cs = C[:, ncol - b:]
-        theta_s = theta[ncol - b:]
-        V = T @ Cs
-        AV = AT @ Cs
+        Cs = C[:, ncol - a:]
+        theta_s[act] = theta[ncol - a:]
+        V[:, act] = T @ Cs
+        AV[:, act] = AT @ Cs
         # Residual matrix R_{i+1} = A^* A_V - V Theta^2 (direct product, as in Alg. 2)
-        Res = AH @ AV - V * (theta_s ** 2)[None, :]
-        res_hist.append(np.linalg.norm(Res, axis=0))
+        Res[:, act] = AH @ AV[:, act] - V[:, act] * (theta_s[act] ** 2)[None, :]
+        rnorm[act] = np.linalg.norm(Res[:, act], axis=0)
+        res_hist.append(rnorm.copy())
         theta_hist.append(theta_s.copy())
         if keep_iterates:
             it_hist.append(V.copy())
@@ -340,24 +382,36 @@ def rlobpcg(A: np.ndarray, k: int, b: int | None = None, d: int | None = None, z
             if tol and s1 and s2:
                 stop_reason = "converged"
                 break
-        # Momentum basis X (eq. x-defining): Q = Orth(C(1:b, 1:ncol-b)^*)
-        Q = orth(C[:b, : ncol - b].conj().T)
-        CQ = C[:, : ncol - b] @ Q
+        # Momentum basis X (eq. x-defining): Q = Orth(C(1:a, 1:ncol-a)^*); column p belongs to
+        # the p-th active column
+        Q = orth(C[:a, : ncol - a].conj().T)
+        CQ = C[:, : ncol - a] @ Q
         X = T @ CQ
         AX = AT @ CQ
+        if locking:
+            newly = rnorm[act] <= sigma11 ** 2 * tau
+            if newly.any():
+                locked[act[newly]] = True
+                X = X[:, ~newly]
+                AX = AX[:, ~newly]
+                act = act[~newly]
+                if act.size == 0 and fixed_iters is None:
+                    stop_reason = "converged"
+                    break
 
     if fixed_iters is not None:
         stop_reason = "fixed_iters"
     # Outputs (the end of Alg. 2), returned in ascending order of sigma
-    order = np.arange(b - 1, b - 1 - k, -1)
-    sig = theta_s[order] if i >= 0 else theta[order]
+    # (theta_s is descending without locking; sorting its reverse keeps the reversed order for ties)
+    order = (b - 1 - np.argsort(theta_s[::-1], kind="stable"))[:k]
+    sig = theta_s[order]
     Vk = V[:, order]
     with np.errstate(divide="ignore", invalid="ignore"):
         U = AV[:, order] / sig[None, :]
     return {
-        "sigma": sig, "V": Vk, "U": U, "resid": np.linalg.norm(Res, axis=0)[order],
+        "sigma": sig, "V": Vk, "U": U, "resid": rnorm[order],
         "iters": i + 1, "stop_reason": stop_reason, "sigma11": sigma11, "sketch_sigma": s,
         "theta0": theta0,
         "res_hist": np.array(res_hist), "theta_hist": np.array(theta_hist), "iterates": it_hist,
-        "matvecs": b * (i + 2),
+        "matvecs": matvecs, "locked": locked.copy(),
     }

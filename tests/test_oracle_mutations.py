@@ -123,3 +123,19 @@ def test_refinement_without_conjugate_is_caught(monkeypatch):
         return orig(SA).conj()                                              # a transposed-only Gram
     _patch(monkeypatch, "refined_factor", bad)
     _expect_failure(lambda: pins.test_refined_factor_is_a_qr_factor_of_the_sketch(True, 1e13))
+
+
+def test_locking_without_deflation_is_caught(monkeypatch):
+    def bad(V, X, act):
+        return np.concatenate([V[:, act], X], axis=1)      # locked columns left out of the projection
+    _patch(monkeypatch, "projection_set", bad)
+    _expect_failure(lambda: pins.test_locking_deflates_converged_columns("householder"))
+
+
+def test_svqb_without_the_eigen_scaling_is_caught(monkeypatch):
+    def bad(W, tau=oracle.EPS):
+        S = W.conj().T @ W
+        D = 1.0 / np.sqrt(np.real(np.diagonal(S)))
+        return W * D[None, :]                             # column scaling only
+    _patch(monkeypatch, "svqb", bad)
+    _expect_failure(lambda: pins.test_svqb_orthonormalises_and_keeps_the_span(False))

@@ -421,3 +421,76 @@ def test_earliest_stagnation_stop_is_iteration_10():
     A, _, _ = wl.planted_small_gap_free(m=2000, n=30)
     r = oracle.rlobpcg(A, k=1, seed=1)
     assert r["iters"] >= 11 and (r["iters"] - 1) % 5 == 0
+
+
+# ---------------------------------------------------------------------------------------------
+# SVQB (Sec. 2.1) and locking (Sec. 2.3)
+# ---------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("complex_", [False, True])
+def test_svqb_orthonormalises_and_keeps_the_span(complex_):
+    """SVQB (Stathopoulos & Wu 2002) returns orthonormal columns spanning those of W, to about
+    u kappa(W D)^2 (D the column scaling); on columns that are already orthogonal, W D is
+    orthonormal, so the result is W D times an orthogonal matrix."""
+    rng = np.random.default_rng(51)
+    n, b = 300, 6
+    G = rng.standard_normal((n, b)) + (1j * rng.standard_normal((n, b)) if complex_ else 0)
+    W = G @ np.diag(np.logspace(0, -3, b)) @ (rng.standard_normal((b, b)) + 3 * np.eye(b))
+    Q = oracle.svqb(W)
+    kap = np.linalg.cond(W / np.linalg.norm(W, axis=0))
+    assert np.linalg.norm(Q.conj().T @ Q - np.eye(b), 2) <= 100 * U64 * kap ** 2
+    Qw, _ = np.linalg.qr(W)
+    assert np.linalg.norm(Q - Qw @ (Qw.conj().T @ Q), 2) <= 100 * U64 * kap ** 2
+    # already orthogonal columns of different norms
+    Qo, _ = np.linalg.qr(G)
+    Wo = Qo * np.array([1e-3, 1.0, 7.0, 1e5, 0.5, 2.0])[None, :]
+    Z = (Wo / np.linalg.norm(Wo, axis=0)).conj().T @ oracle.svqb(Wo)
+    assert np.allclose(Z.conj().T @ Z, np.eye(b), atol=50 * U64)
+
+
+def test_svqb_threshold_keeps_a_zero_column_finite():
+    rng = np.random.default_rng(52)
+    W = rng.standard_normal((100, 4))
+    W[:, 2] = 0.0
+    Q = oracle.svqb(W)
+    assert np.isfinite(Q).all()
+    assert np.allclose(Q[:, np.linalg.norm(Q, axis=0) > 0.5].T @ Q[:, np.linalg.norm(Q, axis=0) > 0.5], np.eye(3),
+                       atol=1e-12)
+
+
+def _spread_bottom():
+    rng = np.random.default_rng(5)
+    n = 60
+    sigma = np.concatenate([np.logspace(0, -3, n - 4), [1e-5, 3e-6, 1e-6, 2e-7]])
+    return wl.planted(rng, 5000, sigma)
+
+
+@pytest.mark.parametrize("orth_mode", ["householder", "svqb"])
+def test_locking_deflates_converged_columns(orth_mode):
+    """Locking (Sec. 2.3): converged columns keep their values while the rest iterate in the
+    orthogonal complement; the result is the planted bottom triplets (within the backward-stable
+    floors of Sec. 4), V stays orthonormal across locked and active columns, the iteration ends
+    once every column is locked, and it spends fewer matrix-vector products (b per iteration
+    without locking, the active count with it)."""
+    A, s, V = _spread_bottom()
+    k = 4
+    r0 = oracle.rlobpcg(A, k=k, seed=3, orth_mode=orth_mode)
+    r1 = oracle.rlobpcg(A, k=k, seed=3, orth_mode=orth_mode, locking=True, keep_iterates=True)
+    truth = np.sort(s)[:k]
+    floor = 10 * np.sqrt(A.shape[1]) * U64 * s[0]
+    assert np.all(np.abs(r1["sigma"] - truth) <= np.maximum(1e-10 * truth, floor))
+    assert np.all(np.abs(r0["sigma"] - truth) <= np.maximum(1e-10 * truth, floor))
+    assert r1["locked"].all() and r1["stop_reason"] == "converged"
+    assert r1["matvecs"] < r0["matvecs"]
+    for Vi in r1["iterates"]:
+        assert np.linalg.norm(Vi.conj().T @ Vi - np.eye(k), 2) <= 1e3 * A.shape[1] * U64
+    # the locked residuals met the tolerance of Sec. 2.1 when they locked, and stay frozen
+    tau = oracle.default_tau(A.shape[1])
+    assert np.all(r1["resid"] <= r1["sigma11"] ** 2 * tau)
+
+
+def test_locking_off_is_the_plain_method():
+    A, s, V = _spread_bottom()
+    a = oracle.rlobpcg(A, k=2, seed=3, fixed_iters=6)
+    b = oracle.rlobpcg(A, k=2, seed=3, fixed_iters=6, locking=False, orth_mode="householder")
+    assert np.array_equal(a["sigma"], b["sigma"]) and a["matvecs"] == 2 * 7
