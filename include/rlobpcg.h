@@ -88,7 +88,20 @@ typedef struct {
                            once per solve into about 16 bytes of device memory per element of A.
                            0: the FP64 CUDA-core Gram pass (rlobpcg_gram).                    */
   double tau;           /* tolerance of ||R(:,j)|| <= Sigma~(1,1)^2 tau; < 0 means 2 sqrt(n) 2^-52 */
+  int orth_mode;        /* orthonormalisation of W after its two block Gram-Schmidt passes against
+                           [V X]: RLOBPCG_ORTH_HOUSEHOLDER (default, Orth of Alg. 2) or
+                           RLOBPCG_ORTH_SVQB (Stathopoulos & Wu's SVQB, the faster, less stable
+                           alternative Sec. 2.1 names)                                          */
+  int locking;          /* 1: deflate converged columns (Sec. 2.3): a column whose residual meets the
+                           tolerance is locked -- kept in V with its value frozen -- while X and W
+                           lose its column and W stays orthogonal to all of V, so Rayleigh-Ritz
+                           runs on the active columns; the solve also ends when all are locked.
+                           The host reads the residual norms after every iteration to decide (one
+                           stream synchronisation per iteration instead of per stop check).      */
 } rlobpcg_opts;
+
+#define RLOBPCG_ORTH_HOUSEHOLDER 0
+#define RLOBPCG_ORTH_SVQB 1
 
 /* Per-solve report. */
 typedef struct {

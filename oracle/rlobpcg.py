@@ -395,7 +395,7 @@ def rlobpcg(A: np.ndarray, k: int, b: int | None = None, d: int | None = None, z
                 X = X[:, ~newly]
                 AX = AX[:, ~newly]
                 act = act[~newly]
-                if act.size == 0 and fixed_iters is None:
+                if act.size == 0:       # every column locked: the solve ends
                     stop_reason = "converged"
                     break
 

@@ -1033,13 +1033,166 @@ __global__ void __launch_bounds__(1024) bcgs2_orth_kernel(T* Tb, int n, int b, i
 // avoid the L2 latency of every dependent step; the FP64 work (2 passes x 2 n q b FMAs, then
 // 2 n b^2 for Householder and Q) runs at the single SM's DFMA rate. With wd.Wsl set (real FP64),
 // the final W is also written as bf16 digits for the split Gram pass (see split.cuh).
+// ------------------------------------------------------------------------------------------
+// SVQB (Stathopoulos & Wu, SISC 2002), the alternative to Orth that Sec. 2.1 names: with
+// S = W^H W and D = diag(S)^{-1/2}, the eigendecomposition D S D = Z Theta Z^H, eigenvalues below
+// eps max(Theta) raised to it, and W <- W D Z Theta^{-1/2}. The b x b eigenproblem runs as a
+// cyclic two-sided Jacobi with the round-robin parallel ordering: per round, the rotations of the
+// disjoint pairs (one thread each), then U^H on their rows and U on their columns (and on Z), with
+// U = diag(1, e^{-i phi}) J on (p, q), phi the phase of M_pq and J the real rotation of
+// Golub & Van Loan's symmetric Schur step. One CTA; M, Z column-major b x b in shared memory.
+// ------------------------------------------------------------------------------------------
+
+// S (col-major b x b) = W^H W over rows [0, rows) of W (row-major rows x b); a warp per entry
+// of the upper triangle, the lower one mirrored.
+template <class T>
+__device__ void cta_gram(const T* Ws, int rows, int b, T* S) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, NW = blockDim.x >> 5;
+  for (int e = warp; e < b * b; e += NW) {
+    const int i = e / b, j = e % b;
+    if (j < i) continue;
+    T a0 = zero_<T>(), a1 = zero_<T>();
+    int r = lane;
+    for (; r + 32 < rows; r += 64) {
+      a0 = madc_(Ws[(size_t)r * b + i], Ws[(size_t)r * b + j], a0);
+      a1 = madc_(Ws[(size_t)(r + 32) * b + i], Ws[(size_t)(r + 32) * b + j], a1);
+    }
+    if (r < rows) a0 = madc_(Ws[(size_t)r * b + i], Ws[(size_t)r * b + j], a0);
+    const T v = warp_sum(add_(a0, a1));
+    if (lane == 0) {
+      S[(size_t)j * b + i] = v;          // (i, j) = sum conj(w_i) w_j
+      S[(size_t)i * b + j] = conj_(v);
+    }
+  }
+  __syncthreads();
+}
+
+template <class T>
+__device__ inline T phase_of_(T g, double ag) { return scale_(g, 1.0 / ag); }
+
+// Hermitian b x b M (b <= 32) -> diagonal; Z accumulates the rotations (starts as I). rot: 2
+// doubles per pair, ph: phases, rf: flags (16 pairs). Returns the sweeps taken.
+template <class T>
+__device__ int herm_jacobi(T* M, T* Z, int b, double* rot, T* ph, int* rf, int* any) {
+  const int tid = threadIdx.x, NT = blockDim.x;
+  const int N = b + (b & 1);
+  const double tol = (double)imax(b, 4) * 2.220446049250313e-16;
+  for (int e = tid; e < b * b; e += NT) Z[e] = (e / b == e % b) ? from_real<T>(1.0) : zero_<T>();
+  __syncthreads();
+  int sweep = 0;
+  for (; sweep < 40; ++sweep) {
+    if (tid == 0) *any = 0;
+    __syncthreads();
+    for (int r = 0; r < N - 1; ++r) {
+      if (tid < N / 2) {
+        int pp = rr_slot(tid, r, N), qq = rr_slot(N - 1 - tid, r, N);
+        if (pp > qq) { const int t = pp; pp = qq; qq = t; }
+        int f = 0;
+        if (qq < b) {
+          const double a = re_(M[(size_t)pp * b + pp]), d = re_(M[(size_t)qq * b + qq]);
+          const T g = M[(size_t)qq * b + pp];   // row pp, column qq
+          const double ag = sqrt(abs2_(g));
+          if (ag > tol * sqrt(fabs(a * d)) && ag > 0.0) {
+            const double tau = (d - a) / (2.0 * ag);
+            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            const double c = 1.0 / sqrt(1.0 + t * t);
+            rot[2 * tid] = c;
+            rot[2 * tid + 1] = t * c;
+            ph[tid] = phase_of_(g, ag);
+            f = 1;
+            *any = 1;
+          }
+        }
+        rf[tid] = f;
+      }
+      __syncthreads();
+      // rows p, q <- U^H rows: p: c row_p - s e row_q, q: s row_p + c e row_q
+      for (int e = tid; e < (N / 2) * b; e += NT) {
+        const int i = e / b, col = e % b;
+        if (!rf[i]) continue;
+        int pp = rr_slot(i, r, N), qq = rr_slot(N - 1 - i, r, N);
+        if (pp > qq) { const int t = pp; pp = qq; qq = t; }
+        const double c = rot[2 * i], sn = rot[2 * i + 1];
+        const T ep = ph[i];
+        const T mp = M[(size_t)col * b + pp], mq = M[(size_t)col * b + qq];
+        M[(size_t)col * b + pp] = sub_(scale_(mp, c), scale_(mul_(ep, mq), sn));
+        M[(size_t)col * b + qq] = add_(scale_(mp, sn), scale_(mul_(ep, mq), c));
+      }
+      __syncthreads();
+      // columns p, q of M and Z <- U: p: c col_p - s conj(e) col_q, q: s col_p + c conj(e) col_q
+      for (int e = tid; e < (N / 2) * b * 2; e += NT) {
+        const int which = e / ((N / 2) * b), e2 = e % ((N / 2) * b);
+        const int i = e2 / b, row = e2 % b;
+        if (!rf[i]) continue;
+        int pp = rr_slot(i, r, N), qq = rr_slot(N - 1 - i, r, N);
+        if (pp > qq) { const int t = pp; pp = qq; qq = t; }
+        T* A = which ? Z : M;
+        const double c = rot[2 * i], sn = rot[2 * i + 1];
+        const T ec = conj_(ph[i]);
+        const T ap = A[(size_t)pp * b + row], aq = A[(size_t)qq * b + row];
+        A[(size_t)pp * b + row] = sub_(scale_(ap, c), scale_(mul_(ec, aq), sn));
+        A[(size_t)qq * b + row] = add_(scale_(ap, sn), scale_(mul_(ec, aq), c));
+      }
+      __syncthreads();
+      if (tid < N / 2 && rf[tid]) {
+        int pp = rr_slot(tid, r, N), qq = rr_slot(N - 1 - tid, r, N);
+        if (pp > qq) { const int t = pp; pp = qq; qq = t; }
+        M[(size_t)qq * b + pp] = zero_<T>();
+        M[(size_t)pp * b + qq] = zero_<T>();
+      }
+      __syncthreads();
+    }
+    if (!*any) { ++sweep; break; }
+    __syncthreads();
+  }
+  return sweep;
+}
+
+// W (rows x b, row-major) -> out (rows x b): W D Z Theta^{-1/2} from S = W^H W (already summed,
+// col-major in S; consumed). M, Z: b x b scratch; dsc, th: b doubles; rot, ph, rf, any: the
+// Jacobi scratch. Every thread of the CTA takes part.
+template <class T>
+__device__ void cta_svqb(const T* Ws, int rows, int b, T* S, T* Z, double* dsc, double* th, T* out, double* rot,
+                         T* ph, int* rf, int* any) {
+  const int tid = threadIdx.x, NT = blockDim.x;
+  for (int j = tid; j < b; j += NT) {
+    const double s = re_(S[(size_t)j * b + j]);
+    dsc[j] = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
+  }
+  __syncthreads();
+  for (int e = tid; e < b * b; e += NT) {
+    const int col = e / b, row = e % b;
+    S[e] = scale_(S[e], dsc[row] * dsc[col]);
+  }
+  __syncthreads();
+  herm_jacobi<T>(S, Z, b, rot, ph, rf, any);
+  if (tid == 0) {
+    double top = 0.0;
+    for (int j = 0; j < b; ++j) top = fmax(top, re_(S[(size_t)j * b + j]));
+    for (int j = 0; j < b; ++j) {
+      const double t = top > 0.0 ? fmax(re_(S[(size_t)j * b + j]), 2.220446049250313e-16 * top) : 1.0;
+      th[j] = 1.0 / sqrt(t);
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < rows * b; e += NT) {
+    const int k = e / b, j = e % b;
+    T v = zero_<T>();
+    for (int i = 0; i < b; ++i) v = mad_(scale_(Ws[(size_t)k * b + i], dsc[i]), Z[(size_t)j * b + i], v);
+    out[e] = scale_(v, th[j]);
+  }
+  __syncthreads();
+}
+
 template <class T>
 __global__ void __launch_bounds__(256) bcgs2_orth_smem_kernel(T* __restrict__ Tb, int n, int b, int64_t ld, int wo,
-                                                              int nx, int passes, split::WDigits wd, int* err) {
+                                                              int nx, int passes, split::WDigits wd, int* err,
+                                                              int svqb, const T* __restrict__ Dl, int nl,
+                                                              int64_t ldl) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int NT = 256, NW = NT / 32;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int q = b + nx;
+  const int q = b + nx + nl;   // V, X, and the deflated (locked) columns Dl
   const int QB = q * b;
   T* Bs = reinterpret_cast<T*>(smem_raw);   // n x q: V then X (row-major); later E = Q (n x b)
   T* Ws = Bs + (size_t)n * q;               // n x b
@@ -1051,7 +1204,9 @@ __global__ void __launch_bounds__(256) bcgs2_orth_smem_kernel(T* __restrict__ Tb
   double* red = reinterpret_cast<double*>(sv + b);   // NW x 16 column maxima
   __shared__ T sh_inv;
   __shared__ int Fs[32];   // digit-block width of the split Gram pass, <= 32
-  auto bcol = [&](int j) { return j < b ? j : (2 * b + (j - b)); };
+  auto pcol = [&](int64_t k, int j) {   // column j of the projection set [V X Dl] in row k
+    return j < b ? Tb[k * ld + j] : j < b + nx ? Tb[k * ld + 2 * b + (j - b)] : Dl[k * ldl + (j - b - nx)];
+  };
   for (int e = tid; e < n * b; e += NT) {
     const int k = e / b, cw = e % b;
     Ws[e] = Tb[(int64_t)k * ld + wo + cw];
@@ -1059,7 +1214,7 @@ __global__ void __launch_bounds__(256) bcgs2_orth_smem_kernel(T* __restrict__ Tb
   if (passes > 0)
     for (int e = tid; e < n * q; e += NT) {
       const int k = e / q, j = e % q;
-      Bs[e] = Tb[(int64_t)k * ld + bcol(j)];
+      Bs[e] = pcol(k, j);
     }
   __syncthreads();
   const int G = QB >= NT ? 1 : imin(4, NT / QB);
@@ -1096,6 +1251,18 @@ __global__ void __launch_bounds__(256) bcgs2_orth_smem_kernel(T* __restrict__ Tb
     }
     __syncthreads();
   }
+  T* E = Bs;
+  if (svqb) {
+    // SVQB in place of Orth: S = W^H W, then W D Z Theta^{-1/2} into E (Pp holds S and Z)
+    __shared__ double sq_rot[32];
+    __shared__ T sq_ph[16];
+    __shared__ int sq_rf[16], sq_any;
+    cta_gram<T>(Ws, n, b, Pp);
+    cta_svqb<T>(Ws, n, b, Pp, Pp + (size_t)b * b, reinterpret_cast<double*>(tauv), reinterpret_cast<double*>(sv), E,
+                sq_rot, sq_ph, sq_rf, &sq_any);
+    for (int j = tid; j < b; j += NT) dg[j] = from_real<T>(1.0);
+    __syncthreads();
+  } else {
   // Householder QR of W (n x b) in place; v (scaled by 1/(alpha - beta)) stored below the diagonal
   for (int j = 0; j < b; ++j) {
     for (int cc = j + warp; cc < b; cc += NW) {
@@ -1133,7 +1300,6 @@ __global__ void __launch_bounds__(256) bcgs2_orth_smem_kernel(T* __restrict__ Tb
     __syncthreads();
   }
   // Q = H_0 ... H_{b-1} I(:, 0:b) into E (the space of [V X]), phases of diag(R) folded in
-  T* E = Bs;
   for (int e = tid; e < n * b; e += NT) {
     const int k = e / b, cc = e % b;
     E[e] = (k == cc) ? from_real<T>(1.0) : zero_<T>();
@@ -1160,6 +1326,7 @@ __global__ void __launch_bounds__(256) bcgs2_orth_smem_kernel(T* __restrict__ Tb
     }
     __syncthreads();
   }
+  }  // Householder
   for (int e = tid; e < n * b; e += NT) {
     const int k = e / b, cc = e % b;
     const T v = mul_(E[e], phase_(dg[cc]));
@@ -1292,13 +1459,14 @@ __device__ void cta_apply_q(const T* Vm, const T* tau, int rows, int b, T* E, T*
 template <class T>
 __global__ void __launch_bounds__(256) bcgs2_orth_coop_kernel(T* __restrict__ Tb, int n, int b, int64_t ld, int wo,
                                                               int nx, int passes, T* __restrict__ gs,
-                                                              split::WDigits wd, int* err) {
+                                                              split::WDigits wd, int* err, int svqb,
+                                                              const T* __restrict__ Dl, int nl, int64_t ldl) {
   namespace cg = cooperative_groups;
   cg::grid_group grid = cg::this_grid();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, NT = blockDim.x, NW = NT >> 5;
   const int G = gridDim.x, g = blockIdx.x;
-  const int q = b + nx, QB = q * b, SB = G * b;
+  const int q = b + nx + nl, QB = q * b, SB = G * b;   // projection set [V X Dl]
   const int r0 = (int)((int64_t)g * n / G), r1 = (int)((int64_t)(g + 1) * n / G), rows = r1 - r0;
   const int rmax = (n + G - 1) / G;
   T* Bs = reinterpret_cast<T*>(smem_raw);   // rmax x q (V, X); later this CTA's rows of Q
@@ -1317,7 +1485,9 @@ __global__ void __launch_bounds__(256) bcgs2_orth_coop_kernel(T* __restrict__ Tb
   T* gP1 = gP0 + (size_t)G * QB;
   T* gR = gP1 + (size_t)G * QB;
   double* gmx = reinterpret_cast<double*>(gR + (size_t)G * b * b);
-  auto bcol = [&](int j) { return j < b ? j : (2 * b + (j - b)); };
+  auto pcol = [&](int64_t k, int j) {   // column j of the projection set [V X Dl] in row k
+    return j < b ? Tb[k * ld + j] : j < b + nx ? Tb[k * ld + 2 * b + (j - b)] : Dl[k * ldl + (j - b - nx)];
+  };
 
   for (int e = tid; e < rows * b; e += NT) {
     const int k = e / b, cw = e % b;
@@ -1326,7 +1496,7 @@ __global__ void __launch_bounds__(256) bcgs2_orth_coop_kernel(T* __restrict__ Tb
   if (passes > 0)
     for (int e = tid; e < rows * q; e += NT) {
       const int k = e / q, j = e % q;
-      Bs[e] = Tb[(int64_t)(r0 + k) * ld + bcol(j)];
+      Bs[e] = pcol((int64_t)(r0 + k), j);
     }
   __syncthreads();
   for (int pass = 0; pass < passes; ++pass) {
@@ -1357,6 +1527,27 @@ __global__ void __launch_bounds__(256) bcgs2_orth_coop_kernel(T* __restrict__ Tb
     }
     __syncthreads();
   }
+  T* QL = Bs;
+  if (svqb) {
+    // SVQB in place of Orth: every CTA sums the same per-CTA Gram partials in CTA order, solves
+    // the same b x b eigenproblem and scales its own rows
+    __shared__ double sq_rot[32];
+    __shared__ T sq_ph[16];
+    __shared__ int sq_rf[16], sq_any;
+    cta_gram<T>(Ws, rows, b, S);
+    for (int e = tid; e < b * b; e += NT) gR[(size_t)g * b * b + e] = S[e];
+    grid.sync();
+    for (int e = tid; e < b * b; e += NT) {
+      T sum = ldcg_(gR + e);
+      for (int h = 1; h < G; ++h) sum = add_(sum, ldcg_(gR + (size_t)h * b * b + e));
+      S[e] = sum;
+    }
+    __syncthreads();
+    cta_svqb<T>(Ws, rows, b, S, E, reinterpret_cast<double*>(tl), reinterpret_cast<double*>(ts), QL, sq_rot, sq_ph,
+                sq_rf, &sq_any);
+    for (int j = tid; j < b; j += NT) dg[j] = from_real<T>(1.0);
+    __syncthreads();
+  } else {
   // local R_g
   cta_householder<T>(Ws, rows, b, tl, dl, sv, &sh_inv);
   for (int e = tid; e < b * b; e += NT) {
@@ -1374,13 +1565,13 @@ __global__ void __launch_bounds__(256) bcgs2_orth_coop_kernel(T* __restrict__ Tb
   __syncthreads();
   cta_apply_q<T>(S, ts, SB, b, E, sv, true);
   // this CTA's rows of Q: H_local [Q_s block g; 0]
-  T* QL = Bs;
   for (int e = tid; e < rows * b; e += NT) {
     const int k = e / b, cc = e % b;
     QL[e] = (k < b) ? E[(size_t)(g * b + k) * b + cc] : zero_<T>();
   }
   __syncthreads();
   cta_apply_q<T>(Ws, tl, rows, b, QL, sv, false);
+  }  // Householder
   for (int e = tid; e < rows * b; e += NT) {
     const int k = e / b, cc = e % b;
     const T v = mul_(QL[e], phase_(dg[cc]));
@@ -1447,6 +1638,20 @@ __global__ void copy_cols_kernel(const T* src, int64_t lds, int so, T* dst, int6
 }
 
 // outputs: ascending order (reverse of the descending Theta_s block), first k of b
+// Per row of buf (row-major, ld): columns dst[t] <- old columns src[t], t < cnt (all reads of a row
+// before its writes, so the map may move columns in place). Compacts the active block when
+// columns are locked and orders the final columns.
+struct ColMap { int cnt; int src[64]; int dst[64]; };
+
+template <class T>
+__global__ void gather_cols_kernel(T* buf, int64_t rows, int64_t ld, ColMap map) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  T v[64];
+  for (int t = 0; t < map.cnt; ++t) v[t] = buf[r * ld + map.src[t]];
+  for (int t = 0; t < map.cnt; ++t) buf[r * ld + map.dst[t]] = v[t];
+}
+
 template <class T>
 __global__ void outputs_kernel(const T* Tb, const T* ATb, int64_t n, int64_t m, int b, int k, int64_t ld,
                                const double* theta_s, const double* res_norm, double* sigma, T* Vout, T* Uout,
@@ -1675,14 +1880,21 @@ size_t bcgs2_coop_bytes(int64_t n, int qmax, int b, size_t esz);
 
 template <class T>
 int bcgs2_orth_launch(T* Tb, int n, int b, int64_t ld, int wo, int nx, T* E, int passes, cudaStream_t st,
-                      const split::WDigits* wd, int* err, bool* digits_done, void* coop, size_t coop_bytes) {
+                      const split::WDigits* wd, int* err, bool* digits_done, void* coop, size_t coop_bytes,
+                      int svqb, const T* Dl, int nl, int64_t ldl) {
   if (digits_done) *digits_done = false;
-  const int q = b + nx;
+  if (svqb && b > 32) {
+    set_last_error("SVQB orthonormalisation takes blocks of at most 32 columns", __FILE__, __LINE__);
+    return RLOBPCG_ERR_UNSUPPORTED;
+  }
+  if (nl > 0 && passes == 0) return RLOBPCG_ERR_INVALID_ARG;
+  if (nl <= 0) { nl = 0; Dl = Tb; ldl = ld; }
+  const int q = b + nx + nl;
   {
     // cooperative version over G CTAs when n is large enough for the grid barriers to pay (every
     // CTA keeps at least max(32, b) rows; below n = 256 the one-CTA kernel is faster)
     const int G = imin(16, n / imax(32, b));
-    if (n >= 256 && G >= 2 && coop && coop_bytes >= bcgs2_coop_bytes(n, b + imax(nx, 0), b, sizeof(T))) {
+    if (n >= 256 && G >= 2 && coop && coop_bytes >= bcgs2_coop_bytes(n, b + imax(nx, 0) + nl, b, sizeof(T))) {
       const int rmax = (n + G - 1) / G, SB = G * b;
       const size_t smem = ((size_t)rmax * (imax(q, b) + b) + (size_t)q * b + 2 * (size_t)SB * b + 6 * b) * sizeof(T);
       if (smem <= max_smem_optin() - 2048) {
@@ -1690,7 +1902,7 @@ int bcgs2_orth_launch(T* Tb, int n, int b, int64_t ld, int wo, int nx, T* E, int
         if (wd && wd->Wsl && sizeof(T) == sizeof(double) && b <= wd->BP) w = *wd;
         RL_TRY(allow_dynamic_smem(bcgs2_orth_coop_kernel<T>, smem));
         T* gsp = (T*)coop;
-        void* args[] = {&Tb, &n, &b, &ld, &wo, &nx, &passes, &gsp, &w, &err};
+        void* args[] = {&Tb, &n, &b, &ld, &wo, &nx, &passes, &gsp, &w, &err, &svqb, &Dl, &nl, &ldl};
         RL_CUDA(cudaLaunchCooperativeKernel((void*)bcgs2_orth_coop_kernel<T>, dim3(G), dim3(256), args, smem, st));
         note_launch();
         if (digits_done) *digits_done = w.Wsl != nullptr;
@@ -1703,10 +1915,15 @@ int bcgs2_orth_launch(T* Tb, int n, int b, int64_t ld, int wo, int nx, T* E, int
     split::WDigits w{};
     if (wd && wd->Wsl && sizeof(T) == sizeof(double) && b <= wd->BP) w = *wd;
     RL_TRY(allow_dynamic_smem(bcgs2_orth_smem_kernel<T>, smem_s));
-    bcgs2_orth_smem_kernel<T><<<1, 256, smem_s, st>>>(Tb, n, b, ld, wo, nx, passes, w, err);
+    bcgs2_orth_smem_kernel<T><<<1, 256, smem_s, st>>>(Tb, n, b, ld, wo, nx, passes, w, err, svqb, Dl, nl, ldl);
     RL_CHECK_LAUNCH();
     if (digits_done) *digits_done = w.Wsl != nullptr;
     return RLOBPCG_OK;
+  }
+  if (svqb || nl > 0) {
+    set_last_error("SVQB orthonormalisation and locking: n too large for the shared-memory and cooperative kernels",
+                   __FILE__, __LINE__);
+    return RLOBPCG_ERR_UNSUPPORTED;
   }
   const size_t smem = ((size_t)2 * b * b + 3 * b) * sizeof(T);
   bcgs2_orth_kernel<T><<<1, 1024, smem, st>>>(Tb, n, b, ld, wo, nx, E, passes);
@@ -1714,9 +1931,10 @@ int bcgs2_orth_launch(T* Tb, int n, int b, int64_t ld, int wo, int nx, T* E, int
   return RLOBPCG_OK;
 }
 template int bcgs2_orth_launch<double>(double*, int, int, int64_t, int, int, double*, int, cudaStream_t,
-                                       const split::WDigits*, int*, bool*, void*, size_t);
+                                       const split::WDigits*, int*, bool*, void*, size_t, int, const double*, int,
+                                       int64_t);
 template int bcgs2_orth_launch<cd>(cd*, int, int, int64_t, int, int, cd*, int, cudaStream_t, const split::WDigits*,
-                                   int*, bool*, void*, size_t);
+                                   int*, bool*, void*, size_t, int, const cd*, int, int64_t);
 
 // global scratch of the cooperative BCGS2 + Orth kernel for up to qmax basis columns and b columns
 size_t bcgs2_coop_bytes(int64_t n, int qmax, int b, size_t esz) {
@@ -1766,4 +1984,20 @@ int nonfinite_scan_launch(const T* A, int64_t m, int n, int64_t lda, int* err, c
 template int nonfinite_scan_launch<double>(const double*, int64_t, int, int64_t, int*, cudaStream_t);
 template int nonfinite_scan_launch<cd>(const cd*, int64_t, int, int64_t, int*, cudaStream_t);
 
+}  // namespace rl
+
+namespace rl {
+template <class T>
+int gather_cols_launch(T* buf, int64_t rows, int64_t ld, const int* src, const int* dst, int cnt, cudaStream_t st) {
+  if (cnt <= 0) return RLOBPCG_OK;
+  if (cnt > 64) return RLOBPCG_ERR_INVALID_ARG;
+  ColMap map{};
+  map.cnt = cnt;
+  for (int t = 0; t < cnt; ++t) { map.src[t] = src[t]; map.dst[t] = dst[t]; }
+  gather_cols_kernel<T><<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(buf, rows, ld, map);
+  RL_CHECK_LAUNCH();
+  return RLOBPCG_OK;
+}
+template int gather_cols_launch<double>(double*, int64_t, int64_t, const int*, const int*, int, cudaStream_t);
+template int gather_cols_launch<cd>(cd*, int64_t, int64_t, const int*, const int*, int, cudaStream_t);
 }  // namespace rl

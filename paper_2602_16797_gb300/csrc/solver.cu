@@ -63,8 +63,14 @@ int precond_launch(const S* Rinv_r, const S* Rinv_c, int n, int b, const T* Rs, 
                    cudaStream_t st);
 template <class T>
 int bcgs2_orth_launch(T* Tb, int n, int b, int64_t ld, int wo, int nx, T* E, int passes, cudaStream_t st,
-                      const split::WDigits* wd, int* err, bool* digits_done, void* coop, size_t coop_bytes);
+                      const split::WDigits* wd, int* err, bool* digits_done, void* coop, size_t coop_bytes,
+                      int svqb, const T* Dl = nullptr, int nl = 0, int64_t ldl = 0);
 size_t bcgs2_coop_bytes(int64_t n, int qmax, int b, size_t esz);
+template <class T>
+int gather_cols_launch(T* buf, int64_t rows, int64_t ld, const int* src, const int* dst, int cnt, cudaStream_t st);
+template <class T>
+int copy_cols_launch(const T* src, int64_t lds, int so, T* dst, int64_t ldd, int dof, int64_t rows, int w,
+                     cudaStream_t st);
 split::WDigits split_w_digits(void* work, int64_t m, int64_t n, int b);
 template <class S, class T>
 int take_start_launch(const S* Vt, int n, int b, T* Tb, int64_t ld, cudaStream_t st);
@@ -124,6 +130,8 @@ struct rlobpcg_plan_s {
   size_t twork_bytes = 0;
   void* coop = nullptr;     // global scratch of the cooperative BCGS2 + Orth kernel
   size_t coop_bytes = 0;
+  void* VL = nullptr;       // locked columns of V (n x b) and of A V (m x b), with locking
+  void* AVL = nullptr;
   cudaEvent_t ev[10] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   // Per-iteration Gram timing events (3 per slot, a ring) and the pinned history of residual
   // norms and Ritz values, copied asynchronously; the host synchronises only to test the stop rule.
@@ -208,13 +216,14 @@ struct StopRule {
 // CUDA cores or, for plans with gram_split, on the tensor cores from the digits of A.
 template <class T>
 int gram_pass(rlobpcg_plan_s* p, const T* A, int64_t lda, const T* W, T* AW, T* G, int resid_mode,
-              cudaEvent_t mid = nullptr, bool w_ready = false) {
+              cudaEvent_t mid = nullptr, bool w_ready = false, int bw = 0) {
   const int64_t ld = 3 * p->b;
+  if (bw <= 0) bw = p->b;   // block width (the active columns with locking)
   if (p->split)
-    return split_gram(p->sprep, p->m, p->n, (const double*)W, p->b, ld, (double*)AW, ld, (double*)G, ld, p->swork,
+    return split_gram(p->sprep, p->m, p->n, (const double*)W, bw, ld, (double*)AW, ld, (double*)G, ld, p->swork,
                       p->swork_bytes, (resid_mode ? split::SPLIT_RESID : 0) | (w_ready ? split::SPLIT_W_READY : 0),
                       p->err, mid, p->st);
-  return gram_dispatch(A, p->m, p->n, lda, p->dtype, W, p->b, ld, AW, ld, G, ld, p->gwork, p->gwork_bytes, resid_mode,
+  return gram_dispatch(A, p->m, p->n, lda, p->dtype, W, bw, ld, AW, ld, G, ld, p->gwork, p->gwork_bytes, resid_mode,
                        p->err, p->st);
 }
 
@@ -276,7 +285,7 @@ int solve_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, double tau, double* s
     for (int it = 0; it < 8; ++it) {
       RL_TRY((trimul_launch<T, S>((const S*)p->R_r, n, Z, qt, qt, Y, qt, 0, 0, st)));
       RL_TRY((trimul_launch<T, S>((const S*)p->R_c, n, Y, qt, qt, Z, qt, 1, 1, st)));
-      RL_TRY(bcgs2_orth_launch<T>(Z, n, qt, qt, 0, 0, (T*)p->E, 0, st, nullptr, p->err, nullptr, p->coop, p->coop_bytes));
+      RL_TRY(bcgs2_orth_launch<T>(Z, n, qt, qt, 0, 0, (T*)p->E, 0, st, nullptr, p->err, nullptr, p->coop, p->coop_bytes, 0));
     }
     RL_TRY((trimul_launch<T, S>((const S*)p->R_r, n, Z, qt, qt, Y, qt, 0, 0, st)));
     RL_TRY(tsqr_impl<T>(Y, n, qt, qt, (T*)p->Rt, p->twork, p->twork_bytes, st));
@@ -289,7 +298,7 @@ int solve_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, double tau, double* s
     for (int it = 0; it < 3; ++it) {
       RL_TRY((trimul_launch<T, S>((const S*)p->Rinv_c, n, Z, q, q, Y, q, 1, 1, st)));
       RL_TRY((trimul_launch<T, S>((const S*)p->Rinv_r, n, Y, q, q, Z, q, 0, 0, st)));
-      RL_TRY(bcgs2_orth_launch<T>(Z, n, q, q, 0, 0, (T*)p->E, 0, st, nullptr, p->err, nullptr, p->coop, p->coop_bytes));
+      RL_TRY(bcgs2_orth_launch<T>(Z, n, q, q, 0, 0, (T*)p->E, 0, st, nullptr, p->err, nullptr, p->coop, p->coop_bytes, 0));
     }
     RL_TRY((trimul_launch<T, S>((const S*)p->R_r, n, Z, q, q, Y, q, 0, 0, st)));
     RL_TRY(tsqr_impl<T>(Y, n, q, q, (T*)p->Rt, p->twork, p->twork_bytes, st));
@@ -304,7 +313,7 @@ int solve_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, double tau, double* s
   if (p->split) wd = split_w_digits(p->swork, m, n, b);
   bool w_ready = false;
   RL_TRY(bcgs2_orth_launch<T>(Tb, n, b, ld, 0, 0, (T*)p->E, 0, st, p->split ? &wd : nullptr, p->err, &w_ready,
-                              p->coop, p->coop_bytes));
+                              p->coop, p->coop_bytes, 0));
   RL_TRY(gram_pass<T>(p, A, lda, Tb, ATb, GTb, 0, nullptr, w_ready));
   RL_TRY(tsqr_impl<T>(ATb, m, b, ld, (T*)p->Rt, p->twork, p->twork_bytes, st));
   RL_TRY(rr_small_launch<T>((const T*)p->Rt, b, b, p->theta, (T*)p->K, p->K_cap, p->info, st));
@@ -352,43 +361,157 @@ int solve_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, double tau, double* s
     drained = upto;
     return RLOBPCG_OK;
   };
+  // Locking (Sec. 2.3): the active columns sit at [0, a) (V), [a, 2a) (W), [2a, 3a) (X) of the
+  // state (row-major, ld 3b); locked columns move to VL / AVL, keep their Ritz value and residual
+  // norm (frozen in the history, which stays indexed by the original column slot), and W is
+  // made orthogonal to them as well. Without locking a = b throughout.
+  const bool locking = p->opts.locking != 0;
+  int a = b, nl = 0;
+  std::vector<int> slot_of(b), lslot;
+  for (int j = 0; j < b; ++j) slot_of[j] = j;
+  std::vector<double> th_cur(b, 0.0), r_cur = hist.r[0], thL, rL;
+  for (int j = 0; j < b; ++j) th_cur[j] = theta0[j];
+  T* VL = (T*)p->VL;
+  T* AVL = (T*)p->AVL;
   for (int i = 0; i < max_iter; ++i) {
-    // W = P (P^* R_i), then BCGS2 against [V X] and Orth
-    RL_TRY((precond_launch<T, S>((const S*)p->Rinv_r, (const S*)p->Rinv_c, n, b, (const T*)p->Rs, (T*)p->Y, Tb, ld, b, st)));
-    RL_TRY(bcgs2_orth_launch<T>(Tb, n, b, ld, b, nx, (T*)p->E, 2, st, p->split ? &wd : nullptr, p->err, &w_ready,
-                                p->coop, p->coop_bytes));
-    const int c = 2 * b + nx;
+    // W = P (P^* R_i), then BCGS2 against [V X] (and the locked columns) and Orth
+    RL_TRY((precond_launch<T, S>((const S*)p->Rinv_r, (const S*)p->Rinv_c, n, a, (const T*)p->Rs, (T*)p->Y, Tb, ld, a,
+                                 st)));
+    RL_TRY(bcgs2_orth_launch<T>(Tb, n, a, ld, a, nx, (T*)p->E, 2, st, p->split ? &wd : nullptr, p->err, &w_ready,
+                                p->coop, p->coop_bytes, p->opts.orth_mode, VL, nl, b));
+    const int c = 2 * a + nx;
     cudaEvent_t* e = &p->gev[(size_t)(i % kRing) * 3];
     RL_CUDA(cudaEventRecord(e[0], st));
     // A W and A^H (A W) (the split path records the boundary between its two kernels in e[1])
-    RL_TRY(gram_pass<T>(p, A, lda, Tb + b, ATb + b, GTb + b, 0, p->split ? e[1] : nullptr, w_ready));
+    RL_TRY(gram_pass<T>(p, A, lda, Tb + a, ATb + a, GTb + a, 0, p->split ? e[1] : nullptr, w_ready, a));
     RL_CUDA(cudaEventRecord(e[2], st));
     // Rayleigh-Ritz by SVD of A_T (TSQR + Jacobi of R_T). Running it on a second stream beside
     // the A^T (A W) kernel was measured slower on GB300 (both contend for the FP64 pipes).
     RL_TRY(tsqr_impl<T>(ATb, m, c, ld, (T*)p->Rt, p->twork, p->twork_bytes, st));
-    RL_TRY(rr_small_launch<T>((const T*)p->Rt, c, b, p->theta, (T*)p->K, p->K_cap, p->info, st));
-    matvecs += b;
-    theta_s = p->theta + (c - b);
-    RL_TRY(update_launch<T>(Tb, n, ATb, m, GTb, ld, c, b, (const T*)p->K, st));
+    RL_TRY(rr_small_launch<T>((const T*)p->Rt, c, a, p->theta, (T*)p->K, p->K_cap, p->info, st));
+    matvecs += a;
+    theta_s = p->theta + (c - a);
+    RL_TRY(update_launch<T>(Tb, n, ATb, m, GTb, ld, c, a, (const T*)p->K, st));
     if (refresh > 0 && (i + 1) % refresh == 0) {
-      RL_TRY(gram_pass<T>(p, A, lda, nullptr, ATb, GTb, 1));
-      matvecs += b;
+      RL_TRY(gram_pass<T>(p, A, lda, nullptr, ATb, GTb, 1, nullptr, false, a));
+      matvecs += a;
     }
-    RL_TRY((residual_launch<T>(Tb, GTb, n, b, ld, theta_s, (T*)p->Res, p->res_norm, (T*)p->Rs, p->err, st)));
+    RL_TRY((residual_launch<T>(Tb, GTb, n, a, ld, theta_s, (T*)p->Res, p->res_norm, (T*)p->Rs, p->err, st)));
     double* slot = p->hist_h + (size_t)(i + 1) * 2 * b;
-    RL_CUDA(cudaMemcpyAsync(slot, p->res_norm, b * sizeof(double), cudaMemcpyDeviceToHost, st));
-    RL_CUDA(cudaMemcpyAsync(slot + b, theta_s, b * sizeof(double), cudaMemcpyDeviceToHost, st));
+    RL_CUDA(cudaMemcpyAsync(slot, p->res_norm, a * sizeof(double), cudaMemcpyDeviceToHost, st));
+    RL_CUDA(cudaMemcpyAsync(slot + b, theta_s, a * sizeof(double), cudaMemcpyDeviceToHost, st));
     it = i + 1;
-    nx = b;
+    nx = a;
     const bool check = fixed <= 0 && i % check_every == 0;
-    if (check || i + 1 == max_iter || i + 1 - drained >= kRing - 1) {
-      RL_CUDA(cudaStreamSynchronize(st));
-      RL_TRY(drain(i + 1));
-      if (check && hist.check(i, sigma11, tau, stag)) {
-        stop = RLOBPCG_STOP_CONVERGED;
-        break;
+    if (!locking) {
+      if (check || i + 1 == max_iter || i + 1 - drained >= kRing - 1) {
+        RL_CUDA(cudaStreamSynchronize(st));
+        RL_TRY(drain(i + 1));
+        if (check && hist.check(i, sigma11, tau, stag)) {
+          stop = RLOBPCG_STOP_CONVERGED;
+          break;
+        }
       }
+      continue;
     }
+    // locking: every iteration, the history row in slot order (locked slots frozen), then the
+    // stop rule and the columns that met the tolerance
+    RL_CUDA(cudaStreamSynchronize(st));
+    for (int q = 0; q < a; ++q) {
+      r_cur[slot_of[q]] = slot[q];
+      th_cur[slot_of[q]] = slot[b + q];
+    }
+    hist.r.push_back(r_cur);
+    hist.th.push_back(th_cur);
+    {
+      float gms = 0;
+      RL_CUDA(cudaEventElapsedTime(&gms, e[0], e[2]));
+      gram_ms += gms;
+      ++gram_passes;
+      if (p->split) {
+        RL_CUDA(cudaEventElapsedTime(&gms, e[0], e[1]));
+        gram_ab_ms += gms;
+        RL_CUDA(cudaEventElapsedTime(&gms, e[1], e[2]));
+        gram_atb_ms += gms;
+      }
+      drained = i + 1;
+    }
+    if (check && hist.check(i, sigma11, tau, stag)) {
+      stop = RLOBPCG_STOP_CONVERGED;
+      break;
+    }
+    std::vector<int> keep, lock;
+    for (int q = 0; q < a; ++q) (slot[q] <= sigma11 * sigma11 * tau ? lock : keep).push_back(q);
+    if (lock.empty()) continue;
+    for (int q : lock) {
+      RL_TRY(copy_cols_launch<T>(Tb, ld, q, VL, b, nl, n, 1, st));
+      RL_TRY(copy_cols_launch<T>(ATb, ld, q, AVL, b, nl, m, 1, st));
+      thL.push_back(slot[b + q]);
+      rL.push_back(slot[q]);
+      lslot.push_back(slot_of[q]);
+      ++nl;
+    }
+    const int an = (int)keep.size();
+    {
+      std::vector<int> src, dst;
+      for (int t = 0; t < an; ++t) {
+        src.push_back(keep[t]);
+        dst.push_back(t);
+        src.push_back(2 * a + keep[t]);
+        dst.push_back(2 * an + t);
+      }
+      RL_TRY(gather_cols_launch<T>(Tb, n, ld, src.data(), dst.data(), (int)src.size(), st));
+      RL_TRY(gather_cols_launch<T>(ATb, m, ld, src.data(), dst.data(), (int)src.size(), st));
+      RL_TRY(gather_cols_launch<T>(GTb, n, ld, src.data(), dst.data(), (int)src.size(), st));
+    }
+    std::vector<int> so(an);
+    std::vector<double> thk(an);
+    for (int t = 0; t < an; ++t) {
+      so[t] = slot_of[keep[t]];
+      thk[t] = slot[b + keep[t]];
+    }
+    slot_of = so;
+    a = an;
+    nx = a;
+    if (a == 0) {   // every column locked: the solve ends (also in fixed-iteration mode)
+      if (fixed <= 0) stop = RLOBPCG_STOP_CONVERGED;
+      break;
+    }
+    if (p->split) wd = split_w_digits(p->swork, m, n, a);
+    w_ready = false;
+    // the residual of the kept columns in the compacted layout (the preconditioner's input)
+    RL_CUDA(cudaMemcpyAsync(p->theta, thk.data(), a * sizeof(double), cudaMemcpyHostToDevice, st));
+    RL_TRY((residual_launch<T>(Tb, GTb, n, a, ld, p->theta, (T*)p->Res, p->res_norm, (T*)p->Rs, p->err, st)));
+    theta_s = p->theta;
+    RL_CUDA(cudaStreamSynchronize(st));   // thk lives on the host stack
+  }
+  if (locking) {
+    // outputs in slot-independent order: the active columns, then the locked ones, sorted by
+    // descending Ritz value (the order outputs_launch expects)
+    std::vector<double> thA(a), rA(a);
+    if (a > 0) {
+      RL_CUDA(cudaMemcpyAsync(thA.data(), theta_s, a * sizeof(double), cudaMemcpyDeviceToHost, st));
+      RL_CUDA(cudaMemcpyAsync(rA.data(), p->res_norm, a * sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
+    if (nl > 0) {
+      RL_TRY(copy_cols_launch<T>(VL, b, 0, Tb, ld, a, n, nl, st));
+      RL_TRY(copy_cols_launch<T>(AVL, b, 0, ATb, ld, a, m, nl, st));
+    }
+    RL_CUDA(cudaStreamSynchronize(st));
+    std::vector<double> thAll(thA), rAll(rA);
+    thAll.insert(thAll.end(), thL.begin(), thL.end());
+    rAll.insert(rAll.end(), rL.begin(), rL.end());
+    std::vector<int> perm(b), dst(b);
+    for (int j = 0; j < b; ++j) { perm[j] = j; dst[j] = j; }
+    std::stable_sort(perm.begin(), perm.end(), [&](int x, int y) { return thAll[x] > thAll[y]; });
+    std::vector<double> ths(b), rs(b);
+    for (int j = 0; j < b; ++j) { ths[j] = thAll[perm[j]]; rs[j] = rAll[perm[j]]; }
+    RL_TRY(gather_cols_launch<T>(Tb, n, ld, perm.data(), dst.data(), b, st));
+    RL_TRY(gather_cols_launch<T>(ATb, m, ld, perm.data(), dst.data(), b, st));
+    RL_CUDA(cudaMemcpyAsync(p->theta, ths.data(), b * sizeof(double), cudaMemcpyHostToDevice, st));
+    RL_CUDA(cudaMemcpyAsync(p->res_norm, rs.data(), b * sizeof(double), cudaMemcpyHostToDevice, st));
+    RL_CUDA(cudaStreamSynchronize(st));
+    theta_s = p->theta;
   }
   RL_CUDA(cudaEventRecord(p->ev[3], st));
   // keep the history for rlobpcg_history (row 0: the start block's Ritz values)
@@ -470,6 +593,8 @@ extern "C" int rlobpcg_default_opts(rlobpcg_opts* o) {
   o->residual_refresh_every = 0;
   o->gram_split = 1;
   o->tau = -1.0;
+  o->orth_mode = RLOBPCG_ORTH_HOUSEHOLDER;
+  o->locking = 0;
   return RLOBPCG_OK;
 }
 
@@ -484,8 +609,10 @@ int resolve_plan_args(int64_t m, int64_t n, int k, int dtype, const rlobpcg_opts
   const int64_t d = o->d > 0 ? o->d : 4 * n;
   if (k < 1 || b < k || 3 * (int64_t)b > n || n > m || o->zeta < 1 || d < n || d < o->zeta || b > 21 ||
       n > (1 << 20) || (o->sketch_prec != RLOBPCG_SKETCH_F64 && o->sketch_prec != RLOBPCG_SKETCH_F32 &&
-                        o->sketch_prec != RLOBPCG_SKETCH_F32_REFINE)) {
-    set_last_error("invalid plan arguments (need 1 <= k <= b <= 21, 3b <= n <= m, n <= d, zeta <= d)", __FILE__, __LINE__);
+                        o->sketch_prec != RLOBPCG_SKETCH_F32_REFINE) ||
+      (o->orth_mode != RLOBPCG_ORTH_HOUSEHOLDER && o->orth_mode != RLOBPCG_ORTH_SVQB) ||
+      (o->locking != 0 && o->locking != 1)) {
+    set_last_error("invalid plan arguments (need 1 <= k <= b <= 21, 3b <= n <= m, n <= d, zeta <= d, a known sketch precision and orth_mode, locking 0 or 1)", __FILE__, __LINE__);
     return RLOBPCG_ERR_INVALID_ARG;
   }
   if (o->max_iter <= 0) o->max_iter = (b == 1) ? 200 : 100;
@@ -575,8 +702,12 @@ int plan_buffers(PlanAlloc& A_, rlobpcg_plan_s* p, int64_t m, int64_t n, int b, 
   }
   *twork = std::max(tsqr_workspace_bytes(m, (int)ld, esz), tsqr_workspace_bytes(n, qmax, esz));
   RL_B(twork, *twork);
+  if (o.locking) {
+    RL_B(VL, (size_t)n * b * esz);
+    RL_B(AVL, (size_t)m * b * esz);
+  }
   {
-    const size_t cb = bcgs2_coop_bytes(n, (int)std::max<int64_t>(ld, qmax), std::max(b, qmax), esz);
+    const size_t cb = bcgs2_coop_bytes(n, (int)std::max<int64_t>(ld, qmax) + b, std::max(b, qmax), esz);
     RL_B(coop, cb);
     if (p) p->coop_bytes = cb;
   }

@@ -489,6 +489,17 @@ def test_locking_deflates_converged_columns(orth_mode):
     assert np.all(r1["resid"] <= r1["sigma11"] ** 2 * tau)
 
 
+def test_locking_ends_a_fixed_iteration_solve_once_every_column_locked():
+    """Sec. 2.3: with every column locked nothing is left to iterate on; a tolerance that the
+    first iteration already meets ends a fixed-iteration solve after one iteration, with b + b
+    matrix-vector products and the same triplets as the plain method's first iteration."""
+    A, s, V = _spread_bottom()
+    r = oracle.rlobpcg(A, k=2, b=3, seed=3, fixed_iters=8, tau=1e-2, locking=True)
+    p = oracle.rlobpcg(A, k=2, b=3, seed=3, fixed_iters=1, tau=1e-2)
+    assert r["iters"] == 1 and r["locked"].all() and r["matvecs"] == 6
+    assert np.array_equal(r["sigma"], p["sigma"])
+
+
 def test_locking_off_is_the_plain_method():
     A, s, V = _spread_bottom()
     a = oracle.rlobpcg(A, k=2, seed=3, fixed_iters=6)
