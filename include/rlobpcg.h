@@ -229,6 +229,48 @@ int rlobpcg_server_stats(rlobpcg_server_t s, int64_t* completed, double* p50_ms,
 int rlobpcg_server_destroy(rlobpcg_server_t s);
 
 /*
+ * Batched solves (an addition of this library for many small problems; the paper solves one at a
+ * time). rlobpcg_solve_batch runs `count` solves, one per plan: plans[i] distinct, each created by
+ * rlobpcg_plan for its own (m_i, n_i, k_i) with dtype RLOBPCG_F64, block b_i <= 5, n_i <= 512, and
+ * neither locking, SVQB nor residual refresh (else RLOBPCG_ERR_UNSUPPORTED, nothing run). A[i] is
+ * a DEVICE pointer to the m_i x n_i row-major matrix with leading dimension lda[i] >= n_i.
+ *
+ * Each solve's set-up -- sketch, factor, start block and first Rayleigh-Ritz step (Alg. 2) -- runs
+ * on its plan's stream (set-ups of different plans overlap, on up to 8 host threads). The LOBPCG
+ * iterations of all solves then run together on a stream of the library's own: per iteration two
+ * persistent kernels over a device work queue of (solve, row block) items, (1) W = P P^* R with
+ * the preconditioner formed once per solve as the n x n matrix (R^H R)^{-1}, then BCGS2 + Orth of
+ * W, and (2) the Gram products A W and A^H (A W) by row tiles, each tile also reducing its rows of
+ * A_T to a triangular factor, the factors and G partials merged in a fixed two-level order, and
+ * Rayleigh-Ritz, the update, the residual and the stopping rule of Sec. 2.1 for a solve in the same
+ * launch, by the CTA that finishes its last tile. Four iterations are replayed as one captured
+ * CUDA graph; a solve that has stopped takes no further part. Outputs, per solve, as rlobpcg_solve:
+ * sigma[i] (k_i, ascending), V[i] (n_i x k_i), U[i] (m_i x k_i; U or U[i] may be NULL), resid[i]
+ * (may be NULL); infos and status (count entries each) may be NULL. Host or device output
+ * pointers are accepted as in rlobpcg_solve. The stopping decisions are the device's.
+ *
+ * A solve's arithmetic depends only on its own data and on the tile shape of its (n, b) class
+ * (rlobpcg_batch_tile), so it gives the same bits alone and in any batch of one process.
+ * Synchronous: returns once every output is written. Returns the first negative per-solve status,
+ * else RLOBPCG_OK (RLOBPCG_NOT_CONVERGED is reported per solve in status).
+ */
+int rlobpcg_solve_batch(int count, rlobpcg_plan_t* plans, const void* const* A, const int64_t* lda,
+                        double* const* sigma, void* const* V, void* const* U, double* const* resid,
+                        rlobpcg_info* infos, int* status, void* stream);
+
+/* The tile shape the batched kernels use for solves of n columns and block b (n <= 512, b <= 5):
+ * trows rows of A per work item and rt rows per shared-memory stage. The class is (the power of
+ * two >= max(n, 32), b). On first use of a class the library's autotuner times every shape that
+ * fits shared memory on synthetic solves of the class (on `stream`) and keeps the fastest; the
+ * choice then stays fixed for the process. */
+int rlobpcg_batch_tile(int64_t n, int b, int* trows, int* rt, void* stream);
+
+/* Pin the tile shape of the (n, b) class (one of the candidates the autotuner considers:
+ * trows in {256, 512, 1024, 2048}, rt in {16, 32}, within shared memory), e.g. to reproduce
+ * results across processes. INVALID_ARG for a shape outside the candidates. */
+int rlobpcg_batch_set_tile(int64_t n, int b, int trows, int rt);
+
+/*
  * Health check of the bounded-wait path (an addition of this library; the paper has no
  * counterpart). Every device-side wait of the library gives up after a bounded number of tries,
  * records the timeout, releases what its kernel holds and returns, so that a lost arrival surfaces

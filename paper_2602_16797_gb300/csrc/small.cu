@@ -15,6 +15,7 @@
 #include <cooperative_groups.h>
 #include <type_traits>
 
+#include "batch.cuh"
 #include "common.cuh"
 #include "split.cuh"
 
@@ -625,10 +626,10 @@ __device__ int jacobi_mixed32(double* X, double* V, int c, int N, double tol, do
   return sweeps;
 }
 
+// One CTA (any multiple of 32 threads); smem_raw: rr_small_smem(c, b) bytes of dynamic shared memory.
 template <class T>
-__global__ void __launch_bounds__(1024) rr_small_kernel(const T* __restrict__ Rt, int c, int b, double* theta_out,
-                                                         T* K_out, int* info) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ void rr_small_cta(unsigned char* smem_raw, const T* __restrict__ Rt, int c, int b, double* theta_out,
+                             T* K_out, int* info) {
   T* X = reinterpret_cast<T*>(smem_raw);        // c x c col-major
   T* V = X + c * c;                             // c x c col-major
   T* C = V + c * c;                             // c x c col-major (sorted)
@@ -824,6 +825,20 @@ __global__ void __launch_bounds__(1024) rr_small_kernel(const T* __restrict__ Rt
     K_out[i] = v;
   }
   if (tid == 0 && info) { info[0] += sweep; info[1] += 1; }   // totals over the solve
+}
+
+template <class T>
+__global__ void __launch_bounds__(1024) rr_small_kernel(const T* __restrict__ Rt, int c, int b, double* theta_out,
+                                                         T* K_out, int* info) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  rr_small_cta<T>(smem_raw, Rt, c, b, theta_out, K_out, info);
+}
+
+template <class T>
+inline size_t rr_small_smem(int c, int b) {
+  const int pdim = c - b;
+  return (size_t)3 * c * c * sizeof(T) + (size_t)c * b * sizeof(T) + c * sizeof(double) + (c + 4) * sizeof(int) + 16 +
+         (size_t)pdim * b * sizeof(T);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1184,12 +1199,11 @@ __device__ void cta_svqb(const T* Ws, int rows, int b, T* S, T* Z, double* dsc, 
   __syncthreads();
 }
 
+// One CTA of exactly 256 threads; smem_raw: bcgs2_smem_bytes(n, b, nx + nl) bytes.
 template <class T>
-__global__ void __launch_bounds__(256) bcgs2_orth_smem_kernel(T* __restrict__ Tb, int n, int b, int64_t ld, int wo,
-                                                              int nx, int passes, split::WDigits wd, int* err,
-                                                              int svqb, const T* __restrict__ Dl, int nl,
-                                                              int64_t ldl) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ void bcgs2_orth_cta(unsigned char* smem_raw, T* __restrict__ Tb, int n, int b, int64_t ld, int wo, int nx,
+                               int passes, split::WDigits wd, int* err, int svqb, const T* __restrict__ Dl, int nl,
+                               int64_t ldl) {
   constexpr int NT = 256, NW = NT / 32;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int q = b + nx + nl;   // V, X, and the deflated (locked) columns Dl
@@ -1366,6 +1380,22 @@ __global__ void __launch_bounds__(256) bcgs2_orth_smem_kernel(T* __restrict__ Tb
     for (int qd = 0; qd < split::SL; ++qd) out[split::core_off(qd * BP + j, kk, N)] = split::bf16_of(d[qd]);
   }
   (void)red;
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) bcgs2_orth_smem_kernel(T* __restrict__ Tb, int n, int b, int64_t ld, int wo,
+                                                              int nx, int passes, split::WDigits wd, int* err,
+                                                              int svqb, const T* __restrict__ Dl, int nl,
+                                                              int64_t ldl) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  bcgs2_orth_cta<T>(smem_raw, Tb, n, b, ld, wo, nx, passes, wd, err, svqb, Dl, nl, ldl);
+}
+
+// dynamic shared memory of bcgs2_orth_cta for q = b + (columns projected out besides V)
+template <class T>
+inline size_t bcgs2_smem_bytes(int n, int b, int extra) {
+  const int q = b + extra;
+  return ((size_t)n * (q + b) + 5 * (size_t)q * b + 3 * b) * sizeof(T) + 16 * 8 * sizeof(double) + 64;
 }
 
 // L2-coherent load (data written by other CTAs of a cooperative grid)
@@ -1787,9 +1817,7 @@ int rr_small_launch(const T* Rt, int c, int b, double* theta, T* K, size_t k_cap
     set_last_error("rr_small: coefficient block larger than its buffer", __FILE__, __LINE__);
     return RLOBPCG_ERR_INVALID_ARG;
   }
-  const int pdim = c - b;
-  size_t smem = (size_t)3 * c * c * sizeof(T) + (size_t)c * b * sizeof(T) + c * sizeof(double) +
-                (c + 4) * sizeof(int) + 16 + (size_t)pdim * b * sizeof(T);
+  const size_t smem = rr_small_smem<T>(c, b);
   RL_TRY(allow_dynamic_smem(rr_small_kernel<T>, smem));
   int threads = min(1024, max(64, ((c + 1) / 2) * 32));
   if (std::is_same<T, double>::value && c <= 16) threads = 128;   // two Jacobi pairs per warp
@@ -1910,7 +1938,7 @@ int bcgs2_orth_launch(T* Tb, int n, int b, int64_t ld, int wo, int nx, T* E, int
       }
     }
   }
-  const size_t smem_s = ((size_t)n * (q + b) + 5 * (size_t)q * b + 3 * b) * sizeof(T) + 16 * 8 * sizeof(double) + 64;
+  const size_t smem_s = bcgs2_smem_bytes<T>(n, b, nx + nl);
   if (smem_s <= max_smem_optin() - 1024) {
     split::WDigits w{};
     if (wd && wd->Wsl && sizeof(T) == sizeof(double) && b <= wd->BP) w = *wd;
@@ -2000,4 +2028,7 @@ int gather_cols_launch(T* buf, int64_t rows, int64_t ld, const int* src, const i
 }
 template int gather_cols_launch<double>(double*, int64_t, int64_t, const int*, const int*, int, cudaStream_t);
 template int gather_cols_launch<cd>(cd*, int64_t, int64_t, const int*, const int*, int, cudaStream_t);
+
+// batched iterations of many small solves (they reuse the one-CTA bodies above)
+#include "batch_kernels.cuh"
 }  // namespace rl

@@ -9,10 +9,16 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <limits>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
 #include <type_traits>
 #include <vector>
 
+#include "batch.cuh"
 #include "common.cuh"
 #include "split.cuh"
 
@@ -227,9 +233,26 @@ int gram_pass(rlobpcg_plan_s* p, const T* A, int64_t lda, const T* W, T* AW, T* 
                        p->err, p->st);
 }
 
+// State of one solve carried between its phases (set-up, iterations, outputs), so that a batch
+// of solves can run the set-up and output phases per solve around one batched iteration loop.
+struct SolveRun {
+  double tau = 0;
+  double sigma11 = 0;
+  std::vector<double> theta0;
+  StopRule hist;
+  int herr = 0;
+  long launches0 = 0;
+  double gram_ms = 0, gram_ab_ms = 0, gram_atb_ms = 0;
+  int gram_passes = 0;
+  int sweeps = 0;
+  int it = 0, stop = 0, matvecs = 0, nx = 0;
+  const double* theta_s = nullptr;
+  split::WDigits wd{};
+  bool w_ready = false;
+};
+
 template <class T, class S>
-int solve_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, double tau, double* sigma, T* Vout, T* Uout,
-               double* resid, rlobpcg_info* info) {
+int setup_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, SolveRun& r, double tau_in) {
   cudaStream_t st = p->st;
   const int64_t m = p->m;
   const int n = (int)p->n, b = p->b, k = p->k, d = p->d;
@@ -237,9 +260,30 @@ int solve_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, double tau, double* s
   T* Tb = (T*)p->Tb;
   T* ATb = (T*)p->ATb;
   T* GTb = (T*)p->GTb;
-  const long launches0 = launch_count();
-  double gram_ms = 0, gram_ab_ms = 0, gram_atb_ms = 0;
-  int gram_passes = 0;
+  double& tau = r.tau;
+  double& sigma11 = r.sigma11;
+  std::vector<double>& theta0 = r.theta0;
+  StopRule& hist = r.hist;
+  int& herr = r.herr;
+  double& gram_ms = r.gram_ms;
+  double& gram_ab_ms = r.gram_ab_ms;
+  double& gram_atb_ms = r.gram_atb_ms;
+  int& gram_passes = r.gram_passes;
+  int& sweeps = r.sweeps;
+  int& it = r.it;
+  int& stop = r.stop;
+  int& matvecs = r.matvecs;
+  int& nx = r.nx;
+  const double*& theta_s = r.theta_s;
+  split::WDigits& wd = r.wd;
+  bool& w_ready = r.w_ready;
+  (void)tau; (void)sigma11; (void)theta0; (void)hist; (void)herr; (void)gram_ms; (void)gram_ab_ms;
+  (void)gram_atb_ms; (void)gram_passes; (void)sweeps; (void)it; (void)stop; (void)matvecs; (void)nx;
+  (void)theta_s; (void)wd; (void)w_ready; (void)A; (void)lda; (void)Tb; (void)ATb; (void)GTb; (void)m; (void)n;
+  (void)k; (void)d; (void)ld; (void)st;
+  r = SolveRun{};
+  r.tau = tau_in;
+  r.launches0 = launch_count();
   RL_CUDA(cudaMemsetAsync(p->err, 0, sizeof(int), st));
   RL_CUDA(cudaMemsetAsync(p->info, 0, 2 * sizeof(int), st));
   RL_CUDA(cudaEventRecord(p->ev[0], st));
@@ -251,7 +295,6 @@ int solve_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, double tau, double* s
   } else {
     RL_TRY(nonfinite_scan_launch<T>(A, m, n, lda, p->err, st));
   }
-  int herr = 0;
   RL_CUDA(cudaMemcpyAsync(&herr, p->err, sizeof(int), cudaMemcpyDeviceToHost, st));
 
   // Sketch and factorise (the first steps of Alg. 2)
@@ -260,7 +303,6 @@ int solve_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, double tau, double* s
   RL_TRY(sketch_dispatch(A, m, n, lda, p->dtype, d, p->opts.zeta, p->opts.seed,
                          refine ? RLOBPCG_SKETCH_F64 : p->opts.sketch_prec, p->SA, st));
   RL_CUDA(cudaEventRecord(p->ev[1], st));
-  int sweeps = 0;
   const bool exact = p->opts.exact_sketch_svd != 0;
   if constexpr (std::is_same<S, T>::value) {
     if (refine)
@@ -270,7 +312,6 @@ int solve_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, double tau, double* s
   if (!refine)
     RL_TRY(factor_impl<S>((S*)p->SA, d, n, (S*)p->R_c, (S*)p->R_r, p->sk_sigma, (S*)p->Vt, (S*)p->Rinv_r,
                           (S*)p->Rinv_c, p->fwork, p->fwork_bytes, st, &sweeps, exact, p->err));
-  double sigma11 = 0;
   if (exact) {
     RL_CUDA(cudaMemcpyAsync(&sigma11, p->sk_sigma, sizeof(double), cudaMemcpyDeviceToHost, st));
     // Sketch-and-solve start V~(:, n-b+1:n) (Alg. 2)
@@ -309,9 +350,7 @@ int solve_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, double tau, double* s
   if (herr & DEV_ERR_NONFINITE) return RLOBPCG_ERR_NONFINITE;
 
   // Sketch-and-solve start and the initial Rayleigh-Ritz step (Alg. 2)
-  split::WDigits wd{};
   if (p->split) wd = split_w_digits(p->swork, m, n, b);
-  bool w_ready = false;
   RL_TRY(bcgs2_orth_launch<T>(Tb, n, b, ld, 0, 0, (T*)p->E, 0, st, p->split ? &wd : nullptr, p->err, &w_ready,
                               p->coop, p->coop_bytes, 0));
   RL_TRY(gram_pass<T>(p, A, lda, Tb, ATb, GTb, 0, nullptr, w_ready));
@@ -321,8 +360,7 @@ int solve_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, double tau, double* s
   RL_TRY((residual_launch<T>(Tb, GTb, n, b, ld, p->theta, (T*)p->Res, p->res_norm, (T*)p->Rs, p->err, st)));
   RL_CUDA(cudaEventRecord(p->ev[2], st));
 
-  StopRule hist;
-  std::vector<double> theta0(b);
+  theta0.assign(b, 0.0);
   {
     std::vector<double> hr(b);
     RL_CUDA(cudaMemcpyAsync(hr.data(), p->res_norm, b * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -332,14 +370,47 @@ int solve_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, double tau, double* s
     hist.th.push_back(std::vector<double>(b, std::numeric_limits<double>::infinity()));
   }
 
+  return RLOBPCG_OK;
+}
+
+template <class T, class S>
+int loop_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, SolveRun& r) {
+  cudaStream_t st = p->st;
+  const int64_t m = p->m;
+  const int n = (int)p->n, b = p->b, k = p->k, d = p->d;
+  const int64_t ld = 3 * b;
+  T* Tb = (T*)p->Tb;
+  T* ATb = (T*)p->ATb;
+  T* GTb = (T*)p->GTb;
+  double& tau = r.tau;
+  double& sigma11 = r.sigma11;
+  std::vector<double>& theta0 = r.theta0;
+  StopRule& hist = r.hist;
+  int& herr = r.herr;
+  double& gram_ms = r.gram_ms;
+  double& gram_ab_ms = r.gram_ab_ms;
+  double& gram_atb_ms = r.gram_atb_ms;
+  int& gram_passes = r.gram_passes;
+  int& sweeps = r.sweeps;
+  int& it = r.it;
+  int& stop = r.stop;
+  int& matvecs = r.matvecs;
+  int& nx = r.nx;
+  const double*& theta_s = r.theta_s;
+  split::WDigits& wd = r.wd;
+  bool& w_ready = r.w_ready;
+  (void)tau; (void)sigma11; (void)theta0; (void)hist; (void)herr; (void)gram_ms; (void)gram_ab_ms;
+  (void)gram_atb_ms; (void)gram_passes; (void)sweeps; (void)it; (void)stop; (void)matvecs; (void)nx;
+  (void)theta_s; (void)wd; (void)w_ready; (void)A; (void)lda; (void)Tb; (void)ATb; (void)GTb; (void)m; (void)n;
+  (void)k; (void)d; (void)ld; (void)st;
   const int fixed = p->opts.fixed_iters;
   const int max_iter = fixed > 0 ? fixed : p->opts.max_iter;
   const bool stag = p->opts.use_stagnation != 0;
   const int check_every = std::max(1, p->opts.check_every);
   const int refresh = p->opts.residual_refresh_every;
-  int nx = 0, it = 0, stop = fixed > 0 ? RLOBPCG_STOP_FIXED : RLOBPCG_STOP_MAX_ITER;
-  int matvecs = b;
-  const double* theta_s = p->theta;
+  nx = 0; it = 0; stop = fixed > 0 ? RLOBPCG_STOP_FIXED : RLOBPCG_STOP_MAX_ITER;
+  matvecs = b;
+  theta_s = p->theta;
   int drained = 0;   // iterations whose history and timings the host has read
   auto drain = [&](int upto) -> int {
     for (int t = drained; t < upto; ++t) {
@@ -513,6 +584,40 @@ int solve_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, double tau, double* s
     RL_CUDA(cudaStreamSynchronize(st));
     theta_s = p->theta;
   }
+  return RLOBPCG_OK;
+}
+
+template <class T, class S>
+int finish_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, SolveRun& r, double* sigma, T* Vout, T* Uout,
+                double* resid, rlobpcg_info* info) {
+  cudaStream_t st = p->st;
+  const int64_t m = p->m;
+  const int n = (int)p->n, b = p->b, k = p->k, d = p->d;
+  const int64_t ld = 3 * b;
+  T* Tb = (T*)p->Tb;
+  T* ATb = (T*)p->ATb;
+  T* GTb = (T*)p->GTb;
+  double& tau = r.tau;
+  double& sigma11 = r.sigma11;
+  std::vector<double>& theta0 = r.theta0;
+  StopRule& hist = r.hist;
+  int& herr = r.herr;
+  double& gram_ms = r.gram_ms;
+  double& gram_ab_ms = r.gram_ab_ms;
+  double& gram_atb_ms = r.gram_atb_ms;
+  int& gram_passes = r.gram_passes;
+  int& sweeps = r.sweeps;
+  int& it = r.it;
+  int& stop = r.stop;
+  int& matvecs = r.matvecs;
+  int& nx = r.nx;
+  const double*& theta_s = r.theta_s;
+  split::WDigits& wd = r.wd;
+  bool& w_ready = r.w_ready;
+  (void)tau; (void)sigma11; (void)theta0; (void)hist; (void)herr; (void)gram_ms; (void)gram_ab_ms;
+  (void)gram_atb_ms; (void)gram_passes; (void)sweeps; (void)it; (void)stop; (void)matvecs; (void)nx;
+  (void)theta_s; (void)wd; (void)w_ready; (void)A; (void)lda; (void)Tb; (void)ATb; (void)GTb; (void)m; (void)n;
+  (void)k; (void)d; (void)ld; (void)st;
   RL_CUDA(cudaEventRecord(p->ev[3], st));
   // keep the history for rlobpcg_history (row 0: the start block's Ritz values)
   p->last_rows = (int)hist.r.size();
@@ -560,7 +665,7 @@ int solve_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, double tau, double* s
     cudaEventElapsedTime(&ms, p->ev[0], p->ev[4]); info->ms_total = ms;
     info->ms_gram = gram_ms;
     info->gram_passes = gram_passes;
-    info->kernel_launches = (int)(launch_count() - launches0);
+    info->kernel_launches = (int)(launch_count() - r.launches0);
     info->jacobi_sweeps = sweeps;
     info->rr_sweeps = rr_stats[0];
     info->rr_calls = rr_stats[1];
@@ -574,6 +679,15 @@ int solve_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, double tau, double* s
   }
   if (dev_err_status(herr) != RLOBPCG_OK) return dev_err_status(herr);
   return stop == RLOBPCG_STOP_MAX_ITER ? RLOBPCG_NOT_CONVERGED : RLOBPCG_OK;
+}
+
+template <class T, class S>
+int solve_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, double tau, double* sigma, T* Vout, T* Uout,
+               double* resid, rlobpcg_info* info) {
+  SolveRun r;
+  RL_TRY((setup_impl<T, S>(p, A, lda, r, tau)));
+  RL_TRY((loop_impl<T, S>(p, A, lda, r)));
+  return finish_impl<T, S>(p, A, lda, r, sigma, Vout, Uout, resid, info);
 }
 
 }  // namespace
@@ -834,4 +948,466 @@ extern "C" int rlobpcg_history(rlobpcg_plan_t p, double* theta, double* resnorm,
   if (theta) memcpy(theta, p->last_theta.data(), (size_t)n * p->b * sizeof(double));
   if (resnorm) memcpy(resnorm, p->last_res.data(), (size_t)n * p->b * sizeof(double));
   return RLOBPCG_OK;
+}
+
+// =================================================================================================
+// Batched solves: many small solves iterate together (Alg. 2 per solve; the iterations of all of
+// them run as two persistent kernels per iteration, replayed from a captured CUDA graph). Each
+// solve's set-up (sketch, factor, start block, first Rayleigh-Ritz step) and outputs use its own
+// plan and stream, exactly as rlobpcg_solve does.
+// =================================================================================================
+namespace {
+
+struct TileChoice {
+  int trows = 0, rt = 0;
+};
+std::mutex g_tile_mu;
+std::map<std::pair<int, int>, TileChoice> g_tile_table;
+
+int n_class(int n) {
+  int c = 32;
+  while (c < n) c *= 2;
+  return c;
+}
+
+// Candidate tile shapes for one (n class, b): every (trows, rt) whose shared memory fits.
+std::vector<TileChoice> tile_candidates(int nc, int b, size_t static_tile) {
+  std::vector<TileChoice> out;
+  for (int trows : {256, 512, 1024, 2048})
+    for (int rt : {16, 32}) {
+      const size_t sm = batch::tile_smem_bytes(nc, batch::abuf_need(nc, b, rt), rt);
+      if (sm + static_tile <= max_smem_optin()) out.push_back({trows, rt});
+    }
+  return out;
+}
+
+struct DevArena {   // one stream-ordered allocation carved into pieces
+  char* base = nullptr;
+  size_t used = 0, cap = 0;
+  std::vector<std::pair<void**, size_t>> req;
+  void want(void** p, size_t bytes) { req.push_back({p, (bytes + 255) & ~(size_t)255}); cap += (bytes + 255) & ~(size_t)255; }
+  int alloc(cudaStream_t st) {
+    if (cap == 0) cap = 256;
+    if (cudaMallocAsync((void**)&base, cap, st) != cudaSuccess) {
+      cudaGetLastError();
+      set_last_error("batch: device workspace", __FILE__, __LINE__);
+      return RLOBPCG_ERR_OOM;
+    }
+    for (auto& r : req) {
+      *r.first = base + used;
+      used += r.second;
+    }
+    return RLOBPCG_OK;
+  }
+  void release(cudaStream_t st) {
+    if (base) cudaFreeAsync(base, st);
+    base = nullptr;
+  }
+};
+
+// The autotuner: times the tile kernel (one full iteration of the Gram, the local factors, the
+// reductions and the Rayleigh-Ritz tails) on synthetic solves of the class, for every candidate,
+// and keeps the fastest. Results depend on the tile shape (it fixes the summation order), so the
+// choice is made once per process and class and then used for every solve of that class.
+int tune_class(int nc, int b, cudaStream_t st, TileChoice* out) {
+  size_t s_pre = 0, s_tile = 0;
+  RL_TRY(batch::static_smem_bytes(&s_pre, &s_tile));
+  const std::vector<TileChoice> cand = tile_candidates(nc, b, s_tile);
+  if (cand.empty()) {
+    set_last_error("batch: no tile shape fits shared memory for this n", __FILE__, __LINE__);
+    return RLOBPCG_ERR_UNSUPPORTED;
+  }
+  constexpr int NS = 4;
+  const int64_t m = 16384;
+  const int n = nc, C = 3 * b;
+  const int tmax = (int)((m + 255) / 256), gmax = (tmax + batch::GS - 1) / batch::GS;
+  DevArena ar;
+  double *A = nullptr, *state = nullptr, *part = nullptr;
+  int *cnt = nullptr, *qh = nullptr, *err = nullptr;
+  batch::Desc* D = nullptr;
+  int2* items = nullptr;
+  const size_t per_state = (size_t)n * C * 3 + (size_t)m * C + (size_t)n * b * 2 + 4 * C + (size_t)C * 2 * b + C * C +
+                           4 * b + 64;
+  const size_t per_part = (size_t)tmax * ((size_t)n * b + C * C) + (size_t)gmax * ((size_t)n * b + C * C);
+  ar.want((void**)&A, (size_t)m * n * 8);
+  ar.want((void**)&state, NS * per_state * 8);
+  ar.want((void**)&part, NS * per_part * 8);
+  ar.want((void**)&cnt, (size_t)NS * (2 + gmax) * 4);
+  ar.want((void**)&qh, 64);
+  ar.want((void**)&err, 64);
+  ar.want((void**)&D, NS * sizeof(batch::Desc));
+  ar.want((void**)&items, (size_t)NS * tmax * sizeof(int2));
+  RL_TRY(ar.alloc(st));
+  int rc = RLOBPCG_OK;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  std::vector<batch::Desc> hd(NS);
+  std::vector<int2> hi;
+  float best = 1e30f;
+  TileChoice pick = cand[0];
+  do {
+    if ((rc = fill_random_launch<double>(A, m, n, n, 0x9E3779B97F4A7C15ull, st))) break;
+    if ((rc = fill_random_launch<double>(state, (int64_t)NS * per_state / 8, 8, 8, 0xD1B54A32D192ED03ull, st))) break;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) { rc = RLOBPCG_ERR_CUDA; break; }
+    for (const TileChoice& tc : cand) {
+      const int nt = (int)((m + tc.trows - 1) / tc.trows), ng = (nt + batch::GS - 1) / batch::GS;
+      hi.clear();
+      for (int s = 0; s < NS; ++s) {
+        double* q = state + (size_t)s * per_state;
+        batch::Desc& d = hd[s];
+        d = batch::Desc{};
+        d.A = A; d.m = m; d.lda = n; d.n = n; d.b = b;
+        d.Tb = q; q += (size_t)n * C;
+        d.GTb = q; q += (size_t)n * C;
+        d.ATb = q; q += (size_t)m * C;
+        d.Rs = q; q += (size_t)n * b;
+        d.Res = q; q += (size_t)n * b;
+        d.res_norm = q; q += C;
+        d.theta = q; q += C;
+        d.K = q; q += (size_t)C * 2 * b;
+        d.Rfin = q; q += (size_t)C * C;
+        d.hist = q; q += 4 * b;
+        double* pp = part + (size_t)s * per_part;
+        d.Gpart = pp; pp += (size_t)tmax * n * b;
+        d.Rpart = pp; pp += (size_t)tmax * C * C;
+        d.Ggrp = pp; pp += (size_t)gmax * n * b;
+        d.Rgrp = pp;
+        d.cnt = cnt + (size_t)s * (2 + gmax);
+        d.err = err; d.rr_info = err + 2;
+        d.ntiles = nt; d.trows = tc.trows; d.rt = tc.rt; d.ngroups = ng; d.nrb = 1;
+        d.iter = 0; d.c = 2 * b; d.nx = 0; d.pending = 0; d.done = 0; d.matvecs = b;
+        d.max_iter = 1; d.fixed = 1; d.check_every = 1; d.use_stag = 0;
+        d.sigma11 = 1.0; d.tau = 0.0;
+        for (int t = 0; t < nt; ++t) hi.push_back(make_int2(s, t));
+      }
+      const int ab = batch::abuf_need(n, b, tc.rt);
+      const size_t smem = batch::tile_smem_bytes(n, ab, tc.rt);
+      if ((rc = batch::prepare(batch::bcgs2_pre_smem(n, b), smem))) break;
+      int per_sm = 1;
+      if ((rc = batch::tile_blocks_per_sm(smem, &per_sm))) break;
+      const int grid = std::max(1, std::min((int)hi.size(), num_sms() * std::max(1, per_sm)));
+      float tot = 0;
+      for (int rep = 0; rep < 4 && !rc; ++rep) {
+        RL_CUDA(cudaMemcpyAsync(D, hd.data(), NS * sizeof(batch::Desc), cudaMemcpyHostToDevice, st));
+        RL_CUDA(cudaMemcpyAsync(items, hi.data(), hi.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
+        RL_CUDA(cudaMemsetAsync(cnt, 0, (size_t)NS * (2 + gmax) * 4, st));
+        RL_CUDA(cudaMemsetAsync(qh, 0, 64, st));
+        RL_CUDA(cudaEventRecord(e0, st));
+        rc = batch::tile_launch(false, D, items, (int)hi.size(), qh, grid, n, ab, smem, st);
+        RL_CUDA(cudaEventRecord(e1, st));
+        RL_CUDA(cudaStreamSynchronize(st));
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0) tot += ms;   // the first launch is a warm-up
+      }
+      if (rc) break;
+      if (tot < best) {
+        best = tot;
+        pick = tc;
+      }
+    }
+  } while (0);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  ar.release(st);
+  cudaStreamSynchronize(st);
+  if (rc) return rc;
+  *out = pick;
+  return RLOBPCG_OK;
+}
+
+int tile_choice(int n, int b, cudaStream_t st, TileChoice* out) {
+  const auto key = std::make_pair(n_class(n), b);
+  {
+    std::lock_guard<std::mutex> lk(g_tile_mu);
+    auto it = g_tile_table.find(key);
+    if (it != g_tile_table.end()) {
+      *out = it->second;
+      return RLOBPCG_OK;
+    }
+  }
+  TileChoice tc;
+  RL_TRY(tune_class(key.first, b, st, &tc));
+  std::lock_guard<std::mutex> lk(g_tile_mu);
+  *out = g_tile_table.emplace(key, tc).first->second;   // the first choice made for a class stays
+  return RLOBPCG_OK;
+}
+
+bool batch_eligible(const rlobpcg_plan_s* p, std::string* why) {
+  if (p->dtype != RLOBPCG_F64) { *why = "batched solves are real FP64"; return false; }
+  if (p->b > batch::BMAX) { *why = "batched solves need b <= 5"; return false; }
+  if (p->n > 512) { *why = "batched solves need n <= 512"; return false; }
+  if (p->opts.locking || p->opts.orth_mode != RLOBPCG_ORTH_HOUSEHOLDER || p->opts.residual_refresh_every > 0) {
+    *why = "batched solves run without locking, SVQB or residual refresh";
+    return false;
+  }
+  return true;
+}
+
+template <class S>
+int batch_setup_one(rlobpcg_plan_s* p, const double* A, int64_t lda, SolveRun& r) {
+  return setup_impl<double, S>(p, A, lda, r, p->opts.tau);
+}
+template <class S>
+int batch_finish_one(rlobpcg_plan_s* p, const double* A, int64_t lda, SolveRun& r, double* sigma, double* V, double* U,
+                     double* resid, rlobpcg_info* info) {
+  return finish_impl<double, S>(p, A, lda, r, sigma, V, U, resid, info);
+}
+
+}  // namespace
+
+extern "C" int rlobpcg_batch_tile(int64_t n, int b, int* trows, int* rt, void* stream) {
+  if (n < 1 || n > 512 || b < 1 || b > batch::BMAX) return RLOBPCG_ERR_INVALID_ARG;
+  TileChoice tc;
+  RL_TRY(tile_choice((int)n, b, (cudaStream_t)stream, &tc));
+  if (trows) *trows = tc.trows;
+  if (rt) *rt = tc.rt;
+  return RLOBPCG_OK;
+}
+
+extern "C" int rlobpcg_batch_set_tile(int64_t n, int b, int trows, int rt) {
+  if (n < 1 || n > 512 || b < 1 || b > batch::BMAX) return RLOBPCG_ERR_INVALID_ARG;
+  size_t s_pre = 0, s_tile = 0;
+  RL_TRY(batch::static_smem_bytes(&s_pre, &s_tile));
+  const int nc = n_class((int)n);
+  bool ok = false;
+  for (const TileChoice& c : tile_candidates(nc, b, s_tile)) ok |= (c.trows == trows && c.rt == rt);
+  if (!ok) {
+    set_last_error("batch: tile shape not among the candidates that fit this class", __FILE__, __LINE__);
+    return RLOBPCG_ERR_INVALID_ARG;
+  }
+  std::lock_guard<std::mutex> lk(g_tile_mu);
+  g_tile_table[std::make_pair(nc, b)] = TileChoice{trows, rt};
+  return RLOBPCG_OK;
+}
+
+extern "C" int rlobpcg_solve_batch(int count, rlobpcg_plan_t* plans, const void* const* A, const int64_t* lda,
+                                   double* const* sigma, void* const* V, void* const* U, double* const* resid,
+                                   rlobpcg_info* infos, int* status, void* stream) {
+  if (count < 1 || !plans || !A || !lda || !sigma || !V) return RLOBPCG_ERR_INVALID_ARG;
+  cudaStream_t ust = (cudaStream_t)stream;
+  std::string why;
+  for (int i = 0; i < count; ++i) {
+    rlobpcg_plan_s* p = plans[i];
+    if (!p || !A[i] || !sigma[i] || !V[i] || lda[i] < p->n || !is_device_ptr(A[i])) return RLOBPCG_ERR_INVALID_ARG;
+    for (int j = 0; j < i; ++j)
+      if (plans[j] == p) return RLOBPCG_ERR_INVALID_ARG;   // one solve per plan
+    if (!batch_eligible(p, &why)) {
+      set_last_error(why.c_str(), __FILE__, __LINE__);
+      return RLOBPCG_ERR_UNSUPPORTED;
+    }
+  }
+  std::vector<TileChoice> tcs(count);
+  for (int i = 0; i < count; ++i) RL_TRY(tile_choice((int)plans[i]->n, plans[i]->b, ust, &tcs[i]));
+
+  // set-up of every solve on its own plan stream; host threads so that the plans' set-ups overlap
+  std::vector<SolveRun> runs(count);
+  std::vector<int> rcs(count, RLOBPCG_OK);
+  {
+    const int nth = std::min(count, 8);
+    std::vector<std::thread> th;
+    std::atomic<int> next{0};
+    for (int t = 0; t < nth; ++t)
+      th.emplace_back([&]() {
+        for (int i = next++; i < count; i = next++) {
+          rlobpcg_plan_s* p = plans[i];
+          const double* Ai = (const double*)A[i];
+          rcs[i] = p->opts.sketch_prec == RLOBPCG_SKETCH_F32 ? batch_setup_one<float>(p, Ai, lda[i], runs[i])
+                                                              : batch_setup_one<double>(p, Ai, lda[i], runs[i]);
+        }
+      });
+    for (auto& t : th) t.join();
+  }
+  for (int i = 0; i < count; ++i)
+    if (rcs[i] != RLOBPCG_OK) {
+      if (status)
+        for (int j = 0; j < count; ++j) status[j] = rcs[j];
+      return rcs[i];
+    }
+
+  // per-solve device state of the batched iterations
+  DevArena ar;
+  std::vector<batch::Desc> hd(count);
+  std::vector<double*> Ruv(count), Rlv(count), Yv(count), Gp(count), Rp(count), Gg(count), Rg(count), Rf(count),
+      Hs(count);
+  std::vector<int*> Cn(count);
+  batch::Desc* Dd = nullptr;
+  int2 *pre_items = nullptr, *tile_items = nullptr;
+  int *qh = nullptr, *act_dev = nullptr;
+  std::vector<int2> hpre, htile;
+  int nmax = 1, abmax = 1, rtmax = 16, hist_rows = 1;
+  size_t pre_smem = 0;
+  for (int i = 0; i < count; ++i) {
+    rlobpcg_plan_s* p = plans[i];
+    const int n = (int)p->n, b = p->b, C = 3 * b;
+    const int nt = (int)((p->m + tcs[i].trows - 1) / tcs[i].trows), ng = (nt + batch::GS - 1) / batch::GS;
+    const int rows = std::max(p->opts.max_iter, p->opts.fixed_iters) + 1;
+    ar.want((void**)&Ruv[i], (size_t)n * n * 8);
+    ar.want((void**)&Rlv[i], (size_t)n * n * 8);
+    ar.want((void**)&Yv[i], (size_t)n * b * 8);
+    ar.want((void**)&Gp[i], (size_t)nt * n * b * 8);
+    ar.want((void**)&Rp[i], (size_t)nt * C * C * 8);
+    ar.want((void**)&Gg[i], (size_t)ng * n * b * 8);
+    ar.want((void**)&Rg[i], (size_t)ng * C * C * 8);
+    ar.want((void**)&Rf[i], (size_t)C * C * 8);
+    ar.want((void**)&Hs[i], (size_t)rows * 2 * b * 8);
+    ar.want((void**)&Cn[i], (size_t)(2 + ng) * 4);
+    batch::Desc& d = hd[i];
+    d = batch::Desc{};
+    d.A = (const double*)A[i]; d.m = p->m; d.lda = lda[i]; d.n = n; d.b = b;
+    d.Tb = (double*)p->Tb; d.ATb = (double*)p->ATb; d.GTb = (double*)p->GTb;
+    d.Rs = (double*)p->Rs; d.Res = (double*)p->Res; d.res_norm = p->res_norm; d.theta = p->theta;
+    d.K = (double*)p->K; d.err = p->err; d.rr_info = p->info;
+    d.ntiles = nt; d.trows = tcs[i].trows; d.rt = tcs[i].rt; d.ngroups = ng; d.nrb = (n + batch::PR - 1) / batch::PR;
+    d.iter = 0; d.c = 2 * b; d.nx = 0; d.pending = 0; d.c_prev = 0; d.done = 0; d.matvecs = b;
+    d.fixed = p->opts.fixed_iters;
+    d.max_iter = d.fixed > 0 ? d.fixed : p->opts.max_iter;
+    d.check_every = std::max(1, p->opts.check_every);
+    d.use_stag = p->opts.use_stagnation != 0;
+    d.sigma11 = runs[i].sigma11;
+    d.tau = runs[i].tau;
+    d.stop_reason = d.fixed > 0 ? RLOBPCG_STOP_FIXED : RLOBPCG_STOP_MAX_ITER;
+    for (int rb = 0; rb < d.nrb; ++rb) hpre.push_back(make_int2(i, rb));
+    nmax = std::max(nmax, n);
+    abmax = std::max(abmax, batch::abuf_need(n, b, tcs[i].rt));
+    rtmax = std::max(rtmax, tcs[i].rt);
+    hist_rows = std::max(hist_rows, rows);
+    pre_smem = std::max(pre_smem, batch::bcgs2_pre_smem(n, b));
+  }
+  // tile items: solves with the most work per iteration first, so that their tails overlap the rest
+  {
+    std::vector<int> order(count);
+    for (int i = 0; i < count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+      return (double)hd[x].m * hd[x].n * hd[x].b > (double)hd[y].m * hd[y].n * hd[y].b;
+    });
+    for (int i : order)
+      for (int t = 0; t < hd[i].ntiles; ++t) htile.push_back(make_int2(i, t));
+  }
+  constexpr int G = 4;   // iterations per graph replay
+  ar.want((void**)&Dd, (size_t)count * sizeof(batch::Desc));
+  ar.want((void**)&pre_items, hpre.size() * sizeof(int2));
+  ar.want((void**)&tile_items, htile.size() * sizeof(int2));
+  ar.want((void**)&qh, (3 * G + 2) * sizeof(int));
+  ar.want((void**)&act_dev, sizeof(int));
+  // the batched iterations run on a stream of their own (a graph cannot be captured on the legacy
+  // default stream), after every set-up
+  cudaStream_t bst = nullptr;
+  RL_CUDA(cudaStreamCreateWithFlags(&bst, cudaStreamNonBlocking));
+  for (int i = 0; i < count; ++i) {
+    RL_CUDA(cudaEventRecord(plans[i]->ev[5], plans[i]->st));
+    RL_CUDA(cudaStreamWaitEvent(bst, plans[i]->ev[5], 0));
+  }
+  RL_TRY(ar.alloc(bst));
+  int rc = RLOBPCG_OK;
+  int* act_h = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  const size_t tile_smem = batch::tile_smem_bytes(nmax, abmax, rtmax);
+  do {
+    for (int i = 0; i < count; ++i) {
+      rlobpcg_plan_s* p = plans[i];
+      batch::Desc& d = hd[i];
+      d.Ru = Ruv[i]; d.Rl = Rlv[i]; d.Y = Yv[i];
+      d.Gpart = Gp[i]; d.Rpart = Rp[i]; d.Ggrp = Gg[i]; d.Rgrp = Rg[i]; d.Rfin = Rf[i]; d.hist = Hs[i];
+      d.cnt = Cn[i];
+      // R^{-1} row-major and column-major (= R^{-H} row-major for real R), widened to FP64
+      const bool f32 = p->opts.sketch_prec == RLOBPCG_SKETCH_F32;
+      const int64_t nn = p->n * p->n;
+      rc = f32 ? batch::widen_launch<float>((const float*)p->Rinv_r, nn, Ruv[i], bst)
+               : batch::widen_launch<double>((const double*)p->Rinv_r, nn, Ruv[i], bst);
+      if (!rc)
+        rc = f32 ? batch::widen_launch<float>((const float*)p->Rinv_c, nn, Rlv[i], bst)
+                 : batch::widen_launch<double>((const double*)p->Rinv_c, nn, Rlv[i], bst);
+      if (rc) break;
+      RL_CUDA(cudaMemcpyAsync(Hs[i], runs[i].hist.r[0].data(), p->b * sizeof(double), cudaMemcpyHostToDevice, bst));
+      RL_CUDA(cudaMemsetAsync(Cn[i], 0, (size_t)(2 + d.ngroups) * 4, bst));
+    }
+    if (rc) break;
+    RL_CUDA(cudaMemcpyAsync(Dd, hd.data(), count * sizeof(batch::Desc), cudaMemcpyHostToDevice, bst));
+    RL_CUDA(cudaMemcpyAsync(pre_items, hpre.data(), hpre.size() * sizeof(int2), cudaMemcpyHostToDevice, bst));
+    RL_CUDA(cudaMemcpyAsync(tile_items, htile.data(), htile.size() * sizeof(int2), cudaMemcpyHostToDevice, bst));
+    if ((rc = batch::prepare(pre_smem, tile_smem))) break;
+    int per_sm = 1;
+    if ((rc = batch::tile_blocks_per_sm(tile_smem, &per_sm))) break;
+    const int slots = num_sms() * std::max(1, per_sm);
+    const int pre_grid = std::max(1, std::min((int)hpre.size(), num_sms() * 2));
+    const int tile_grid = std::max(1, std::min((int)htile.size(), slots));
+    if (cudaMallocHost((void**)&act_h, sizeof(int)) != cudaSuccess) { cudaGetLastError(); rc = RLOBPCG_ERR_CUDA; break; }
+    *act_h = count;
+    // G iterations as one graph: reset the work queues, then (precondition, tile) x G, then the
+    // number of solves still running
+    RL_CUDA(cudaStreamBeginCapture(bst, cudaStreamCaptureModeThreadLocal));
+    int crc = cudaMemsetAsync(qh, 0, (3 * G + 2) * sizeof(int), bst) == cudaSuccess ? RLOBPCG_OK : RLOBPCG_ERR_CUDA;
+    for (int g = 0; g < G && !crc; ++g) {
+      crc = batch::pre_launch(0, Dd, pre_items, (int)hpre.size(), qh + 3 * g, pre_grid, pre_smem, bst);
+      if (!crc) crc = batch::pre_launch(1, Dd, pre_items, (int)hpre.size(), qh + 3 * g + 1, pre_grid, pre_smem, bst);
+      if (!crc) crc = batch::tile_launch(false, Dd, tile_items, (int)htile.size(), qh + 3 * g + 2, tile_grid, nmax, abmax,
+                                         tile_smem, bst);
+    }
+    if (!crc) crc = batch::active_launch(Dd, count, act_dev, bst);
+    if (!crc && cudaMemcpyAsync(act_h, act_dev, sizeof(int), cudaMemcpyDeviceToHost, bst) != cudaSuccess)
+      crc = RLOBPCG_ERR_CUDA;
+    const cudaError_t ce = cudaStreamEndCapture(bst, &graph);
+    if (crc || ce != cudaSuccess) {
+      cudaGetLastError();
+      rc = crc ? crc : RLOBPCG_ERR_CUDA;
+      break;
+    }
+    RL_CUDA(cudaGraphInstantiate(&gexec, graph, 0));
+    const int max_rep = (hist_rows + G - 1) / G + 1;
+    for (int rep = 0; rep < max_rep; ++rep) {
+      RL_CUDA(cudaGraphLaunch(gexec, bst));
+      RL_CUDA(cudaStreamSynchronize(bst));
+      if (*act_h == 0) break;
+    }
+    // the coefficients of the last Rayleigh-Ritz step, applied to A V and A X
+    RL_CUDA(cudaMemsetAsync(qh + 3 * G, 0, sizeof(int), bst));
+    if ((rc = batch::tile_launch(true, Dd, tile_items, (int)htile.size(), qh + 3 * G, tile_grid, nmax, abmax, tile_smem,
+                                 bst)))
+      break;
+    RL_CUDA(cudaMemcpyAsync(hd.data(), Dd, count * sizeof(batch::Desc), cudaMemcpyDeviceToHost, bst));
+    RL_CUDA(cudaStreamSynchronize(bst));
+    for (int i = 0; i < count; ++i) {
+      rlobpcg_plan_s* p = plans[i];
+      const batch::Desc& d = hd[i];
+      SolveRun& r = runs[i];
+      const int b = p->b;
+      std::vector<double> h((size_t)(d.iter + 1) * 2 * b);
+      RL_CUDA(cudaMemcpy(h.data(), Hs[i], h.size() * sizeof(double), cudaMemcpyDeviceToHost));
+      for (int t = 1; t <= d.iter; ++t) {
+        r.hist.r.emplace_back(h.begin() + (size_t)t * 2 * b, h.begin() + (size_t)t * 2 * b + b);
+        r.hist.th.emplace_back(h.begin() + (size_t)t * 2 * b + b, h.begin() + (size_t)(t + 1) * 2 * b);
+      }
+      r.it = d.iter;
+      r.stop = d.stop_reason;
+      r.matvecs = d.matvecs;
+      r.nx = d.nx;
+      r.theta_s = p->theta + (d.iter > 0 ? d.c_prev - b : 0);
+    }
+  } while (0);
+  if (gexec) cudaGraphExecDestroy(gexec);
+  if (graph) cudaGraphDestroy(graph);
+  if (act_h) cudaFreeHost(act_h);
+  // outputs per solve on its own stream, after the batch stream
+  RL_CUDA(cudaEventRecord(plans[0]->ev[6], bst));
+  int first = rc;
+  for (int i = 0; i < count; ++i) {
+    rlobpcg_plan_s* p = plans[i];
+    int ri = rc;
+    if (!ri) {
+      RL_CUDA(cudaStreamWaitEvent(p->st, plans[0]->ev[6], 0));
+      const double* Ai = (const double*)A[i];
+      ri = p->opts.sketch_prec == RLOBPCG_SKETCH_F32
+               ? batch_finish_one<float>(p, Ai, lda[i], runs[i], sigma[i], (double*)V[i], U ? (double*)U[i] : nullptr,
+                                         resid ? resid[i] : nullptr, infos ? &infos[i] : nullptr)
+               : batch_finish_one<double>(p, Ai, lda[i], runs[i], sigma[i], (double*)V[i], U ? (double*)U[i] : nullptr,
+                                          resid ? resid[i] : nullptr, infos ? &infos[i] : nullptr);
+    }
+    if (status) status[i] = ri;
+    if (ri < 0 && first >= 0) first = ri;
+  }
+  ar.release(bst);
+  cudaStreamSynchronize(bst);
+  cudaStreamDestroy(bst);
+  return first < 0 ? first : RLOBPCG_OK;
 }

@@ -100,6 +100,12 @@ _SIGS = {
                                      ctypes.POINTER(c_int)]),
     "rlobpcg_server_destroy": (c_int, [c_void_p]),
     "rlobpcg_check_bounded_wait": (c_int, [c_int, c_int, c_void_p]),
+    "rlobpcg_solve_batch": (c_int, [c_int, ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p),
+                                    ctypes.POINTER(c_int64), ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p),
+                                    ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p),
+                                    ctypes.POINTER(rlobpcg_info), ctypes.POINTER(c_int), c_void_p]),
+    "rlobpcg_batch_tile": (c_int, [c_int64, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int), c_void_p]),
+    "rlobpcg_batch_set_tile": (c_int, [c_int64, c_int, c_int, c_int]),
 }
 
 _lib = None
@@ -335,3 +341,27 @@ def rlobpcg_server_destroy(server: int) -> None:
 def rlobpcg_check_bounded_wait(kind: int, spins: int, stream: int | None = None) -> int:
     """Status of the bounded-wait health check (RLOBPCG_ERR_TIMEOUT when the path works)."""
     return load().rlobpcg_check_bounded_wait(kind, spins, stream)
+
+
+def rlobpcg_solve_batch(plans, A, lda, sigma, V, U, resid, stream: int | None = None):
+    """Batched solves (pointers as ints; U / resid entries may be None). Returns (rc, infos,
+    statuses)."""
+    n = len(plans)
+    arr = lambda xs: (c_void_p * n)(*[x if x else None for x in xs])
+    infos = (rlobpcg_info * n)()
+    st = (c_int * n)()
+    rc = load().rlobpcg_solve_batch(n, arr(plans), arr(A), (c_int64 * n)(*lda), arr(sigma), arr(V),
+                                    arr(U) if U is not None else None, arr(resid) if resid is not None else None,
+                                    infos, st, stream)
+    return rc, list(infos), list(st)
+
+
+def rlobpcg_batch_tile(n: int, b: int, stream: int | None = None):
+    """(trows, rt) of the batched kernels for the (n, b) class (autotuned on first use)."""
+    t, r = c_int(), c_int()
+    _check("rlobpcg_batch_tile", load().rlobpcg_batch_tile(n, b, ctypes.byref(t), ctypes.byref(r), stream))
+    return t.value, r.value
+
+
+def rlobpcg_batch_set_tile(n: int, b: int, trows: int, rt: int) -> None:
+    _check("rlobpcg_batch_set_tile", load().rlobpcg_batch_set_tile(n, b, trows, rt))
