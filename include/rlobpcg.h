@@ -199,6 +199,19 @@ typedef struct rlobpcg_server_s* rlobpcg_server_t;
  * stream could not be created; nothing is left behind). */
 int rlobpcg_server_create(rlobpcg_server_t* out, size_t hbm_budget_bytes, int max_active, int device);
 
+/* Serving modes of rlobpcg_server_create_ex (rlobpcg_server_create is RLOBPCG_SERVE_STREAMS). */
+#define RLOBPCG_SERVE_STREAMS 0   /* each admitted solve runs whole on its worker's stream           */
+#define RLOBPCG_SERVE_BATCHED 1   /* set-up and outputs per worker; the iterations of every admitted
+                                     solve the batched kernels take (see rlobpcg_solve_batch) run
+                                     together in one batch engine, solves joining and leaving
+                                     between graph replays; other requests run whole             */
+
+/* As rlobpcg_server_create, with a serving mode; max_active may be up to 256 in batched mode
+ * (the number of solves iterating together). A batched request's footprint adds the batched
+ * iterations' buffers. Each result equals that of rlobpcg_solve (streams mode) or of
+ * rlobpcg_solve_batch with that request alone (batched mode), whatever else runs. */
+int rlobpcg_server_create_ex(rlobpcg_server_t* out, size_t hbm_budget_bytes, int max_active, int device, int mode);
+
 /* Queue a solve of the k smallest singular triplets of A (HOST memory, m x n row-major, lda >= n,
  * F64 or C128; it must stay valid until rlobpcg_server_wait returns for this ticket).
  * opts may be NULL (defaults). Errors: INVALID_ARG, OOM when the request alone exceeds the

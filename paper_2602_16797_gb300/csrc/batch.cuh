@@ -47,9 +47,10 @@ struct Desc {
 };
 
 
-inline size_t tile_smem_bytes(int nmax, int abuf_elems, int rtmax) {
-  return ((size_t)2 * nmax * BMAX + (size_t)abuf_elems + (size_t)rtmax * BMAX * G1 + (size_t)rtmax * BMAX) *
-         sizeof(double);
+// dynamic shared memory of the tile kernel: W^T and the G accumulator (nw doubles each, nw >= n b
+// for every solve of the launch), the staging area, and the phase-1 partials and row sums
+inline size_t tile_smem_bytes(int nw, int abuf_elems, int rtmax) {
+  return ((size_t)2 * nw + (size_t)abuf_elems + (size_t)rtmax * BMAX * G1 + (size_t)rtmax * BMAX) * sizeof(double);
 }
 
 int abuf_need(int n, int b, int rt);
@@ -57,7 +58,7 @@ size_t bcgs2_pre_smem(int n, int b);
 int prepare(size_t pre_smem, size_t tile_smem);
 int tile_blocks_per_sm(size_t tile_smem, int* out);
 int pre_launch(int phase, Desc* D, const int2* items, int nitems, int* qhead, int grid, size_t smem, cudaStream_t st);
-int tile_launch(bool flush, Desc* D, const int2* items, int nitems, int* qhead, int grid, int nmax, int abuf,
+int tile_launch(bool flush, Desc* D, const int2* items, int nitems, int* qhead, int grid, int nw, int abuf,
                 size_t smem, cudaStream_t st);
 int active_launch(const Desc* D, int count, int* out, cudaStream_t st);
 template <class S>

@@ -250,7 +250,7 @@ __device__ void tail(Desc& sd, Desc* Dg, double* sm, double* qtau, double* qdg, 
   for (int e = tid; e < c * c; e += blockDim.x) sd.Rfin[e] = sm[e];
   __syncthreads();
   // Rayleigh-Ritz: [~, Theta, C] = SVD(A_T) through R (Alg. 2)
-  rr_small_cta<double>(reinterpret_cast<unsigned char*>(sm), sd.Rfin, c, b, sd.theta, sd.K, sd.rr_info);
+  rr_small_cta<double, 16>(reinterpret_cast<unsigned char*>(sm), sd.Rfin, c, b, sd.theta, sd.K, sd.rr_info);
   __syncthreads();
   // V, X and their G columns (the A_T columns follow in the next launch's tiles)
   apply_coeffs(sd.Tb, 0, n, b, c, sd.K, sm);
@@ -302,15 +302,15 @@ __device__ void tail(Desc& sd, Desc* Dg, double* sm, double* qtau, double* qdg, 
 // ---- Gram tile + local factor + reductions + tail ----------------------------------------------
 
 template <int FLUSH>
-__global__ void __launch_bounds__(NT, 1) tile_kernel(Desc* D, const int2* __restrict__ items, int nitems, int* qhead,
-                                                     int nmax, int abuf_elems) {
+__global__ void __launch_bounds__(NT, 2) tile_kernel(Desc* D, const int2* __restrict__ items, int nitems, int* qhead,
+                                                     int nw, int abuf_elems) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ Desc sd;
   __shared__ int s_item, s_flag;
   __shared__ double qtau[3 * BMAX], qdg[3 * BMAX], qsv[3 * BMAX], qinv;
-  double* Wt = reinterpret_cast<double*>(smem_raw);        // b x n (transposed W)
-  double* Gacc = Wt + (size_t)nmax * BMAX;                  // n x b
-  double* Abuf = Gacc + (size_t)nmax * BMAX;                // staging (A rows, A_T rows, tail scratch)
+  double* Wt = reinterpret_cast<double*>(smem_raw);        // b x n (transposed W); nw >= n b over the batch
+  double* Gacc = Wt + nw;                                   // n x b
+  double* Abuf = Gacc + nw;                                 // staging (A rows, A_T rows, tail scratch)
   double* Ps = Abuf + abuf_elems;                           // phase-1 partials
   const int tid = threadIdx.x;
   for (;;) {
@@ -346,16 +346,13 @@ __global__ void __launch_bounds__(NT, 1) tile_kernel(Desc* D, const int2* __rest
           }
           asm volatile("cp.async.commit_group;\n" ::: "memory");
         };
+        // one stage of rt rows (two CTAs share an SM: one's loads and reductions overlap the other's
+        // FP64 products)
         const int nsub = (rows + rt - 1) / rt;
-        issue(0, Abuf);
         for (int q = 0; q < nsub; ++q) {
-          double* cur = Abuf + (size_t)(q & 1) * rt * n;
-          if (q + 1 < nsub) {
-            issue((q + 1) * rt, Abuf + (size_t)((q + 1) & 1) * rt * n);
-            asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-          } else {
-            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-          }
+          double* cur = Abuf;
+          issue(q * rt, cur);
+          asm volatile("cp.async.wait_group 0;\n" ::: "memory");
           __syncthreads();
           const int nr = min(rt, rows - q * rt);
           // phase 1: partial dot products, G1 threads per row, columns k = ps (mod G1)
@@ -448,10 +445,10 @@ namespace batch {
 // update and the tail's Rayleigh-Ritz scratch
 int abuf_need(int n, int b, int rt) {
   const int C = 3 * b;
-  size_t need = (size_t)2 * rt * n;
+  size_t need = (size_t)rt * n;
   need = std::max(need, (size_t)(C + QRC) * C);
   need = std::max(need, (size_t)C * 2 * b + (size_t)UR * C);
-  need = std::max(need, (rr_small_smem<double>(C, b) + 7) / 8 + 2);
+  need = std::max(need, (rr_small_smem<double>(C, b) + 7) / 8 + 2);   // 3b <= 15
   return (int)need;
 }
 
@@ -479,12 +476,12 @@ int pre_launch(int phase, Desc* D, const int2* items, int nitems, int* qhead, in
   return RLOBPCG_OK;
 }
 
-int tile_launch(bool flush, Desc* D, const int2* items, int nitems, int* qhead, int grid, int nmax, int abuf,
+int tile_launch(bool flush, Desc* D, const int2* items, int nitems, int* qhead, int grid, int nw, int abuf,
                 size_t smem, cudaStream_t st) {
   if (flush)
-    tile_kernel<1><<<grid, NT, smem, st>>>(D, items, nitems, qhead, nmax, abuf);
+    tile_kernel<1><<<grid, NT, smem, st>>>(D, items, nitems, qhead, nw, abuf);
   else
-    tile_kernel<0><<<grid, NT, smem, st>>>(D, items, nitems, qhead, nmax, abuf);
+    tile_kernel<0><<<grid, NT, smem, st>>>(D, items, nitems, qhead, nw, abuf);
   RL_CHECK_LAUNCH();
   return RLOBPCG_OK;
 }

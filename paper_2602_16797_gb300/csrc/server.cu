@@ -2,11 +2,17 @@
 //
 // Requests (A on the host, m, n, k, options) join a FIFO queue. A request is admitted when its
 // device footprint (plan workspace + a device copy of A) fits in what the budget has left and a
-// worker slot is free; each worker owns a CUDA stream, so admitted solves run concurrently on the
-// GPU and their kernels overlap. A solve keeps its whole LOBPCG state in its plan's device
-// buffers between iterations and releases them (stream-ordered) when it finishes, which admits
-// the next request. Every solve runs the same deterministic kernels as rlobpcg_solve, so a result
-// does not depend on what else is running.
+// worker slot is free; each worker owns a CUDA stream. A solve keeps its whole LOBPCG state in
+// its plan's device buffers between iterations and releases them (stream-ordered) when it
+// finishes, which admits the next request.
+//
+// Two modes. RLOBPCG_SERVE_STREAMS: each worker runs the whole solve (rlobpcg_solve) on its
+// stream; admitted solves overlap on the GPU. RLOBPCG_SERVE_BATCHED: each worker runs its
+// request's set-up and outputs on its stream, and the LOBPCG iterations of every admitted small
+// solve run together in the batch engine (one thread, one stream, persistent kernels over all
+// joined solves, replayed from a captured graph); solves join and leave between replays.
+// Requests the batched kernels do not take (complex, block > 5, n > 512, locking, SVQB) run whole
+// on their worker. In both modes a result does not depend on what else is running.
 #include <algorithm>
 #include <chrono>
 #include <cstdio>
@@ -19,6 +25,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "engine.h"
 
 namespace {
 
@@ -47,6 +54,8 @@ size_t elem_bytes(int dtype) { return dtype == RLOBPCG_C128 ? 16 : 8; }
 
 struct rlobpcg_server_s {
   int device = 0;
+  int mode = RLOBPCG_SERVE_STREAMS;
+  rl::BatchEngine* engine = nullptr;   // batched mode
   size_t budget = 0, in_use = 0, peak = 0;
   int max_active = 1, running = 0, peak_running = 0;
   bool stop = false;
@@ -103,8 +112,20 @@ void worker_main(rlobpcg_server_s* s, cudaStream_t st) {
         rc = RLOBPCG_ERR_CUDA;
       }
     }
-    if (rc == RLOBPCG_OK)
-      rc = rlobpcg_solve(plan, Ad, r->n, -1.0, r->sigma.data(), r->V.data(), nullptr, r->resid.data(), &r->info);
+    if (rc == RLOBPCG_OK) {
+      if (s->engine && rl::batch_request_eligible(r->n, r->k, r->dtype, r->opts)) {
+        // set-up here, iterations in the batch engine with every other admitted solve, outputs here
+        rl::BatchSolve* h = nullptr;
+        rc = rl::batch_solve_setup(plan, (const double*)Ad, r->n, &h);
+        if (rc == RLOBPCG_OK) {
+          rl::batch_solve_submit(s->engine, h);
+          rl::batch_solve_wait(h);
+          rc = rl::batch_solve_finish(h, r->sigma.data(), r->V.data(), nullptr, r->resid.data(), &r->info);
+        }
+      } else {
+        rc = rlobpcg_solve(plan, Ad, r->n, -1.0, r->sigma.data(), r->V.data(), nullptr, r->resid.data(), &r->info);
+      }
+    }
     if (rc < 0) snprintf(r->err, sizeof(r->err), "%s", rlobpcg_last_error());
     if (Ad) cudaFreeAsync(Ad, st);
     rlobpcg_plan_destroy(plan);
@@ -125,11 +146,14 @@ void worker_main(rlobpcg_server_s* s, cudaStream_t st) {
   }
 }
 
-// Device footprint of one request: the plan's workspace plus a device copy of A.
-size_t request_bytes(int64_t m, int64_t n, int k, int dtype, const rlobpcg_opts& o) {
+// Device footprint of one request: the plan's workspace plus a device copy of A (plus the
+// batched iterations' buffers when the batch engine takes it).
+size_t request_bytes(int64_t m, int64_t n, int k, int dtype, const rlobpcg_opts& o, bool batched) {
   const size_t ws = rlobpcg_plan_workspace_size(m, n, k, dtype, &o);
   if (ws == 0) return 0;
-  return ws + (((size_t)m * n * elem_bytes(dtype) + 255) & ~(size_t)255);
+  size_t extra = 0;
+  if (batched && rl::batch_request_eligible(n, k, dtype, o)) extra = rl::batch_extra_bytes(m, n, o.block > 0 ? o.block : k);
+  return ws + extra + (((size_t)m * n * elem_bytes(dtype) + 255) & ~(size_t)255);
 }
 
 }  // namespace
@@ -137,7 +161,15 @@ size_t request_bytes(int64_t m, int64_t n, int k, int dtype, const rlobpcg_opts&
 using namespace rl;
 
 extern "C" int rlobpcg_server_create(rlobpcg_server_t* out, size_t hbm_budget_bytes, int max_active, int device) {
-  if (!out || hbm_budget_bytes == 0 || max_active < 1 || max_active > 64) return RLOBPCG_ERR_INVALID_ARG;
+  return rlobpcg_server_create_ex(out, hbm_budget_bytes, max_active, device, RLOBPCG_SERVE_STREAMS);
+}
+
+extern "C" int rlobpcg_server_create_ex(rlobpcg_server_t* out, size_t hbm_budget_bytes, int max_active, int device,
+                                        int mode) {
+  const int cap = mode == RLOBPCG_SERVE_BATCHED ? 256 : 64;
+  if (!out || hbm_budget_bytes == 0 || max_active < 1 || max_active > cap ||
+      (mode != RLOBPCG_SERVE_STREAMS && mode != RLOBPCG_SERVE_BATCHED))
+    return RLOBPCG_ERR_INVALID_ARG;
   int ndev = 0;
   RL_CUDA(cudaGetDeviceCount(&ndev));
   if (device < 0 || device >= ndev) return RLOBPCG_ERR_INVALID_ARG;
@@ -150,6 +182,14 @@ extern "C" int rlobpcg_server_create(rlobpcg_server_t* out, size_t hbm_budget_by
   }
   auto* s = new rlobpcg_server_s();
   s->device = device;
+  s->mode = mode;
+  if (mode == RLOBPCG_SERVE_BATCHED) {
+    const int rc = rl::batch_engine_create(device, &s->engine);
+    if (rc != RLOBPCG_OK) {
+      delete s;
+      return rc;
+    }
+  }
   s->budget = hbm_budget_bytes;
   s->max_active = max_active;
   // every worker's stream exists before any worker starts: a server either has all its slots or
@@ -161,6 +201,7 @@ extern "C" int rlobpcg_server_create(rlobpcg_server_t* out, size_t hbm_budget_by
       cudaGetLastError();
       set_last_error(cudaGetErrorString(e), __FILE__, __LINE__);
       for (cudaStream_t q : s->streams) cudaStreamDestroy(q);
+      if (s->engine) rl::batch_engine_destroy(s->engine);
       delete s;
       return RLOBPCG_ERR_CUDA;
     }
@@ -178,7 +219,7 @@ extern "C" int rlobpcg_server_submit(rlobpcg_server_t s, const void* A, int64_t 
   auto* r = new Request();
   if (opts) r->opts = *opts; else rlobpcg_default_opts(&r->opts);
   r->A = A; r->m = m; r->n = n; r->lda = lda; r->k = k; r->dtype = dtype;
-  r->bytes = request_bytes(m, n, k, dtype, r->opts);
+  r->bytes = request_bytes(m, n, k, dtype, r->opts, s->engine != nullptr);
   if (r->bytes == 0) {
     delete r;
     return RLOBPCG_ERR_INVALID_ARG;
@@ -293,6 +334,7 @@ extern "C" int rlobpcg_server_destroy(rlobpcg_server_t s) {
     s->cv_done.wait(lk, [&] { return s->waiters == 0; });
   }
   for (auto& kv : s->all) delete kv.second;
+  if (s->engine) rl::batch_engine_destroy(s->engine);   // every batched solve has been waited for
   for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
   delete s;
   return RLOBPCG_OK;

@@ -627,7 +627,7 @@ __device__ int jacobi_mixed32(double* X, double* V, int c, int N, double tol, do
 }
 
 // One CTA (any multiple of 32 threads); smem_raw: rr_small_smem(c, b) bytes of dynamic shared memory.
-template <class T>
+template <class T, int CMAX = 32>   // CMAX: the largest c the FP32-preconditioned Jacobi path serves
 __device__ void rr_small_cta(unsigned char* smem_raw, const T* __restrict__ Rt, int c, int b, double* theta_out,
                              T* K_out, int* info) {
   T* X = reinterpret_cast<T*>(smem_raw);        // c x c col-major
@@ -665,12 +665,12 @@ __device__ void rr_small_cta(unsigned char* smem_raw, const T* __restrict__ Rt, 
   int sweep = 0;
   bool fast = false;
   if constexpr (std::is_same<T, double>::value) {
-    if (c <= 32) {
-      __shared__ float Xf[1024], Vf[1024];
-      __shared__ double Ms[1024], Ws2[1024];
+    if (c <= CMAX) {
+      __shared__ float Xf[CMAX * CMAX], Vf[CMAX * CMAX];
+      __shared__ double Ms[CMAX * CMAX], Ws2[CMAX * CMAX];
       if (c <= 16) {
         sweep = jacobi_mixed16(X, V, c, N, tol, tiny2, mx0, Xf, Vf, Ms, Ws2);
-      } else {
+      } else if constexpr (CMAX > 16) {
         __shared__ uint16_t sched32[31 * 16];
         __shared__ double dots[48], rotp[32];
         __shared__ int rflag[16];

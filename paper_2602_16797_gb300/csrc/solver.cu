@@ -10,6 +10,8 @@
 
 #include <algorithm>
 #include <atomic>
+#include <condition_variable>
+#include <deque>
 #include <limits>
 #include <map>
 #include <mutex>
@@ -20,6 +22,7 @@
 
 #include "batch.cuh"
 #include "common.cuh"
+#include "engine.h"
 #include "split.cuh"
 
 namespace rl {
@@ -975,7 +978,7 @@ std::vector<TileChoice> tile_candidates(int nc, int b, size_t static_tile) {
   std::vector<TileChoice> out;
   for (int trows : {256, 512, 1024, 2048})
     for (int rt : {16, 32}) {
-      const size_t sm = batch::tile_smem_bytes(nc, batch::abuf_need(nc, b, rt), rt);
+      const size_t sm = batch::tile_smem_bytes(nc * b, batch::abuf_need(nc, b, rt), rt);
       if (sm + static_tile <= max_smem_optin()) out.push_back({trows, rt});
     }
   return out;
@@ -1080,7 +1083,7 @@ int tune_class(int nc, int b, cudaStream_t st, TileChoice* out) {
         for (int t = 0; t < nt; ++t) hi.push_back(make_int2(s, t));
       }
       const int ab = batch::abuf_need(n, b, tc.rt);
-      const size_t smem = batch::tile_smem_bytes(n, ab, tc.rt);
+      const size_t smem = batch::tile_smem_bytes(n * b, ab, tc.rt);
       if ((rc = batch::prepare(batch::bcgs2_pre_smem(n, b), smem))) break;
       int per_sm = 1;
       if ((rc = batch::tile_blocks_per_sm(smem, &per_sm))) break;
@@ -1092,7 +1095,7 @@ int tune_class(int nc, int b, cudaStream_t st, TileChoice* out) {
         RL_CUDA(cudaMemsetAsync(cnt, 0, (size_t)NS * (2 + gmax) * 4, st));
         RL_CUDA(cudaMemsetAsync(qh, 0, 64, st));
         RL_CUDA(cudaEventRecord(e0, st));
-        rc = batch::tile_launch(false, D, items, (int)hi.size(), qh, grid, n, ab, smem, st);
+        rc = batch::tile_launch(false, D, items, (int)hi.size(), qh, grid, n * b, ab, smem, st);
         RL_CUDA(cudaEventRecord(e1, st));
         RL_CUDA(cudaStreamSynchronize(st));
         float ms = 0;
@@ -1155,6 +1158,423 @@ int batch_finish_one(rlobpcg_plan_s* p, const double* A, int64_t lda, SolveRun& 
 
 }  // namespace
 
+// -------------------------------------------------------------------------------------------------
+// The batch engine: one host thread and one stream that iterate every solve handed to it. Solves
+// join and leave between graph replays (continuous batching); a solve's device state of the
+// batched iterations is allocated when it joins and freed when it leaves.
+// -------------------------------------------------------------------------------------------------
+namespace rl {
+
+struct BatchSolve {
+  rlobpcg_plan_s* p = nullptr;
+  const double* A = nullptr;
+  int64_t lda = 0;
+  SolveRun r;
+  TileChoice tc;
+  void* mem = nullptr;       // the solve's batched-iteration buffers (one allocation)
+  batch::Desc d{};           // host copy of its descriptor
+  std::mutex mu;
+  std::condition_variable cv;
+  bool finished = false;     // the engine has retired it
+  int rc = RLOBPCG_OK;
+};
+
+struct BatchEngine {
+  int device = 0;
+  cudaStream_t st = nullptr;
+  std::thread th;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<BatchSolve*> incoming;
+  bool stop = false;
+  std::vector<BatchSolve*> active;
+  // device arrays of the current membership
+  void* dmem = nullptr;
+  size_t dmem_bytes = 0;
+  batch::Desc* Dd = nullptr;
+  int2 *pre_items = nullptr, *tile_items = nullptr;
+  int* qh = nullptr;
+  batch::Desc* Dh = nullptr;   // pinned copy the graph writes back after every replay
+  size_t Dh_cap = 0;
+  int npre = 0, ntile = 0;
+  int nwmax = 1, abmax = 1, rtmax = 16;
+  size_t pre_smem = 0, tile_smem = 0;
+  int pre_grid = 1, tile_grid = 1;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  bool dirty = true;
+  static constexpr int G = 4;   // iterations per graph replay
+};
+
+namespace {
+
+size_t batch_solve_bytes(int64_t m, int64_t n, int b, int trows, int* nt_out, int* ng_out) {
+  const int C = 3 * b;
+  const int nt = (int)((m + trows - 1) / trows), ng = (nt + batch::GS - 1) / batch::GS;
+  if (nt_out) *nt_out = nt;
+  if (ng_out) *ng_out = ng;
+  auto r = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  return r((size_t)n * n * 8) * 2 + r((size_t)n * b * 8) + r((size_t)nt * n * b * 8) + r((size_t)nt * C * C * 8) +
+         r((size_t)ng * n * b * 8) + r((size_t)ng * C * C * 8) + r((size_t)C * C * 8) + r((size_t)201 * 2 * b * 8) +
+         r((size_t)(2 + ng) * 4);
+}
+
+void complete(BatchSolve* s, int rc) {
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->rc = rc;
+  s->finished = true;
+  s->cv.notify_all();
+}
+
+// device state of a joining solve: its buffers, FP64 copies of R^{-1} (row- and column-major), the
+// first history row, and its descriptor
+int engine_join(BatchEngine* e, BatchSolve* s) {
+  rlobpcg_plan_s* p = s->p;
+  const int n = (int)p->n, b = p->b, C = 3 * b;
+  int nt = 0, ng = 0;
+  const int rows = std::max(p->opts.max_iter, p->opts.fixed_iters) + 1;
+  if (rows > 201) {
+    set_last_error("batched solves run at most 200 iterations", __FILE__, __LINE__);
+    return RLOBPCG_ERR_UNSUPPORTED;
+  }
+  const size_t bytes = batch_solve_bytes(p->m, n, b, s->tc.trows, &nt, &ng);
+  if (cudaMallocAsync(&s->mem, bytes, e->st) != cudaSuccess) {
+    cudaGetLastError();
+    s->mem = nullptr;
+    set_last_error("batch: solve workspace", __FILE__, __LINE__);
+    return RLOBPCG_ERR_OOM;
+  }
+  char* q = (char*)s->mem;
+  auto take = [&](size_t x) { char* r = q; q += (x + 255) & ~(size_t)255; return r; };
+  batch::Desc& d = s->d;
+  d = batch::Desc{};
+  d.Ru = (double*)take((size_t)n * n * 8);
+  d.Rl = (double*)take((size_t)n * n * 8);
+  d.Y = (double*)take((size_t)n * b * 8);
+  d.Gpart = (double*)take((size_t)nt * n * b * 8);
+  d.Rpart = (double*)take((size_t)nt * C * C * 8);
+  d.Ggrp = (double*)take((size_t)ng * n * b * 8);
+  d.Rgrp = (double*)take((size_t)ng * C * C * 8);
+  d.Rfin = (double*)take((size_t)C * C * 8);
+  d.hist = (double*)take((size_t)201 * 2 * b * 8);
+  d.cnt = (int*)take((size_t)(2 + ng) * 4);
+  d.A = s->A; d.m = p->m; d.lda = s->lda; d.n = n; d.b = b;
+  d.Tb = (double*)p->Tb; d.ATb = (double*)p->ATb; d.GTb = (double*)p->GTb;
+  d.Rs = (double*)p->Rs; d.Res = (double*)p->Res; d.res_norm = p->res_norm; d.theta = p->theta;
+  d.K = (double*)p->K; d.err = p->err; d.rr_info = p->info;
+  d.ntiles = nt; d.trows = s->tc.trows; d.rt = s->tc.rt; d.ngroups = ng; d.nrb = (n + batch::PR - 1) / batch::PR;
+  d.iter = 0; d.c = 2 * b; d.nx = 0; d.pending = 0; d.c_prev = 0; d.done = 0; d.matvecs = b;
+  d.fixed = p->opts.fixed_iters;
+  d.max_iter = d.fixed > 0 ? d.fixed : p->opts.max_iter;
+  d.check_every = std::max(1, p->opts.check_every);
+  d.use_stag = p->opts.use_stagnation != 0;
+  d.sigma11 = s->r.sigma11;
+  d.tau = s->r.tau;
+  d.stop_reason = d.fixed > 0 ? RLOBPCG_STOP_FIXED : RLOBPCG_STOP_MAX_ITER;
+  const bool f32 = p->opts.sketch_prec == RLOBPCG_SKETCH_F32;
+  const int64_t nn = p->n * p->n;
+  RL_TRY(f32 ? batch::widen_launch<float>((const float*)p->Rinv_r, nn, (double*)d.Ru, e->st)
+             : batch::widen_launch<double>((const double*)p->Rinv_r, nn, (double*)d.Ru, e->st));
+  RL_TRY(f32 ? batch::widen_launch<float>((const float*)p->Rinv_c, nn, (double*)d.Rl, e->st)
+             : batch::widen_launch<double>((const double*)p->Rinv_c, nn, (double*)d.Rl, e->st));
+  RL_CUDA(cudaMemcpyAsync(d.hist, s->r.hist.r[0].data(), b * sizeof(double), cudaMemcpyHostToDevice, e->st));
+  RL_CUDA(cudaMemsetAsync(d.cnt, 0, (size_t)(2 + ng) * 4, e->st));
+  RL_CUDA(cudaStreamSynchronize(e->st));   // the host history row is read before this returns
+  return RLOBPCG_OK;
+}
+
+// device arrays, work lists and the graph for the current membership (descriptors from the host
+// copies, which hold every solve's state after the last replay)
+int engine_rebuild(BatchEngine* e) {
+  if (e->gexec) cudaGraphExecDestroy(e->gexec);
+  if (e->graph) cudaGraphDestroy(e->graph);
+  e->gexec = nullptr;
+  e->graph = nullptr;
+  const int count = (int)e->active.size();
+  std::vector<int2> hpre, htile;
+  e->nwmax = 1; e->abmax = 1; e->rtmax = 16; e->pre_smem = 0;
+  for (int i = 0; i < count; ++i) {
+    const batch::Desc& d = e->active[i]->d;
+    for (int rb = 0; rb < d.nrb; ++rb) hpre.push_back(make_int2(i, rb));
+    e->nwmax = std::max(e->nwmax, d.n * d.b);
+    e->abmax = std::max(e->abmax, batch::abuf_need(d.n, d.b, d.rt));
+    e->rtmax = std::max(e->rtmax, d.rt);
+    e->pre_smem = std::max(e->pre_smem, batch::bcgs2_pre_smem(d.n, d.b));
+  }
+  // tile items: the solves with the most work per iteration first, so that their tails overlap
+  // the other solves' tiles
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    const batch::Desc &a = e->active[x]->d, &b = e->active[y]->d;
+    return (double)a.m * a.n * a.b > (double)b.m * b.n * b.b;
+  });
+  for (int i : order)
+    for (int t = 0; t < e->active[i]->d.ntiles; ++t) htile.push_back(make_int2(i, t));
+  e->npre = (int)hpre.size();
+  e->ntile = (int)htile.size();
+  const size_t need = count * sizeof(batch::Desc) + 256 + hpre.size() * sizeof(int2) + 256 +
+                      htile.size() * sizeof(int2) + 256 + (3 * BatchEngine::G + 2) * sizeof(int) + 256;
+  if (need > e->dmem_bytes) {
+    if (e->dmem) cudaFreeAsync(e->dmem, e->st);
+    e->dmem = nullptr;
+    e->dmem_bytes = 0;
+    if (cudaMallocAsync(&e->dmem, need * 2, e->st) != cudaSuccess) {
+      cudaGetLastError();
+      return RLOBPCG_ERR_OOM;
+    }
+    e->dmem_bytes = need * 2;
+  }
+  if ((size_t)count > e->Dh_cap) {
+    if (e->Dh) cudaFreeHost(e->Dh);
+    e->Dh = nullptr;
+    e->Dh_cap = 0;
+    if (cudaMallocHost((void**)&e->Dh, (size_t)count * 2 * sizeof(batch::Desc)) != cudaSuccess) {
+      cudaGetLastError();
+      return RLOBPCG_ERR_CUDA;
+    }
+    e->Dh_cap = (size_t)count * 2;
+  }
+  char* q = (char*)e->dmem;
+  auto take = [&](size_t x) { char* r = q; q += (x + 255) & ~(size_t)255; return r; };
+  e->Dd = (batch::Desc*)take(count * sizeof(batch::Desc));
+  e->pre_items = (int2*)take(hpre.size() * sizeof(int2));
+  e->tile_items = (int2*)take(htile.size() * sizeof(int2));
+  e->qh = (int*)take((3 * BatchEngine::G + 2) * sizeof(int));
+  for (int i = 0; i < count; ++i) e->Dh[i] = e->active[i]->d;
+  RL_CUDA(cudaMemcpyAsync(e->Dd, e->Dh, count * sizeof(batch::Desc), cudaMemcpyHostToDevice, e->st));
+  RL_CUDA(cudaMemcpyAsync(e->pre_items, hpre.data(), hpre.size() * sizeof(int2), cudaMemcpyHostToDevice, e->st));
+  RL_CUDA(cudaMemcpyAsync(e->tile_items, htile.data(), htile.size() * sizeof(int2), cudaMemcpyHostToDevice, e->st));
+  e->tile_smem = batch::tile_smem_bytes(e->nwmax, e->abmax, e->rtmax);
+  RL_TRY(batch::prepare(e->pre_smem, e->tile_smem));
+  int per_sm = 1;
+  RL_TRY(batch::tile_blocks_per_sm(e->tile_smem, &per_sm));
+  e->pre_grid = std::max(1, std::min(e->npre, num_sms() * 2));
+  e->tile_grid = std::max(1, std::min(e->ntile, num_sms() * std::max(1, per_sm)));
+  RL_CUDA(cudaStreamSynchronize(e->st));   // the item vectors are host locals
+  // G iterations as one graph: reset the work queues, (R^{-H} Rs, R^{-1} Y + BCGS2, tiles) x G,
+  // then the descriptors back to the host
+  const int G = BatchEngine::G;
+  RL_CUDA(cudaStreamBeginCapture(e->st, cudaStreamCaptureModeThreadLocal));
+  int crc = cudaMemsetAsync(e->qh, 0, (3 * G + 2) * sizeof(int), e->st) == cudaSuccess ? RLOBPCG_OK : RLOBPCG_ERR_CUDA;
+  for (int g = 0; g < G && !crc; ++g) {
+    crc = batch::pre_launch(0, e->Dd, e->pre_items, e->npre, e->qh + 3 * g, e->pre_grid, e->pre_smem, e->st);
+    if (!crc) crc = batch::pre_launch(1, e->Dd, e->pre_items, e->npre, e->qh + 3 * g + 1, e->pre_grid, e->pre_smem, e->st);
+    if (!crc)
+      crc = batch::tile_launch(false, e->Dd, e->tile_items, e->ntile, e->qh + 3 * g + 2, e->tile_grid, e->nwmax, e->abmax,
+                               e->tile_smem, e->st);
+  }
+  if (!crc && cudaMemcpyAsync(e->Dh, e->Dd, count * sizeof(batch::Desc), cudaMemcpyDeviceToHost, e->st) != cudaSuccess)
+    crc = RLOBPCG_ERR_CUDA;
+  const cudaError_t ce = cudaStreamEndCapture(e->st, &e->graph);
+  if (crc || ce != cudaSuccess) {
+    cudaGetLastError();
+    return crc ? crc : RLOBPCG_ERR_CUDA;
+  }
+  RL_CUDA(cudaGraphInstantiate(&e->gexec, e->graph, 0));
+  e->dirty = false;
+  return RLOBPCG_OK;
+}
+
+// solves that stopped: A V and A X brought up to date, the state handed back, buffers released
+int engine_retire(BatchEngine* e, const std::vector<int>& idx) {
+  std::vector<int2> items;
+  for (int i : idx)
+    for (int t = 0; t < e->active[i]->d.ntiles; ++t) items.push_back(make_int2(i, t));
+  int2* ditems = nullptr;
+  RL_CUDA(cudaMallocAsync((void**)&ditems, items.size() * sizeof(int2), e->st));
+  RL_CUDA(cudaMemcpyAsync(ditems, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice, e->st));
+  RL_CUDA(cudaMemsetAsync(e->qh + 3 * BatchEngine::G, 0, sizeof(int), e->st));
+  RL_TRY(batch::tile_launch(true, e->Dd, ditems, (int)items.size(), e->qh + 3 * BatchEngine::G, e->tile_grid, e->nwmax,
+                            e->abmax, e->tile_smem, e->st));
+  RL_CUDA(cudaFreeAsync(ditems, e->st));
+  for (int i : idx) {
+    BatchSolve* s = e->active[i];
+    const batch::Desc& d = s->d;
+    const int b = d.b;
+    std::vector<double> h((size_t)(d.iter + 1) * 2 * b);
+    RL_CUDA(cudaMemcpyAsync(h.data(), d.hist, h.size() * sizeof(double), cudaMemcpyDeviceToHost, e->st));
+    RL_CUDA(cudaStreamSynchronize(e->st));
+    for (int t = 1; t <= d.iter; ++t) {
+      s->r.hist.r.emplace_back(h.begin() + (size_t)t * 2 * b, h.begin() + (size_t)t * 2 * b + b);
+      s->r.hist.th.emplace_back(h.begin() + (size_t)t * 2 * b + b, h.begin() + (size_t)(t + 1) * 2 * b);
+    }
+    s->r.it = d.iter;
+    s->r.stop = d.stop_reason;
+    s->r.matvecs = d.matvecs;
+    s->r.nx = d.nx;
+    s->r.theta_s = s->p->theta + (d.iter > 0 ? d.c_prev - b : 0);
+    cudaFreeAsync(s->mem, e->st);
+    s->mem = nullptr;
+  }
+  RL_CUDA(cudaStreamSynchronize(e->st));
+  return RLOBPCG_OK;
+}
+
+void engine_fail_all(BatchEngine* e, int rc) {
+  for (BatchSolve* s : e->active) {
+    if (s->mem) cudaFreeAsync(s->mem, e->st);
+    s->mem = nullptr;
+    complete(s, rc);
+  }
+  e->active.clear();
+  e->dirty = true;
+}
+
+void engine_main(BatchEngine* e) {
+  cudaSetDevice(e->device);
+  for (;;) {
+    std::vector<BatchSolve*> joining;
+    {
+      std::unique_lock<std::mutex> lk(e->mu);
+      e->cv.wait(lk, [&] { return e->stop || !e->incoming.empty() || !e->active.empty(); });
+      if (e->stop && e->incoming.empty() && e->active.empty()) break;
+      joining.assign(e->incoming.begin(), e->incoming.end());
+      e->incoming.clear();
+    }
+    for (BatchSolve* s : joining) {
+      const int rc = engine_join(e, s);
+      if (rc) {
+        if (s->mem) cudaFreeAsync(s->mem, e->st);
+        s->mem = nullptr;
+        complete(s, rc);
+      } else {
+        e->active.push_back(s);
+        e->dirty = true;
+      }
+    }
+    if (e->active.empty()) continue;
+    int rc = e->dirty ? engine_rebuild(e) : RLOBPCG_OK;
+    if (!rc && cudaGraphLaunch(e->gexec, e->st) != cudaSuccess) rc = RLOBPCG_ERR_CUDA;
+    if (!rc && cudaStreamSynchronize(e->st) != cudaSuccess) rc = RLOBPCG_ERR_CUDA;
+    if (rc) {
+      cudaGetLastError();
+      engine_fail_all(e, rc);
+      continue;
+    }
+    std::vector<int> done;
+    for (size_t i = 0; i < e->active.size(); ++i) {
+      e->active[i]->d = e->Dh[i];
+      if (e->Dh[i].done) done.push_back((int)i);
+    }
+    if (done.empty()) continue;
+    rc = engine_retire(e, done);
+    if (rc) {
+      cudaGetLastError();
+      engine_fail_all(e, rc);
+      continue;
+    }
+    std::vector<BatchSolve*> keep;
+    size_t di = 0;
+    for (size_t i = 0; i < e->active.size(); ++i) {
+      if (di < done.size() && (size_t)done[di] == i) {
+        complete(e->active[i], RLOBPCG_OK);
+        ++di;
+      } else {
+        keep.push_back(e->active[i]);
+      }
+    }
+    e->active.swap(keep);
+    e->dirty = true;
+  }
+}
+
+}  // namespace
+
+int batch_engine_create(int device, BatchEngine** out) {
+  auto* e = new BatchEngine();
+  e->device = device;
+  if (cudaStreamCreateWithFlags(&e->st, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    delete e;
+    return RLOBPCG_ERR_CUDA;
+  }
+  e->th = std::thread(engine_main, e);
+  *out = e;
+  return RLOBPCG_OK;
+}
+
+void batch_engine_destroy(BatchEngine* e) {
+  if (!e) return;
+  {
+    std::lock_guard<std::mutex> lk(e->mu);
+    e->stop = true;
+  }
+  e->cv.notify_all();
+  e->th.join();
+  if (e->gexec) cudaGraphExecDestroy(e->gexec);
+  if (e->graph) cudaGraphDestroy(e->graph);
+  if (e->dmem) cudaFreeAsync(e->dmem, e->st);
+  cudaStreamSynchronize(e->st);
+  if (e->Dh) cudaFreeHost(e->Dh);
+  cudaStreamDestroy(e->st);
+  delete e;
+}
+
+bool batch_request_eligible(int64_t n, int k, int dtype, const rlobpcg_opts& o) {
+  const int b = o.block > 0 ? o.block : k;
+  return dtype == RLOBPCG_F64 && b <= batch::BMAX && n <= 512 && !o.locking && o.orth_mode == RLOBPCG_ORTH_HOUSEHOLDER &&
+         o.residual_refresh_every <= 0 && std::max(o.max_iter, o.fixed_iters) <= 200;
+}
+
+size_t batch_extra_bytes(int64_t m, int64_t n, int b) {
+  return batch_solve_bytes(m, n, b, 256, nullptr, nullptr);   // the smallest tile height: the most partials
+}
+
+// set-up of one solve on its plan's stream (host-synchronous); A stays valid until finish
+int batch_solve_setup(rlobpcg_plan_t p, const double* A, int64_t lda, BatchSolve** out) {
+  std::string why;
+  if (!batch_eligible(p, &why)) {
+    set_last_error(why.c_str(), __FILE__, __LINE__);
+    return RLOBPCG_ERR_UNSUPPORTED;
+  }
+  auto* s = new BatchSolve();
+  s->p = p;
+  s->A = A;
+  s->lda = lda;
+  int rc = tile_choice((int)p->n, p->b, p->st, &s->tc);
+  if (!rc)
+    rc = p->opts.sketch_prec == RLOBPCG_SKETCH_F32 ? batch_setup_one<float>(p, A, lda, s->r)
+                                                   : batch_setup_one<double>(p, A, lda, s->r);
+  if (rc) {
+    delete s;
+    return rc;
+  }
+  *out = s;
+  return RLOBPCG_OK;
+}
+
+void batch_solve_submit(BatchEngine* e, BatchSolve* s) {
+  {
+    std::lock_guard<std::mutex> lk(e->mu);
+    e->incoming.push_back(s);
+  }
+  e->cv.notify_all();
+}
+
+int batch_solve_wait(BatchSolve* s) {
+  std::unique_lock<std::mutex> lk(s->mu);
+  s->cv.wait(lk, [&] { return s->finished; });
+  return s->rc;
+}
+
+// outputs of a retired solve on its plan's stream; releases the handle
+int batch_solve_finish(BatchSolve* s, double* sigma, void* V, void* U, double* resid, rlobpcg_info* info) {
+  rlobpcg_plan_s* p = s->p;
+  int rc = s->rc;
+  if (!rc)
+    rc = p->opts.sketch_prec == RLOBPCG_SKETCH_F32
+             ? batch_finish_one<float>(p, s->A, s->lda, s->r, sigma, (double*)V, (double*)U, resid, info)
+             : batch_finish_one<double>(p, s->A, s->lda, s->r, sigma, (double*)V, (double*)U, resid, info);
+  delete s;
+  return rc;
+}
+
+}  // namespace rl
+
+namespace {
+}  // namespace
+
 extern "C" int rlobpcg_batch_tile(int64_t n, int b, int* trows, int* rt, void* stream) {
   if (n < 1 || n > 512 || b < 1 || b > batch::BMAX) return RLOBPCG_ERR_INVALID_ARG;
   TileChoice tc;
@@ -1180,11 +1600,11 @@ extern "C" int rlobpcg_batch_set_tile(int64_t n, int b, int trows, int rt) {
   return RLOBPCG_OK;
 }
 
+
 extern "C" int rlobpcg_solve_batch(int count, rlobpcg_plan_t* plans, const void* const* A, const int64_t* lda,
                                    double* const* sigma, void* const* V, void* const* U, double* const* resid,
                                    rlobpcg_info* infos, int* status, void* stream) {
   if (count < 1 || !plans || !A || !lda || !sigma || !V) return RLOBPCG_ERR_INVALID_ARG;
-  cudaStream_t ust = (cudaStream_t)stream;
   std::string why;
   for (int i = 0; i < count; ++i) {
     rlobpcg_plan_s* p = plans[i];
@@ -1196,11 +1616,17 @@ extern "C" int rlobpcg_solve_batch(int count, rlobpcg_plan_t* plans, const void*
       return RLOBPCG_ERR_UNSUPPORTED;
     }
   }
-  std::vector<TileChoice> tcs(count);
-  for (int i = 0; i < count; ++i) RL_TRY(tile_choice((int)plans[i]->n, plans[i]->b, ust, &tcs[i]));
-
-  // set-up of every solve on its own plan stream; host threads so that the plans' set-ups overlap
-  std::vector<SolveRun> runs(count);
+  int dev = 0;
+  RL_CUDA(cudaGetDevice(&dev));
+  // every class's tile shape first (the autotuner times kernels; nothing else runs meanwhile)
+  for (int i = 0; i < count; ++i) {
+    TileChoice tc;
+    RL_TRY(tile_choice((int)plans[i]->n, plans[i]->b, (cudaStream_t)stream, &tc));
+  }
+  BatchEngine* e = nullptr;
+  RL_TRY(batch_engine_create(dev, &e));
+  // set-ups on up to 8 host threads; each solve joins the running batch as soon as its set-up ends
+  std::vector<BatchSolve*> hs(count, nullptr);
   std::vector<int> rcs(count, RLOBPCG_OK);
   {
     const int nth = std::min(count, 8);
@@ -1208,206 +1634,38 @@ extern "C" int rlobpcg_solve_batch(int count, rlobpcg_plan_t* plans, const void*
     std::atomic<int> next{0};
     for (int t = 0; t < nth; ++t)
       th.emplace_back([&]() {
+        cudaSetDevice(dev);
         for (int i = next++; i < count; i = next++) {
-          rlobpcg_plan_s* p = plans[i];
-          const double* Ai = (const double*)A[i];
-          rcs[i] = p->opts.sketch_prec == RLOBPCG_SKETCH_F32 ? batch_setup_one<float>(p, Ai, lda[i], runs[i])
-                                                              : batch_setup_one<double>(p, Ai, lda[i], runs[i]);
+          rcs[i] = batch_solve_setup(plans[i], (const double*)A[i], lda[i], &hs[i]);
+          if (!rcs[i]) batch_solve_submit(e, hs[i]);
         }
       });
     for (auto& t : th) t.join();
   }
   for (int i = 0; i < count; ++i)
-    if (rcs[i] != RLOBPCG_OK) {
-      if (status)
-        for (int j = 0; j < count; ++j) status[j] = rcs[j];
-      return rcs[i];
-    }
-
-  // per-solve device state of the batched iterations
-  DevArena ar;
-  std::vector<batch::Desc> hd(count);
-  std::vector<double*> Ruv(count), Rlv(count), Yv(count), Gp(count), Rp(count), Gg(count), Rg(count), Rf(count),
-      Hs(count);
-  std::vector<int*> Cn(count);
-  batch::Desc* Dd = nullptr;
-  int2 *pre_items = nullptr, *tile_items = nullptr;
-  int *qh = nullptr, *act_dev = nullptr;
-  std::vector<int2> hpre, htile;
-  int nmax = 1, abmax = 1, rtmax = 16, hist_rows = 1;
-  size_t pre_smem = 0;
-  for (int i = 0; i < count; ++i) {
-    rlobpcg_plan_s* p = plans[i];
-    const int n = (int)p->n, b = p->b, C = 3 * b;
-    const int nt = (int)((p->m + tcs[i].trows - 1) / tcs[i].trows), ng = (nt + batch::GS - 1) / batch::GS;
-    const int rows = std::max(p->opts.max_iter, p->opts.fixed_iters) + 1;
-    ar.want((void**)&Ruv[i], (size_t)n * n * 8);
-    ar.want((void**)&Rlv[i], (size_t)n * n * 8);
-    ar.want((void**)&Yv[i], (size_t)n * b * 8);
-    ar.want((void**)&Gp[i], (size_t)nt * n * b * 8);
-    ar.want((void**)&Rp[i], (size_t)nt * C * C * 8);
-    ar.want((void**)&Gg[i], (size_t)ng * n * b * 8);
-    ar.want((void**)&Rg[i], (size_t)ng * C * C * 8);
-    ar.want((void**)&Rf[i], (size_t)C * C * 8);
-    ar.want((void**)&Hs[i], (size_t)rows * 2 * b * 8);
-    ar.want((void**)&Cn[i], (size_t)(2 + ng) * 4);
-    batch::Desc& d = hd[i];
-    d = batch::Desc{};
-    d.A = (const double*)A[i]; d.m = p->m; d.lda = lda[i]; d.n = n; d.b = b;
-    d.Tb = (double*)p->Tb; d.ATb = (double*)p->ATb; d.GTb = (double*)p->GTb;
-    d.Rs = (double*)p->Rs; d.Res = (double*)p->Res; d.res_norm = p->res_norm; d.theta = p->theta;
-    d.K = (double*)p->K; d.err = p->err; d.rr_info = p->info;
-    d.ntiles = nt; d.trows = tcs[i].trows; d.rt = tcs[i].rt; d.ngroups = ng; d.nrb = (n + batch::PR - 1) / batch::PR;
-    d.iter = 0; d.c = 2 * b; d.nx = 0; d.pending = 0; d.c_prev = 0; d.done = 0; d.matvecs = b;
-    d.fixed = p->opts.fixed_iters;
-    d.max_iter = d.fixed > 0 ? d.fixed : p->opts.max_iter;
-    d.check_every = std::max(1, p->opts.check_every);
-    d.use_stag = p->opts.use_stagnation != 0;
-    d.sigma11 = runs[i].sigma11;
-    d.tau = runs[i].tau;
-    d.stop_reason = d.fixed > 0 ? RLOBPCG_STOP_FIXED : RLOBPCG_STOP_MAX_ITER;
-    for (int rb = 0; rb < d.nrb; ++rb) hpre.push_back(make_int2(i, rb));
-    nmax = std::max(nmax, n);
-    abmax = std::max(abmax, batch::abuf_need(n, b, tcs[i].rt));
-    rtmax = std::max(rtmax, tcs[i].rt);
-    hist_rows = std::max(hist_rows, rows);
-    pre_smem = std::max(pre_smem, batch::bcgs2_pre_smem(n, b));
-  }
-  // tile items: solves with the most work per iteration first, so that their tails overlap the rest
+    if (hs[i]) rcs[i] = batch_solve_wait(hs[i]);
+  // outputs on each plan's stream
   {
-    std::vector<int> order(count);
-    for (int i = 0; i < count; ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-      return (double)hd[x].m * hd[x].n * hd[x].b > (double)hd[y].m * hd[y].n * hd[y].b;
-    });
-    for (int i : order)
-      for (int t = 0; t < hd[i].ntiles; ++t) htile.push_back(make_int2(i, t));
+    const int nth = std::min(count, 8);
+    std::vector<std::thread> th;
+    std::atomic<int> next{0};
+    for (int t = 0; t < nth; ++t)
+      th.emplace_back([&]() {
+        cudaSetDevice(dev);
+        for (int i = next++; i < count; i = next++) {
+          if (!hs[i]) continue;
+          rcs[i] = batch_solve_finish(hs[i], sigma[i], V[i], U ? U[i] : nullptr, resid ? resid[i] : nullptr,
+                                      infos ? &infos[i] : nullptr);
+          hs[i] = nullptr;
+        }
+      });
+    for (auto& t : th) t.join();
   }
-  constexpr int G = 4;   // iterations per graph replay
-  ar.want((void**)&Dd, (size_t)count * sizeof(batch::Desc));
-  ar.want((void**)&pre_items, hpre.size() * sizeof(int2));
-  ar.want((void**)&tile_items, htile.size() * sizeof(int2));
-  ar.want((void**)&qh, (3 * G + 2) * sizeof(int));
-  ar.want((void**)&act_dev, sizeof(int));
-  // the batched iterations run on a stream of their own (a graph cannot be captured on the legacy
-  // default stream), after every set-up
-  cudaStream_t bst = nullptr;
-  RL_CUDA(cudaStreamCreateWithFlags(&bst, cudaStreamNonBlocking));
+  batch_engine_destroy(e);
+  int first = RLOBPCG_OK;
   for (int i = 0; i < count; ++i) {
-    RL_CUDA(cudaEventRecord(plans[i]->ev[5], plans[i]->st));
-    RL_CUDA(cudaStreamWaitEvent(bst, plans[i]->ev[5], 0));
+    if (status) status[i] = rcs[i];
+    if (rcs[i] < 0 && first >= 0) first = rcs[i];
   }
-  RL_TRY(ar.alloc(bst));
-  int rc = RLOBPCG_OK;
-  int* act_h = nullptr;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t gexec = nullptr;
-  const size_t tile_smem = batch::tile_smem_bytes(nmax, abmax, rtmax);
-  do {
-    for (int i = 0; i < count; ++i) {
-      rlobpcg_plan_s* p = plans[i];
-      batch::Desc& d = hd[i];
-      d.Ru = Ruv[i]; d.Rl = Rlv[i]; d.Y = Yv[i];
-      d.Gpart = Gp[i]; d.Rpart = Rp[i]; d.Ggrp = Gg[i]; d.Rgrp = Rg[i]; d.Rfin = Rf[i]; d.hist = Hs[i];
-      d.cnt = Cn[i];
-      // R^{-1} row-major and column-major (= R^{-H} row-major for real R), widened to FP64
-      const bool f32 = p->opts.sketch_prec == RLOBPCG_SKETCH_F32;
-      const int64_t nn = p->n * p->n;
-      rc = f32 ? batch::widen_launch<float>((const float*)p->Rinv_r, nn, Ruv[i], bst)
-               : batch::widen_launch<double>((const double*)p->Rinv_r, nn, Ruv[i], bst);
-      if (!rc)
-        rc = f32 ? batch::widen_launch<float>((const float*)p->Rinv_c, nn, Rlv[i], bst)
-                 : batch::widen_launch<double>((const double*)p->Rinv_c, nn, Rlv[i], bst);
-      if (rc) break;
-      RL_CUDA(cudaMemcpyAsync(Hs[i], runs[i].hist.r[0].data(), p->b * sizeof(double), cudaMemcpyHostToDevice, bst));
-      RL_CUDA(cudaMemsetAsync(Cn[i], 0, (size_t)(2 + d.ngroups) * 4, bst));
-    }
-    if (rc) break;
-    RL_CUDA(cudaMemcpyAsync(Dd, hd.data(), count * sizeof(batch::Desc), cudaMemcpyHostToDevice, bst));
-    RL_CUDA(cudaMemcpyAsync(pre_items, hpre.data(), hpre.size() * sizeof(int2), cudaMemcpyHostToDevice, bst));
-    RL_CUDA(cudaMemcpyAsync(tile_items, htile.data(), htile.size() * sizeof(int2), cudaMemcpyHostToDevice, bst));
-    if ((rc = batch::prepare(pre_smem, tile_smem))) break;
-    int per_sm = 1;
-    if ((rc = batch::tile_blocks_per_sm(tile_smem, &per_sm))) break;
-    const int slots = num_sms() * std::max(1, per_sm);
-    const int pre_grid = std::max(1, std::min((int)hpre.size(), num_sms() * 2));
-    const int tile_grid = std::max(1, std::min((int)htile.size(), slots));
-    if (cudaMallocHost((void**)&act_h, sizeof(int)) != cudaSuccess) { cudaGetLastError(); rc = RLOBPCG_ERR_CUDA; break; }
-    *act_h = count;
-    // G iterations as one graph: reset the work queues, then (precondition, tile) x G, then the
-    // number of solves still running
-    RL_CUDA(cudaStreamBeginCapture(bst, cudaStreamCaptureModeThreadLocal));
-    int crc = cudaMemsetAsync(qh, 0, (3 * G + 2) * sizeof(int), bst) == cudaSuccess ? RLOBPCG_OK : RLOBPCG_ERR_CUDA;
-    for (int g = 0; g < G && !crc; ++g) {
-      crc = batch::pre_launch(0, Dd, pre_items, (int)hpre.size(), qh + 3 * g, pre_grid, pre_smem, bst);
-      if (!crc) crc = batch::pre_launch(1, Dd, pre_items, (int)hpre.size(), qh + 3 * g + 1, pre_grid, pre_smem, bst);
-      if (!crc) crc = batch::tile_launch(false, Dd, tile_items, (int)htile.size(), qh + 3 * g + 2, tile_grid, nmax, abmax,
-                                         tile_smem, bst);
-    }
-    if (!crc) crc = batch::active_launch(Dd, count, act_dev, bst);
-    if (!crc && cudaMemcpyAsync(act_h, act_dev, sizeof(int), cudaMemcpyDeviceToHost, bst) != cudaSuccess)
-      crc = RLOBPCG_ERR_CUDA;
-    const cudaError_t ce = cudaStreamEndCapture(bst, &graph);
-    if (crc || ce != cudaSuccess) {
-      cudaGetLastError();
-      rc = crc ? crc : RLOBPCG_ERR_CUDA;
-      break;
-    }
-    RL_CUDA(cudaGraphInstantiate(&gexec, graph, 0));
-    const int max_rep = (hist_rows + G - 1) / G + 1;
-    for (int rep = 0; rep < max_rep; ++rep) {
-      RL_CUDA(cudaGraphLaunch(gexec, bst));
-      RL_CUDA(cudaStreamSynchronize(bst));
-      if (*act_h == 0) break;
-    }
-    // the coefficients of the last Rayleigh-Ritz step, applied to A V and A X
-    RL_CUDA(cudaMemsetAsync(qh + 3 * G, 0, sizeof(int), bst));
-    if ((rc = batch::tile_launch(true, Dd, tile_items, (int)htile.size(), qh + 3 * G, tile_grid, nmax, abmax, tile_smem,
-                                 bst)))
-      break;
-    RL_CUDA(cudaMemcpyAsync(hd.data(), Dd, count * sizeof(batch::Desc), cudaMemcpyDeviceToHost, bst));
-    RL_CUDA(cudaStreamSynchronize(bst));
-    for (int i = 0; i < count; ++i) {
-      rlobpcg_plan_s* p = plans[i];
-      const batch::Desc& d = hd[i];
-      SolveRun& r = runs[i];
-      const int b = p->b;
-      std::vector<double> h((size_t)(d.iter + 1) * 2 * b);
-      RL_CUDA(cudaMemcpy(h.data(), Hs[i], h.size() * sizeof(double), cudaMemcpyDeviceToHost));
-      for (int t = 1; t <= d.iter; ++t) {
-        r.hist.r.emplace_back(h.begin() + (size_t)t * 2 * b, h.begin() + (size_t)t * 2 * b + b);
-        r.hist.th.emplace_back(h.begin() + (size_t)t * 2 * b + b, h.begin() + (size_t)(t + 1) * 2 * b);
-      }
-      r.it = d.iter;
-      r.stop = d.stop_reason;
-      r.matvecs = d.matvecs;
-      r.nx = d.nx;
-      r.theta_s = p->theta + (d.iter > 0 ? d.c_prev - b : 0);
-    }
-  } while (0);
-  if (gexec) cudaGraphExecDestroy(gexec);
-  if (graph) cudaGraphDestroy(graph);
-  if (act_h) cudaFreeHost(act_h);
-  // outputs per solve on its own stream, after the batch stream
-  RL_CUDA(cudaEventRecord(plans[0]->ev[6], bst));
-  int first = rc;
-  for (int i = 0; i < count; ++i) {
-    rlobpcg_plan_s* p = plans[i];
-    int ri = rc;
-    if (!ri) {
-      RL_CUDA(cudaStreamWaitEvent(p->st, plans[0]->ev[6], 0));
-      const double* Ai = (const double*)A[i];
-      ri = p->opts.sketch_prec == RLOBPCG_SKETCH_F32
-               ? batch_finish_one<float>(p, Ai, lda[i], runs[i], sigma[i], (double*)V[i], U ? (double*)U[i] : nullptr,
-                                         resid ? resid[i] : nullptr, infos ? &infos[i] : nullptr)
-               : batch_finish_one<double>(p, Ai, lda[i], runs[i], sigma[i], (double*)V[i], U ? (double*)U[i] : nullptr,
-                                          resid ? resid[i] : nullptr, infos ? &infos[i] : nullptr);
-    }
-    if (status) status[i] = ri;
-    if (ri < 0 && first >= 0) first = ri;
-  }
-  ar.release(bst);
-  cudaStreamSynchronize(bst);
-  cudaStreamDestroy(bst);
-  return first < 0 ? first : RLOBPCG_OK;
+  return first;
 }

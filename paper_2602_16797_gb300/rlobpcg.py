@@ -34,6 +34,8 @@ RLOBPCG_ORTH_SVQB = 1
 RLOBPCG_STOP_CONVERGED = 0
 RLOBPCG_STOP_MAX_ITER = 1
 RLOBPCG_STOP_FIXED = 2
+RLOBPCG_SERVE_STREAMS = 0
+RLOBPCG_SERVE_BATCHED = 1
 
 
 class rlobpcg_opts(ctypes.Structure):
@@ -90,6 +92,7 @@ _SIGS = {
     "rlobpcg_history": (c_int, [c_void_p, c_void_p, c_void_p, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
     "rlobpcg_plan_workspace_size": (c_size_t, [c_int64, c_int64, c_int, c_int, ctypes.POINTER(rlobpcg_opts)]),
     "rlobpcg_server_create": (c_int, [ctypes.POINTER(c_void_p), c_size_t, c_int, c_int]),
+    "rlobpcg_server_create_ex": (c_int, [ctypes.POINTER(c_void_p), c_size_t, c_int, c_int, c_int]),
     "rlobpcg_server_submit": (c_int, [c_void_p, c_void_p, c_int64, c_int64, c_int64, c_int, c_int,
                                       ctypes.POINTER(rlobpcg_opts), ctypes.POINTER(c_int64)]),
     "rlobpcg_server_poll": (c_int, [c_void_p, c_int64]),
@@ -297,9 +300,13 @@ def rlobpcg_plan_workspace_size(m: int, n: int, k: int, dtype: int, opts: rlobpc
     return load().rlobpcg_plan_workspace_size(m, n, k, dtype, ctypes.byref(opts) if opts is not None else None)
 
 
-def rlobpcg_server_create(budget_bytes: int, max_active: int, device: int = 0) -> int:
+def rlobpcg_server_create(budget_bytes: int, max_active: int, device: int = 0, mode: int | None = None) -> int:
     h = c_void_p()
-    _check("rlobpcg_server_create", load().rlobpcg_server_create(ctypes.byref(h), budget_bytes, max_active, device))
+    if mode is None:
+        _check("rlobpcg_server_create", load().rlobpcg_server_create(ctypes.byref(h), budget_bytes, max_active, device))
+    else:
+        _check("rlobpcg_server_create_ex",
+               load().rlobpcg_server_create_ex(ctypes.byref(h), budget_bytes, max_active, device, mode))
     return h.value
 
 

@@ -130,3 +130,54 @@ def test_one_waiter_per_ticket():
             rl.rlobpcg_server_wait(srv, t, None, None, None)
     finally:
         rl.rlobpcg_server_destroy(srv)
+
+
+def _batch_alone(A, k, opts):
+    """rlobpcg_solve_batch with this request alone (the reference for the batched server)."""
+    m, n = A.shape
+    st = torch.cuda.current_stream().cuda_stream
+    Ad = torch.from_numpy(A).cuda()
+    plan = rl.rlobpcg_plan(m, n, k, rl.RLOBPCG_F64, opts, st)
+    sig = torch.empty(k, dtype=torch.float64, device="cuda")
+    V = torch.empty((n, k), dtype=torch.float64, device="cuda")
+    try:
+        rc, infos, status = rl.rlobpcg_solve_batch([plan], [Ad.data_ptr()], [n], [sig.data_ptr()], [V.data_ptr()],
+                                                   None, None, st)
+    finally:
+        rl.rlobpcg_plan_destroy(plan)
+    assert rc >= 0
+    return sig.cpu().numpy(), V.cpu().numpy(), infos[0].iters
+
+
+def test_batched_server_results_equal_the_batch_alone_and_budget_holds():
+    """Batched serving: the iterations of every admitted small solve run together in the batch
+    engine, solves joining and leaving between replays; each result is bit-identical to
+    rlobpcg_solve_batch of that request alone. A complex request in the mix (not batchable) runs
+    whole on its worker and equals rlobpcg_solve."""
+    reqs = _requests(12)
+    alone = [_batch_alone(A, k, _opts(seed)) for A, k, seed in reqs]
+    rng = np.random.default_rng(77)
+    Ac = wl.planted(rng, 6000, np.concatenate([np.logspace(0, -6, 37), np.logspace(-9, -10, 3)]), complex_=True)[0]
+    Ac = np.ascontiguousarray(Ac)
+    sc, Vc, _, _, _ = rl.solve(torch.from_numpy(Ac).cuda(), 3, opts=_opts(5))
+    srv = rl.rlobpcg_server_create(4 << 30, 16, 0, rl.RLOBPCG_SERVE_BATCHED)
+    try:
+        tickets = [rl.rlobpcg_server_submit(srv, A.ctypes.data, A.shape[0], A.shape[1], A.shape[1], k,
+                                            rl.RLOBPCG_F64, _opts(seed)) for A, k, seed in reqs]
+        tc = rl.rlobpcg_server_submit(srv, Ac.ctypes.data, Ac.shape[0], Ac.shape[1], Ac.shape[1], 3,
+                                      rl.RLOBPCG_C128, _opts(5))
+        for (A, k, seed), t, (s0, V0, it0) in zip(reqs, tickets, alone):
+            sig = np.zeros(k)
+            V = np.zeros((A.shape[1], k))
+            info = rl.rlobpcg_info()
+            rl.rlobpcg_server_wait(srv, t, sig.ctypes.data, V.ctypes.data, None, info)
+            assert info.iters == it0
+            assert np.array_equal(sig, s0) and np.array_equal(V, V0)
+        sig = np.zeros(3)
+        V = np.zeros((Ac.shape[1], 3), dtype=np.complex128)
+        rl.rlobpcg_server_wait(srv, tc, sig.ctypes.data, V.ctypes.data, None, rl.rlobpcg_info())
+        assert np.array_equal(sig, sc.cpu().numpy()) and np.array_equal(V, Vc.cpu().numpy())
+        st = rl.rlobpcg_server_stats(srv)
+        assert st["completed"] == len(reqs) + 1 and st["peak_bytes"] <= 4 << 30 and st["peak_running"] >= 2
+    finally:
+        rl.rlobpcg_server_destroy(srv)
