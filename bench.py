@@ -649,10 +649,15 @@ def run_block_study(args, rank, world, local_rank):
 
 
 def run_serve(args, rank, world, local_rank):
-    """Serving stream: half Loewner, half planted requests (m log-uniform in [2e3, 5e5], n uniform
-    in [20, 400], k in {1, 2, 4}), HBM admission budget 150 GB. Measures the saturated rate with
-    `--slots` concurrent solves, the same stream one solve at a time, and Poisson arrivals at
-    0.5 / 0.9 / 1.2 x the saturated rate (p50 / p99 latency from submit to result)."""
+    """Serving stream: `--requests` requests (half Loewner, half planted; m log-uniform in
+    [2e3, 5e5], n uniform in [20, 400], k in {1, 2, 4}) under an HBM admission budget of 150 GB,
+    drawn from a pool of `--pool` seeded matrices in pinned host memory (request r: pool entry
+    r mod pool, its own sketch seed). Measures the saturated rate of the batched server (`--slots`
+    workers; the iterations of every admitted request with m n b <= 2^23 in one batch engine,
+    larger ones whole with their Gram products on the tensor cores), the same stream on the
+    per-stream server (`--stream-slots` whole solves overlapping) and one solve at a time, and
+    Poisson arrivals at 0.5 / 0.9 / 1.2 x the batched saturated rate (p50 / p99 latency from
+    submit to result, host copy of A included)."""
     import torch
 
     from paper_2602_16797_gb300 import rlobpcg as rl
@@ -661,19 +666,22 @@ def run_serve(args, rank, world, local_rank):
         return None
     torch.cuda.set_device(local_rank)
     rl.load()
+    t_gen = time.perf_counter()
+    pool = wl.serve_pool(args.pool)
+    t_gen = time.perf_counter() - t_gen
     reqs = []
     for r in range(args.requests):
-        A, k, kind = wl.serve_request(r)
-        reqs.append((np.ascontiguousarray(A), k, wl.SERVE_SEED_BASE + r))
+        A, k, kind = pool[r % len(pool)]
+        reqs.append((A, k, wl.SERVE_SEED_BASE + r))
     budget = 150 * (1 << 30)
 
     def opts(seed):
-        o = rl.rlobpcg_default_opts()
+        o = rl.rlobpcg_default_opts()   # whole solves: Gram products on the tensor cores
         o.seed = seed
         return o
 
-    def stream(slots, arrivals=None):
-        srv = rl.rlobpcg_server_create(budget, slots, local_rank)
+    def stream(slots, mode, arrivals=None):
+        srv = rl.rlobpcg_server_create(budget, slots, local_rank, mode)
         t0 = time.perf_counter()
         tickets = []
         for i, (A, k, seed) in enumerate(reqs):
@@ -681,7 +689,7 @@ def run_serve(args, rank, world, local_rank):
                 dt = t0 + arrivals[i] - time.perf_counter()
                 if dt > 0:
                     time.sleep(dt)
-            tickets.append(rl.rlobpcg_server_submit(srv, A.ctypes.data, A.shape[0], A.shape[1], A.shape[1], k,
+            tickets.append(rl.rlobpcg_server_submit(srv, A.data_ptr(), A.shape[0], A.shape[1], A.shape[1], k,
                                                     rl.RLOBPCG_F64, opts(seed)))
         iters = []
         for (A, k, seed), t in zip(reqs, tickets):
@@ -690,36 +698,44 @@ def run_serve(args, rank, world, local_rank):
             iters.append(info.iters)
         makespan = time.perf_counter() - t0
         st = rl.rlobpcg_server_stats(srv)
+        st["engine"] = rl.rlobpcg_server_engine_stats(srv)
         rl.rlobpcg_server_destroy(srv)
         st["makespan_s"] = makespan
         st["rate"] = len(reqs) / makespan
         st["mean_iters"] = float(np.mean(iters))
         return st
 
-    warm = reqs[:4]
-    for A, k, seed in warm:
-        rl.solve(torch.from_numpy(A).cuda(), k, opts=opts(seed))
-    sat = stream(args.slots)
-    seq = stream(1)
+    # warm-up: the batched kernels' tile shapes for every class of the pool, then a short stream
+    for A, k, seed in reqs[:len(pool)]:
+        rl.rlobpcg_batch_tile(A.shape[1], k)
+    B, S = rl.RLOBPCG_SERVE_BATCHED, rl.RLOBPCG_SERVE_STREAMS
+    sat = stream(args.slots, B)
+    per_stream = stream(args.stream_slots, S)
+    seq = stream(1, S)
     lat = {}
     rng = np.random.default_rng(4242)
     for f in (0.5, 0.9, 1.2):
         lam = f * sat["rate"]
         arr = np.cumsum(rng.exponential(1.0 / lam, len(reqs)))
-        st = stream(args.slots, arr)
+        st = stream(args.slots, B, arr)
         lat[f"{f}x"] = {"offered_per_s": lam, "solves_per_s": st["rate"], "p50_ms": st["p50_ms"],
                         "p99_ms": st["p99_ms"], "peak_running": st["peak_running"], "peak_gb": st["peak_bytes"] / 1e9}
-    bytes_in = float(np.mean([A.nbytes for A, _, _ in reqs]))
+    bytes_in = float(np.mean([A.numel() * 8 for A, _, _ in reqs]))
     return {"metric": METRIC, "value": sat["rate"], "unit": "solves/s", "n_gpus": 1, "steps": len(reqs),
-            "warmup": len(warm), "ms_per_step": 1e3 / sat["rate"], "higher_is_better": True, "scaling": "weak",
+            "warmup": len(pool), "ms_per_step": 1e3 / sat["rate"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded; the paper's matrix families)",
-            "config": {"workload": f"serving stream of {len(reqs)} requests (half Loewner, half planted; m log-uniform "
-                                   f"[2e3,5e5], n U[20,400], k in {{1,2,4}}), HBM budget 150 GB, {args.slots} slots",
-                       "parallelism": "continuous batching on one GPU"},
-            "saturated": {"solves_per_s": sat["rate"], "p50_ms": sat["p50_ms"], "p99_ms": sat["p99_ms"],
-                          "peak_running": sat["peak_running"], "mean_iters": sat["mean_iters"]},
+            "config": {"workload": f"serving stream of {len(reqs)} requests over a pool of {len(pool)} matrices "
+                                   f"(half Loewner, half planted; m log-uniform [2e3,5e5], n U[20,400], k in "
+                                   f"{{1,2,4}}), HBM budget 150 GB, batched server with {args.slots} slots",
+                       "parallelism": "continuous batching on one GPU", "pool_generation_s": t_gen},
+            "batched": {"solves_per_s": sat["rate"], "p50_ms": sat["p50_ms"], "p99_ms": sat["p99_ms"],
+                        "peak_running": sat["peak_running"], "mean_iters": sat["mean_iters"],
+                        "engine": sat["engine"]},
+            "per_stream": {"slots": args.stream_slots, "solves_per_s": per_stream["rate"],
+                           "p50_ms": per_stream["p50_ms"], "p99_ms": per_stream["p99_ms"],
+                           "mean_iters": per_stream["mean_iters"]},
             "one_at_a_time": {"solves_per_s": seq["rate"], "p50_ms": seq["p50_ms"], "p99_ms": seq["p99_ms"]},
-            "poisson": lat,
+            "poisson_batched": lat,
             "e2e": {"value": sat["rate"], "unit": "solves/s", "h2d_bytes_per_step": bytes_in,
                     "d2h_bytes_per_step": None}}
 
@@ -743,7 +759,9 @@ def main():
                     help="run exactly this many LOBPCG iterations per solve (no stop test)")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision form beside the plain one")
     ap.add_argument("--requests", type=int, default=2000, help="serve_stream: number of requests")
-    ap.add_argument("--slots", type=int, default=8, help="serve_stream: concurrent solves")
+    ap.add_argument("--slots", type=int, default=64, help="serve_stream: solves iterating together (batched server)")
+    ap.add_argument("--stream-slots", type=int, default=8, help="serve_stream: whole solves overlapping (per-stream server)")
+    ap.add_argument("--pool", type=int, default=48, help="serve_stream: distinct matrices the requests are drawn from")
     args = ap.parse_args()
     rank, world, local_rank = replicas.world_from_env()
     if world > 1 and args.impl == "ours":

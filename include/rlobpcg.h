@@ -212,6 +212,25 @@ int rlobpcg_server_create(rlobpcg_server_t* out, size_t hbm_budget_bytes, int ma
  * rlobpcg_solve_batch with that request alone (batched mode), whatever else runs. */
 int rlobpcg_server_create_ex(rlobpcg_server_t* out, size_t hbm_budget_bytes, int max_active, int device, int mode);
 
+/* Batched mode: the largest m n b (rows x columns x block) a request may have to iterate in the
+ * batch engine; larger requests run whole on their worker, where the Gram products of real FP64
+ * solves run on the tensor cores (gram_split). Applies to requests submitted afterwards.
+ * Default RLOBPCG_SERVE_BATCH_LIMIT_DEFAULT. INVALID_ARG for a negative limit. */
+#define RLOBPCG_SERVE_BATCH_LIMIT_DEFAULT ((int64_t)1 << 23)
+int rlobpcg_server_set_batch_limit(rlobpcg_server_t s, int64_t max_mnb);
+
+/* Counters of a batched server's engine since creation (all zero in streams mode). */
+typedef struct {
+  int64_t replays;      /* graph replays (4 iterations of every joined solve each)               */
+  int64_t joins;        /* solves that joined the batch                                           */
+  int64_t retires;      /* solves handed back                                                     */
+  int64_t rebuilds;     /* work-list + graph rebuilds (membership changes)                        */
+  double gpu_ms;        /* device time inside replays (CUDA events on the engine stream)          */
+  double host_ms;       /* engine thread time outside replays (joins, retires, rebuilds, waits)   */
+  double active_mean;   /* solves per replay, averaged over replays                               */
+} rlobpcg_engine_stats;
+int rlobpcg_server_engine_stats(rlobpcg_server_t s, rlobpcg_engine_stats* out);
+
 /* Queue a solve of the k smallest singular triplets of A (HOST memory, m x n row-major, lda >= n,
  * F64 or C128; it must stay valid until rlobpcg_server_wait returns for this ticket).
  * opts may be NULL (defaults). Errors: INVALID_ARG, OOM when the request alone exceeds the
@@ -279,7 +298,7 @@ int rlobpcg_solve_batch(int count, rlobpcg_plan_t* plans, const void* const* A, 
 int rlobpcg_batch_tile(int64_t n, int b, int* trows, int* rt, void* stream);
 
 /* Pin the tile shape of the (n, b) class (one of the candidates the autotuner considers:
- * trows in {256, 512, 1024, 2048}, rt in {16, 32}, within shared memory), e.g. to reproduce
+ * trows in {256, 512, 1024, 2048}, rt in {8, 16}, within shared memory), e.g. to reproduce
  * results across processes. INVALID_ARG for a shape outside the candidates. */
 int rlobpcg_batch_set_tile(int64_t n, int b, int trows, int rt);
 

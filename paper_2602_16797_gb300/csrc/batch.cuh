@@ -12,7 +12,6 @@ constexpr int NT = 256;         // threads of every batched kernel
 constexpr int GS = 16;          // tiles per group of the two-level reduction
 constexpr int PR = 32;          // rows of W per precondition item
 constexpr int QRC = 128;        // rows folded into the running R per Householder step
-constexpr int G1 = 16;          // threads per row in the first product (fixes its summation order)
 constexpr int UR = 64;          // rows per staging step of the coefficient update
 constexpr int BMAX = 5;         // block size limit of the batched path (3b <= 15: the 16-column Jacobi)
 
@@ -48,9 +47,10 @@ struct Desc {
 
 
 // dynamic shared memory of the tile kernel: W^T and the G accumulator (nw doubles each, nw >= n b
-// for every solve of the launch), the staging area, and the phase-1 partials and row sums
+// for every solve of the launch), the staging area (two stages of A rows, or the factor and tail
+// scratch), and the stage's row products Y
 inline size_t tile_smem_bytes(int nw, int abuf_elems, int rtmax) {
-  return ((size_t)2 * nw + (size_t)abuf_elems + (size_t)rtmax * BMAX * G1 + (size_t)rtmax * BMAX) * sizeof(double);
+  return ((size_t)2 * nw + (size_t)abuf_elems + (size_t)rtmax * BMAX) * sizeof(double);
 }
 
 int abuf_need(int n, int b, int rt);

@@ -25,7 +25,7 @@
 //
 // Nothing waits on another CTA: a dependency is met by the CTA that completes it (a fenced atomic
 // counter), so there are no spin waits. Every sum runs in an order fixed by the solve's own shape
-// and tile height (tiles in order, groups in order, phase-1 partials in order), so a solve gives
+// and tile height (tiles in order, groups in order, a fixed butterfly per row), so a solve gives
 // the same bits alone and in any batch. A solve that has stopped skips its items.
 namespace batch {
 
@@ -129,24 +129,29 @@ __device__ inline void tri_rows(const double* L, int n, bool lower, const double
   }
 }
 
-// phase 1: Ps[(r, j), ps] = sum over k = ps (mod G1) of A[r, k] W[k, j]
+// phase 1: a warp per row r of the stage: lane l sums A[r, k] W[k, j] over k = l (mod 32), then a
+// butterfly over the warp (a fixed order); lane 0 writes Y[r, :] (shared) and A W (global)
 template <int B>
-__device__ inline void gram_phase1(const double* cur, int nr, int n, const double* Wt, double* Ps) {
-  const int tid = threadIdx.x;
-  for (int rb = 0; rb < nr; rb += NT / G1) {
-    const int r = rb + tid / G1, ps = tid % G1;
-    if (r < nr) {
-      double y[B];
+__device__ inline void gram_phase1(const double* cur, int nr, int n, const double* Wt, double* Ys, double* aw,
+                                   int64_t ldaw) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int r = warp; r < nr; r += NT / 32) {
+    double y[B];
 #pragma unroll
-      for (int j = 0; j < B; ++j) y[j] = 0.0;
-      const double* ar = cur + (size_t)r * n;
-      for (int k = ps; k < n; k += G1) {
-        const double a = ar[k];
+    for (int j = 0; j < B; ++j) y[j] = 0.0;
+    const double* ar = cur + (size_t)r * n;
+    for (int k = lane; k < n; k += 32) {
+      const double a = ar[k];
 #pragma unroll
-        for (int j = 0; j < B; ++j) y[j] = fma(a, Wt[(size_t)j * n + k], y[j]);
+      for (int j = 0; j < B; ++j) y[j] = fma(a, Wt[(size_t)j * n + k], y[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+      const double v = warp_sum(y[j]);
+      if (lane == 0) {
+        Ys[r * B + j] = v;
+        aw[(int64_t)r * ldaw + j] = v;
       }
-#pragma unroll
-      for (int j = 0; j < B; ++j) Ps[((size_t)r * B + j) * G1 + ps] = y[j];
     }
   }
 }
@@ -334,7 +339,7 @@ __global__ void __launch_bounds__(NT, 2) tile_kernel(Desc* D, const int2* __rest
           Wt[(size_t)j * n + k] = sd.Tb[(int64_t)k * C + b + j];
           Gacc[e] = 0.0;
         }
-        double* Ys = Ps + (size_t)rt * b * G1;
+        double* Ys = Ps;
         auto issue = [&](int q, double* dst) {   // cp.async of rows [q, q + rt) of the tile
           const int nr = min(rt, rows - q);
           const double* src = sd.A + (r0 + q) * sd.lda;
@@ -346,27 +351,24 @@ __global__ void __launch_bounds__(NT, 2) tile_kernel(Desc* D, const int2* __rest
           }
           asm volatile("cp.async.commit_group;\n" ::: "memory");
         };
-        // one stage of rt rows (two CTAs share an SM: one's loads and reductions overlap the other's
-        // FP64 products)
+        // two stages of rt rows: the next stage loads while this one computes
         const int nsub = (rows + rt - 1) / rt;
+        issue(0, Abuf);
         for (int q = 0; q < nsub; ++q) {
-          double* cur = Abuf;
-          issue(q * rt, cur);
-          asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+          double* cur = Abuf + (size_t)(q & 1) * rt * n;
+          if (q + 1 < nsub) {
+            issue((q + 1) * rt, Abuf + (size_t)((q + 1) & 1) * rt * n);
+            asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+          } else {
+            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+          }
           __syncthreads();
           const int nr = min(rt, rows - q * rt);
-          // phase 1: partial dot products, G1 threads per row, columns k = ps (mod G1)
-#define RL_P1(B) gram_phase1<B>(cur, nr, n, Wt, Ps)
+          double* aw = sd.ATb + (r0 + q * rt) * C + b;
+          // phase 1: Y = A W for the stage's rows (also the A W columns of A_T)
+#define RL_P1(B) gram_phase1<B>(cur, nr, n, Wt, Ys, aw, C)
           RL_BATCH_DISPATCH_B(b, RL_P1)
 #undef RL_P1
-          __syncthreads();
-          for (int e = tid; e < nr * b; e += NT) {
-            const double* p = Ps + (size_t)e * G1;
-            double s = p[0];
-            for (int t = 1; t < G1; ++t) s += p[t];
-            Ys[e] = s;
-            sd.ATb[(r0 + q * rt + e / b) * C + b + (e % b)] = s;
-          }
           __syncthreads();
           // phase 2: Gacc[k, :] += A[r, k] Y[r, :] over the rows in order
 #define RL_P2(B) gram_phase2<B>(cur, nr, n, Ys, Gacc)
@@ -445,7 +447,7 @@ namespace batch {
 // update and the tail's Rayleigh-Ritz scratch
 int abuf_need(int n, int b, int rt) {
   const int C = 3 * b;
-  size_t need = (size_t)rt * n;
+  size_t need = (size_t)2 * rt * n;
   need = std::max(need, (size_t)(C + QRC) * C);
   need = std::max(need, (size_t)C * 2 * b + (size_t)UR * C);
   need = std::max(need, (rr_small_smem<double>(C, b) + 7) / 8 + 2);   // 3b <= 15

@@ -14,6 +14,7 @@ struct BatchEngine;
 struct BatchSolve;
 
 int batch_engine_create(int device, BatchEngine** out);
+void batch_engine_stats(BatchEngine* e, rlobpcg_engine_stats* out);
 // every submitted solve must have been waited for
 void batch_engine_destroy(BatchEngine* e);
 // real FP64, block <= 5, n <= 512, at most 200 iterations, no locking, SVQB or residual refresh

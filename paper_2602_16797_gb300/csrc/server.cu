@@ -14,6 +14,7 @@
 // Requests the batched kernels do not take (complex, block > 5, n > 512, locking, SVQB) run whole
 // on their worker. In both modes a result does not depend on what else is running.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cstdio>
 #include <cstring>
@@ -40,6 +41,7 @@ struct Request {
   size_t bytes = 0;
   int state = 0;  // 0 queued, 1 running, 2 done
   bool claimed = false;  // a thread is in rlobpcg_server_wait for this ticket
+  bool engine = false;   // its iterations run in the batch engine
   int rc = 0;
   char err[512] = "";  // the worker's last error message when rc != RLOBPCG_OK
   clock_t_::time_point t_arrive, t_start, t_done;
@@ -56,6 +58,7 @@ struct rlobpcg_server_s {
   int device = 0;
   int mode = RLOBPCG_SERVE_STREAMS;
   rl::BatchEngine* engine = nullptr;   // batched mode
+  std::atomic<int64_t> batch_limit{RLOBPCG_SERVE_BATCH_LIMIT_DEFAULT};   // largest m n b the engine takes
   size_t budget = 0, in_use = 0, peak = 0;
   int max_active = 1, running = 0, peak_running = 0;
   bool stop = false;
@@ -73,6 +76,27 @@ struct rlobpcg_server_s {
 };
 
 namespace {
+
+// Does the batch engine take this request? Batched mode, a shape and options the batched kernels
+// run, and m n b at most the server's limit (larger solves keep their own launches, where the Gram
+// products run on the tensor cores).
+bool routed_to_engine(const rlobpcg_server_s* s, int64_t m, int64_t n, int k, int dtype, const rlobpcg_opts& o) {
+  const int b = o.block > 0 ? o.block : k;
+  return s->engine && rl::batch_request_eligible(n, k, dtype, o) && m * n * (int64_t)b <= s->batch_limit;
+}
+
+// Device footprint of one request: the plan's workspace plus a device copy of A (plus the
+// batched iterations' buffers when the batch engine takes it; its plan then has no split of A).
+size_t request_bytes(int64_t m, int64_t n, int k, int dtype, rlobpcg_opts o, bool engine) {
+  size_t extra = 0;
+  if (engine) {
+    o.gram_split = 0;
+    extra = rl::batch_extra_bytes(m, n, o.block > 0 ? o.block : k);
+  }
+  const size_t ws = rlobpcg_plan_workspace_size(m, n, k, dtype, &o);
+  if (ws == 0) return 0;
+  return ws + extra + (((size_t)m * n * elem_bytes(dtype) + 255) & ~(size_t)255);
+}
 
 void worker_main(rlobpcg_server_s* s, cudaStream_t st) {
   cudaSetDevice(s->device);
@@ -98,7 +122,10 @@ void worker_main(rlobpcg_server_s* s, cudaStream_t st) {
     const size_t esz = elem_bytes(r->dtype);
     rlobpcg_plan_t plan = nullptr;
     void* Ad = nullptr;
-    int rc = rlobpcg_plan(&plan, r->m, r->n, r->k, r->dtype, &r->opts, st);
+    const bool engine = r->engine;
+    rlobpcg_opts po = r->opts;
+    if (engine) po.gram_split = 0;   // the set-up's one Gram pass on the FP64 cores: no split of A
+    int rc = rlobpcg_plan(&plan, r->m, r->n, r->k, r->dtype, &po, st);
     if (rc == RLOBPCG_OK) {
       if (cudaMallocAsync(&Ad, (size_t)r->m * r->n * esz, st) != cudaSuccess) {
         cudaGetLastError();
@@ -113,7 +140,7 @@ void worker_main(rlobpcg_server_s* s, cudaStream_t st) {
       }
     }
     if (rc == RLOBPCG_OK) {
-      if (s->engine && rl::batch_request_eligible(r->n, r->k, r->dtype, r->opts)) {
+      if (engine) {
         // set-up here, iterations in the batch engine with every other admitted solve, outputs here
         rl::BatchSolve* h = nullptr;
         rc = rl::batch_solve_setup(plan, (const double*)Ad, r->n, &h);
@@ -144,16 +171,6 @@ void worker_main(rlobpcg_server_s* s, cudaStream_t st) {
     s->cv_done.notify_all();
     s->cv_work.notify_all();
   }
-}
-
-// Device footprint of one request: the plan's workspace plus a device copy of A (plus the
-// batched iterations' buffers when the batch engine takes it).
-size_t request_bytes(int64_t m, int64_t n, int k, int dtype, const rlobpcg_opts& o, bool batched) {
-  const size_t ws = rlobpcg_plan_workspace_size(m, n, k, dtype, &o);
-  if (ws == 0) return 0;
-  size_t extra = 0;
-  if (batched && rl::batch_request_eligible(n, k, dtype, o)) extra = rl::batch_extra_bytes(m, n, o.block > 0 ? o.block : k);
-  return ws + extra + (((size_t)m * n * elem_bytes(dtype) + 255) & ~(size_t)255);
 }
 
 }  // namespace
@@ -194,9 +211,13 @@ extern "C" int rlobpcg_server_create_ex(rlobpcg_server_t* out, size_t hbm_budget
   s->max_active = max_active;
   // every worker's stream exists before any worker starts: a server either has all its slots or
   // is not created
+  // batched mode: worker streams (set-ups, outputs) at the highest priority, above the engine's
+  int least = 0, greatest = 0;
+  cudaDeviceGetStreamPriorityRange(&least, &greatest);
+  const int prio = mode == RLOBPCG_SERVE_BATCHED ? greatest : 0;
   for (int i = 0; i < max_active; ++i) {
     cudaStream_t st = nullptr;
-    const cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    const cudaError_t e = cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, prio);
     if (e != cudaSuccess) {
       cudaGetLastError();
       set_last_error(cudaGetErrorString(e), __FILE__, __LINE__);
@@ -219,7 +240,8 @@ extern "C" int rlobpcg_server_submit(rlobpcg_server_t s, const void* A, int64_t 
   auto* r = new Request();
   if (opts) r->opts = *opts; else rlobpcg_default_opts(&r->opts);
   r->A = A; r->m = m; r->n = n; r->lda = lda; r->k = k; r->dtype = dtype;
-  r->bytes = request_bytes(m, n, k, dtype, r->opts, s->engine != nullptr);
+  r->engine = routed_to_engine(s, m, n, k, dtype, r->opts);
+  r->bytes = request_bytes(m, n, k, dtype, r->opts, r->engine);
   if (r->bytes == 0) {
     delete r;
     return RLOBPCG_ERR_INVALID_ARG;
@@ -305,6 +327,22 @@ extern "C" int rlobpcg_server_stats(rlobpcg_server_t s, int64_t* completed, doub
   }
   if (peak_bytes) *peak_bytes = s->peak;
   if (peak_running) *peak_running = s->peak_running;
+  return RLOBPCG_OK;
+}
+
+extern "C" int rlobpcg_server_set_batch_limit(rlobpcg_server_t s, int64_t max_mnb) {
+  if (!s || max_mnb < 0) return RLOBPCG_ERR_INVALID_ARG;
+  s->batch_limit = max_mnb;
+  return RLOBPCG_OK;
+}
+
+extern "C" int rlobpcg_server_engine_stats(rlobpcg_server_t s, rlobpcg_engine_stats* out) {
+  if (!s || !out) return RLOBPCG_ERR_INVALID_ARG;
+  if (!s->engine) {
+    *out = rlobpcg_engine_stats{};
+    return RLOBPCG_OK;
+  }
+  rl::batch_engine_stats(s->engine, out);
   return RLOBPCG_OK;
 }
 

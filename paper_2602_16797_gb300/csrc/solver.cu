@@ -10,6 +10,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <condition_variable>
 #include <deque>
 #include <limits>
@@ -977,7 +978,7 @@ int n_class(int n) {
 std::vector<TileChoice> tile_candidates(int nc, int b, size_t static_tile) {
   std::vector<TileChoice> out;
   for (int trows : {256, 512, 1024, 2048})
-    for (int rt : {16, 32}) {
+    for (int rt : {8, 16}) {
       const size_t sm = batch::tile_smem_bytes(nc * b, batch::abuf_need(nc, b, rt), rt);
       if (sm + static_tile <= max_smem_optin()) out.push_back({trows, rt});
     }
@@ -1197,13 +1198,18 @@ struct BatchEngine {
   batch::Desc* Dh = nullptr;   // pinned copy the graph writes back after every replay
   size_t Dh_cap = 0;
   int npre = 0, ntile = 0;
-  int nwmax = 1, abmax = 1, rtmax = 16;
+  int nwmax = 1, abmax = 1, rtmax = 8;
   size_t pre_smem = 0, tile_smem = 0;
   int pre_grid = 1, tile_grid = 1;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   bool dirty = true;
-  static constexpr int G = 4;   // iterations per graph replay
+  int stable = 0;               // replays since the last membership change
+  static constexpr int G = 4;   // iterations per replay
+  // telemetry (engine thread writes, readers take mu)
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  rlobpcg_engine_stats stats{};
+  double active_sum = 0;
 };
 
 namespace {
@@ -1277,9 +1283,9 @@ int engine_join(BatchEngine* e, BatchSolve* s) {
              : batch::widen_launch<double>((const double*)p->Rinv_r, nn, (double*)d.Ru, e->st));
   RL_TRY(f32 ? batch::widen_launch<float>((const float*)p->Rinv_c, nn, (double*)d.Rl, e->st)
              : batch::widen_launch<double>((const double*)p->Rinv_c, nn, (double*)d.Rl, e->st));
+  // (the host history row lives in the solve's run state until the solve is finished)
   RL_CUDA(cudaMemcpyAsync(d.hist, s->r.hist.r[0].data(), b * sizeof(double), cudaMemcpyHostToDevice, e->st));
   RL_CUDA(cudaMemsetAsync(d.cnt, 0, (size_t)(2 + ng) * 4, e->st));
-  RL_CUDA(cudaStreamSynchronize(e->st));   // the host history row is read before this returns
   return RLOBPCG_OK;
 }
 
@@ -1292,7 +1298,7 @@ int engine_rebuild(BatchEngine* e) {
   e->graph = nullptr;
   const int count = (int)e->active.size();
   std::vector<int2> hpre, htile;
-  e->nwmax = 1; e->abmax = 1; e->rtmax = 16; e->pre_smem = 0;
+  e->nwmax = 1; e->abmax = 1; e->rtmax = 8; e->pre_smem = 0;
   for (int i = 0; i < count; ++i) {
     const batch::Desc& d = e->active[i]->d;
     for (int rb = 0; rb < d.nrb; ++rb) hpre.push_back(make_int2(i, rb));
@@ -1349,31 +1355,52 @@ int engine_rebuild(BatchEngine* e) {
   RL_TRY(batch::prepare(e->pre_smem, e->tile_smem));
   int per_sm = 1;
   RL_TRY(batch::tile_blocks_per_sm(e->tile_smem, &per_sm));
-  e->pre_grid = std::max(1, std::min(e->npre, num_sms() * 2));
-  e->tile_grid = std::max(1, std::min(e->ntile, num_sms() * std::max(1, per_sm)));
+  // one CTA per work item (up to 64 waves): CTAs retire all through a launch, so that kernels of
+  // other streams (the set-ups of joining solves, at a higher stream priority) start in between
+  // instead of waiting for a persistent grid to drain
+  const int slots = num_sms() * std::max(1, per_sm);
+  e->pre_grid = std::max(1, std::min(e->npre, slots * 64));
+  e->tile_grid = std::max(1, std::min(e->ntile, slots * 64));
   RL_CUDA(cudaStreamSynchronize(e->st));   // the item vectors are host locals
-  // G iterations as one graph: reset the work queues, (R^{-H} Rs, R^{-1} Y + BCGS2, tiles) x G,
-  // then the descriptors back to the host
+  e->dirty = false;
+  e->stable = 0;
+  return RLOBPCG_OK;
+}
+
+// One replay: reset the work queues, (R^{-H} Rs, R^{-1} Y + BCGS2, tiles) x G, then the
+// descriptors back to the host. Issued directly on the stream, or captured once as a graph when
+// the membership has stayed the same for a replay (and relaunched while it stays so).
+int engine_issue(BatchEngine* e) {
   const int G = BatchEngine::G;
-  RL_CUDA(cudaStreamBeginCapture(e->st, cudaStreamCaptureModeThreadLocal));
-  int crc = cudaMemsetAsync(e->qh, 0, (3 * G + 2) * sizeof(int), e->st) == cudaSuccess ? RLOBPCG_OK : RLOBPCG_ERR_CUDA;
-  for (int g = 0; g < G && !crc; ++g) {
-    crc = batch::pre_launch(0, e->Dd, e->pre_items, e->npre, e->qh + 3 * g, e->pre_grid, e->pre_smem, e->st);
-    if (!crc) crc = batch::pre_launch(1, e->Dd, e->pre_items, e->npre, e->qh + 3 * g + 1, e->pre_grid, e->pre_smem, e->st);
-    if (!crc)
-      crc = batch::tile_launch(false, e->Dd, e->tile_items, e->ntile, e->qh + 3 * g + 2, e->tile_grid, e->nwmax, e->abmax,
-                               e->tile_smem, e->st);
+  const int count = (int)e->active.size();
+  int rc = cudaMemsetAsync(e->qh, 0, (3 * G + 2) * sizeof(int), e->st) == cudaSuccess ? RLOBPCG_OK : RLOBPCG_ERR_CUDA;
+  for (int g = 0; g < G && !rc; ++g) {
+    rc = batch::pre_launch(0, e->Dd, e->pre_items, e->npre, e->qh + 3 * g, e->pre_grid, e->pre_smem, e->st);
+    if (!rc) rc = batch::pre_launch(1, e->Dd, e->pre_items, e->npre, e->qh + 3 * g + 1, e->pre_grid, e->pre_smem, e->st);
+    if (!rc)
+      rc = batch::tile_launch(false, e->Dd, e->tile_items, e->ntile, e->qh + 3 * g + 2, e->tile_grid, e->nwmax, e->abmax,
+                              e->tile_smem, e->st);
   }
-  if (!crc && cudaMemcpyAsync(e->Dh, e->Dd, count * sizeof(batch::Desc), cudaMemcpyDeviceToHost, e->st) != cudaSuccess)
-    crc = RLOBPCG_ERR_CUDA;
+  if (!rc && cudaMemcpyAsync(e->Dh, e->Dd, count * sizeof(batch::Desc), cudaMemcpyDeviceToHost, e->st) != cudaSuccess)
+    rc = RLOBPCG_ERR_CUDA;
+  return rc;
+}
+
+int engine_replay(BatchEngine* e) {
+  if (e->gexec) return cudaGraphLaunch(e->gexec, e->st) == cudaSuccess ? RLOBPCG_OK : RLOBPCG_ERR_CUDA;
+  if (e->stable < 1) {
+    ++e->stable;
+    return engine_issue(e);
+  }
+  RL_CUDA(cudaStreamBeginCapture(e->st, cudaStreamCaptureModeThreadLocal));
+  const int crc = engine_issue(e);
   const cudaError_t ce = cudaStreamEndCapture(e->st, &e->graph);
   if (crc || ce != cudaSuccess) {
     cudaGetLastError();
     return crc ? crc : RLOBPCG_ERR_CUDA;
   }
   RL_CUDA(cudaGraphInstantiate(&e->gexec, e->graph, 0));
-  e->dirty = false;
-  return RLOBPCG_OK;
+  return cudaGraphLaunch(e->gexec, e->st) == cudaSuccess ? RLOBPCG_OK : RLOBPCG_ERR_CUDA;
 }
 
 // solves that stopped: A V and A X brought up to date, the state handed back, buffers released
@@ -1388,13 +1415,18 @@ int engine_retire(BatchEngine* e, const std::vector<int>& idx) {
   RL_TRY(batch::tile_launch(true, e->Dd, ditems, (int)items.size(), e->qh + 3 * BatchEngine::G, e->tile_grid, e->nwmax,
                             e->abmax, e->tile_smem, e->st));
   RL_CUDA(cudaFreeAsync(ditems, e->st));
-  for (int i : idx) {
-    BatchSolve* s = e->active[i];
+  std::vector<std::vector<double>> hs(idx.size());
+  for (size_t q = 0; q < idx.size(); ++q) {
+    const batch::Desc& d = e->active[idx[q]]->d;
+    hs[q].resize((size_t)(d.iter + 1) * 2 * d.b);
+    RL_CUDA(cudaMemcpyAsync(hs[q].data(), d.hist, hs[q].size() * sizeof(double), cudaMemcpyDeviceToHost, e->st));
+  }
+  RL_CUDA(cudaStreamSynchronize(e->st));
+  for (size_t q = 0; q < idx.size(); ++q) {
+    BatchSolve* s = e->active[idx[q]];
     const batch::Desc& d = s->d;
     const int b = d.b;
-    std::vector<double> h((size_t)(d.iter + 1) * 2 * b);
-    RL_CUDA(cudaMemcpyAsync(h.data(), d.hist, h.size() * sizeof(double), cudaMemcpyDeviceToHost, e->st));
-    RL_CUDA(cudaStreamSynchronize(e->st));
+    const std::vector<double>& h = hs[q];
     for (int t = 1; t <= d.iter; ++t) {
       s->r.hist.r.emplace_back(h.begin() + (size_t)t * 2 * b, h.begin() + (size_t)t * 2 * b + b);
       s->r.hist.th.emplace_back(h.begin() + (size_t)t * 2 * b + b, h.begin() + (size_t)(t + 1) * 2 * b);
@@ -1423,6 +1455,12 @@ void engine_fail_all(BatchEngine* e, int rc) {
 
 void engine_main(BatchEngine* e) {
   cudaSetDevice(e->device);
+  using clk = std::chrono::steady_clock;
+  auto t_host = clk::now();
+  auto host_add = [&](clk::time_point a, clk::time_point b) {
+    std::lock_guard<std::mutex> lk(e->mu);
+    e->stats.host_ms += std::chrono::duration<double, std::milli>(b - a).count();
+  };
   for (;;) {
     std::vector<BatchSolve*> joining;
     {
@@ -1432,6 +1470,7 @@ void engine_main(BatchEngine* e) {
       joining.assign(e->incoming.begin(), e->incoming.end());
       e->incoming.clear();
     }
+    t_host = clk::now();
     for (BatchSolve* s : joining) {
       const int rc = engine_join(e, s);
       if (rc) {
@@ -1444,9 +1483,25 @@ void engine_main(BatchEngine* e) {
       }
     }
     if (e->active.empty()) continue;
+    const bool rebuilt = e->dirty;
     int rc = e->dirty ? engine_rebuild(e) : RLOBPCG_OK;
-    if (!rc && cudaGraphLaunch(e->gexec, e->st) != cudaSuccess) rc = RLOBPCG_ERR_CUDA;
+    host_add(t_host, clk::now());
+    if (!rc && cudaEventRecord(e->ev0, e->st) != cudaSuccess) rc = RLOBPCG_ERR_CUDA;
+    if (!rc) rc = engine_replay(e);
+    if (!rc && cudaEventRecord(e->ev1, e->st) != cudaSuccess) rc = RLOBPCG_ERR_CUDA;
     if (!rc && cudaStreamSynchronize(e->st) != cudaSuccess) rc = RLOBPCG_ERR_CUDA;
+    t_host = clk::now();
+    if (!rc) {
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e->ev0, e->ev1);
+      std::lock_guard<std::mutex> lk(e->mu);
+      e->stats.replays += 1;
+      e->stats.rebuilds += rebuilt ? 1 : 0;
+      e->stats.joins += (int64_t)joining.size();
+      e->stats.gpu_ms += ms;
+      e->active_sum += (double)e->active.size();
+      e->stats.active_mean = e->active_sum / (double)e->stats.replays;
+    }
     if (rc) {
       cudaGetLastError();
       engine_fail_all(e, rc);
@@ -1457,7 +1512,10 @@ void engine_main(BatchEngine* e) {
       e->active[i]->d = e->Dh[i];
       if (e->Dh[i].done) done.push_back((int)i);
     }
-    if (done.empty()) continue;
+    if (done.empty()) {
+      host_add(t_host, clk::now());
+      continue;
+    }
     rc = engine_retire(e, done);
     if (rc) {
       cudaGetLastError();
@@ -1476,6 +1534,11 @@ void engine_main(BatchEngine* e) {
     }
     e->active.swap(keep);
     e->dirty = true;
+    {
+      std::lock_guard<std::mutex> lk(e->mu);
+      e->stats.retires += (int64_t)done.size();
+    }
+    host_add(t_host, clk::now());
   }
 }
 
@@ -1484,14 +1547,28 @@ void engine_main(BatchEngine* e) {
 int batch_engine_create(int device, BatchEngine** out) {
   auto* e = new BatchEngine();
   e->device = device;
-  if (cudaStreamCreateWithFlags(&e->st, cudaStreamNonBlocking) != cudaSuccess) {
+  // the lowest stream priority: set-ups and outputs of other solves run first when both wait
+  int least = 0, greatest = 0;
+  cudaDeviceGetStreamPriorityRange(&least, &greatest);
+  if (cudaStreamCreateWithPriority(&e->st, cudaStreamNonBlocking, least) != cudaSuccess) {
     cudaGetLastError();
+    delete e;
+    return RLOBPCG_ERR_CUDA;
+  }
+  if (cudaEventCreate(&e->ev0) != cudaSuccess || cudaEventCreate(&e->ev1) != cudaSuccess) {
+    cudaGetLastError();
+    cudaStreamDestroy(e->st);
     delete e;
     return RLOBPCG_ERR_CUDA;
   }
   e->th = std::thread(engine_main, e);
   *out = e;
   return RLOBPCG_OK;
+}
+
+void batch_engine_stats(BatchEngine* e, rlobpcg_engine_stats* out) {
+  std::lock_guard<std::mutex> lk(e->mu);
+  *out = e->stats;
 }
 
 void batch_engine_destroy(BatchEngine* e) {
@@ -1507,6 +1584,8 @@ void batch_engine_destroy(BatchEngine* e) {
   if (e->dmem) cudaFreeAsync(e->dmem, e->st);
   cudaStreamSynchronize(e->st);
   if (e->Dh) cudaFreeHost(e->Dh);
+  if (e->ev0) cudaEventDestroy(e->ev0);
+  if (e->ev1) cudaEventDestroy(e->ev1);
   cudaStreamDestroy(e->st);
   delete e;
 }

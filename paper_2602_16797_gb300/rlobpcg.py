@@ -56,6 +56,11 @@ class rlobpcg_info(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class rlobpcg_engine_stats(ctypes.Structure):
+    _fields_ = [("replays", c_int64), ("joins", c_int64), ("retires", c_int64), ("rebuilds", c_int64),
+                ("gpu_ms", c_double), ("host_ms", c_double), ("active_mean", c_double)]
+
+
 class RlobpcgError(RuntimeError):
     def __init__(self, fn, code):
         self.code = code
@@ -93,6 +98,8 @@ _SIGS = {
     "rlobpcg_plan_workspace_size": (c_size_t, [c_int64, c_int64, c_int, c_int, ctypes.POINTER(rlobpcg_opts)]),
     "rlobpcg_server_create": (c_int, [ctypes.POINTER(c_void_p), c_size_t, c_int, c_int]),
     "rlobpcg_server_create_ex": (c_int, [ctypes.POINTER(c_void_p), c_size_t, c_int, c_int, c_int]),
+    "rlobpcg_server_engine_stats": (c_int, [c_void_p, ctypes.POINTER(rlobpcg_engine_stats)]),
+    "rlobpcg_server_set_batch_limit": (c_int, [c_void_p, c_int64]),
     "rlobpcg_server_submit": (c_int, [c_void_p, c_void_p, c_int64, c_int64, c_int64, c_int, c_int,
                                       ctypes.POINTER(rlobpcg_opts), ctypes.POINTER(c_int64)]),
     "rlobpcg_server_poll": (c_int, [c_void_p, c_int64]),
@@ -372,3 +379,13 @@ def rlobpcg_batch_tile(n: int, b: int, stream: int | None = None):
 
 def rlobpcg_batch_set_tile(n: int, b: int, trows: int, rt: int) -> None:
     _check("rlobpcg_batch_set_tile", load().rlobpcg_batch_set_tile(n, b, trows, rt))
+
+
+def rlobpcg_server_engine_stats(server: int) -> dict:
+    st = rlobpcg_engine_stats()
+    _check("rlobpcg_server_engine_stats", load().rlobpcg_server_engine_stats(server, ctypes.byref(st)))
+    return {f: getattr(st, f) for f, _ in rlobpcg_engine_stats._fields_}
+
+
+def rlobpcg_server_set_batch_limit(server: int, max_mnb: int) -> None:
+    _check("rlobpcg_server_set_batch_limit", load().rlobpcg_server_set_batch_limit(server, max_mnb))

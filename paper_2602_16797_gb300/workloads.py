@@ -186,6 +186,57 @@ def serve_request(r: int):
     return A, k, "planted"
 
 
+def serve_shape(r: int):
+    """(m, n, k, kind) of request r of the serving stream (the draws of serve_request)."""
+    rng = np.random.default_rng(SERVE_SEED_BASE + r)
+    m = int(round(np.exp(rng.uniform(np.log(2e3), np.log(5e5)))))
+    n = int(rng.integers(20, 401))
+    k = int(rng.choice([1, 2, 4]))
+    return max(m, 4 * n), n, k, ("loewner" if r % 2 == 0 else "planted")
+
+
+def loewner_on_device(seed: int, m: int, n: int, device="cuda"):
+    """The Loewner matrix of `loewner` built with torch on a GPU (x_i drawn on the host with the same
+    seeded generator, so the matrix equals loewner(seed, m, n) up to rounding of f)."""
+    import torch
+    rng = np.random.default_rng(seed)
+    z = np.cos(np.pi * np.arange(n) / (n - 1))
+    x = rng.uniform(-1.0, 1.0, m)
+    for _ in range(100):
+        bad = np.min(np.abs(x[:, None] - z[None, :]), axis=1) < 1e-12
+        if not bad.any():
+            break
+        x[bad] = rng.uniform(-1.0, 1.0, int(bad.sum()))
+    xd = torch.from_numpy(x).to(device)
+    zd = torch.from_numpy(z).to(device)
+    f = lambda t: torch.exp(t) / (1.0 + 25.0 * t * t)  # noqa: E731
+    return ((f(xd)[:, None] - f(zd)[None, :]) / (xd[:, None] - zd[None, :])).contiguous()
+
+
+def serve_pool(size: int, device="cuda"):
+    """A pool of `size` matrices with the serving stream's shapes (entry j has request j's m, n, k
+    and kind), built on a GPU and held in pinned host memory. The serving benchmark draws its
+    requests from this pool, each request with its own sketch seed: the stream keeps the shape
+    distribution (m log-uniform in [2e3, 5e5], n uniform in [20, 400], k in {1, 2, 4}, half
+    Loewner, half planted) while the host holds `size` matrices instead of one per request.
+    Returns a list of (A host tensor, k, kind)."""
+    import torch
+    out = []
+    for j in range(size):
+        m, n, k, kind = serve_shape(j)
+        if kind == "loewner":
+            Ad = loewner_on_device(SERVE_SEED_BASE + j, m, n, device)
+        else:
+            sigma = np.concatenate([np.logspace(0, -6, n - k), np.logspace(-9, -10, k)])
+            Ad = planted_on_device(SERVE_SEED_BASE + j, m, sigma, device)[0]
+        Ah = torch.empty(Ad.shape, dtype=Ad.dtype, pin_memory=True)
+        Ah.copy_(Ad)
+        del Ad
+        out.append((Ah, k, kind))
+    torch.cuda.synchronize()
+    return out
+
+
 def planted_on_device(seed: int, m: int, sigma: np.ndarray, device="cuda", complex_: bool = False):
     """A = U diag(sigma) V^H built on a GPU with torch (for sizes where a host QR of the m x n
     Gaussian takes minutes, e.g. 1e6 x 1000). U: Q of a seeded Gaussian (Philox stream of
