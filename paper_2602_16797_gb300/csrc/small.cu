@@ -54,22 +54,34 @@ __device__ inline void householder_scalars(T alpha, double xnorm2, T* tau, T* be
 // ------------------------------------------------------------------------------------------
 // TSQR level: CTA i reduces rows [i*rpc, min((i+1)*rpc, rows)) of X (row-major, ldx, c cols)
 // to a c x c upper-triangular R by Householder steps on [R_running; next chunk of CH rows].
-// Q is never formed. Thread (column cc, row phase p) with cc = tid / RP, p = tid % RP: the RP
-// lanes of a column are contiguous, so the column sums are shuffle trees. Per column j:
+// Q is never formed. For column j the a = c - j active columns (cc = j .. c-1) each get L lanes,
+// L the largest power of two with a L <= 256 (at most 32): as the active columns shrink, the lanes
+// per column grow, so the threads issuing FP64 instructions stay contiguous and nearly all lanes
+// of an issuing warp do useful work (an FP64 warp instruction costs its sub-partition the same
+// issue slot whatever the number of active lanes). Thread (q, p) = (tid / L, tid % L) takes
+// column cc = j + q and rows r = j+1+p, j+1+p+L, ...; the L lanes of a column are contiguous,
+// so its sums are shuffle trees. Per column j:
 //   d_cc = sum_{r > j} conj(S[r][j]) S[r][cc]   (cc = j gives ||x(1:)||^2)
 //   reflector scalars from alpha = S[j][j] and d_j (one thread), then for cc > j
 //   s = S[j][cc] + conj(1/(alpha - beta)) d_cc,  f = conj(tau) s,
 //   S[j][cc] -= f,  S[r][cc] -= S[r][j] (f / (alpha - beta))  for r > j.
+// Rows of the running R below the diagonal of column j are zero and are skipped.
 // ------------------------------------------------------------------------------------------
+__device__ inline int lanes_for(int a) {
+  int L = 32;
+  while (L > 1 && a * L > 256) L >>= 1;
+  return L;
+}
+
 template <class T>
 __global__ void __launch_bounds__(256) tsqr_level_kernel(const T* __restrict__ X, int64_t rows, int c, int64_t ldx,
                                                           int64_t rpc, int CH, int RP, T* __restrict__ Rout) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int NT = blockDim.x;
-  const int tid = threadIdx.x, cc = tid / RP, p = tid % RP;
-  const int SR = c + CH;                       // stacked rows
-  T* S = reinterpret_cast<T*>(smem_raw);       // SR x c row-major
+  const int tid = threadIdx.x;
+  T* S = reinterpret_cast<T*>(smem_raw);       // (c + CH) x c row-major
   __shared__ T sh_tau, sh_inv, sh_beta;
+  (void)RP;
 
   const int64_t r_begin = (int64_t)blockIdx.x * rpc;
   const int64_t r_end = imin<int64_t>(rows, r_begin + rpc);
@@ -88,35 +100,41 @@ __global__ void __launch_bounds__(256) tsqr_level_kernel(const T* __restrict__ X
     __syncthreads();
     const int SRu = c + imax(nr, 1);            // rows that can be nonzero
     for (int j = 0; j < c; ++j) {
+      const int a = c - j, L = lanes_for(a);
+      const int q = tid / L, p = tid % L;
+      const int cc = j + q;
+      const bool on = q < a;
+      // rows of column j that can be nonzero: row j of R (the pivot), then the chunk (rows c..)
+      const int rs = c;                         // first chunk row (R rows j+1..c-1 are zero in column j)
       T d = zero_<T>();
-      if (cc < c && cc >= j) {
+      if (on) {
         T a0 = zero_<T>(), a1 = zero_<T>(), a2 = zero_<T>(), a3 = zero_<T>();
-        int r = j + 1 + p;
-        for (; r + 3 * RP < SRu; r += 4 * RP) {
+        int r = rs + p;
+        for (; r + 3 * L < SRu; r += 4 * L) {
           a0 = madc_(S[(size_t)r * c + j], S[(size_t)r * c + cc], a0);
-          a1 = madc_(S[(size_t)(r + RP) * c + j], S[(size_t)(r + RP) * c + cc], a1);
-          a2 = madc_(S[(size_t)(r + 2 * RP) * c + j], S[(size_t)(r + 2 * RP) * c + cc], a2);
-          a3 = madc_(S[(size_t)(r + 3 * RP) * c + j], S[(size_t)(r + 3 * RP) * c + cc], a3);
+          a1 = madc_(S[(size_t)(r + L) * c + j], S[(size_t)(r + L) * c + cc], a1);
+          a2 = madc_(S[(size_t)(r + 2 * L) * c + j], S[(size_t)(r + 2 * L) * c + cc], a2);
+          a3 = madc_(S[(size_t)(r + 3 * L) * c + j], S[(size_t)(r + 3 * L) * c + cc], a3);
         }
-        for (; r < SRu; r += RP) a0 = madc_(S[(size_t)r * c + j], S[(size_t)r * c + cc], a0);
+        for (; r < SRu; r += L) a0 = madc_(S[(size_t)r * c + j], S[(size_t)r * c + cc], a0);
         d = add_(add_(a0, a1), add_(a2, a3));
       }
-      for (int o = RP >> 1; o > 0; o >>= 1) d = add_(d, shfl_xor_(d, o));
-      if (cc == j && p == 0) {
+      for (int o = L >> 1; o > 0; o >>= 1) d = add_(d, shfl_xor_(d, o));
+      if (q == 0 && p == 0) {
         T tau, beta, inv_ab;
         householder_scalars(S[(size_t)j * c + j], re_(d), &tau, &beta, &inv_ab);
         sh_tau = tau; sh_inv = inv_ab; sh_beta = beta;
       }
       __syncthreads();
-      if (cc < c && cc > j) {
+      if (on && q > 0) {
         const T inv_ab = sh_inv;
         const T f = mul_(conj_(sh_tau), add_(S[(size_t)j * c + cc], mul_(conj_(inv_ab), d)));
         const T fv = mul_(inv_ab, f);            // v_r = S[r][j] / (alpha - beta) folded into f
         if (p == 0) S[(size_t)j * c + cc] = sub_(S[(size_t)j * c + cc], f);
-        for (int r = j + 1 + p; r < SRu; r += RP)
+        for (int r = rs + p; r < SRu; r += L)
           S[(size_t)r * c + cc] = sub_(S[(size_t)r * c + cc], mul_(S[(size_t)r * c + j], fv));
       }
-      if (cc == j && p == 0) S[(size_t)j * c + j] = sh_beta;
+      if (q == 0 && p == 0) S[(size_t)j * c + j] = sh_beta;
       __syncthreads();
     }
     if (r_end <= r_begin) break;
@@ -1747,8 +1765,8 @@ __global__ void nonfinite_scan_kernel(const T* A, int64_t m, int n, int64_t lda,
 // host launchers
 // ------------------------------------------------------------------------------------------
 static int tsqr_chunk(int c, size_t esz) {
-  int ch = (int)(64 * 1024 / ((size_t)c * esz)) - c;   // ~64 KB of smem: 3 CTAs per SM
-  ch = imax(32, imin(256, ch));
+  int ch = (int)(100 * 1024 / ((size_t)c * esz)) - c;   // ~100 KB of smem: 2 CTAs per SM
+  ch = imax(32, imin(512, ch));
   return ch;
 }
 
@@ -1758,11 +1776,11 @@ static int tsqr_rp(int c) { return imin(32, 256 / pow2_at_least(c)); }
 
 static size_t tsqr_level_smem(int c, int CH, size_t esz) { return (size_t)(c + CH) * c * esz; }
 
-// Level 1: up to three CTAs per SM (one chunk each when m allows): the level is bound by FP64
-// issue (about 2 m c^2 FMAs), so all SMs' FP64 pipes take part.
+// Level 1: up to two CTAs per SM (one chunk each when m allows): the level is bound by FP64
+// issue (about m c^2 FMAs), so all SMs' FP64 pipes take part.
 static int64_t tsqr_level1_ctas(int64_t m, int c, size_t esz) {
   const int CH = tsqr_chunk(c, esz);
-  return imin<int64_t>(3 * (int64_t)num_sms(), imax<int64_t>(1, (m + CH - 1) / CH));
+  return imin<int64_t>(2 * (int64_t)num_sms(), imax<int64_t>(1, (m + CH - 1) / CH));
 }
 
 static constexpr int kTsqrFan = 20;   // R factors merged per CTA in the upper levels

@@ -133,8 +133,10 @@ def test_one_waiter_per_ticket():
 
 
 def _batch_alone(A, k, opts):
-    """rlobpcg_solve_batch with this request alone (the reference for the batched server)."""
+    """rlobpcg_solve_batch with this request alone (the reference for the batched server, which
+    plans a request it hands to the batch engine without a split of A: gram_split = 0)."""
     m, n = A.shape
+    opts.gram_split = 0
     st = torch.cuda.current_stream().cuda_stream
     Ad = torch.from_numpy(A).cuda()
     plan = rl.rlobpcg_plan(m, n, k, rl.RLOBPCG_F64, opts, st)
@@ -150,12 +152,21 @@ def _batch_alone(A, k, opts):
 
 
 def test_batched_server_results_equal_the_batch_alone_and_budget_holds():
-    """Batched serving: the iterations of every admitted small solve run together in the batch
-    engine, solves joining and leaving between replays; each result is bit-identical to
-    rlobpcg_solve_batch of that request alone. A complex request in the mix (not batchable) runs
-    whole on its worker and equals rlobpcg_solve."""
+    """Batched serving: the iterations of every admitted small solve (m n b <= 2^23) run together
+    in the batch engine, solves joining and leaving between replays, and each such result is
+    bit-identical to rlobpcg_solve_batch of that request alone; larger requests and a complex one
+    (not batchable) run whole on their worker and equal rlobpcg_solve."""
     reqs = _requests(12)
-    alone = [_batch_alone(A, k, _opts(seed)) for A, k, seed in reqs]
+    limit = 1 << 23                                # rlobpcg_server_set_batch_limit's default
+    routed = [A.shape[0] * A.shape[1] * k <= limit for A, k, _ in reqs]
+    assert any(routed) and not all(routed)         # both paths are exercised
+    alone = []
+    for (A, k, seed), eng in zip(reqs, routed):
+        if eng:
+            alone.append(_batch_alone(A, k, _opts(seed)))
+        else:                                      # larger requests run whole, as rlobpcg_solve
+            sig, V, _, _, info = rl.solve(torch.from_numpy(A).cuda(), k, opts=_opts(seed))
+            alone.append((sig.cpu().numpy(), V.cpu().numpy(), info["iters"]))
     rng = np.random.default_rng(77)
     Ac = wl.planted(rng, 6000, np.concatenate([np.logspace(0, -6, 37), np.logspace(-9, -10, 3)]), complex_=True)[0]
     Ac = np.ascontiguousarray(Ac)
