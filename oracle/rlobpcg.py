@@ -282,7 +282,8 @@ def rlobpcg(A: np.ndarray, k: int, b: int | None = None, d: int | None = None, z
             seed: int = 0, tau: float | None = None, max_iter: int | None = None,
             check_every: int | None = None, use_stagnation: bool = True,
             sketch_precision: str = "f64", fixed_iters: int | None = None,
-            keep_iterates: bool = False, orth_mode: str = "householder", locking: bool = False) -> dict:
+            keep_iterates: bool = False, orth_mode: str = "householder", locking: bool = False,
+            precond: str = "sketch") -> dict:
     """Block RLOBPCG (Alg. 2) for the k smallest singular triplets of a tall A (m x n).
 
     b is the block size (default k), d the sketch rows (default 4n), zeta the SparseStack
@@ -293,6 +294,10 @@ def rlobpcg(A: np.ndarray, k: int, b: int | None = None, d: int | None = None, z
     with its value frozen, while X and W lose its column, W is made orthogonal to all of V, and
     Rayleigh-Ritz runs on the active columns only, so the trial space stays orthogonal to the
     converged vectors; the solve also ends when every column is locked.
+    precond: the P of W = P (P^* R): "sketch" (P = V~ Sigma~^{-1}, Alg. 2), "diag"
+    (P = diag(||A(:, i)||^{-1}), the diagonally preconditioned LOBPCG of Sec. 1.1) or "none"
+    (P = I, LOBPCG without a preconditioner, Sec. 1.1); every variant starts from the same
+    sketch-and-solve block and stops by the same rule (Sec. 1.1 starts all methods from v0).
     Returns a dict with sigma (k, ascending), V (n x k), U = A V diag(sigma)^{-1} (m x k),
     resid (k residual column norms), iters, stop_reason, sigma11 (= Sigma~(1,1)) and the
     per-iteration history of the b estimates and residual norms.
@@ -324,7 +329,14 @@ def rlobpcg(A: np.ndarray, k: int, b: int | None = None, d: int | None = None, z
     s = s.astype(np.float64)
     Vt = Vt.astype(wt)
     sigma11 = float(s[0])
-    P = Vt / s[None, :]
+    if precond == "sketch":
+        P = Vt / s[None, :]
+    elif precond == "diag":
+        P = np.diag(1.0 / np.linalg.norm(A, axis=0)).astype(wt)
+    elif precond == "none":
+        P = np.eye(n, dtype=wt)
+    else:
+        raise ValueError(f"unknown precond {precond!r}")
 
     # Sketch-and-solve start and the initial Rayleigh-Ritz step (Alg. 2)
     V = orth(Vt[:, n - b:])

@@ -139,3 +139,25 @@ def test_svqb_without_the_eigen_scaling_is_caught(monkeypatch):
         return W * D[None, :]                             # column scaling only
     _patch(monkeypatch, "svqb", bad)
     _expect_failure(lambda: pins.test_svqb_orthonormalises_and_keeps_the_span(False))
+
+
+def test_no_preconditioner_that_is_diagonal_is_caught(monkeypatch):
+    orig = oracle.rlobpcg
+
+    def bad(*a, **kw):
+        if kw.get("precond") == "none":
+            kw["precond"] = "diag"
+        return orig(*a, **kw)
+    monkeypatch.setattr(oracle, "rlobpcg", bad)
+    _expect_failure(pins.test_no_preconditioner_is_rotation_covariant)
+
+
+def test_diagonal_preconditioner_that_is_none_is_caught(monkeypatch):
+    orig = oracle.rlobpcg
+
+    def bad(*a, **kw):
+        if kw.get("precond") == "diag":
+            kw["precond"] = "none"
+        return orig(*a, **kw)
+    monkeypatch.setattr(oracle, "rlobpcg", bad)
+    _expect_failure(pins.test_diagonal_preconditioner_is_exact_for_orthogonal_columns)

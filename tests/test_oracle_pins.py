@@ -505,3 +505,52 @@ def test_locking_off_is_the_plain_method():
     a = oracle.rlobpcg(A, k=2, seed=3, fixed_iters=6)
     b = oracle.rlobpcg(A, k=2, seed=3, fixed_iters=6, locking=False, orth_mode="householder")
     assert np.array_equal(a["sigma"], b["sigma"]) and a["matvecs"] == 2 * 7
+
+
+# ---------------------------------------------------------------------------------------------
+# Preconditioner variants of Sec. 1.1 (diagonal, none) beside the randomized one
+# ---------------------------------------------------------------------------------------------
+
+def _small_planted(seed, m=3000, n=30, V=None, sigma=None):
+    rng = np.random.default_rng(seed)
+    sigma = np.concatenate([np.geomspace(1.0, 1e-3, n - 1), [1e-6]]) if sigma is None else sigma
+    return wl.planted(rng, m, sigma, V=V)
+
+
+def test_no_preconditioner_is_rotation_covariant():
+    """LOBPCG without a preconditioner (P = I) and the sketch-and-solve start are covariant under
+    A -> A Q for an orthogonal Q (S A Q = (S A) Q), so the Ritz values of every iteration are the
+    same for A and A Q; a diagonal P is not (it depends on the columns' basis)."""
+    A, s, V = _small_planted(61)
+    Q = wl.haar_orthonormal(np.random.default_rng(62), A.shape[1], A.shape[1])
+    r1 = oracle.rlobpcg(A, k=2, seed=5, fixed_iters=5, precond="none")
+    r2 = oracle.rlobpcg(A @ Q, k=2, seed=5, fixed_iters=5, precond="none")
+    np.testing.assert_allclose(r2["theta_hist"][1:], r1["theta_hist"][1:], rtol=1e-6)
+    d1 = oracle.rlobpcg(A, k=2, seed=5, fixed_iters=5, precond="diag")
+    d2 = oracle.rlobpcg(A @ Q, k=2, seed=5, fixed_iters=5, precond="diag")
+    assert not np.allclose(d2["theta_hist"][1:], d1["theta_hist"][1:], rtol=1e-3)
+
+
+def test_diagonal_preconditioner_equals_none_for_equal_column_norms():
+    """P = diag(||A(:, i)||^{-1}) is a multiple of I when every column has the same norm; W is then
+    a multiple of R, the trial space is the same, and so are the Ritz values."""
+    A, s, V = _small_planted(63)
+    A = A / np.linalg.norm(A, axis=0)[None, :] * 0.37
+    r1 = oracle.rlobpcg(A, k=1, seed=5, fixed_iters=6, precond="none")
+    r2 = oracle.rlobpcg(A, k=1, seed=5, fixed_iters=6, precond="diag")
+    np.testing.assert_allclose(r2["theta_hist"][1:], r1["theta_hist"][1:], rtol=1e-9)
+
+
+def test_diagonal_preconditioner_is_exact_for_orthogonal_columns():
+    """For A = U diag(sigma) (orthogonal columns, coherent V = I) the diagonal P P^* equals
+    (A^* A)^{-1}: each step is an inverse-iteration step, so the diagonally preconditioned method
+    is far ahead of the unpreconditioned one after two iterations (Sec. 1.1's easy problem is the
+    coherent case where a diagonal preconditioner works)."""
+    n = 30
+    sigma = np.concatenate([np.geomspace(1.0, 0.1, n - 1), [1e-7]])
+    A, s, V = _small_planted(64, n=n, V=np.eye(n), sigma=sigma)
+    rd = oracle.rlobpcg(A, k=1, seed=5, fixed_iters=2, precond="diag")
+    rn = oracle.rlobpcg(A, k=1, seed=5, fixed_iters=2, precond="none")
+    ed = abs(rd["sigma"][0] - 1e-7) / 1e-7
+    en = abs(rn["sigma"][0] - 1e-7) / 1e-7
+    assert ed < 1e-6 and ed < 1e-3 * en, (ed, en)
