@@ -740,6 +740,69 @@ def run_serve(args, rank, world, local_rank):
                     "d2h_bytes_per_step": None}}
 
 
+def run_fig1(args, rank, world, local_rank):
+    """Sec. 1.1's comparison (Fig. 1) on the GPU: the easy and hard m x n problems (default
+    2e6 x 4e3, 64 GB FP64 each), the smallest singular triplet (b = k = 1) by RLOBPCG and by the
+    same LOBPCG with the diagonal preconditioner and with none, all from the sketch-and-solve
+    start v0 and with the paper's iteration cap (200 for b = 1). Reported per method: the relative
+    error (theta_t - sigma_n) / sigma_n of the estimate after every iteration (theta_t = ||A v_t||
+    for the Ritz vector), the one-time and per-iteration device times, and the time to reach the
+    best error RLOBPCG reaches."""
+    import torch
+
+    from paper_2602_16797_gb300 import rlobpcg as rl
+    from paper_2602_16797_gb300 import workloads as wl
+    if rank != 0:
+        return None
+    torch.cuda.set_device(local_rank)
+    rl.load()
+    m, n = args.fig1_m, args.fig1_n
+    variants = [("rlobpcg", rl.RLOBPCG_PRECOND_SKETCH), ("lobpcg_diag", rl.RLOBPCG_PRECOND_DIAG),
+                ("lobpcg_none", rl.RLOBPCG_PRECOND_NONE)]
+    out = {}
+    t_gen = time.perf_counter()
+    for kind, A, sigma in wl.fig1_device(m, n):
+        torch.cuda.synchronize()
+        gen_s = time.perf_counter() - t_gen
+        sn = float(sigma[-1])
+        res = {"sigma_n": sn, "generation_s": gen_s}
+        for name, pc in variants:
+            o = rl.rlobpcg_default_opts()
+            o.seed = 7
+            o.block = 1
+            o.precond = pc
+            o.gram_split = 0   # FP64 Gram: A (64 GB) and the solve fit beside the generator's U
+            st = torch.cuda.current_stream().cuda_stream
+            plan = rl.rlobpcg_plan(m, n, 1, rl.RLOBPCG_F64, o, st)
+            sig = torch.empty(1, dtype=torch.float64, device="cuda")
+            V = torch.empty((n, 1), dtype=torch.float64, device="cuda")
+            info = rl.rlobpcg_info()
+            try:
+                rc = rl.rlobpcg_solve(plan, A.data_ptr(), n, -1.0, sig.data_ptr(), V.data_ptr(), None, None, info)
+                th, rs = rl.rlobpcg_history(plan)
+            finally:
+                rl.rlobpcg_plan_destroy(plan)
+            err = (th[:, -1] - sn) / sn
+            per_it = info.ms_iterate / max(1, info.iters)
+            setup = info.ms_sketch + info.ms_factor
+            res[name] = {"status": rc, "iters": info.iters, "stop_reason": info.stop_reason,
+                         "setup_ms": setup, "ms_per_iteration": per_it, "ms_total": info.ms_total,
+                         "rel_err_v0": float(err[0]), "rel_err_final": float(err[-1]),
+                         "rel_err_every_10": [float(x) for x in err[::10]]}
+        best = res["rlobpcg"]["rel_err_final"]
+        for name, _ in variants:
+            r = res[name]
+            errs = r["rel_err_every_10"]
+            hit = next((i * 10 for i, e in enumerate(errs) if e <= max(best, 0) * 1.0001 + 1e-300), None)
+            r["ms_to_rlobpcg_best"] = (r["setup_ms"] + hit * r["ms_per_iteration"]) if hit is not None else None
+        out[kind] = res
+        t_gen = time.perf_counter()
+    return {"metric": "Fig. 1 (Sec. 1.1): relative error of the smallest singular value vs time", "unit": "ms",
+            "config": {"workload": f"Sec. 1.1 easy and hard problems, m={m} n={n}, b=k=1, FP64 Gram",
+                       "data": "synthetic (Haar U from a GPU QR; the paper's V and sigma recipes)"},
+            "results": out}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -747,7 +810,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["serve_stream", "block_study"], default=DEFAULT_WORKLOAD)
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["serve_stream", "block_study", "fig1"],
+                    default=DEFAULT_WORKLOAD)
+    ap.add_argument("--fig1-m", type=int, default=2_000_000, help="fig1: rows")
+    ap.add_argument("--fig1-n", type=int, default=4000, help="fig1: columns")
     ap.add_argument("--blocks", default="1,3,5,10,20", help="block_study: block sizes")
     ap.add_argument("--study-m", type=int, default=1_000_000, help="block_study: rows")
     ap.add_argument("--study-n", type=int, default=2000, help="block_study: columns")
@@ -774,6 +840,8 @@ def main():
         out = run_serve(args, rank, world, local_rank)
     elif args.workload == "block_study":
         out = run_block_study(args, rank, world, local_rank)
+    elif args.workload == "fig1":
+        out = run_fig1(args, rank, world, local_rank)
     else:
         out = run_ours(args, rank, world, local_rank)
     replicas.finish(world)

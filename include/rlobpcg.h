@@ -98,7 +98,18 @@ typedef struct {
                            runs on the active columns; the solve also ends when all are locked.
                            The host reads the residual norms after every iteration to decide (one
                            stream synchronisation per iteration instead of per stop check).      */
+  int precond;          /* P of W = P (P^* R): RLOBPCG_PRECOND_SKETCH (default; Alg. 2,
+                           P P^* = (R^H R)^{-1} from the sketch), RLOBPCG_PRECOND_DIAG
+                           (P = diag(||A(:,i)||^{-1}), the diagonally preconditioned LOBPCG of
+                           Sec. 1.1; one more pass over A for the column norms) or
+                           RLOBPCG_PRECOND_NONE (P = I, LOBPCG without a preconditioner). Every
+                           variant starts from the sketch-and-solve block and stops by the rule
+                           of Sec. 2.1, as the comparison of Sec. 1.1 does.                      */
 } rlobpcg_opts;
+
+#define RLOBPCG_PRECOND_SKETCH 0
+#define RLOBPCG_PRECOND_DIAG 1
+#define RLOBPCG_PRECOND_NONE 2
 
 #define RLOBPCG_ORTH_HOUSEHOLDER 0
 #define RLOBPCG_ORTH_SVQB 1

@@ -2047,6 +2047,73 @@ int gather_cols_launch(T* buf, int64_t rows, int64_t ld, const int* src, const i
 template int gather_cols_launch<double>(double*, int64_t, int64_t, const int*, const int*, int, cudaStream_t);
 template int gather_cols_launch<cd>(cd*, int64_t, int64_t, const int*, const int*, int, cudaStream_t);
 
+// ---- the preconditioner variants of Sec. 1.1 ------------------------------------------------
+// Squared column norms of A (m x n row-major): block g sums rows [g rb, (g+1) rb) of every column
+// (thread per column, rows in order), then one thread per column adds the blocks in order.
+constexpr int kColnormParts = 256;
+int colnorm_parts(int64_t m) { return (int)imin<int64_t>(kColnormParts, imax<int64_t>(1, (m + 1023) / 1024)); }
+
+template <class T>
+__global__ void colnorm_part_kernel(const T* __restrict__ A, int64_t m, int n, int64_t lda, int64_t rb,
+                                    double* __restrict__ part) {
+  const int64_t g = blockIdx.y;
+  const int j = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+  if (j >= n) return;
+  const int64_t r0 = g * rb, r1 = imin<int64_t>(m, r0 + rb);
+  double s0 = 0, s1 = 0;
+  int64_t r = r0;
+  for (; r + 1 < r1; r += 2) {
+    s0 += abs2_(A[r * lda + j]);
+    s1 += abs2_(A[(r + 1) * lda + j]);
+  }
+  if (r < r1) s0 += abs2_(A[r * lda + j]);
+  part[g * n + j] = s0 + s1;
+}
+
+__global__ void colnorm_sum_kernel(const double* __restrict__ part, int G, int n, double* __restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double s = 0;
+  for (int g = 0; g < G; ++g) s += part[(int64_t)g * n + j];
+  out[j] = s;
+}
+
+template <class T>
+int colnorm2_launch(const T* A, int64_t m, int n, int64_t lda, double* part, double* out, cudaStream_t st) {
+  const int G = colnorm_parts(m);
+  const int64_t rb = (m + G - 1) / G;
+  colnorm_part_kernel<T><<<dim3((unsigned)((n + 127) / 128), (unsigned)G), 128, 0, st>>>(A, m, n, lda, rb, part);
+  RL_CHECK_LAUNCH();
+  colnorm_sum_kernel<<<(n + 255) / 256, 256, 0, st>>>(part, G, n, out);
+  RL_CHECK_LAUNCH();
+  return RLOBPCG_OK;
+}
+template int colnorm2_launch<double>(const double*, int64_t, int, int64_t, double*, double*, cudaStream_t);
+template int colnorm2_launch<cd>(const cd*, int64_t, int, int64_t, double*, double*, cudaStream_t);
+
+// W(k, :) = Rs(k, :) / d2(k) (diagonal preconditioner, d2 = squared column norms of A), or
+// W = Rs when d2 is null (no preconditioner); W into columns [wo, wo + b) of Tb (ld)
+template <class T>
+__global__ void scale_rows_kernel(const T* __restrict__ Rs, int n, int b, const double* __restrict__ d2, T* Tb,
+                                  int64_t ld, int wo) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)n * b) return;
+  const int64_t k = e / b;
+  const int j = (int)(e % b);
+  const T r = Rs[e];
+  Tb[k * ld + wo + j] = d2 ? scale_(r, 1.0 / d2[k]) : r;
+}
+
+template <class T>
+int scale_rows_launch(const T* Rs, int n, int b, const double* d2, T* Tb, int64_t ld, int wo, cudaStream_t st) {
+  const int64_t tot = (int64_t)n * b;
+  scale_rows_kernel<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(Rs, n, b, d2, Tb, ld, wo);
+  RL_CHECK_LAUNCH();
+  return RLOBPCG_OK;
+}
+template int scale_rows_launch<double>(const double*, int, int, const double*, double*, int64_t, int, cudaStream_t);
+template int scale_rows_launch<cd>(const cd*, int, int, const double*, cd*, int64_t, int, cudaStream_t);
+
 // batched iterations of many small solves (they reuse the one-CTA bodies above)
 #include "batch_kernels.cuh"
 }  // namespace rl

@@ -78,6 +78,11 @@ int bcgs2_orth_launch(T* Tb, int n, int b, int64_t ld, int wo, int nx, T* E, int
 size_t bcgs2_coop_bytes(int64_t n, int qmax, int b, size_t esz);
 template <class T>
 int gather_cols_launch(T* buf, int64_t rows, int64_t ld, const int* src, const int* dst, int cnt, cudaStream_t st);
+int colnorm_parts(int64_t m);
+template <class T>
+int colnorm2_launch(const T* A, int64_t m, int n, int64_t lda, double* part, double* out, cudaStream_t st);
+template <class T>
+int scale_rows_launch(const T* Rs, int n, int b, const double* d2, T* Tb, int64_t ld, int wo, cudaStream_t st);
 template <class T>
 int copy_cols_launch(const T* src, int64_t lds, int so, T* dst, int64_t ldd, int dof, int64_t rows, int w,
                      cudaStream_t st);
@@ -140,6 +145,8 @@ struct rlobpcg_plan_s {
   size_t twork_bytes = 0;
   void* coop = nullptr;     // global scratch of the cooperative BCGS2 + Orth kernel
   size_t coop_bytes = 0;
+  void* cn2 = nullptr;      // squared column norms of A (diagonal preconditioner)
+  void* cnpart = nullptr;   // their per-block partial sums
   void* VL = nullptr;       // locked columns of V (n x b) and of A V (m x b), with locking
   void* AVL = nullptr;
   cudaEvent_t ev[10] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -301,6 +308,10 @@ int setup_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, SolveRun& r, double t
   }
   RL_CUDA(cudaMemcpyAsync(&herr, p->err, sizeof(int), cudaMemcpyDeviceToHost, st));
 
+  // squared column norms of A for the diagonal preconditioner (one pass over A)
+  if (p->opts.precond == RLOBPCG_PRECOND_DIAG)
+    RL_TRY(colnorm2_launch<T>(A, m, n, lda, (double*)p->cnpart, (double*)p->cn2, st));
+
   // Sketch and factorise (the first steps of Alg. 2)
   // the refined form keeps SA in FP64; its QR input is rounded to FP32 inside the factor step
   const bool refine = p->opts.sketch_prec == RLOBPCG_SKETCH_F32_REFINE;
@@ -450,8 +461,13 @@ int loop_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, SolveRun& r) {
   T* AVL = (T*)p->AVL;
   for (int i = 0; i < max_iter; ++i) {
     // W = P (P^* R_i), then BCGS2 against [V X] (and the locked columns) and Orth
-    RL_TRY((precond_launch<T, S>((const S*)p->Rinv_r, (const S*)p->Rinv_c, n, a, (const T*)p->Rs, (T*)p->Y, Tb, ld, a,
-                                 st)));
+    if (p->opts.precond == RLOBPCG_PRECOND_SKETCH)
+      RL_TRY((precond_launch<T, S>((const S*)p->Rinv_r, (const S*)p->Rinv_c, n, a, (const T*)p->Rs, (T*)p->Y, Tb, ld,
+                                   a, st)));
+    else   // W = D^2 Rs with D = diag(||A(:, i)||^{-1}), or W = Rs
+      RL_TRY(scale_rows_launch<T>((const T*)p->Rs, n, a, p->opts.precond == RLOBPCG_PRECOND_DIAG ? (const double*)p->cn2
+                                                                                                  : nullptr,
+                                  Tb, ld, a, st));
     RL_TRY(bcgs2_orth_launch<T>(Tb, n, a, ld, a, nx, (T*)p->E, 2, st, p->split ? &wd : nullptr, p->err, &w_ready,
                                 p->coop, p->coop_bytes, p->opts.orth_mode, VL, nl, b));
     const int c = 2 * a + nx;
@@ -713,6 +729,7 @@ extern "C" int rlobpcg_default_opts(rlobpcg_opts* o) {
   o->tau = -1.0;
   o->orth_mode = RLOBPCG_ORTH_HOUSEHOLDER;
   o->locking = 0;
+  o->precond = RLOBPCG_PRECOND_SKETCH;
   return RLOBPCG_OK;
 }
 
@@ -729,7 +746,9 @@ int resolve_plan_args(int64_t m, int64_t n, int k, int dtype, const rlobpcg_opts
       n > (1 << 20) || (o->sketch_prec != RLOBPCG_SKETCH_F64 && o->sketch_prec != RLOBPCG_SKETCH_F32 &&
                         o->sketch_prec != RLOBPCG_SKETCH_F32_REFINE) ||
       (o->orth_mode != RLOBPCG_ORTH_HOUSEHOLDER && o->orth_mode != RLOBPCG_ORTH_SVQB) ||
-      (o->locking != 0 && o->locking != 1)) {
+      (o->locking != 0 && o->locking != 1) ||
+      (o->precond != RLOBPCG_PRECOND_SKETCH && o->precond != RLOBPCG_PRECOND_DIAG &&
+       o->precond != RLOBPCG_PRECOND_NONE)) {
     set_last_error("invalid plan arguments (need 1 <= k <= b <= 21, 3b <= n <= m, n <= d, zeta <= d, a known sketch precision and orth_mode, locking 0 or 1)", __FILE__, __LINE__);
     return RLOBPCG_ERR_INVALID_ARG;
   }
@@ -820,6 +839,10 @@ int plan_buffers(PlanAlloc& A_, rlobpcg_plan_s* p, int64_t m, int64_t n, int b, 
   }
   *twork = std::max(tsqr_workspace_bytes(m, (int)ld, esz), tsqr_workspace_bytes(n, qmax, esz));
   RL_B(twork, *twork);
+  if (o.precond == RLOBPCG_PRECOND_DIAG) {
+    RL_B(cn2, (size_t)n * sizeof(double));
+    RL_B(cnpart, (size_t)colnorm_parts(m) * n * sizeof(double));
+  }
   if (o.locking) {
     RL_B(VL, (size_t)n * b * esz);
     RL_B(AVL, (size_t)m * b * esz);
@@ -1140,8 +1163,9 @@ bool batch_eligible(const rlobpcg_plan_s* p, std::string* why) {
   if (p->dtype != RLOBPCG_F64) { *why = "batched solves are real FP64"; return false; }
   if (p->b > batch::BMAX) { *why = "batched solves need b <= 5"; return false; }
   if (p->n > 512) { *why = "batched solves need n <= 512"; return false; }
-  if (p->opts.locking || p->opts.orth_mode != RLOBPCG_ORTH_HOUSEHOLDER || p->opts.residual_refresh_every > 0) {
-    *why = "batched solves run without locking, SVQB or residual refresh";
+  if (p->opts.locking || p->opts.orth_mode != RLOBPCG_ORTH_HOUSEHOLDER || p->opts.residual_refresh_every > 0 ||
+      p->opts.precond != RLOBPCG_PRECOND_SKETCH) {
+    *why = "batched solves run with the sketch preconditioner, without locking, SVQB or residual refresh";
     return false;
   }
   return true;
@@ -1593,7 +1617,8 @@ void batch_engine_destroy(BatchEngine* e) {
 bool batch_request_eligible(int64_t n, int k, int dtype, const rlobpcg_opts& o) {
   const int b = o.block > 0 ? o.block : k;
   return dtype == RLOBPCG_F64 && b <= batch::BMAX && n <= 512 && !o.locking && o.orth_mode == RLOBPCG_ORTH_HOUSEHOLDER &&
-         o.residual_refresh_every <= 0 && std::max(o.max_iter, o.fixed_iters) <= 200;
+         o.residual_refresh_every <= 0 && std::max(o.max_iter, o.fixed_iters) <= 200 &&
+         o.precond == RLOBPCG_PRECOND_SKETCH;
 }
 
 size_t batch_extra_bytes(int64_t m, int64_t n, int b) {

@@ -29,6 +29,9 @@ RLOBPCG_C128 = 1
 RLOBPCG_SKETCH_F64 = 0
 RLOBPCG_SKETCH_F32 = 1
 RLOBPCG_SKETCH_F32_REFINE = 2
+RLOBPCG_PRECOND_SKETCH = 0
+RLOBPCG_PRECOND_DIAG = 1
+RLOBPCG_PRECOND_NONE = 2
 RLOBPCG_ORTH_HOUSEHOLDER = 0
 RLOBPCG_ORTH_SVQB = 1
 RLOBPCG_STOP_CONVERGED = 0
@@ -42,7 +45,7 @@ class rlobpcg_opts(ctypes.Structure):
     _fields_ = [("seed", c_uint64), ("d", c_int), ("zeta", c_int), ("block", c_int), ("max_iter", c_int),
                 ("check_every", c_int), ("use_stagnation", c_int), ("sketch_prec", c_int), ("fixed_iters", c_int),
                 ("residual_refresh_every", c_int), ("exact_sketch_svd", c_int), ("gram_split", c_int),
-                ("tau", c_double), ("orth_mode", c_int), ("locking", c_int)]
+                ("tau", c_double), ("orth_mode", c_int), ("locking", c_int), ("precond", c_int)]
 
 
 class rlobpcg_info(ctypes.Structure):

@@ -237,6 +237,42 @@ def serve_pool(size: int, device="cuda"):
     return out
 
 
+def fig1_device(m: int = 2_000_000, n: int = 4000, seed: int = SEED_BASE + 7, device="cuda", kinds=("easy", "hard")):
+    """Sec. 1.1's two m x n problems A = U diag(sigma) V^T, built on a GPU one at a time (a
+    generator: each A is dropped before the next is made). Both use one Haar U (Q of a seeded
+    Gaussian, phases of diag(R) folded back).
+      easy: V = orth(diag(randn(n)) + 1e-4 randn(n)) (coherent), sigma_1..sigma_{n-1} geometric
+            1 -> 0.1, sigma_n = 1e-7;
+      hard: Haar V, sigma geometric 1 -> 1e-10.
+    Yields (kind, A on the device, sigma sorted descending)."""
+    import torch
+    gen = torch.Generator(device=device).manual_seed(int(seed))
+    G = torch.randn((m, n), generator=gen, device=device, dtype=torch.float64)
+    U, R = torch.linalg.qr(G)
+    del G
+    d = torch.diagonal(R)
+    U *= torch.where(d.abs() > 0, torch.sign(d), torch.ones_like(d))[None, :]
+    del R, d
+    for kind in kinds:
+        rng = np.random.default_rng(seed + (1 if kind == "easy" else 2))
+        if kind == "easy":
+            M = np.diag(rng.standard_normal(n)) + 1e-4 * rng.standard_normal((n, n))
+            V, _ = np.linalg.qr(M)
+            sigma = np.concatenate([np.geomspace(1.0, 0.1, n - 1), [1e-7]])
+        else:
+            V = haar_orthonormal(rng, n, n)
+            sigma = np.geomspace(1.0, 1e-10, n)
+        Vt = torch.from_numpy(np.ascontiguousarray((V * sigma[None, :]).T)).to(device)   # diag(sigma) V^T
+        A = torch.empty((m, n), dtype=torch.float64, device=device)
+        step = 1 << 17
+        for r0 in range(0, m, step):
+            torch.matmul(U[r0:r0 + step], Vt, out=A[r0:r0 + step])
+        del Vt
+        yield kind, A, np.sort(sigma)[::-1]
+        del A
+    del U
+
+
 def planted_on_device(seed: int, m: int, sigma: np.ndarray, device="cuda", complex_: bool = False):
     """A = U diag(sigma) V^H built on a GPU with torch (for sizes where a host QR of the m x n
     Gaussian takes minutes, e.g. 1e6 x 1000). U: Q of a seeded Gaussian (Philox stream of
