@@ -93,6 +93,11 @@ WORKLOADS = {
         zeta=8, cplx=False, prec=0, device=_device_large, seeds=(1004,), mixed_prec=2,
         host_sample=_host_large_sample, sample_m=100_000, ref_sample_m=20_000,
         matrices="planted sigma_1..990 logspace(0,-4), sigma_991..1000 logspace(-9,-10), Haar U, V"),
+    "profile_2e5x1000": dict(
+        desc="planted m=2e5 n=1000 k=10 d=4n zeta=8 fp64 (the 1e6 x 1000 recipe on 2e5 rows, for profiling)",
+        m=200_000, n=1000, k=10, d=4000, zeta=8, cplx=False, prec=0, device=_device_large, seeds=(1004,),
+        host_sample=_host_large_sample, sample_m=20_000, ref_sample_m=20_000,
+        matrices="planted sigma_1..990 logspace(0,-4), sigma_991..1000 logspace(-9,-10), Haar U, V"),
     "nullspace_1e5x500": dict(
         desc="nullspace+planted m=1e5 n=500 k=5 d=3n zeta=8 fp64", m=100_000, n=500, k=5, d=1500, zeta=8,
         cplx=False, prec=0, host=_host_pair, seeds=(2002, 2003), sample_m=20_000,
@@ -803,6 +808,85 @@ def run_fig1(args, rank, world, local_rank):
             "results": out}
 
 
+def run_batch_small(args, rank, world, local_rank):
+    """Many small solves at once: `--batch-count` planted matrices (m log-uniform in [2e3, 1e5],
+    n uniform in [20, 400], k in {1, 2, 4}; sigma logspace(0,-6) with the k smallest logspace(-10,-9))
+    on the device, solved by rlobpcg_solve_batch (set-ups on their plan streams, iterations of all
+    solves together in the batch engine) and, as the baseline, by rlobpcg_solve one at a time.
+    Timed: `--steps` batches after `--warmup` (the first also tunes the tile shapes)."""
+    import torch
+
+    from paper_2602_16797_gb300 import rlobpcg as rl
+    from paper_2602_16797_gb300 import workloads as wl
+    if rank != 0:
+        return None
+    torch.cuda.set_device(local_rank)
+    rl.load()
+    if args.batch_tile:   # pin every class's tile shape (e.g. to profile without the autotuner's launches)
+        tr, rt = (int(x) for x in args.batch_tile.split(":"))
+        for nc in (32, 64, 128, 256, 512):
+            for b in (1, 2, 4):
+                rl.rlobpcg_batch_set_tile(nc, b, tr, rt)
+    rng = np.random.default_rng(3)
+    mats, ks = [], []
+    for r in range(args.batch_count):
+        m = int(np.exp(rng.uniform(np.log(2e3), np.log(1e5))))
+        n = int(rng.integers(20, 401))
+        k = int(rng.choice([1, 2, 4]))
+        m = max(m, 4 * n)
+        sigma = np.concatenate([np.logspace(0, -6, n - k), np.logspace(-10, -9, k)])
+        mats.append(wl.planted_on_device(50000 + r, m, sigma)[0])
+        ks.append(k)
+    torch.cuda.synchronize()
+    streams = [torch.cuda.Stream() for _ in range(8)]
+
+    def opts(k):
+        o = rl.rlobpcg_default_opts()
+        o.seed = 1
+        o.block = k
+        o.gram_split = 0
+        return o
+
+    def batch():
+        plans = [rl.rlobpcg_plan(A.shape[0], A.shape[1], k, rl.RLOBPCG_F64, opts(k), streams[i % 8].cuda_stream)
+                 for i, (A, k) in enumerate(zip(mats, ks))]
+        outs = [(torch.empty(k, dtype=torch.float64, device="cuda"),
+                 torch.empty((A.shape[1], k), dtype=torch.float64, device="cuda")) for A, k in zip(mats, ks)]
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        rc, infos, st = rl.rlobpcg_solve_batch(plans, [A.data_ptr() for A in mats], [A.shape[1] for A in mats],
+                                              [o[0].data_ptr() for o in outs], [o[1].data_ptr() for o in outs],
+                                              None, None, 0)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+        for p in plans:
+            rl.rlobpcg_plan_destroy(p)
+        return dt, infos
+
+    for _ in range(args.warmup):
+        batch()
+    times, iters = [], []
+    for _ in range(args.steps):
+        dt, infos = batch()
+        times.append(dt)
+        iters.append(float(np.mean([i.iters for i in infos])))
+    t = time.perf_counter()
+    seq_iters = []
+    for A, k in zip(mats, ks):
+        sig, V, U, res, info = rl.solve(A, k, opts=opts(k))
+        seq_iters.append(info["iters"])
+    torch.cuda.synchronize()
+    seq = time.perf_counter() - t
+    dt = float(np.median(times))
+    return {"metric": "solves/s of many small solves (batched iterations)", "value": len(mats) / dt,
+            "unit": "solves/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+            "higher_is_better": True, "dtype": "f64", "data": "synthetic (seeded planted spectra)",
+            "config": {"workload": f"{len(mats)} small solves (m log-uniform [2e3,1e5], n U[20,400], k in {{1,2,4}})",
+                       "parallelism": "batch engine on one GPU"},
+            "mean_iters": float(np.mean(iters)), "one_at_a_time": {"solves_per_s": len(mats) / seq,
+                                                                   "mean_iters": float(np.mean(seq_iters))}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -810,8 +894,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["serve_stream", "block_study", "fig1"],
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["serve_stream", "block_study", "fig1", "batch_small"],
                     default=DEFAULT_WORKLOAD)
+    ap.add_argument("--batch-count", type=int, default=64, help="batch_small: solves per batch")
+    ap.add_argument("--batch-tile", default="", help="batch_small: pin every class's tile shape, trows:rt")
     ap.add_argument("--fig1-m", type=int, default=2_000_000, help="fig1: rows")
     ap.add_argument("--fig1-n", type=int, default=4000, help="fig1: columns")
     ap.add_argument("--blocks", default="1,3,5,10,20", help="block_study: block sizes")
@@ -842,6 +928,8 @@ def main():
         out = run_block_study(args, rank, world, local_rank)
     elif args.workload == "fig1":
         out = run_fig1(args, rank, world, local_rank)
+    elif args.workload == "batch_small":
+        out = run_batch_small(args, rank, world, local_rank)
     else:
         out = run_ours(args, rank, world, local_rank)
     replicas.finish(world)
