@@ -108,16 +108,15 @@ __global__ void __launch_bounds__(256) tsqr_level_kernel(const T* __restrict__ X
       const int rs = c;                         // first chunk row (R rows j+1..c-1 are zero in column j)
       T d = zero_<T>();
       if (on) {
-        T a0 = zero_<T>(), a1 = zero_<T>(), a2 = zero_<T>(), a3 = zero_<T>();
+        // two accumulators: the FP64 pipe, not the dependency chain, bounds this loop
+        T a0 = zero_<T>(), a1 = zero_<T>();
         int r = rs + p;
-        for (; r + 3 * L < SRu; r += 4 * L) {
+        for (; r + L < SRu; r += 2 * L) {
           a0 = madc_(S[(size_t)r * c + j], S[(size_t)r * c + cc], a0);
           a1 = madc_(S[(size_t)(r + L) * c + j], S[(size_t)(r + L) * c + cc], a1);
-          a2 = madc_(S[(size_t)(r + 2 * L) * c + j], S[(size_t)(r + 2 * L) * c + cc], a2);
-          a3 = madc_(S[(size_t)(r + 3 * L) * c + j], S[(size_t)(r + 3 * L) * c + cc], a3);
         }
-        for (; r < SRu; r += L) a0 = madc_(S[(size_t)r * c + j], S[(size_t)r * c + cc], a0);
-        d = add_(add_(a0, a1), add_(a2, a3));
+        if (r < SRu) a0 = madc_(S[(size_t)r * c + j], S[(size_t)r * c + cc], a0);
+        d = add_(a0, a1);
       }
       for (int o = L >> 1; o > 0; o >>= 1) d = add_(d, shfl_xor_(d, o));
       if (q == 0 && p == 0) {
@@ -126,14 +125,18 @@ __global__ void __launch_bounds__(256) tsqr_level_kernel(const T* __restrict__ X
         sh_tau = tau; sh_inv = inv_ab; sh_beta = beta;
       }
       __syncthreads();
-      if (on && q > 0) {
+      // f and f / (alpha - beta) once per column (lane p = 0), then passed to the column's lanes
+      T fv = zero_<T>();
+      if (on && q > 0 && p == 0) {
         const T inv_ab = sh_inv;
         const T f = mul_(conj_(sh_tau), add_(S[(size_t)j * c + cc], mul_(conj_(inv_ab), d)));
-        const T fv = mul_(inv_ab, f);            // v_r = S[r][j] / (alpha - beta) folded into f
-        if (p == 0) S[(size_t)j * c + cc] = sub_(S[(size_t)j * c + cc], f);
+        fv = mul_(inv_ab, f);                    // v_r = S[r][j] / (alpha - beta) folded into f
+        S[(size_t)j * c + cc] = sub_(S[(size_t)j * c + cc], f);
+      }
+      fv = shfl_(fv, (threadIdx.x & 31) & ~(L - 1));
+      if (on && q > 0)
         for (int r = rs + p; r < SRu; r += L)
           S[(size_t)r * c + cc] = sub_(S[(size_t)r * c + cc], mul_(S[(size_t)r * c + j], fv));
-      }
       if (q == 0 && p == 0) S[(size_t)j * c + j] = sh_beta;
       __syncthreads();
     }
