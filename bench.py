@@ -752,7 +752,8 @@ def run_fig1(args, rank, world, local_rank):
     start v0 and with the paper's iteration cap (200 for b = 1). Reported per method: the relative
     error (theta_t - sigma_n) / sigma_n of the estimate after every iteration (theta_t = ||A v_t||
     for the Ritz vector), the one-time and per-iteration device times, and the time to reach the
-    best error RLOBPCG reaches."""
+    best error RLOBPCG reaches. Gram products on the tensor cores (split-bf16: A 64 GB + its byte
+    digits 128 GB on the device)."""
     import torch
 
     from paper_2602_16797_gb300 import rlobpcg as rl
@@ -762,8 +763,12 @@ def run_fig1(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     rl.load()
     m, n = args.fig1_m, args.fig1_n
-    variants = [("rlobpcg", rl.RLOBPCG_PRECOND_SKETCH), ("lobpcg_diag", rl.RLOBPCG_PRECOND_DIAG),
-                ("lobpcg_none", rl.RLOBPCG_PRECOND_NONE)]
+    # (name, preconditioner, sketch precision): the three methods of Sec. 1.1, and RLOBPCG with its
+    # factor in FP32 refined once in FP64 (the mixed-precision form)
+    variants = [("rlobpcg", rl.RLOBPCG_PRECOND_SKETCH, rl.RLOBPCG_SKETCH_F64),
+                ("rlobpcg_f32_refined", rl.RLOBPCG_PRECOND_SKETCH, rl.RLOBPCG_SKETCH_F32_REFINE),
+                ("lobpcg_diag", rl.RLOBPCG_PRECOND_DIAG, rl.RLOBPCG_SKETCH_F64),
+                ("lobpcg_none", rl.RLOBPCG_PRECOND_NONE, rl.RLOBPCG_SKETCH_F64)]
     out = {}
     t_gen = time.perf_counter()
     for kind, A, sigma in wl.fig1_device(m, n):
@@ -771,12 +776,12 @@ def run_fig1(args, rank, world, local_rank):
         gen_s = time.perf_counter() - t_gen
         sn = float(sigma[-1])
         res = {"sigma_n": sn, "generation_s": gen_s}
-        for name, pc in variants:
+        for name, pc, prec in variants:
             o = rl.rlobpcg_default_opts()
             o.seed = 7
             o.block = 1
             o.precond = pc
-            o.gram_split = 0   # FP64 Gram: A (64 GB) and the solve fit beside the generator's U
+            o.sketch_prec = prec
             st = torch.cuda.current_stream().cuda_stream
             plan = rl.rlobpcg_plan(m, n, 1, rl.RLOBPCG_F64, o, st)
             sig = torch.empty(1, dtype=torch.float64, device="cuda")
@@ -791,11 +796,12 @@ def run_fig1(args, rank, world, local_rank):
             per_it = info.ms_iterate / max(1, info.iters)
             setup = info.ms_sketch + info.ms_factor
             res[name] = {"status": rc, "iters": info.iters, "stop_reason": info.stop_reason,
-                         "setup_ms": setup, "ms_per_iteration": per_it, "ms_total": info.ms_total,
+                         "setup_ms": setup, "sketch_ms": info.ms_sketch, "factor_ms": info.ms_factor,
+                         "ms_per_iteration": per_it, "ms_total": info.ms_total,
                          "rel_err_v0": float(err[0]), "rel_err_final": float(err[-1]),
                          "rel_err_every_10": [float(x) for x in err[::10]]}
         best = res["rlobpcg"]["rel_err_final"]
-        for name, _ in variants:
+        for name, _, _ in variants:
             r = res[name]
             errs = r["rel_err_every_10"]
             hit = next((i * 10 for i, e in enumerate(errs) if e <= max(best, 0) * 1.0001 + 1e-300), None)
@@ -803,7 +809,7 @@ def run_fig1(args, rank, world, local_rank):
         out[kind] = res
         t_gen = time.perf_counter()
     return {"metric": "Fig. 1 (Sec. 1.1): relative error of the smallest singular value vs time", "unit": "ms",
-            "config": {"workload": f"Sec. 1.1 easy and hard problems, m={m} n={n}, b=k=1, FP64 Gram",
+            "config": {"workload": f"Sec. 1.1 easy and hard problems, m={m} n={n}, b=k=1, split-bf16 Gram",
                        "data": "synthetic (Haar U from a GPU QR; the paper's V and sigma recipes)"},
             "results": out}
 

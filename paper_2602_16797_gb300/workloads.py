@@ -239,21 +239,22 @@ def serve_pool(size: int, device="cuda"):
 
 def fig1_device(m: int = 2_000_000, n: int = 4000, seed: int = SEED_BASE + 7, device="cuda", kinds=("easy", "hard")):
     """Sec. 1.1's two m x n problems A = U diag(sigma) V^T, built on a GPU one at a time (a
-    generator: each A is dropped before the next is made). Both use one Haar U (Q of a seeded
-    Gaussian, phases of diag(R) folded back).
+    generator: each A is dropped before the next is made, and U is dropped before A is handed
+    out, so that a solve has the rest of the device). Both use the same Haar U (Q of a seeded
+    Gaussian, phases of diag(R) folded back; rebuilt for each problem from the same seed).
       easy: V = orth(diag(randn(n)) + 1e-4 randn(n)) (coherent), sigma_1..sigma_{n-1} geometric
             1 -> 0.1, sigma_n = 1e-7;
       hard: Haar V, sigma geometric 1 -> 1e-10.
     Yields (kind, A on the device, sigma sorted descending)."""
     import torch
-    gen = torch.Generator(device=device).manual_seed(int(seed))
-    G = torch.randn((m, n), generator=gen, device=device, dtype=torch.float64)
-    U, R = torch.linalg.qr(G)
-    del G
-    d = torch.diagonal(R)
-    U *= torch.where(d.abs() > 0, torch.sign(d), torch.ones_like(d))[None, :]
-    del R, d
     for kind in kinds:
+        gen = torch.Generator(device=device).manual_seed(int(seed))
+        G = torch.randn((m, n), generator=gen, device=device, dtype=torch.float64)
+        U, R = torch.linalg.qr(G)
+        del G
+        d = torch.diagonal(R)
+        U *= torch.where(d.abs() > 0, torch.sign(d), torch.ones_like(d))[None, :]
+        del R, d
         rng = np.random.default_rng(seed + (1 if kind == "easy" else 2))
         if kind == "easy":
             M = np.diag(rng.standard_normal(n)) + 1e-4 * rng.standard_normal((n, n))
@@ -267,10 +268,10 @@ def fig1_device(m: int = 2_000_000, n: int = 4000, seed: int = SEED_BASE + 7, de
         step = 1 << 17
         for r0 in range(0, m, step):
             torch.matmul(U[r0:r0 + step], Vt, out=A[r0:r0 + step])
-        del Vt
+        del Vt, U
+        torch.cuda.empty_cache()
         yield kind, A, np.sort(sigma)[::-1]
         del A
-    del U
 
 
 def planted_on_device(seed: int, m: int, sigma: np.ndarray, device="cuda", complex_: bool = False):
