@@ -351,14 +351,16 @@ def gram_roofline(m, n, b, cplx, split, t_pass_s, peaks, fp64_peak_tf, fp64_peak
                 "traffic": hbm_obj["traffic"], "flops_per_pass": fl, "peak_source": fp64_peak_src,
                 "kernel": "gram_kernel (fused A W, A^H A W), " + ("complex128" if cplx else "FP64"),
                 "ms_per_pass": t_pass_s * 1e3, "hbm": hbm_obj}
-    fl = pass_tensor_flops(m, n, b)
+    # complex A runs the real pass on its real view: m x 2n, block width 2b
+    fl = pass_tensor_flops(m, 2 * n, 2 * b) if cplx else pass_tensor_flops(m, n, b)
     tc_obj = {"bound": "tensor", "achieved": fl / t_pass_s / 1e12, "peak": tc, "unit": "TFLOP/s",
               "frac": fl / t_pass_s / 1e12 / tc, "traffic": None, "flops_per_pass": fl, "peak_source": tc_src}
-    hbm_obj["traffic"] = pass_traffic(m, n)
+    hbm_obj["traffic"] = pass_traffic(m, 2 * n if cplx else n)
     t_hbm, t_tc = by / (hbm * 1e9), fl / (tc * 1e12)
     main, other = (tc_obj, hbm_obj) if t_tc > t_hbm else (hbm_obj, tc_obj)
     out = dict(main)
-    out.update({"kernel": "split-bf16 Gram pass (gram_tc.cu: split of W, A W and A^T (A W) on tcgen05)",
+    out.update({"kernel": "split-bf16 Gram pass (gram_tc.cu: split of W, A W and A^T (A W) on tcgen05)"
+                + ("; complex128 through its real view (gram_split_c.cu)" if cplx else ""),
                 "ms_per_pass": t_pass_s * 1e3, "roof_ms": max(t_hbm, t_tc) * 1e3,
                 "other": other})
     return out
@@ -419,7 +421,7 @@ def run_ours(args, rank, world, local_rank):
     tdt = torch.complex128 if w["cplx"] else torch.float64
     esz = 16 if w["cplx"] else 8
     stream = torch.cuda.current_stream(dev)
-    split = args.gram == "split" and not w["cplx"] and K <= 24
+    split = args.gram == "split" and (2 * K if w["cplx"] else K) <= 24
     seeds = w["seeds"]
     # one plan per seed: a plan keeps the options it was made with (the seed of S among them)
     plans = [rl.rlobpcg_plan(M, N, K, dtype, _opts(rl, w, sd, w["prec"], args.fixed_iters, args.gram),
@@ -503,8 +505,8 @@ def run_ours(args, rank, world, local_rank):
             "data": "synthetic (seeded; the paper's matrix families)",
             "config": {"workload": w["desc"], "m": M, "n": N, "k": K, "d": D, "zeta": w["zeta"],
                        "sketch": "fp32" if w["prec"] == 1 else "fp64", "matrices": w["matrices"],
-                       "gram": "split-bf16 tensor cores" if split else ("fp64 CUDA cores" if not w["cplx"]
-                                                                         else "complex128 CUDA cores"),
+                       "gram": ("split-bf16 tensor cores" + (" (real view of complex A)" if w["cplx"] else ""))
+                               if split else ("fp64 CUDA cores" if not w["cplx"] else "complex128 CUDA cores"),
                        "fixed_iters": args.fixed_iters or None,
                        "l2": "input larger than L2; no flush" if M * N * esz > 129e6 else
                              "input smaller than L2 (each step is a full solve)",

@@ -84,8 +84,9 @@ typedef struct {
                            clustered top spectrum; it only scales the stop tolerance)           */
   int gram_split;       /* 1 (default): run the Gram products on the tensor cores by an exact split
                            of A, W and A W into bf16 digits (rlobpcg_gram_split; about FP64
-                           accuracy). Real FP64 and b <= 24 only (ignored otherwise); A is split
-                           once per solve into about 16 bytes of device memory per element of A.
+                           accuracy). Real FP64 with b <= 24 and complex128 with b <= 12
+                           (rlobpcg_gram_split_c128) only (ignored otherwise); A is split once per
+                           solve into about 16 bytes of device memory per real number of A.
                            0: the FP64 CUDA-core Gram pass (rlobpcg_gram).                    */
   double tau;           /* tolerance of ||R(:,j)|| <= Sigma~(1,1)^2 tau; < 0 means 2 sqrt(n) 2^-52 */
   int orth_mode;        /* orthonormalisation of W after its two block Gram-Schmidt passes against
@@ -224,8 +225,8 @@ int rlobpcg_server_create(rlobpcg_server_t* out, size_t hbm_budget_bytes, int ma
 int rlobpcg_server_create_ex(rlobpcg_server_t* out, size_t hbm_budget_bytes, int max_active, int device, int mode);
 
 /* Batched mode: the largest m n b (rows x columns x block) a request may have to iterate in the
- * batch engine; larger requests run whole on their worker, where the Gram products of real FP64
- * solves run on the tensor cores (gram_split). Applies to requests submitted afterwards.
+ * batch engine; larger requests run whole on their worker, where the Gram products of FP64 and
+ * complex128 solves run on the tensor cores (gram_split). Applies to requests submitted afterwards.
  * Default RLOBPCG_SERVE_BATCH_LIMIT_DEFAULT. INVALID_ARG for a negative limit. */
 #define RLOBPCG_SERVE_BATCH_LIMIT_DEFAULT ((int64_t)1 << 23)
 int rlobpcg_server_set_batch_limit(rlobpcg_server_t s, int64_t max_mnb);
@@ -433,6 +434,26 @@ int rlobpcg_gram_split_prepare(const double* A, int64_t m, int64_t n, int64_t ld
 size_t rlobpcg_gram_split_workspace_size(int64_t m, int64_t n, int b);
 int rlobpcg_gram_split(const void* prep, int64_t m, int64_t n, const double* W, int b, int64_t ldw, double* AW,
                        int64_t ldaw, double* G, int64_t ldg, void* work, size_t work_bytes, void* stream);
+
+/*
+ * The same pass for complex128 A (the Gram pass of Alg. 2: AW = A W, G = A^H AW). A complex m x n
+ * row-major matrix read as doubles is the real m x 2n row-major matrix B (leading dimension
+ * 2 lda; B(i, 2j) = Re A(i, j), B(i, 2j+1) = Im A(i, j)), so
+ *   prep: rlobpcg_gram_split_prepare((const double*)A, m, 2 n, 2 lda, ...) -- the split of B,
+ *         rlobpcg_gram_split_prepare_size(m, 2 n) bytes;
+ *   rlobpcg_gram_split_c128: one pass; W (n x b), AW (m x b), G (n x b), complex128 row-major with
+ *         leading dimensions ldw, ldaw, ldg (in complex elements), 1 <= b <= 12; work:
+ *         rlobpcg_gram_split_c128_workspace_size(m, n, b) bytes of device scratch (0 when b > 12).
+ * Each complex entry w of W becomes the real 2 x 2 block [Re w, Im w; -Im w, Re w] of a 2n x 2b
+ * real W', so that B W' is A W in its interleaved storage; the real pass forms B W' and
+ * B^T (B W'), and G = A^H AW is combined from the four real products of B^T (B W') in FP64
+ * (Re G = Re A^T Re Z + Im A^T Im Z, Im G = Re A^T Im Z - Im A^T Re Z for Z = A W). Error per
+ * term as for the real pass, plus one FP64 rounding per entry of G. Pointers, synchronisation and
+ * errors as for rlobpcg_gram_split.
+ */
+size_t rlobpcg_gram_split_c128_workspace_size(int64_t m, int64_t n, int b);
+int rlobpcg_gram_split_c128(const void* prep, int64_t m, int64_t n, const void* W, int b, int64_t ldw, void* AW,
+                            int64_t ldaw, void* G, int64_t ldg, void* work, size_t work_bytes, void* stream);
 
 /*
  * R factor of a tall block (the TSQR used for Rayleigh-Ritz by SVD of A_T, Alg. 2): X is m x c

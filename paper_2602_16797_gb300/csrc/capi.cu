@@ -28,6 +28,10 @@ int split_prepare(const double* A, int64_t m, int64_t n, int64_t lda, void* prep
 int split_gram(const void* prep, int64_t m, int64_t n, const double* W, int b, int64_t ldw, double* AW, int64_t ldaw,
                double* G, int64_t ldg, void* work, size_t work_bytes, int flags, int* err, cudaEvent_t mid,
                cudaStream_t st);
+size_t split_work_bytes_c128(int64_t m, int64_t n, int b);
+int split_gram_c128(const void* prep, int64_t m, int64_t n, const cd* W, int b, int64_t ldw, cd* AW, int64_t ldaw,
+                    cd* G, int64_t ldg, void* work, size_t work_bytes, int flags, int* err, cudaEvent_t mid,
+                    cudaStream_t st);
 template <class T>
 int tsqr_impl(const T* X, int64_t m, int c, int64_t ldx, T* R, void* work, size_t work_bytes, cudaStream_t st);
 
@@ -220,6 +224,23 @@ extern "C" int rlobpcg_gram_split(const void* prep, int64_t m, int64_t n, const 
   int* err = step_err_word(st);
   if (!err) return RLOBPCG_ERR_OOM;
   const int rc = split_gram(prep, m, n, W, b, ldw, AW, ldaw, G, ldg, work, work_bytes, 0, err, nullptr, st);
+  if (rc) return rc;
+  return finish(st, err);
+}
+
+extern "C" size_t rlobpcg_gram_split_c128_workspace_size(int64_t m, int64_t n, int b) {
+  return split_work_bytes_c128(m, n, b);
+}
+
+extern "C" int rlobpcg_gram_split_c128(const void* prep, int64_t m, int64_t n, const void* W, int b, int64_t ldw,
+                                       void* AW, int64_t ldaw, void* G, int64_t ldg, void* work, size_t work_bytes,
+                                       void* stream) {
+  if (!W) return RLOBPCG_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  int* err = step_err_word(st);
+  if (!err) return RLOBPCG_ERR_OOM;
+  const int rc = split_gram_c128(prep, m, n, (const cd*)W, b, ldw, (cd*)AW, ldaw, (cd*)G, ldg, work, work_bytes, 0,
+                                 err, nullptr, st);
   if (rc) return rc;
   return finish(st, err);
 }

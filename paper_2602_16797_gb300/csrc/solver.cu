@@ -58,6 +58,10 @@ int split_prepare(const double* A, int64_t m, int64_t n, int64_t lda, void* prep
 int split_gram(const void* prep, int64_t m, int64_t n, const double* W, int b, int64_t ldw, double* AW, int64_t ldaw,
                double* G, int64_t ldg, void* work, size_t work_bytes, int flags, int* err, cudaEvent_t mid,
                cudaStream_t st);
+size_t split_work_bytes_c128(int64_t m, int64_t n, int b);
+int split_gram_c128(const void* prep, int64_t m, int64_t n, const cd* W, int b, int64_t ldw, cd* AW, int64_t ldaw,
+                    cd* G, int64_t ldg, void* work, size_t work_bytes, int flags, int* err, cudaEvent_t mid,
+                    cudaStream_t st);
 size_t tsqr_workspace_bytes(int64_t m, int c, size_t esz);
 template <class T>
 int tsqr_impl(const T* X, int64_t m, int c, int64_t ldx, T* R, void* work, size_t work_bytes, cudaStream_t st);
@@ -137,6 +141,7 @@ struct rlobpcg_plan_s {
   void* gwork = nullptr;
   size_t gwork_bytes = 0;
   bool split = false;       // Gram products on the tensor cores (split-bf16)
+  bool csplit = false;      // ... of complex A, through its real view (W digits formed per pass)
   void* sprep = nullptr;    // digits of A (split once per solve)
   size_t sprep_bytes = 0;
   void* swork = nullptr;
@@ -236,6 +241,9 @@ int gram_pass(rlobpcg_plan_s* p, const T* A, int64_t lda, const T* W, T* AW, T* 
               cudaEvent_t mid = nullptr, bool w_ready = false, int bw = 0) {
   const int64_t ld = 3 * p->b;
   if (bw <= 0) bw = p->b;   // block width (the active columns with locking)
+  if (p->csplit)
+    return split_gram_c128(p->sprep, p->m, p->n, (const cd*)W, bw, ld, (cd*)AW, ld, (cd*)G, ld, p->swork,
+                           p->swork_bytes, resid_mode ? split::SPLIT_RESID : 0, p->err, mid, p->st);
   if (p->split)
     return split_gram(p->sprep, p->m, p->n, (const double*)W, bw, ld, (double*)AW, ld, (double*)G, ld, p->swork,
                       p->swork_bytes, (resid_mode ? split::SPLIT_RESID : 0) | (w_ready ? split::SPLIT_W_READY : 0),
@@ -287,10 +295,11 @@ int setup_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, SolveRun& r, double t
   int& nx = r.nx;
   const double*& theta_s = r.theta_s;
   split::WDigits& wd = r.wd;
+  const bool rwd = p->split && !p->csplit;   // BCGS2 writes the W digits of the real split pass
   bool& w_ready = r.w_ready;
   (void)tau; (void)sigma11; (void)theta0; (void)hist; (void)herr; (void)gram_ms; (void)gram_ab_ms;
   (void)gram_atb_ms; (void)gram_passes; (void)sweeps; (void)it; (void)stop; (void)matvecs; (void)nx;
-  (void)theta_s; (void)wd; (void)w_ready; (void)A; (void)lda; (void)Tb; (void)ATb; (void)GTb; (void)m; (void)n;
+  (void)theta_s; (void)wd; (void)rwd; (void)w_ready; (void)A; (void)lda; (void)Tb; (void)ATb; (void)GTb; (void)m; (void)n;
   (void)k; (void)d; (void)ld; (void)st;
   r = SolveRun{};
   r.tau = tau_in;
@@ -301,7 +310,9 @@ int setup_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, SolveRun& r, double t
   if (p->split) {
     // the split of A (constant through the solve) also flags NaN and infinity
     RL_CUDA(cudaEventRecord(p->ev[8], st));
-    RL_TRY(split_prepare((const double*)A, m, n, lda, p->sprep, p->sprep_bytes, p->err, st));
+    // complex A: the split of its real view (m x 2n, leading dimension 2 lda)
+    const int64_t f = p->csplit ? 2 : 1;
+    RL_TRY(split_prepare((const double*)A, m, f * n, f * lda, p->sprep, p->sprep_bytes, p->err, st));
     RL_CUDA(cudaEventRecord(p->ev[9], st));
   } else {
     RL_TRY(nonfinite_scan_launch<T>(A, m, n, lda, p->err, st));
@@ -365,8 +376,8 @@ int setup_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, SolveRun& r, double t
   if (herr & DEV_ERR_NONFINITE) return RLOBPCG_ERR_NONFINITE;
 
   // Sketch-and-solve start and the initial Rayleigh-Ritz step (Alg. 2)
-  if (p->split) wd = split_w_digits(p->swork, m, n, b);
-  RL_TRY(bcgs2_orth_launch<T>(Tb, n, b, ld, 0, 0, (T*)p->E, 0, st, p->split ? &wd : nullptr, p->err, &w_ready,
+  if (rwd) wd = split_w_digits(p->swork, m, n, b);
+  RL_TRY(bcgs2_orth_launch<T>(Tb, n, b, ld, 0, 0, (T*)p->E, 0, st, rwd ? &wd : nullptr, p->err, &w_ready,
                               p->coop, p->coop_bytes, 0));
   RL_TRY(gram_pass<T>(p, A, lda, Tb, ATb, GTb, 0, nullptr, w_ready));
   RL_TRY(tsqr_impl<T>(ATb, m, b, ld, (T*)p->Rt, p->twork, p->twork_bytes, st));
@@ -413,10 +424,11 @@ int loop_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, SolveRun& r) {
   int& nx = r.nx;
   const double*& theta_s = r.theta_s;
   split::WDigits& wd = r.wd;
+  const bool rwd = p->split && !p->csplit;   // BCGS2 writes the W digits of the real split pass
   bool& w_ready = r.w_ready;
   (void)tau; (void)sigma11; (void)theta0; (void)hist; (void)herr; (void)gram_ms; (void)gram_ab_ms;
   (void)gram_atb_ms; (void)gram_passes; (void)sweeps; (void)it; (void)stop; (void)matvecs; (void)nx;
-  (void)theta_s; (void)wd; (void)w_ready; (void)A; (void)lda; (void)Tb; (void)ATb; (void)GTb; (void)m; (void)n;
+  (void)theta_s; (void)wd; (void)rwd; (void)w_ready; (void)A; (void)lda; (void)Tb; (void)ATb; (void)GTb; (void)m; (void)n;
   (void)k; (void)d; (void)ld; (void)st;
   const int fixed = p->opts.fixed_iters;
   const int max_iter = fixed > 0 ? fixed : p->opts.max_iter;
@@ -468,7 +480,7 @@ int loop_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, SolveRun& r) {
       RL_TRY(scale_rows_launch<T>((const T*)p->Rs, n, a, p->opts.precond == RLOBPCG_PRECOND_DIAG ? (const double*)p->cn2
                                                                                                   : nullptr,
                                   Tb, ld, a, st));
-    RL_TRY(bcgs2_orth_launch<T>(Tb, n, a, ld, a, nx, (T*)p->E, 2, st, p->split ? &wd : nullptr, p->err, &w_ready,
+    RL_TRY(bcgs2_orth_launch<T>(Tb, n, a, ld, a, nx, (T*)p->E, 2, st, rwd ? &wd : nullptr, p->err, &w_ready,
                                 p->coop, p->coop_bytes, p->opts.orth_mode, VL, nl, b));
     const int c = 2 * a + nx;
     cudaEvent_t* e = &p->gev[(size_t)(i % kRing) * 3];
@@ -568,7 +580,7 @@ int loop_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, SolveRun& r) {
       if (fixed <= 0) stop = RLOBPCG_STOP_CONVERGED;
       break;
     }
-    if (p->split) wd = split_w_digits(p->swork, m, n, a);
+    if (rwd) wd = split_w_digits(p->swork, m, n, a);
     w_ready = false;
     // the residual of the kept columns in the compacted layout (the preconditioner's input)
     RL_CUDA(cudaMemcpyAsync(p->theta, thk.data(), a * sizeof(double), cudaMemcpyHostToDevice, st));
@@ -633,10 +645,11 @@ int finish_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, SolveRun& r, double*
   int& nx = r.nx;
   const double*& theta_s = r.theta_s;
   split::WDigits& wd = r.wd;
+  const bool rwd = p->split && !p->csplit;   // BCGS2 writes the W digits of the real split pass
   bool& w_ready = r.w_ready;
   (void)tau; (void)sigma11; (void)theta0; (void)hist; (void)herr; (void)gram_ms; (void)gram_ab_ms;
   (void)gram_atb_ms; (void)gram_passes; (void)sweeps; (void)it; (void)stop; (void)matvecs; (void)nx;
-  (void)theta_s; (void)wd; (void)w_ready; (void)A; (void)lda; (void)Tb; (void)ATb; (void)GTb; (void)m; (void)n;
+  (void)theta_s; (void)wd; (void)rwd; (void)w_ready; (void)A; (void)lda; (void)Tb; (void)ATb; (void)GTb; (void)m; (void)n;
   (void)k; (void)d; (void)ld; (void)st;
   RL_CUDA(cudaEventRecord(p->ev[3], st));
   // keep the history for rlobpcg_history (row 0: the start block's Ritz values)
@@ -760,7 +773,10 @@ int resolve_plan_args(int64_t m, int64_t n, int k, int dtype, const rlobpcg_opts
   return RLOBPCG_OK;
 }
 
-bool uses_split(const rlobpcg_opts& o, int dtype, int b) { return o.gram_split && dtype == RLOBPCG_F64 && b <= 24; }
+// real FP64 with b <= 24; complex128 (its real view, block width 2b) with b <= 12
+bool uses_split(const rlobpcg_opts& o, int dtype, int b) {
+  return o.gram_split && ((dtype == RLOBPCG_F64 && b <= 24) || (dtype == RLOBPCG_C128 && 2 * b <= 24));
+}
 
 // Every device buffer of a plan, in one place: with p == nullptr only the bytes are summed.
 struct PlanAlloc {
@@ -823,11 +839,13 @@ int plan_buffers(PlanAlloc& A_, rlobpcg_plan_s* p, int64_t m, int64_t n, int b, 
     rc = A_(sl, 64); if (rc) return rc;
   }
   if (uses_split(o, dtype, b)) {
-    const size_t sp = split_prep_bytes(m, n), sw = split_work_bytes(m, n, b);
+    const bool cx = dtype == RLOBPCG_C128;
+    const size_t sp = split_prep_bytes(m, cx ? 2 * n : n);
+    const size_t sw = cx ? split_work_bytes_c128(m, n, b) : split_work_bytes(m, n, b);
     if (sp == 0 || sw == 0) return RLOBPCG_ERR_INVALID_ARG;
     RL_B(sprep, sp);
     RL_B(swork, sw);
-    if (p) { p->split = true; p->sprep_bytes = sp; p->swork_bytes = sw; }
+    if (p) { p->split = true; p->csplit = cx; p->sprep_bytes = sp; p->swork_bytes = sw; }
     *gwork = 0;
   } else {
     *gwork = gram_workspace_bytes(m, n, b, dtype);

@@ -94,6 +94,9 @@ _SIGS = {
     "rlobpcg_gram_split_workspace_size": (c_size_t, [c_int64, c_int64, c_int]),
     "rlobpcg_gram_split": (c_int, [c_void_p, c_int64, c_int64, c_void_p, c_int, c_int64, c_void_p, c_int64, c_void_p,
                                    c_int64, c_void_p, c_size_t, c_void_p]),
+    "rlobpcg_gram_split_c128_workspace_size": (c_size_t, [c_int64, c_int64, c_int]),
+    "rlobpcg_gram_split_c128": (c_int, [c_void_p, c_int64, c_int64, c_void_p, c_int, c_int64, c_void_p, c_int64,
+                                        c_void_p, c_int64, c_void_p, c_size_t, c_void_p]),
     "rlobpcg_tsqr": (c_int, [c_void_p, c_int64, c_int, c_int64, c_int, c_void_p, c_void_p, c_size_t, c_void_p]),
     "rlobpcg_tsqr_workspace_size": (c_size_t, [c_int64, c_int, c_int]),
     "rlobpcg_plan_device_bytes": (c_size_t, [c_void_p]),
@@ -239,6 +242,16 @@ def rlobpcg_gram_split(prep: int, m: int, n: int, W: int, b: int, ldw: int, AW: 
                        work: int, work_bytes: int, stream: int = 0) -> None:
     _check("rlobpcg_gram_split", load().rlobpcg_gram_split(prep, m, n, W, b, ldw, AW, ldaw, G, ldg, work, work_bytes,
                                                            stream))
+
+
+def rlobpcg_gram_split_c128_workspace_size(m: int, n: int, b: int) -> int:
+    return load().rlobpcg_gram_split_c128_workspace_size(m, n, b)
+
+
+def rlobpcg_gram_split_c128(prep: int, m: int, n: int, W: int, b: int, ldw: int, AW: int, ldaw: int, G: int,
+                            ldg: int, work: int, work_bytes: int, stream: int = 0) -> None:
+    _check("rlobpcg_gram_split_c128", load().rlobpcg_gram_split_c128(prep, m, n, W, b, ldw, AW, ldaw, G, ldg, work,
+                                                                      work_bytes, stream))
 
 
 def rlobpcg_tsqr_workspace_size(m: int, c: int, dtype: int) -> int:

@@ -45,6 +45,12 @@ def test_roofline_takes_the_slower_roof_as_the_bound():
     # FP64 path: FP64 flops against the derived FP64 peak
     r = bench.gram_roofline(200000, 300, 3, True, False, 3.0e-3, peaks, 1.259, "derived")
     assert r["bound"] == "alu" and r["frac"] == pytest.approx(16 * 200000 * 300 * 3 / 3.0e-3 / 1e12 / 1.259)
+    # complex split path: the real pass on the real view (m x 2n, block 2b), 16-byte elements
+    r = bench.gram_roofline(200000, 300, 3, True, True, 0.4e-3, peaks, 1.259, "derived")
+    tc = r if r["bound"] == "tensor" else r["other"]
+    hb = r if r["bound"] == "hbm" else r["other"]
+    assert tc["flops_per_pass"] == bench.pass_tensor_flops(200000, 600, 6) == 4 * bench.pass_tensor_flops(200000, 300, 3)
+    assert hb["bytes_per_pass"] == 16 * 200000 * 300 + 16 * 200000 * 3
 
 
 def _fake_tree(tmp_path, src_text, summary_sha, per=8.2):
