@@ -461,6 +461,221 @@ __device__ int jacobi_mixed16(double* X, double* V, int c, int N, double tol, do
   return sweeps;
 }
 
+// ---- complex c <= 16: the preconditioned scheme of jacobi_mixed16 -------------------------
+// Column pair (p, q) with a = ||x_p||^2, b = ||x_q||^2, g = x_p^H x_q: the phase e = g / |g|
+// turns it into the real problem of jacobi_pairs16 on (|g|, a, b), and the rotation
+//     x_p <- c x_p - conj(s e) x_q,   x_q <- s e x_p + c x_q      (c = 1 / sqrt(1 + t^2), s = c t)
+// is unitary to FP64 rounding for any t; V takes the same rotation. FP64 sums, FP32 angle (as in
+// jacobi_pairs16), two pairs per warp (a half-warp each, lane = row).
+__device__ int jacobi_pairs16_c(cd* X, cd* V, int c, int N, double tol, double tiny2, const uint8_t* sched,
+                                int max_sweeps) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
+  const int half = lane >> 4, row = lane & 15;
+  const double tol2 = tol * tol;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    int rotated = 0;
+    for (int r = 0; r < N - 1; ++r) {
+      for (int p0 = 2 * warp; p0 < N / 2; p0 += 2 * nw) {   // warp-uniform
+        const int pi = p0 + half;
+        const int code = pi < N / 2 ? sched[r * 8 + pi] : 0xFF;
+        const int pp = code & 15, qq = code >> 4;
+        const bool valid = code != 0xFF;
+        const bool live = valid && row < c;
+        const cd xp = live ? X[pp * c + row] : zero_<cd>(), xq = live ? X[qq * c + row] : zero_<cd>();
+        double a = abs2_(xp), bb = abs2_(xq);
+        cd g = madc_(xp, xq, zero_<cd>());
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) {
+          a += __shfl_xor_sync(0xffffffffu, a, o);
+          bb += __shfl_xor_sync(0xffffffffu, bb, o);
+          g = add_(g, shfl_xor_(g, o));
+        }
+        const double g2 = abs2_(g);
+        bool rot = valid && (g2 > tol2 * a * bb) && a > tiny2 && bb > tiny2;
+        double cs = 1.0, sn = 0.0;
+        cd e = from_real<cd>(1.0);
+        {
+          const double mx = rot ? fmax(a, bb) : 1.0;
+          const int ex = (int)((__double_as_longlong(mx) >> 52) & 0x7ff) - 1023;
+          const double sc = __longlong_as_double((long long)(1023 - imax(-1022, imin(1022, ex))) << 52);
+          const float df = (float)((bb - a) * sc), gf = sqrtf((float)(g2 * sc * sc));
+          const float tf = copysignf(2.0f * gf, df) / (fabsf(df) + sqrtf(df * df + 4.0f * gf * gf));
+          rot = rot && fabsf(tf) > 2.220446049250313e-16f;
+          const double t = rot ? (double)tf : 0.0;
+          cs = rsqrt(fma(t, t, 1.0));
+          sn = cs * t;
+          if (rot) e = scale_(g, rsqrt(g2));
+        }
+        const cd se = scale_(e, sn), sec = conj_(se);
+        if (live) {
+          const cd vp = V[pp * c + row], vq = V[qq * c + row];
+          X[pp * c + row] = sub_(scale_(xp, cs), mul_(sec, xq));
+          X[qq * c + row] = add_(mul_(se, xp), scale_(xq, cs));
+          V[pp * c + row] = sub_(scale_(vp, cs), mul_(sec, vq));
+          V[qq * c + row] = add_(mul_(se, vp), scale_(vq, cs));
+        }
+        rotated |= rot;
+      }
+      __syncthreads();
+    }
+    if (!__syncthreads_or(rotated)) { ++sweep; break; }
+  }
+  return sweep;
+}
+
+// jacobi_pending for complex columns
+__device__ bool jacobi_pending_c(const cd* X, int c, double tol, double tiny2) {
+  const double tol2 = tol * tol;
+  int bad = 0;
+  for (int e = threadIdx.x; e < c * c; e += blockDim.x) {
+    const int i = e / c, j = e % c;
+    if (j <= i) continue;
+    double a = 0, bb = 0;
+    cd g = zero_<cd>();
+    for (int r = 0; r < c; ++r) {
+      const cd x = X[i * c + r], y = X[j * c + r];
+      a += abs2_(x);
+      bb += abs2_(y);
+      g = madc_(x, y, g);
+    }
+    const double g2 = abs2_(g);
+    if ((g2 > tol2 * a * bb) && a > tiny2 && bb > tiny2) {
+      const double d = bb - a;
+      const double t = 2.0 * sqrt(g2) / (fabs(d) + sqrt(d * d + 4.0 * g2));
+      bad |= t > 2.220446049250313e-16;
+    }
+  }
+  return __syncthreads_or(bad) != 0;
+}
+
+// FP32 sweeps for complex c <= 16 (same layout and rule as jacobi_pairs16_f32)
+__device__ int jacobi_pairs16_f32_c(cf* X, cf* V, int c, int N, float tol, float tiny2, const uint8_t* sched) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
+  const int half = lane >> 4, row = lane & 15;
+  const float tol2 = tol * tol;
+  int sweep = 0;
+  for (; sweep < 12; ++sweep) {
+    int rotated = 0;
+    for (int r = 0; r < N - 1; ++r) {
+      for (int p0 = 2 * warp; p0 < N / 2; p0 += 2 * nw) {   // warp-uniform
+        const int pi = p0 + half;
+        const int code = pi < N / 2 ? sched[r * 8 + pi] : 0xFF;
+        const int pp = code & 15, qq = code >> 4;
+        const bool valid = code != 0xFF;
+        const bool live = valid && row < c;
+        const cf zf = {0.f, 0.f};
+        const cf xp = live ? X[pp * c + row] : zf, xq = live ? X[qq * c + row] : zf;
+        float a = abs2_(xp), bb = abs2_(xq);
+        cf g = madc_(xp, xq, zf);
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) {
+          a += __shfl_xor_sync(0xffffffffu, a, o);
+          bb += __shfl_xor_sync(0xffffffffu, bb, o);
+          g = add_(g, shfl_xor_(g, o));
+        }
+        const float g2 = abs2_(g), ga = sqrtf(g2);
+        const float d = bb - a;
+        const float tf = copysignf(2.0f * ga, d) / (fabsf(d) + sqrtf(d * d + 4.0f * g2));
+        const bool rot = valid && (g2 > tol2 * a * bb) && a > tiny2 && bb > tiny2 && fabsf(tf) > 1.0e-12f;
+        const float t = rot ? tf : 0.0f;
+        const float cs = rsqrtf(fmaf(t, t, 1.0f));
+        const float sn = cs * t;
+        const cf e = rot ? scale_(g, 1.0f / ga) : cf{1.0f, 0.0f};
+        const cf se = scale_(e, sn), sec = conj_(se);
+        if (live && rot) {
+          const cf vp = V[pp * c + row], vq = V[qq * c + row];
+          X[pp * c + row] = sub_(scale_(xp, cs), mul_(sec, xq));
+          X[qq * c + row] = add_(mul_(se, xp), scale_(xq, cs));
+          V[pp * c + row] = sub_(scale_(vp, cs), mul_(sec, vq));
+          V[qq * c + row] = add_(mul_(se, vp), scale_(vq, cs));
+        }
+        rotated |= rot;
+      }
+      __syncthreads();
+    }
+    if (!__syncthreads_or(rotated)) { ++sweep; break; }
+  }
+  return sweep;
+}
+
+// Out = In * M for complex c x c column-major matrices in shared memory (all threads)
+__device__ void small_matmul_c(const cd* In, const cd* M, cd* Out, int c) {
+  for (int o = threadIdx.x; o < c * c; o += blockDim.x) {
+    const int j = o / c, r = o % c;
+    cd s0 = zero_<cd>(), s1 = zero_<cd>();
+    int i = 0;
+    for (; i + 1 < c; i += 2) {
+      s0 = mad_(In[i * c + r], M[j * c + i], s0);
+      s1 = mad_(In[(i + 1) * c + r], M[j * c + i + 1], s1);
+    }
+    if (i < c) s0 = mad_(In[i * c + r], M[j * c + i], s0);
+    Out[o] = add_(s0, s1);
+  }
+}
+
+// jacobi_mixed16 for complex c <= 16: FP32 sweeps on the scaled complex64 copy, V made unitary
+// in FP64 by two Newton-Schulz steps V <- V (3 I - V^H V) / 2, X <- X V, FP64 sweeps from there.
+__device__ int jacobi_mixed16_c(cd* X, cd* V, int c, int N, double tol, double tiny2, double mx0, cf* Xf, cf* Vf,
+                                cd* Ms, cd* Ws) {
+  const int tid = threadIdx.x, NT = blockDim.x;
+  const int ex = (int)((__double_as_longlong(fmax(mx0, 1e-300)) >> 52) & 0x7ff) - 1023;
+  const double sc = __longlong_as_double((long long)(1023 - imax(-1022, imin(1022, ex))) << 52);
+  for (int i = tid; i < c * c; i += NT) {
+    Xf[i] = cvt_<cf, cd>(scale_(X[i], sc));
+    Vf[i] = (i / c == i % c) ? cf{1.0f, 0.0f} : cf{0.0f, 0.0f};
+  }
+  __syncthreads();
+  const float tol32 = (float)imax(c, 4) * 1.1920929e-7f;
+  const float tiny32 = (float)(tiny2 * sc * sc);
+  __shared__ uint8_t sched[15 * 8];
+  for (int e = tid; e < (N - 1) * 8; e += NT) {
+    const int r = e / 8, i = e % 8;
+    uint8_t code = 0xFF;
+    if (i < N / 2) {
+      int pp = rr_slot(i, r, N), qq = rr_slot(N - 1 - i, r, N);
+      if (pp > qq) { const int t = pp; pp = qq; qq = t; }
+      if (qq < c) code = (uint8_t)(pp | (qq << 4));
+    }
+    sched[e] = code;
+  }
+  __syncthreads();
+  jacobi_pairs16_f32_c(Xf, Vf, c, N, tol32, tiny32, sched);
+  for (int i = tid; i < c * c; i += NT) V[i] = cvt_<cd, cf>(Vf[i]);
+  __syncthreads();
+  for (int step = 0; step < 2; ++step) {
+    // Ms = (3 I - V^H V) / 2
+    for (int o = tid; o < c * c; o += NT) {
+      const int i = o / c, j = o % c;
+      cd s0 = zero_<cd>(), s1 = zero_<cd>();
+      int k = 0;
+      for (; k + 1 < c; k += 2) {
+        s0 = madc_(V[j * c + k], V[i * c + k], s0);
+        s1 = madc_(V[j * c + k + 1], V[i * c + k + 1], s1);
+      }
+      if (k < c) s0 = madc_(V[j * c + k], V[i * c + k], s0);
+      const cd s = add_(s0, s1);   // (V^H V)(j, i), stored at column i, row j
+      Ms[o] = cd{(i == j ? 1.5 : 0.0) - 0.5 * s.x, -0.5 * s.y};
+    }
+    __syncthreads();
+    small_matmul_c(V, Ms, Ws, c);
+    __syncthreads();
+    for (int i = tid; i < c * c; i += NT) V[i] = Ws[i];
+    __syncthreads();
+  }
+  small_matmul_c(X, V, Ws, c);
+  __syncthreads();
+  for (int i = tid; i < c * c; i += NT) X[i] = Ws[i];
+  __syncthreads();
+  int sweeps = 0;
+  for (int round = 0; round < 30; ++round) {
+    const int s2 = jacobi_pairs16_c(X, V, c, N, tol, tiny2, sched, 2);
+    sweeps += s2;
+    if (s2 < 2 || !jacobi_pending_c(X, c, tol, tiny2)) break;
+  }
+  return sweeps;
+}
+
 // ---- real c in (16, 32]: the same preconditioned scheme with one pair per warp -------------
 // Round-robin schedule for N <= 32 slots: pair i of round r is coded pp | qq << 8 (pp < qq), or
 // 0xFFFF when a member is the padding column c (odd c).
@@ -697,6 +912,13 @@ __device__ void rr_small_cta(unsigned char* smem_raw, const T* __restrict__ Rt, 
         __shared__ int rflag[16];
         sweep = jacobi_mixed32(X, V, c, N, tol, tiny2, mx0, Xf, Vf, Ms, Ws2, sched32, dots, rotp, rflag);
       }
+      fast = true;
+    }
+  } else {
+    if (c <= 16) {
+      __shared__ cf Xc[16 * 16], Vc[16 * 16];
+      __shared__ cd Mc[16 * 16], Wc[16 * 16];
+      sweep = jacobi_mixed16_c(X, V, c, N, tol, tiny2, mx0, Xc, Vc, Mc, Wc);
       fast = true;
     }
   }
@@ -1841,7 +2063,7 @@ int rr_small_launch(const T* Rt, int c, int b, double* theta, T* K, size_t k_cap
   const size_t smem = rr_small_smem<T>(c, b);
   RL_TRY(allow_dynamic_smem(rr_small_kernel<T>, smem));
   int threads = min(1024, max(64, ((c + 1) / 2) * 32));
-  if (std::is_same<T, double>::value && c <= 16) threads = 128;   // two Jacobi pairs per warp
+  if (c <= 16) threads = 128;   // two Jacobi pairs per warp (real and complex)
   else if (std::is_same<T, double>::value && c <= 32) threads = 512;   // a warp per pair, 16 pairs
   rr_small_kernel<T><<<1, threads, smem, st>>>(Rt, c, b, theta, K, info);
   RL_CHECK_LAUNCH();
