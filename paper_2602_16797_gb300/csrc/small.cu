@@ -1162,7 +1162,26 @@ __global__ void trimul_kernel(const S* __restrict__ L, int n, const T* __restric
     T acc[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) acc[q] = zero_<T>();
-    for (int l = lo + lane; l <= hi; l += 32) {
+    // four steps of a lane's walk per trip: their loads are issued together (the latency of
+    // L2 loads, not the FP64 work, bounds this kernel); each lane still adds its terms in
+    // ascending l, so the sums are the same as one step at a time
+    int l = lo + lane;
+    for (; l + 96 <= hi; l += 128) {
+      T lk[4], xv[4][8];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        lk[u] = cvt_<T, S>(conj_l ? conj_(Lk[l + 32 * u]) : Lk[l + 32 * u]);
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          xv[u][q] = (c0 + q < b) ? X[(int64_t)(l + 32 * u) * ldx + c0 + q] : zero_<T>();
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if (c0 + q < b) acc[q] = mad_(lk[u], xv[u][q], acc[q]);
+    }
+    for (; l <= hi; l += 32) {
       const T lk = cvt_<T, S>(conj_l ? conj_(Lk[l]) : Lk[l]);
 #pragma unroll
       for (int q = 0; q < 8; ++q)
@@ -2101,12 +2120,12 @@ template int residual_launch<cd>(const cd*, const cd*, int, int, int64_t, const 
 template <class T, class S>
 int precond_launch(const S* Rinv_r, const S* Rinv_c, int n, int b, const T* Rs, T* Y, T* Tb, int64_t ld, int wo,
                    cudaStream_t st) {
-  const int blocks = (n * 32 + 255) / 256;
+  const int blocks = (n * 32 + 127) / 128;   // a warp per row, four per CTA (rows over more SMs)
   // Y(k) = sum_{l <= k} conj(Rinv(l, k)) Rs(l): row k of Rinv^H = conj(column k of Rinv)
-  trimul_kernel<S, T><<<blocks, 256, 0, st>>>(Rinv_c, n, Rs, b, b, Y, b, 1, 1);
+  trimul_kernel<S, T><<<blocks, 128, 0, st>>>(Rinv_c, n, Rs, b, b, Y, b, 1, 1);
   RL_CHECK_LAUNCH();
   // W(k) = sum_{l >= k} Rinv(k, l) Y(l)
-  trimul_kernel<S, T><<<blocks, 256, 0, st>>>(Rinv_r, n, Y, b, b, Tb + wo, ld, 0, 0);
+  trimul_kernel<S, T><<<blocks, 128, 0, st>>>(Rinv_r, n, Y, b, b, Tb + wo, ld, 0, 0);
   RL_CHECK_LAUNCH();
   return RLOBPCG_OK;
 }
