@@ -396,7 +396,7 @@ size_t rlobpcg_gram_workspace_size(int64_t m, int64_t n, int b, int dtype);
  *   - The call is synchronous: it reads the device error word back and synchronises `stream`
  *     before it returns.
  *   - The first call on a device looks up the buffer's device address (once per device, with
- *     that device current); make that first call before any stream capture.
+ *     that device current).
  *   - All calls share the one buffer, which keeps the last call's contents: calls that overlap
  *     on the GPU (other streams, other threads) race and must be serialised by the caller.
  *   - Problems whose partials need more than 16 MiB (about 152 * n * b * 8 bytes for real A,
