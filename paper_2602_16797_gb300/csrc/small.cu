@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(256) tsqr_level_kernel(const T* __restrict__ X
   const int NT = blockDim.x;
   const int tid = threadIdx.x;
   T* S = reinterpret_cast<T*>(smem_raw);       // (c + CH) x c row-major
-  __shared__ T sh_tau, sh_inv, sh_beta;
+  __shared__ T s_d[64], s_fv[64];              // per active column: its sum d, then f / (alpha - beta)
   (void)RP;
 
   const int64_t r_begin = (int64_t)blockIdx.x * rpc;
@@ -119,25 +119,30 @@ __global__ void __launch_bounds__(256) tsqr_level_kernel(const T* __restrict__ X
         d = add_(a0, a1);
       }
       for (int o = L >> 1; o > 0; o >>= 1) d = add_(d, shfl_xor_(d, o));
-      if (q == 0 && p == 0) {
-        T tau, beta, inv_ab;
-        householder_scalars(S[(size_t)j * c + j], re_(d), &tau, &beta, &inv_ab);
-        sh_tau = tau; sh_inv = inv_ab; sh_beta = beta;
+      if (on && p == 0) s_d[q] = d;
+      __syncthreads();
+      // Warp 0 forms the reflector (lane 0) and then f and f / (alpha - beta) of every active
+      // column, a lane per column: done by the column groups themselves, these few FP64
+      // instructions would be issued by every warp at one active lane in L.
+      if (tid < 32) {
+        T tau = zero_<T>(), beta = zero_<T>(), inv_ab = zero_<T>();
+        if (tid == 0) householder_scalars(S[(size_t)j * c + j], re_(s_d[0]), &tau, &beta, &inv_ab);
+        tau = shfl_(tau, 0);
+        inv_ab = shfl_(inv_ab, 0);
+        for (int l = 1 + tid; l < a; l += 32) {
+          T* rj = S + (size_t)j * c + j + l;
+          const T f = mul_(conj_(tau), add_(*rj, mul_(conj_(inv_ab), s_d[l])));
+          s_fv[l] = mul_(inv_ab, f);             // v_r = S[r][j] / (alpha - beta) folded into f
+          *rj = sub_(*rj, f);
+        }
+        if (tid == 0) S[(size_t)j * c + j] = beta;
       }
       __syncthreads();
-      // f and f / (alpha - beta) once per column (lane p = 0), then passed to the column's lanes
-      T fv = zero_<T>();
-      if (on && q > 0 && p == 0) {
-        const T inv_ab = sh_inv;
-        const T f = mul_(conj_(sh_tau), add_(S[(size_t)j * c + cc], mul_(conj_(inv_ab), d)));
-        fv = mul_(inv_ab, f);                    // v_r = S[r][j] / (alpha - beta) folded into f
-        S[(size_t)j * c + cc] = sub_(S[(size_t)j * c + cc], f);
-      }
-      fv = shfl_(fv, (threadIdx.x & 31) & ~(L - 1));
-      if (on && q > 0)
+      if (on && q > 0) {
+        const T fv = s_fv[q];
         for (int r = rs + p; r < SRu; r += L)
           S[(size_t)r * c + cc] = sub_(S[(size_t)r * c + cc], mul_(S[(size_t)r * c + j], fv));
-      if (q == 0 && p == 0) S[(size_t)j * c + j] = sh_beta;
+      }
       __syncthreads();
     }
     if (r_end <= r_begin) break;
