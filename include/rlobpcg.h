@@ -175,6 +175,20 @@ int rlobpcg_solve(rlobpcg_plan_t plan, const void* A, int64_t lda, double tol, d
                   void* V, void* U, double* resid, rlobpcg_info* info);
 
 /* Release a plan and its device workspace. NULL is accepted. */
+/* Asynchronous form of rlobpcg_solve (same arguments and results). It returns at once: 0 once the
+ * solve has started, INVALID_ARG (bad arguments, or a solve of this plan already in flight) or OOM
+ * without starting one. The solve -- its work on the plan's stream and the stopping rule that the
+ * host evaluates between iterations -- runs on a host thread of the library with the caller's
+ * current device, so the calling thread is free meanwhile. A, the outputs and info must stay valid,
+ * and the plan must not be used (solve, history, batch), until rlobpcg_solve_wait returns.
+ * rlobpcg_plan_destroy waits for a solve still in flight. */
+int rlobpcg_solve_async(rlobpcg_plan_t plan, const void* A, int64_t lda, double tol, double* sigma, void* V,
+                        void* U, double* resid, rlobpcg_info* info);
+
+/* Waits for the plan's asynchronous solve; returns what rlobpcg_solve would have returned, with its
+ * message in rlobpcg_last_error() on the calling thread. INVALID_ARG when no solve is in flight. */
+int rlobpcg_solve_wait(rlobpcg_plan_t plan);
+
 int rlobpcg_plan_destroy(rlobpcg_plan_t plan);
 
 /* Per-iteration history of the plan's last solve (host memory, row-major, b columns, b = the block

@@ -104,6 +104,11 @@ int nonfinite_scan_launch(const T* A, int64_t m, int n, int64_t lda, int* err, c
 using namespace rl;
 
 struct rlobpcg_plan_s {
+  // rlobpcg_solve_async: the solve runs on this host thread until rlobpcg_solve_wait joins it
+  std::thread async_th;
+  bool async_busy = false;
+  int async_rc = 0;
+  std::string async_err;
   int64_t m = 0, n = 0;
   int k = 0, b = 0, d = 0, dtype = 0;
   rlobpcg_opts opts{};
@@ -931,8 +936,56 @@ extern "C" int rlobpcg_plan(rlobpcg_plan_t* out, int64_t m, int64_t n, int k, in
   return RLOBPCG_OK;
 }
 
+static int async_in_flight(rlobpcg_plan_t p) {
+  rl::set_last_error("the plan has an asynchronous solve in flight: call rlobpcg_solve_wait first", __FILE__, __LINE__);
+  (void)p;
+  return RLOBPCG_ERR_INVALID_ARG;
+}
+
+static int solve_entry(rlobpcg_plan_t p, const void* A, int64_t lda, double tol, double* sigma, void* V, void* U,
+                       double* resid, rlobpcg_info* info);
+
 extern "C" int rlobpcg_solve(rlobpcg_plan_t p, const void* A, int64_t lda, double tol, double* sigma, void* V, void* U,
                              double* resid, rlobpcg_info* info) {
+  if (p && p->async_busy) return async_in_flight(p);
+  return solve_entry(p, A, lda, tol, sigma, V, U, resid, info);
+}
+
+extern "C" int rlobpcg_solve_async(rlobpcg_plan_t p, const void* A, int64_t lda, double tol, double* sigma, void* V,
+                                   void* U, double* resid, rlobpcg_info* info) {
+  if (!p || !A || !sigma || !V || lda < p->n) return RLOBPCG_ERR_INVALID_ARG;
+  if (p->async_busy) return async_in_flight(p);
+  int dev = 0;
+  RL_CUDA(cudaGetDevice(&dev));
+  p->async_rc = 0;
+  p->async_err.clear();
+  try {
+    p->async_th = std::thread([=]() {
+      // the solve's launches go to the plan's stream from this thread, on the caller's device
+      int rc = cudaSetDevice(dev) == cudaSuccess ? RLOBPCG_OK : RLOBPCG_ERR_CUDA;
+      if (rc == RLOBPCG_OK) rc = solve_entry(p, A, lda, tol, sigma, V, U, resid, info);
+      else rl::set_last_error("rlobpcg_solve_async: cudaSetDevice failed on the solve thread", __FILE__, __LINE__);
+      p->async_rc = rc;
+      if (rc < 0) p->async_err = rlobpcg_last_error();
+    });
+  } catch (...) {
+    rl::set_last_error("rlobpcg_solve_async: could not start the solve thread", __FILE__, __LINE__);
+    return RLOBPCG_ERR_OOM;
+  }
+  p->async_busy = true;
+  return RLOBPCG_OK;
+}
+
+extern "C" int rlobpcg_solve_wait(rlobpcg_plan_t p) {
+  if (!p || !p->async_busy) return RLOBPCG_ERR_INVALID_ARG;
+  p->async_th.join();
+  p->async_busy = false;
+  if (p->async_rc < 0) rl::set_last_error_text(p->async_err.c_str());
+  return p->async_rc;
+}
+
+static int solve_entry(rlobpcg_plan_t p, const void* A, int64_t lda, double tol, double* sigma, void* V, void* U,
+                       double* resid, rlobpcg_info* info) {
   if (!p || !A || !sigma || !V || lda < p->n) return RLOBPCG_ERR_INVALID_ARG;
   const double tau = tol >= 0 ? tol : p->opts.tau;
   const void* Ause = A;
@@ -977,6 +1030,10 @@ extern "C" int rlobpcg_solve(rlobpcg_plan_t p, const void* A, int64_t lda, doubl
 
 extern "C" int rlobpcg_plan_destroy(rlobpcg_plan_t p) {
   if (!p) return RLOBPCG_OK;
+  if (p->async_busy) {   // a solve still in flight finishes first
+    p->async_th.join();
+    p->async_busy = false;
+  }
   cudaStreamSynchronize(p->st);
   free_plan(p);
   delete p;
@@ -987,6 +1044,7 @@ extern "C" size_t rlobpcg_plan_device_bytes(rlobpcg_plan_t p) { return p ? p->by
 
 extern "C" int rlobpcg_history(rlobpcg_plan_t p, double* theta, double* resnorm, int cap_rows, int* rows, int* block) {
   if (!p || !rows || cap_rows < 0) return RLOBPCG_ERR_INVALID_ARG;
+  if (p->async_busy) return async_in_flight(p);
   *rows = p->last_rows;
   if (block) *block = p->b;
   const int n = std::min(cap_rows, p->last_rows);
@@ -1731,6 +1789,7 @@ extern "C" int rlobpcg_solve_batch(int count, rlobpcg_plan_t* plans, const void*
   for (int i = 0; i < count; ++i) {
     rlobpcg_plan_s* p = plans[i];
     if (!p || !A[i] || !sigma[i] || !V[i] || lda[i] < p->n || !is_device_ptr(A[i])) return RLOBPCG_ERR_INVALID_ARG;
+    if (p->async_busy) return async_in_flight(p);
     for (int j = 0; j < i; ++j)
       if (plans[j] == p) return RLOBPCG_ERR_INVALID_ARG;   // one solve per plan
     if (!batch_eligible(p, &why)) {

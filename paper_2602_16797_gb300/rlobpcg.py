@@ -76,6 +76,9 @@ _SIGS = {
                              c_void_p]),
     "rlobpcg_solve": (c_int, [c_void_p, c_void_p, c_int64, c_double, c_void_p, c_void_p, c_void_p, c_void_p,
                               ctypes.POINTER(rlobpcg_info)]),
+    "rlobpcg_solve_async": (c_int, [c_void_p, c_void_p, c_int64, c_double, c_void_p, c_void_p, c_void_p, c_void_p,
+                                    ctypes.POINTER(rlobpcg_info)]),
+    "rlobpcg_solve_wait": (c_int, [c_void_p]),
     "rlobpcg_plan_destroy": (c_int, [c_void_p]),
     "rlobpcg_status_string": (c_char_p, [c_int]),
     "rlobpcg_last_error": (c_char_p, []),
@@ -188,6 +191,18 @@ def rlobpcg_solve(plan: int, A: int, lda: int, tol: float, sigma: int, V: int, U
                   resid: int | None = None, info: rlobpcg_info | None = None) -> int:
     rc = load().rlobpcg_solve(plan, A, lda, tol, sigma, V, U, resid, ctypes.byref(info) if info is not None else None)
     return _check("rlobpcg_solve", rc, ok=(RLOBPCG_OK, RLOBPCG_NOT_CONVERGED))
+
+
+def rlobpcg_solve_async(plan: int, A: int, lda: int, tol: float, sigma: int, V: int, U: int | None = None,
+                        resid: int | None = None, info: rlobpcg_info | None = None) -> None:
+    """Start the solve on a library thread; the buffers (and info) must outlive rlobpcg_solve_wait."""
+    rc = load().rlobpcg_solve_async(plan, A, lda, tol, sigma, V, U, resid,
+                                    ctypes.byref(info) if info is not None else None)
+    _check("rlobpcg_solve_async", rc)
+
+
+def rlobpcg_solve_wait(plan: int) -> int:
+    return _check("rlobpcg_solve_wait", load().rlobpcg_solve_wait(plan), ok=(RLOBPCG_OK, RLOBPCG_NOT_CONVERGED))
 
 
 def rlobpcg_plan_destroy(plan: int) -> None:

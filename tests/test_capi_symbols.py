@@ -57,3 +57,6 @@ def test_host_only_calls(lib):
     assert rl.load().rlobpcg_plan(ctypes.byref(h), 100, 10, 1, 7, None, None) == rl.RLOBPCG_ERR_INVALID_ARG  # dtype
     assert rl.load().rlobpcg_sketch(None, 10, 10, 10, 0, 8, 8, 0, 0, None, None) == rl.RLOBPCG_ERR_INVALID_ARG
     assert rl.load().rlobpcg_gram(None, 10, 10, 10, 0, None, 1, 1, None, 1, None, 1, None, 0, None) == rl.RLOBPCG_ERR_INVALID_ARG
+    # the asynchronous solve's entry points check their arguments before starting a thread
+    assert rl.load().rlobpcg_solve_wait(None) == rl.RLOBPCG_ERR_INVALID_ARG
+    assert rl.load().rlobpcg_solve_async(None, None, 0, -1.0, None, None, None, None, None) == rl.RLOBPCG_ERR_INVALID_ARG
