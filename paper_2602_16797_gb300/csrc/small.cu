@@ -2013,11 +2013,8 @@ __global__ void nonfinite_scan_kernel(const T* A, int64_t m, int n, int64_t lda,
 // ------------------------------------------------------------------------------------------
 // host launchers
 // ------------------------------------------------------------------------------------------
-static int tsqr_chunk(int c, size_t esz) {
-  int ch = (int)(100 * 1024 / ((size_t)c * esz)) - c;   // ~100 KB of smem: 2 CTAs per SM
-  ch = imax(32, imin(512, ch));
-  return ch;
-}
+// the most rows of one chunk: [R; chunk] in ~100 KB of shared memory (2 CTAs per SM)
+static int tsqr_chunk(int c, size_t esz) { return imax(32, (int)(100 * 1024 / ((size_t)c * esz)) - c); }
 
 static int pow2_at_least(int x) { int p = 1; while (p < x) p <<= 1; return p; }
 
@@ -2025,11 +2022,12 @@ static int tsqr_rp(int c) { return imin(32, 256 / pow2_at_least(c)); }
 
 static size_t tsqr_level_smem(int c, int CH, size_t esz) { return (size_t)(c + CH) * c * esz; }
 
-// Level 1: up to two CTAs per SM (one chunk each when m allows): the level is bound by FP64
-// issue (about m c^2 FMAs), so all SMs' FP64 pipes take part.
+// Level 1: two CTAs per SM, each with at least 256 rows: the level is bound by FP64 issue (about
+// m c^2 FMAs), so all SMs' FP64 pipes take part, while short blocks keep few R factors to merge.
 static int64_t tsqr_level1_ctas(int64_t m, int c, size_t esz) {
-  const int CH = tsqr_chunk(c, esz);
-  return imin<int64_t>(2 * (int64_t)num_sms(), imax<int64_t>(1, (m + CH - 1) / CH));
+  (void)c;
+  (void)esz;
+  return imin<int64_t>(2 * (int64_t)num_sms(), imax<int64_t>(1, (m + 255) / 256));
 }
 
 static constexpr int kTsqrFan = 20;   // R factors merged per CTA in the upper levels
@@ -2045,16 +2043,19 @@ int tsqr_impl(const T* X, int64_t m, int c, int64_t ldx, T* R, void* work, size_
   if (c < 1 || c > 64) return RLOBPCG_ERR_INVALID_ARG;
   const size_t esz = sizeof(T);
   if (work_bytes < tsqr_workspace_bytes(m, c, esz)) return RLOBPCG_ERR_INVALID_ARG;
-  const int CH = tsqr_chunk(c, esz);
   const int RP = tsqr_rp(c);
-  const size_t smem = tsqr_level_smem(c, CH, esz);
-  RL_TRY(allow_dynamic_smem(tsqr_level_kernel<T>, smem));
   const int64_t g1 = tsqr_level1_ctas(m, c, esz);
   const size_t half = (((size_t)g1 * c * c * esz + 255) & ~(size_t)255);
   T* buf[2] = {(T*)work, (T*)((unsigned char*)work + half)};
   int64_t rpc = (m + g1 - 1) / g1;
   int64_t grid = (m + rpc - 1) / rpc;
   if (grid < 1) grid = 1;
+  // a CTA's rows in equal chunks of at most tsqr_chunk rows (each chunk costs a fixed serial
+  // part per column, so no short remainder chunk)
+  const int64_t nch = (rpc + tsqr_chunk(c, esz) - 1) / tsqr_chunk(c, esz);
+  const int CH = (int)imax<int64_t>(1, (rpc + nch - 1) / nch);
+  const size_t smem = tsqr_level_smem(c, CH, esz);
+  RL_TRY(allow_dynamic_smem(tsqr_level_kernel<T>, smem));
   tsqr_level_kernel<T><<<(int)grid, 256, smem, st>>>(X, m, c, ldx, rpc, CH, RP, buf[0]);
   RL_CHECK_LAUNCH();
   int cur = 0;
