@@ -276,6 +276,14 @@ def oracle_rate_one_thread(workload, iters, timeout=300):
 
 # --------------------------------------------------------------------------------- roofline helpers
 
+def sigma_err(sig, truth, sigma11):
+    """max_j |sigma_j - sigma_true_j| / max(sigma_true_j, Sigma~(1,1) 2^-52): relative to the planted
+    value, or, where that is below what a backward-stable solve resolves (an exact nullspace has
+    sigma_true = 0), in units of Sigma~(1,1) 2^-52."""
+    floor = max(float(sigma11), 1e-300) * 2.0 ** -52
+    return float(np.max(np.abs(np.asarray(sig) - truth) / np.maximum(truth, floor)))
+
+
 def pass_algorithmic_bytes(m, n, b, cplx):
     """Bytes one Gram pass must move at least: A once (m n elements) and A W written once (m b)."""
     esz = 16 if cplx else 8
@@ -442,8 +450,7 @@ def run_ours(args, rank, world, local_rank):
     replicas.barrier(world)
     ms_total = replicas.max_over_ranks(ms_total, world, device=dev)
     sig_last = sigma.cpu().numpy().copy()
-    err_truth = float(np.max(np.abs(sig_last - truth[(args.steps - 1) % len(truth)]) /
-                             np.maximum(truth[(args.steps - 1) % len(truth)], 1e-300)))
+    err_truth = sigma_err(sig_last, truth[(args.steps - 1) % len(truth)], infos[-1].sigma11)
 
     # mixed-precision form (FP32 sketch and R) on the same matrices, beside the plain form
     mixed = None
@@ -461,7 +468,7 @@ def run_ours(args, rank, world, local_rank):
                  "per_iteration_ms": statistics.mean(x.ms_iterate / max(x.iters, 1) for x in minfos),
                  "phase_ms": {"sketch": statistics.mean(x.ms_sketch for x in minfos),
                               "factor": statistics.mean(x.ms_factor for x in minfos)},
-                 "sigma_rel_err_vs_planted": float(np.max(np.abs(ms_sig - tr) / np.maximum(tr, 1e-300)))}
+                 "sigma_rel_err_vs_planted": sigma_err(ms_sig, tr, minfos[-1].sigma11)}
         for p in mplans:
             rl.rlobpcg_plan_destroy(p)
 

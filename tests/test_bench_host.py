@@ -11,6 +11,7 @@ import hashlib
 import os
 import sys
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -88,3 +89,11 @@ def test_single_thread_oracle_sample_runs_in_a_fresh_interpreter():
     one = bench.oracle_rate_one_thread("small_4000x50", 5, timeout=240)
     assert one is not None and one[0] > 0 and one[1] > 0
     assert bench.oracle_rate_one_thread("no_such_workload", 5, timeout=120) is None
+
+
+def test_sigma_error_is_relative_and_floored_for_a_nullspace():
+    # planted values well above the floor: plain relative error
+    assert bench.sigma_err([1.0e-10 * (1 + 1e-6)], np.array([1.0e-10]), 1.0) == pytest.approx(1e-6)
+    # an exact nullspace (sigma_true = 0): the error in units of Sigma~(1,1) 2^-52, finite
+    e = bench.sigma_err([3.0 * 2.0 ** -52], np.array([0.0]), 1.0)
+    assert e == pytest.approx(3.0)
