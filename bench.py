@@ -367,7 +367,8 @@ def gram_roofline(m, n, b, cplx, split, t_pass_s, peaks, fp64_peak_tf, fp64_peak
     t_hbm, t_tc = by / (hbm * 1e9), fl / (tc * 1e12)
     main, other = (tc_obj, hbm_obj) if t_tc > t_hbm else (hbm_obj, tc_obj)
     out = dict(main)
-    out.update({"kernel": "split-bf16 Gram pass (gram_tc.cu: split of W, A W and A^T (A W) on tcgen05)"
+    out.update({"kernel": "split-bf16 Gram pass (gram_tc.cu: split of W, A W and A^T (A W) on tcgen05; A^T (A W) "
+                          "on all SMs but those left to the TSQR merges and the Rayleigh-Ritz SVD beside it)"
                 + ("; complex128 through its real view (gram_split_c.cu)" if cplx else ""),
                 "ms_per_pass": t_pass_s * 1e3, "roof_ms": max(t_hbm, t_tc) * 1e3,
                 "other": other})

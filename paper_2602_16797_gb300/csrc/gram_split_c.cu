@@ -84,11 +84,13 @@ size_t split_work_bytes_c128(int64_t m, int64_t n, int b) {
 }
 
 // prep: the real split of B (split_prepare of A read as doubles, m x 2n, leading dimension 2 lda).
-// flags: split::SPLIT_RESID (G = A^H AW for the AW given) or 0; W digits are always formed here.
+// flags: split::SPLIT_RESID (G = A^H AW for the AW given), SPLIT_FIRST_ONLY / SPLIT_SECOND_ONLY and
+// the reserved SMs of the real pass; W digits are always formed here.
 int split_gram_c128(const void* prep, int64_t m, int64_t n, const cd* W, int b, int64_t ldw, cd* AW, int64_t ldaw,
                     cd* G, int64_t ldg, void* work, size_t work_bytes, int flags, int* err, cudaEvent_t mid,
                     cudaStream_t st) {
   const bool resid_mode = (flags & split::SPLIT_RESID) != 0;
+  const bool first = (flags & split::SPLIT_SECOND_ONLY) == 0, second = (flags & split::SPLIT_FIRST_ONLY) == 0;
   if (!prep || !AW || !G || !work || m < 1 || n < 1 || b < 1 || 2 * b > 24 || ldaw < b || ldg < b ||
       (!resid_mode && (!W || ldw < b)))
     return RLOBPCG_ERR_INVALID_ARG;
@@ -98,14 +100,18 @@ int split_gram_c128(const void* prep, int64_t m, int64_t n, const cd* W, int b, 
   unsigned char* wk = (unsigned char*)work;
   double* Wr = (double*)(wk + L.wr);
   double* Gr = (double*)(wk + L.gr);
-  if (!resid_mode) {
+  if (!resid_mode && first) {
     cplx_w_kernel<<<blocks_of(n * b), 256, 0, st>>>(W, (int)n, b, ldw, Wr);
     RL_CHECK_LAUNCH();
   }
+  const int pass_flags =
+      flags & (split::SPLIT_RESID | split::SPLIT_FIRST_ONLY | split::SPLIT_SECOND_ONLY | split::split_reserve_flag(255));
   RL_TRY(split_gram(prep, m, 2 * n, Wr, 2 * b, 2 * b, (double*)AW, 2 * ldaw, Gr, 2 * b, wk + L.real,
-                    work_bytes - L.real, resid_mode ? split::SPLIT_RESID : 0, err, mid, st));
-  cplx_g_kernel<<<blocks_of(n * b), 256, 0, st>>>(Gr, (int)n, b, G, ldg);
-  RL_CHECK_LAUNCH();
+                    work_bytes - L.real, pass_flags, err, mid, st));
+  if (second) {
+    cplx_g_kernel<<<blocks_of(n * b), 256, 0, st>>>(Gr, (int)n, b, G, ldg);
+    RL_CHECK_LAUNCH();
+  }
   return RLOBPCG_OK;
 }
 

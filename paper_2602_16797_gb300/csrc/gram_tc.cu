@@ -817,12 +817,15 @@ int split_gram_bp(const unsigned char* prep, int64_t m, int64_t n, const double*
                   int64_t ldaw, double* G, int64_t ldg, unsigned char* work, int flags, int* err,
                   cudaEvent_t mid, cudaStream_t st) {
   const bool resid_mode = (flags & SPLIT_RESID) != 0;
+  const bool first = (flags & split::SPLIT_SECOND_ONLY) == 0, second = (flags & split::SPLIT_FIRST_ONLY) == 0;
   const Dims d = dims_of(m, n);
   const PrepLayout P = prep_layout(m, n);
   const WorkLayout L = work_layout(m, n, b);
   uint16_t* Ysl = (uint16_t*)(work + L.ysl);
   int* H = (int*)(work + L.h);
-  if (!resid_mode) {
+  if (!first) {
+    // the second product alone
+  } else if (!resid_mode) {
     if (!(flags & SPLIT_W_READY)) {
       w_digits_kernel<BP><<<1, 512, 0, st>>>(W, (int)n, b, ldw, d.NKB, (uint16_t*)(work + L.wsl), (int*)(work + L.f),
                                             err);
@@ -842,20 +845,26 @@ int split_gram_bp(const unsigned char* prep, int64_t m, int64_t n, const double*
     RL_CHECK_LAUNCH();
   }
   if (mid) RL_CUDA(cudaEventRecord(mid, st));
+  if (!second) return RLOBPCG_OK;
+  // row ranges per column tile: fewer when SMs are to be left free for another stream (the
+  // partials of the ranges are summed in range order either way)
+  const int reserve = (flags >> 16) & 0xff;
+  const int NR = (int)std::max<int64_t>(
+      1, std::min<int64_t>(L.NR, (num_sms() - reserve) / std::max<int64_t>(1, d.CT)));
   PassArgs a{};
   a.Aop = prep + P.act;
   a.Bop = Ysl;
   a.eA = (const int*)(prep + P.ecol);
   a.eB = H;
   a.m = m; a.R1 = d.R1; a.NKB = d.NKB; a.CT = d.CT; a.NC = d.NC;
-  a.b = b; a.NR = L.NR;
+  a.b = b; a.NR = NR;
   a.part = (double*)(work + L.part);
   a.G = G;
   a.ldg = ldg;
   a.n = n;
   a.cnt = (int*)(prep + P.cnt);
   a.err = err;
-  RL_TRY((launch_pass<BP, 1>(a, (int)(d.CT * L.NR), st)));
+  RL_TRY((launch_pass<BP, 1>(a, (int)(d.CT * NR), st)));
   return RLOBPCG_OK;
 }
 

@@ -2038,8 +2038,34 @@ size_t tsqr_workspace_bytes(int64_t m, int c, size_t esz) {
   return 2 * (((size_t)g1 * c * c * esz + 255) & ~(size_t)255);
 }
 
+static int tsqr_fan(int c, size_t esz) {
+  return (int)imax<int64_t>(2, imin<int64_t>(kTsqrFan, (int64_t)(max_smem_optin() * 9 / 10) / ((int64_t)c * c * esz)));
+}
+
+// CTAs of the first merge level (0 when the level kernel leaves a single R)
+int tsqr_merge1_ctas(int64_t m, int c, size_t esz) {
+  const int64_t g1 = tsqr_level1_ctas(m, c, esz);
+  const int64_t rpc = (m + g1 - 1) / g1;
+  const int64_t grid = (m + rpc - 1) / rpc;
+  if (grid <= 1) return 0;
+  const int fan = tsqr_fan(c, esz);
+  return (int)((grid + fan - 1) / fan);
+}
+
+// The level kernel on st; with mst, the merges (and the copy of R) on mst after lvl_done, so that
+// they can run beside other work of st.
+template <class T>
+int tsqr_split_impl(const T* X, int64_t m, int c, int64_t ldx, T* R, void* work, size_t work_bytes, cudaStream_t st,
+                    cudaStream_t mst, cudaEvent_t lvl_done);
+
 template <class T>
 int tsqr_impl(const T* X, int64_t m, int c, int64_t ldx, T* R, void* work, size_t work_bytes, cudaStream_t st) {
+  return tsqr_split_impl<T>(X, m, c, ldx, R, work, work_bytes, st, nullptr, nullptr);
+}
+
+template <class T>
+int tsqr_split_impl(const T* X, int64_t m, int c, int64_t ldx, T* R, void* work, size_t work_bytes, cudaStream_t st,
+                    cudaStream_t mst, cudaEvent_t lvl_done) {
   if (c < 1 || c > 64) return RLOBPCG_ERR_INVALID_ARG;
   const size_t esz = sizeof(T);
   if (work_bytes < tsqr_workspace_bytes(m, c, esz)) return RLOBPCG_ERR_INVALID_ARG;
@@ -2058,9 +2084,14 @@ int tsqr_impl(const T* X, int64_t m, int c, int64_t ldx, T* R, void* work, size_
   RL_TRY(allow_dynamic_smem(tsqr_level_kernel<T>, smem));
   tsqr_level_kernel<T><<<(int)grid, 256, smem, st>>>(X, m, c, ldx, rpc, CH, RP, buf[0]);
   RL_CHECK_LAUNCH();
+  if (mst) {
+    RL_CUDA(cudaEventRecord(lvl_done, st));
+    RL_CUDA(cudaStreamWaitEvent(mst, lvl_done, 0));
+    st = mst;
+  }
   int cur = 0;
   // fixed-order tree of triangular merges, up to kTsqrFan factors per CTA (balanced)
-  const int fan = (int)imax<int64_t>(2, imin<int64_t>(kTsqrFan, (int64_t)(max_smem_optin() * 9 / 10) / ((int64_t)c * c * esz)));
+  const int fan = tsqr_fan(c, esz);
   while (grid > 1) {
     const int64_t g2 = (grid + fan - 1) / fan;
     const int F = (int)((grid + g2 - 1) / g2);
@@ -2078,6 +2109,10 @@ int tsqr_impl(const T* X, int64_t m, int c, int64_t ldx, T* R, void* work, size_
 }
 template int tsqr_impl<double>(const double*, int64_t, int, int64_t, double*, void*, size_t, cudaStream_t);
 template int tsqr_impl<cd>(const cd*, int64_t, int, int64_t, cd*, void*, size_t, cudaStream_t);
+template int tsqr_split_impl<double>(const double*, int64_t, int, int64_t, double*, void*, size_t, cudaStream_t,
+                                     cudaStream_t, cudaEvent_t);
+template int tsqr_split_impl<cd>(const cd*, int64_t, int, int64_t, cd*, void*, size_t, cudaStream_t, cudaStream_t,
+                                 cudaEvent_t);
 
 template <class T>
 int rr_small_launch(const T* Rt, int c, int b, double* theta, T* K, size_t k_cap, int* info, cudaStream_t st) {

@@ -66,6 +66,10 @@ size_t tsqr_workspace_bytes(int64_t m, int c, size_t esz);
 template <class T>
 int tsqr_impl(const T* X, int64_t m, int c, int64_t ldx, T* R, void* work, size_t work_bytes, cudaStream_t st);
 template <class T>
+int tsqr_split_impl(const T* X, int64_t m, int c, int64_t ldx, T* R, void* work, size_t work_bytes, cudaStream_t st,
+                    cudaStream_t mst, cudaEvent_t lvl_done);
+int tsqr_merge1_ctas(int64_t m, int c, size_t esz);
+template <class T>
 int rr_small_launch(const T* Rt, int c, int b, double* theta, T* K, size_t k_cap, int* info, cudaStream_t st);
 template <class T>
 int update_launch(T* Tb, int64_t n, T* ATb, int64_t m, T* GTb, int64_t ld, int c, int b, const T* K, cudaStream_t st);
@@ -160,7 +164,12 @@ struct rlobpcg_plan_s {
   void* VL = nullptr;       // locked columns of V (n x b) and of A V (m x b), with locking
   void* AVL = nullptr;
   cudaEvent_t ev[10] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-  // Per-iteration Gram timing events (3 per slot, a ring) and the pinned history of residual
+  // Split Gram path: the TSQR merges and the Rayleigh-Ritz SVD of an iteration run on st2 beside
+  // the second split product, which leaves them the SMs they need (ev_lvl: TSQR level done on st;
+  // ev_rr: the SVD done on st2)
+  cudaStream_t st2 = nullptr;
+  cudaEvent_t ev_lvl = nullptr, ev_rr = nullptr;
+  // Per-iteration Gram timing events (4 per slot, a ring) and the pinned history of residual
   // norms and Ritz values, copied asynchronously; the host synchronises only to test the stop rule.
   std::vector<cudaEvent_t> gev;
   double* hist_h = nullptr;
@@ -203,6 +212,14 @@ void free_plan(rlobpcg_plan_s* p) {
   for (auto& e : p->gev)
     if (e) cudaEventDestroy(e);
   p->gev.clear();
+  if (p->st2) {
+    cudaStreamSynchronize(p->st2);
+    cudaStreamDestroy(p->st2);
+    p->st2 = nullptr;
+  }
+  if (p->ev_lvl) cudaEventDestroy(p->ev_lvl);
+  if (p->ev_rr) cudaEventDestroy(p->ev_rr);
+  p->ev_lvl = p->ev_rr = nullptr;
   if (p->hist_h) cudaFreeHost(p->hist_h);
   p->hist_h = nullptr;
 }
@@ -240,19 +257,22 @@ struct StopRule {
 };
 
 // One Gram pass: AW = A W and G = A^H AW (resid_mode: G = A^H AW for the given AW), on the FP64
-// CUDA cores or, for plans with gram_split, on the tensor cores from the digits of A.
+// CUDA cores or, for plans with gram_split, on the tensor cores from the digits of A. phase: 0,
+// or split::SPLIT_FIRST_ONLY / SPLIT_SECOND_ONLY (with reserved SMs) to run the split path's two
+// products as separate launches.
 template <class T>
 int gram_pass(rlobpcg_plan_s* p, const T* A, int64_t lda, const T* W, T* AW, T* G, int resid_mode,
-              cudaEvent_t mid = nullptr, bool w_ready = false, int bw = 0) {
+              cudaEvent_t mid = nullptr, bool w_ready = false, int bw = 0, int phase = 0) {
   const int64_t ld = 3 * p->b;
   if (bw <= 0) bw = p->b;   // block width (the active columns with locking)
   if (p->csplit)
     return split_gram_c128(p->sprep, p->m, p->n, (const cd*)W, bw, ld, (cd*)AW, ld, (cd*)G, ld, p->swork,
-                           p->swork_bytes, resid_mode ? split::SPLIT_RESID : 0, p->err, mid, p->st);
+                           p->swork_bytes, (resid_mode ? split::SPLIT_RESID : 0) | phase, p->err, mid, p->st);
   if (p->split)
     return split_gram(p->sprep, p->m, p->n, (const double*)W, bw, ld, (double*)AW, ld, (double*)G, ld, p->swork,
-                      p->swork_bytes, (resid_mode ? split::SPLIT_RESID : 0) | (w_ready ? split::SPLIT_W_READY : 0),
-                      p->err, mid, p->st);
+                      p->swork_bytes,
+                      (resid_mode ? split::SPLIT_RESID : 0) | (w_ready ? split::SPLIT_W_READY : 0) | phase, p->err,
+                      mid, p->st);
   return gram_dispatch(A, p->m, p->n, lda, p->dtype, W, bw, ld, AW, ld, G, ld, p->gwork, p->gwork_bytes, resid_mode,
                        p->err, p->st);
 }
@@ -444,22 +464,30 @@ int loop_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, SolveRun& r) {
   matvecs = b;
   theta_s = p->theta;
   int drained = 0;   // iterations whose history and timings the host has read
+  // the Gram pass of one iteration: e[0] -> e[2] on the FP64 path; on the split path the first
+  // product e[0] -> e[1] and the second e[3] -> e[2] (the TSQR level runs between them)
+  auto gram_time = [&](cudaEvent_t* e) -> int {
+    float gms = 0;
+    ++gram_passes;
+    if (!p->split) {
+      RL_CUDA(cudaEventElapsedTime(&gms, e[0], e[2]));
+      gram_ms += gms;
+      return RLOBPCG_OK;
+    }
+    RL_CUDA(cudaEventElapsedTime(&gms, e[0], e[1]));
+    gram_ab_ms += gms;
+    gram_ms += gms;
+    RL_CUDA(cudaEventElapsedTime(&gms, e[3], e[2]));
+    gram_atb_ms += gms;
+    gram_ms += gms;
+    return RLOBPCG_OK;
+  };
   auto drain = [&](int upto) -> int {
     for (int t = drained; t < upto; ++t) {
       const double* slot = p->hist_h + (size_t)(t + 1) * 2 * b;
       hist.r.emplace_back(slot, slot + b);
       hist.th.emplace_back(slot + b, slot + 2 * b);
-      cudaEvent_t* e = &p->gev[(size_t)(t % kRing) * 3];
-      float gms = 0;
-      RL_CUDA(cudaEventElapsedTime(&gms, e[0], e[2]));
-      gram_ms += gms;
-      ++gram_passes;
-      if (p->split) {
-        RL_CUDA(cudaEventElapsedTime(&gms, e[0], e[1]));
-        gram_ab_ms += gms;
-        RL_CUDA(cudaEventElapsedTime(&gms, e[1], e[2]));
-        gram_atb_ms += gms;
-      }
+      RL_TRY(gram_time(&p->gev[(size_t)(t % kRing) * 4]));
     }
     drained = upto;
     return RLOBPCG_OK;
@@ -488,15 +516,35 @@ int loop_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, SolveRun& r) {
     RL_TRY(bcgs2_orth_launch<T>(Tb, n, a, ld, a, nx, (T*)p->E, 2, st, rwd ? &wd : nullptr, p->err, &w_ready,
                                 p->coop, p->coop_bytes, p->opts.orth_mode, VL, nl, b));
     const int c = 2 * a + nx;
-    cudaEvent_t* e = &p->gev[(size_t)(i % kRing) * 3];
+    cudaEvent_t* e = &p->gev[(size_t)(i % kRing) * 4];
     RL_CUDA(cudaEventRecord(e[0], st));
-    // A W and A^H (A W) (the split path records the boundary between its two kernels in e[1])
-    RL_TRY(gram_pass<T>(p, A, lda, Tb + a, ATb + a, GTb + a, 0, p->split ? e[1] : nullptr, w_ready, a));
-    RL_CUDA(cudaEventRecord(e[2], st));
-    // Rayleigh-Ritz by SVD of A_T (TSQR + Jacobi of R_T). Running it on a second stream beside
-    // the A^T (A W) kernel was measured slower on GB300 (both contend for the FP64 pipes).
-    RL_TRY(tsqr_impl<T>(ATb, m, c, ld, (T*)p->Rt, p->twork, p->twork_bytes, st));
-    RL_TRY(rr_small_launch<T>((const T*)p->Rt, c, a, p->theta, (T*)p->K, p->K_cap, p->info, st));
+    if (p->split) {
+      // A W, then the TSQR level of A_T = [A_V A_W A_X] over all SMs. The Rayleigh-Ritz step
+      // needs only A_T, so the TSQR merges and the SVD of R_T (chains of small single-CTA
+      // kernels) run on st2 while A^H (A W) runs on st on all but the SMs they need: a split
+      // kernel's CTA fills its SM's register file on two sub-partitions, so nothing else is ever
+      // placed beside it, and reserving the SMs is what lets the two run at the same time.
+      RL_TRY(gram_pass<T>(p, A, lda, Tb + a, ATb + a, GTb + a, 0, e[1], w_ready, a, split::SPLIT_FIRST_ONLY));
+      RL_TRY(tsqr_split_impl<T>(ATb, m, c, ld, (T*)p->Rt, p->twork, p->twork_bytes, st, p->st2, p->ev_lvl));
+      RL_TRY(rr_small_launch<T>((const T*)p->Rt, c, a, p->theta, (T*)p->K, p->K_cap, p->info, p->st2));
+      RL_CUDA(cudaEventRecord(p->ev_rr, p->st2));
+      // SMs left to the side chain: one per CTA of the first merge level, all of which launch at
+      // once (with fewer, they take SMs that the second product then waits for). A function of
+      // the shape only, so that the order of the partial sums, and the results, do not depend on
+      // timing.
+      const int reserve = std::max(1, tsqr_merge1_ctas(m, c, sizeof(T)));
+      RL_CUDA(cudaEventRecord(e[3], st));
+      RL_TRY(gram_pass<T>(p, A, lda, Tb + a, ATb + a, GTb + a, 0, nullptr, w_ready, a,
+                          split::SPLIT_SECOND_ONLY | split::split_reserve_flag(reserve)));
+      RL_CUDA(cudaEventRecord(e[2], st));
+      RL_CUDA(cudaStreamWaitEvent(st, p->ev_rr, 0));
+    } else {
+      RL_TRY(gram_pass<T>(p, A, lda, Tb + a, ATb + a, GTb + a, 0, nullptr, w_ready, a));
+      RL_CUDA(cudaEventRecord(e[2], st));
+      // Rayleigh-Ritz by SVD of A_T (TSQR + Jacobi of R_T)
+      RL_TRY(tsqr_impl<T>(ATb, m, c, ld, (T*)p->Rt, p->twork, p->twork_bytes, st));
+      RL_TRY(rr_small_launch<T>((const T*)p->Rt, c, a, p->theta, (T*)p->K, p->K_cap, p->info, st));
+    }
     matvecs += a;
     theta_s = p->theta + (c - a);
     RL_TRY(update_launch<T>(Tb, n, ATb, m, GTb, ld, c, a, (const T*)p->K, st));
@@ -531,19 +579,8 @@ int loop_impl(rlobpcg_plan_s* p, const T* A, int64_t lda, SolveRun& r) {
     }
     hist.r.push_back(r_cur);
     hist.th.push_back(th_cur);
-    {
-      float gms = 0;
-      RL_CUDA(cudaEventElapsedTime(&gms, e[0], e[2]));
-      gram_ms += gms;
-      ++gram_passes;
-      if (p->split) {
-        RL_CUDA(cudaEventElapsedTime(&gms, e[0], e[1]));
-        gram_ab_ms += gms;
-        RL_CUDA(cudaEventElapsedTime(&gms, e[1], e[2]));
-        gram_atb_ms += gms;
-      }
-      drained = i + 1;
-    }
+    RL_TRY(gram_time(e));
+    drained = i + 1;
     if (check && hist.check(i, sigma11, tau, stag)) {
       stop = RLOBPCG_STOP_CONVERGED;
       break;
@@ -917,9 +954,22 @@ extern "C" int rlobpcg_plan(rlobpcg_plan_t* out, int64_t m, int64_t n, int k, in
   for (auto& e : p->ev) {
     if (cudaEventCreate(&e) != cudaSuccess) { free_plan(p); delete p; return RLOBPCG_ERR_CUDA; }
   }
-  p->gev.assign((size_t)kRing * 3, nullptr);
+  p->gev.assign((size_t)kRing * 4, nullptr);
   for (auto& e : p->gev) {
     if (cudaEventCreate(&e) != cudaSuccess) { free_plan(p); delete p; return RLOBPCG_ERR_CUDA; }
+  }
+  if (p->split) {
+    int lo = 0, hi = 0;
+    if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&p->st2, cudaStreamNonBlocking, hi) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_lvl, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_rr, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      set_last_error("plan: side stream of the split Gram path", __FILE__, __LINE__);
+      free_plan(p);
+      delete p;
+      return RLOBPCG_ERR_CUDA;
+    }
   }
   {
     const int iters = std::max(o.max_iter, o.fixed_iters);

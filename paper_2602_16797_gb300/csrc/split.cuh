@@ -85,6 +85,10 @@ struct WDigits {
 // flags of split_gram
 constexpr int SPLIT_RESID = 1;    // G = A^T Y for the given Y = AW (no first product)
 constexpr int SPLIT_W_READY = 2;  // the digits of W are already in the work buffer
+constexpr int SPLIT_FIRST_ONLY = 4;    // only the first product (A W and its digits)
+constexpr int SPLIT_SECOND_ONLY = 8;   // only the second product, from the digits of A W in the work buffer
+// SMs the second product leaves free for other streams (bits 16..23 of the flags)
+constexpr int split_reserve_flag(int sms) { return (sms & 0xff) << 16; }
 
 }  // namespace split
 }  // namespace rl
