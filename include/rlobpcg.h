@@ -148,7 +148,11 @@ int rlobpcg_default_opts(rlobpcg_opts* opts);
  * as (m + n) * 3b plus d * n and n * n elements), so solve() itself allocates nothing unless it
  * is given host pointers. The workspace is stream-ordered (cudaMallocAsync on `stream`, from the
  * device's default memory pool), so creating a plan does not synchronise the device.
- * `stream` is a cudaStream_t (NULL = default stream).
+ * `stream` is a cudaStream_t (NULL = default stream). A plan on the tensor-core Gram path
+ * (gram_split) also creates a second, non-blocking stream of its own. Each iteration runs its
+ * TSQR merges and Rayleigh-Ritz SVD there, beside the second Gram product. That work starts after
+ * an event recorded on `stream`, and `stream` waits for its end before the iteration goes on, so
+ * to the caller the solve stays ordered on `stream`.
  * Errors: INVALID_ARG when k < 1, b < k, 3b > n, n > m, d < n, d < zeta or zeta < 1;
  * OOM when the workspace does not fit; CUDA for runtime failures.
  */
